@@ -1,0 +1,139 @@
+"""Voxel microstructure generators (inputs only).
+
+Boolean-sphere electrodes stand in for the stochastic anode structures of the
+paper's Sec. 2.1 (Laguerre tessellation + Gaussian random fields on spheres),
+whose fitted parameters are not available.  Each electrode slab is filled with
+spheres whose centres are uniform in the slab box and whose radii follow a
+given law; spheres are added until the solid fraction first reaches
+``1 - porosity``.  Voxel (t, y, z) is solid when its centre lies within a
+sphere radius of a sphere centre; spheres are clipped to their slab.
+"""
+import json
+import math
+import os
+
+import numpy as np
+
+E, G, K, L, CN, CP = 0, 1, 2, 3, 4, 5
+
+_MASK64 = (1 << 64) - 1
+
+
+class SplitMix64:
+    """SplitMix64 (Steele, Lea and Flood, OOPSLA 2014), written from its
+    published definition: a Weyl sequence with increment 0x9E3779B97F4A7C15
+    followed by the two xor-shift-multiply finalisation rounds."""
+
+    def __init__(self, seed):
+        self.state = int(seed) & _MASK64
+
+    def next_u64(self):
+        self.state = (self.state + 0x9E3779B97F4A7C15) & _MASK64
+        z = self.state
+        z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & _MASK64
+        z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & _MASK64
+        return z ^ (z >> 31)
+
+    def uniform(self):
+        """Double in [0, 1) from the top 53 bits."""
+        return (self.next_u64() >> 11) * (1.0 / 9007199254740992.0)
+
+    def normal(self):
+        """Standard normal by the Box-Muller transform (one value per call)."""
+        u1 = self.uniform()
+        u2 = self.uniform()
+        return math.sqrt(-2.0 * math.log(1.0 - u1)) * math.cos(2.0 * math.pi * u2)
+
+
+def _mix_seed(seed, stream):
+    return (int(seed) * 0x100000001B3 + int(stream) * 0x9E3779B97F4A7C15) & _MASK64
+
+
+def boolean_sphere_slab(nt, ny, nz, porosity, radius, seed, stream=0):
+    """Boolean-sphere solid indicator for one slab of shape (nt, ny, nz).
+
+    radius: ("uniform", rmin, rmax) or ("lognormal_mean", mean, sigma_log),
+    in voxel units.  For the log-normal law the mean of r is ``mean``, i.e.
+    mu_log = ln(mean) - sigma_log**2 / 2.
+    Returns (solid bool array, number of spheres, achieved solid fraction).
+    """
+    rng = SplitMix64(_mix_seed(seed, stream))
+    solid = np.zeros((nt, ny, nz), dtype=bool)
+    target = (1.0 - porosity) * solid.size
+    count = 0
+    nsph = 0
+    tc = np.arange(nt) + 0.5
+    yc = np.arange(ny) + 0.5
+    zc = np.arange(nz) + 0.5
+    while count < target:
+        ct = rng.uniform() * nt
+        cy = rng.uniform() * ny
+        cz = rng.uniform() * nz
+        if radius[0] == "uniform":
+            r = radius[1] + (radius[2] - radius[1]) * rng.uniform()
+        elif radius[0] == "lognormal_mean":
+            mu = math.log(radius[1]) - 0.5 * radius[2] ** 2
+            r = math.exp(mu + radius[2] * rng.normal())
+        else:
+            raise ValueError("unknown radius law %r" % (radius[0],))
+        t0, t1 = max(0, int(math.floor(ct - r))), min(nt, int(math.ceil(ct + r)) + 1)
+        y0, y1 = max(0, int(math.floor(cy - r))), min(ny, int(math.ceil(cy + r)) + 1)
+        z0, z1 = max(0, int(math.floor(cz - r))), min(nz, int(math.ceil(cz + r)) + 1)
+        nsph += 1
+        if t0 >= t1 or y0 >= y1 or z0 >= z1:
+            continue
+        d2 = ((tc[t0:t1, None, None] - ct) ** 2 + (yc[None, y0:y1, None] - cy) ** 2
+              + (zc[None, None, z0:z1] - cz) ** 2)
+        ball = d2 <= r * r
+        sub = solid[t0:t1, y0:y1, z0:z1]
+        count += int(np.count_nonzero(ball & ~sub))
+        sub |= ball
+    return solid, nsph, count / solid.size
+
+
+def full_cell(ny, nz, n_anode, n_sep, n_cathode, porosity_anode, porosity_cathode,
+              radius, seeds):
+    """Full cell label grid with one CN layer at t=0 and one CP layer at the end.
+
+    Layout along t: CN | anode (G spheres in E) | separator (E) | cathode (K
+    spheres in E) | CP.  ``seeds`` = (anode seed, cathode seed).
+    """
+    nt = n_anode + n_sep + n_cathode + 2
+    lab = np.full((nt, ny, nz), E, dtype=np.uint8)
+    lab[0] = CN
+    lab[-1] = CP
+    sa, _, _ = boolean_sphere_slab(n_anode, ny, nz, porosity_anode, radius, seeds[0], 1)
+    sc, _, _ = boolean_sphere_slab(n_cathode, ny, nz, porosity_cathode, radius, seeds[1], 2)
+    a0 = 1
+    lab[a0:a0 + n_anode][sa] = G
+    c0 = 1 + n_anode + n_sep
+    lab[c0:c0 + n_cathode][sc] = K
+    return lab
+
+
+def half_cell(ny, nz, n_anode, n_sep, n_foil, porosity_anode, radius, seed):
+    """Half cell: CN | anode (G spheres in E) | separator (E) | Li foil (L) | CP."""
+    nt = n_anode + n_sep + n_foil + 2
+    lab = np.full((nt, ny, nz), E, dtype=np.uint8)
+    lab[0] = CN
+    lab[-1] = CP
+    sa, _, _ = boolean_sphere_slab(n_anode, ny, nz, porosity_anode, radius, seed, 1)
+    lab[1:1 + n_anode][sa] = G
+    lab[1 + n_anode + n_sep:1 + n_anode + n_sep + n_foil] = L
+    return lab
+
+
+def slab_1d(phases, ny=1, nz=1):
+    """Label grid made of full layers: ``phases`` lists one label per t-layer."""
+    lab = np.empty((len(phases), ny, nz), dtype=np.uint8)
+    for t, p in enumerate(phases):
+        lab[t] = p
+    return lab
+
+
+def load_params(path=None):
+    """Load the parameter table (a JSON file of plain numbers)."""
+    if path is None:
+        path = os.path.join(os.path.dirname(__file__), "params.json")
+    with open(path) as f:
+        return json.load(f)
