@@ -1,0 +1,297 @@
+#!/usr/bin/env python3
+"""Benchmark of the full-order implicit step (the hot path) on one GB300.
+
+Workload (default): the 128x128x256-voxel full cell at h = 1 um (anode 112 |
+separator 32 | cathode 112 voxels + one collector layer at each end),
+Boolean-sphere electrodes with log-normal radii (mean 5 voxels, sigma_log 0.3)
+at porosity 0.30 (anode) / 0.35 (cathode), seeds (21, 22), charged at 2C with
+plating enabled, implicit Euler with dt = 1 s.  A *step* is one implicit Euler
+time step of that charge (Newton-Krylov with the multigrid preconditioner and
+the plating active-set passes), run through the C-ABI on resident device
+state.  Metric: simulated seconds per wall second.
+
+The first warm-up step switches the current on from rest; the timed steps
+continue the charge.  Inputs (state ~0.2 GB, operators ~1 GB) exceed the
+129 MB L2, so no flush is needed between steps.
+
+--impl reference times the FP64 CPU oracle (SciPy SuperLU Newton) on a bounded
+sample of the same workload: one step of a 258x8x8-voxel window cut from the
+same cell, per reported step, scaled to the full cell by voxel count.
+
+Multi-GPU: the full-order step does not shard in this build (replicas only):
+each rank runs its own copy of the workload and value = total simulated
+seconds of all ranks / max wall time.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "sim-s/wall-s full-order; ROM solves/s + p50/p99 vs FP64 plain, V err≤1e-6"
+UNIT = "sim-s/wall-s"
+
+
+def workload_labels(name):
+    import synthetic as syn
+    if name == "cell128x128x256":
+        return syn.full_cell(128, 128, 112, 32, 112, 0.30, 0.35, ("lognormal_mean", 5, 0.3), (21, 22))
+    if name == "cell16x16x48":
+        return syn.full_cell(16, 16, 20, 8, 20, 0.35, 0.35, ("uniform", 2, 4), (11, 12))
+    if name == "cell64x64x128":
+        return syn.full_cell(64, 64, 53, 22, 53, 0.35, 0.35, ("uniform", 2, 4), (31, 32))
+    raise SystemExit("unknown workload %s" % name)
+
+
+CRATE = {"cell128x128x256": -2.0, "cell16x16x48": -1.0, "cell64x64x128": -2.0}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    if ws <= 1:
+        return 0, 0, 1, None
+    import torch.distributed as dist
+    rank = int(os.environ["RANK"]); local = int(os.environ.get("LOCAL_RANK", rank))
+    backend = "nccl"
+    import torch
+    torch.cuda.set_device(local)
+    dist.init_process_group(backend)
+    return rank, local, ws, dist
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle sampling every 200 ms during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except FileNotFoundError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm = [float(r[0]) for r in self.rows if r and r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if len(r) > 1 and r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in self.rows:
+            for k, nm in enumerate(names):
+                if len(r) > 4 + k and r[4 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(self.rows)}
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def jvp_traffic(workload):
+    """DRAM bytes per JVP launch from the committed ncu summary, or None."""
+    path = os.path.join(ROOT, "profiles", "k_jvp_mixed__%s.json" % workload)
+    try:
+        with open(path) as f:
+            return float(json.load(f)["dram_bytes_per_launch"])
+    except Exception:
+        return None
+
+
+def oracle_sample(labels, params, crate_sign, nsteps=1):
+    """Oracle (FP64, SciPy SuperLU) on a 258x8x8 window of the workload cell:
+    returns (sim-s/wall-s scaled to the full cell, seconds, sample text)."""
+    import synthetic.geometry as geo
+    from oracle.fom import Cell as OCell
+    win = geo.percolating(np.ascontiguousarray(labels[:, :8, :8]))
+    oc = OCell(win, 1e-6, params)
+    u = oc.initial_state()
+    I = crate_sign * oc.i_1c
+    t0 = time.perf_counter()
+    for _ in range(nsteps):
+        u, _ = oc.step(u, 1.0, I)
+    wall = time.perf_counter() - t0
+    scale = win.size / labels.size
+    return (nsteps * 1.0 / wall) * scale, wall, ("%d oracle step(s) of a %dx8x8 window (%d voxels) of the %s cell, "
+                                                  "scaled by voxel count %d/%d" %
+                                                  (nsteps, win.shape[0], win.size, "workload", win.size, labels.size))
+
+
+def run_reference(args):
+    rank, local, ws, dist = _dist()
+    if rank != 0:
+        return
+    import synthetic as syn
+    params = syn.load_params()
+    labels = workload_labels(args.workload)
+    cores = 1
+    vals = []
+    for _ in range(args.warmup):
+        oracle_sample(labels, params, np.sign(CRATE[args.workload]))
+    t_all = 0.0
+    for _ in range(args.steps):
+        v, wall, sample = oracle_sample(labels, params, np.sign(CRATE[args.workload]))
+        vals.append(v)
+        t_all += wall
+    value = float(np.mean(vals))
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * t_all / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "config": {"workload": args.workload, "dt_s": 1.0, "crate": CRATE[args.workload]},
+           "cpu_baseline": {"kind": "oracle", "value": value, "unit": UNIT, "cores": cores, "sample": sample},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="cell128x128x256")
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    rank, local, ws, dist = _dist()
+    torch.cuda.set_device(local)
+    import synthetic as syn
+    from paper_1704_04139_gb300 import binding as B
+    if not os.path.exists(B.LIB_PATH):
+        from paper_1704_04139_gb300 import build
+        build.build()
+    params = syn.load_params()
+    labels = workload_labels(args.workload)
+    prec = B.PREC_MIXED if args.precision == "mixed" else B.PREC_FP64
+    opts = B.default_opts(precision=prec, newton_tol=1e-9, krylov_rtol=1e-4 if prec else 1e-6,
+                          newton_maxit=20, krylov_maxit=300, max_halvings=3)
+    cell = B.Cell(labels, 1e-6, params, opts)
+    I = CRATE[args.workload] * cell.i_1c
+    dt = 1.0
+    for _ in range(args.warmup):
+        cell.step(dt, I)
+    stream = torch.cuda.ExternalStream(cell.stream_ptr())
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(torch.cuda.current_device())
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    cell.prof_enable(True)
+    l0 = cell.launch_count()
+    clocks.start()
+    ev0.record(stream)
+    infos = []
+    for _ in range(args.steps):
+        infos.append(cell.step(dt, I))
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    launches = cell.launch_count() - l0
+    ms = ev0.elapsed_time(ev1)
+    n_jvp, ms_jvp = cell.prof_read(B.Cell.PROF_JVP)
+    n_res, ms_res = cell.prof_read(B.Cell.PROF_RESIDUAL)
+    n_pc, ms_pc = cell.prof_read(B.Cell.PROF_PRECOND)
+    cell.prof_enable(False)
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        dist.barrier()
+    sim_s = args.steps * dt
+    value = ws * sim_s / (ms / 1000.0)
+
+    # end to end through the C-ABI with host buffers: state uploaded from
+    # pinned host memory before and read back after every step
+    u_host = torch.empty(cell.n, dtype=torch.float64).pin_memory().numpy()
+    u_host[:] = cell.state()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        cell.set_state(u_host)
+        cell.step(dt, I)
+        u_host[:] = cell.state()
+    e2e_wall = time.perf_counter() - t0
+    e2e = {"value": ws * args.e2e_steps * dt / e2e_wall, "unit": UNIT,
+           "h2d_bytes_per_step": 8 * cell.n, "d2h_bytes_per_step": 8 * cell.n}
+
+    # roofline of the dominant kernel: the JVP (Krylov operator and fine smoother)
+    peak, peak_kind = measured_peaks()
+    N, F = cell.N, cell.F
+    # compulsory bytes per launch: vcode 4 + FP32 (c, phi) 8 + FP64 direction 16 + FP64 result 16 per
+    # voxel; per plating face FP32 n 4 + gate 1 + FP64 direction 8 + FP64 result 8
+    bytes_per_launch = 44.0 * N + 21.0 * F
+    avg_jvp_ms = ms_jvp / max(n_jvp, 1)
+    achieved = bytes_per_launch / (avg_jvp_ms / 1000.0) / 1e9 if n_jvp else None
+    roof = {"kernel": "k_jvp<float,double> (mixed Krylov operator / fine smoother)", "bound": "hbm",
+            "achieved": achieved, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
+            "frac": (achieved / peak) if achieved else None, "traffic": jvp_traffic(args.workload),
+            "bytes_per_launch": bytes_per_launch, "launches": n_jvp, "avg_launch_ms": avg_jvp_ms,
+            "share_of_step": ms_jvp / ms if ms else None}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        v, wall, sample = oracle_sample(labels, params, np.sign(CRATE[args.workload]))
+        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample, "wall_s": wall}
+    if rank == 0:
+        out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+               "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+               "scaling": "weak", "vs_baseline": None,
+               "dtype": "f32+f64" if prec == B.PREC_MIXED else "f64", "data": "synthetic",
+               "config": {"workload": args.workload, "voxels": int(cell.N), "plating_faces": int(cell.F),
+                          "dt_s": dt, "crate": CRATE[args.workload], "precision": args.precision,
+                          "l2": "working set > 129 MB L2, no flush", "parallelism": "replicas" if ws > 1 else "1 GPU"},
+               "clocks": clk, "e2e": e2e, "gpu_launches": int(launches), "roofline": roof,
+               "cpu_baseline": cpu,
+               "solver": {"newton_its": [i["newton_its"] for i in infos], "krylov_its": [i["krylov_its"] for i in infos],
+                          "V_cell": infos[-1]["V_cell"], "precond_ms": ms_pc, "precond_calls": n_pc,
+                          "residual_ms": ms_res, "residual_calls": n_res}}
+        print(json.dumps(out))
+    cell.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

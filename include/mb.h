@@ -1,0 +1,170 @@
+/*
+ * mb.h -- C-ABI of libmb: GB300-native hot path of the MULTIBAT 3-D Li-ion
+ * cell model with lithium plating (arXiv:1704.04139).
+ *
+ * Every function returns an int status (MB_OK = 0, negative on error); the
+ * message of the last error of the calling thread is returned by
+ * mb_last_error().  Handles are opaque and owned by the library; every array
+ * argument is owned by the caller and only borrowed for the duration of the
+ * call.  Plain pointers are host pointers unless the function name ends in
+ * _dev, in which case they are device pointers of the current CUDA device and
+ * the work is enqueued on the given stream (a cudaStream_t passed as void*;
+ * NULL = the legacy default stream) and the call returns when that stream
+ * has completed it.  SI units throughout.
+ *
+ * State layout of a cell with N voxels and F plating faces (n = 2N + F):
+ *   u = [ c (N) | phi (N) | n_pl (F) ]
+ * Voxels are in [t][y][z] order with z fastest; t is the through-cell axis.
+ * Plating faces are all graphite-electrolyte faces, ordered by the graphite
+ * voxel's linear index, then by direction (-t, +t, -y, +y, -z, +z).
+ * Residual rows have the same layout: R = [ R_c | R_phi | R_n ].
+ *
+ * Phase labels: 0 electrolyte (E), 1 graphite anode (G), 2 cathode (K),
+ * 3 lithium foil (L), 4 negative collector (CN), 5 positive collector (CP).
+ *
+ * Sign convention: I_app > 0 delithiates the anode (the paper's delithiation
+ * current density mu, Sec. 3.2); a charge is I_app < 0.
+ */
+#ifndef MB_H
+#define MB_H
+
+#include <stdint.h>
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---- */
+#define MB_OK        0
+#define MB_EINVAL   -1   /* bad argument */
+#define MB_ENOMEM   -2   /* device memory exhausted / admission refused */
+#define MB_EBADGEOM -3   /* forbidden phase contact (e.g. anode touching cathode) */
+#define MB_ENOCONV  -4   /* Newton did not converge after all step halvings */
+#define MB_ECUTOFF  -5   /* step completed, voltage limit reached */
+#define MB_ETIMEOUT -6   /* a bounded device wait gave up */
+#define MB_EPENDING -7   /* serving: result not ready yet */
+#define MB_ECUDA    -8   /* CUDA runtime error */
+
+/* ---- parameter table (Sec. 2.2-2.3; values are placeholders, see params.json) ----
+ * U0(x) = ocp[0] + ocp[1] x + ocp[2] exp(-ocp[3] x) + ocp[4] tanh((x - ocp[5]) / ocp[6]),
+ * x = c / cmax.  n_c = Pl_layer_m / Pl_Vm_Li (mol/m^2). */
+typedef struct {
+    double F, R, T, clamp_rel;
+    double E_c0, E_D, E_kappa, E_tplus, E_tdf;
+    double G_cmax, G_D, G_sigma, G_i00, G_x0, G_ocp[7];
+    double K_cmax, K_D, K_sigma, K_i00, K_x0, K_ocp[7];
+    double L_sigma, L_i00;
+    double CN_sigma, CP_sigma;
+    double Pl_i00, Pl_layer_m, Pl_Vm_Li;
+} mb_params;
+
+#define MB_PREC_FP64  0   /* plain: FP64 residual, JVP and Krylov vectors */
+#define MB_PREC_MIXED 1   /* FP64 Newton residual; FP32 JVP/Krylov/preconditioner */
+
+typedef struct {
+    int    precision;      /* MB_PREC_FP64 or MB_PREC_MIXED */
+    double newton_tol;     /* stop when lam*||delta||_s <= tol (scaled max-norm) */
+    int    newton_maxit;   /* per active-set pass */
+    int    gmres_m;        /* FGMRES restart length */
+    int    krylov_maxit;   /* per Newton iteration */
+    double krylov_rtol;    /* relative residual reduction per linear solve */
+    int    max_passes;     /* plating active-set passes per step (>= 1) */
+    int    max_halvings;   /* dt halvings on Newton failure */
+    int    mg_coarse_cells;/* multigrid: coarsen until at most this many cells */
+    int    mg_smooth;      /* block-Jacobi sweeps per level, pre and post */
+} mb_solver_opts;
+
+typedef struct {
+    int    newton_its;     /* summed over passes and sub-steps */
+    int    krylov_its;
+    int    passes;
+    int    flips;          /* plating gates flipped between passes */
+    int    halvings;
+    double dt_used;
+    double V_cell;         /* mean Phi over the t = nt-1 collector layer (s_cp) */
+    double mean_c_solid;   /* mean graphite concentration (s_ac) */
+    double Li_total;       /* V * sum_{E,G,K} c + A * sum n  (mol) */
+    double Li_anode;       /* V * sum_G c + A * sum n (mol) */
+    double Li_plated;      /* A * sum n (mol) */
+    double res_norm;       /* final scaled max-norm of the FP64 residual */
+} mb_step_info;
+
+typedef struct {
+    int64_t n_vox, n_faces, n_unknowns;
+    int     nt, ny, nz;
+    double  h;
+    double  i_1c;          /* 1C current density: F V cmax_G (1-x0_G) n_G / 3600 s / (ny nz h^2) */
+    int64_t count[6];      /* voxels per phase label */
+    int64_t device_bytes;  /* device memory held by the cell */
+} mb_cell_info;
+
+typedef struct mb_cell mb_cell;
+
+const char* mb_last_error(void);
+void mb_opts_default(mb_solver_opts* o);
+
+/* Geometry ingest and face classification (Sec. 2.4, Table interfaceCond).
+ * labels: host uint8[nt*ny*nz].  Sets the rest state (table concentrations,
+ * equilibrium potentials, no plated Li).  MB_EBADGEOM on a G-K, G-CP, K-CN,
+ * K-L or CN-CP contact. */
+int mb_cell_create(const uint8_t* labels, int nt, int ny, int nz, double h,
+                   const mb_params* p, const mb_solver_opts* o, mb_cell** out);
+int mb_cell_destroy(mb_cell* cell);
+int mb_cell_info_get(mb_cell* cell, mb_cell_info* info);
+/* kinetic scales of the parameter study: exchange-current scale s_i0 (both
+ * electrodes' Butler-Volmer prefactors) and plating rate scale k_pl. */
+int mb_cell_set_scales(mb_cell* cell, double s_i0, double k_pl);
+int mb_cell_set_opts(mb_cell* cell, const mb_solver_opts* o);
+/* plating face list: graphite voxel, electrolyte voxel, direction 0..5 (host int32[F] each) */
+int mb_plating_faces(mb_cell* cell, int32_t* g, int32_t* e, int32_t* dir);
+
+/* State u (host double[n]) in the layout above. */
+int mb_state_get(mb_cell* cell, double* u);
+int mb_state_set(mb_cell* cell, const double* u);
+
+/* One implicit Euler step of Eq. (ap4:detailed): Newton-Krylov with the
+ * plating active-set passes; dt halved on failure up to max_halvings times.
+ * Returns MB_ENOCONV when every halving failed (state unchanged). */
+int mb_step(mb_cell* cell, double dt, double I_app, mb_step_info* info);
+
+/* FP64 residual R(u; u_old, dt, I_app) of Eq. (ap4:detailed) with plating
+ * gates gate (uint8[F], 1 = active; NULL = gates taken at u_old as mb_step
+ * does).  u, u_old, r: double[n]. */
+int mb_residual(mb_cell* cell, const double* u, const double* u_old, const uint8_t* gate,
+                double dt, double I_app, double* r);
+int mb_residual_dev(mb_cell* cell, const double* u, const double* u_old, const uint8_t* gate,
+                    double dt, double I_app, double* r, void* stream);
+
+/* Jacobian-vector product J(u) v of the residual above (analytic, no finite
+ * differences).  J does not depend on u_old or I_app.  FP64 variant:
+ * double[n] in/out; FP32 variant: float u, v, jv (the mixed-precision Krylov
+ * operator). */
+int mb_jvp(mb_cell* cell, const double* u, const uint8_t* gate, double dt,
+           const double* v, double* jv);
+int mb_jvp_dev(mb_cell* cell, const double* u, const uint8_t* gate, double dt,
+               const double* v, double* jv, void* stream);
+int mb_jvp_f32_dev(mb_cell* cell, const float* u, const uint8_t* gate, double dt,
+                   const float* v, float* jv, void* stream);
+
+/* Kernel timing and launch counting.  While enabled, every launch of the
+ * timed kernel classes below is bracketed by CUDA events recorded on the
+ * stream it is launched on; mb_prof_read returns the number of timed
+ * launches and their summed device time (ms) since the last enable/reset.
+ * mb_launch_count returns the number of kernels the library has launched
+ * for this cell since its creation (always counted). */
+#define MB_PROF_JVP      0   /* Jacobian-vector product kernel (Krylov operator and smoother) */
+#define MB_PROF_RESIDUAL 1   /* FP64 residual kernel */
+#define MB_PROF_PRECOND  2   /* one whole preconditioner application (many kernels) */
+int mb_prof_enable(mb_cell* cell, int on);
+int mb_prof_read(mb_cell* cell, int kind, int64_t* count, double* total_ms);
+int mb_prof_reset(mb_cell* cell);
+int mb_launch_count(mb_cell* cell, int64_t* count);
+/* The CUDA stream (cudaStream_t, as void*) on which mb_step and the other
+ * host-pointer calls of this cell enqueue their work. */
+int mb_cell_stream(mb_cell* cell, void** stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MB_H */

@@ -1,0 +1,45 @@
+/*
+ * mb_debug.h -- inspection hooks of libmb's Newton-Krylov preconditioner,
+ * used by the test suite to check each stage against an independent
+ * reference.  Not needed by applications.  Host pointers throughout; every
+ * call synchronises.
+ */
+#ifndef MB_DEBUG_H
+#define MB_DEBUG_H
+
+#include "mb.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Assemble the preconditioner at state u (double[n], converted to FP32) for
+ * step dt with plating gates gate (uint8[F]) and apply it to r (double[n],
+ * the scaled Krylov residual): z = M^-1 r. */
+int mb_debug_precond(mb_cell* cell, const double* u, const uint8_t* gate, double dt, const double* r,
+                     double* z);
+
+/* Number of coarse levels and the grid of level l (1-based). */
+int mb_debug_levels(mb_cell* cell, int* nlev);
+int mb_debug_level_dims(mb_cell* cell, int level, int* nt, int* ny, int* nz);
+
+/* Copy level l's operator after mb_debug_precond: aself float[cells*16]
+ * (4x4 self block per coarse cell, row-major, classes: 0 electrolyte c,
+ * 1 electrolyte phi, 2 anode-side phi, 3 cathode-side phi), off
+ * float[cells*96] (six outgoing 4x4 blocks in direction order -t,+t,-y,+y,
+ * -z,+z), mask uint8[cells] (classes present). */
+int mb_debug_level_op(mb_cell* cell, int level, float* aself, float* off, uint8_t* mask);
+
+/* Fine level after mb_debug_precond: dinv float[4N] (inverse of the scaled
+ * condensed 2x2 (c, phi) diagonal block per voxel, row-major) and fc
+ * float[8F] (per plating face: scaled D_n, dR_n/dphi_g, dR_n/dc_e,
+ * dR_n/dphi_e, dR_phi(g)/dn, dR_c(e)/dn, dR_phi(e)/dn, unused) and rowdiag
+ * float[n] (magnitude of each row's diagonal entry of the scaled Jacobian,
+ * by which the Krylov rows are divided; mb_debug_precond's r and z are in
+ * those row-equilibrated units on input). */
+int mb_debug_fine(mb_cell* cell, float* dinv, float* fc, float* rowdiag);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MB_DEBUG_H */

@@ -147,6 +147,18 @@ class Cell:
                 itf[s][0].append(np.concatenate([ia[m1], ib[m2]]))
                 itf[s][1].append(np.concatenate([ib[m1], ia[m2]]))
         cat = lambda xs: np.concatenate(xs) if xs else np.zeros(0, np.int64)
+        # each collector present must touch electrode solid, else its potential
+        # floats and the applied current has no path (singular system)
+        for cc_, sol in ((CN, (G, L)), (CP, (K, L))):
+            if np.any(flat == cc_):
+                touch = False
+                for ax in range(3):
+                    sl_lo = [slice(None)] * 3; sl_hi = [slice(None)] * 3
+                    sl_lo[ax] = slice(0, -1); sl_hi[ax] = slice(1, None)
+                    la = lab[tuple(sl_lo)]; lb = lab[tuple(sl_hi)]
+                    touch |= bool(np.any(((la == cc_) & np.isin(lb, sol)) | ((lb == cc_) & np.isin(la, sol))))
+                if not touch:
+                    raise GeometryError("collector %d touches no electrode solid" % cc_)
         self.ee = (cat(ee_a), cat(ee_b))
         self.sd = (cat(sd_a), cat(sd_b), cat(sd_D), cat(sd_s))
         self.cd = (cat(cd_a), cat(cd_b), cat(cd_s))

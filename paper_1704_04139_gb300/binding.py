@@ -1,0 +1,290 @@
+"""ctypes binding of libmb (include/mb.h): argument marshalling only.
+
+Every computation runs in the CUDA library; there is no CPU fallback.  If
+libmb.so has not been built, importing the library raises ``RuntimeError``.
+Device-pointer variants accept torch CUDA tensors (their data_ptr is passed
+with torch's current stream).
+"""
+import ctypes as C
+import json
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libmb.so")
+
+MB_OK, MB_EINVAL, MB_ENOMEM, MB_EBADGEOM, MB_ENOCONV, MB_ECUTOFF, MB_ETIMEOUT, MB_EPENDING, MB_ECUDA = (
+    0, -1, -2, -3, -4, -5, -6, -7, -8)
+PREC_FP64, PREC_MIXED = 0, 1
+
+
+class MBError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("libmb error %d: %s" % (code, msg))
+        self.code = code
+
+
+class Params(C.Structure):
+    _fields_ = [(n, C.c_double) for n in (
+        "F", "R", "T", "clamp_rel", "E_c0", "E_D", "E_kappa", "E_tplus", "E_tdf",
+        "G_cmax", "G_D", "G_sigma", "G_i00", "G_x0")] + [("G_ocp", C.c_double * 7)] + [
+        (n, C.c_double) for n in ("K_cmax", "K_D", "K_sigma", "K_i00", "K_x0")] + [
+        ("K_ocp", C.c_double * 7)] + [(n, C.c_double) for n in (
+            "L_sigma", "L_i00", "CN_sigma", "CP_sigma", "Pl_i00", "Pl_layer_m", "Pl_Vm_Li")]
+
+
+class SolverOpts(C.Structure):
+    _fields_ = [("precision", C.c_int), ("newton_tol", C.c_double), ("newton_maxit", C.c_int),
+                ("gmres_m", C.c_int), ("krylov_maxit", C.c_int), ("krylov_rtol", C.c_double),
+                ("max_passes", C.c_int), ("max_halvings", C.c_int), ("mg_coarse_cells", C.c_int),
+                ("mg_smooth", C.c_int)]
+
+
+class StepInfo(C.Structure):
+    _fields_ = [("newton_its", C.c_int), ("krylov_its", C.c_int), ("passes", C.c_int),
+                ("flips", C.c_int), ("halvings", C.c_int), ("dt_used", C.c_double),
+                ("V_cell", C.c_double), ("mean_c_solid", C.c_double), ("Li_total", C.c_double),
+                ("Li_anode", C.c_double), ("Li_plated", C.c_double), ("res_norm", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class CellInfo(C.Structure):
+    _fields_ = [("n_vox", C.c_int64), ("n_faces", C.c_int64), ("n_unknowns", C.c_int64),
+                ("nt", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("h", C.c_double),
+                ("i_1c", C.c_double), ("count", C.c_int64 * 6), ("device_bytes", C.c_int64)]
+
+
+_lib = None
+P_u8 = C.POINTER(C.c_uint8)
+P_d = C.POINTER(C.c_double)
+P_i32 = C.POINTER(C.c_int32)
+VP = C.c_void_p
+
+
+def _declare(lib):
+    def fn(name, res, args):
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    fn("mb_last_error", C.c_char_p, [])
+    fn("mb_opts_default", None, [C.POINTER(SolverOpts)])
+    fn("mb_cell_create", C.c_int, [VP, C.c_int, C.c_int, C.c_int, C.c_double, C.POINTER(Params),
+                                   C.POINTER(SolverOpts), C.POINTER(VP)])
+    fn("mb_cell_destroy", C.c_int, [VP])
+    fn("mb_cell_info_get", C.c_int, [VP, C.POINTER(CellInfo)])
+    fn("mb_cell_set_scales", C.c_int, [VP, C.c_double, C.c_double])
+    fn("mb_cell_set_opts", C.c_int, [VP, C.POINTER(SolverOpts)])
+    fn("mb_plating_faces", C.c_int, [VP, VP, VP, VP])
+    fn("mb_state_get", C.c_int, [VP, VP])
+    fn("mb_state_set", C.c_int, [VP, VP])
+    fn("mb_step", C.c_int, [VP, C.c_double, C.c_double, C.POINTER(StepInfo)])
+    fn("mb_residual", C.c_int, [VP, VP, VP, VP, C.c_double, C.c_double, VP])
+    fn("mb_residual_dev", C.c_int, [VP, VP, VP, VP, C.c_double, C.c_double, VP, VP])
+    fn("mb_jvp", C.c_int, [VP, VP, VP, C.c_double, VP, VP])
+    fn("mb_jvp_dev", C.c_int, [VP, VP, VP, C.c_double, VP, VP, VP])
+    fn("mb_jvp_f32_dev", C.c_int, [VP, VP, VP, C.c_double, VP, VP, VP])
+    fn("mb_prof_enable", C.c_int, [VP, C.c_int])
+    fn("mb_prof_read", C.c_int, [VP, C.c_int, C.POINTER(C.c_int64), C.POINTER(C.c_double)])
+    fn("mb_prof_reset", C.c_int, [VP])
+    fn("mb_launch_count", C.c_int, [VP, C.POINTER(C.c_int64)])
+    fn("mb_cell_stream", C.c_int, [VP, C.POINTER(VP)])
+    # inspection hooks (include/mb_debug.h)
+    fn("mb_debug_precond", C.c_int, [VP, VP, VP, C.c_double, VP, VP])
+    fn("mb_debug_levels", C.c_int, [VP, C.POINTER(C.c_int)])
+    fn("mb_debug_level_dims", C.c_int, [VP, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)])
+    fn("mb_debug_level_op", C.c_int, [VP, C.c_int, VP, VP, VP])
+    fn("mb_debug_fine", C.c_int, [VP, VP, VP, VP])
+    return lib
+
+
+def lib():
+    """Load libmb.so (built by ``paper_1704_04139_gb300.build``)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libmb.so is not built (run paper_1704_04139_gb300/build.py); "
+                               "there is no CPU fallback")
+        _lib = _declare(C.CDLL(LIB_PATH))
+    return _lib
+
+
+def _check(rc):
+    if rc != MB_OK:
+        raise MBError(rc, lib().mb_last_error().decode())
+    return rc
+
+
+def params_from_dict(d):
+    p = Params()
+    p.F, p.R, p.T, p.clamp_rel = d["F"], d["R"], d["T"], d["clamp_rel"]
+    e = d["E"]; p.E_c0, p.E_D, p.E_kappa, p.E_tplus, p.E_tdf = e["c0"], e["D"], e["kappa"], e["tplus"], e["tdf"]
+    g = d["G"]; p.G_cmax, p.G_D, p.G_sigma, p.G_i00, p.G_x0 = g["cmax"], g["D"], g["sigma"], g["i00"], g["x0"]
+    p.G_ocp[:] = g["ocp"]
+    k = d["K"]; p.K_cmax, p.K_D, p.K_sigma, p.K_i00, p.K_x0 = k["cmax"], k["D"], k["sigma"], k["i00"], k["x0"]
+    p.K_ocp[:] = k["ocp"]
+    p.L_sigma, p.L_i00 = d["L"]["sigma"], d["L"]["i00"]
+    p.CN_sigma, p.CP_sigma = d["CN"]["sigma"], d["CP"]["sigma"]
+    p.Pl_i00, p.Pl_layer_m, p.Pl_Vm_Li = d["Pl"]["i00"], d["Pl"]["layer_m"], d["Pl"]["Vm_Li"]
+    return p
+
+
+def default_opts(**kw):
+    o = SolverOpts()
+    lib().mb_opts_default(C.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+def _ptr(a):
+    return a.ctypes.data_as(VP)
+
+
+def _stream_of(t):
+    import torch
+    return C.c_void_p(torch.cuda.current_stream(t.device).cuda_stream)
+
+
+class Cell:
+    """A voxel cell resident on the current CUDA device (mb_cell)."""
+
+    def __init__(self, labels, h, params, opts=None):
+        labels = np.ascontiguousarray(labels, dtype=np.uint8)
+        nt, ny, nz = labels.shape
+        self._p = params_from_dict(params) if isinstance(params, dict) else params
+        self._o = opts if opts is not None else default_opts()
+        h_ = VP()
+        _check(lib().mb_cell_create(_ptr(labels), nt, ny, nz, float(h), C.byref(self._p),
+                                    C.byref(self._o), C.byref(h_)))
+        self.h = h_
+        info = CellInfo()
+        _check(lib().mb_cell_info_get(self.h, C.byref(info)))
+        self.info = info
+        self.shape = (nt, ny, nz)
+        self.N = info.n_vox
+        self.F = info.n_faces
+        self.n = info.n_unknowns
+        self.i_1c = info.i_1c
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().mb_cell_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_scales(self, s_i0=1.0, k_pl=1.0):
+        _check(lib().mb_cell_set_scales(self.h, float(s_i0), float(k_pl)))
+
+    def set_opts(self, opts):
+        self._o = opts
+        _check(lib().mb_cell_set_opts(self.h, C.byref(opts)))
+
+    def plating_faces(self):
+        g = np.zeros(self.F, np.int32); e = np.zeros(self.F, np.int32); d = np.zeros(self.F, np.int32)
+        _check(lib().mb_plating_faces(self.h, _ptr(g), _ptr(e), _ptr(d)))
+        return g, e, d
+
+    def state(self):
+        u = np.empty(self.n)
+        _check(lib().mb_state_get(self.h, _ptr(u)))
+        return u
+
+    def set_state(self, u):
+        u = np.ascontiguousarray(u, dtype=np.float64)
+        assert u.shape == (self.n,)
+        _check(lib().mb_state_set(self.h, _ptr(u)))
+
+    def step(self, dt, I_app):
+        info = StepInfo()
+        _check(lib().mb_step(self.h, float(dt), float(I_app), C.byref(info)))
+        return info.as_dict()
+
+    def residual(self, u, u_old, dt, I_app, gate=None):
+        u = np.ascontiguousarray(u, np.float64); uo = np.ascontiguousarray(u_old, np.float64)
+        r = np.empty(self.n)
+        g = None if gate is None else np.ascontiguousarray(gate, np.uint8)
+        _check(lib().mb_residual(self.h, _ptr(u), _ptr(uo), None if g is None else _ptr(g),
+                                 float(dt), float(I_app), _ptr(r)))
+        return r
+
+    def jvp(self, u, v, dt, gate=None):
+        u = np.ascontiguousarray(u, np.float64); v = np.ascontiguousarray(v, np.float64)
+        out = np.empty(self.n)
+        g = None if gate is None else np.ascontiguousarray(gate, np.uint8)
+        _check(lib().mb_jvp(self.h, _ptr(u), None if g is None else _ptr(g), float(dt), _ptr(v), _ptr(out)))
+        return out
+
+    # kernel timing (CUDA events on the launching stream) and launch counting
+    PROF_JVP, PROF_RESIDUAL, PROF_PRECOND = 0, 1, 2
+
+    def prof_enable(self, on=True):
+        _check(lib().mb_prof_enable(self.h, 1 if on else 0))
+
+    def prof_read(self, kind):
+        n = C.c_int64(); ms = C.c_double()
+        _check(lib().mb_prof_read(self.h, int(kind), C.byref(n), C.byref(ms)))
+        return n.value, ms.value
+
+    def stream_ptr(self):
+        s = VP()
+        _check(lib().mb_cell_stream(self.h, C.byref(s)))
+        return s.value or 0
+
+    def launch_count(self):
+        n = C.c_int64()
+        _check(lib().mb_launch_count(self.h, C.byref(n)))
+        return n.value
+
+    # inspection hooks of the preconditioner (tests)
+    def debug_precond(self, u, gate, dt, r):
+        u = np.ascontiguousarray(u, np.float64); r = np.ascontiguousarray(r, np.float64)
+        g = np.ascontiguousarray(gate, np.uint8)
+        z = np.empty(self.n)
+        _check(lib().mb_debug_precond(self.h, _ptr(u), _ptr(g), float(dt), _ptr(r), _ptr(z)))
+        return z
+
+    def debug_levels(self):
+        n = C.c_int()
+        _check(lib().mb_debug_levels(self.h, C.byref(n)))
+        out = []
+        for l in range(1, n.value + 1):
+            a, b, c = C.c_int(), C.c_int(), C.c_int()
+            _check(lib().mb_debug_level_dims(self.h, l, C.byref(a), C.byref(b), C.byref(c)))
+            out.append((a.value, b.value, c.value))
+        return out
+
+    def debug_level_op(self, level):
+        dims = self.debug_levels()[level - 1]
+        cells = dims[0] * dims[1] * dims[2]
+        aself = np.empty((cells, 4, 4), np.float32); off = np.empty((cells, 6, 4, 4), np.float32)
+        mask = np.empty(cells, np.uint8)
+        _check(lib().mb_debug_level_op(self.h, level, _ptr(aself), _ptr(off), _ptr(mask)))
+        return dims, aself, off, mask
+
+    def debug_fine(self):
+        dinv = np.empty((self.N, 2, 2), np.float32); fc = np.empty((max(self.F, 1), 8), np.float32)
+        rowdiag = np.empty(self.n, np.float32)
+        _check(lib().mb_debug_fine(self.h, _ptr(dinv), _ptr(fc), _ptr(rowdiag)))
+        return dinv, fc[:self.F], rowdiag
+
+    # device-pointer variants (torch CUDA tensors)
+    def residual_dev(self, u, u_old, dt, I_app, r, gate=None):
+        _check(lib().mb_residual_dev(self.h, VP(u.data_ptr()), VP(u_old.data_ptr()),
+                                     None if gate is None else VP(gate.data_ptr()), float(dt),
+                                     float(I_app), VP(r.data_ptr()), _stream_of(u)))
+
+    def jvp_dev(self, u, v, dt, out, gate=None):
+        _check(lib().mb_jvp_dev(self.h, VP(u.data_ptr()), None if gate is None else VP(gate.data_ptr()),
+                                float(dt), VP(v.data_ptr()), VP(out.data_ptr()), _stream_of(u)))
+
+    def jvp_f32_dev(self, u, v, dt, out, gate):
+        _check(lib().mb_jvp_f32_dev(self.h, VP(u.data_ptr()), VP(gate.data_ptr()), float(dt),
+                                    VP(v.data_ptr()), VP(out.data_ptr()), _stream_of(u)))

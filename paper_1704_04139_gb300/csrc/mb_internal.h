@@ -1,0 +1,152 @@
+// mb_internal.h -- host-side structures shared by the libmb translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string>
+#include <vector>
+
+#include "../../include/mb.h"
+#include "mb_model.cuh"
+
+namespace mb {
+
+void set_error(const std::string& msg);
+int cuda_fail(cudaError_t e, const char* what);
+
+#define MB_CUDA(call)                                                   \
+    do {                                                                \
+        cudaError_t e_ = (call);                                        \
+        if (e_ != cudaSuccess) return ::mb::cuda_fail(e_, #call);       \
+    } while (0)
+
+#define MB_CUDA_LAUNCH(what)                                            \
+    do {                                                                \
+        cudaError_t e_ = cudaGetLastError();                            \
+        if (e_ != cudaSuccess) return ::mb::cuda_fail(e_, what);        \
+    } while (0)
+
+// Device buffer owned by a cell.
+struct DBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+};
+
+struct Precond;   // multigrid preconditioner (precond.cu)
+template <class T> struct Krylov;   // FGMRES workspace (solver.cu)
+
+// Kernel timing and launch counting (mb_prof_* in the C-ABI).  When enabled,
+// launches of the timed kernel classes are bracketed by CUDA events recorded
+// on the launching stream; every kernel launch of the library increments the
+// cell's launch counter whether or not timing is enabled.
+enum ProfKernel { PROF_JVP = 0, PROF_RESIDUAL = 1, PROF_PRECOND = 2, PROF_NKERNELS = 3 };
+struct Prof {
+    bool enabled = false;
+    std::vector<cudaEvent_t> pool;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> rec[PROF_NKERNELS];
+    size_t used = 0;
+    cudaEvent_t get();
+};
+
+// Reduction scratch (deterministic two-pass reductions).
+constexpr int RED_BLOCKS = 1216;      // 8 x 152 SMs
+constexpr int RED_THREADS = 256;
+
+}  // namespace mb
+
+struct mb_cell {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    mb::Dims D{};
+    mb::DevParams P{};
+    mb_params prm{};
+    mb_solver_opts opt{};
+    double s_i0 = 1.0, k_pl = 1.0;
+    double i_1c = 0.0;
+    int64_t count[6] = {0, 0, 0, 0, 0, 0};
+    int64_t n = 0;                 // unknowns 2N + F
+    int64_t device_bytes = 0;
+    std::vector<mb::DBuf> owned;
+
+    // geometry
+    uint32_t* vcode = nullptr;     // N
+    int32_t* pf_g = nullptr;       // F
+    int32_t* pf_e = nullptr;       // F
+    int8_t* pf_dir = nullptr;      // F
+
+    // state and Newton work (FP64)
+    double* u = nullptr;           // n
+    double* u_old = nullptr;       // n
+    double* u_pass = nullptr;      // n (start of the step, kept across halvings)
+    double* r = nullptr;           // n
+    double* du = nullptr;          // n
+    uint8_t* gate = nullptr;       // F
+    uint8_t* gate2 = nullptr;      // F
+    double* red = nullptr;         // RED_BLOCKS * 64 partials
+    double* red_out = nullptr;     // 64 results
+    double* h_red = nullptr;       // pinned host copy of results (64)
+
+    // mixed precision copies
+    float* u32 = nullptr;          // n (linearisation point)
+    float* rowdiag = nullptr;      // n: |diagonal| of the scaled Jacobian rows (Krylov equilibration)
+
+    mb::Precond* pc = nullptr;
+    mb::Krylov<double>* kd = nullptr;
+
+    mb::Prof prof;
+    int64_t launches = 0;          // kernel launches issued by the library for this cell
+};
+
+namespace mb {
+// count n launches; bracket timed launches with events when profiling is on
+inline void count_launch(mb_cell* c, int n = 1) { c->launches += n; }
+inline void prof_begin(mb_cell* c, cudaStream_t s, cudaEvent_t* ev) {
+    *ev = nullptr;
+    if (c->prof.enabled) {
+        *ev = c->prof.get();
+        cudaEventRecord(*ev, s);
+    }
+}
+inline void prof_end(mb_cell* c, cudaStream_t s, int kind, cudaEvent_t ev0) {
+    if (c->prof.enabled && ev0) {
+        cudaEvent_t ev1 = c->prof.get();
+        cudaEventRecord(ev1, s);
+        c->prof.rec[kind].push_back({ev0, ev1});
+    }
+}
+}  // namespace mb
+
+namespace mb {
+
+void* cell_alloc(mb_cell* c, size_t bytes);   // cudaMalloc + bookkeeping; nullptr on failure
+
+// ---- fom.cu launchers (all on c->stream) ----
+int launch_classify(mb_cell* c, const uint8_t* d_labels);
+int launch_init_state(mb_cell* c, double* u);
+template <class T>
+int launch_residual(mb_cell* c, const T* u, const double* u_old, const uint8_t* gate, double dt,
+                    double I_app, T* r, cudaStream_t s);
+// mode 0: J v;  1: S_r^-1 J S_u v (scaled units);  2: the scaled rows further divided by
+// the magnitude of their diagonal entry (the row-equilibrated Krylov operator)
+template <class TC, class TV>
+int launch_jvp(mb_cell* c, const TC* u, const uint8_t* gate, double dt, const TV* v, TV* jv,
+               cudaStream_t s, int mode = 0);
+int launch_gate(mb_cell* c, const double* u, const double* n_old, uint8_t* gate, cudaStream_t s);
+// scaled max norms: which = 0 unknown scale, 1 residual scale (needs dt)
+int scaled_maxnorm(mb_cell* c, const double* x, int which, double dt, double* out);
+int functionals(mb_cell* c, const double* u, mb_step_info* info);
+int count_diff_u8(mb_cell* c, const uint8_t* a, const uint8_t* b, int64_t n, int64_t* out);
+
+// ---- precond.cu ----
+int precond_create(mb_cell* c);
+void precond_destroy(mb_cell* c);
+// build at linearisation point u32 (float) for time step dt with gates
+int precond_setup(mb_cell* c, const float* u32, const uint8_t* gate, double dt);
+// z = M^{-1} r (FP64 vectors of length n, row-equilibrated Krylov units); uses the fine JVP at u32
+int precond_apply(mb_cell* c, const float* u32, const uint8_t* gate, double dt, const double* r,
+                  double* z);
+
+// ---- solver.cu ----
+int newton_step(mb_cell* c, double dt, double I_app, mb_step_info* info);
+void krylov_destroy(mb_cell* c);   // frees the host structs; buffers stay owned by the cell
+
+}  // namespace mb

@@ -1,0 +1,299 @@
+// mb_model.cuh -- device-side model of the voxel finite-volume operator.
+//
+// Per-face fluxes of the cell-centred finite volume scheme (Sec. 2.4) for the
+// transport equations of Sec. 2.2 (Eqs. cgr, phigr, cel, phiel), the
+// interface conditions of Eq. (interfaceCond) with the kinetics of
+// Eqs. (ise_gr), (ise_li) and the plating/stripping kinetics of Eq. (iplel)
+// with the regulariser f_pre of Sec. 2.3.  Everything is written from the
+// point of view of one voxel v and one neighbour w; the face's contribution
+// to v's rows is returned.  T is double (plain path, outer Newton residual)
+// or float (mixed-precision Krylov operator).
+#pragma once
+#include <stdint.h>
+#include <cuda_runtime.h>
+
+namespace mb {
+
+enum Phase : int { PE = 0, PG = 1, PK = 2, PL = 3, PCN = 4, PCP = 5 };
+
+// per-voxel code: bits 0-2 phase, bits 3-8 mask of electrolyte neighbours of a
+// graphite voxel (bit d = direction d), bits 9-31 index of its first plating face
+constexpr int VC_FBASE_SHIFT = 9;
+constexpr uint32_t VC_MAX_FACES = (1u << 23);
+__host__ __device__ inline int vc_phase(uint32_t c) { return int(c & 7u); }
+__host__ __device__ inline uint32_t vc_emask(uint32_t c) { return (c >> 3) & 63u; }
+__host__ __device__ inline uint32_t vc_fbase(uint32_t c) { return c >> VC_FBASE_SHIFT; }
+__device__ inline int opp_dir(int d) { return d ^ 1; }
+
+struct Dims {
+    int nt, ny, nz;
+    int64_t N;      // voxels
+    int64_t F;      // plating faces
+    int64_t syz;    // ny*nz
+};
+
+// Constants of the model with the voxel geometry folded in (A = h^2).
+struct DevParams {
+    double h, A, V;
+    double invF, f2;               // 1/F, F/(2RT)
+    double E_gD;                   // A D_E / h
+    double E_gk;                   // A kappa / h
+    double E_gm;                   // A 2 kappa (t+ - 1) (RT/F) TDF / h  (divided by c_a + c_b)
+    double E_tF;                   // t+ / F
+    double cmin[6];                // concentration clamp per phase
+    double cref[6];                // concentration scale per phase (1 where no c)
+    double gD[6];                  // A D_s / h for G, K
+    double gsig[6][6];             // A sigma_face / h for conductor pairs (harmonic mean)
+    double i00[6];                 // BV prefactor per solid phase (G, K: i00; L: i00_L)
+    double icmax[6];
+    double ocpG[7], ocpK[7];
+    double g_dir;                  // 2 A sigma_CN / h  (Dirichlet half-voxel ghost)
+    double Pl_i00, nc4;            // plating prefactor, n_c^4
+};
+
+__host__ __device__ inline bool is_conductor(int p) { return p != PE; }
+__host__ __device__ inline bool has_c(int p) { return p == PE || p == PG || p == PK; }
+
+template <class T> __device__ inline T tmax(T a, T b) { return a > b ? a : b; }
+
+template <class T>
+__device__ inline T ocp_val(const double* a, T x) {
+    return T(a[0]) + T(a[1]) * x + T(a[2]) * exp(-T(a[3]) * x) + T(a[4]) * tanh((x - T(a[5])) / T(a[6]));
+}
+template <class T>
+__device__ inline T ocp_der(const double* a, T x) {   // dU0/dx
+    T th = tanh((x - T(a[5])) / T(a[6]));
+    return T(a[1]) - T(a[2]) * T(a[3]) * exp(-T(a[3]) * x) + T(a[4]) / T(a[6]) * (T(1) - th * th);
+}
+
+// Interface current density from solid s into electrolyte e (A/m^2):
+// Butler-Volmer part ibv (Eq. ise_gr for G and K, Eq. ise_li for L) and the
+// plating part ipl (Eq. iplel, graphite faces with an active gate).
+template <class T>
+__device__ inline void interface_current(const DevParams& P, int ls, T cs, T ps, T ce, T pe, T nf,
+                                         bool gate, T s_i0, T k_pl, T& ibv, T& ipl) {
+    const T f2 = T(P.f2);
+    ipl = T(0);
+    if (ls == PL) {
+        ibv = T(2) * T(P.i00[PL]) * sinh(f2 * (ps - pe));
+        return;
+    }
+    T csa = tmax(cs, T(P.cmin[ls]));
+    T cea = tmax(ce, T(P.cmin[PE]));
+    T x = csa * T(P.icmax[ls]);
+    T U = ocp_val<T>(ls == PG ? P.ocpG : P.ocpK, x);
+    T eta = ps - U - pe;
+    ibv = T(2) * T(P.i00[ls]) * s_i0 * sqrt(csa * cea) * sinh(f2 * eta);
+    if (ls == PG && gate) {
+        T etap = ps - pe;
+        T np = tmax(nf, T(0));
+        T n4 = np * np * np * np;
+        T fpre = n4 / (T(P.nc4) + n4);
+        ipl = k_pl * T(P.Pl_i00) * sqrt(cea) * (fpre * exp(f2 * etap) - exp(-f2 * etap));
+    }
+}
+
+// Contribution of face (v, w) to v's rows R_c(v), R_phi(v); for a graphite
+// v next to electrolyte w also returns i_pl (for the face row R_n).
+template <class T>
+__device__ inline void face_residual(const DevParams& P, int lv, int lw, T cv, T pv, T cw, T pw,
+                                     T nf, bool gate, T s_i0, T k_pl, T& rc, T& rp, T& ipl_out) {
+    if (lv == PE && lw == PE) {
+        T S = tmax(cv, T(P.cmin[PE])) + tmax(cw, T(P.cmin[PE]));
+        T dc = cw - cv, dp = pw - pv;
+        T j = -T(P.E_gk) * dp - T(P.E_gm) * dc / S;        // A * current density
+        rc += -T(P.E_gD) * dc + T(P.E_tF) * j;
+        rp += j;
+    } else if (lv == lw && (lv == PG || lv == PK)) {
+        rc += -T(P.gD[lv]) * (cw - cv);
+        rp += -T(P.gsig[lv][lw]) * (pw - pv);
+    } else if (is_conductor(lv) && is_conductor(lw)) {
+        rp += -T(P.gsig[lv][lw]) * (pw - pv);
+    } else if (lw == PE && (lv == PG || lv == PK || lv == PL)) {
+        T ibv, ipl;
+        interface_current<T>(P, lv, cv, pv, cw, pw, nf, gate, s_i0, k_pl, ibv, ipl);
+        if (lv != PL) rc += T(P.A) * ibv * T(P.invF);
+        rp += T(P.A) * (ibv + ipl);
+        ipl_out = ipl;
+    } else if (lv == PE && (lw == PG || lw == PK || lw == PL)) {
+        T ibv, ipl;
+        interface_current<T>(P, lw, cw, pw, cv, pv, nf, gate, s_i0, k_pl, ibv, ipl);
+        rc -= T(P.A) * (ibv + ipl) * T(P.invF);
+        rp -= T(P.A) * (ibv + ipl);
+    }
+}
+
+// Partial derivatives of one face's contribution to v's rows with respect to
+// x = (c_v, phi_v, c_w, phi_w, n_f):  c[k] = d R_c(v)/d x_k, p[k] = d R_phi(v)/d x_k,
+// and for a graphite v next to electrolyte w, n[k] = d (i_pl/F)/d x_k (face row).
+template <class T>
+struct FaceJac {
+    T c[5], p[5], n[5];
+};
+
+template <class T>
+__device__ inline void interface_partials(const DevParams& P, int ls, T cs, T ps, T ce, T pe, T nf,
+                                          bool gate, T s_i0, T k_pl,
+                                          T& i_eta, T& i_cs, T& i_ce,
+                                          T& ip_eta, T& ip_ce, T& ip_n) {
+    const T f2 = T(P.f2);
+    ip_eta = ip_ce = ip_n = T(0);
+    if (ls == PL) {
+        i_eta = T(2) * T(P.i00[PL]) * f2 * cosh(f2 * (ps - pe));
+        i_cs = i_ce = T(0);
+        return;
+    }
+    T ms = cs >= T(P.cmin[ls]) ? T(1) : T(0);
+    T me = ce >= T(P.cmin[PE]) ? T(1) : T(0);
+    T csa = tmax(cs, T(P.cmin[ls]));
+    T cea = tmax(ce, T(P.cmin[PE]));
+    const double* a = ls == PG ? P.ocpG : P.ocpK;
+    T x = csa * T(P.icmax[ls]);
+    T eta = ps - ocp_val<T>(a, x) - pe;
+    T k0 = T(2) * T(P.i00[ls]) * s_i0;
+    T q = sqrt(csa * cea);
+    T sh = sinh(f2 * eta), ch = cosh(f2 * eta);
+    i_eta = k0 * q * f2 * ch;
+    i_cs = ms * (k0 * q / (T(2) * csa) * sh - i_eta * ocp_der<T>(a, x) * T(P.icmax[ls]));
+    i_ce = me * k0 * q / (T(2) * cea) * sh;
+    if (ls == PG && gate) {
+        T etap = ps - pe;
+        T ep = exp(f2 * etap), em = exp(-f2 * etap);
+        T np = tmax(nf, T(0));
+        T n2 = np * np, n4 = n2 * n2;
+        T den = T(P.nc4) + n4;
+        T fpre = n4 / den;
+        T dfpre = nf > T(0) ? T(4) * n2 * np * T(P.nc4) / (den * den) : T(0);
+        T k1 = k_pl * T(P.Pl_i00);
+        T rce = sqrt(cea);
+        ip_eta = k1 * rce * f2 * (fpre * ep + em);
+        ip_ce = me * k1 / (T(2) * rce) * (fpre * ep - em);
+        ip_n = k1 * rce * dfpre * ep;
+    }
+}
+
+template <class T>
+__device__ inline void face_jacobian(const DevParams& P, int lv, int lw, T cv, T pv, T cw, T pw,
+                                     T nf, bool gate, T s_i0, T k_pl, FaceJac<T>& J) {
+#pragma unroll
+    for (int k = 0; k < 5; ++k) { J.c[k] = T(0); J.p[k] = T(0); J.n[k] = T(0); }
+    if (lv == PE && lw == PE) {
+        T cmin = T(P.cmin[PE]);
+        T mv = cv >= cmin ? T(1) : T(0), mw = cw >= cmin ? T(1) : T(0);
+        T S = tmax(cv, cmin) + tmax(cw, cmin);
+        T iS = T(1) / S;
+        T dc = cw - cv;
+        T r = dc * iS * iS;
+        T gm = T(P.E_gm), gk = T(P.E_gk), tF = T(P.E_tF), gD = T(P.E_gD);
+        T jcv = gm * (iS + r * mv);       // d j / d c_v
+        T jcw = -gm * (iS - r * mw);      // d j / d c_w
+        J.p[0] = jcv; J.p[1] = gk; J.p[2] = jcw; J.p[3] = -gk;
+        J.c[0] = gD + tF * jcv; J.c[1] = tF * gk; J.c[2] = -gD + tF * jcw; J.c[3] = -tF * gk;
+    } else if (lv == lw && (lv == PG || lv == PK)) {
+        T gD = T(P.gD[lv]), gs = T(P.gsig[lv][lw]);
+        J.c[0] = gD; J.c[2] = -gD;
+        J.p[1] = gs; J.p[3] = -gs;
+    } else if (is_conductor(lv) && is_conductor(lw)) {
+        T gs = T(P.gsig[lv][lw]);
+        J.p[1] = gs; J.p[3] = -gs;
+    } else if (lw == PE && (lv == PG || lv == PK || lv == PL)) {
+        T i_eta, i_cs, i_ce, ip_eta, ip_ce, ip_n;
+        interface_partials<T>(P, lv, cv, pv, cw, pw, nf, gate, s_i0, k_pl, i_eta, i_cs, i_ce,
+                              ip_eta, ip_ce, ip_n);
+        T A = T(P.A), AF = T(P.A) * T(P.invF);
+        if (lv != PL) {
+            J.c[0] = AF * i_cs; J.c[1] = AF * i_eta; J.c[2] = AF * i_ce; J.c[3] = -AF * i_eta;
+        }
+        J.p[0] = A * i_cs; J.p[1] = A * (i_eta + ip_eta); J.p[2] = A * (i_ce + ip_ce);
+        J.p[3] = -A * (i_eta + ip_eta); J.p[4] = A * ip_n;
+        T iF = T(P.invF);
+        J.n[1] = iF * ip_eta; J.n[2] = iF * ip_ce; J.n[3] = -iF * ip_eta; J.n[4] = iF * ip_n;
+    } else if (lv == PE && (lw == PG || lw == PK || lw == PL)) {
+        T i_eta, i_cs, i_ce, ip_eta, ip_ce, ip_n;
+        interface_partials<T>(P, lw, cw, pw, cv, pv, nf, gate, s_i0, k_pl, i_eta, i_cs, i_ce,
+                              ip_eta, ip_ce, ip_n);
+        T A = T(P.A), AF = T(P.A) * T(P.invF);
+        T te = i_eta + ip_eta;
+        J.c[0] = -AF * (i_ce + ip_ce); J.c[1] = AF * te; J.c[2] = -AF * i_cs; J.c[3] = -AF * te;
+        J.c[4] = -AF * ip_n;
+        J.p[0] = -A * (i_ce + ip_ce); J.p[1] = A * te; J.p[2] = -A * i_cs; J.p[3] = -A * te;
+        J.p[4] = -A * ip_n;
+        // face row i_pl/F seen from the electrolyte side: x = (c_e, phi_e, c_g, phi_g, n)
+        T iF = T(P.invF);
+        J.n[0] = iF * ip_ce; J.n[1] = -iF * ip_eta; J.n[3] = iF * ip_eta; J.n[4] = iF * ip_n;
+    }
+}
+
+// Directional derivative of one face's contribution to v's rows, written so
+// that every conduction, diffusion and overpotential coupling multiplies a
+// difference of the direction's entries (g (dx_v - dx_w), i_eta (dPhi_s -
+// dphi_e)).  A uniform shift of a conductor's potential then produces an
+// exactly zero flux change even in FP32, which keeps the weakly pinned modes
+// (particles and electrolyte held only by Butler-Volmer conductances ~1e-6 of
+// the bulk ones) intact; multiplying absolute entries and subtracting would
+// leave rounding of the size of those conductances.  Also returns the
+// diagonal entries dR_c(v)/dc_v, dR_phi(v)/dphi_v of this face (dgc, dgp) and,
+// for a graphite v next to electrolyte w, the face row's change jn and its
+// diagonal d(i_pl/F)/dn (jnn, without the 1/dt of the storage term).
+// TC: precision of the state and of the nonlinear coefficients (sqrt, sinh,
+// cosh, exp, OCP, divisions); TV: precision of the direction, its
+// differences and the accumulated result.
+template <class TC, class TV>
+__device__ inline void face_jvp(const DevParams& P, int lv, int lw, TC cv, TC pv, TC cw, TC pw, TC nf, bool gate,
+                                TC s_i0, TC k_pl, TV dcv, TV dpv, TV dcw, TV dpw, TV dnf, TV& jc, TV& jp, TV& jn,
+                                TV& jnn, TV& dgc, TV& dgp) {
+    if (lv == PE && lw == PE) {
+        TC cmin = TC(P.cmin[PE]);
+        TC mv = cv >= cmin ? TC(1) : TC(0), mw = cw >= cmin ? TC(1) : TC(0);
+        TC S = tmax(cv, cmin) + tmax(cw, cmin);
+        TC iS = TC(1) / S;
+        TC dc = cw - cv;
+        TC r = dc * iS * iS;
+        TC gm = TC(P.E_gm), gk = TC(P.E_gk), tF = TC(P.E_tF), gD = TC(P.E_gD);
+        TV ddc = dcw - dcv, ddp = dpw - dpv;
+        // j = -gk dphi - gm dc/S ;  d(dc/S) = ddc/S - dc/S^2 (m_v dc_v + m_w dc_w)
+        TV dj = -TV(gk) * ddp - TV(gm) * (ddc * TV(iS) - TV(r) * (TV(mv) * dcv + TV(mw) * dcw));
+        jc += -TV(gD) * ddc + TV(tF) * dj;
+        jp += dj;
+        TC jcv = gm * (iS + r * mv);
+        dgc += TV(gD + tF * jcv);
+        dgp += TV(gk);
+    } else if (lv == lw && (lv == PG || lv == PK)) {
+        TV gD = TV(TC(P.gD[lv])), gs = TV(TC(P.gsig[lv][lw]));
+        jc += -gD * (dcw - dcv);
+        jp += -gs * (dpw - dpv);
+        dgc += gD;
+        dgp += gs;
+    } else if (is_conductor(lv) && is_conductor(lw)) {
+        TV gs = TV(TC(P.gsig[lv][lw]));
+        jp += -gs * (dpw - dpv);
+        dgp += gs;
+    } else if (lw == PE && (lv == PG || lv == PK || lv == PL)) {
+        TC i_eta, i_cs, i_ce, ip_eta, ip_ce, ip_n;
+        interface_partials<TC>(P, lv, cv, pv, cw, pw, nf, gate, s_i0, k_pl, i_eta, i_cs, i_ce, ip_eta, ip_ce, ip_n);
+        TV deta = dpv - dpw;
+        TV dibv = TV(i_eta) * deta + TV(i_cs) * dcv + TV(i_ce) * dcw;
+        TV dipl = TV(ip_eta) * deta + TV(ip_ce) * dcw + TV(ip_n) * dnf;
+        TV A = TV(TC(P.A)), AF = TV(TC(P.A) * TC(P.invF));
+        if (lv != PL) {
+            jc += AF * dibv;
+            dgc += AF * TV(i_cs);
+        }
+        jp += A * (dibv + dipl);
+        dgp += A * TV(i_eta + ip_eta);
+        jn = TV(TC(P.invF)) * dipl;
+        jnn = TV(TC(P.invF) * ip_n);
+    } else if (lv == PE && (lw == PG || lw == PK || lw == PL)) {
+        TC i_eta, i_cs, i_ce, ip_eta, ip_ce, ip_n;
+        interface_partials<TC>(P, lw, cw, pw, cv, pv, nf, gate, s_i0, k_pl, i_eta, i_cs, i_ce, ip_eta, ip_ce, ip_n);
+        TV deta = dpw - dpv;
+        TV di = TV(i_eta + ip_eta) * deta + TV(i_cs) * dcw + TV(i_ce + ip_ce) * dcv + TV(ip_n) * dnf;
+        TV A = TV(TC(P.A)), AF = TV(TC(P.A) * TC(P.invF));
+        jc -= AF * di;
+        jp -= A * di;
+        dgc += -AF * TV(i_ce + ip_ce);
+        dgp += A * TV(i_eta + ip_eta);
+    }
+}
+
+}  // namespace mb

@@ -1,0 +1,422 @@
+// solver.cu -- Newton-Krylov driver of one implicit Euler step (Eq.
+// ap4:detailed): scaled right-preconditioned flexible GMRES with classical
+// Gram-Schmidt and one re-orthogonalisation (dot products accumulated in
+// FP64, deterministic), the damped Newton update, the plating active-set
+// passes and step halving on failure.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <vector>
+
+#include "mb_internal.h"
+#include "mb_reduce.cuh"
+
+namespace mb {
+
+// MB_DEBUG=1 in the environment prints one line per Newton iteration to stderr.
+int debug_level() {
+    static int lvl = -1;
+    if (lvl < 0) {
+        const char* e = getenv("MB_DEBUG");
+        lvl = e ? atoi(e) : 0;
+    }
+    return lvl;
+}
+
+constexpr int MDOT_G = 8;   // dot products per launch
+
+struct HParam {
+    double h[64];
+};
+
+template <class T>
+struct Krylov {
+    int m = 0;
+    int64_t n = 0;
+    T* V = nullptr;      // (m+1) x n
+    T* Z = nullptr;      // m x n
+    T* w = nullptr;      // n
+    T* b = nullptr;      // n  right-hand side (scaled)
+    T* x = nullptr;      // n  solution (scaled)
+};
+
+// ------------------------------------------------------------ vector kernels
+template <class T>
+__global__ void __launch_bounds__(RED_THREADS)
+k_mdot(const T* __restrict__ V, int64_t stride, int cnt, const T* __restrict__ w, int64_t n,
+       double* partials) {
+    double acc[MDOT_G];
+#pragma unroll
+    for (int j = 0; j < MDOT_G; ++j) acc[j] = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        double wi = (double)w[i];
+#pragma unroll
+        for (int j = 0; j < MDOT_G; ++j)
+            if (j < cnt) acc[j] += (double)V[j * stride + i] * wi;
+    }
+    block_reduce_store<MDOT_G, false>(acc, partials);
+}
+
+template <class T>
+__global__ void k_mupdate(const T* __restrict__ V, int64_t stride, int cnt, HParam hp, T* __restrict__ w,
+                          int64_t n, double sign) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double acc = 0.0;
+    for (int j = 0; j < cnt; ++j) acc += hp.h[j] * (double)V[j * stride + i];
+    w[i] = (T)((double)w[i] + sign * acc);
+}
+
+template <class T>
+__global__ void k_scale(const T* __restrict__ a, double alpha, T* __restrict__ b, int64_t n) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) b[i] = (T)(alpha * (double)a[i]);
+}
+
+template <class A, class B>
+__global__ void k_convert(const A* __restrict__ a, B* __restrict__ b, int64_t n) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) b[i] = (B)a[i];
+}
+
+__global__ void k_axpy_d(double alpha, const double* __restrict__ x, double* __restrict__ y, int64_t n) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) y[i] += alpha * x[i];
+}
+
+// b_hat = -R / s_r / |diag|  (row-equilibrated right-hand side)
+template <class T>
+__global__ void k_scale_rhs(DevParams P, Dims D, const uint32_t* __restrict__ vc, const double* __restrict__ R,
+                            double dt_inv, const float* __restrict__ rowdiag, T* __restrict__ b) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int64_t n = 2 * D.N + D.F;
+    if (i >= n) return;
+    double s;
+    if (i < D.N) {
+        int l = vc_phase(vc[i]);
+        s = has_c(l) ? P.V * P.cref[l] * dt_inv : 1.0;
+    } else if (i < 2 * D.N) {
+        s = P.A;
+    } else {
+        s = sqrt(sqrt(P.nc4)) * dt_inv;
+    }
+    b[i] = (T)(-R[i] / (s * (double)rowdiag[i]));
+}
+
+// delta = s_u * x_hat
+template <class T>
+__global__ void k_unscale(DevParams P, Dims D, const uint32_t* __restrict__ vc, const T* __restrict__ x,
+                          double* __restrict__ d) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int64_t n = 2 * D.N + D.F;
+    if (i >= n) return;
+    double s;
+    if (i < D.N) s = P.cref[vc_phase(vc[i])];
+    else if (i < 2 * D.N) s = 1.0;
+    else s = sqrt(sqrt(P.nc4));
+    d[i] = s * (double)x[i];
+}
+
+static inline unsigned nblk(int64_t n) { return (unsigned)((n + 255) / 256); }
+
+// dots out[j] = <V_j, w> for j in [0, cnt)
+template <class T>
+static int mdot(mb_cell* c, const T* V, int64_t stride, int cnt, const T* w, int64_t n, double* out) {
+    cudaStream_t s = c->stream;
+    for (int j0 = 0; j0 < cnt; j0 += MDOT_G) {
+        int k = cnt - j0 < MDOT_G ? cnt - j0 : MDOT_G;
+        k_mdot<T><<<RED_BLOCKS, RED_THREADS, 0, s>>>(V + j0 * stride, stride, k, w, n, c->red), ::mb::count_launch(c);
+        k_reduce_final<false><<<k, RED_THREADS, 0, s>>>(c->red, k, c->red_out + j0), ::mb::count_launch(c);
+    }
+    MB_CUDA_LAUNCH("mdot");
+    MB_CUDA(cudaMemcpyAsync(c->h_red, c->red_out, 8 * cnt, cudaMemcpyDeviceToHost, s));
+    MB_CUDA(cudaStreamSynchronize(s));
+    memcpy(out, c->h_red, 8 * cnt);
+    return MB_OK;
+}
+
+template <class T>
+static int mupdate(mb_cell* c, const T* V, int64_t stride, int cnt, const double* h, T* w, int64_t n,
+                   double sign) {
+    for (int j0 = 0; j0 < cnt; j0 += 64) {
+        int k = cnt - j0 < 64 ? cnt - j0 : 64;
+        HParam hp;
+        for (int j = 0; j < k; ++j) hp.h[j] = h[j0 + j];
+        k_mupdate<T><<<nblk(n), 256, 0, c->stream>>>(V + j0 * stride, stride, k, hp, w, n, sign), ::mb::count_launch(c);
+    }
+    MB_CUDA_LAUNCH("mupdate");
+    return MB_OK;
+}
+
+// Krylov operator: the row-equilibrated scaled JVP at the current Newton
+// iterate.  FP64 path: coefficients from the FP64 state; mixed path: the
+// nonlinear per-face coefficients from the FP32 copy of the state, applied to
+// FP64 vectors.
+struct OpCtx {
+    const double* u64;
+    const float* u32;
+    bool mixed;
+    const uint8_t* gate;
+    double dt;
+};
+
+template <class T>
+static int apply_op(mb_cell* c, const OpCtx& o, const T* x, T* y) {
+    if (o.mixed) return launch_jvp<float, T>(c, o.u32, o.gate, o.dt, x, y, c->stream, 2);
+    return launch_jvp<double, T>(c, o.u64, o.gate, o.dt, x, y, c->stream, 2);
+}
+
+static int apply_prec(mb_cell* c, Krylov<double>* K, const OpCtx& o, const double* x, double* y) {
+    (void)K;
+    return precond_apply(c, o.u32, o.gate, o.dt, x, y);
+}
+
+// Flexible GMRES(m) on A x = b (x starts at zero), stopping at
+// ||b - A x||_2 <= rtol ||b||_2 or after maxit iterations.
+template <class T>
+static int fgmres(mb_cell* c, Krylov<T>* K, const OpCtx& o, double rtol, int maxit, int* its_out,
+                  double* relres_out) {
+    const int64_t n = K->n;
+    const int m = K->m;
+    cudaStream_t s = c->stream;
+    std::vector<double> H((m + 1) * m), cs(m), sn(m), g(m + 1), y(m), hv(m + 1), h2(m + 1);
+    MB_CUDA(cudaMemsetAsync(K->x, 0, n * sizeof(T), s));
+    double beta0 = 0.0;
+    {
+        double d;
+        int rc = mdot<T>(c, K->b, 0, 1, K->b, n, &d);
+        if (rc) return rc;
+        beta0 = sqrt(d);
+    }
+    *its_out = 0;
+    *relres_out = 0.0;
+    if (beta0 == 0.0) return MB_OK;
+    if (!(beta0 == beta0)) { set_error("non-finite Newton residual"); return MB_ENOCONV; }
+    int its = 0;
+    double relres = 1.0;
+    bool first = true;
+    while (its < maxit) {
+        // r = b - A x  (first cycle: r = b)
+        double beta;
+        if (first) {
+            k_scale<T><<<nblk(n), 256, 0, s>>>(K->b, 1.0, K->w, n), ::mb::count_launch(c);
+            beta = beta0;
+        } else {
+            int rc = apply_op<T>(c, o, K->x, K->w);
+            if (rc) return rc;
+            k_scale<T><<<nblk(n), 256, 0, s>>>(K->w, -1.0, K->w, n), ::mb::count_launch(c);
+            double one = 1.0;
+            HParam hp; hp.h[0] = one;
+            k_mupdate<T><<<nblk(n), 256, 0, s>>>(K->b, 0, 1, hp, K->w, n, 1.0), ::mb::count_launch(c);
+            double d;
+            rc = mdot<T>(c, K->w, 0, 1, K->w, n, &d);
+            if (rc) return rc;
+            beta = sqrt(d);
+        }
+        first = false;
+        k_scale<T><<<nblk(n), 256, 0, s>>>(K->w, 1.0 / beta, K->V, n), ::mb::count_launch(c);
+        std::fill(g.begin(), g.end(), 0.0);
+        g[0] = beta;
+        int j = 0;
+        for (; j < m && its < maxit; ++j) {
+            T* Vj = K->V + j * n;
+            T* Zj = K->Z + j * n;
+            int rc = apply_prec(c, K, o, Vj, Zj);
+            if (rc) return rc;
+            rc = apply_op<T>(c, o, Zj, K->w);
+            if (rc) return rc;
+            // CGS2
+            rc = mdot<T>(c, K->V, n, j + 1, K->w, n, hv.data());
+            if (rc) return rc;
+            rc = mupdate<T>(c, K->V, n, j + 1, hv.data(), K->w, n, -1.0);
+            if (rc) return rc;
+            rc = mdot<T>(c, K->V, n, j + 1, K->w, n, h2.data());
+            if (rc) return rc;
+            rc = mupdate<T>(c, K->V, n, j + 1, h2.data(), K->w, n, -1.0);
+            if (rc) return rc;
+            for (int i = 0; i <= j; ++i) hv[i] += h2[i];
+            double d;
+            rc = mdot<T>(c, K->w, 0, 1, K->w, n, &d);
+            if (rc) return rc;
+            double hn = sqrt(d);
+            hv[j + 1] = hn;
+            if (hn > 0) k_scale<T><<<nblk(n), 256, 0, s>>>(K->w, 1.0 / hn, K->V + (j + 1) * n, n), ::mb::count_launch(c);
+            // Givens rotations
+            for (int i = 0; i < j; ++i) {
+                double a = cs[i] * hv[i] + sn[i] * hv[i + 1];
+                double b = -sn[i] * hv[i] + cs[i] * hv[i + 1];
+                hv[i] = a; hv[i + 1] = b;
+            }
+            double den = sqrt(hv[j] * hv[j] + hv[j + 1] * hv[j + 1]);
+            cs[j] = den > 0 ? hv[j] / den : 1.0;
+            sn[j] = den > 0 ? hv[j + 1] / den : 0.0;
+            hv[j] = den;
+            hv[j + 1] = 0.0;
+            g[j + 1] = -sn[j] * g[j];
+            g[j] = cs[j] * g[j];
+            for (int i = 0; i <= j; ++i) H[i * m + j] = hv[i];
+            ++its;
+            relres = fabs(g[j + 1]) / beta0;
+            if (!(relres == relres)) { set_error("non-finite Krylov residual"); return MB_ENOCONV; }
+            if (relres <= rtol || hn == 0.0) { ++j; break; }
+        }
+        // back substitution and x += Z y
+        int k = j;
+        for (int i = k - 1; i >= 0; --i) {
+            double acc = g[i];
+            for (int l = i + 1; l < k; ++l) acc -= H[i * m + l] * y[l];
+            y[i] = acc / H[i * m + i];
+        }
+        int rc = mupdate<T>(c, K->Z, n, k, y.data(), K->x, n, 1.0);
+        if (rc) return rc;
+        if (relres <= rtol) break;
+    }
+    *its_out = its;
+    *relres_out = relres;
+    return MB_OK;
+}
+
+template <class T>
+static int krylov_create(mb_cell* c, Krylov<T>** out) {
+    Krylov<T>* K = new Krylov<T>();
+    K->m = c->opt.gmres_m;
+    K->n = c->n;
+    size_t vb = sizeof(T) * (size_t)c->n;
+    K->V = (T*)cell_alloc(c, vb * (K->m + 1));
+    K->Z = (T*)cell_alloc(c, vb * K->m);
+    K->w = (T*)cell_alloc(c, vb);
+    K->b = (T*)cell_alloc(c, vb);
+    K->x = (T*)cell_alloc(c, vb);
+    *out = K;
+    if (!K->V || !K->Z || !K->w || !K->b || !K->x) return MB_ENOMEM;
+    return MB_OK;
+}
+
+// Solve J delta = -R at the current c->u (FP64 residual in c->r) into c->du.
+static int linear_solve(mb_cell* c, double dt, int* its, double* relres) {
+    int64_t n = c->n;
+    cudaStream_t s = c->stream;
+    k_convert<double, float><<<nblk(n), 256, 0, s>>>(c->u, c->u32, n), ::mb::count_launch(c);
+    MB_CUDA_LAUNCH("u32");
+    int rc = precond_setup(c, c->u32, c->gate, dt);
+    if (rc) return rc;
+    if (!c->kd && (rc = krylov_create<double>(c, &c->kd))) return rc;
+    Krylov<double>* K = c->kd;
+    k_scale_rhs<double><<<nblk(n), 256, 0, s>>>(c->P, c->D, c->vcode, c->r, 1.0 / dt, c->rowdiag, K->b), ::mb::count_launch(c);
+    OpCtx o{c->u, c->u32, c->opt.precision == MB_PREC_MIXED, c->gate, dt};
+    rc = fgmres<double>(c, K, o, c->opt.krylov_rtol, c->opt.krylov_maxit, its, relres);
+    if (rc) return rc;
+    k_unscale<double><<<nblk(n), 256, 0, s>>>(c->P, c->D, c->vcode, K->x, c->du), ::mb::count_launch(c);
+    MB_CUDA_LAUNCH("linear_solve");
+    return MB_OK;
+}
+
+void krylov_destroy(mb_cell* c) {
+    delete c->kd;
+    c->kd = nullptr;
+}
+
+static constexpr double DELTA_MAX = 0.25;
+
+// Newton with frozen gates from c->u_old; c->u holds the result.
+static int newton(mb_cell* c, double dt, double I_app, int* its_out, int* kits, double* rnorm_out, bool* ok) {
+    int64_t n = c->n;
+    cudaStream_t s = c->stream;
+    MB_CUDA(cudaMemcpyAsync(c->u, c->u_old, 8 * n, cudaMemcpyDeviceToDevice, s));
+    *ok = false;
+    for (int it = 1; it <= c->opt.newton_maxit; ++it) {
+        int rc = launch_residual<double>(c, c->u, c->u_old, c->gate, dt, I_app, c->r, s);
+        if (rc) return rc;
+        double rn;
+        if ((rc = scaled_maxnorm(c, c->r, 1, dt, &rn))) return rc;
+        *rnorm_out = rn;
+        if (!(rn < 1e200)) { *its_out = it; return MB_OK; }
+        int ki = 0;
+        double rr = 0;
+        rc = linear_solve(c, dt, &ki, &rr);
+        if (rc == MB_ENOCONV) { *its_out = it; return MB_OK; }
+        if (rc) return rc;
+        *kits += ki;
+        double dn;
+        if ((rc = scaled_maxnorm(c, c->du, 0, dt, &dn))) return rc;
+        if (!(dn < 1e200)) { *its_out = it; return MB_OK; }
+        double lam = dn <= DELTA_MAX ? 1.0 : DELTA_MAX / dn;
+        if (debug_level() > 0)
+            fprintf(stderr, "[mb] newton it %d |R|_s %.3e |d|_s %.3e lam %.3f krylov %d relres %.2e\n", it, rn,
+                    dn, lam, ki, rr);
+        k_axpy_d<<<nblk(n), 256, 0, s>>>(lam, c->du, c->u, n), ::mb::count_launch(c);
+        MB_CUDA_LAUNCH("newton update");
+        // a small update only means convergence if the linear solve made progress
+        if (lam * dn <= c->opt.newton_tol && rr <= 0.5) {
+            *its_out = it;
+            *ok = true;
+            return MB_OK;
+        }
+    }
+    *its_out = c->opt.newton_maxit;
+    return MB_OK;
+}
+
+// One step of size dt from c->u_old with the active-set passes; result in c->u.
+static int try_step(mb_cell* c, double dt, double I_app, mb_step_info* info, bool* ok) {
+    cudaStream_t s = c->stream;
+    int64_t N = c->D.N, F = c->D.F;
+    int rc = launch_gate(c, c->u_old, c->u_old + 2 * N, c->gate, s);
+    if (rc) return rc;
+    *ok = false;
+    for (int pass = 1; pass <= c->opt.max_passes; ++pass) {
+        int its = 0;
+        double rn = 0;
+        bool nok = false;
+        rc = newton(c, dt, I_app, &its, &info->krylov_its, &rn, &nok);
+        if (rc) return rc;
+        info->newton_its += its;
+        info->passes = pass;
+        info->res_norm = rn;
+        if (!nok) return MB_OK;
+        if (F == 0) { *ok = true; return MB_OK; }
+        rc = launch_gate(c, c->u, c->u_old + 2 * N, c->gate2, s);
+        if (rc) return rc;
+        int64_t flips = 0;
+        if ((rc = count_diff_u8(c, c->gate, c->gate2, F, &flips))) return rc;
+        if (flips == 0 || pass == c->opt.max_passes) { *ok = true; return MB_OK; }
+        info->flips += (int)flips;
+        MB_CUDA(cudaMemcpyAsync(c->gate, c->gate2, F, cudaMemcpyDeviceToDevice, s));
+    }
+    return MB_OK;
+}
+
+int newton_step(mb_cell* c, double dt, double I_app, mb_step_info* info) {
+    memset(info, 0, sizeof(*info));
+    int64_t n = c->n;
+    cudaStream_t s = c->stream;
+    MB_CUDA(cudaMemcpyAsync(c->u_pass, c->u, 8 * n, cudaMemcpyDeviceToDevice, s));
+    // try the full step; on failure halve dt and take 2^h sub-steps
+    for (int h = 0; h <= c->opt.max_halvings; ++h) {
+        int nsub = 1 << h;
+        double dts = dt / nsub;
+        bool all_ok = true;
+        MB_CUDA(cudaMemcpyAsync(c->u, c->u_pass, 8 * n, cudaMemcpyDeviceToDevice, s));
+        for (int k = 0; k < nsub; ++k) {
+            MB_CUDA(cudaMemcpyAsync(c->u_old, c->u, 8 * n, cudaMemcpyDeviceToDevice, s));
+            bool ok = false;
+            int rc = try_step(c, dts, I_app, info, &ok);
+            if (rc) return rc;
+            if (!ok) { all_ok = false; break; }
+        }
+        if (all_ok) {
+            info->halvings = h;
+            info->dt_used = dts;
+            return functionals(c, c->u, info);
+        }
+    }
+    MB_CUDA(cudaMemcpyAsync(c->u, c->u_pass, 8 * n, cudaMemcpyDeviceToDevice, s));
+    MB_CUDA(cudaStreamSynchronize(s));
+    set_error("Newton did not converge after all step halvings");
+    return MB_ENOCONV;
+}
+
+}  // namespace mb

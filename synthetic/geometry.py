@@ -52,6 +52,11 @@ def _mix_seed(seed, stream):
 def boolean_sphere_slab(nt, ny, nz, porosity, radius, seed, stream=0):
     """Boolean-sphere solid indicator for one slab of shape (nt, ny, nz).
 
+    Sphere centres are uniform in the slab box dilated by the largest radius
+    (uniform law: rmax; log-normal law: mean * exp(2 sigma_log)), radii follow
+    the given law, and spheres are added until the solid fraction inside the
+    slab first reaches 1 - porosity.
+
     radius: ("uniform", rmin, rmax) or ("lognormal_mean", mean, sigma_log),
     in voxel units.  For the log-normal law the mean of r is ``mean``, i.e.
     mu_log = ln(mean) - sigma_log**2 / 2.
@@ -65,17 +70,24 @@ def boolean_sphere_slab(nt, ny, nz, porosity, radius, seed, stream=0):
     tc = np.arange(nt) + 0.5
     yc = np.arange(ny) + 0.5
     zc = np.arange(nz) + 0.5
+    # germs are drawn in the slab box dilated by a typical maximum radius, so
+    # that the solid density does not thin out towards the slab faces (the
+    # usual edge correction of a Boolean model observed in a window)
+    if radius[0] == "uniform":
+        rpad = radius[2]
+    elif radius[0] == "lognormal_mean":
+        rpad = radius[1] * math.exp(2.0 * radius[2])
+    else:
+        raise ValueError("unknown radius law %r" % (radius[0],))
     while count < target:
-        ct = rng.uniform() * nt
-        cy = rng.uniform() * ny
-        cz = rng.uniform() * nz
+        ct = -rpad + rng.uniform() * (nt + 2 * rpad)
+        cy = -rpad + rng.uniform() * (ny + 2 * rpad)
+        cz = -rpad + rng.uniform() * (nz + 2 * rpad)
         if radius[0] == "uniform":
             r = radius[1] + (radius[2] - radius[1]) * rng.uniform()
-        elif radius[0] == "lognormal_mean":
+        else:
             mu = math.log(radius[1]) - 0.5 * radius[2] ** 2
             r = math.exp(mu + radius[2] * rng.normal())
-        else:
-            raise ValueError("unknown radius law %r" % (radius[0],))
         t0, t1 = max(0, int(math.floor(ct - r))), min(nt, int(math.ceil(ct + r)) + 1)
         y0, y1 = max(0, int(math.floor(cy - r))), min(ny, int(math.ceil(cy + r)) + 1)
         z0, z1 = max(0, int(math.floor(cz - r))), min(nz, int(math.ceil(cz + r)) + 1)
@@ -91,12 +103,51 @@ def boolean_sphere_slab(nt, ny, nz, porosity, radius, seed, stream=0):
     return solid, nsph, count / solid.size
 
 
+def percolating(lab):
+    """Keep only the connected parts of a cell, as in a wetted electrode:
+    electrolyte pockets (6-connected) that do not reach the separator's
+    electrolyte are closed pores and become the surrounding electrode solid;
+    solid clusters that do not reach their current collector (anode solid
+    with CN, cathode solid with CP) become electrolyte.  Returns a new grid."""
+    from scipy import ndimage
+    lab = lab.copy()
+    nt = lab.shape[0]
+    conn = ndimage.generate_binary_structure(3, 1)
+    # 1. closed pores: E components without a voxel in the middle third along t
+    ecomp, ne = ndimage.label(lab == E, structure=conn)
+    if ne:
+        mid = ecomp[nt // 3: max(nt // 3 + 1, 2 * nt // 3)]
+        keep = np.zeros(ne + 1, bool)
+        keep[np.unique(mid[mid > 0])] = True
+        closed = (ecomp > 0) & ~keep[ecomp]
+        if closed.any():
+            t_idx = np.nonzero(closed)[0]
+            fill = np.where(t_idx < nt // 2, G, K)
+            has_g, has_k = np.any(lab == G), np.any(lab == K)
+            if not has_k:
+                fill[:] = G
+            if not has_g:
+                fill[:] = K
+            lab[closed] = fill
+    # 2. floating solid: components of (solid + collector) not containing a collector voxel
+    for sol, cc in ((G, CN), (K, CP)):
+        comp, nc_ = ndimage.label((lab == sol) | (lab == cc), structure=conn)
+        if not nc_:
+            continue
+        keep = np.zeros(nc_ + 1, bool)
+        keep[np.unique(comp[(lab == cc) & (comp > 0)])] = True
+        floating = (comp > 0) & ~keep[comp] & (lab == sol)
+        lab[floating] = E
+    return lab
+
+
 def full_cell(ny, nz, n_anode, n_sep, n_cathode, porosity_anode, porosity_cathode,
               radius, seeds):
     """Full cell label grid with one CN layer at t=0 and one CP layer at the end.
 
     Layout along t: CN | anode (G spheres in E) | separator (E) | cathode (K
-    spheres in E) | CP.  ``seeds`` = (anode seed, cathode seed).
+    spheres in E) | CP.  ``seeds`` = (anode seed, cathode seed).  Closed
+    pores and floating particles are removed (``percolating``).
     """
     nt = n_anode + n_sep + n_cathode + 2
     lab = np.full((nt, ny, nz), E, dtype=np.uint8)
@@ -108,7 +159,7 @@ def full_cell(ny, nz, n_anode, n_sep, n_cathode, porosity_anode, porosity_cathod
     lab[a0:a0 + n_anode][sa] = G
     c0 = 1 + n_anode + n_sep
     lab[c0:c0 + n_cathode][sc] = K
-    return lab
+    return percolating(lab)
 
 
 def half_cell(ny, nz, n_anode, n_sep, n_foil, porosity_anode, radius, seed):
@@ -120,7 +171,7 @@ def half_cell(ny, nz, n_anode, n_sep, n_foil, porosity_anode, radius, seed):
     sa, _, _ = boolean_sphere_slab(n_anode, ny, nz, porosity_anode, radius, seed, 1)
     lab[1:1 + n_anode][sa] = G
     lab[1 + n_anode + n_sep:1 + n_anode + n_sep + n_foil] = L
-    return lab
+    return percolating(lab)
 
 
 def slab_1d(phases, ny=1, nz=1):

@@ -1,0 +1,301 @@
+"""The multigrid preconditioner of the GPU Newton-Krylov solve, checked stage
+by stage against an independent dense/sparse reference built from the
+oracle's complex-step Jacobian J:
+
+* the scaled operator A = S_r^-1 J S_u (residual and unknown scales),
+* the plating-row condensation S = A_vv - A_vn A_nn^-1 A_nv,
+* the class-aggregation Galerkin products A_1 = P_0^T S P_0, A_2 = P_1^T A_1 P_1,
+* the fine 2x2 block inverses,
+* and the whole preconditioner inside a right-preconditioned FGMRES.
+
+The GPU assembles in FP32, so entries are compared to 2e-3 of the row's
+largest magnitude (a few hundred FP32 roundings of sums of up to 8^l terms).
+"""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+import synthetic as syn
+from synthetic import E, G, K, L, CN, CP
+from oracle.fom import Cell as OCell
+
+pytestmark = pytest.mark.gpu
+
+
+def _gpu():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1704_04139_gb300 import binding, build
+    import os
+    if not os.path.exists(binding.LIB_PATH):
+        build.build()
+    return binding
+
+
+def _case(params):
+    lab = syn.full_cell(5, 7, 9, 4, 8, 0.35, 0.35, ("uniform", 1.5, 3), (3, 4))
+    oc = OCell(lab, 1e-6, params)
+    rng = np.random.default_rng(3)
+    u_old = oc.initial_state()
+    u = u_old.copy()
+    N = oc.N
+    u[:N] *= 1.0 + 0.02 * rng.standard_normal(N)
+    u[N:2 * N] += 0.003 * rng.standard_normal(N)
+    u[2 * N:] = 4e-5 * (rng.random(oc.F_pl) < 0.4)
+    gate = (u[2 * N:] > 0).astype(np.uint8)
+    gate[rng.random(oc.F_pl) < 0.2] = 1
+    return lab, oc, u, u_old, gate
+
+
+def _reference(oc, u, u_old, gate, dt):
+    N, F = oc.N, oc.F_pl
+    J = oc.jacobian(u, u_old, dt, 0.0, gate.astype(float))
+    A = (sp.diags(1.0 / oc.residual_scale(dt)) @ J @ sp.diags(oc.unknown_scale())).tocsr()
+    Avv, Avn, Anv = A[:2 * N, :2 * N], A[:2 * N, 2 * N:], A[2 * N:, :2 * N]
+    Ann = A[2 * N:, 2 * N:].diagonal()
+    S = (Avv - Avn @ sp.diags(1.0 / Ann) @ Anv).tocsr()
+    return A, S, Ann
+
+
+def _classes(flat):
+    return np.where(flat == E, 1, np.where((flat == G) | (flat == CN), 2, 3))
+
+
+def _p0(oc, d1):
+    N = oc.N
+    tt, yy, zz = np.unravel_index(np.arange(N), oc.shape)
+    cell = np.ravel_multi_index((tt // 2, yy // 2, zz // 2), d1)
+    e = np.nonzero(oc.flat == E)[0]
+    rows = np.concatenate([e, N + np.arange(N)])
+    cols = np.concatenate([cell[e] * 4, cell * 4 + _classes(oc.flat)])
+    return sp.csr_matrix((np.ones(len(rows)), (rows, cols)), shape=(2 * N, int(np.prod(d1)) * 4))
+
+
+def _pup(dims, nd):
+    n = int(np.prod(dims))
+    t, y, z = np.unravel_index(np.arange(n), dims)
+    par = np.ravel_multi_index((t // 2, y // 2, z // 2), nd)
+    rows = np.arange(n * 4)
+    cols = par.repeat(4) * 4 + np.tile(np.arange(4), n)
+    return sp.csr_matrix((np.ones(len(rows)), (rows, cols)), shape=(n * 4, int(np.prod(nd)) * 4))
+
+
+def _compare_level(Aref, dims, aself, off, mask):
+    """Entry-wise: |gpu - ref| <= 2e-3 |ref| + 1e-6 max|row|, so that the weak
+    (Butler-Volmer) couplings are checked to FP32 accuracy too."""
+    Ad = Aref.toarray()
+    nt, ny, nz = dims
+    floor = 1e-6 * np.abs(Ad).max(axis=1) + 1e-30
+    steps = [(-1, 0, 0), (1, 0, 0), (0, -1, 0), (0, 1, 0), (0, 0, -1), (0, 0, 1)]
+    worst = 0.0
+
+    def chk(g, r, row):
+        return abs(g - r) / (2e-3 * abs(r) + floor[row])
+
+    for cell in range(nt * ny * nz):
+        t, y, z = np.unravel_index(cell, dims)
+        for k in range(4):
+            if not (mask[cell] >> k) & 1:
+                continue
+            row = 4 * cell + k
+            for kk in range(4):
+                if (mask[cell] >> kk) & 1:
+                    worst = max(worst, chk(aself[cell, k, kk], Ad[row, 4 * cell + kk], row))
+            for d, (dt_, dy_, dz_) in enumerate(steps):
+                tn, yn, zn = t + dt_, y + dy_, z + dz_
+                if not (0 <= tn < nt and 0 <= yn < ny and 0 <= zn < nz):
+                    continue
+                nb = np.ravel_multi_index((tn, yn, zn), dims)
+                for kk in range(4):
+                    worst = max(worst, chk(off[cell, d, k, kk], Ad[row, 4 * nb + kk], row))
+    assert worst <= 1.0, worst
+
+
+def test_precond_stages_match_reference(params):
+    B = _gpu()
+    lab, oc, u, u_old, gate = _case(params)
+    dt = 1.0
+    gc = B.Cell(lab, 1e-6, params)
+    A, S, Ann = _reference(oc, u, u_old, gate, dt)
+    N, F = oc.N, oc.F_pl
+    gc.debug_precond(u, gate, dt, np.ones(gc.n))
+    dinv, fc, rowdiag = gc.debug_fine()
+    # Krylov row equilibration: magnitude of the scaled Jacobian's diagonal
+    assert np.all(np.abs(rowdiag - np.abs(A.diagonal())) <= 2e-3 * np.abs(A.diagonal()) + 1e-30)
+    # condensation coefficients
+    g, e = oc.pf_g, oc.pf_e
+    f = np.arange(F)
+    Ad = A.tocsr()
+    ref = np.stack([Ann, Ad[2 * N + f, N + g].A1, Ad[2 * N + f, e].A1, Ad[2 * N + f, N + e].A1,
+                    Ad[N + g, 2 * N + f].A1, Ad[e, 2 * N + f].A1, Ad[N + e, 2 * N + f].A1], axis=1)
+    scale = np.abs(ref).max(axis=0) + 1e-30
+    assert np.all(np.abs(fc[:, :7] - ref) <= 1e-3 * np.abs(ref) + 1e-5 * scale)
+    # fine condensed 2x2 block inverses
+    v = np.arange(N)
+    blk = np.stack([np.stack([S[v, v].A1, S[v, N + v].A1], 1), np.stack([S[N + v, v].A1, S[N + v, N + v].A1], 1)], 1)
+    prod = np.einsum("vij,vjk->vik", dinv.astype(np.float64), blk)
+    assert np.max(np.abs(prod - np.eye(2))) < 2e-3
+    # Galerkin coarse operators
+    levels = gc.debug_levels()
+    assert len(levels) >= 2
+    P = _p0(oc, levels[0])
+    Aref = (P.T @ S @ P).tocsr()
+    for l, dims in enumerate(levels, start=1):
+        d, aself, off, mask = gc.debug_level_op(l)
+        assert d == dims
+        _compare_level(Aref, dims, aself, off, mask)
+        if l < len(levels):
+            Pu = _pup(dims, levels[l])
+            Aref = (Pu.T @ Aref @ Pu).tocsr()
+
+
+class _Emulation:
+    """FP64 emulation of the preconditioner's algorithm on the reference
+    operators: condensation, 4 damped 2x2 block-Jacobi sweeps (omega 0.8)
+    before and after a level-1 correction; level 1 solved by FGMRES(6) whose
+    preconditioner is a V-cycle with 2 damped (0.7) 4x4 block-Jacobi sweeps
+    before and after each coarse correction; exact coarsest level."""
+
+    def __init__(self, oc, A, S, Ann, dims):
+        N = oc.N
+        self.N = N
+        self.Avn, self.Anv, self.Ann, self.S = A[:2 * N, 2 * N:], A[2 * N:, :2 * N], Ann, S
+        v = np.arange(N)
+        blk = np.stack([np.stack([S[v, v].A1, S[v, N + v].A1], 1), np.stack([S[N + v, v].A1, S[N + v, N + v].A1], 1)], 1)
+        self.D = np.linalg.inv(blk)
+        self.P = [_p0(oc, dims[0])]
+        self.A = [S, None]
+        Al = (self.P[0].T @ S @ self.P[0]).tocsr()
+        self.A[1] = self._fix(Al)
+        for l in range(1, len(dims)):
+            Pu = _pup(dims[l - 1], dims[l])
+            self.P.append(Pu)
+            Al = (Pu.T @ Al @ Pu).tocsr()
+            self.A.append(self._fix(Al))
+        self.Sinv = [None] + [self._binv(a) for a in self.A[1:]]
+        self.L = len(self.A) - 1
+
+    @staticmethod
+    def _fix(M):
+        M = M.tolil()
+        d = M.diagonal()
+        empty = np.nonzero((abs(M).sum(axis=1).A1 == 0))[0]
+        for i in empty:
+            M[i, i] = 1.0
+        return M.tocsr()
+
+    @staticmethod
+    def _binv(M):
+        nb = M.shape[0] // 4
+        out = [np.linalg.inv(M[4 * b:4 * b + 4, 4 * b:4 * b + 4].toarray()) for b in range(nb)]
+        return sp.block_diag(out, format="csr")
+
+    def fine(self, r, om=0.8):
+        N = self.N
+        z = np.zeros(2 * N)
+        z[:N] = om * (self.D[:, 0, 0] * r[:N] + self.D[:, 0, 1] * r[N:])
+        z[N:] = om * (self.D[:, 1, 0] * r[:N] + self.D[:, 1, 1] * r[N:])
+        return z
+
+    def vcycle(self, l, b):
+        if l == self.L:
+            return np.linalg.solve(self.A[l].toarray(), b)
+        A, Si = self.A[l], self.Sinv[l]
+        x = 0.7 * (Si @ b)
+        x = x + 0.7 * (Si @ (b - A @ x))
+        e = self.vcycle(l + 1, self.P[l].T @ (b - A @ x))
+        x = x + self.P[l] @ e
+        for _ in range(2):
+            x = x + 0.7 * (Si @ (b - A @ x))
+        return x
+
+    def level1(self, b):
+        if self.L == 1:
+            return self.vcycle(1, b)
+        A = self.A[1]
+        k = 6
+        beta = np.linalg.norm(b)
+        V = [b / beta]; Z = []; H = np.zeros((k + 1, k))
+        for j in range(k):
+            z = self.vcycle(1, V[j]); Z.append(z); w = A @ z
+            for _ in range(2):
+                h = np.array([v @ w for v in V]); w = w - sum(hh * v for hh, v in zip(h, V)); H[:j + 1, j] += h
+            H[j + 1, j] = np.linalg.norm(w); V.append(w / H[j + 1, j])
+        g = np.zeros(k + 1); g[0] = beta
+        y = np.linalg.lstsq(H, g, rcond=None)[0]
+        return sum(yy * z for yy, z in zip(y, Z))
+
+    def apply(self, r):
+        N = self.N
+        rv = r[:2 * N] - self.Avn @ (r[2 * N:] / self.Ann)
+        z = self.fine(rv)
+        for _ in range(3):
+            z = z + self.fine(rv - self.S @ z)
+        z = z + self.P[0] @ self.level1(self.P[0].T @ (rv - self.S @ z))
+        for _ in range(4):
+            z = z + self.fine(rv - self.S @ z)
+        zn = (r[2 * N:] - self.Anv @ z) / self.Ann
+        return np.concatenate([z, zn])
+
+
+def test_precond_matches_emulation(params):
+    B = _gpu()
+    lab, oc, u, u_old, gate = _case(params)
+    dt = 1.0
+    gc = B.Cell(lab, 1e-6, params)
+    A, S, Ann = _reference(oc, u, u_old, gate, dt)
+    gc.debug_precond(u, gate, dt, np.ones(gc.n))
+    rowdiag = gc.debug_fine()[2].astype(np.float64)
+    em = _Emulation(oc, A, S, Ann, gc.debug_levels())
+    r = np.random.default_rng(7).standard_normal(gc.n)
+    zg = gc.debug_precond(u, gate, dt, r)
+    ze = em.apply(r * rowdiag)      # the GPU input is row-equilibrated
+    N = oc.N
+    errs = {}
+    for name, sl in (("c", slice(0, N)), ("phi", slice(N, 2 * N)), ("n", slice(2 * N, None))):
+        errs[name] = float(np.max(np.abs(zg[sl] - ze[sl])) / np.max(np.abs(ze[sl])))
+    # FP32 fine level against the FP64 emulation (a float32 emulation differs by ~2e-2 too)
+    assert max(errs.values()) < 5e-2, errs
+
+
+def _fgmres(Aop, b, M, m=30, maxit=150, rtol=1e-6):
+    x = np.zeros_like(b)
+    beta0 = np.linalg.norm(b)
+    its = 0
+    while its < maxit:
+        r = b - Aop(x)
+        beta = np.linalg.norm(r)
+        if beta <= rtol * beta0:
+            break
+        V = [r / beta]; Z = []
+        H = np.zeros((m + 1, m)); g = np.zeros(m + 1); g[0] = beta
+        for j in range(m):
+            z = M(V[j]); Z.append(z); w = Aop(z)
+            Vm = np.array(V)
+            h = Vm @ w; w = w - Vm.T @ h
+            h2 = Vm @ w; w = w - Vm.T @ h2
+            H[:j + 1, j] = h + h2; H[j + 1, j] = np.linalg.norm(w)
+            V.append(w / H[j + 1, j]); its += 1
+            y = np.linalg.lstsq(H[:j + 2, :j + 1], g[:j + 2], rcond=None)[0]
+            res = np.linalg.norm(g[:j + 2] - H[:j + 2, :j + 1] @ y)
+            if res <= rtol * beta0 or its >= maxit:
+                break
+        x = x + np.array(Z).T @ y
+    return x, its, np.linalg.norm(b - Aop(x)) / beta0
+
+
+def test_precond_drives_fgmres(params):
+    """FGMRES (FP64, on the host) on the oracle's scaled Jacobian with the GPU
+    preconditioner reaches 1e-6 in a bounded number of iterations."""
+    B = _gpu()
+    lab, oc, u, u_old, gate = _case(params)
+    dt = 1.0
+    gc = B.Cell(lab, 1e-6, params)
+    A, S, Ann = _reference(oc, u, u_old, gate, dt)
+    gc.debug_precond(u, gate, dt, np.ones(gc.n))
+    E = sp.diags(1.0 / gc.debug_fine()[2].astype(np.float64))
+    Ae = (E @ A).tocsr()                 # the row-equilibrated Krylov operator
+    b = np.random.default_rng(5).standard_normal(gc.n)
+    x, its, rel = _fgmres(lambda v: Ae @ v, b, lambda r: gc.debug_precond(u, gate, dt, r))
+    assert rel <= 1e-6 and its <= 100, (its, rel)
