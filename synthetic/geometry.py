@@ -103,32 +103,77 @@ def boolean_sphere_slab(nt, ny, nz, porosity, radius, seed, stream=0):
     return solid, nsph, count / solid.size
 
 
+def _electrode_ranges(lab):
+    """t-ranges [lo, hi] of the anode solid (G) and cathode solid (K or L
+    foil), and the separator layers strictly between them (None if absent)."""
+    nt = lab.shape[0]
+
+    def span(mask):
+        t = np.nonzero(mask.any(axis=(1, 2)))[0]
+        return (int(t[0]), int(t[-1])) if t.size else None
+
+    ga = span(lab == G)
+    kc = span((lab == K) | (lab == L))
+    if ga is not None and kc is not None and kc[0] - ga[1] > 1:
+        sep = (ga[1] + 1, kc[0] - 1)
+    else:
+        sep = (nt // 3, max(nt // 3, 2 * nt // 3 - 1))
+    return span(lab == G), span(lab == K), sep
+
+
+def _fill_solid(lab, mask, ga, kc):
+    """Turn the voxels of ``mask`` that lie in the t-range of an electrode into
+    that electrode's solid; voxels outside both ranges stay electrolyte."""
+    t_idx, y_idx, z_idx = np.nonzero(mask)
+    fill = np.full(t_idx.shape, E, dtype=lab.dtype)
+    if ga is not None:
+        fill[(t_idx >= ga[0]) & (t_idx <= ga[1])] = G
+    if kc is not None:
+        fill[(t_idx >= kc[0]) & (t_idx <= kc[1])] = K
+    lab[t_idx, y_idx, z_idx] = fill
+
+
+def _reaches(comp, n, sep):
+    keep = np.zeros(n + 1, bool)
+    mid = comp[sep[0]:sep[1] + 1]
+    keep[np.unique(mid[mid > 0])] = True
+    keep[0] = False
+    return keep
+
+
 def percolating(lab):
     """Keep only the connected parts of a cell, as in a wetted electrode:
-    electrolyte pockets (6-connected) that do not reach the separator's
-    electrolyte are closed pores and become the surrounding electrode solid;
-    solid clusters that do not reach their current collector (anode solid
-    with CN, cathode solid with CP) become electrolyte.  Returns a new grid."""
+    pore regions reached from the separator only through necks thinner than
+    three voxels, and electrolyte pockets (6-connected) that do not reach the
+    separator at all, become the solid of the electrode they lie in (closed
+    pores); solid clusters that do not reach their current collector (anode
+    solid with CN, cathode solid with CP) become electrolyte.  Separator
+    layers are never filled.  This plays the role of the morphological
+    smoothing of the paper's generator (Sec. 2.1).  Returns a new grid."""
     from scipy import ndimage
     lab = lab.copy()
-    nt = lab.shape[0]
     conn = ndimage.generate_binary_structure(3, 1)
-    # 1. closed pores: E components without a voxel in the middle third along t
+    ga, kc, sep = _electrode_ranges(lab)
+    # 0. pores reached only through necks thinner than three voxels: keep the
+    #    pore voxels within one voxel of the morphologically opened pore network
+    #    that reaches the separator; the rest become the surrounding solid
+    pore = lab == E
+    # the lateral walls are no-flux mirror planes: pad y and z by one mirrored
+    # voxel so that a pore along a wall is not taken for a neck
+    padded = np.pad(pore, ((1, 1), (1, 1), (1, 1)), mode="edge")
+    padded[0] = False
+    padded[-1] = False
+    opened = ndimage.binary_opening(padded, structure=conn)[1:-1, 1:-1, 1:-1]
+    ocomp, no = ndimage.label(opened, structure=conn)
+    if no:
+        keep = _reaches(ocomp, no, sep)
+        near = ndimage.binary_dilation(keep[ocomp], structure=conn)
+        _fill_solid(lab, pore & ~near, ga, kc)
+    # 1. closed pores: E components without a voxel in the separator layers
     ecomp, ne = ndimage.label(lab == E, structure=conn)
     if ne:
-        mid = ecomp[nt // 3: max(nt // 3 + 1, 2 * nt // 3)]
-        keep = np.zeros(ne + 1, bool)
-        keep[np.unique(mid[mid > 0])] = True
-        closed = (ecomp > 0) & ~keep[ecomp]
-        if closed.any():
-            t_idx = np.nonzero(closed)[0]
-            fill = np.where(t_idx < nt // 2, G, K)
-            has_g, has_k = np.any(lab == G), np.any(lab == K)
-            if not has_k:
-                fill[:] = G
-            if not has_g:
-                fill[:] = K
-            lab[closed] = fill
+        keep = _reaches(ecomp, ne, sep)
+        _fill_solid(lab, (ecomp > 0) & ~keep[ecomp], ga, kc)
     # 2. floating solid: components of (solid + collector) not containing a collector voxel
     for sol, cc in ((G, CN), (K, CP)):
         comp, nc_ = ndimage.label((lab == sol) | (lab == cc), structure=conn)
@@ -146,32 +191,66 @@ def full_cell(ny, nz, n_anode, n_sep, n_cathode, porosity_anode, porosity_cathod
     """Full cell label grid with one CN layer at t=0 and one CP layer at the end.
 
     Layout along t: CN | anode (G spheres in E) | separator (E) | cathode (K
-    spheres in E) | CP.  ``seeds`` = (anode seed, cathode seed).  Closed
-    pores and floating particles are removed (``percolating``).
+    spheres in E) | CP.  ``seeds`` = (anode seed, cathode seed).  Closed and
+    necked pores and floating particles are removed (``percolating``); the
+    sphere-filling targets are corrected twice (half the measured error each
+    time) and the pass whose electrode porosities after that cleanup lie
+    closest to the requested ones is returned.
     """
     nt = n_anode + n_sep + n_cathode + 2
-    lab = np.full((nt, ny, nz), E, dtype=np.uint8)
-    lab[0] = CN
-    lab[-1] = CP
-    sa, _, _ = boolean_sphere_slab(n_anode, ny, nz, porosity_anode, radius, seeds[0], 1)
-    sc, _, _ = boolean_sphere_slab(n_cathode, ny, nz, porosity_cathode, radius, seeds[1], 2)
-    a0 = 1
-    lab[a0:a0 + n_anode][sa] = G
-    c0 = 1 + n_anode + n_sep
-    lab[c0:c0 + n_cathode][sc] = K
-    return percolating(lab)
+    a0, c0 = 1, 1 + n_anode + n_sep
+    ta, tc = porosity_anode, porosity_cathode
+    best = None
+    for _ in range(3):
+        lab = np.full((nt, ny, nz), E, dtype=np.uint8)
+        lab[0] = CN
+        lab[-1] = CP
+        sa, _, _ = boolean_sphere_slab(n_anode, ny, nz, ta, radius, seeds[0], 1)
+        sc, _, _ = boolean_sphere_slab(n_cathode, ny, nz, tc, radius, seeds[1], 2)
+        lab[a0:a0 + n_anode][sa] = G
+        lab[c0:c0 + n_cathode][sc] = K
+        lab = percolating(lab)
+        ea = float(np.mean(lab[a0:a0 + n_anode] == E))
+        ec = float(np.mean(lab[c0:c0 + n_cathode] == E))
+        err = abs(ea - porosity_anode) + abs(ec - porosity_cathode)
+        if _collectors_touch(lab) and (best is None or err < best[0]):
+            best = (err, lab)
+        ta = min(0.9, max(0.05, ta + 0.5 * (porosity_anode - ea)))
+        tc = min(0.9, max(0.05, tc + 0.5 * (porosity_cathode - ec)))
+    if best is None:
+        raise ValueError("no valid cell generated: a collector touches no solid")
+    return best[1]
 
 
 def half_cell(ny, nz, n_anode, n_sep, n_foil, porosity_anode, radius, seed):
     """Half cell: CN | anode (G spheres in E) | separator (E) | Li foil (L) | CP."""
     nt = n_anode + n_sep + n_foil + 2
-    lab = np.full((nt, ny, nz), E, dtype=np.uint8)
-    lab[0] = CN
-    lab[-1] = CP
-    sa, _, _ = boolean_sphere_slab(n_anode, ny, nz, porosity_anode, radius, seed, 1)
-    lab[1:1 + n_anode][sa] = G
-    lab[1 + n_anode + n_sep:1 + n_anode + n_sep + n_foil] = L
-    return percolating(lab)
+    ta = porosity_anode
+    best = None
+    for _ in range(3):
+        lab = np.full((nt, ny, nz), E, dtype=np.uint8)
+        lab[0] = CN
+        lab[-1] = CP
+        sa, _, _ = boolean_sphere_slab(n_anode, ny, nz, ta, radius, seed, 1)
+        lab[1:1 + n_anode][sa] = G
+        lab[1 + n_anode + n_sep:1 + n_anode + n_sep + n_foil] = L
+        lab = percolating(lab)
+        ea = float(np.mean(lab[1:1 + n_anode] == E))
+        err = abs(ea - porosity_anode)
+        if _collectors_touch(lab) and (best is None or err < best[0]):
+            best = (err, lab)
+        ta = min(0.9, max(0.05, ta + 0.5 * (porosity_anode - ea)))
+    if best is None:
+        raise ValueError("no valid cell generated: a collector touches no solid")
+    return best[1]
+
+
+def _collectors_touch(lab):
+    """True when the CN layer touches anode solid and the CP layer touches
+    cathode solid or a Li foil layer (the first and last t-layers)."""
+    ok_n = bool(np.any(lab[1][lab[0] == CN] == G))
+    ok_p = bool(np.any(np.isin(lab[-2][lab[-1] == CP], (K, L))))
+    return ok_n and ok_p
 
 
 def slab_1d(phases, ny=1, nz=1):

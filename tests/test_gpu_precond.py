@@ -214,7 +214,7 @@ class _Emulation:
         if self.L == 1:
             return self.vcycle(1, b)
         A = self.A[1]
-        k = 6
+        k = 16  # FGMRES length of the kernel's level-1 K-cycle (KCYC in precond.cu)
         beta = np.linalg.norm(b)
         V = [b / beta]; Z = []; H = np.zeros((k + 1, k))
         for j in range(k):
