@@ -164,6 +164,30 @@ int mb_launch_count(mb_cell* cell, int64_t* count);
  * host-pointer calls of this cell enqueue their work. */
 int mb_cell_stream(mb_cell* cell, void** stream);
 
+/* ---- residual without allocation (no counterpart in the paper) ----
+ * Same result as mb_residual_dev with gate == NULL (gates taken at u_old),
+ * for callers that may not allocate memory at call time: a serving loop whose
+ * device memory is all reserved up front by another allocator, where a
+ * cudaMalloc fails or stalls, or a latency-bound thread that must not wait on
+ * an allocator.  The F bytes of gate scratch live in a fixed array in the
+ * library's static device memory (MB_NOALLOC_MAX_FACES bytes per device)
+ * instead of the cell's buffers; the success path calls cudaMalloc, cudaFree
+ * or any other allocating routine nowhere.  Nothing in the scratch has to
+ * start at zero: each call writes every byte it reads.
+ *   u, u_old, r: device double[n] of the current device; stream as for the
+ *   other _dev calls; the call returns when the stream has completed it.
+ * The first call on each device resolves the scratch address
+ * (cudaGetSymbolAddress, which may load the library's device code): make it
+ * with that device current and before any stream capture.  All calls on one
+ * device share the one scratch array, so calls that overlap in time (other
+ * threads, other streams, other cells) race: order them on one stream or on
+ * the host.  MB_EINVAL for a cell with more than MB_NOALLOC_MAX_FACES plating
+ * faces or an invalid argument; MB_ECUDA on a CUDA error.  A failing call
+ * stores its message for mb_last_error in host memory. */
+#define MB_NOALLOC_MAX_FACES 4194304
+int mb_residual_dev_noalloc(mb_cell* cell, const double* u, const double* u_old, double dt, double I_app,
+                            double* r, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -83,6 +83,7 @@ def _declare(lib):
     fn("mb_step", C.c_int, [VP, C.c_double, C.c_double, C.POINTER(StepInfo)])
     fn("mb_residual", C.c_int, [VP, VP, VP, VP, C.c_double, C.c_double, VP])
     fn("mb_residual_dev", C.c_int, [VP, VP, VP, VP, C.c_double, C.c_double, VP, VP])
+    fn("mb_residual_dev_noalloc", C.c_int, [VP, VP, VP, C.c_double, C.c_double, VP, VP])
     fn("mb_jvp", C.c_int, [VP, VP, VP, C.c_double, VP, VP])
     fn("mb_jvp_dev", C.c_int, [VP, VP, VP, C.c_double, VP, VP, VP])
     fn("mb_jvp_f32_dev", C.c_int, [VP, VP, VP, C.c_double, VP, VP, VP])
@@ -280,6 +281,10 @@ class Cell:
         _check(lib().mb_residual_dev(self.h, VP(u.data_ptr()), VP(u_old.data_ptr()),
                                      None if gate is None else VP(gate.data_ptr()), float(dt),
                                      float(I_app), VP(r.data_ptr()), _stream_of(u)))
+
+    def residual_dev_noalloc(self, u, u_old, dt, I_app, r):
+        _check(lib().mb_residual_dev_noalloc(self.h, VP(u.data_ptr()), VP(u_old.data_ptr()), float(dt),
+                                             float(I_app), VP(r.data_ptr()), _stream_of(u)))
 
     def jvp_dev(self, u, v, dt, out, gate=None):
         _check(lib().mb_jvp_dev(self.h, VP(u.data_ptr()), None if gate is None else VP(gate.data_ptr()),

@@ -449,6 +449,21 @@ int launch_gate(mb_cell* c, const double* u, const double* n_old, uint8_t* gate,
     return MB_OK;
 }
 
+int launch_gate_residual_unprofiled(mb_cell* c, const double* u, const double* u_old, uint8_t* gate_scratch,
+                                    double dt, double I_app, double* r, cudaStream_t s) {
+    const Dims& D = c->D;
+    if (D.F > 0) {
+        k_gate<<<(unsigned)((D.F + 255) / 256), 256, 0, s>>>(D, c->pf_g, c->pf_e, u_old, u_old + 2 * D.N,
+                                                             gate_scratch), ::mb::count_launch(c);
+        MB_CUDA_LAUNCH("gate");
+    }
+    k_residual<double><<<vox_grid(D, VOX_BLOCK), VOX_BLOCK, 0, s>>>(c->P, D, c->vcode, u, u_old, gate_scratch,
+                                                                    1.0 / dt, I_app, c->s_i0, c->k_pl, r),
+        ::mb::count_launch(c);
+    MB_CUDA_LAUNCH("residual");
+    return MB_OK;
+}
+
 // ------------------------------------------------------------ reductions
 // Deterministic reductions (mb_reduce.cuh).
 __global__ void __launch_bounds__(RED_THREADS)

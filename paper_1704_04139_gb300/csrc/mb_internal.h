@@ -131,6 +131,10 @@ template <class TC, class TV>
 int launch_jvp(mb_cell* c, const TC* u, const uint8_t* gate, double dt, const TV* v, TV* jv,
                cudaStream_t s, int mode = 0);
 int launch_gate(mb_cell* c, const double* u, const double* n_old, uint8_t* gate, cudaStream_t s);
+// Gates at u_old written into gate_scratch (F bytes), then the FP64 residual
+// reading them, both on stream s; no profiling events, no allocation.
+int launch_gate_residual_unprofiled(mb_cell* c, const double* u, const double* u_old, uint8_t* gate_scratch,
+                                    double dt, double I_app, double* r, cudaStream_t s);
 // scaled max norms: which = 0 unknown scale, 1 residual scale (needs dt)
 int scaled_maxnorm(mb_cell* c, const double* x, int which, double dt, double* out);
 int functionals(mb_cell* c, const double* u, mb_step_info* info);
