@@ -124,12 +124,13 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
-def jvp_traffic(workload):
-    """DRAM bytes per JVP launch from the committed ncu summary, or None."""
-    path = os.path.join(ROOT, "profiles", "k_jvp_mixed__%s.json" % workload)
+def jvp_traffic(workload, mode):
+    """DRAM bytes per launch of the JVP in the given mode from the committed
+    ncu summary, or None."""
+    path = os.path.join(ROOT, "profiles", "k_jvp_lin__%s.json" % workload)
     try:
         with open(path) as f:
-            return float(json.load(f)["dram_bytes_per_launch"])
+            return float(json.load(f)["dram_bytes_per_launch"][mode])
     except Exception:
         return None
 
@@ -221,11 +222,13 @@ def main():
     cell.prof_enable(True)
     l0 = cell.launch_count()
     clocks.start()
+    torch.cuda.nvtx.range_push("timed")
     ev0.record(stream)
     infos = []
     for _ in range(args.steps):
         infos.append(cell.step(dt, I))
     ev1.record(stream)
+    torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     clk = clocks.stop()
     launches = cell.launch_count() - l0
@@ -233,6 +236,7 @@ def main():
     n_jvp, ms_jvp = cell.prof_read(B.Cell.PROF_JVP)
     n_res, ms_res = cell.prof_read(B.Cell.PROF_RESIDUAL)
     n_pc, ms_pc = cell.prof_read(B.Cell.PROF_PRECOND)
+    n_sm, ms_sm = cell.prof_read(B.Cell.PROF_SMOOTH)
     cell.prof_enable(False)
     if dist is not None:
         t = torch.tensor([ms], device="cuda", dtype=torch.float64)
@@ -256,19 +260,27 @@ def main():
     e2e = {"value": ws * args.e2e_steps * dt / e2e_wall, "unit": UNIT,
            "h2d_bytes_per_step": 8 * cell.n, "d2h_bytes_per_step": 8 * cell.n}
 
-    # roofline of the dominant kernel: the JVP (Krylov operator and fine smoother)
+    # roofline of the dominant kernel: the stencil JVP k_jvp_lin, launched as
+    # the fine smoother's S z (mode 1) and as the Krylov operator (mode 2)
     peak, peak_kind = measured_peaks()
-    N, F = cell.N, cell.F
-    # compulsory bytes per launch: vcode 4 + FP32 (c, phi) 8 + FP64 direction 16 + FP64 result 16 per
-    # voxel; per plating face FP32 n 4 + gate 1 + FP64 direction 8 + FP64 result 8
-    bytes_per_launch = 44.0 * N + 21.0 * F
-    avg_jvp_ms = ms_jvp / max(n_jvp, 1)
-    achieved = bytes_per_launch / (avg_jvp_ms / 1000.0) / 1e9 if n_jvp else None
-    roof = {"kernel": "k_jvp<float,double> (mixed Krylov operator / fine smoother)", "bound": "hbm",
+    N, F, NI = cell.N, cell.F, cell.NI
+    # algorithmic bytes per launch.  Per voxel: vcode 4 + FP32 c 4 + float-float direction (c, phi) 16
+    # + FP32 result (c, phi) 8 (+ FP32 row scales (c, phi) 8 in mode 2).  Per interface face: six FP32
+    # partials 24.  Per plating face: float-float direction 8 (+ FP32 result 4 + row scale 4 in mode 2).
+    kinds = {"smoother": (n_sm, ms_sm, 32.0 * N + 24.0 * NI + 8.0 * F, "k_jvp_lin<1> (fine smoother S z)"),
+             "operator": (n_jvp, ms_jvp, 40.0 * N + 24.0 * NI + 16.0 * F, "k_jvp_lin<2> (Krylov operator)")}
+    dom = max(kinds, key=lambda k: kinds[k][1])
+    n_k, ms_k, bytes_per_launch, kname = kinds[dom]
+    avg_ms = ms_k / max(n_k, 1)
+    achieved = bytes_per_launch / (avg_ms / 1000.0) / 1e9 if n_k else None
+    roof = {"kernel": kname, "bound": "hbm",
             "achieved": achieved, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
-            "frac": (achieved / peak) if achieved else None, "traffic": jvp_traffic(args.workload),
-            "bytes_per_launch": bytes_per_launch, "launches": n_jvp, "avg_launch_ms": avg_jvp_ms,
-            "share_of_step": ms_jvp / ms if ms else None}
+            "frac": (achieved / peak) if achieved else None, "traffic": jvp_traffic(args.workload, dom),
+            "bytes_per_launch": bytes_per_launch, "launches": n_k, "avg_launch_ms": avg_ms,
+            "share_of_step": ms_k / ms if ms else None,
+            "other": {k: {"launches": v[0], "avg_launch_ms": v[1] / max(v[0], 1),
+                          "gbs": (v[2] / (v[1] / max(v[0], 1) / 1000.0) / 1e9) if v[0] else None}
+                      for k, v in kinds.items()}}
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:

@@ -59,8 +59,12 @@ typedef struct {
     double Pl_i00, Pl_layer_m, Pl_Vm_Li;
 } mb_params;
 
-#define MB_PREC_FP64  0   /* plain: FP64 residual, JVP and Krylov vectors */
-#define MB_PREC_MIXED 1   /* FP64 Newton residual; FP32 JVP/Krylov/preconditioner */
+/* Both paths: FP64 state and Newton residual; FP32 arithmetic in the Krylov
+ * solver and the preconditioner, with float-float storage of the vectors that
+ * carry near-null components.  They differ in the Krylov operator's
+ * linearisation coefficients: */
+#define MB_PREC_FP64  0   /* coefficients from the FP64 state in FP64 */
+#define MB_PREC_MIXED 1   /* coefficients from the FP32 copy of the state in FP32 */
 
 typedef struct {
     int    precision;      /* MB_PREC_FP64 or MB_PREC_MIXED */
@@ -73,6 +77,7 @@ typedef struct {
     int    max_halvings;   /* dt halvings on Newton failure */
     int    mg_coarse_cells;/* multigrid: coarsen until at most this many cells */
     int    mg_smooth;      /* block-Jacobi sweeps per level, pre and post */
+    int    mg_kcycle;      /* FGMRES iterations of the level-1 K-cycle (1..16) */
 } mb_solver_opts;
 
 typedef struct {
@@ -97,6 +102,7 @@ typedef struct {
     double  i_1c;          /* 1C current density: F V cmax_G (1-x0_G) n_G / 3600 s / (ny nz h^2) */
     int64_t count[6];      /* voxels per phase label */
     int64_t device_bytes;  /* device memory held by the cell */
+    int64_t n_iface;       /* solid-electrolyte faces with kinetics (G, K, L): F plating faces first */
 } mb_cell_info;
 
 typedef struct mb_cell mb_cell;
@@ -153,9 +159,10 @@ int mb_jvp_f32_dev(mb_cell* cell, const float* u, const uint8_t* gate, double dt
  * launches and their summed device time (ms) since the last enable/reset.
  * mb_launch_count returns the number of kernels the library has launched
  * for this cell since its creation (always counted). */
-#define MB_PROF_JVP      0   /* Jacobian-vector product kernel (Krylov operator and smoother) */
+#define MB_PROF_JVP      0   /* Jacobian-vector product kernel (Krylov operator) */
 #define MB_PROF_RESIDUAL 1   /* FP64 residual kernel */
 #define MB_PROF_PRECOND  2   /* one whole preconditioner application (many kernels) */
+#define MB_PROF_SMOOTH   3   /* Jacobian-vector product kernel inside the fine-level smoother */
 int mb_prof_enable(mb_cell* cell, int on);
 int mb_prof_read(mb_cell* cell, int kind, int64_t* count, double* total_ms);
 int mb_prof_reset(mb_cell* cell);

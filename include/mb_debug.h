@@ -39,6 +39,13 @@ int mb_debug_level_op(mb_cell* cell, int level, float* aself, float* off, uint8_
  * those row-equilibrated units on input). */
 int mb_debug_fine(mb_cell* cell, float* dinv, float* fc, float* rowdiag);
 
+/* The solver's own Newton residual (interface currents evaluated once per
+ * face, then the voxel rows) at u, u_old with gates gate (uint8[F]); the
+ * result equals mb_residual's up to the rounding of the summation order.
+ * Host double[n] in and out. */
+int mb_debug_residual_split(mb_cell* cell, const double* u, const double* u_old, const uint8_t* gate,
+                            double dt, double I_app, double* r);
+
 #ifdef __cplusplus
 }
 #endif

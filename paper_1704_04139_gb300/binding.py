@@ -38,7 +38,7 @@ class SolverOpts(C.Structure):
     _fields_ = [("precision", C.c_int), ("newton_tol", C.c_double), ("newton_maxit", C.c_int),
                 ("gmres_m", C.c_int), ("krylov_maxit", C.c_int), ("krylov_rtol", C.c_double),
                 ("max_passes", C.c_int), ("max_halvings", C.c_int), ("mg_coarse_cells", C.c_int),
-                ("mg_smooth", C.c_int)]
+                ("mg_smooth", C.c_int), ("mg_kcycle", C.c_int)]
 
 
 class StepInfo(C.Structure):
@@ -54,7 +54,8 @@ class StepInfo(C.Structure):
 class CellInfo(C.Structure):
     _fields_ = [("n_vox", C.c_int64), ("n_faces", C.c_int64), ("n_unknowns", C.c_int64),
                 ("nt", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("h", C.c_double),
-                ("i_1c", C.c_double), ("count", C.c_int64 * 6), ("device_bytes", C.c_int64)]
+                ("i_1c", C.c_double), ("count", C.c_int64 * 6), ("device_bytes", C.c_int64),
+                ("n_iface", C.c_int64)]
 
 
 _lib = None
@@ -98,6 +99,7 @@ def _declare(lib):
     fn("mb_debug_level_dims", C.c_int, [VP, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)])
     fn("mb_debug_level_op", C.c_int, [VP, C.c_int, VP, VP, VP])
     fn("mb_debug_fine", C.c_int, [VP, VP, VP, VP])
+    fn("mb_debug_residual_split", C.c_int, [VP, VP, VP, VP, C.c_double, C.c_double, VP])
     return lib
 
 
@@ -167,6 +169,7 @@ class Cell:
         self.shape = (nt, ny, nz)
         self.N = info.n_vox
         self.F = info.n_faces
+        self.NI = info.n_iface
         self.n = info.n_unknowns
         self.i_1c = info.i_1c
 
@@ -216,6 +219,13 @@ class Cell:
                                  float(dt), float(I_app), _ptr(r)))
         return r
 
+    def debug_residual_split(self, u, u_old, dt, I_app, gate):
+        u = np.ascontiguousarray(u, np.float64); uo = np.ascontiguousarray(u_old, np.float64)
+        r = np.empty(self.n)
+        g = np.ascontiguousarray(gate, np.uint8)
+        _check(lib().mb_debug_residual_split(self.h, _ptr(u), _ptr(uo), _ptr(g), float(dt), float(I_app), _ptr(r)))
+        return r
+
     def jvp(self, u, v, dt, gate=None):
         u = np.ascontiguousarray(u, np.float64); v = np.ascontiguousarray(v, np.float64)
         out = np.empty(self.n)
@@ -224,7 +234,7 @@ class Cell:
         return out
 
     # kernel timing (CUDA events on the launching stream) and launch counting
-    PROF_JVP, PROF_RESIDUAL, PROF_PRECOND = 0, 1, 2
+    PROF_JVP, PROF_RESIDUAL, PROF_PRECOND, PROF_SMOOTH = 0, 1, 2, 3
 
     def prof_enable(self, on=True):
         _check(lib().mb_prof_enable(self.h, 1 if on else 0))

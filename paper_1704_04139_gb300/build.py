@@ -43,7 +43,7 @@ def build(verbose=False, extra=()):
                 print(err, file=sys.stderr)
     objs = [o for o, _ in res]
     cmd = [_nvcc(), "-shared", "-o", OUT] + objs + ["-gencode", "arch=compute_103a,code=sm_103a",
-                                                    "-lcudart"]
+                                                    "-lcudart", "-Xlinker", "--no-undefined"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n%s\n%s" % (" ".join(cmd), r.stderr))

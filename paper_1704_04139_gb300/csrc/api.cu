@@ -66,6 +66,7 @@ static void fill_devparams(const mb_params& p, double h, DevParams& P) {
     P.Pl_i00 = p.Pl_i00;
     double nc = p.Pl_layer_m / p.Pl_Vm_Li;
     P.nc4 = nc * nc * nc * nc;
+    P.nc = nc;
 }
 
 cudaEvent_t Prof::get() {
@@ -108,6 +109,7 @@ void mb_opts_default(mb_solver_opts* o) {
     o->max_halvings = 6;
     o->mg_coarse_cells = 32;
     o->mg_smooth = 2;
+    o->mg_kcycle = 16;
 }
 
 static int check_opts(const mb_solver_opts* o) {
@@ -115,7 +117,7 @@ static int check_opts(const mb_solver_opts* o) {
     // gmres_m + 1 dot products must fit the 64-slot reduction buffers
     if (o->gmres_m < 1 || o->gmres_m > 63 || o->newton_maxit < 1 || o->krylov_maxit < 1 ||
         o->max_passes < 1 || o->max_halvings < 0 || o->max_halvings > 20 || !(o->newton_tol > 0) ||
-        !(o->krylov_rtol > 0))
+        !(o->krylov_rtol > 0) || o->mg_kcycle < 1 || o->mg_kcycle > 16)
         return MB_EINVAL;
     return MB_OK;
 }
@@ -140,6 +142,7 @@ int mb_cell_create(const uint8_t* labels, int nt, int ny, int nz, double h, cons
     cudaGetDevice(&c->device);
     c->D.nt = nt; c->D.ny = ny; c->D.nz = nz; c->D.N = N; c->D.syz = (int64_t)ny * nz; c->D.F = 0;
     fill_devparams(*p, h, c->P);
+    par_convert(c->P, c->Pf);
     for (int64_t i = 0; i < N; ++i) {
         if (labels[i] > 5) { set_error("mb_cell_create: labels must be in 0..5"); delete c; return MB_EINVAL; }
         c->count[labels[i]]++;
@@ -168,8 +171,11 @@ int mb_cell_create(const uint8_t* labels, int nt, int ny, int nz, double h, cons
         c->gate2 = (uint8_t*)cell_alloc(c, F);
         c->red = (double*)cell_alloc(c, 8 * (size_t)RED_BLOCKS * 64);
         c->red_out = (double*)cell_alloc(c, 8 * 64);
+        c->icoef = (float*)cell_alloc(c, 4 * (size_t)NCOEF * (c->D.NI ? c->D.NI : 1));
+        c->d_dtinv = (float*)cell_alloc(c, 256);
+        c->icur = (double*)cell_alloc(c, 16 * (size_t)(c->D.NI ? c->D.NI : 1));
         if (!c->u || !c->u_old || !c->u_pass || !c->r || !c->du || !c->u32 || !c->gate || !c->gate2 ||
-            !c->red || !c->red_out) { rc = MB_ENOMEM; break; }
+            !c->red || !c->red_out || !c->icoef || !c->d_dtinv || !c->icur) { rc = MB_ENOMEM; break; }
         if ((rc = launch_init_state(c, c->u))) break;
         if ((rc = precond_create(c))) break;
         double nG = (double)c->count[PG];
@@ -199,6 +205,7 @@ int mb_cell_info_get(mb_cell* c, mb_cell_info* info) {
     info->i_1c = c->i_1c;
     for (int i = 0; i < 6; ++i) info->count[i] = c->count[i];
     info->device_bytes = c->device_bytes;
+    info->n_iface = c->D.NI;
     return MB_OK;
 }
 
@@ -344,8 +351,10 @@ extern "C" {
 int mb_prof_enable(mb_cell* c, int on) {
     if (!c) { set_error("mb_prof_enable: invalid argument"); return MB_EINVAL; }
     cudaStreamSynchronize(c->stream);
+    precond_harvest(c);
     c->prof.enabled = on != 0;
     for (auto& r : c->prof.rec) r.clear();
+    for (int k = 0; k < PROF_NKERNELS; ++k) { c->prof.acc_ms[k] = 0.0; c->prof.acc_n[k] = 0; }
     c->prof.used = 0;
     return MB_OK;
 }
@@ -356,13 +365,14 @@ int mb_prof_read(mb_cell* c, int kind, int64_t* count, double* total_ms) {
         return MB_EINVAL;
     }
     MB_CUDA(cudaStreamSynchronize(c->stream));
-    double tot = 0.0;
+    precond_harvest(c);
+    double tot = c->prof.acc_ms[kind];
     for (auto& pr : c->prof.rec[kind]) {
         float ms = 0.f;
         MB_CUDA(cudaEventElapsedTime(&ms, pr.first, pr.second));
         tot += ms;
     }
-    *count = (int64_t)c->prof.rec[kind].size();
+    *count = (int64_t)c->prof.rec[kind].size() + c->prof.acc_n[kind];
     *total_ms = tot;
     return MB_OK;
 }
@@ -370,7 +380,9 @@ int mb_prof_read(mb_cell* c, int kind, int64_t* count, double* total_ms) {
 int mb_prof_reset(mb_cell* c) {
     if (!c) return MB_EINVAL;
     cudaStreamSynchronize(c->stream);
+    precond_harvest(c);
     for (auto& r : c->prof.rec) r.clear();
+    for (int k = 0; k < PROF_NKERNELS; ++k) { c->prof.acc_ms[k] = 0.0; c->prof.acc_n[k] = 0; }
     c->prof.used = 0;
     return MB_OK;
 }

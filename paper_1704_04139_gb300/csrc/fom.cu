@@ -30,10 +30,11 @@ __device__ inline bool forbidden_pair(int a, int b) {
 }
 
 // --------------------------------------------------- K0: face classification
-// Pass 1: per voxel, mask of electrolyte neighbours of graphite voxels and the
-// number of plating faces it owns; flags forbidden contacts.
+// Pass 1: per voxel, mask of electrolyte neighbours of solid voxels with
+// interface kinetics (G, K, L), the number of plating faces it owns (G) and
+// the number of its other interface faces (K, L); flags forbidden contacts.
 __global__ void k_classify_count(Dims D, const uint8_t* __restrict__ lab, uint8_t* __restrict__ emask,
-                                 uint32_t* __restrict__ cnt, int* __restrict__ err) {
+                                 uint32_t* __restrict__ cnt, uint32_t* __restrict__ cnt2, int* __restrict__ err) {
     int z, y, t;
     vox_coords(D, z, y, t);
     if (z >= D.nz || y >= D.ny) return;
@@ -48,13 +49,14 @@ __global__ void k_classify_count(Dims D, const uint8_t* __restrict__ lab, uint8_
         if (!inb[d]) continue;
         int lw = lab[v + off[d]];
         if (forbidden_pair(lv, lw)) atomicOr(err, 1);
-        if (lv == PG && lw == PE) m |= 1u << d;
+        if ((lv == PG || lv == PK || lv == PL) && lw == PE) m |= 1u << d;
         // collector contacts with electrode solid (bit 2: CN, bit 3: CP)
         if (lv == PCN && (lw == PG || lw == PL)) atomicOr(err, 4);
         if (lv == PCP && (lw == PK || lw == PL)) atomicOr(err, 8);
     }
     emask[v] = (uint8_t)m;
-    cnt[v] = __popc(m);
+    cnt[v] = lv == PG ? __popc(m) : 0u;
+    cnt2[v] = lv == PG ? 0u : __popc(m);
 }
 
 // Exclusive scan of uint32 counts (three kernels: block scans, scan of block
@@ -109,17 +111,23 @@ __global__ void k_scan_add(uint32_t* out, int64_t n, const uint32_t* bsum) {
     if (i < n) out[i] += bsum[i / SCAN_B];
 }
 
-// Pass 2: per-voxel code and the plating face list.
+// Pass 2: per-voxel code and the plating face list.  Interface faces are
+// numbered plating faces first (G voxels, [0, F)), then the faces of K and L
+// voxels ([F, NI)), each group by solid voxel index, then direction.
 __global__ void k_classify_write(Dims D, const uint8_t* __restrict__ lab, const uint8_t* __restrict__ emask,
-                                 const uint32_t* __restrict__ fbase, uint32_t* __restrict__ vcode,
-                                 int32_t* __restrict__ pf_g, int32_t* __restrict__ pf_e,
-                                 int8_t* __restrict__ pf_dir) {
+                                 const uint32_t* __restrict__ fbase, const uint32_t* __restrict__ kbase,
+                                 uint32_t* __restrict__ vcode, int32_t* __restrict__ pf_g,
+                                 int32_t* __restrict__ pf_e, int8_t* __restrict__ pf_dir) {
     int z, y, t;
     vox_coords(D, z, y, t);
     if (z >= D.nz || y >= D.ny) return;
     int64_t v = (int64_t)t * D.syz + (int64_t)y * D.nz + z;
     uint32_t m = emask[v];
     uint32_t fb = fbase[v];
+    if (lab[v] != PG) {
+        vcode[v] = (uint32_t)lab[v] | (m << 3) | (m ? ((uint32_t)D.F + kbase[v]) << VC_FBASE_SHIFT : 0u);
+        return;
+    }
     vcode[v] = (uint32_t)lab[v] | (m << 3) | (fb << VC_FBASE_SHIFT);
     const int64_t off[6] = {-D.syz, D.syz, -(int64_t)D.nz, (int64_t)D.nz, -1, 1};
     uint32_t f = fb;
@@ -139,24 +147,30 @@ int launch_classify(mb_cell* c, const uint8_t* d_lab) {
     int64_t N = D.N;
     int64_t nb = (N + SCAN_B - 1) / SCAN_B;
     uint8_t* emask = nullptr;
-    uint32_t *cnt = nullptr, *fbase = nullptr, *bsum = nullptr, *total = nullptr;
+    uint32_t *cnt = nullptr, *cnt2 = nullptr, *fbase = nullptr, *kbase = nullptr, *bsum = nullptr,
+             *total = nullptr;
     int* err = nullptr;
     MB_CUDA(cudaMalloc(&emask, N));
     MB_CUDA(cudaMalloc(&cnt, N * 4));
+    MB_CUDA(cudaMalloc(&cnt2, N * 4));
     MB_CUDA(cudaMalloc(&fbase, N * 4));
+    MB_CUDA(cudaMalloc(&kbase, N * 4));
     MB_CUDA(cudaMalloc(&bsum, nb * 4 + 16));
     MB_CUDA(cudaMalloc(&total, 16));
     MB_CUDA(cudaMalloc(&err, 16));
     MB_CUDA(cudaMemsetAsync(err, 0, 4, s));
-    k_classify_count<<<vox_grid(D, VOX_BLOCK), VOX_BLOCK, 0, s>>>(D, d_lab, emask, cnt, err), ::mb::count_launch(c);
+    k_classify_count<<<vox_grid(D, VOX_BLOCK), VOX_BLOCK, 0, s>>>(D, d_lab, emask, cnt, cnt2, err), ::mb::count_launch(c);
     k_scan_blocks<<<(unsigned)nb, SCAN_T, 0, s>>>(cnt, N, fbase, bsum), ::mb::count_launch(c);
     k_scan_sums<<<1, 1024, 0, s>>>(bsum, nb, total), ::mb::count_launch(c);
     k_scan_add<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(fbase, N, bsum), ::mb::count_launch(c);
+    k_scan_blocks<<<(unsigned)nb, SCAN_T, 0, s>>>(cnt2, N, kbase, bsum), ::mb::count_launch(c);
+    k_scan_sums<<<1, 1024, 0, s>>>(bsum, nb, total + 1), ::mb::count_launch(c);
+    k_scan_add<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(kbase, N, bsum), ::mb::count_launch(c);
     MB_CUDA_LAUNCH("classify");
     int h_err = 0;
-    uint32_t h_total = 0;
+    uint32_t h_tot[2] = {0, 0};
     MB_CUDA(cudaMemcpyAsync(&h_err, err, 4, cudaMemcpyDeviceToHost, s));
-    MB_CUDA(cudaMemcpyAsync(&h_total, total, 4, cudaMemcpyDeviceToHost, s));
+    MB_CUDA(cudaMemcpyAsync(h_tot, total, 8, cudaMemcpyDeviceToHost, s));
     MB_CUDA(cudaStreamSynchronize(s));
     int rc = MB_OK;
     if (h_err & 2) {
@@ -168,12 +182,14 @@ int launch_classify(mb_cell* c, const uint8_t* d_lab) {
     } else if ((c->count[PCN] > 0 && !(h_err & 4)) || (c->count[PCP] > 0 && !(h_err & 8))) {
         set_error("a current collector touches no electrode solid (its potential would float)");
         rc = MB_EBADGEOM;
-    } else if (h_total >= VC_MAX_FACES) {
-        set_error("too many plating faces for the 23-bit face index");
+    } else if ((uint64_t)h_tot[0] + h_tot[1] >= VC_MAX_FACES) {
+        set_error("too many interface faces for the 23-bit face index");
         rc = MB_EINVAL;
     }
+    const uint32_t h_total = h_tot[0];
     if (rc == MB_OK) {
         c->D.F = h_total;
+        c->D.NI = (int64_t)h_tot[0] + h_tot[1];
         c->n = 2 * N + (int64_t)h_total;
         size_t F = h_total ? h_total : 1;
         c->vcode = (uint32_t*)cell_alloc(c, N * 4);
@@ -184,12 +200,13 @@ int launch_classify(mb_cell* c, const uint8_t* d_lab) {
     }
     if (rc == MB_OK) {
         k_classify_write<<<vox_grid(D, VOX_BLOCK), VOX_BLOCK, 0, s>>>(
-            c->D, d_lab, emask, fbase, c->vcode, c->pf_g, c->pf_e, c->pf_dir), ::mb::count_launch(c);
+            c->D, d_lab, emask, fbase, kbase, c->vcode, c->pf_g, c->pf_e, c->pf_dir), ::mb::count_launch(c);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) rc = cuda_fail(e, "classify_write");
     }
     cudaStreamSynchronize(s);
-    cudaFree(emask); cudaFree(cnt); cudaFree(fbase); cudaFree(bsum); cudaFree(total); cudaFree(err);
+    cudaFree(emask); cudaFree(cnt); cudaFree(cnt2); cudaFree(fbase); cudaFree(kbase); cudaFree(bsum);
+    cudaFree(total); cudaFree(err);
     return rc;
 }
 
@@ -234,7 +251,7 @@ int launch_init_state(mb_cell* c, double* u) {
 // plating faces.
 template <class T>
 __global__ void __launch_bounds__(256)
-k_residual(DevParams P, Dims D, const uint32_t* __restrict__ vc, const T* __restrict__ u,
+k_residual(ParT<T> P, Dims D, const uint32_t* __restrict__ vc, const T* __restrict__ u,
            const double* __restrict__ uold, const uint8_t* __restrict__ gate, double dt_inv,
            double I_app, double s_i0d, double k_pld, T* __restrict__ r) {
     int z, y, t;
@@ -288,13 +305,122 @@ k_residual(DevParams P, Dims D, const uint32_t* __restrict__ vc, const T* __rest
     r[N + v] = rp;
 }
 
+// Residual in two passes (the solver's Newton residual): k_iface_current
+// evaluates the Butler-Volmer and plating current densities of every
+// interface face once (FP64; the transcendental part of the residual), then
+// k_residual_split assembles every voxel's rows from them and the bulk and
+// conduction fluxes.  Same arithmetic per term as k_residual, which
+// evaluates each interface current twice (once from each side); the C-ABI
+// residual entry points use that single-kernel form.
+__global__ void __launch_bounds__(256)
+k_iface_current(DevParams P, Dims D, const uint32_t* __restrict__ vc, const double* __restrict__ u,
+                const uint8_t* __restrict__ gate, double s_i0, double k_pl, double* __restrict__ icur) {
+    int z, y, t;
+    vox_coords(D, z, y, t);
+    if (z >= D.nz || y >= D.ny) return;
+    int64_t v = (int64_t)t * D.syz + (int64_t)y * D.nz + z;
+    uint32_t code = vc[v];
+    int lv = vc_phase(code);
+    uint32_t m = vc_emask(code);
+    if (!m || !(lv == PG || lv == PK || lv == PL)) return;
+    const int64_t N = D.N, NI = D.NI;
+    const double cs = u[v], ps = u[N + v];
+    const int64_t off[6] = {-D.syz, D.syz, -(int64_t)D.nz, (int64_t)D.nz, -1, 1};
+    int64_t i = vc_fbase(code);
+    for (int d = 0; d < 6; ++d) {
+        if (!(m & (1u << d))) continue;
+        int64_t w = v + off[d];
+        double nf = 0.0;
+        bool g = false;
+        if (lv == PG) {
+            nf = u[2 * N + i];
+            g = gate[i] != 0;
+        }
+        double ibv, ipl;
+        interface_current<double>(P, lv, cs, ps, u[w], u[N + w], nf, g, s_i0, k_pl, ibv, ipl);
+        icur[i] = ibv;
+        icur[NI + i] = ipl;
+        ++i;
+    }
+}
+
+__global__ void __launch_bounds__(256)
+k_residual_split(DevParams P, Dims D, const uint32_t* __restrict__ vc, const double* __restrict__ u,
+                 const double* __restrict__ uold, const double* __restrict__ icur, double dt_inv, double I_app,
+                 double* __restrict__ r) {
+    int z, y, t;
+    vox_coords(D, z, y, t);
+    if (z >= D.nz || y >= D.ny) return;
+    const int64_t N = D.N, NI = D.NI;
+    int64_t v = (int64_t)t * D.syz + (int64_t)y * D.nz + z;
+    const uint32_t code = vc[v];
+    const int lv = vc_phase(code);
+    const double cv = u[v], pv = u[N + v];
+    double rc = 0.0, rp = 0.0;
+    const int64_t off[6] = {-D.syz, D.syz, -(int64_t)D.nz, (int64_t)D.nz, -1, 1};
+    const bool inb[6] = {t > 0, t < D.nt - 1, y > 0, y < D.ny - 1, z > 0, z < D.nz - 1};
+    int64_t ibase = vc_fbase(code);
+#pragma unroll
+    for (int d = 0; d < 6; ++d) {
+        if (!inb[d]) continue;
+        const int64_t w = v + off[d];
+        const uint32_t cw_code = vc[w];
+        const int lw = vc_phase(cw_code);
+        if (lv == PE && lw == PE) {
+            const double cw = u[w], pw = u[N + w];
+            const double S = fmax(cv, P.cmin[PE]) + fmax(cw, P.cmin[PE]);
+            const double dc = cw - cv, dp = pw - pv;
+            const double j = -P.E_gk * dp - P.E_gm * dc / S;
+            rc += -P.E_gD * dc + P.E_tF * j;
+            rp += j;
+        } else if (lv == lw && (lv == PG || lv == PK)) {
+            rc += -P.gD[lv] * (u[w] - cv);
+            rp += -P.gsig[lv][lw] * (u[N + w] - pv);
+        } else if (lv != PE && lw != PE) {
+            rp += -P.gsig[lv][lw] * (u[N + w] - pv);
+        } else if (lw == PE && (lv == PG || lv == PK || lv == PL)) {
+            const int64_t i = ibase++;
+            const double ibv = icur[i], ipl = icur[NI + i];
+            if (lv != PL) rc += P.A * ibv * P.invF;
+            rp += P.A * (ibv + ipl);
+            if (lv == PG) r[2 * N + i] = (u[2 * N + i] - uold[2 * N + i]) * dt_inv + ipl * P.invF;
+        } else if (lv == PE && (lw == PG || lw == PK || lw == PL)) {
+            const int64_t i = (int64_t)vc_fbase(cw_code) + __popc(vc_emask(cw_code) & ((1u << opp_dir(d)) - 1u));
+            const double it = icur[i] + icur[NI + i];
+            rc -= P.A * it * P.invF;
+            rp -= P.A * it;
+        }
+    }
+    if (t == 0 && lv == PCN) rp += P.g_dir * pv;
+    if (t == D.nt - 1 && lv == PCP) rp += P.A * I_app;
+    if (has_c(lv)) rc += P.V * (cv - uold[v]) * dt_inv;
+    else rc = cv;
+    r[v] = rc;
+    r[N + v] = rp;
+}
+
+int launch_residual_split(mb_cell* c, const double* u, const double* u_old, const uint8_t* gate, double dt,
+                          double I_app, double* r, cudaStream_t s) {
+    const Dims& D = c->D;
+    cudaEvent_t ev;
+    prof_begin(c, s, &ev);
+    if (D.NI)
+        k_iface_current<<<vox_grid(D, VOX_BLOCK), VOX_BLOCK, 0, s>>>(c->P, D, c->vcode, u, gate, c->s_i0, c->k_pl,
+                                                                     c->icur), ::mb::count_launch(c);
+    k_residual_split<<<vox_grid(D, VOX_BLOCK), VOX_BLOCK, 0, s>>>(c->P, D, c->vcode, u, u_old, c->icur, 1.0 / dt,
+                                                                  I_app, r), ::mb::count_launch(c);
+    prof_end(c, s, PROF_RESIDUAL, ev);
+    MB_CUDA_LAUNCH("residual_split");
+    return MB_OK;
+}
+
 template <class T>
 int launch_residual(mb_cell* c, const T* u, const double* u_old, const uint8_t* gate, double dt,
                     double I_app, T* r, cudaStream_t s) {
     const Dims& D = c->D;
     cudaEvent_t ev;
     prof_begin(c, s, &ev);
-    k_residual<T><<<vox_grid(D, VOX_BLOCK), VOX_BLOCK, 0, s>>>(c->P, D, c->vcode, u, u_old, gate,
+    k_residual<T><<<vox_grid(D, VOX_BLOCK), VOX_BLOCK, 0, s>>>(cell_par<T>(c), D, c->vcode, u, u_old, gate,
                                                                1.0 / dt, I_app, c->s_i0, c->k_pl, r), ::mb::count_launch(c);
     prof_end(c, s, PROF_RESIDUAL, ev);
     MB_CUDA_LAUNCH("residual");
@@ -302,8 +428,6 @@ int launch_residual(mb_cell* c, const T* u, const double* u_old, const uint8_t* 
 }
 template int launch_residual<double>(mb_cell*, const double*, const double*, const uint8_t*, double,
                                      double, double*, cudaStream_t);
-template int launch_residual<float>(mb_cell*, const float*, const double*, const uint8_t*, double,
-                                    double, float*, cudaStream_t);
 
 // ------------------------------------------------------------ K2: JVP
 // J(u) v from the analytic per-face partial derivatives (chain rule through
@@ -314,14 +438,13 @@ template int launch_residual<float>(mb_cell*, const float*, const double*, const
 // E = |diag(S_r^-1 J S_u)|^-1, so that every row of the Krylov system has a
 // unit diagonal whatever its physical scale (collector and electrolyte rows
 // differ by ~1e10 otherwise).
-// TC: precision of the linearisation point and of the nonlinear per-face
-// coefficients; TV: precision of the direction x, of its differences and of
-// the result.  (TC, TV) = (double, double) is the FP64 operator, (float,
-// double) the mixed one (FP32 transcendentals/divisions, FP64 vectors), and
-// (float, float) the all-FP32 variant of the C-ABI.
+// k_jvp: direction and result in one precision TV (the FP64 and FP32 JVPs of
+// the C-ABI), all per-face coefficients evaluated on the fly.  TC: precision
+// of the linearisation point and of the nonlinear per-face coefficients.  The
+// solver itself uses the stencil form k_jvp_lin below.
 template <class TC, class TV, int MODE>
 __global__ void __launch_bounds__(256)
-k_jvp(DevParams P, Dims D, const uint32_t* __restrict__ vc, const TC* __restrict__ u,
+k_jvp(ParT<TC> P, Dims D, const uint32_t* __restrict__ vc, const TC* __restrict__ u,
       const uint8_t* __restrict__ gate, double dt_inv, double s_i0d, double k_pld,
       const TV* __restrict__ x, TV* __restrict__ y_out) {
     int z, y, t;
@@ -337,7 +460,7 @@ k_jvp(DevParams P, Dims D, const uint32_t* __restrict__ vc, const TC* __restrict
     uint32_t code = vc[v];
     int lv = vc_phase(code);
     TC cv = cc[v], pv = ph[v];
-    const TV nc = TV(sqrt(sqrt(P.nc4)));
+    const TV nc = TV(P.nc);
     const TV idt = TV(dt_inv);
     TV dcv = x[v], dpv = x[N + v];
     if (SCALED) dcv *= TV(P.cref[lv]);
@@ -374,8 +497,8 @@ k_jvp(DevParams P, Dims D, const uint32_t* __restrict__ vc, const TC* __restrict
             g = gate[f] != 0;
         }
         TV jn = TV(0), jnn = TV(0);
-        face_jvp<TC, TV>(P, lv, lw, cv, pv, cw, pw, nf, g, s_i0, k_pl, dcv, dpv, dcw, dpw, dnf, jc, jp, jn, jnn,
-                         dgc, dgp);
+        face_jvp<TC, TV>(P, lv, lw, cv, pv, cw, pw, nf, g, s_i0, k_pl, dcv, dcw, dcw - dcv, dpw - dpv, dnf, jc, jp,
+                         jn, jnn, dgc, dgp);
         if (lv == PG && lw == PE) {
             jn += dnf * idt;
             if (SCALED) jn *= TV(1) / (nc * idt);
@@ -387,7 +510,7 @@ k_jvp(DevParams P, Dims D, const uint32_t* __restrict__ vc, const TC* __restrict
         jp += TV(P.g_dir) * dpv;
         dgp += TV(P.g_dir);
     }
-    const TV Vdt = TV(P.V * dt_inv);
+    const TV Vdt = TV(P.V) * idt;
     if (has_c(lv)) {
         jc += Vdt * dcv;
         dgc += Vdt;
@@ -412,24 +535,239 @@ int launch_jvp(mb_cell* c, const TC* u, const uint8_t* gate, double dt, const TV
                int mode) {
     const Dims& D = c->D;
     const dim3 g = vox_grid(D, VOX_BLOCK);
+    const ParT<TC>& P = cell_par<TC>(c);
     cudaEvent_t ev;
     prof_begin(c, s, &ev);
     if (mode == 2)
-        k_jvp<TC, TV, 2><<<g, VOX_BLOCK, 0, s>>>(c->P, D, c->vcode, u, gate, 1.0 / dt, c->s_i0, c->k_pl, v, jv), ::mb::count_launch(c);
+        k_jvp<TC, TV, 2><<<g, VOX_BLOCK, 0, s>>>(P, D, c->vcode, u, gate, 1.0 / dt, c->s_i0, c->k_pl, v, jv), ::mb::count_launch(c);
     else if (mode == 1)
-        k_jvp<TC, TV, 1><<<g, VOX_BLOCK, 0, s>>>(c->P, D, c->vcode, u, gate, 1.0 / dt, c->s_i0, c->k_pl, v, jv), ::mb::count_launch(c);
+        k_jvp<TC, TV, 1><<<g, VOX_BLOCK, 0, s>>>(P, D, c->vcode, u, gate, 1.0 / dt, c->s_i0, c->k_pl, v, jv), ::mb::count_launch(c);
     else
-        k_jvp<TC, TV, 0><<<g, VOX_BLOCK, 0, s>>>(c->P, D, c->vcode, u, gate, 1.0 / dt, c->s_i0, c->k_pl, v, jv), ::mb::count_launch(c);
+        k_jvp<TC, TV, 0><<<g, VOX_BLOCK, 0, s>>>(P, D, c->vcode, u, gate, 1.0 / dt, c->s_i0, c->k_pl, v, jv), ::mb::count_launch(c);
     prof_end(c, s, PROF_JVP, ev);
     MB_CUDA_LAUNCH("jvp");
     return MB_OK;
 }
 template int launch_jvp<double, double>(mb_cell*, const double*, const uint8_t*, double, const double*, double*,
                                         cudaStream_t, int);
-template int launch_jvp<float, double>(mb_cell*, const float*, const uint8_t*, double, const double*, double*,
-                                       cudaStream_t, int);
 template int launch_jvp<float, float>(mb_cell*, const float*, const uint8_t*, double, const float*, float*,
                                       cudaStream_t, int);
+
+// ------------------------------------------- K2': linearised JVP (stencil)
+// The interface kinetics are the only costly part of the Jacobian (sqrt,
+// sinh, cosh, exp, the OCP and its derivative) and they are fixed during a
+// linear solve: k_lin_setup evaluates their six partial derivatives once per
+// interface face, and k_jvp_lin applies the Jacobian as a stencil on them.
+// One thread per voxel; solid voxels with electrolyte neighbours write the
+// partials of their own interface faces.
+template <class TC>
+__global__ void __launch_bounds__(256)
+k_lin_setup(ParT<TC> P, Dims D, const uint32_t* __restrict__ vc, const TC* __restrict__ u,
+            const uint8_t* __restrict__ gate, double s_i0d, double k_pld, float* __restrict__ icoef) {
+    int z, y, t;
+    vox_coords(D, z, y, t);
+    if (z >= D.nz || y >= D.ny) return;
+    int64_t v = (int64_t)t * D.syz + (int64_t)y * D.nz + z;
+    uint32_t code = vc[v];
+    int lv = vc_phase(code);
+    uint32_t m = vc_emask(code);
+    if (!m || !(lv == PG || lv == PK || lv == PL)) return;
+    const int64_t N = D.N, NI = D.NI;
+    const TC s_i0 = TC(s_i0d), k_pl = TC(k_pld);
+    const TC cs = u[v], ps = u[N + v];
+    const int64_t off[6] = {-D.syz, D.syz, -(int64_t)D.nz, (int64_t)D.nz, -1, 1};
+    int64_t i = vc_fbase(code);
+    for (int d = 0; d < 6; ++d) {
+        if (!(m & (1u << d))) continue;
+        int64_t w = v + off[d];
+        TC nf = TC(0);
+        bool g = false;
+        if (lv == PG) {   // plating face i (same index as the interface face)
+            nf = u[2 * N + i];
+            g = gate[i] != 0;
+        }
+        TC i_eta, i_cs, i_ce, ip_eta, ip_ce, ip_n;
+        interface_partials<TC>(P, lv, cs, ps, u[w], u[N + w], nf, g, s_i0, k_pl, i_eta, i_cs, i_ce, ip_eta, ip_ce,
+                               ip_n);
+        icoef[0 * NI + i] = float(i_eta);
+        icoef[1 * NI + i] = float(ip_eta);
+        icoef[2 * NI + i] = float(i_cs);
+        icoef[3 * NI + i] = float(i_ce);
+        icoef[4 * NI + i] = float(ip_ce);
+        icoef[5 * NI + i] = float(ip_n);
+        ++i;
+    }
+}
+
+template <class TC>
+int launch_lin_setup(mb_cell* c, const TC* u, const uint8_t* gate, cudaStream_t s) {
+    const Dims& D = c->D;
+    if (D.NI == 0) return MB_OK;
+    k_lin_setup<TC><<<vox_grid(D, VOX_BLOCK), VOX_BLOCK, 0, s>>>(cell_par<TC>(c), D, c->vcode, u, gate, c->s_i0,
+                                                                 c->k_pl, c->icoef), ::mb::count_launch(c);
+    MB_CUDA_LAUNCH("lin_setup");
+    return MB_OK;
+}
+template int launch_lin_setup<float>(mb_cell*, const float*, const uint8_t*, cudaStream_t);
+template int launch_lin_setup<double>(mb_cell*, const double*, const uint8_t*, cudaStream_t);
+
+// J v on a float-float direction in scaled units: MODE 1 output rows divided
+// by the residual scale s_r (the smoother's S z; face rows not written),
+// MODE 2 further multiplied by the inverse row scale rowinv (the Krylov
+// operator, face rows written).  FP32 arithmetic; differences taken before
+// rounding (see face_jvp).  Each face first selects its coefficients on
+// (dphi_w - dphi_v, dc_w - dc_v, dc_v, dc_w, dn_f) for the phi and c rows in a
+// short branch, then all faces share one update, so that a warp of mixed
+// phases pays little for divergence.  scal: [0] 1/dt, [1 + phase]
+// 1/(V c_ref/dt), [7] 1/A, [8] dt/n_c.
+template <int MODE>
+__global__ void __launch_bounds__(256)
+k_jvp_lin(ParT<float> P, Dims D, const uint32_t* __restrict__ vc, const float* __restrict__ c32,
+          const float* __restrict__ icoef, const float* __restrict__ rowinv, const float* __restrict__ scal,
+          const float2* __restrict__ x, float* __restrict__ y_out) {
+    int z, y, t;
+    vox_coords(D, z, y, t);
+    if (z >= D.nz || y >= D.ny) return;
+    constexpr bool EQUIL = MODE == 2;
+    const int syz = (int)D.syz, nz = D.nz;
+    const int NI = (int)D.NI;
+    const int v = t * syz + y * nz + z;
+    const float2* __restrict__ xp = x + D.N;        // potentials
+    const float2* __restrict__ xn = x + 2 * D.N;    // plating faces
+    const float dt_inv = scal[0];
+    const uint32_t code = vc[v];
+    const int lv = vc_phase(code);
+    const float crv = P.cref[lv], crE = P.cref[PE];
+    const float2 xcv = x[v], xpv = xp[v];
+    const float dcv = df_val(xcv) * crv, dpv = df_val(xpv);
+    const float A = P.A, AF = P.A * P.invF;
+    const bool vkin = lv == PG || lv == PK || lv == PL;
+    float jc = 0.f, jp = 0.f;
+    const int off[6] = {-syz, syz, -nz, nz, -1, 1};
+    const bool inb[6] = {t > 0, t < D.nt - 1, y > 0, y < D.ny - 1, z > 0, z < D.nz - 1};
+    int ibase = (int)vc_fbase(code);
+    // all neighbour loads first (indices clamped to v outside the grid), so
+    // that they are in flight together
+    uint32_t cwc[6];
+    float2 xpn[6], xcn[6];
+#pragma unroll
+    for (int d = 0; d < 6; ++d) {
+        const int w = inb[d] ? v + off[d] : v;
+        cwc[d] = vc[w];
+        xpn[d] = xp[w];
+        xcn[d] = x[w];
+    }
+#pragma unroll
+    for (int d = 0; d < 6; ++d) {
+        if (!inb[d]) continue;
+        const int w = v + off[d];
+        const uint32_t cw_code = cwc[d];
+        const int lw = vc_phase(cw_code);
+        const float ddp = df_diff(xpn[d], xpv);
+        const float2 xcw = xcn[d];
+        float p1 = 0.f, p2 = 0.f, p3 = 0.f, p4 = 0.f, p5 = 0.f;   // phi row
+        float q1 = 0.f, q2 = 0.f, q3 = 0.f, q4 = 0.f, q5 = 0.f;   // c row
+        float ddc = 0.f, dcw = 0.f, dnf = 0.f;
+        if (lv == PE && lw == PE) {
+            ddc = df_diff(xcw, xcv) * crE;
+            dcw = df_val(xcw) * crE;
+            const float cv = c32[v], cw = c32[w], cmin = P.cmin[PE];
+            const float iS = __frcp_rn(fmaxf(cv, cmin) + fmaxf(cw, cmin));
+            const float gr = P.E_gm * (cw - cv) * iS * iS;
+            p1 = -P.E_gk;
+            p2 = -P.E_gm * iS;
+            p3 = cv >= cmin ? gr : 0.f;
+            p4 = cw >= cmin ? gr : 0.f;
+            q1 = P.E_tF * p1;
+            q2 = -P.E_gD + P.E_tF * p2;
+            q3 = P.E_tF * p3;
+            q4 = P.E_tF * p4;
+        } else if (lv == lw && (lv == PG || lv == PK)) {
+            ddc = df_diff(xcw, xcv) * crv;
+            q2 = -P.gD[lv];
+            p1 = -P.gsig[lv][lw];
+        } else if (lv != PE && lw != PE) {
+            p1 = -P.gsig[lv][lw];   // conduction between electronic conductors
+        } else if (vkin && lw == PE) {
+            // solid v next to electrolyte w: interface face ibase (deta = -ddp)
+            const int i = ibase++;
+            const float i_eta = icoef[i], ip_eta = icoef[NI + i], i_cs = icoef[2 * NI + i];
+            const float i_ce = icoef[3 * NI + i], ip_ce = icoef[4 * NI + i], ip_n = icoef[5 * NI + i];
+            dcw = df_val(xcw) * crE;
+            if (lv == PG) dnf = df_val(xn[i]) * P.nc;
+            p1 = -A * (i_eta + ip_eta);
+            p3 = A * i_cs;
+            p4 = A * (i_ce + ip_ce);
+            p5 = A * ip_n;
+            if (lv != PL) {
+                q1 = -AF * i_eta;
+                q3 = AF * i_cs;
+                q4 = AF * i_ce;
+            }
+            if (EQUIL && lv == PG) {
+                const float dipl = -ip_eta * ddp + ip_ce * dcw + ip_n * dnf;
+                y_out[2 * D.N + i] = (P.invF * dipl + dnf * dt_inv) * scal[8] * rowinv[2 * D.N + i];
+            }
+        } else if (lv == PE && (lw == PG || lw == PK || lw == PL)) {
+            // electrolyte v next to solid w: di = (i_eta + ip_eta) ddp + i_cs dc_w + (i_ce + ip_ce) dc_v + ip_n dn
+            const int i = (int)vc_fbase(cw_code) + __popc(vc_emask(cw_code) & ((1u << opp_dir(d)) - 1u));
+            const float i_eta = icoef[i], ip_eta = icoef[NI + i], i_cs = icoef[2 * NI + i];
+            const float i_ce = icoef[3 * NI + i], ip_ce = icoef[4 * NI + i], ip_n = icoef[5 * NI + i];
+            dcw = df_val(xcw) * P.cref[lw];
+            if (lw == PG) dnf = df_val(xn[i]) * P.nc;
+            p1 = -A * (i_eta + ip_eta);
+            p3 = -A * (i_ce + ip_ce);
+            p4 = -A * i_cs;
+            p5 = -A * ip_n;
+            q1 = -AF * (i_eta + ip_eta);
+            q3 = -AF * (i_ce + ip_ce);
+            q4 = -AF * i_cs;
+            q5 = -AF * ip_n;
+        }
+        jp += p1 * ddp + p2 * ddc + p3 * dcv + p4 * dcw + p5 * dnf;
+        jc += q1 * ddp + q2 * ddc + q3 * dcv + q4 * dcw + q5 * dnf;
+    }
+    if (t == 0 && lv == PCN) jp += P.g_dir * dpv;
+    if (has_c(lv)) jc = (jc + P.V * dt_inv * dcv) * scal[1 + lv];
+    else jc = dcv;
+    jp *= scal[7];
+    if (EQUIL) {
+        jc *= rowinv[v];
+        jp *= rowinv[D.N + v];
+    }
+    y_out[v] = jc;
+    y_out[D.N + v] = jp;
+}
+
+// per-solve scalars of k_jvp_lin (layout there), one thread
+__global__ void k_set_scal(DevParams P, double dt, float* scal) {
+    const double idt = 1.0 / dt;
+    scal[0] = float(idt);
+    for (int l = 0; l < 6; ++l) scal[1 + l] = float(1.0 / (P.V * idt * P.cref[l]));
+    scal[7] = float(1.0 / P.A);
+    scal[8] = float(1.0 / (P.nc * idt));
+}
+
+int set_dt(mb_cell* c, double dt, cudaStream_t s) {
+    k_set_scal<<<1, 1, 0, s>>>(c->P, dt, c->d_dtinv), ::mb::count_launch(c);
+    MB_CUDA_LAUNCH("set_dt");
+    return MB_OK;
+}
+
+int launch_jvp_lin(mb_cell* c, const float2* v, float* jv, cudaStream_t s, int mode) {
+    const Dims& D = c->D;
+    const dim3 g = vox_grid(D, VOX_BLOCK);
+    const float* sc = c->d_dtinv;
+    cudaEvent_t ev;
+    prof_begin(c, s, &ev);
+    if (mode == 2)
+        k_jvp_lin<2><<<g, VOX_BLOCK, 0, s>>>(c->Pf, D, c->vcode, c->u32, c->icoef, c->rowinv, sc, v, jv), ::mb::count_launch(c);
+    else
+        k_jvp_lin<1><<<g, VOX_BLOCK, 0, s>>>(c->Pf, D, c->vcode, c->u32, c->icoef, c->rowinv, sc, v, jv), ::mb::count_launch(c);
+    prof_end(c, s, mode == 2 ? PROF_JVP : PROF_SMOOTH, ev);
+    MB_CUDA_LAUNCH("jvp_lin");
+    return MB_OK;
+}
 
 // ------------------------------------------------------------ plating gates
 __global__ void k_gate(Dims D, const int32_t* __restrict__ pg, const int32_t* __restrict__ pe,
@@ -467,31 +805,35 @@ int launch_gate_residual_unprofiled(mb_cell* c, const double* u, const double* u
 // ------------------------------------------------------------ reductions
 // Deterministic reductions (mb_reduce.cuh).
 __global__ void __launch_bounds__(RED_THREADS)
-k_scaled_max(DevParams P, Dims D, const uint32_t* __restrict__ vc, const double* __restrict__ x,
-             int which, double dt_inv, double* partials) {
+k_scaled_max(Dims D, const uint32_t* __restrict__ vc, const double* __restrict__ x, InvScales is,
+             double* partials) {
     double acc[1] = {0.0};
     int64_t n = 2 * D.N + D.F;
-    double nc = sqrt(sqrt(P.nc4));
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         double s;
-        if (i < D.N) {
-            int l = vc_phase(vc[i]);
-            s = which == 0 ? P.cref[l] : (has_c(l) ? P.V * P.cref[l] * dt_inv : 1.0);
-        } else if (i < 2 * D.N) {
-            s = which == 0 ? 1.0 : P.A;
-        } else {
-            s = which == 0 ? nc : nc * dt_inv;
-        }
-        double a = fabs(x[i]) / s;
+        if (i < D.N) s = is.c[vc_phase(vc[i])];
+        else if (i < 2 * D.N) s = is.phi;
+        else s = is.n;
+        double a = fabs(x[i]) * s;
         if (!(a == a)) a = 1e300;   // NaN -> huge
         acc[0] = fmax(acc[0], a);
     }
     block_reduce_store<1, true>(acc, partials);
 }
 
+InvScales inv_scales(const mb_cell* c, int which, double dt) {
+    InvScales is;
+    const DevParams& P = c->P;
+    for (int l = 0; l < 6; ++l)
+        is.c[l] = which == 0 ? 1.0 / P.cref[l] : (has_c(l) ? dt / (P.V * P.cref[l]) : 1.0);
+    is.phi = which == 0 ? 1.0 : 1.0 / P.A;
+    is.n = which == 0 ? 1.0 / P.nc : dt / P.nc;
+    return is;
+}
+
 int scaled_maxnorm(mb_cell* c, const double* x, int which, double dt, double* out) {
     cudaStream_t s = c->stream;
-    k_scaled_max<<<RED_BLOCKS, RED_THREADS, 0, s>>>(c->P, c->D, c->vcode, x, which, 1.0 / dt, c->red), ::mb::count_launch(c);
+    k_scaled_max<<<RED_BLOCKS, RED_THREADS, 0, s>>>(c->D, c->vcode, x, inv_scales(c, which, dt), c->red), ::mb::count_launch(c);
     k_reduce_final<true><<<1, RED_THREADS, 0, s>>>(c->red, 1, c->red_out), ::mb::count_launch(c);
     MB_CUDA_LAUNCH("scaled_max");
     MB_CUDA(cudaMemcpyAsync(c->h_red, c->red_out, 8, cudaMemcpyDeviceToHost, s));

@@ -6,6 +6,7 @@
 #include <vector>
 
 #include "../../include/mb.h"
+#include "mb_df.cuh"
 #include "mb_model.cuh"
 
 namespace mb {
@@ -32,20 +33,35 @@ struct DBuf {
 };
 
 struct Precond;   // multigrid preconditioner (precond.cu)
-template <class T> struct Krylov;   // FGMRES workspace (solver.cu)
+struct Krylov;    // FGMRES workspace (solver.cu)
 
 // Kernel timing and launch counting (mb_prof_* in the C-ABI).  When enabled,
 // launches of the timed kernel classes are bracketed by CUDA events recorded
 // on the launching stream; every kernel launch of the library increments the
 // cell's launch counter whether or not timing is enabled.
-enum ProfKernel { PROF_JVP = 0, PROF_RESIDUAL = 1, PROF_PRECOND = 2, PROF_NKERNELS = 3 };
+enum ProfKernel { PROF_JVP = 0, PROF_RESIDUAL = 1, PROF_PRECOND = 2, PROF_SMOOTH = 3, PROF_NKERNELS = 4 };
+struct ProfPair {
+    cudaEvent_t e0, e1;
+    int kind;
+};
 struct Prof {
     bool enabled = false;
     std::vector<cudaEvent_t> pool;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> rec[PROF_NKERNELS];
     size_t used = 0;
+    // While a CUDA graph is captured, timed launches record dedicated events
+    // (graph nodes) into *capture; their times are harvested into acc_* after
+    // each execution of the graph.
+    std::vector<ProfPair>* capture = nullptr;
+    double acc_ms[PROF_NKERNELS] = {};
+    int64_t acc_n[PROF_NKERNELS] = {};
     cudaEvent_t get();
 };
+
+// Interface partial derivatives stored per interface face (structure of
+// arrays, entry k of face i at [k * NI + i]): d i_bv/d eta, d i_pl/d eta,
+// d i_bv/d c_s, d i_bv/d c_e, d i_pl/d c_e, d i_pl/d n (A/m^2 per unit).
+constexpr int NCOEF = 6;
 
 // Reduction scratch (deterministic two-pass reductions).
 constexpr int RED_BLOCKS = 1216;      // 8 x 152 SMs
@@ -58,6 +74,7 @@ struct mb_cell {
     cudaStream_t stream = nullptr;
     mb::Dims D{};
     mb::DevParams P{};
+    mb::DevParamsF Pf{};           // FP32 copy of P for the FP32 kernels
     mb_params prm{};
     mb_solver_opts opt{};
     double s_i0 = 1.0, k_pl = 1.0;
@@ -87,28 +104,45 @@ struct mb_cell {
 
     // mixed precision copies
     float* u32 = nullptr;          // n (linearisation point)
+    float* icoef = nullptr;        // NCOEF x NI interface partials at the linearisation point
+    double* icur = nullptr;        // 2 x NI interface currents (Butler-Volmer, plating) of the residual
+    float* d_dtinv = nullptr;      // per-solve scalars of the stencil JVP (1/dt and row scales)
     float* rowdiag = nullptr;      // n: |diagonal| of the scaled Jacobian rows (Krylov equilibration)
+    float* rowinv = nullptr;       // n: 1 / rowdiag
 
     mb::Precond* pc = nullptr;
-    mb::Krylov<double>* kd = nullptr;
+    mb::Krylov* kd = nullptr;
 
     mb::Prof prof;
     int64_t launches = 0;          // kernel launches issued by the library for this cell
 };
 
 namespace mb {
+// parameter table in the arithmetic type of a kernel
+template <class T> inline const ParT<T>& cell_par(const mb_cell* c);
+template <> inline const ParT<double>& cell_par<double>(const mb_cell* c) { return c->P; }
+template <> inline const ParT<float>& cell_par<float>(const mb_cell* c) { return c->Pf; }
+
 // count n launches; bracket timed launches with events when profiling is on
 inline void count_launch(mb_cell* c, int n = 1) { c->launches += n; }
 inline void prof_begin(mb_cell* c, cudaStream_t s, cudaEvent_t* ev) {
     *ev = nullptr;
     if (c->prof.enabled) {
-        *ev = c->prof.get();
+        if (c->prof.capture) cudaEventCreate(ev);
+        else *ev = c->prof.get();
         cudaEventRecord(*ev, s);
     }
 }
 inline void prof_end(mb_cell* c, cudaStream_t s, int kind, cudaEvent_t ev0) {
     if (c->prof.enabled && ev0) {
-        cudaEvent_t ev1 = c->prof.get();
+        cudaEvent_t ev1 = nullptr;
+        if (c->prof.capture) {
+            cudaEventCreate(&ev1);
+            cudaEventRecord(ev1, s);
+            c->prof.capture->push_back({ev0, ev1, kind});
+            return;
+        }
+        ev1 = c->prof.get();
         cudaEventRecord(ev1, s);
         c->prof.rec[kind].push_back({ev0, ev1});
     }
@@ -125,16 +159,38 @@ int launch_init_state(mb_cell* c, double* u);
 template <class T>
 int launch_residual(mb_cell* c, const T* u, const double* u_old, const uint8_t* gate, double dt,
                     double I_app, T* r, cudaStream_t s);
+// the same FP64 residual in two passes (interface currents once per face into
+// c->icur, then the voxel rows): the solver's Newton residual
+int launch_residual_split(mb_cell* c, const double* u, const double* u_old, const uint8_t* gate, double dt,
+                          double I_app, double* r, cudaStream_t s);
 // mode 0: J v;  1: S_r^-1 J S_u v (scaled units);  2: the scaled rows further divided by
 // the magnitude of their diagonal entry (the row-equilibrated Krylov operator)
 template <class TC, class TV>
 int launch_jvp(mb_cell* c, const TC* u, const uint8_t* gate, double dt, const TV* v, TV* jv,
                cudaStream_t s, int mode = 0);
+// interface partials at the linearisation point u (FP64 state in FP64, or its
+// FP32 copy in FP32) into c->icoef
+template <class TC>
+int launch_lin_setup(mb_cell* c, const TC* u, const uint8_t* gate, cudaStream_t s);
+// J v from the stored interface partials (c->icoef), the FP32 concentrations
+// c->u32, the row scales c->rowdiag and 1/dt from c->d_dtinv, on a float-float
+// direction v in scaled units, FP32 result; mode 1: rows divided by the
+// residual scale (the smoother's S z), mode 2: further divided by the row
+// scale (the row-equilibrated Krylov operator)
+int launch_jvp_lin(mb_cell* c, const float2* v, float* jv, cudaStream_t s, int mode);
+// c->d_dtinv = 1/dt (stream-ordered)
+int set_dt(mb_cell* c, double dt, cudaStream_t s);
 int launch_gate(mb_cell* c, const double* u, const double* n_old, uint8_t* gate, cudaStream_t s);
 // Gates at u_old written into gate_scratch (F bytes), then the FP64 residual
 // reading them, both on stream s; no profiling events, no allocation.
 int launch_gate_residual_unprofiled(mb_cell* c, const double* u, const double* u_old, uint8_t* gate_scratch,
                                     double dt, double I_app, double* r, cudaStream_t s);
+// inverse scales of the unknowns (which = 0: c_ref, 1, n_c) or of the
+// residual rows (which = 1: V c_ref / dt or 1 for rows without c, A, n_c / dt)
+struct InvScales {
+    double c[6], phi, n;
+};
+InvScales inv_scales(const mb_cell* c, int which, double dt);
 // scaled max norms: which = 0 unknown scale, 1 residual scale (needs dt)
 int scaled_maxnorm(mb_cell* c, const double* x, int which, double dt, double* out);
 int functionals(mb_cell* c, const double* u, mb_step_info* info);
@@ -145,9 +201,14 @@ int precond_create(mb_cell* c);
 void precond_destroy(mb_cell* c);
 // build at linearisation point u32 (float) for time step dt with gates
 int precond_setup(mb_cell* c, const float* u32, const uint8_t* gate, double dt);
-// z = M^{-1} r (FP64 vectors of length n, row-equilibrated Krylov units); uses the fine JVP at u32
-int precond_apply(mb_cell* c, const float* u32, const uint8_t* gate, double dt, const double* r,
-                  double* z);
+// z = M^{-1} r (length n, row-equilibrated Krylov units; r FP32, z float-float);
+// uses the stencil JVP at the current linearisation.  With graph = true the
+// whole application is replayed from a CUDA graph captured once per (r, z)
+// buffer pair.
+int precond_apply(mb_cell* c, const float* u32, const uint8_t* gate, double dt, const float* r, float2* z,
+                  bool graph = true);
+// add the kernel times of the last graph execution to the profile totals
+void precond_harvest(mb_cell* c);
 
 // ---- solver.cu ----
 int newton_step(mb_cell* c, double dt, double I_app, mb_step_info* info);

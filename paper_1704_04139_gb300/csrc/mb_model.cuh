@@ -6,8 +6,9 @@
 // Eqs. (ise_gr), (ise_li) and the plating/stripping kinetics of Eq. (iplel)
 // with the regulariser f_pre of Sec. 2.3.  Everything is written from the
 // point of view of one voxel v and one neighbour w; the face's contribution
-// to v's rows is returned.  T is double (plain path, outer Newton residual)
-// or float (mixed-precision Krylov operator).
+// to v's rows is returned.  T is double (outer Newton residual, FP64
+// linearisation) or float (Jacobian coefficients of the preconditioner and
+// of the mixed-precision Krylov operator).
 #pragma once
 #include <stdint.h>
 #include <cuda_runtime.h>
@@ -17,7 +18,8 @@ namespace mb {
 enum Phase : int { PE = 0, PG = 1, PK = 2, PL = 3, PCN = 4, PCP = 5 };
 
 // per-voxel code: bits 0-2 phase, bits 3-8 mask of electrolyte neighbours of a
-// graphite voxel (bit d = direction d), bits 9-31 index of its first plating face
+// solid voxel with interface kinetics (G, K, L; bit d = direction d), bits
+// 9-31 index of its first interface face (for G: its first plating face)
 constexpr int VC_FBASE_SHIFT = 9;
 constexpr uint32_t VC_MAX_FACES = (1u << 23);
 __host__ __device__ inline int vc_phase(uint32_t c) { return int(c & 7u); }
@@ -28,28 +30,44 @@ __device__ inline int opp_dir(int d) { return d ^ 1; }
 struct Dims {
     int nt, ny, nz;
     int64_t N;      // voxels
-    int64_t F;      // plating faces
+    int64_t F;      // plating faces (graphite-electrolyte)
+    int64_t NI;     // interface faces: plating faces, then cathode/foil-electrolyte faces
     int64_t syz;    // ny*nz
 };
 
-// Constants of the model with the voxel geometry folded in (A = h^2).
-struct DevParams {
-    double h, A, V;
-    double invF, f2;               // 1/F, F/(2RT)
-    double E_gD;                   // A D_E / h
-    double E_gk;                   // A kappa / h
-    double E_gm;                   // A 2 kappa (t+ - 1) (RT/F) TDF / h  (divided by c_a + c_b)
-    double E_tF;                   // t+ / F
-    double cmin[6];                // concentration clamp per phase
-    double cref[6];                // concentration scale per phase (1 where no c)
-    double gD[6];                  // A D_s / h for G, K
-    double gsig[6][6];             // A sigma_face / h for conductor pairs (harmonic mean)
-    double i00[6];                 // BV prefactor per solid phase (G, K: i00; L: i00_L)
-    double icmax[6];
-    double ocpG[7], ocpK[7];
-    double g_dir;                  // 2 A sigma_CN / h  (Dirichlet half-voxel ghost)
-    double Pl_i00, nc4;            // plating prefactor, n_c^4
+// Constants of the model with the voxel geometry folded in (A = h^2), in
+// the arithmetic type T of the kernels that read them: the FP32 kernels get
+// an FP32 copy so that no parameter is converted from FP64 on the device.
+// Every member has type T (par_convert relies on that).
+template <class T>
+struct ParT {
+    T h, A, V;
+    T invF, f2;                    // 1/F, F/(2RT)
+    T E_gD;                        // A D_E / h
+    T E_gk;                        // A kappa / h
+    T E_gm;                        // A 2 kappa (t+ - 1) (RT/F) TDF / h  (divided by c_a + c_b)
+    T E_tF;                        // t+ / F
+    T cmin[6];                     // concentration clamp per phase
+    T cref[6];                     // concentration scale per phase (1 where no c)
+    T gD[6];                       // A D_s / h for G, K
+    T gsig[6][6];                  // A sigma_face / h for conductor pairs (harmonic mean)
+    T i00[6];                      // BV prefactor per solid phase (G, K: i00; L: i00_L)
+    T icmax[6];
+    T ocpG[7], ocpK[7];
+    T g_dir;                       // 2 A sigma_CN / h  (Dirichlet half-voxel ghost)
+    T Pl_i00, nc4, nc;             // plating prefactor, n_c^4, n_c
 };
+using DevParams = ParT<double>;
+using DevParamsF = ParT<float>;
+
+// member-wise conversion (both structs are plain arrays of their type)
+template <class A, class B>
+inline void par_convert(const ParT<A>& a, ParT<B>& b) {
+    static_assert(sizeof(ParT<A>) / sizeof(A) == sizeof(ParT<B>) / sizeof(B), "ParT layout");
+    const A* src = reinterpret_cast<const A*>(&a);
+    B* dst = reinterpret_cast<B*>(&b);
+    for (size_t i = 0; i < sizeof(ParT<A>) / sizeof(A); ++i) dst[i] = B(src[i]);
+}
 
 __host__ __device__ inline bool is_conductor(int p) { return p != PE; }
 __host__ __device__ inline bool has_c(int p) { return p == PE || p == PG || p == PK; }
@@ -57,11 +75,11 @@ __host__ __device__ inline bool has_c(int p) { return p == PE || p == PG || p ==
 template <class T> __device__ inline T tmax(T a, T b) { return a > b ? a : b; }
 
 template <class T>
-__device__ inline T ocp_val(const double* a, T x) {
+__device__ inline T ocp_val(const T* a, T x) {
     return T(a[0]) + T(a[1]) * x + T(a[2]) * exp(-T(a[3]) * x) + T(a[4]) * tanh((x - T(a[5])) / T(a[6]));
 }
 template <class T>
-__device__ inline T ocp_der(const double* a, T x) {   // dU0/dx
+__device__ inline T ocp_der(const T* a, T x) {   // dU0/dx
     T th = tanh((x - T(a[5])) / T(a[6]));
     return T(a[1]) - T(a[2]) * T(a[3]) * exp(-T(a[3]) * x) + T(a[4]) / T(a[6]) * (T(1) - th * th);
 }
@@ -70,7 +88,7 @@ __device__ inline T ocp_der(const double* a, T x) {   // dU0/dx
 // Butler-Volmer part ibv (Eq. ise_gr for G and K, Eq. ise_li for L) and the
 // plating part ipl (Eq. iplel, graphite faces with an active gate).
 template <class T>
-__device__ inline void interface_current(const DevParams& P, int ls, T cs, T ps, T ce, T pe, T nf,
+__device__ inline void interface_current(const ParT<T>& P, int ls, T cs, T ps, T ce, T pe, T nf,
                                          bool gate, T s_i0, T k_pl, T& ibv, T& ipl) {
     const T f2 = T(P.f2);
     ipl = T(0);
@@ -96,7 +114,7 @@ __device__ inline void interface_current(const DevParams& P, int ls, T cs, T ps,
 // Contribution of face (v, w) to v's rows R_c(v), R_phi(v); for a graphite
 // v next to electrolyte w also returns i_pl (for the face row R_n).
 template <class T>
-__device__ inline void face_residual(const DevParams& P, int lv, int lw, T cv, T pv, T cw, T pw,
+__device__ inline void face_residual(const ParT<T>& P, int lv, int lw, T cv, T pv, T cw, T pw,
                                      T nf, bool gate, T s_i0, T k_pl, T& rc, T& rp, T& ipl_out) {
     if (lv == PE && lw == PE) {
         T S = tmax(cv, T(P.cmin[PE])) + tmax(cw, T(P.cmin[PE]));
@@ -132,7 +150,7 @@ struct FaceJac {
 };
 
 template <class T>
-__device__ inline void interface_partials(const DevParams& P, int ls, T cs, T ps, T ce, T pe, T nf,
+__device__ inline void interface_partials(const ParT<T>& P, int ls, T cs, T ps, T ce, T pe, T nf,
                                           bool gate, T s_i0, T k_pl,
                                           T& i_eta, T& i_cs, T& i_ce,
                                           T& ip_eta, T& ip_ce, T& ip_n) {
@@ -147,7 +165,7 @@ __device__ inline void interface_partials(const DevParams& P, int ls, T cs, T ps
     T me = ce >= T(P.cmin[PE]) ? T(1) : T(0);
     T csa = tmax(cs, T(P.cmin[ls]));
     T cea = tmax(ce, T(P.cmin[PE]));
-    const double* a = ls == PG ? P.ocpG : P.ocpK;
+    const T* a = ls == PG ? P.ocpG : P.ocpK;
     T x = csa * T(P.icmax[ls]);
     T eta = ps - ocp_val<T>(a, x) - pe;
     T k0 = T(2) * T(P.i00[ls]) * s_i0;
@@ -173,7 +191,7 @@ __device__ inline void interface_partials(const DevParams& P, int ls, T cs, T ps
 }
 
 template <class T>
-__device__ inline void face_jacobian(const DevParams& P, int lv, int lw, T cv, T pv, T cw, T pw,
+__device__ inline void face_jacobian(const ParT<T>& P, int lv, int lw, T cv, T pv, T cw, T pw,
                                      T nf, bool gate, T s_i0, T k_pl, FaceJac<T>& J) {
 #pragma unroll
     for (int k = 0; k < 5; ++k) { J.c[k] = T(0); J.p[k] = T(0); J.n[k] = T(0); }
@@ -226,31 +244,34 @@ __device__ inline void face_jacobian(const DevParams& P, int lv, int lw, T cv, T
 
 // Directional derivative of one face's contribution to v's rows, written so
 // that every conduction, diffusion and overpotential coupling multiplies a
-// difference of the direction's entries (g (dx_v - dx_w), i_eta (dPhi_s -
-// dphi_e)).  A uniform shift of a conductor's potential then produces an
-// exactly zero flux change even in FP32, which keeps the weakly pinned modes
-// (particles and electrolyte held only by Butler-Volmer conductances ~1e-6 of
-// the bulk ones) intact; multiplying absolute entries and subtracting would
-// leave rounding of the size of those conductances.  Also returns the
-// diagonal entries dR_c(v)/dc_v, dR_phi(v)/dphi_v of this face (dgc, dgp) and,
-// for a graphite v next to electrolyte w, the face row's change jn and its
-// diagonal d(i_pl/F)/dn (jnn, without the 1/dt of the storage term).
+// difference of the direction's entries (g (dx_w - dx_v), i_eta (dPhi_s -
+// dphi_e)).  The caller passes those differences, ddc = dc_w - dc_v (used only
+// between voxels of one phase) and ddp = dphi_w - dphi_v, computed from the
+// direction's full-precision storage (float-float or FP64), so that a uniform
+// shift of a conductor's potential produces an exactly zero flux change and
+// the weakly pinned modes (particles and electrolyte held only by
+// Butler-Volmer conductances ~1e-6 of the bulk ones) survive FP32 arithmetic;
+// multiplying absolute entries and subtracting would leave rounding of the
+// size of those conductances.  dc_v, dc_w, dn_f enter only through terms
+// without cancellation.  Also returns the diagonal entries dR_c(v)/dc_v,
+// dR_phi(v)/dphi_v of this face (dgc, dgp) and, for a graphite v next to
+// electrolyte w, the face row's change jn and its diagonal d(i_pl/F)/dn (jnn,
+// without the 1/dt of the storage term).
 // TC: precision of the state and of the nonlinear coefficients (sqrt, sinh,
-// cosh, exp, OCP, divisions); TV: precision of the direction, its
-// differences and the accumulated result.
+// cosh, exp, OCP, divisions); TV: precision of the direction and of the
+// accumulated result.
 template <class TC, class TV>
-__device__ inline void face_jvp(const DevParams& P, int lv, int lw, TC cv, TC pv, TC cw, TC pw, TC nf, bool gate,
-                                TC s_i0, TC k_pl, TV dcv, TV dpv, TV dcw, TV dpw, TV dnf, TV& jc, TV& jp, TV& jn,
+__device__ inline void face_jvp(const ParT<TC>& P, int lv, int lw, TC cv, TC pv, TC cw, TC pw, TC nf, bool gate,
+                                TC s_i0, TC k_pl, TV dcv, TV dcw, TV ddc, TV ddp, TV dnf, TV& jc, TV& jp, TV& jn,
                                 TV& jnn, TV& dgc, TV& dgp) {
     if (lv == PE && lw == PE) {
-        TC cmin = TC(P.cmin[PE]);
+        TC cmin = P.cmin[PE];
         TC mv = cv >= cmin ? TC(1) : TC(0), mw = cw >= cmin ? TC(1) : TC(0);
         TC S = tmax(cv, cmin) + tmax(cw, cmin);
         TC iS = TC(1) / S;
         TC dc = cw - cv;
         TC r = dc * iS * iS;
-        TC gm = TC(P.E_gm), gk = TC(P.E_gk), tF = TC(P.E_tF), gD = TC(P.E_gD);
-        TV ddc = dcw - dcv, ddp = dpw - dpv;
+        TC gm = P.E_gm, gk = P.E_gk, tF = P.E_tF, gD = P.E_gD;
         // j = -gk dphi - gm dc/S ;  d(dc/S) = ddc/S - dc/S^2 (m_v dc_v + m_w dc_w)
         TV dj = -TV(gk) * ddp - TV(gm) * (ddc * TV(iS) - TV(r) * (TV(mv) * dcv + TV(mw) * dcw));
         jc += -TV(gD) * ddc + TV(tF) * dj;
@@ -259,36 +280,36 @@ __device__ inline void face_jvp(const DevParams& P, int lv, int lw, TC cv, TC pv
         dgc += TV(gD + tF * jcv);
         dgp += TV(gk);
     } else if (lv == lw && (lv == PG || lv == PK)) {
-        TV gD = TV(TC(P.gD[lv])), gs = TV(TC(P.gsig[lv][lw]));
-        jc += -gD * (dcw - dcv);
-        jp += -gs * (dpw - dpv);
+        TV gD = TV(P.gD[lv]), gs = TV(P.gsig[lv][lw]);
+        jc += -gD * ddc;
+        jp += -gs * ddp;
         dgc += gD;
         dgp += gs;
     } else if (is_conductor(lv) && is_conductor(lw)) {
-        TV gs = TV(TC(P.gsig[lv][lw]));
-        jp += -gs * (dpw - dpv);
+        TV gs = TV(P.gsig[lv][lw]);
+        jp += -gs * ddp;
         dgp += gs;
     } else if (lw == PE && (lv == PG || lv == PK || lv == PL)) {
         TC i_eta, i_cs, i_ce, ip_eta, ip_ce, ip_n;
         interface_partials<TC>(P, lv, cv, pv, cw, pw, nf, gate, s_i0, k_pl, i_eta, i_cs, i_ce, ip_eta, ip_ce, ip_n);
-        TV deta = dpv - dpw;
+        TV deta = -ddp;   // dPhi_s - dphi_e
         TV dibv = TV(i_eta) * deta + TV(i_cs) * dcv + TV(i_ce) * dcw;
         TV dipl = TV(ip_eta) * deta + TV(ip_ce) * dcw + TV(ip_n) * dnf;
-        TV A = TV(TC(P.A)), AF = TV(TC(P.A) * TC(P.invF));
+        TV A = TV(P.A), AF = TV(P.A * P.invF);
         if (lv != PL) {
             jc += AF * dibv;
             dgc += AF * TV(i_cs);
         }
         jp += A * (dibv + dipl);
         dgp += A * TV(i_eta + ip_eta);
-        jn = TV(TC(P.invF)) * dipl;
-        jnn = TV(TC(P.invF) * ip_n);
+        jn = TV(P.invF) * dipl;
+        jnn = TV(P.invF * ip_n);
     } else if (lv == PE && (lw == PG || lw == PK || lw == PL)) {
         TC i_eta, i_cs, i_ce, ip_eta, ip_ce, ip_n;
         interface_partials<TC>(P, lw, cw, pw, cv, pv, nf, gate, s_i0, k_pl, i_eta, i_cs, i_ce, ip_eta, ip_ce, ip_n);
-        TV deta = dpw - dpv;
+        TV deta = ddp;    // dPhi_s - dphi_e with the solid at w
         TV di = TV(i_eta + ip_eta) * deta + TV(i_cs) * dcw + TV(i_ce + ip_ce) * dcv + TV(ip_n) * dnf;
-        TV A = TV(TC(P.A)), AF = TV(TC(P.A) * TC(P.invF));
+        TV A = TV(P.A), AF = TV(P.A * P.invF);
         jc -= AF * di;
         jp -= A * di;
         dgc += -AF * TV(i_ce + ip_ce);

@@ -28,6 +28,28 @@ __device__ inline void block_reduce_store(double (&acc)[K], double* partials) {
     }
 }
 
+// Sums of FP32 per-thread partials: FP32 within a warp (32 terms), FP64
+// across the block's warps and blocks, so that per-element work stays off the
+// FP64 pipe.
+template <int K>
+__device__ inline void block_reduce_store_f32(float (&acc)[K], double* partials) {
+    __shared__ double sh[K][RED_THREADS / 32];
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        float a = acc[k];
+        for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+        if (lane == 0) sh[k][wid] = (double)a;
+    }
+    __syncthreads();
+    if (threadIdx.x < K) {
+        int k = threadIdx.x;
+        double a = sh[k][0];
+        for (int w = 1; w < RED_THREADS / 32; ++w) a += sh[k][w];
+        partials[k * RED_BLOCKS + blockIdx.x] = a;
+    }
+}
+
 // one block (RED_THREADS threads) per result k; out[k] = reduction of partials[k][*]
 template <bool MAX>
 __global__ void k_reduce_final(const double* __restrict__ partials, int K, double* __restrict__ out) {

@@ -15,13 +15,17 @@
 // 3. Coarse levels: aggregation of 2x2x2 blocks split by class
 //    (0 electrolyte c, 1 electrolyte phi, 2 anode-side phi: G, CN,
 //    3 cathode-side phi: K, CP, L); Galerkin operators with piecewise-constant
-//    prolongation stored per coarse cell as a 4x4 self block and six 4x4
-//    outgoing blocks.  The self block is (row sums by class) - (outgoing
-//    couplings), so the large intra-phase conductances never cancel.
+//    prolongation stored per coarse cell as the block row sums by class (ex)
+//    and six 4x4 outgoing blocks (off), applied in difference form
+//    A x = ex x_i + sum_d off_d (x_nb - x_i), so that the large intra-phase
+//    conductances never meet the iterate's large near-null components.
 //    Level 1 is solved by a K-cycle: FGMRES(KCYC) run entirely on the device,
 //    preconditioned by a V-cycle (NU damped 4x4 block-Jacobi sweeps before and
 //    after each coarse correction); the coarsest level is solved with an
-//    explicit FP64 inverse.  Coarse vectors are FP64, operators FP32.
+//    explicit FP64 inverse.
+// Precision: all arithmetic of the application is FP32; iterates and
+// corrections (z, coarse x, K-cycle directions) are float-float, residuals and
+// Krylov bases FP32, operators FP32.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdio.h>
@@ -37,51 +41,96 @@ constexpr int NCLS = 4;
 constexpr int BLK = NCLS * NCLS;          // 16 floats per 4x4 block
 constexpr int OFFW = 6 * BLK;             // 96 floats of outgoing couplings per cell
 constexpr float OMEGA_FINE = 0.8f;
-constexpr double OMEGA_COARSE = 0.7;
-constexpr double ALPHA = 1.0;             // scaling of coarse corrections below level 1
+constexpr float OMEGA_COARSE = 0.7f;
 constexpr int NU = 2;                     // smoothing sweeps per coarse level (pre and post)
 constexpr int NU_FINE = 4;                // fine-level block-Jacobi sweeps (pre and post)
-constexpr int KCYC = 16;                  // FGMRES iterations of the level-1 K-cycle (<= 16)
+constexpr int KCYC_MAX = 16;              // longest level-1 K-cycle (FGMRES iterations)
 constexpr int MAX_LEVELS = 16;
 constexpr int COARSE_MAX = 256;           // dense coarsest system size bound (4 x cells)
 constexpr int FCW = 8;                    // floats of condensation coefficients per face
 
-// coarse-level vectors are FP64: FP32 coarse iterates lose the weakly
-// coupled (Butler-Volmer) modes to rounding, while FP32 operators are fine
-struct alignas(32) D4 {
-    double x, y, z, w;
+// float-float 4-vector of one coarse cell
+struct alignas(32) DF4 {
+    float4 h, l;
 };
-__host__ __device__ inline D4 d4(double a, double b, double c, double d) { return D4{a, b, c, d}; }
+__device__ inline float4 df4_val(const DF4& a) {
+    return make_float4(a.h.x + a.l.x, a.h.y + a.l.y, a.h.z + a.l.z, a.h.w + a.l.w);
+}
+__device__ inline float4 df4_diff(const DF4& a, const DF4& b) {
+    return make_float4(df_diff(make_float2(a.h.x, a.l.x), make_float2(b.h.x, b.l.x)),
+                       df_diff(make_float2(a.h.y, a.l.y), make_float2(b.h.y, b.l.y)),
+                       df_diff(make_float2(a.h.z, a.l.z), make_float2(b.h.z, b.l.z)),
+                       df_diff(make_float2(a.h.w, a.l.w), make_float2(b.h.w, b.l.w)));
+}
+__device__ inline DF4 df4_pack(float2 x, float2 y, float2 z, float2 w) {
+    DF4 r;
+    r.h = make_float4(x.x, y.x, z.x, w.x);
+    r.l = make_float4(x.y, y.y, z.y, w.y);
+    return r;
+}
+__device__ inline DF4 df4_add(const DF4& a, const DF4& b) {
+    return df4_pack(df_add(make_float2(a.h.x, a.l.x), make_float2(b.h.x, b.l.x)),
+                    df_add(make_float2(a.h.y, a.l.y), make_float2(b.h.y, b.l.y)),
+                    df_add(make_float2(a.h.z, a.l.z), make_float2(b.h.z, b.l.z)),
+                    df_add(make_float2(a.h.w, a.l.w), make_float2(b.h.w, b.l.w)));
+}
+__device__ inline DF4 df4_add_f(const DF4& a, float4 b) {
+    return df4_pack(df_add_f(make_float2(a.h.x, a.l.x), b.x), df_add_f(make_float2(a.h.y, a.l.y), b.y),
+                    df_add_f(make_float2(a.h.z, a.l.z), b.z), df_add_f(make_float2(a.h.w, a.l.w), b.w));
+}
+__device__ inline DF4 df4_zero() {
+    DF4 r;
+    r.h = make_float4(0.f, 0.f, 0.f, 0.f);
+    r.l = r.h;
+    return r;
+}
 
 struct Level {
     int nt = 0, ny = 0, nz = 0;
     int64_t cells = 0;
-    float* off = nullptr;     // cells x 6 x 16
-    float* ex = nullptr;      // cells x 16  row sums by class
-    float* aself = nullptr;   // cells x 16
-    float* sinv = nullptr;    // cells x 16
+    // operators, structure of arrays: entry e of cell i at [e * cells + i]
+    float* off = nullptr;     // 6 x 16 x cells  outgoing couplings (direction d, block entry k*4+kk)
+    float* ex = nullptr;      // 16 x cells  row sums by class (summed up the hierarchy)
+    float* exd = nullptr;     // 16 x cells  self block of the difference form (absent classes fixed up)
+    float* aself = nullptr;   // 16 x cells  self block ex - sum_d off_d (absent classes fixed up)
+    float* sinv = nullptr;    // 16 x cells  inverse of the self block
     uint8_t* mask = nullptr;  // cells: classes present
-    D4* x = nullptr;          // cells
-    D4* x2 = nullptr;         // cells
-    D4* b = nullptr;          // cells
+    DF4* x = nullptr;         // cells
+    DF4* x2 = nullptr;        // cells
+    float4* b = nullptr;      // cells
+};
+
+// One captured preconditioner application for a fixed (r, z) buffer pair.
+struct PcGraph {
+    const float* r = nullptr;
+    float2* z = nullptr;
+    int kcyc = 0;
+    bool prof = false;
+    cudaGraphExec_t exec = nullptr;
+    int64_t nodes = 0;                 // kernels per execution
+    std::vector<ProfPair> ev;          // timing events recorded by the graph (prof graphs)
 };
 
 struct Precond {
+    std::vector<PcGraph> graphs;
+    int pending = -1;          // graph whose last execution still has to be harvested
+    bool graphs_off = false;   // capture failed once: direct launches from then on
     float* dinv = nullptr;     // 4 per voxel: inverse of the condensed scaled (c, phi) block
     float* fc = nullptr;       // FCW per plating face: condensation coefficients (scaled)
-    double* rv = nullptr;      // n: condensed right-hand side
-    double* t = nullptr;       // n: S z
+    float* rv = nullptr;       // 2N: condensed right-hand side
+    float* t = nullptr;        // 2N: S z
     int nlev = 0;              // coarse levels (index 1..nlev; lv[0] unused)
     Level lv[MAX_LEVELS + 1];
     int ncoarse = 0;
     double* cdense = nullptr;
     double* cinv = nullptr;
     int* cstat = nullptr;
-    // level-1 K-cycle workspace (FP64 arrays of 4 x cells)
-    double* kV = nullptr;      // (KCYC+1) x m4
-    double* kZ = nullptr;      // KCYC x m4
-    double* kw = nullptr;      // m4
-    double* kH = nullptr;      // (KCYC+1) x KCYC + scalars
+    int kcyc = 0;              // level-1 K-cycle length
+    // level-1 K-cycle workspace
+    float* kV = nullptr;       // (KCYC_MAX+1) x m4  FP32 basis
+    DF4* kZ = nullptr;         // KCYC_MAX x cells   preconditioned directions
+    float* kw = nullptr;       // m4
+    double* kH = nullptr;      // (KCYC_MAX+1) x KCYC_MAX + scalars
     double* kred = nullptr;    // RED_BLOCKS x 8 partials
 };
 
@@ -103,9 +152,10 @@ __device__ inline int64_t face_of(int lv, int lw, uint32_t code, uint32_t cw_cod
 
 // ------------------------------------------------------------ fine level
 __global__ void __launch_bounds__(256)
-k_bj_setup(DevParams P, Dims D, const uint32_t* __restrict__ vc, const float* __restrict__ u,
+k_bj_setup(ParT<float> P, Dims D, const uint32_t* __restrict__ vc, const float* __restrict__ u,
            const uint8_t* __restrict__ gate, double dt, double s_i0d, double k_pld,
-           float* __restrict__ dinv, float* __restrict__ fc, float* __restrict__ rowdiag) {
+           float* __restrict__ dinv, float* __restrict__ fc, float* __restrict__ rowdiag,
+           float* __restrict__ rowinv) {
     int z = blockIdx.x * blockDim.x + threadIdx.x;
     int y = blockIdx.y * blockDim.y + threadIdx.y;
     int t = blockIdx.z;
@@ -117,7 +167,7 @@ k_bj_setup(DevParams P, Dims D, const uint32_t* __restrict__ vc, const float* __
     const float* nn = u + 2 * N;
     const float s_i0 = float(s_i0d), k_pl = float(k_pld);
     const float dtf = float(dt), idt = float(1.0 / dt);
-    const float nc = float(sqrt(sqrt(P.nc4)));
+    const float nc = P.nc;
     const float A = float(P.A), c0 = float(P.cref[PE]);
     uint32_t code = vc[v];
     int lv = vc_phase(code);
@@ -149,6 +199,7 @@ k_bj_setup(DevParams P, Dims D, const uint32_t* __restrict__ vc, const float* __
                 d11 -= J.p[4] * J.n[1] / jnn;         // Schur term on phi_g
                 fc[FCW * f + 0] = dtf * jnn;          // scaled D_n
                 rowdiag[2 * N + f] = fabsf(dtf * jnn);
+                rowinv[2 * N + f] = 1.f / fabsf(dtf * jnn);
                 fc[FCW * f + 1] = J.n[1] * dtf / nc;  // dR_n/dphi_g
                 fc[FCW * f + 2] = J.n[2] * c0 * dtf / nc;   // dR_n/dc_e
                 fc[FCW * f + 3] = J.n[3] * dtf / nc;  // dR_n/dphi_e
@@ -170,22 +221,23 @@ k_bj_setup(DevParams P, Dims D, const uint32_t* __restrict__ vc, const float* __
         dgc += float(P.V / dt);
         src = float(P.V * P.cref[lv] / dt);
         rowdiag[v] = fmaxf(fabsf(dgc * float(dt / P.V)), 1e-30f);
+        rowinv[v] = 1.f / rowdiag[v];
     } else {
         d00 = 1.f; d01 = 0.f; src = 1.f;
         rowdiag[v] = 1.f;
+        rowinv[v] = 1.f;
     }
     rowdiag[N + v] = fmaxf(fabsf(dgp / A), 1e-30f);
+    rowinv[N + v] = 1.f / rowdiag[N + v];
     float a = d00 * suc / src, b = d01 / src, c = d10 * suc / A, e = d11 / A;
     float id = 1.f / (a * e - b * c);
     reinterpret_cast<float4*>(dinv)[v] = make_float4(e * id, -b * id, -c * id, a * id);
 }
 
-// condensed right-hand side r_v - J_vn D_n^-1 r_n (voxel rows of rv); FP64
-// vectors (the preconditioned directions carry large near-null components
-// whose small structure FP32 would lose), FP32 coefficients
+// condensed right-hand side r_v - J_vn D_n^-1 r_n (voxel rows of rv), FP32
 __global__ void __launch_bounds__(256)
-k_condense_rhs(Dims D, const uint32_t* __restrict__ vc, const float* __restrict__ fc, const double* __restrict__ r,
-               const float* __restrict__ rowdiag, double* __restrict__ rv) {
+k_condense_rhs(Dims D, const uint32_t* __restrict__ vc, const float* __restrict__ fc, const float* __restrict__ r,
+               const float* __restrict__ rowdiag, float* __restrict__ rv) {
     int z = blockIdx.x * blockDim.x + threadIdx.x;
     int y = blockIdx.y * blockDim.y + threadIdx.y;
     int t = blockIdx.z;
@@ -195,7 +247,7 @@ k_condense_rhs(Dims D, const uint32_t* __restrict__ vc, const float* __restrict_
     uint32_t code = vc[v];
     int lv = vc_phase(code);
     // the Krylov residual is row-equilibrated: undo it first
-    double rc = r[v] * (double)rowdiag[v], rp = r[N + v] * (double)rowdiag[N + v];
+    float rc = r[v] * rowdiag[v], rp = r[N + v] * rowdiag[N + v];
     if (lv == PG || lv == PE) {
         const int64_t off[6] = {-D.syz, D.syz, -(int64_t)D.nz, (int64_t)D.nz, -1, 1};
         const bool inb[6] = {t > 0, t < D.nt - 1, y > 0, y < D.ny - 1, z > 0, z < D.nz - 1};
@@ -205,12 +257,12 @@ k_condense_rhs(Dims D, const uint32_t* __restrict__ vc, const float* __restrict_
             uint32_t cw_code = vc[v + off[d]];
             int64_t f = face_of(lv, vc_phase(cw_code), code, cw_code, d, rank);
             if (f < 0) continue;
-            double q = r[2 * N + f] * (double)rowdiag[2 * N + f] / (double)fc[FCW * f + 0];
+            float q = r[2 * N + f] * rowdiag[2 * N + f] / fc[FCW * f + 0];
             if (lv == PG) {
-                rp -= (double)fc[FCW * f + 4] * q;
+                rp -= fc[FCW * f + 4] * q;
             } else {
-                rc -= (double)fc[FCW * f + 5] * q;
-                rp -= (double)fc[FCW * f + 6] * q;
+                rc -= fc[FCW * f + 5] * q;
+                rp -= fc[FCW * f + 6] * q;
             }
         }
     }
@@ -218,40 +270,46 @@ k_condense_rhs(Dims D, const uint32_t* __restrict__ vc, const float* __restrict_
     rv[N + v] = rp;
 }
 
-// z_n = (rn - J_nv z_v) / D_n  with rn = r_n (back-substitution) or 0 (elimination)
+// z_n = (rn - J_nv z_v) / D_n  with rn = r_n (back-substitution) or 0
+// (elimination).  dR_n/dphi_e = -dR_n/dphi_g exactly, so J_nv z_v is taken in
+// difference form: fc1 (z_phi_g - z_phi_e) + fc2 z_c_e.
 __global__ void k_face_solve(Dims D, const int32_t* __restrict__ pg, const int32_t* __restrict__ pe,
-                             const float* __restrict__ fc, const double* __restrict__ r,
-                             const float* __restrict__ rowdiag, double* __restrict__ z) {
+                             const float* __restrict__ fc, const float* __restrict__ r,
+                             const float* __restrict__ rowdiag, float2* __restrict__ z) {
     int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (f >= D.F) return;
     const int64_t N = D.N;
     int64_t g = pg[f], e = pe[f];
     const float* cf = fc + FCW * f;
-    double jz = (double)cf[1] * z[N + g] + (double)cf[2] * z[e] + (double)cf[3] * z[N + e];
-    double rn = r ? r[2 * N + f] * (double)rowdiag[2 * N + f] : 0.0;
-    z[2 * N + f] = (rn - jz) / (double)cf[0];
+    float jz = cf[1] * df_diff(z[N + g], z[N + e]) + cf[2] * df_val(z[e]);
+    float rn = r ? r[2 * N + f] * rowdiag[2 * N + f] : 0.f;
+    z[2 * N + f] = make_float2((rn - jz) / cf[0], 0.f);
 }
 
 // z = omega D^-1 rv  (accumulate = false);  z += omega D^-1 (rv - t)  (accumulate = true); voxel rows
-__global__ void k_bj_apply(Dims D, const float* __restrict__ dinv, const double* __restrict__ rv,
-                           const double* __restrict__ t, double omega, bool accumulate, double* __restrict__ z) {
+__global__ void k_bj_apply(Dims D, const float* __restrict__ dinv, const float* __restrict__ rv,
+                           const float* __restrict__ t, float omega, bool accumulate, float2* __restrict__ z) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t N = D.N;
     if (i >= N) return;
-    double rc = rv[i], rp = rv[N + i];
+    float rc = rv[i], rp = rv[N + i];
     if (accumulate) { rc -= t[i]; rp -= t[N + i]; }
     float4 m = reinterpret_cast<const float4*>(dinv)[i];
-    double zc = omega * ((double)m.x * rc + (double)m.y * rp), zp = omega * ((double)m.z * rc + (double)m.w * rp);
-    if (accumulate) { zc += z[i]; zp += z[N + i]; }
-    z[i] = zc;
-    z[N + i] = zp;
+    float zc = omega * (m.x * rc + m.y * rp), zp = omega * (m.z * rc + m.w * rp);
+    if (accumulate) {
+        z[i] = df_add_f(z[i], zc);
+        z[N + i] = df_add_f(z[N + i], zp);
+    } else {
+        z[i] = make_float2(zc, 0.f);
+        z[N + i] = make_float2(zp, 0.f);
+    }
 }
 
 // ------------------------------------------------------- level-1 assembly
 __device__ inline void acc_blk(float* blk, int k, int kk, float v) { blk[k * NCLS + kk] += v; }
 
 __global__ void __launch_bounds__(128)
-k_assemble_l1(DevParams P, Dims D, const uint32_t* __restrict__ vc, const float* __restrict__ u,
+k_assemble_l1(ParT<float> P, Dims D, const uint32_t* __restrict__ vc, const float* __restrict__ u,
               const uint8_t* __restrict__ gate, double dt, double s_i0d, double k_pld, Level L1) {
     int64_t cell = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (cell >= L1.cells) return;
@@ -377,8 +435,8 @@ k_assemble_l1(DevParams P, Dims D, const uint32_t* __restrict__ vc, const float*
                     }
                 }
             }
-    for (int i = 0; i < BLK; ++i) L1.ex[cell * BLK + i] = ex[i];
-    for (int i = 0; i < OFFW; ++i) L1.off[cell * OFFW + i] = off[i];
+    for (int i = 0; i < BLK; ++i) L1.ex[(int64_t)i * L1.cells + cell] = ex[i];
+    for (int i = 0; i < OFFW; ++i) L1.off[(int64_t)i * L1.cells + cell] = off[i];
     L1.mask[cell] = (uint8_t)mask;
 }
 
@@ -402,21 +460,24 @@ __global__ void k_assemble_up(Level F, Level C) {
                 if (t >= F.nt || y >= F.ny || z >= F.nz) continue;
                 int64_t ch = ((int64_t)t * F.ny + y) * F.nz + z;
                 mask |= F.mask[ch];
-                for (int i = 0; i < BLK; ++i) ex[i] += F.ex[ch * BLK + i];
+                for (int i = 0; i < BLK; ++i) ex[i] += F.ex[(int64_t)i * F.cells + ch];
                 const int loc[6] = {a, a, b, b, e, e};
                 for (int d = 0; d < 6; ++d) {
                     bool other = (d & 1) ? (loc[d] == 1) : (loc[d] == 0);
                     if (!other) continue;
-                    for (int i = 0; i < BLK; ++i) off[d * BLK + i] += F.off[ch * OFFW + d * BLK + i];
+                    for (int i = 0; i < BLK; ++i) off[d * BLK + i] += F.off[(int64_t)(d * BLK + i) * F.cells + ch];
                 }
             }
-    for (int i = 0; i < BLK; ++i) C.ex[cell * BLK + i] = ex[i];
-    for (int i = 0; i < OFFW; ++i) C.off[cell * OFFW + i] = off[i];
+    for (int i = 0; i < BLK; ++i) C.ex[(int64_t)i * C.cells + cell] = ex[i];
+    for (int i = 0; i < OFFW; ++i) C.off[(int64_t)i * C.cells + cell] = off[i];
     C.mask[cell] = (uint8_t)mask;
 }
 
 // self block = row sums - outgoing couplings; absent classes get an identity
-// row; the block inverse by Gauss-Jordan with partial pivoting (FP64).
+// row (and zero columns); the block inverse by Gauss-Jordan with partial
+// pivoting (FP64).  exd is the self block of the difference form:
+// ex for present classes, the fixed-up self block plus the outgoing sums
+// elsewhere, so that exd x_i + sum_d off_d (x_nb - x_i) = aself x_i + sum_d off_d x_nb.
 __global__ void k_finalize(Level L) {
     int64_t cell = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (cell >= L.cells) return;
@@ -424,12 +485,18 @@ __global__ void k_finalize(Level L) {
     uint32_t mask = L.mask[cell];
     for (int k = 0; k < NCLS; ++k)
         for (int kk = 0; kk < NCLS; ++kk) {
-            double s = L.ex[cell * BLK + k * NCLS + kk];
-            for (int d = 0; d < 6; ++d) s -= L.off[cell * OFFW + d * BLK + k * NCLS + kk];
-            if (!((mask >> k) & 1u) || !((mask >> kk) & 1u)) s = (k == kk && !((mask >> k) & 1u)) ? 1.0 : 0.0;
+            double so = 0.0;
+            for (int d = 0; d < 6; ++d) so += L.off[(int64_t)(d * BLK + k * NCLS + kk) * L.cells + cell];
+            double s = L.ex[(int64_t)(k * NCLS + kk) * L.cells + cell] - so;
+            double sd = L.ex[(int64_t)(k * NCLS + kk) * L.cells + cell];
+            if (!((mask >> k) & 1u) || !((mask >> kk) & 1u)) {
+                s = (k == kk && !((mask >> k) & 1u)) ? 1.0 : 0.0;
+                sd = s + so;
+            }
             a[k][kk] = s;
             a[k][NCLS + kk] = (k == kk) ? 1.0 : 0.0;
-            L.aself[cell * BLK + k * NCLS + kk] = (float)s;
+            L.aself[(int64_t)(k * NCLS + kk) * L.cells + cell] = (float)s;
+            L.exd[(int64_t)(k * NCLS + kk) * L.cells + cell] = (float)sd;
         }
     for (int col = 0; col < NCLS; ++col) {
         int piv = col;
@@ -448,10 +515,13 @@ __global__ void k_finalize(Level L) {
         }
     }
     for (int k = 0; k < NCLS; ++k)
-        for (int kk = 0; kk < NCLS; ++kk) L.sinv[cell * BLK + k * NCLS + kk] = (float)a[k][NCLS + kk];
+        for (int kk = 0; kk < NCLS; ++kk) L.sinv[(int64_t)(k * NCLS + kk) * L.cells + cell] = (float)a[k][NCLS + kk];
 }
 
 // ----------------------------------------------------- coarsest dense solve
+// dense FP64 matrix of the coarsest level; the self block is formed in FP64
+// from the difference-form data (exd - sum_d off_d), as the level's own
+// difference-form product does, so no FP32 rounding breaks its row sums
 __global__ void k_coarse_dense(Level L, int n, double* __restrict__ Ad) {
     int row = blockIdx.x * blockDim.x + threadIdx.x;
     if (row >= n) return;
@@ -461,14 +531,22 @@ __global__ void k_coarse_dense(Level L, int n, double* __restrict__ Ad) {
     int cz = (int)(cell % L.nz);
     int cy = (int)((cell / L.nz) % L.ny);
     int ct = (int)(cell / ((int64_t)L.nz * L.ny));
-    for (int kk = 0; kk < NCLS; ++kk) Ad[(int64_t)row * n + cell * NCLS + kk] = L.aself[cell * BLK + k * NCLS + kk];
     const int dt_[6] = {-1, 1, 0, 0, 0, 0}, dy_[6] = {0, 0, -1, 1, 0, 0}, dz_[6] = {0, 0, 0, 0, -1, 1};
+    for (int kk = 0; kk < NCLS; ++kk) {
+        double sd = L.exd[(int64_t)(k * NCLS + kk) * L.cells + cell];
+        for (int d = 0; d < 6; ++d) {
+            int t = ct + dt_[d], y = cy + dy_[d], z = cz + dz_[d];
+            if (t < 0 || t >= L.nt || y < 0 || y >= L.ny || z < 0 || z >= L.nz) continue;
+            sd -= L.off[(int64_t)(d * BLK + k * NCLS + kk) * L.cells + cell];
+        }
+        Ad[(int64_t)row * n + cell * NCLS + kk] = sd;
+    }
     for (int d = 0; d < 6; ++d) {
         int t = ct + dt_[d], y = cy + dy_[d], z = cz + dz_[d];
         if (t < 0 || t >= L.nt || y < 0 || y >= L.ny || z < 0 || z >= L.nz) continue;
         int64_t nb = ((int64_t)t * L.ny + y) * L.nz + z;
         for (int kk = 0; kk < NCLS; ++kk)
-            Ad[(int64_t)row * n + nb * NCLS + kk] += L.off[cell * OFFW + d * BLK + k * NCLS + kk];
+            Ad[(int64_t)row * n + nb * NCLS + kk] += L.off[(int64_t)(d * BLK + k * NCLS + kk) * L.cells + cell];
     }
 }
 
@@ -519,51 +597,57 @@ __global__ void k_coarse_invert(int n, double* __restrict__ A, double* __restric
     }
 }
 
-// x = Ainv b (FP64 accumulation), one block
-__global__ void k_coarse_solve(int n, const double* __restrict__ Ainv, const D4* __restrict__ b,
-                               D4* __restrict__ x) {
+// x = Ainv b (FP64 accumulation), one block; x stored float-float
+__global__ void k_coarse_solve(int n, const double* __restrict__ Ainv, const float4* __restrict__ b,
+                               DF4* __restrict__ x) {
     __shared__ double sb[COARSE_MAX];
-    const double* bf = reinterpret_cast<const double*>(b);
-    for (int i = threadIdx.x; i < n; i += blockDim.x) sb[i] = bf[i];
+    __shared__ double sx[COARSE_MAX];
+    const float* bf = reinterpret_cast<const float*>(b);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) sb[i] = (double)bf[i];
     __syncthreads();
-    double* xf = reinterpret_cast<double*>(x);
     for (int r = threadIdx.x; r < n; r += blockDim.x) {
         double acc = 0.0;
         for (int j = 0; j < n; ++j) acc += Ainv[(int64_t)r * n + j] * sb[j];
-        xf[r] = acc;
+        sx[r] = acc;
     }
+    __syncthreads();
+    for (int cell = threadIdx.x; cell < n / NCLS; cell += blockDim.x)
+        x[cell] = df4_pack(df_from_double(sx[4 * cell]), df_from_double(sx[4 * cell + 1]),
+                           df_from_double(sx[4 * cell + 2]), df_from_double(sx[4 * cell + 3]));
 }
 
 // --------------------------------------------------------- coarse smoothing
-__device__ inline D4 mv4(const float* m, D4 x) {
-    return d4((double)m[0] * x.x + (double)m[1] * x.y + (double)m[2] * x.z + (double)m[3] * x.w,
-              (double)m[4] * x.x + (double)m[5] * x.y + (double)m[6] * x.z + (double)m[7] * x.w,
-              (double)m[8] * x.x + (double)m[9] * x.y + (double)m[10] * x.z + (double)m[11] * x.w,
-              (double)m[12] * x.x + (double)m[13] * x.y + (double)m[14] * x.z + (double)m[15] * x.w);
+// 4x4 block (row-major entries k*4+kk stored st apart: structure-of-arrays
+// over the cells, so that a warp's loads of one entry are contiguous) times x
+__device__ inline float4 mv4(const float* __restrict__ m, int64_t st, float4 x) {
+    return make_float4(m[0] * x.x + m[st] * x.y + m[2 * st] * x.z + m[3 * st] * x.w,
+                       m[4 * st] * x.x + m[5 * st] * x.y + m[6 * st] * x.z + m[7 * st] * x.w,
+                       m[8 * st] * x.x + m[9 * st] * x.y + m[10 * st] * x.z + m[11 * st] * x.w,
+                       m[12 * st] * x.x + m[13 * st] * x.y + m[14 * st] * x.z + m[15 * st] * x.w);
 }
-__device__ inline D4 f4sub(D4 a, D4 b) { return d4(a.x - b.x, a.y - b.y, a.z - b.z, a.w - b.w); }
-__device__ inline D4 f4add(D4 a, D4 b) { return d4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w); }
-__device__ inline D4 f4scale(double s, D4 a) { return d4(s * a.x, s * a.y, s * a.z, s * a.w); }
+__device__ inline float4 f4add(float4 a, float4 b) { return make_float4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w); }
+__device__ inline float4 f4sub(float4 a, float4 b) { return make_float4(a.x - b.x, a.y - b.y, a.z - b.z, a.w - b.w); }
+__device__ inline float4 f4scale(float s, float4 a) { return make_float4(s * a.x, s * a.y, s * a.z, s * a.w); }
 
-// effective iterate of a cell: x (if given) plus alpha times the prolonged coarse correction (if given)
-__device__ inline D4 xeff(const D4* x, const D4* ec, double alpha, int ccny, int ccnz, int t, int y, int z,
-                          int64_t cell) {
-    D4 r = x ? x[cell] : d4(0.0, 0.0, 0.0, 0.0);
-    if (ec) r = f4add(r, f4scale(alpha, ec[((int64_t)(t >> 1) * ccny + (y >> 1)) * ccnz + (z >> 1)]));
+// effective iterate of a cell: x (if given) plus the prolonged coarse correction (if given)
+__device__ inline DF4 xeff(const DF4* x, const DF4* ec, int ccny, int ccnz, int t, int y, int z, int64_t cell) {
+    DF4 r = x ? x[cell] : df4_zero();
+    if (ec) r = df4_add(r, ec[((int64_t)(t >> 1) * ccny + (y >> 1)) * ccnz + (z >> 1)]);
     return r;
 }
 
-// A x at one cell of level L
-__device__ inline D4 cell_apply(const Level& L, const D4* x, const D4* ec, double alpha, int ccny, int ccnz, int t,
-                                int y, int z, int64_t cell) {
-    D4 acc = mv4(L.aself + cell * BLK, xeff(x, ec, alpha, ccny, ccnz, t, y, z, cell));
+// A xe at one cell of level L in difference form (xe_i given)
+__device__ inline float4 cell_apply(const Level& L, const DF4* x, const DF4* ec, int ccny, int ccnz, int t, int y,
+                                    int z, int64_t cell, const DF4& xi) {
+    float4 acc = mv4(L.exd + cell, L.cells, df4_val(xi));
     const int dt_[6] = {-1, 1, 0, 0, 0, 0}, dy_[6] = {0, 0, -1, 1, 0, 0}, dz_[6] = {0, 0, 0, 0, -1, 1};
 #pragma unroll
     for (int d = 0; d < 6; ++d) {
         int tt = t + dt_[d], yy = y + dy_[d], zz = z + dz_[d];
         if (tt < 0 || tt >= L.nt || yy < 0 || yy >= L.ny || zz < 0 || zz >= L.nz) continue;
         int64_t nb = ((int64_t)tt * L.ny + yy) * L.nz + zz;
-        acc = f4add(acc, mv4(L.off + cell * OFFW + d * BLK, xeff(x, ec, alpha, ccny, ccnz, tt, yy, zz, nb)));
+        acc = f4add(acc, mv4(L.off + (int64_t)d * BLK * L.cells + cell, L.cells,
+                                 df4_diff(xeff(x, ec, ccny, ccnz, tt, yy, zz, nb), xi)));
     }
     return acc;
 }
@@ -574,52 +658,68 @@ __device__ inline void cell_coords(const Level& L, int64_t cell, int& t, int& y,
     t = (int)(cell / ((int64_t)L.nz * L.ny));
 }
 
-// x_out = xe + omega Sinv (b - A xe), xe = x_in (+ alpha * prolonged ec)
-__global__ void k_lvl_smooth(Level L, const D4* __restrict__ x_in, const D4* __restrict__ ec, double alpha, int ccny,
-                             int ccnz, double omega, D4* __restrict__ x_out) {
+// x_out = xe + omega Sinv (b - A xe), xe = x_in (+ prolonged ec); both absent: x_out = omega Sinv b
+__global__ void k_lvl_smooth(Level L, const DF4* __restrict__ x_in, const DF4* __restrict__ ec, int ccny,
+                             int ccnz, float omega, DF4* __restrict__ x_out) {
     int64_t cell = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (cell >= L.cells) return;
     int t, y, z;
     cell_coords(L, cell, t, y, z);
-    D4 xe = xeff(x_in, ec, alpha, ccny, ccnz, t, y, z, cell);
-    D4 r = (x_in || ec) ? f4sub(L.b[cell], cell_apply(L, x_in, ec, alpha, ccny, ccnz, t, y, z, cell)) : L.b[cell];
-    x_out[cell] = f4add(xe, f4scale(omega, mv4(L.sinv + cell * BLK, r)));
+    if (!x_in && !ec) {
+        float4 c = f4scale(omega, mv4(L.sinv + cell, L.cells, L.b[cell]));
+        DF4 o;
+        o.h = c;
+        o.l = make_float4(0.f, 0.f, 0.f, 0.f);
+        x_out[cell] = o;
+        return;
+    }
+    DF4 xe = xeff(x_in, ec, ccny, ccnz, t, y, z, cell);
+    float4 r = f4sub(L.b[cell], cell_apply(L, x_in, ec, ccny, ccnz, t, y, z, cell, xe));
+    x_out[cell] = df4_add_f(xe, f4scale(omega, mv4(L.sinv + cell, L.cells, r)));
 }
 
-__global__ void k_lvl_matvec(Level L, const D4* __restrict__ x, D4* __restrict__ y_out) {
+__global__ void k_lvl_matvec(Level L, const DF4* __restrict__ x, float4* __restrict__ y_out) {
     int64_t cell = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (cell >= L.cells) return;
     int t, y, z;
     cell_coords(L, cell, t, y, z);
-    y_out[cell] = cell_apply(L, x, nullptr, 0.0, 0, 0, t, y, z, cell);
+    y_out[cell] = cell_apply(L, x, nullptr, 0, 0, t, y, z, cell, x[cell]);
 }
 
-// bc(parent) = sum over children of (b - A x)
-__global__ void k_lvl_restrict(Level L, const D4* __restrict__ x, Level C) {
-    int64_t cell = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (cell >= C.cells) return;
-    int ct, cy, cz;
-    cell_coords(C, cell, ct, cy, cz);
-    D4 acc = d4(0.0, 0.0, 0.0, 0.0);
-    for (int a = 0; a < 2; ++a)
-        for (int b = 0; b < 2; ++b)
-            for (int e = 0; e < 2; ++e) {
-                int t = 2 * ct + a, y = 2 * cy + b, z = 2 * cz + e;
-                if (t >= L.nt || y >= L.ny || z >= L.nz) continue;
-                int64_t ch = ((int64_t)t * L.ny + y) * L.nz + z;
-                acc = f4add(acc, f4sub(L.b[ch], cell_apply(L, x, nullptr, 0.0, 0, 0, t, y, z, ch)));
-            }
-    C.b[cell] = acc;
+// bc(parent) = sum over children of (b - A x): one thread per child (eight
+// consecutive threads per parent), summed by shuffles within the octet
+__global__ void k_lvl_restrict(Level L, const DF4* __restrict__ x, Level C) {
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t cell = tid >> 3;
+    const int k = (int)(tid & 7);
+    float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (cell < C.cells) {
+        int ct, cy, cz;
+        cell_coords(C, cell, ct, cy, cz);
+        int t = 2 * ct + (k >> 2), y = 2 * cy + ((k >> 1) & 1), z = 2 * cz + (k & 1);
+        if (t < L.nt && y < L.ny && z < L.nz) {
+            int64_t ch = ((int64_t)t * L.ny + y) * L.nz + z;
+            r = f4sub(L.b[ch], cell_apply(L, x, nullptr, 0, 0, t, y, z, ch, x[ch]));
+        }
+    }
+#pragma unroll
+    for (int o = 1; o < 8; o <<= 1) {
+        r.x += __shfl_xor_sync(0xffffffffu, r.x, o);
+        r.y += __shfl_xor_sync(0xffffffffu, r.y, o);
+        r.z += __shfl_xor_sync(0xffffffffu, r.z, o);
+        r.w += __shfl_xor_sync(0xffffffffu, r.w, o);
+    }
+    if (k == 0 && cell < C.cells) C.b[cell] = r;
 }
 
 // ----------------------------------------------------- fine <-> level 1
-__global__ void k_restrict_fine(Dims D, const uint32_t* __restrict__ vc, const double* __restrict__ r,
-                                const double* __restrict__ t, Level C) {
+__global__ void k_restrict_fine(Dims D, const uint32_t* __restrict__ vc, const float* __restrict__ r,
+                                const float* __restrict__ t, Level C) {
     int64_t cell = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (cell >= C.cells) return;
     int ct, cy, cz;
     cell_coords(C, cell, ct, cy, cz);
-    double acc[NCLS] = {0.0, 0.0, 0.0, 0.0};
+    float acc[NCLS] = {0.f, 0.f, 0.f, 0.f};
     const int64_t N = D.N;
     for (int a = 0; a < 2; ++a)
         for (int b = 0; b < 2; ++b)
@@ -631,75 +731,83 @@ __global__ void k_restrict_fine(Dims D, const uint32_t* __restrict__ vc, const d
                 acc[phi_class(lv)] += r[N + v] - t[N + v];
                 if (lv == PE) acc[0] += r[v] - t[v];
             }
-    C.b[cell] = d4(acc[0], acc[1], acc[2], acc[3]);
+    C.b[cell] = make_float4(acc[0], acc[1], acc[2], acc[3]);
 }
 
-__global__ void k_prolong_fine(Dims D, const uint32_t* __restrict__ vc, Level C, const D4* __restrict__ e1,
-                               double* __restrict__ z) {
+__global__ void k_prolong_fine(Dims D, const uint32_t* __restrict__ vc, Level C, const DF4* __restrict__ e1,
+                               float2* __restrict__ z) {
     int zz = blockIdx.x * blockDim.x + threadIdx.x;
     int y = blockIdx.y * blockDim.y + threadIdx.y;
     int t = blockIdx.z;
     if (zz >= D.nz || y >= D.ny) return;
     int64_t v = (int64_t)t * D.syz + (int64_t)y * D.nz + zz;
     int lv = vc_phase(vc[v]);
-    D4 e = e1[((int64_t)(t >> 1) * C.ny + (y >> 1)) * C.nz + (zz >> 1)];
-    double ev[NCLS] = {e.x, e.y, e.z, e.w};
-    z[D.N + v] += ev[phi_class(lv)];
-    if (lv == PE) z[v] += e.x;
+    const DF4 e = e1[((int64_t)(t >> 1) * C.ny + (y >> 1)) * C.nz + (zz >> 1)];
+    const int k = phi_class(lv);
+    const float2 ek = k == 1 ? make_float2(e.h.y, e.l.y) : (k == 2 ? make_float2(e.h.z, e.l.z) : make_float2(e.h.w, e.l.w));
+    z[D.N + v] = df_add(z[D.N + v], ek);
+    if (lv == PE) z[v] = df_add(z[v], make_float2(e.h.x, e.l.x));
 }
 
 // ------------------------------------------- device-side FGMRES (K-cycle)
 // Small Krylov kernels whose scalars stay in device memory, so the level-1
-// K-cycle needs no host round trip.
+// K-cycle needs no host round trip.  Basis vectors FP32, dot products with
+// FP32 products and FP64 block sums.
 __global__ void __launch_bounds__(RED_THREADS)
-k_kdot(const double* __restrict__ V, int64_t stride, int cnt, const double* __restrict__ w, int64_t n,
+k_kdot(const float* __restrict__ V, int64_t stride, int cnt, const float* __restrict__ w, int64_t n,
        double* partials) {
-    double acc[8];
+    float acc32[8];
 #pragma unroll
-    for (int j = 0; j < 8; ++j) acc[j] = 0.0;
+    for (int j = 0; j < 8; ++j) acc32[j] = 0.f;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        double wi = w[i];
+        float wi = w[i];
 #pragma unroll
         for (int j = 0; j < 8; ++j)
-            if (j < cnt) acc[j] += V[j * stride + i] * wi;
+            if (j < cnt) acc32[j] = fmaf(V[j * stride + i], wi, acc32[j]);
     }
-    block_reduce_store<8, false>(acc, partials);
+    block_reduce_store_f32<8>(acc32, partials);
 }
 
-// w += sign * sum_j h[j] V_j (h on the device)
-__global__ void k_kupdate(const double* __restrict__ V, int64_t stride, int cnt, const double* __restrict__ h,
-                          double sign, double* __restrict__ w, int64_t n) {
+// w += sign * sum_j h[j] V_j (h on the device; converted once per block)
+__global__ void k_kupdate(const float* __restrict__ V, int64_t stride, int cnt, const double* __restrict__ h,
+                          float sign, float* __restrict__ w, int64_t n) {
+    __shared__ float hs[KCYC_MAX + 1];
+    if (threadIdx.x < cnt) hs[threadIdx.x] = (float)h[threadIdx.x];
+    __syncthreads();
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    double acc = 0.0;
-    for (int j = 0; j < cnt; ++j) acc += h[j] * V[j * stride + i];
-    w[i] = w[i] + sign * acc;
+    float acc = 0.f;
+    for (int j = 0; j < cnt; ++j) acc = fmaf(hs[j], V[j * stride + i], acc);
+    w[i] = fmaf(sign, acc, w[i]);
 }
 
-// out = a / sqrt(max(d2, tiny))
-__global__ void k_knormalize(const double* __restrict__ a, const double* __restrict__ d2, double* __restrict__ out,
+// out = a / sqrt(max(d2, tiny)) (the scale computed once per block)
+__global__ void k_knormalize(const float* __restrict__ a, const double* __restrict__ d2, float* __restrict__ out,
                              int64_t n) {
+    __shared__ float inv;
+    if (threadIdx.x == 0) inv = (float)(1.0 / sqrt(fmax(*d2, 1e-300)));
+    __syncthreads();
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    double nrm = sqrt(fmax(*d2, 1e-300));
-    out[i] = a[i] / nrm;
+    out[i] = a[i] * inv;
 }
 
-// H layout: col-major (KCYC+1) x KCYC at H[j*(KCYC+1) + i]; s[0] = ||b||^2, s[1..] CGS scratch
+// H layout: col-major (KCYC_MAX+1) x KCYC_MAX at H[j*(KCYC_MAX+1) + i]
 // After CGS2 of column j: h = h1 + h2, H[j+1, j] = ||w||.
 __global__ void k_kcol(double* H, int j, const double* h1, const double* h2, const double* wn2) {
     int i = threadIdx.x;
-    if (i <= j) H[j * (KCYC + 1) + i] = h1[i] + h2[i];
-    if (i == 0) H[j * (KCYC + 1) + j + 1] = sqrt(fmax(*wn2, 0.0));
+    if (i <= j) H[j * (KCYC_MAX + 1) + i] = h1[i] + h2[i];
+    if (i == 0) H[j * (KCYC_MAX + 1) + j + 1] = sqrt(fmax(*wn2, 0.0));
 }
 
-// least squares min || beta e1 - H y || by Givens rotations (one thread)
-__global__ void k_klsq(const double* H, const double* b2, int k, double* y) {
+// least squares min || beta e1 - H y || by Givens rotations (one thread);
+// y also written as float-float pairs for the combination kernel
+__global__ void k_klsq(const double* H, const double* b2, int k, double* y, float2* ydf) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    double R[KCYC + 1][KCYC];
-    double g[KCYC + 1];
+    double R[KCYC_MAX + 1][KCYC_MAX];
+    double g[KCYC_MAX + 1];
     for (int j = 0; j < k; ++j)
-        for (int i = 0; i <= k; ++i) R[i][j] = H[j * (KCYC + 1) + i];
+        for (int i = 0; i <= k; ++i) R[i][j] = H[j * (KCYC_MAX + 1) + i];
     for (int i = 0; i <= k; ++i) g[i] = 0.0;
     g[0] = sqrt(fmax(*b2, 0.0));
     for (int j = 0; j < k; ++j) {
@@ -720,6 +828,24 @@ __global__ void k_klsq(const double* H, const double* b2, int k, double* y) {
         for (int l = i + 1; l < k; ++l) acc -= R[i][l] * y[l];
         y[i] = R[i][i] != 0.0 ? acc / R[i][i] : 0.0;
     }
+    for (int i = 0; i < k; ++i) ydf[i] = df_from_double(y[i]);
+}
+
+// x = sum_j y_j Z_j in float-float arithmetic
+__global__ void k_kcombine(const DF4* __restrict__ Z, int64_t cells, int k, const float2* __restrict__ ydf,
+                           DF4* __restrict__ x) {
+    int64_t cell = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (cell >= cells) return;
+    float2 a0 = make_float2(0.f, 0.f), a1 = a0, a2 = a0, a3 = a0;
+    for (int j = 0; j < k; ++j) {
+        const float2 yj = ydf[j];
+        const DF4 z = Z[j * cells + cell];
+        a0 = df_add(a0, df_mul(make_float2(z.h.x, z.l.x), yj));
+        a1 = df_add(a1, df_mul(make_float2(z.h.y, z.l.y), yj));
+        a2 = df_add(a2, df_mul(make_float2(z.h.z, z.l.z), yj));
+        a3 = df_add(a3, df_mul(make_float2(z.h.w, z.l.w), yj));
+    }
+    x[cell] = df4_pack(a0, a1, a2, a3);
 }
 
 // ------------------------------------------------------------ host side
@@ -729,10 +855,11 @@ int precond_create(mb_cell* c) {
     const Dims& D = c->D;
     p->dinv = (float*)cell_alloc(c, 16 * D.N);
     p->fc = (float*)cell_alloc(c, 4 * FCW * (D.F ? D.F : 1));
-    p->rv = (double*)cell_alloc(c, 8 * c->n);
-    p->t = (double*)cell_alloc(c, 8 * c->n);
+    p->rv = (float*)cell_alloc(c, 8 * D.N);
+    p->t = (float*)cell_alloc(c, 8 * D.N);
     c->rowdiag = (float*)cell_alloc(c, 4 * c->n);
-    if (!p->dinv || !p->fc || !p->rv || !p->t || !c->rowdiag) return MB_ENOMEM;
+    c->rowinv = (float*)cell_alloc(c, 4 * c->n);
+    if (!p->dinv || !p->fc || !p->rv || !p->t || !c->rowdiag || !c->rowinv) return MB_ENOMEM;
     int coarse_cells = c->opt.mg_coarse_cells;
     if (coarse_cells < 1) coarse_cells = 1;
     if (coarse_cells * NCLS > COARSE_MAX) coarse_cells = COARSE_MAX / NCLS;
@@ -746,13 +873,14 @@ int precond_create(mb_cell* c) {
         L.cells = (int64_t)nt * ny * nz;
         L.off = (float*)cell_alloc(c, 4 * (size_t)L.cells * OFFW);
         L.ex = (float*)cell_alloc(c, 4 * (size_t)L.cells * BLK);
+        L.exd = (float*)cell_alloc(c, 4 * (size_t)L.cells * BLK);
         L.aself = (float*)cell_alloc(c, 4 * (size_t)L.cells * BLK);
         L.sinv = (float*)cell_alloc(c, 4 * (size_t)L.cells * BLK);
         L.mask = (uint8_t*)cell_alloc(c, (size_t)L.cells);
-        L.x = (D4*)cell_alloc(c, 32 * (size_t)L.cells);
-        L.x2 = (D4*)cell_alloc(c, 32 * (size_t)L.cells);
-        L.b = (D4*)cell_alloc(c, 32 * (size_t)L.cells);
-        if (!L.off || !L.ex || !L.aself || !L.sinv || !L.mask || !L.x || !L.x2 || !L.b) return MB_ENOMEM;
+        L.x = (DF4*)cell_alloc(c, sizeof(DF4) * (size_t)L.cells);
+        L.x2 = (DF4*)cell_alloc(c, sizeof(DF4) * (size_t)L.cells);
+        L.b = (float4*)cell_alloc(c, 16 * (size_t)L.cells);
+        if (!L.off || !L.ex || !L.exd || !L.aself || !L.sinv || !L.mask || !L.x || !L.x2 || !L.b) return MB_ENOMEM;
         if (L.cells <= coarse_cells) break;
         if (nt == 1 && ny == 1 && nz == 1) break;
     }
@@ -767,28 +895,41 @@ int precond_create(mb_cell* c) {
     p->cinv = (double*)cell_alloc(c, 8 * nn);
     p->cstat = (int*)cell_alloc(c, 16);
     int64_t m4 = 4 * p->lv[1].cells;
-    p->kV = (double*)cell_alloc(c, 8 * (size_t)m4 * (KCYC + 1));
-    p->kZ = (double*)cell_alloc(c, 8 * (size_t)m4 * KCYC);
-    p->kw = (double*)cell_alloc(c, 8 * (size_t)m4);
-    p->kH = (double*)cell_alloc(c, 8 * (size_t)((KCYC + 1) * KCYC + 64));
+    p->kV = (float*)cell_alloc(c, 4 * (size_t)m4 * (KCYC_MAX + 1));
+    p->kZ = (DF4*)cell_alloc(c, sizeof(DF4) * (size_t)p->lv[1].cells * KCYC_MAX);
+    p->kw = (float*)cell_alloc(c, 4 * (size_t)m4);
+    p->kH = (double*)cell_alloc(c, 8 * (size_t)((KCYC_MAX + 1) * KCYC_MAX + 128));
     p->kred = (double*)cell_alloc(c, 8 * (size_t)RED_BLOCKS * 8);
     if (!p->cdense || !p->cinv || !p->cstat || !p->kV || !p->kZ || !p->kw || !p->kH || !p->kred) return MB_ENOMEM;
     return MB_OK;
 }
 
+static void graph_free(PcGraph& G) {
+    if (G.exec) cudaGraphExecDestroy(G.exec);
+    for (auto& e : G.ev) {
+        cudaEventDestroy(e.e0);
+        cudaEventDestroy(e.e1);
+    }
+    G.exec = nullptr;
+    G.ev.clear();
+}
+
 void precond_destroy(mb_cell* c) {
+    if (c->pc)
+        for (auto& G : c->pc->graphs) graph_free(G);
     delete c->pc;
     c->pc = nullptr;
 }
 
 int precond_setup(mb_cell* c, const float* u32, const uint8_t* gate, double dt) {
     Precond* p = c->pc;
+    p->kcyc = c->opt.mg_kcycle < 1 ? 1 : (c->opt.mg_kcycle > KCYC_MAX ? KCYC_MAX : c->opt.mg_kcycle);
     const Dims& D = c->D;
     cudaStream_t s = c->stream;
-    k_bj_setup<<<pgrid(D.nt, D.ny, D.nz), PB, 0, s>>>(c->P, D, c->vcode, u32, gate, dt, c->s_i0, c->k_pl,
-                                                       p->dinv, p->fc, c->rowdiag), ::mb::count_launch(c);
+    k_bj_setup<<<pgrid(D.nt, D.ny, D.nz), PB, 0, s>>>(c->Pf, D, c->vcode, u32, gate, dt, c->s_i0, c->k_pl,
+                                                       p->dinv, p->fc, c->rowdiag, c->rowinv), ::mb::count_launch(c);
     Level& L1 = p->lv[1];
-    k_assemble_l1<<<(unsigned)((L1.cells + 127) / 128), 128, 0, s>>>(c->P, D, c->vcode, u32, gate, dt, c->s_i0,
+    k_assemble_l1<<<(unsigned)((L1.cells + 127) / 128), 128, 0, s>>>(c->Pf, D, c->vcode, u32, gate, dt, c->s_i0,
                                                                       c->k_pl, L1), ::mb::count_launch(c);
     for (int l = 2; l <= p->nlev; ++l)
         k_assemble_up<<<nblk(p->lv[l].cells), 256, 0, s>>>(p->lv[l - 1], p->lv[l]), ::mb::count_launch(c);
@@ -813,23 +954,23 @@ static void vcycle(mb_cell* c, int l) {
     }
     Level& C = p->lv[l + 1];
     unsigned g = nblk(L.cells);
-    k_lvl_smooth<<<g, 256, 0, s>>>(L, nullptr, nullptr, 0.0, 0, 0, OMEGA_COARSE, L.x), ::mb::count_launch(c);
+    k_lvl_smooth<<<g, 256, 0, s>>>(L, nullptr, nullptr, 0, 0, OMEGA_COARSE, L.x), ::mb::count_launch(c);
     for (int k = 1; k < NU; ++k) {
-        k_lvl_smooth<<<g, 256, 0, s>>>(L, L.x, nullptr, 0.0, 0, 0, OMEGA_COARSE, L.x2), ::mb::count_launch(c);
+        k_lvl_smooth<<<g, 256, 0, s>>>(L, L.x, nullptr, 0, 0, OMEGA_COARSE, L.x2), ::mb::count_launch(c);
         std::swap(L.x, L.x2);
     }
-    k_lvl_restrict<<<nblk(C.cells), 256, 0, s>>>(L, L.x, C), ::mb::count_launch(c);
+    k_lvl_restrict<<<nblk(8 * C.cells), 256, 0, s>>>(L, L.x, C), ::mb::count_launch(c);
     vcycle(c, l + 1);
-    // post-smoothing, the first sweep applied to x + ALPHA P e
-    k_lvl_smooth<<<g, 256, 0, s>>>(L, L.x, C.x, ALPHA, C.ny, C.nz, OMEGA_COARSE, L.x2), ::mb::count_launch(c);
+    // post-smoothing, the first sweep applied to x + P e
+    k_lvl_smooth<<<g, 256, 0, s>>>(L, L.x, C.x, C.ny, C.nz, OMEGA_COARSE, L.x2), ::mb::count_launch(c);
     std::swap(L.x, L.x2);
     for (int k = 1; k < NU; ++k) {
-        k_lvl_smooth<<<g, 256, 0, s>>>(L, L.x, nullptr, 0.0, 0, 0, OMEGA_COARSE, L.x2), ::mb::count_launch(c);
+        k_lvl_smooth<<<g, 256, 0, s>>>(L, L.x, nullptr, 0, 0, OMEGA_COARSE, L.x2), ::mb::count_launch(c);
         std::swap(L.x, L.x2);
     }
 }
 
-static void kdots(mb_cell* c, const double* V, int64_t stride, int cnt, const double* w, int64_t n, double* out) {
+static void kdots(mb_cell* c, const float* V, int64_t stride, int cnt, const float* w, int64_t n, double* out) {
     Precond* p = c->pc;
     cudaStream_t s = c->stream;
     for (int j0 = 0; j0 < cnt; j0 += 8) {
@@ -839,7 +980,7 @@ static void kdots(mb_cell* c, const double* V, int64_t stride, int cnt, const do
     }
 }
 
-// Level-1 K-cycle: KCYC iterations of FGMRES on A1 x = b1 (b1 = lv[1].b),
+// Level-1 K-cycle: kcyc iterations of FGMRES on A1 x = b1 (b1 = lv[1].b),
 // preconditioned by the V-cycle; result in lv[1].x.  No host synchronisation.
 static void kcycle_l1(mb_cell* c) {
     Precond* p = c->pc;
@@ -849,46 +990,53 @@ static void kcycle_l1(mb_cell* c) {
         vcycle(c, 1);
         return;
     }
+    const int K = p->kcyc;
     const int64_t m4 = 4 * L.cells;
     const unsigned g = nblk(m4);
     double* H = p->kH;
-    double* sc = p->kH + (KCYC + 1) * KCYC;   // scalars: [0] ||b||^2, [8..] h1, [24..] h2, [40] ||w||^2, [48..] y
+    // scalars: [0] ||b||^2, [8..] h1, [24..] h2, [40] ||w||^2, [48..] y, [64..] y as float-float pairs
+    double* sc = p->kH + (KCYC_MAX + 1) * KCYC_MAX;
     double* b2 = sc;
     double* h1 = sc + 8;
     double* h2 = sc + 24;
     double* wn2 = sc + 40;
     double* y = sc + 48;
-    const double* b = reinterpret_cast<const double*>(L.b);
+    float2* ydf = reinterpret_cast<float2*>(sc + 64);
+    const float* b = reinterpret_cast<const float*>(L.b);
     kdots(c, b, 0, 1, b, m4, b2);
     k_knormalize<<<g, 256, 0, s>>>(b, b2, p->kV, m4), ::mb::count_launch(c);
-    D4* bsave = L.b;   // the V-cycle reads lv[1].b: point it at the Krylov vector
-    for (int j = 0; j < KCYC; ++j) {
-        double* Vj = p->kV + j * m4;
-        double* Zj = p->kZ + j * m4;
-        L.b = reinterpret_cast<D4*>(Vj);
+    float4* bsave = L.b;   // the V-cycle reads lv[1].b: point it at the Krylov vector
+    for (int j = 0; j < K; ++j) {
+        float* Vj = p->kV + j * m4;
+        DF4* Zj = p->kZ + j * L.cells;
+        L.b = reinterpret_cast<float4*>(Vj);
         vcycle(c, 1);
-        cudaMemcpyAsync(Zj, L.x, 8 * m4, cudaMemcpyDeviceToDevice, s);
-        k_lvl_matvec<<<nblk(L.cells), 256, 0, s>>>(L, reinterpret_cast<const D4*>(Zj), reinterpret_cast<D4*>(p->kw)), ::mb::count_launch(c);
+        cudaMemcpyAsync(Zj, L.x, sizeof(DF4) * L.cells, cudaMemcpyDeviceToDevice, s);
+        k_lvl_matvec<<<nblk(L.cells), 256, 0, s>>>(L, Zj, reinterpret_cast<float4*>(p->kw)), ::mb::count_launch(c);
         kdots(c, p->kV, m4, j + 1, p->kw, m4, h1);
-        k_kupdate<<<g, 256, 0, s>>>(p->kV, m4, j + 1, h1, -1.0, p->kw, m4), ::mb::count_launch(c);
+        k_kupdate<<<g, 256, 0, s>>>(p->kV, m4, j + 1, h1, -1.f, p->kw, m4), ::mb::count_launch(c);
         kdots(c, p->kV, m4, j + 1, p->kw, m4, h2);
-        k_kupdate<<<g, 256, 0, s>>>(p->kV, m4, j + 1, h2, -1.0, p->kw, m4), ::mb::count_launch(c);
+        k_kupdate<<<g, 256, 0, s>>>(p->kV, m4, j + 1, h2, -1.f, p->kw, m4), ::mb::count_launch(c);
         kdots(c, p->kw, 0, 1, p->kw, m4, wn2);
         k_kcol<<<1, 32, 0, s>>>(H, j, h1, h2, wn2), ::mb::count_launch(c);
         k_knormalize<<<g, 256, 0, s>>>(p->kw, wn2, p->kV + (j + 1) * m4, m4), ::mb::count_launch(c);
     }
     L.b = bsave;
-    k_klsq<<<1, 1, 0, s>>>(H, b2, KCYC, y), ::mb::count_launch(c);
-    cudaMemsetAsync(L.x, 0, 32 * L.cells, s);
-    k_kupdate<<<g, 256, 0, s>>>(p->kZ, m4, KCYC, y, 1.0, reinterpret_cast<double*>(L.x), m4), ::mb::count_launch(c);
+    k_klsq<<<1, 1, 0, s>>>(H, b2, K, y, ydf), ::mb::count_launch(c);
+    k_kcombine<<<nblk(L.cells), 256, 0, s>>>(p->kZ, L.cells, K, ydf, L.x), ::mb::count_launch(c);
 }
 
 // ---- MB_DEBUG >= 2: 2-norms of the intermediate vectors of one application
 template <class T>
+__device__ inline double dbg_sq(T a) { return (double)a * (double)a; }
+template <>
+__device__ inline double dbg_sq<float2>(float2 a) { double v = df_to_double(a); return v * v; }
+
+template <class T>
 __global__ void __launch_bounds__(RED_THREADS) k_sumsq(const T* __restrict__ a, int64_t n, double* partials) {
     double acc[1] = {0.0};
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        acc[0] += (double)a[i] * (double)a[i];
+        acc[0] += dbg_sq<T>(a[i]);
     block_reduce_store<1, false>(acc, partials);
 }
 
@@ -904,29 +1052,24 @@ static double dbg_norm(mb_cell* c, const T* a, int64_t n) {
 
 int debug_level();
 
-int precond_apply(mb_cell* c, const float* u32, const uint8_t* gate, double dt, const double* r, double* z) {
-    if (debug_level() >= 2) {
-        Precond* p = c->pc;
-        int rc = 0;
-        const Dims& D = c->D;
-        fprintf(stderr, "[mb-pc] levels %d coarse n %d |r| %.3e |rowdiag| %.3e\n", p->nlev, p->ncoarse,
-                dbg_norm(c, r, c->n), dbg_norm(c, c->rowdiag, c->n));
-        (void)rc; (void)D;
-    }
+// the kernel sequence of one application (stream-ordered, no host synchronisation
+// unless MB_DEBUG >= 2)
+static int apply_body(mb_cell* c, const float* r, float2* z) {
     Precond* p = c->pc;
     const Dims& D = c->D;
     cudaStream_t s = c->stream;
+    if (debug_level() >= 2)
+        fprintf(stderr, "[mb-pc] levels %d coarse n %d |r| %.3e |rowdiag| %.3e\n", p->nlev, p->ncoarse,
+                dbg_norm(c, r, c->n), dbg_norm(c, c->rowdiag, c->n));
     const dim3 vg = pgrid(D.nt, D.ny, D.nz);
     const unsigned fg = nblk(D.F ? D.F : 1);
-    cudaEvent_t ev_pc;
-    prof_begin(c, s, &ev_pc);
     // condensed right-hand side, then NU_FINE damped block-Jacobi sweeps from zero
     k_condense_rhs<<<vg, PB, 0, s>>>(D, c->vcode, p->fc, r, c->rowdiag, p->rv), ::mb::count_launch(c);
     k_bj_apply<<<nblk(D.N), 256, 0, s>>>(D, p->dinv, p->rv, nullptr, OMEGA_FINE, false, z), ::mb::count_launch(c);
     // t = S z_v  (S applied as the JVP of [z_v, -D_n^-1 J_nv z_v])
     auto apply_S = [&]() -> int {
         if (D.F) k_face_solve<<<fg, 256, 0, s>>>(D, c->pf_g, c->pf_e, p->fc, nullptr, c->rowdiag, z), ::mb::count_launch(c);
-        return launch_jvp<float, double>(c, u32, gate, dt, z, p->t, s, 1);
+        return launch_jvp_lin(c, z, p->t, s, 1);
     };
     int rc;
     for (int k = 1; k < NU_FINE; ++k) {
@@ -939,10 +1082,13 @@ int precond_apply(mb_cell* c, const float* u32, const uint8_t* gate, double dt, 
     if (debug_level() >= 2)
         fprintf(stderr, "[mb-pc] |rv| %.3e |z0| %.3e |Sz0| %.3e |b1| %.3e\n", dbg_norm(c, p->rv, 2 * D.N),
                 dbg_norm(c, z, 2 * D.N), dbg_norm(c, p->t, 2 * D.N),
-                dbg_norm(c, reinterpret_cast<const double*>(L1.b), 4 * L1.cells));
+                dbg_norm(c, reinterpret_cast<const float*>(L1.b), 4 * L1.cells));
     kcycle_l1(c);
-    if (debug_level() >= 2)
-        fprintf(stderr, "[mb-pc] |x1| %.3e\n", dbg_norm(c, reinterpret_cast<const double*>(L1.x), 4 * L1.cells));
+    if (debug_level() >= 2) {
+        k_lvl_matvec<<<nblk(L1.cells), 256, 0, s>>>(L1, L1.x, reinterpret_cast<float4*>(p->kw)), ::mb::count_launch(c);
+        fprintf(stderr, "[mb-pc] |x1| %.3e |A1 x1| %.3e\n",
+                dbg_norm(c, reinterpret_cast<const float2*>(L1.x), 4 * L1.cells), dbg_norm(c, p->kw, 4 * L1.cells));
+    }
     k_prolong_fine<<<vg, PB, 0, s>>>(D, c->vcode, L1, L1.x, z), ::mb::count_launch(c);
     // NU_FINE post-smoothing sweeps (they remove the jumps of the piecewise-constant prolongation)
     for (int k = 0; k < NU_FINE; ++k) {
@@ -951,9 +1097,90 @@ int precond_apply(mb_cell* c, const float* u32, const uint8_t* gate, double dt, 
     }
     // back-substitution of the plating rows
     if (D.F) k_face_solve<<<fg, 256, 0, s>>>(D, c->pf_g, c->pf_e, p->fc, r, c->rowdiag, z), ::mb::count_launch(c);
-    prof_end(c, s, PROF_PRECOND, ev_pc);
     if (debug_level() >= 2) fprintf(stderr, "[mb-pc] |z| %.3e\n", dbg_norm(c, z, c->n));
     MB_CUDA_LAUNCH("precond_apply");
+    return MB_OK;
+}
+
+void precond_harvest(mb_cell* c) {
+    Precond* p = c->pc;
+    if (!p || p->pending < 0) return;
+    PcGraph& G = p->graphs[p->pending];
+    p->pending = -1;
+    if (G.ev.empty()) return;
+    if (cudaEventSynchronize(G.ev.back().e1) != cudaSuccess) return;
+    for (auto& e : G.ev) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, e.e0, e.e1) == cudaSuccess) {
+            c->prof.acc_ms[e.kind] += ms;
+            c->prof.acc_n[e.kind] += 1;
+        }
+    }
+}
+
+// capture the application for (r, z) into a new graph; false if capture is not possible
+static bool capture_graph(mb_cell* c, const float* r, float2* z, PcGraph& G) {
+    Precond* p = c->pc;
+    cudaStream_t s = c->stream;
+    G.r = r;
+    G.z = z;
+    G.kcyc = p->kcyc;
+    G.prof = c->prof.enabled;
+    if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    const int64_t saved = c->launches;
+    if (G.prof) c->prof.capture = &G.ev;
+    int rc = apply_body(c, r, z);
+    c->prof.capture = nullptr;
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(s, &g);
+    G.nodes = c->launches - saved;
+    c->launches = saved;
+    bool ok = rc == MB_OK && e == cudaSuccess && g;
+    if (ok) ok = cudaGraphInstantiate(&G.exec, g, 0) == cudaSuccess;
+    if (g) cudaGraphDestroy(g);
+    if (!ok) {
+        cudaGetLastError();
+        graph_free(G);
+    }
+    return ok;
+}
+
+int precond_apply(mb_cell* c, const float* u32, const uint8_t* gate, double dt, const float* r, float2* z,
+                  bool graph) {
+    (void)u32; (void)gate; (void)dt;
+    Precond* p = c->pc;
+    cudaStream_t s = c->stream;
+    cudaEvent_t ev_pc;
+    if (!graph || p->graphs_off || debug_level() >= 2) {
+        prof_begin(c, s, &ev_pc);
+        int rc = apply_body(c, r, z);
+        prof_end(c, s, PROF_PRECOND, ev_pc);
+        return rc;
+    }
+    precond_harvest(c);
+    int idx = -1;
+    for (size_t i = 0; i < p->graphs.size(); ++i) {
+        const PcGraph& G = p->graphs[i];
+        if (G.r == r && G.z == z && G.kcyc == p->kcyc && G.prof == c->prof.enabled) { idx = (int)i; break; }
+    }
+    if (idx < 0) {
+        PcGraph G;
+        if (!capture_graph(c, r, z, G)) {
+            p->graphs_off = true;
+            return precond_apply(c, u32, gate, dt, r, z, false);
+        }
+        p->graphs.push_back(G);
+        idx = (int)p->graphs.size() - 1;
+    }
+    PcGraph& G = p->graphs[idx];
+    prof_begin(c, s, &ev_pc);
+    MB_CUDA(cudaGraphLaunch(G.exec, s));
+    prof_end(c, s, PROF_PRECOND, ev_pc);
+    count_launch(c, (int)G.nodes);
+    if (!G.ev.empty()) p->pending = idx;
     return MB_OK;
 }
 
@@ -970,6 +1197,11 @@ __global__ void k_cvt(const A* __restrict__ a, B* __restrict__ b, int64_t n) {
     if (i < n) b[i] = (B)a[i];
 }
 
+__global__ void k_df_to_double(const float2* __restrict__ a, double* __restrict__ b, int64_t n) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) b[i] = df_to_double(a[i]);
+}
+
 extern "C" {
 
 int mb_debug_precond(mb_cell* c, const double* u, const uint8_t* gate, double dt, const double* r, double* z) {
@@ -977,22 +1209,45 @@ int mb_debug_precond(mb_cell* c, const double* u, const uint8_t* gate, double dt
     int64_t n = c->n, F = c->D.F;
     cudaStream_t s = c->stream;
     double *du = nullptr, *r64 = nullptr, *z64 = nullptr;
+    float* r32 = nullptr;
+    float2* zdf = nullptr;
     MB_CUDA(cudaMalloc(&du, 8 * n));
     MB_CUDA(cudaMalloc(&r64, 8 * n));
     MB_CUDA(cudaMalloc(&z64, 8 * n));
+    MB_CUDA(cudaMalloc(&r32, 4 * n));
+    MB_CUDA(cudaMalloc(&zdf, 8 * n));
     MB_CUDA(cudaMemcpyAsync(du, u, 8 * n, cudaMemcpyHostToDevice, s));
     k_cvt<double, float><<<nblk(n), 256, 0, s>>>(du, c->u32, n), ::mb::count_launch(c);
     if (F) MB_CUDA(cudaMemcpyAsync(c->gate2, gate, F, cudaMemcpyHostToDevice, s));
     MB_CUDA(cudaMemcpyAsync(r64, r, 8 * n, cudaMemcpyHostToDevice, s));
+    k_cvt<double, float><<<nblk(n), 256, 0, s>>>(r64, r32, n), ::mb::count_launch(c);
     int rc = precond_setup(c, c->u32, c->gate2, dt);
-    if (!rc) rc = precond_apply(c, c->u32, c->gate2, dt, r64, z64);
+    if (!rc) rc = launch_lin_setup<float>(c, c->u32, c->gate2, s);
+    if (!rc) rc = set_dt(c, dt, s);
+    if (!rc) rc = precond_apply(c, c->u32, c->gate2, dt, r32, zdf, false);
     if (!rc) {
+        k_df_to_double<<<nblk(n), 256, 0, s>>>(zdf, z64, n), ::mb::count_launch(c);
         cudaMemcpyAsync(z, z64, 8 * n, cudaMemcpyDeviceToHost, s);
         if (cudaStreamSynchronize(s) != cudaSuccess) rc = cuda_fail(cudaGetLastError(), "debug_precond");
     }
     cudaStreamSynchronize(s);
-    cudaFree(du); cudaFree(r64); cudaFree(z64);
+    cudaFree(du); cudaFree(r64); cudaFree(z64); cudaFree(r32); cudaFree(zdf);
     return rc;
+}
+
+int mb_debug_residual_split(mb_cell* c, const double* u, const double* u_old, const uint8_t* gate, double dt,
+                            double I_app, double* r) {
+    if (!c || !u || !u_old || !r || !(dt > 0)) { set_error("mb_debug_residual_split: invalid argument"); return MB_EINVAL; }
+    int64_t n = c->n, F = c->D.F;
+    cudaStream_t s = c->stream;
+    MB_CUDA(cudaMemcpyAsync(c->du, u, 8 * n, cudaMemcpyHostToDevice, s));
+    MB_CUDA(cudaMemcpyAsync(c->u_pass, u_old, 8 * n, cudaMemcpyHostToDevice, s));
+    if (F) MB_CUDA(cudaMemcpyAsync(c->gate2, gate, F, cudaMemcpyHostToDevice, s));
+    int rc = launch_residual_split(c, c->du, c->u_pass, c->gate2, dt, I_app, c->r, s);
+    if (rc) return rc;
+    MB_CUDA(cudaMemcpyAsync(r, c->r, 8 * n, cudaMemcpyDeviceToHost, s));
+    MB_CUDA(cudaStreamSynchronize(s));
+    return MB_OK;
 }
 
 int mb_debug_levels(mb_cell* c, int* nlev) {
@@ -1011,8 +1266,20 @@ int mb_debug_level_dims(mb_cell* c, int level, int* nt, int* ny, int* nz) {
 int mb_debug_level_op(mb_cell* c, int level, float* aself, float* off, uint8_t* mask) {
     if (!c || level < 1 || level > c->pc->nlev) { set_error("mb_debug_level_op: bad level"); return MB_EINVAL; }
     const Level& L = c->pc->lv[level];
-    if (aself) MB_CUDA(cudaMemcpy(aself, L.aself, 4 * BLK * L.cells, cudaMemcpyDeviceToHost));
-    if (off) MB_CUDA(cudaMemcpy(off, L.off, 4 * OFFW * L.cells, cudaMemcpyDeviceToHost));
+    // device layout is structure of arrays; the caller gets one record per cell
+    std::vector<float> tmp;
+    if (aself) {
+        tmp.resize((size_t)BLK * L.cells);
+        MB_CUDA(cudaMemcpy(tmp.data(), L.aself, 4 * BLK * L.cells, cudaMemcpyDeviceToHost));
+        for (int64_t i = 0; i < L.cells; ++i)
+            for (int e = 0; e < BLK; ++e) aself[i * BLK + e] = tmp[(size_t)e * L.cells + i];
+    }
+    if (off) {
+        tmp.resize((size_t)OFFW * L.cells);
+        MB_CUDA(cudaMemcpy(tmp.data(), L.off, 4 * OFFW * L.cells, cudaMemcpyDeviceToHost));
+        for (int64_t i = 0; i < L.cells; ++i)
+            for (int e = 0; e < OFFW; ++e) off[i * OFFW + e] = tmp[(size_t)e * L.cells + i];
+    }
     if (mask) MB_CUDA(cudaMemcpy(mask, L.mask, L.cells, cudaMemcpyDeviceToHost));
     return MB_OK;
 }

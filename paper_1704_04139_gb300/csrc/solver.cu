@@ -1,8 +1,12 @@
 // solver.cu -- Newton-Krylov driver of one implicit Euler step (Eq.
 // ap4:detailed): scaled right-preconditioned flexible GMRES with classical
-// Gram-Schmidt and one re-orthogonalisation (dot products accumulated in
-// FP64, deterministic), the damped Newton update, the plating active-set
-// passes and step halving on failure.
+// Gram-Schmidt and one re-orthogonalisation, the damped Newton update, the
+// plating active-set passes and step halving on failure.
+// Precision: the state and the Newton residual are FP64; the Krylov solver
+// works in FP32 arithmetic with an FP32 basis V and float-float (hi + lo)
+// preconditioned directions Z and solution x, whose large near-null
+// components must keep their small structure; dot products use FP32 products
+// and FP64 sums (deterministic order).
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdio.h>
@@ -29,51 +33,67 @@ int debug_level() {
 constexpr int MDOT_G = 8;   // dot products per launch
 
 struct HParam {
-    double h[64];
+    float h[64];
+};
+struct HParamDF {
+    float2 y[64];
 };
 
-template <class T>
 struct Krylov {
     int m = 0;
     int64_t n = 0;
-    T* V = nullptr;      // (m+1) x n
-    T* Z = nullptr;      // m x n
-    T* w = nullptr;      // n
-    T* b = nullptr;      // n  right-hand side (scaled)
-    T* x = nullptr;      // n  solution (scaled)
+    float* V = nullptr;      // (m+1) x n
+    float2* Z = nullptr;     // m x n
+    float* w = nullptr;      // n
+    float* b = nullptr;      // n  right-hand side (scaled, row-equilibrated)
+    float2* x = nullptr;     // n  solution (scaled)
 };
 
 // ------------------------------------------------------------ vector kernels
-template <class T>
 __global__ void __launch_bounds__(RED_THREADS)
-k_mdot(const T* __restrict__ V, int64_t stride, int cnt, const T* __restrict__ w, int64_t n,
+k_mdot(const float* __restrict__ V, int64_t stride, int cnt, const float* __restrict__ w, int64_t n,
        double* partials) {
-    double acc[MDOT_G];
+    float a32[MDOT_G];
 #pragma unroll
-    for (int j = 0; j < MDOT_G; ++j) acc[j] = 0.0;
+    for (int j = 0; j < MDOT_G; ++j) a32[j] = 0.f;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        double wi = (double)w[i];
+        float wi = w[i];
 #pragma unroll
         for (int j = 0; j < MDOT_G; ++j)
-            if (j < cnt) acc[j] += (double)V[j * stride + i] * wi;
+            if (j < cnt) a32[j] = fmaf(V[j * stride + i], wi, a32[j]);
     }
-    block_reduce_store<MDOT_G, false>(acc, partials);
+    block_reduce_store_f32<MDOT_G>(a32, partials);
 }
 
-template <class T>
-__global__ void k_mupdate(const T* __restrict__ V, int64_t stride, int cnt, HParam hp, T* __restrict__ w,
-                          int64_t n, double sign) {
+// w += sign * sum_j h[j] V_j
+__global__ void k_mupdate(const float* __restrict__ V, int64_t stride, int cnt, HParam hp, float* __restrict__ w,
+                          int64_t n, float sign) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    double acc = 0.0;
-    for (int j = 0; j < cnt; ++j) acc += hp.h[j] * (double)V[j * stride + i];
-    w[i] = (T)((double)w[i] + sign * acc);
+    float acc = 0.f;
+    for (int j = 0; j < cnt; ++j) acc = fmaf(hp.h[j], V[j * stride + i], acc);
+    w[i] = fmaf(sign, acc, w[i]);
 }
 
-template <class T>
-__global__ void k_scale(const T* __restrict__ a, double alpha, T* __restrict__ b, int64_t n) {
+// x += sum_j y[j] Z_j in float-float arithmetic
+__global__ void k_combine(const float2* __restrict__ Z, int64_t stride, int cnt, HParamDF hp,
+                          float2* __restrict__ x, int64_t n) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) b[i] = (T)(alpha * (double)a[i]);
+    if (i >= n) return;
+    float2 acc = x[i];
+    for (int j = 0; j < cnt; ++j) acc = df_add(acc, df_mul(Z[j * stride + i], hp.y[j]));
+    x[i] = acc;
+}
+
+__global__ void k_scale(const float* __restrict__ a, float alpha, float* __restrict__ b, int64_t n) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) b[i] = alpha * a[i];
+}
+
+// w = b - w
+__global__ void k_rsub(const float* __restrict__ b, float* __restrict__ w, int64_t n) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) w[i] = b[i] - w[i];
 }
 
 template <class A, class B>
@@ -87,28 +107,21 @@ __global__ void k_axpy_d(double alpha, const double* __restrict__ x, double* __r
     if (i < n) y[i] += alpha * x[i];
 }
 
-// b_hat = -R / s_r / |diag|  (row-equilibrated right-hand side)
-template <class T>
-__global__ void k_scale_rhs(DevParams P, Dims D, const uint32_t* __restrict__ vc, const double* __restrict__ R,
-                            double dt_inv, const float* __restrict__ rowdiag, T* __restrict__ b) {
+// b_hat = -R / s_r / |diag|  (row-equilibrated right-hand side; is = 1/s_r)
+__global__ void k_scale_rhs(Dims D, const uint32_t* __restrict__ vc, const double* __restrict__ R, InvScales is,
+                            const float* __restrict__ rowinv, float* __restrict__ b) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int64_t n = 2 * D.N + D.F;
     if (i >= n) return;
     double s;
-    if (i < D.N) {
-        int l = vc_phase(vc[i]);
-        s = has_c(l) ? P.V * P.cref[l] * dt_inv : 1.0;
-    } else if (i < 2 * D.N) {
-        s = P.A;
-    } else {
-        s = sqrt(sqrt(P.nc4)) * dt_inv;
-    }
-    b[i] = (T)(-R[i] / (s * (double)rowdiag[i]));
+    if (i < D.N) s = is.c[vc_phase(vc[i])];
+    else if (i < 2 * D.N) s = is.phi;
+    else s = is.n;
+    b[i] = (float)(-R[i] * s) * rowinv[i];
 }
 
 // delta = s_u * x_hat
-template <class T>
-__global__ void k_unscale(DevParams P, Dims D, const uint32_t* __restrict__ vc, const T* __restrict__ x,
+__global__ void k_unscale(DevParams P, Dims D, const uint32_t* __restrict__ vc, const float2* __restrict__ x,
                           double* __restrict__ d) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int64_t n = 2 * D.N + D.F;
@@ -116,19 +129,18 @@ __global__ void k_unscale(DevParams P, Dims D, const uint32_t* __restrict__ vc, 
     double s;
     if (i < D.N) s = P.cref[vc_phase(vc[i])];
     else if (i < 2 * D.N) s = 1.0;
-    else s = sqrt(sqrt(P.nc4));
-    d[i] = s * (double)x[i];
+    else s = P.nc;
+    d[i] = s * df_to_double(x[i]);
 }
 
 static inline unsigned nblk(int64_t n) { return (unsigned)((n + 255) / 256); }
 
 // dots out[j] = <V_j, w> for j in [0, cnt)
-template <class T>
-static int mdot(mb_cell* c, const T* V, int64_t stride, int cnt, const T* w, int64_t n, double* out) {
+static int mdot(mb_cell* c, const float* V, int64_t stride, int cnt, const float* w, int64_t n, double* out) {
     cudaStream_t s = c->stream;
     for (int j0 = 0; j0 < cnt; j0 += MDOT_G) {
         int k = cnt - j0 < MDOT_G ? cnt - j0 : MDOT_G;
-        k_mdot<T><<<RED_BLOCKS, RED_THREADS, 0, s>>>(V + j0 * stride, stride, k, w, n, c->red), ::mb::count_launch(c);
+        k_mdot<<<RED_BLOCKS, RED_THREADS, 0, s>>>(V + j0 * stride, stride, k, w, n, c->red), ::mb::count_launch(c);
         k_reduce_final<false><<<k, RED_THREADS, 0, s>>>(c->red, k, c->red_out + j0), ::mb::count_launch(c);
     }
     MB_CUDA_LAUNCH("mdot");
@@ -138,56 +150,46 @@ static int mdot(mb_cell* c, const T* V, int64_t stride, int cnt, const T* w, int
     return MB_OK;
 }
 
-template <class T>
-static int mupdate(mb_cell* c, const T* V, int64_t stride, int cnt, const double* h, T* w, int64_t n,
-                   double sign) {
+static int mupdate(mb_cell* c, const float* V, int64_t stride, int cnt, const double* h, float* w, int64_t n,
+                   float sign) {
     for (int j0 = 0; j0 < cnt; j0 += 64) {
         int k = cnt - j0 < 64 ? cnt - j0 : 64;
         HParam hp;
-        for (int j = 0; j < k; ++j) hp.h[j] = h[j0 + j];
-        k_mupdate<T><<<nblk(n), 256, 0, c->stream>>>(V + j0 * stride, stride, k, hp, w, n, sign), ::mb::count_launch(c);
+        for (int j = 0; j < k; ++j) hp.h[j] = (float)h[j0 + j];
+        k_mupdate<<<nblk(n), 256, 0, c->stream>>>(V + j0 * stride, stride, k, hp, w, n, sign), ::mb::count_launch(c);
     }
     MB_CUDA_LAUNCH("mupdate");
     return MB_OK;
 }
 
 // Krylov operator: the row-equilibrated scaled JVP at the current Newton
-// iterate.  FP64 path: coefficients from the FP64 state; mixed path: the
-// nonlinear per-face coefficients from the FP32 copy of the state, applied to
-// FP64 vectors.
+// iterate, FP32 arithmetic on a float-float direction, from the interface
+// partials stored by launch_lin_setup (evaluated from the FP64 state in FP64
+// for MB_PREC_FP64, from its FP32 copy in FP32 for MB_PREC_MIXED).
 struct OpCtx {
-    const double* u64;
     const float* u32;
-    bool mixed;
     const uint8_t* gate;
     double dt;
 };
 
-template <class T>
-static int apply_op(mb_cell* c, const OpCtx& o, const T* x, T* y) {
-    if (o.mixed) return launch_jvp<float, T>(c, o.u32, o.gate, o.dt, x, y, c->stream, 2);
-    return launch_jvp<double, T>(c, o.u64, o.gate, o.dt, x, y, c->stream, 2);
-}
-
-static int apply_prec(mb_cell* c, Krylov<double>* K, const OpCtx& o, const double* x, double* y) {
-    (void)K;
-    return precond_apply(c, o.u32, o.gate, o.dt, x, y);
+static int apply_op(mb_cell* c, const OpCtx& o, const float2* x, float* y) {
+    (void)o;
+    return launch_jvp_lin(c, x, y, c->stream, 2);
 }
 
 // Flexible GMRES(m) on A x = b (x starts at zero), stopping at
 // ||b - A x||_2 <= rtol ||b||_2 or after maxit iterations.
-template <class T>
-static int fgmres(mb_cell* c, Krylov<T>* K, const OpCtx& o, double rtol, int maxit, int* its_out,
+static int fgmres(mb_cell* c, Krylov* K, const OpCtx& o, double rtol, int maxit, int* its_out,
                   double* relres_out) {
     const int64_t n = K->n;
     const int m = K->m;
     cudaStream_t s = c->stream;
     std::vector<double> H((m + 1) * m), cs(m), sn(m), g(m + 1), y(m), hv(m + 1), h2(m + 1);
-    MB_CUDA(cudaMemsetAsync(K->x, 0, n * sizeof(T), s));
+    MB_CUDA(cudaMemsetAsync(K->x, 0, n * sizeof(float2), s));
     double beta0 = 0.0;
     {
         double d;
-        int rc = mdot<T>(c, K->b, 0, 1, K->b, n, &d);
+        int rc = mdot(c, K->b, 0, 1, K->b, n, &d);
         if (rc) return rc;
         beta0 = sqrt(d);
     }
@@ -201,49 +203,47 @@ static int fgmres(mb_cell* c, Krylov<T>* K, const OpCtx& o, double rtol, int max
     while (its < maxit) {
         // r = b - A x  (first cycle: r = b)
         double beta;
+        const float* r0 = K->b;
         if (first) {
-            k_scale<T><<<nblk(n), 256, 0, s>>>(K->b, 1.0, K->w, n), ::mb::count_launch(c);
             beta = beta0;
         } else {
-            int rc = apply_op<T>(c, o, K->x, K->w);
+            int rc = apply_op(c, o, K->x, K->w);
             if (rc) return rc;
-            k_scale<T><<<nblk(n), 256, 0, s>>>(K->w, -1.0, K->w, n), ::mb::count_launch(c);
-            double one = 1.0;
-            HParam hp; hp.h[0] = one;
-            k_mupdate<T><<<nblk(n), 256, 0, s>>>(K->b, 0, 1, hp, K->w, n, 1.0), ::mb::count_launch(c);
+            k_rsub<<<nblk(n), 256, 0, s>>>(K->b, K->w, n), ::mb::count_launch(c);
             double d;
-            rc = mdot<T>(c, K->w, 0, 1, K->w, n, &d);
+            rc = mdot(c, K->w, 0, 1, K->w, n, &d);
             if (rc) return rc;
             beta = sqrt(d);
+            r0 = K->w;
         }
         first = false;
-        k_scale<T><<<nblk(n), 256, 0, s>>>(K->w, 1.0 / beta, K->V, n), ::mb::count_launch(c);
+        k_scale<<<nblk(n), 256, 0, s>>>(r0, (float)(1.0 / beta), K->V, n), ::mb::count_launch(c);
         std::fill(g.begin(), g.end(), 0.0);
         g[0] = beta;
         int j = 0;
         for (; j < m && its < maxit; ++j) {
-            T* Vj = K->V + j * n;
-            T* Zj = K->Z + j * n;
-            int rc = apply_prec(c, K, o, Vj, Zj);
+            float* Vj = K->V + j * n;
+            float2* Zj = K->Z + j * n;
+            int rc = precond_apply(c, o.u32, o.gate, o.dt, Vj, Zj);
             if (rc) return rc;
-            rc = apply_op<T>(c, o, Zj, K->w);
+            rc = apply_op(c, o, Zj, K->w);
             if (rc) return rc;
             // CGS2
-            rc = mdot<T>(c, K->V, n, j + 1, K->w, n, hv.data());
+            rc = mdot(c, K->V, n, j + 1, K->w, n, hv.data());
             if (rc) return rc;
-            rc = mupdate<T>(c, K->V, n, j + 1, hv.data(), K->w, n, -1.0);
+            rc = mupdate(c, K->V, n, j + 1, hv.data(), K->w, n, -1.f);
             if (rc) return rc;
-            rc = mdot<T>(c, K->V, n, j + 1, K->w, n, h2.data());
+            rc = mdot(c, K->V, n, j + 1, K->w, n, h2.data());
             if (rc) return rc;
-            rc = mupdate<T>(c, K->V, n, j + 1, h2.data(), K->w, n, -1.0);
+            rc = mupdate(c, K->V, n, j + 1, h2.data(), K->w, n, -1.f);
             if (rc) return rc;
             for (int i = 0; i <= j; ++i) hv[i] += h2[i];
             double d;
-            rc = mdot<T>(c, K->w, 0, 1, K->w, n, &d);
+            rc = mdot(c, K->w, 0, 1, K->w, n, &d);
             if (rc) return rc;
             double hn = sqrt(d);
             hv[j + 1] = hn;
-            if (hn > 0) k_scale<T><<<nblk(n), 256, 0, s>>>(K->w, 1.0 / hn, K->V + (j + 1) * n, n), ::mb::count_launch(c);
+            if (hn > 0) k_scale<<<nblk(n), 256, 0, s>>>(K->w, (float)(1.0 / hn), K->V + (j + 1) * n, n), ::mb::count_launch(c);
             // Givens rotations
             for (int i = 0; i < j; ++i) {
                 double a = cs[i] * hv[i] + sn[i] * hv[i + 1];
@@ -270,8 +270,16 @@ static int fgmres(mb_cell* c, Krylov<T>* K, const OpCtx& o, double rtol, int max
             for (int l = i + 1; l < k; ++l) acc -= H[i * m + l] * y[l];
             y[i] = acc / H[i * m + i];
         }
-        int rc = mupdate<T>(c, K->Z, n, k, y.data(), K->x, n, 1.0);
-        if (rc) return rc;
+        for (int j0 = 0; j0 < k; j0 += 64) {
+            int kk = k - j0 < 64 ? k - j0 : 64;
+            HParamDF hp;
+            for (int jj = 0; jj < kk; ++jj) {
+                float yh = (float)y[j0 + jj];
+                hp.y[jj] = make_float2(yh, (float)(y[j0 + jj] - (double)yh));
+            }
+            k_combine<<<nblk(n), 256, 0, s>>>(K->Z + j0 * n, n, kk, hp, K->x, n), ::mb::count_launch(c);
+        }
+        MB_CUDA_LAUNCH("fgmres update");
         if (relres <= rtol) break;
     }
     *its_out = its;
@@ -279,17 +287,16 @@ static int fgmres(mb_cell* c, Krylov<T>* K, const OpCtx& o, double rtol, int max
     return MB_OK;
 }
 
-template <class T>
-static int krylov_create(mb_cell* c, Krylov<T>** out) {
-    Krylov<T>* K = new Krylov<T>();
+static int krylov_create(mb_cell* c, Krylov** out) {
+    Krylov* K = new Krylov();
     K->m = c->opt.gmres_m;
     K->n = c->n;
-    size_t vb = sizeof(T) * (size_t)c->n;
-    K->V = (T*)cell_alloc(c, vb * (K->m + 1));
-    K->Z = (T*)cell_alloc(c, vb * K->m);
-    K->w = (T*)cell_alloc(c, vb);
-    K->b = (T*)cell_alloc(c, vb);
-    K->x = (T*)cell_alloc(c, vb);
+    size_t n = (size_t)c->n;
+    K->V = (float*)cell_alloc(c, 4 * n * (K->m + 1));
+    K->Z = (float2*)cell_alloc(c, 8 * n * K->m);
+    K->w = (float*)cell_alloc(c, 4 * n);
+    K->b = (float*)cell_alloc(c, 4 * n);
+    K->x = (float2*)cell_alloc(c, 8 * n);
     *out = K;
     if (!K->V || !K->Z || !K->w || !K->b || !K->x) return MB_ENOMEM;
     return MB_OK;
@@ -303,13 +310,17 @@ static int linear_solve(mb_cell* c, double dt, int* its, double* relres) {
     MB_CUDA_LAUNCH("u32");
     int rc = precond_setup(c, c->u32, c->gate, dt);
     if (rc) return rc;
-    if (!c->kd && (rc = krylov_create<double>(c, &c->kd))) return rc;
-    Krylov<double>* K = c->kd;
-    k_scale_rhs<double><<<nblk(n), 256, 0, s>>>(c->P, c->D, c->vcode, c->r, 1.0 / dt, c->rowdiag, K->b), ::mb::count_launch(c);
-    OpCtx o{c->u, c->u32, c->opt.precision == MB_PREC_MIXED, c->gate, dt};
-    rc = fgmres<double>(c, K, o, c->opt.krylov_rtol, c->opt.krylov_maxit, its, relres);
+    if ((rc = set_dt(c, dt, s))) return rc;
+    rc = c->opt.precision == MB_PREC_MIXED ? launch_lin_setup<float>(c, c->u32, c->gate, s)
+                                           : launch_lin_setup<double>(c, c->u, c->gate, s);
     if (rc) return rc;
-    k_unscale<double><<<nblk(n), 256, 0, s>>>(c->P, c->D, c->vcode, K->x, c->du), ::mb::count_launch(c);
+    if (!c->kd && (rc = krylov_create(c, &c->kd))) return rc;
+    Krylov* K = c->kd;
+    k_scale_rhs<<<nblk(n), 256, 0, s>>>(c->D, c->vcode, c->r, inv_scales(c, 1, dt), c->rowinv, K->b), ::mb::count_launch(c);
+    OpCtx o{c->u32, c->gate, dt};
+    rc = fgmres(c, K, o, c->opt.krylov_rtol, c->opt.krylov_maxit, its, relres);
+    if (rc) return rc;
+    k_unscale<<<nblk(n), 256, 0, s>>>(c->P, c->D, c->vcode, K->x, c->du), ::mb::count_launch(c);
     MB_CUDA_LAUNCH("linear_solve");
     return MB_OK;
 }
@@ -328,7 +339,7 @@ static int newton(mb_cell* c, double dt, double I_app, int* its_out, int* kits, 
     MB_CUDA(cudaMemcpyAsync(c->u, c->u_old, 8 * n, cudaMemcpyDeviceToDevice, s));
     *ok = false;
     for (int it = 1; it <= c->opt.newton_maxit; ++it) {
-        int rc = launch_residual<double>(c, c->u, c->u_old, c->gate, dt, I_app, c->r, s);
+        int rc = launch_residual_split(c, c->u, c->u_old, c->gate, dt, I_app, c->r, s);
         if (rc) return rc;
         double rn;
         if ((rc = scaled_maxnorm(c, c->r, 1, dt, &rn))) return rc;
