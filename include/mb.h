@@ -76,7 +76,7 @@ typedef struct {
     int    max_passes;     /* plating active-set passes per step (>= 1) */
     int    max_halvings;   /* dt halvings on Newton failure */
     int    mg_coarse_cells;/* multigrid: coarsen until at most this many cells */
-    int    mg_smooth;      /* block-Jacobi sweeps per level, pre and post */
+    int    mg_smooth;      /* fine-level block-Jacobi sweeps before and after the coarse correction (1..8) */
     int    mg_kcycle;      /* FGMRES iterations of the level-1 K-cycle (1..16) */
 } mb_solver_opts;
 

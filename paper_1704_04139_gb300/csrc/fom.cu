@@ -116,26 +116,23 @@ __global__ void k_scan_add(uint32_t* out, int64_t n, const uint32_t* bsum) {
 // voxels ([F, NI)), each group by solid voxel index, then direction.
 __global__ void k_classify_write(Dims D, const uint8_t* __restrict__ lab, const uint8_t* __restrict__ emask,
                                  const uint32_t* __restrict__ fbase, const uint32_t* __restrict__ kbase,
-                                 uint32_t* __restrict__ vcode, int32_t* __restrict__ pf_g,
-                                 int32_t* __restrict__ pf_e, int8_t* __restrict__ pf_dir) {
+                                 uint32_t* __restrict__ vcode, int32_t* __restrict__ if_s,
+                                 int32_t* __restrict__ if_e, int8_t* __restrict__ pf_dir) {
     int z, y, t;
     vox_coords(D, z, y, t);
     if (z >= D.nz || y >= D.ny) return;
     int64_t v = (int64_t)t * D.syz + (int64_t)y * D.nz + z;
     uint32_t m = emask[v];
-    uint32_t fb = fbase[v];
-    if (lab[v] != PG) {
-        vcode[v] = (uint32_t)lab[v] | (m << 3) | (m ? ((uint32_t)D.F + kbase[v]) << VC_FBASE_SHIFT : 0u);
-        return;
-    }
+    const bool g = lab[v] == PG;
+    uint32_t fb = g ? fbase[v] : (m ? (uint32_t)D.F + kbase[v] : 0u);
     vcode[v] = (uint32_t)lab[v] | (m << 3) | (fb << VC_FBASE_SHIFT);
     const int64_t off[6] = {-D.syz, D.syz, -(int64_t)D.nz, (int64_t)D.nz, -1, 1};
     uint32_t f = fb;
     for (int d = 0; d < 6; ++d) {
         if (m & (1u << d)) {
-            pf_g[f] = (int32_t)v;
-            pf_e[f] = (int32_t)(v + off[d]);
-            pf_dir[f] = (int8_t)d;
+            if_s[f] = (int32_t)v;
+            if_e[f] = (int32_t)(v + off[d]);
+            if (g) pf_dir[f] = (int8_t)d;
             ++f;
         }
     }
@@ -192,15 +189,19 @@ int launch_classify(mb_cell* c, const uint8_t* d_lab) {
         c->D.NI = (int64_t)h_tot[0] + h_tot[1];
         c->n = 2 * N + (int64_t)h_total;
         size_t F = h_total ? h_total : 1;
+        size_t NI = c->D.NI ? (size_t)c->D.NI : 1;
         c->vcode = (uint32_t*)cell_alloc(c, N * 4);
-        c->pf_g = (int32_t*)cell_alloc(c, F * 4);
-        c->pf_e = (int32_t*)cell_alloc(c, F * 4);
+        // interface face list; the plating faces are its first F entries
+        c->if_s = (int32_t*)cell_alloc(c, NI * 4);
+        c->if_e = (int32_t*)cell_alloc(c, NI * 4);
+        c->pf_g = c->if_s;
+        c->pf_e = c->if_e;
         c->pf_dir = (int8_t*)cell_alloc(c, F);
-        if (!c->vcode || !c->pf_g || !c->pf_e || !c->pf_dir) rc = MB_ENOMEM;
+        if (!c->vcode || !c->if_s || !c->if_e || !c->pf_dir) rc = MB_ENOMEM;
     }
     if (rc == MB_OK) {
         k_classify_write<<<vox_grid(D, VOX_BLOCK), VOX_BLOCK, 0, s>>>(
-            c->D, d_lab, emask, fbase, kbase, c->vcode, c->pf_g, c->pf_e, c->pf_dir), ::mb::count_launch(c);
+            c->D, d_lab, emask, fbase, kbase, c->vcode, c->if_s, c->if_e, c->pf_dir), ::mb::count_launch(c);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) rc = cuda_fail(e, "classify_write");
     }
@@ -313,35 +314,23 @@ k_residual(ParT<T> P, Dims D, const uint32_t* __restrict__ vc, const T* __restri
 // evaluates each interface current twice (once from each side); the C-ABI
 // residual entry points use that single-kernel form.
 __global__ void __launch_bounds__(256)
-k_iface_current(DevParams P, Dims D, const uint32_t* __restrict__ vc, const double* __restrict__ u,
-                const uint8_t* __restrict__ gate, double s_i0, double k_pl, double* __restrict__ icur) {
-    int z, y, t;
-    vox_coords(D, z, y, t);
-    if (z >= D.nz || y >= D.ny) return;
-    int64_t v = (int64_t)t * D.syz + (int64_t)y * D.nz + z;
-    uint32_t code = vc[v];
-    int lv = vc_phase(code);
-    uint32_t m = vc_emask(code);
-    if (!m || !(lv == PG || lv == PK || lv == PL)) return;
+k_iface_current(DevParams P, Dims D, const uint32_t* __restrict__ vc, const int32_t* __restrict__ if_s,
+                const int32_t* __restrict__ if_e, const double* __restrict__ u, const uint8_t* __restrict__ gate,
+                double s_i0, double k_pl, double* __restrict__ icur) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t N = D.N, NI = D.NI;
-    const double cs = u[v], ps = u[N + v];
-    const int64_t off[6] = {-D.syz, D.syz, -(int64_t)D.nz, (int64_t)D.nz, -1, 1};
-    int64_t i = vc_fbase(code);
-    for (int d = 0; d < 6; ++d) {
-        if (!(m & (1u << d))) continue;
-        int64_t w = v + off[d];
-        double nf = 0.0;
-        bool g = false;
-        if (lv == PG) {
-            nf = u[2 * N + i];
-            g = gate[i] != 0;
-        }
-        double ibv, ipl;
-        interface_current<double>(P, lv, cs, ps, u[w], u[N + w], nf, g, s_i0, k_pl, ibv, ipl);
-        icur[i] = ibv;
-        icur[NI + i] = ipl;
-        ++i;
+    if (i >= NI) return;
+    const int64_t v = if_s[i], w = if_e[i];
+    double nf = 0.0;
+    bool g = false;
+    if (i < D.F) {   // plating face
+        nf = u[2 * N + i];
+        g = gate[i] != 0;
     }
+    double ibv, ipl;
+    interface_current<double>(P, vc_phase(vc[v]), u[v], u[N + v], u[w], u[N + w], nf, g, s_i0, k_pl, ibv, ipl);
+    icur[i] = ibv;
+    icur[NI + i] = ipl;
 }
 
 __global__ void __launch_bounds__(256)
@@ -405,8 +394,8 @@ int launch_residual_split(mb_cell* c, const double* u, const double* u_old, cons
     cudaEvent_t ev;
     prof_begin(c, s, &ev);
     if (D.NI)
-        k_iface_current<<<vox_grid(D, VOX_BLOCK), VOX_BLOCK, 0, s>>>(c->P, D, c->vcode, u, gate, c->s_i0, c->k_pl,
-                                                                     c->icur), ::mb::count_launch(c);
+        k_iface_current<<<(unsigned)((D.NI + 255) / 256), 256, 0, s>>>(c->P, D, c->vcode, c->if_s, c->if_e, u, gate,
+                                                                       c->s_i0, c->k_pl, c->icur), ::mb::count_launch(c);
     k_residual_split<<<vox_grid(D, VOX_BLOCK), VOX_BLOCK, 0, s>>>(c->P, D, c->vcode, u, u_old, c->icur, 1.0 / dt,
                                                                   I_app, r), ::mb::count_launch(c);
     prof_end(c, s, PROF_RESIDUAL, ev);
@@ -560,51 +549,42 @@ template int launch_jvp<float, float>(mb_cell*, const float*, const uint8_t*, do
 // interface face, and k_jvp_lin applies the Jacobian as a stencil on them.
 // One thread per voxel; solid voxels with electrolyte neighbours write the
 // partials of their own interface faces.
+// One thread per interface face (solid voxel if_s[i], electrolyte voxel
+// if_e[i]); faces [0, F) are the plating faces.
 template <class TC>
 __global__ void __launch_bounds__(256)
-k_lin_setup(ParT<TC> P, Dims D, const uint32_t* __restrict__ vc, const TC* __restrict__ u,
-            const uint8_t* __restrict__ gate, double s_i0d, double k_pld, float* __restrict__ icoef) {
-    int z, y, t;
-    vox_coords(D, z, y, t);
-    if (z >= D.nz || y >= D.ny) return;
-    int64_t v = (int64_t)t * D.syz + (int64_t)y * D.nz + z;
-    uint32_t code = vc[v];
-    int lv = vc_phase(code);
-    uint32_t m = vc_emask(code);
-    if (!m || !(lv == PG || lv == PK || lv == PL)) return;
+k_lin_setup(ParT<TC> P, Dims D, const uint32_t* __restrict__ vc, const int32_t* __restrict__ if_s,
+            const int32_t* __restrict__ if_e, const TC* __restrict__ u, const uint8_t* __restrict__ gate,
+            double s_i0d, double k_pld, float* __restrict__ icoef) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t N = D.N, NI = D.NI;
+    if (i >= NI) return;
+    const int64_t v = if_s[i], w = if_e[i];
+    const int lv = vc_phase(vc[v]);
     const TC s_i0 = TC(s_i0d), k_pl = TC(k_pld);
-    const TC cs = u[v], ps = u[N + v];
-    const int64_t off[6] = {-D.syz, D.syz, -(int64_t)D.nz, (int64_t)D.nz, -1, 1};
-    int64_t i = vc_fbase(code);
-    for (int d = 0; d < 6; ++d) {
-        if (!(m & (1u << d))) continue;
-        int64_t w = v + off[d];
-        TC nf = TC(0);
-        bool g = false;
-        if (lv == PG) {   // plating face i (same index as the interface face)
-            nf = u[2 * N + i];
-            g = gate[i] != 0;
-        }
-        TC i_eta, i_cs, i_ce, ip_eta, ip_ce, ip_n;
-        interface_partials<TC>(P, lv, cs, ps, u[w], u[N + w], nf, g, s_i0, k_pl, i_eta, i_cs, i_ce, ip_eta, ip_ce,
-                               ip_n);
-        icoef[0 * NI + i] = float(i_eta);
-        icoef[1 * NI + i] = float(ip_eta);
-        icoef[2 * NI + i] = float(i_cs);
-        icoef[3 * NI + i] = float(i_ce);
-        icoef[4 * NI + i] = float(ip_ce);
-        icoef[5 * NI + i] = float(ip_n);
-        ++i;
+    TC nf = TC(0);
+    bool g = false;
+    if (i < D.F) {   // plating face
+        nf = u[2 * N + i];
+        g = gate[i] != 0;
     }
+    TC i_eta, i_cs, i_ce, ip_eta, ip_ce, ip_n;
+    interface_partials<TC>(P, lv, u[v], u[N + v], u[w], u[N + w], nf, g, s_i0, k_pl, i_eta, i_cs, i_ce, ip_eta,
+                           ip_ce, ip_n);
+    icoef[0 * NI + i] = float(i_eta);
+    icoef[1 * NI + i] = float(ip_eta);
+    icoef[2 * NI + i] = float(i_cs);
+    icoef[3 * NI + i] = float(i_ce);
+    icoef[4 * NI + i] = float(ip_ce);
+    icoef[5 * NI + i] = float(ip_n);
 }
 
 template <class TC>
 int launch_lin_setup(mb_cell* c, const TC* u, const uint8_t* gate, cudaStream_t s) {
     const Dims& D = c->D;
     if (D.NI == 0) return MB_OK;
-    k_lin_setup<TC><<<vox_grid(D, VOX_BLOCK), VOX_BLOCK, 0, s>>>(cell_par<TC>(c), D, c->vcode, u, gate, c->s_i0,
-                                                                 c->k_pl, c->icoef), ::mb::count_launch(c);
+    k_lin_setup<TC><<<(unsigned)((D.NI + 255) / 256), 256, 0, s>>>(cell_par<TC>(c), D, c->vcode, c->if_s, c->if_e, u,
+                                                                   gate, c->s_i0, c->k_pl, c->icoef), ::mb::count_launch(c);
     MB_CUDA_LAUNCH("lin_setup");
     return MB_OK;
 }

@@ -86,8 +86,10 @@ struct mb_cell {
 
     // geometry
     uint32_t* vcode = nullptr;     // N
-    int32_t* pf_g = nullptr;       // F
-    int32_t* pf_e = nullptr;       // F
+    int32_t* if_s = nullptr;       // NI: solid voxel of each interface face
+    int32_t* if_e = nullptr;       // NI: electrolyte voxel of each interface face
+    int32_t* pf_g = nullptr;       // F (= if_s: plating faces come first)
+    int32_t* pf_e = nullptr;       // F (= if_e)
     int8_t* pf_dir = nullptr;      // F
 
     // state and Newton work (FP64)
@@ -125,20 +127,25 @@ template <> inline const ParT<float>& cell_par<float>(const mb_cell* c) { return
 
 // count n launches; bracket timed launches with events when profiling is on
 inline void count_launch(mb_cell* c, int n = 1) { c->launches += n; }
+// While a graph is captured the events are always recorded (as graph nodes),
+// so that one graph serves with profiling on and off.
 inline void prof_begin(mb_cell* c, cudaStream_t s, cudaEvent_t* ev) {
     *ev = nullptr;
-    if (c->prof.enabled) {
-        if (c->prof.capture) cudaEventCreate(ev);
-        else *ev = c->prof.get();
+    if (c->prof.capture) {
+        // an external record node: the event is recorded each time the graph runs
+        cudaEventCreate(ev);
+        cudaEventRecordWithFlags(*ev, s, cudaEventRecordExternal);
+    } else if (c->prof.enabled) {
+        *ev = c->prof.get();
         cudaEventRecord(*ev, s);
     }
 }
 inline void prof_end(mb_cell* c, cudaStream_t s, int kind, cudaEvent_t ev0) {
-    if (c->prof.enabled && ev0) {
+    if ((c->prof.enabled || c->prof.capture) && ev0) {
         cudaEvent_t ev1 = nullptr;
         if (c->prof.capture) {
             cudaEventCreate(&ev1);
-            cudaEventRecord(ev1, s);
+            cudaEventRecordWithFlags(ev1, s, cudaEventRecordExternal);
             c->prof.capture->push_back({ev0, ev1, kind});
             return;
         }

@@ -6,7 +6,7 @@
 //    the sparsity of the face couplings.  The preconditioner solves
 //    S z_v = r_v - J_vn D_n^-1 r_n approximately and back-substitutes
 //    z_n = D_n^-1 (r_n - J_nv z_v).
-// 2. Fine level: NU_FINE damped 2x2 (c, phi) block-Jacobi sweeps of S before
+// 2. Fine level: nu_fine (mg_smooth) damped 2x2 (c, phi) block-Jacobi sweeps of S before
 //    and after the coarse correction; S z is applied as the matrix-free JVP
 //    of [z_v, -D_n^-1 J_nv z_v].  Several post-sweeps are needed: with a
 //    current source the correction carries a large, weakly pinned potential
@@ -43,7 +43,6 @@ constexpr int OFFW = 6 * BLK;             // 96 floats of outgoing couplings per
 constexpr float OMEGA_FINE = 0.8f;
 constexpr float OMEGA_COARSE = 0.7f;
 constexpr int NU = 2;                     // smoothing sweeps per coarse level (pre and post)
-constexpr int NU_FINE = 4;                // fine-level block-Jacobi sweeps (pre and post)
 constexpr int KCYC_MAX = 16;              // longest level-1 K-cycle (FGMRES iterations)
 constexpr int MAX_LEVELS = 16;
 constexpr int COARSE_MAX = 256;           // dense coarsest system size bound (4 x cells)
@@ -105,7 +104,7 @@ struct PcGraph {
     const float* r = nullptr;
     float2* z = nullptr;
     int kcyc = 0;
-    bool prof = false;
+    int nu = 0;
     cudaGraphExec_t exec = nullptr;
     int64_t nodes = 0;                 // kernels per execution
     std::vector<ProfPair> ev;          // timing events recorded by the graph (prof graphs)
@@ -126,6 +125,7 @@ struct Precond {
     double* cinv = nullptr;
     int* cstat = nullptr;
     int kcyc = 0;              // level-1 K-cycle length
+    int nu_fine = 0;           // fine-level block-Jacobi sweeps before and after the coarse correction
     // level-1 K-cycle workspace
     float* kV = nullptr;       // (KCYC_MAX+1) x m4  FP32 basis
     DF4* kZ = nullptr;         // KCYC_MAX x cells   preconditioned directions
@@ -924,6 +924,7 @@ void precond_destroy(mb_cell* c) {
 int precond_setup(mb_cell* c, const float* u32, const uint8_t* gate, double dt) {
     Precond* p = c->pc;
     p->kcyc = c->opt.mg_kcycle < 1 ? 1 : (c->opt.mg_kcycle > KCYC_MAX ? KCYC_MAX : c->opt.mg_kcycle);
+    p->nu_fine = c->opt.mg_smooth < 1 ? 1 : (c->opt.mg_smooth > 8 ? 8 : c->opt.mg_smooth);
     const Dims& D = c->D;
     cudaStream_t s = c->stream;
     k_bj_setup<<<pgrid(D.nt, D.ny, D.nz), PB, 0, s>>>(c->Pf, D, c->vcode, u32, gate, dt, c->s_i0, c->k_pl,
@@ -1063,7 +1064,7 @@ static int apply_body(mb_cell* c, const float* r, float2* z) {
                 dbg_norm(c, r, c->n), dbg_norm(c, c->rowdiag, c->n));
     const dim3 vg = pgrid(D.nt, D.ny, D.nz);
     const unsigned fg = nblk(D.F ? D.F : 1);
-    // condensed right-hand side, then NU_FINE damped block-Jacobi sweeps from zero
+    // condensed right-hand side, then nu_fine damped block-Jacobi sweeps from zero
     k_condense_rhs<<<vg, PB, 0, s>>>(D, c->vcode, p->fc, r, c->rowdiag, p->rv), ::mb::count_launch(c);
     k_bj_apply<<<nblk(D.N), 256, 0, s>>>(D, p->dinv, p->rv, nullptr, OMEGA_FINE, false, z), ::mb::count_launch(c);
     // t = S z_v  (S applied as the JVP of [z_v, -D_n^-1 J_nv z_v])
@@ -1072,7 +1073,7 @@ static int apply_body(mb_cell* c, const float* r, float2* z) {
         return launch_jvp_lin(c, z, p->t, s, 1);
     };
     int rc;
-    for (int k = 1; k < NU_FINE; ++k) {
+    for (int k = 1; k < p->nu_fine; ++k) {
         if ((rc = apply_S())) return rc;
         k_bj_apply<<<nblk(D.N), 256, 0, s>>>(D, p->dinv, p->rv, p->t, OMEGA_FINE, true, z), ::mb::count_launch(c);
     }
@@ -1090,8 +1091,8 @@ static int apply_body(mb_cell* c, const float* r, float2* z) {
                 dbg_norm(c, reinterpret_cast<const float2*>(L1.x), 4 * L1.cells), dbg_norm(c, p->kw, 4 * L1.cells));
     }
     k_prolong_fine<<<vg, PB, 0, s>>>(D, c->vcode, L1, L1.x, z), ::mb::count_launch(c);
-    // NU_FINE post-smoothing sweeps (they remove the jumps of the piecewise-constant prolongation)
-    for (int k = 0; k < NU_FINE; ++k) {
+    // nu_fine post-smoothing sweeps (they remove the jumps of the piecewise-constant prolongation)
+    for (int k = 0; k < p->nu_fine; ++k) {
         if ((rc = apply_S())) return rc;
         k_bj_apply<<<nblk(D.N), 256, 0, s>>>(D, p->dinv, p->rv, p->t, OMEGA_FINE, true, z), ::mb::count_launch(c);
     }
@@ -1108,14 +1109,16 @@ void precond_harvest(mb_cell* c) {
     PcGraph& G = p->graphs[p->pending];
     p->pending = -1;
     if (G.ev.empty()) return;
-    if (cudaEventSynchronize(G.ev.back().e1) != cudaSuccess) return;
-    for (auto& e : G.ev) {
+    bool ok = cudaEventSynchronize(G.ev.back().e1) == cudaSuccess;
+    for (size_t k = 0; ok && k < G.ev.size(); ++k) {
         float ms = 0.f;
-        if (cudaEventElapsedTime(&ms, e.e0, e.e1) == cudaSuccess) {
-            c->prof.acc_ms[e.kind] += ms;
-            c->prof.acc_n[e.kind] += 1;
+        if (cudaEventElapsedTime(&ms, G.ev[k].e0, G.ev[k].e1) == cudaSuccess) {
+            c->prof.acc_ms[G.ev[k].kind] += ms;
+            c->prof.acc_n[G.ev[k].kind] += 1;
         }
     }
+    // a failed timing query must not surface as the error of a later launch
+    cudaGetLastError();
 }
 
 // capture the application for (r, z) into a new graph; false if capture is not possible
@@ -1125,13 +1128,13 @@ static bool capture_graph(mb_cell* c, const float* r, float2* z, PcGraph& G) {
     G.r = r;
     G.z = z;
     G.kcyc = p->kcyc;
-    G.prof = c->prof.enabled;
+    G.nu = p->nu_fine;
     if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
     const int64_t saved = c->launches;
-    if (G.prof) c->prof.capture = &G.ev;
+    c->prof.capture = &G.ev;
     int rc = apply_body(c, r, z);
     c->prof.capture = nullptr;
     cudaGraph_t g = nullptr;
@@ -1164,7 +1167,7 @@ int precond_apply(mb_cell* c, const float* u32, const uint8_t* gate, double dt, 
     int idx = -1;
     for (size_t i = 0; i < p->graphs.size(); ++i) {
         const PcGraph& G = p->graphs[i];
-        if (G.r == r && G.z == z && G.kcyc == p->kcyc && G.prof == c->prof.enabled) { idx = (int)i; break; }
+        if (G.r == r && G.z == z && G.kcyc == p->kcyc && G.nu == p->nu_fine) { idx = (int)i; break; }
     }
     if (idx < 0) {
         PcGraph G;
@@ -1180,7 +1183,7 @@ int precond_apply(mb_cell* c, const float* u32, const uint8_t* gate, double dt, 
     MB_CUDA(cudaGraphLaunch(G.exec, s));
     prof_end(c, s, PROF_PRECOND, ev_pc);
     count_launch(c, (int)G.nodes);
-    if (!G.ev.empty()) p->pending = idx;
+    if (c->prof.enabled && !G.ev.empty()) p->pending = idx;
     return MB_OK;
 }
 

@@ -150,10 +150,13 @@ def test_precond_stages_match_reference(params):
             Aref = (Pu.T @ Aref @ Pu).tocsr()
 
 
+KCYCLE = 6   # level-1 K-cycle length used by the emulation test
+
+
 class _Emulation:
     """FP64 emulation of the preconditioner's algorithm on the reference
     operators: condensation, 4 damped 2x2 block-Jacobi sweeps (omega 0.8)
-    before and after a level-1 correction; level 1 solved by FGMRES(6) whose
+    before and after a level-1 correction; level 1 solved by FGMRES(KCYCLE) whose
     preconditioner is a V-cycle with 2 damped (0.7) 4x4 block-Jacobi sweeps
     before and after each coarse correction; exact coarsest level."""
 
@@ -214,7 +217,7 @@ class _Emulation:
         if self.L == 1:
             return self.vcycle(1, b)
         A = self.A[1]
-        k = 16  # FGMRES length of the kernel's level-1 K-cycle (KCYC in precond.cu)
+        k = KCYCLE  # FGMRES length of the level-1 K-cycle, as set in the cell's options
         beta = np.linalg.norm(b)
         V = [b / beta]; Z = []; H = np.zeros((k + 1, k))
         for j in range(k):
@@ -243,7 +246,7 @@ def test_precond_matches_emulation(params):
     B = _gpu()
     lab, oc, u, u_old, gate = _case(params)
     dt = 1.0
-    gc = B.Cell(lab, 1e-6, params)
+    gc = B.Cell(lab, 1e-6, params, B.default_opts(mg_kcycle=KCYCLE, mg_smooth=4))
     A, S, Ann = _reference(oc, u, u_old, gate, dt)
     gc.debug_precond(u, gate, dt, np.ones(gc.n))
     rowdiag = gc.debug_fine()[2].astype(np.float64)
