@@ -292,6 +292,7 @@ def main():
                "scaling": "weak", "vs_baseline": None,
                "dtype": "f32+f64" if prec == B.PREC_MIXED else "f64", "data": "synthetic",
                "config": {"workload": args.workload, "voxels": int(cell.N), "plating_faces": int(cell.F),
+                          "device_bytes": int(cell.device_bytes),
                           "dt_s": dt, "crate": CRATE[args.workload], "precision": args.precision,
                           "l2": "working set > 129 MB L2, no flush", "parallelism": "replicas" if ws > 1 else "1 GPU"},
                "clocks": clk, "e2e": e2e, "gpu_launches": int(launches), "roofline": roof,

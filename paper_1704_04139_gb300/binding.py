@@ -170,6 +170,7 @@ class Cell:
         self.N = info.n_vox
         self.F = info.n_faces
         self.NI = info.n_iface
+        self.device_bytes = info.device_bytes
         self.n = info.n_unknowns
         self.i_1c = info.i_1c
 
