@@ -50,8 +50,8 @@ Face fluxes from voxel a to its neighbour b (Delta = (.)_b - (.)_a, A = h^2):
 Clamps: c is replaced by max(c, clamp_rel * c_ref) inside sqrt and 1/cbar.
 
 Gate g_f (plating active set, the build's reading of "plating occurs when the
-overpotential is negative", Sec. 2.3): g_f = 1 if n_old,f > 0 or eta_p < 0 at
-the state where the gate is taken, else 0.  The gate is frozen during one
+overpotential is negative", Sec. 2.3): g_f = 1 if n_old,f > 1e-9 n_c or
+eta_p < 0 at the state where the gate is taken, else 0.  The gate is frozen during one
 Newton solve; after convergence it is re-taken at the converged state and
 the step is re-solved from u_old if any face flipped (at most 3 passes).
 
@@ -70,6 +70,7 @@ from synthetic.geometry import E, G, K, L, CN, CP
 DIRS = ((0, -1), (0, 1), (1, -1), (1, 1), (2, -1), (2, 1))
 _CONDUCTORS = (G, K, L, CN, CP)
 DELTA_MAX = 0.25
+N_GATE_REL = 1e-9
 _FORBIDDEN = {(G, K), (G, CP), (K, CN), (CN, CP), (K, L)}
 
 
@@ -335,10 +336,13 @@ class Cell:
         return np.concatenate([rc, np.full(self.N, self.A * 1.0), np.full(self.F_pl, self.nc / dt)])
 
     def gate_at(self, u, n_old):
-        """Active set: g = 1 where n_old > 0 or eta_p = Phi_G - phi_E < 0."""
+        """Active set: g = 1 where plated Li is present (n_old > N_GATE_REL n_c)
+        or eta_p = Phi_G - phi_E < 0.  An inventory below 1e-9 of the
+        critical layer counts as none (f_pre ~ 1e-36 there): the rule must
+        not switch on rounding noise of a reconstructed state."""
         c, phi, n = self.split(u)
         etap = phi[self.pf_g] - phi[self.pf_e]
-        return ((n_old > 0) | (etap < 0)).astype(np.float64)
+        return ((n_old > N_GATE_REL * self.nc) | (etap < 0)).astype(np.float64)
 
     # --------------------------------------------------------------- Jacobian
     def _pattern(self):
@@ -413,13 +417,15 @@ class Cell:
                        options=dict(SymmetricMode=True))
         return us * lu.solve(b / dr)
 
-    def newton(self, u0, u_old, dt, I_app, gate, s_i0=1.0, k_pl=1.0, tol=1e-12, maxit=40):
+    def newton(self, u0, u_old, dt, I_app, gate, s_i0=1.0, k_pl=1.0, tol=1e-12, maxit=40, record=None):
         """Newton's method with sparse direct LU (SciPy SuperLU) for the linear
         correction equations (the paper's BEST solver used AMG there, Sec. 2.4).
 
         Step length: lam = min(1, DELTA_MAX / ||delta||_s) where ||.||_s is the
         max-norm scaled by the unknown scales (c_ref, 1 V, n_c); DELTA_MAX = 0.25.
-        Stops after the first applied update with lam * ||delta||_s <= tol."""
+        Stops after the first applied update with lam * ||delta||_s <= tol.
+        With a list `record`, every iterate (after each update) is appended
+        together with the gate it was computed with."""
         u = u0.copy()
         us = self.unknown_scale()
         for it in range(1, maxit + 1):
@@ -431,19 +437,22 @@ class Cell:
                 return u, it, False
             lam = 1.0 if dn <= DELTA_MAX else DELTA_MAX / dn
             u = u + lam * d
+            if record is not None:
+                record.append((u.copy(), np.array(gate, dtype=np.float64)))
             if lam * dn <= tol:
                 return u, it, True
         return u, maxit, False
 
-    def step(self, u_old, dt, I_app, s_i0=1.0, k_pl=1.0, tol=1e-12, max_passes=3):
+    def step(self, u_old, dt, I_app, s_i0=1.0, k_pl=1.0, tol=1e-12, max_passes=3, record=None):
         """One implicit Euler step of Eq. (ap4:detailed) with the plating
-        active-set passes.  Returns (u_new, info dict)."""
+        active-set passes.  Returns (u_new, info dict).  `record` collects
+        the Newton stages (see newton)."""
         n_old = self.split(u_old)[2]
         gate = self.gate_at(u_old, n_old)
         its = 0
         flips = 0
         for npass in range(1, max_passes + 1):
-            u, it, ok = self.newton(u_old, u_old, dt, I_app, gate, s_i0, k_pl, tol)
+            u, it, ok = self.newton(u_old, u_old, dt, I_app, gate, s_i0, k_pl, tol, record=record)
             its += it
             if not ok:
                 raise RuntimeError("oracle Newton did not converge")

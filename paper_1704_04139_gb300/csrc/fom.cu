@@ -750,19 +750,22 @@ int launch_jvp_lin(mb_cell* c, const float2* v, float* jv, cudaStream_t s, int m
 }
 
 // ------------------------------------------------------------ plating gates
+// g_f = 1 where plated Li is present (n_old > 1e-9 n_c: smaller inventories
+// count as none, f_pre ~ 1e-36 there) or the plating overpotential
+// Phi_G - phi_E is negative (Sec. workflow:degradation_modeling).
 __global__ void k_gate(Dims D, const int32_t* __restrict__ pg, const int32_t* __restrict__ pe,
-                       const double* __restrict__ u, const double* __restrict__ n_old,
+                       const double* __restrict__ u, const double* __restrict__ n_old, double n_gate,
                        uint8_t* __restrict__ gate) {
     int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (f >= D.F) return;
     const double* ph = u + D.N;
     double etap = ph[pg[f]] - ph[pe[f]];
-    gate[f] = (n_old[f] > 0.0 || etap < 0.0) ? 1 : 0;
+    gate[f] = (n_old[f] > n_gate || etap < 0.0) ? 1 : 0;
 }
 
 int launch_gate(mb_cell* c, const double* u, const double* n_old, uint8_t* gate, cudaStream_t s) {
     if (c->D.F == 0) return MB_OK;
-    k_gate<<<(unsigned)((c->D.F + 255) / 256), 256, 0, s>>>(c->D, c->pf_g, c->pf_e, u, n_old, gate), ::mb::count_launch(c);
+    k_gate<<<(unsigned)((c->D.F + 255) / 256), 256, 0, s>>>(c->D, c->pf_g, c->pf_e, u, n_old, GATE_N_REL * c->P.nc, gate), ::mb::count_launch(c);
     MB_CUDA_LAUNCH("gate");
     return MB_OK;
 }
@@ -772,7 +775,7 @@ int launch_gate_residual_unprofiled(mb_cell* c, const double* u, const double* u
     const Dims& D = c->D;
     if (D.F > 0) {
         k_gate<<<(unsigned)((D.F + 255) / 256), 256, 0, s>>>(D, c->pf_g, c->pf_e, u_old, u_old + 2 * D.N,
-                                                             gate_scratch), ::mb::count_launch(c);
+                                                             GATE_N_REL * c->P.nc, gate_scratch), ::mb::count_launch(c);
         MB_CUDA_LAUNCH("gate");
     }
     k_residual<double><<<vox_grid(D, VOX_BLOCK), VOX_BLOCK, 0, s>>>(c->P, D, c->vcode, u, u_old, gate_scratch,

@@ -63,6 +63,10 @@ struct Prof {
 // d i_bv/d c_s, d i_bv/d c_e, d i_pl/d c_e, d i_pl/d n (A/m^2 per unit).
 constexpr int NCOEF = 6;
 
+// plated-Li inventory (relative to the critical layer n_c) below which the
+// plating gate treats a face as bare
+constexpr double GATE_N_REL = 1e-9;
+
 // Reduction scratch (deterministic two-pass reductions).
 constexpr int RED_BLOCKS = 1216;      // 8 x 152 SMs
 constexpr int RED_THREADS = 256;

@@ -1,0 +1,116 @@
+"""Pins of the reduced-order model oracle (CPU): each checks it against
+something other than itself (the full-order oracle's residual and
+trajectories, the interpolation property, the rest state)."""
+import numpy as np
+import pytest
+
+import synthetic as syn
+from oracle.fom import Cell
+from oracle import rom as R
+
+
+@pytest.fixture(scope="module")
+def tiny(params):
+    lab = syn.full_cell(4, 4, 5, 3, 5, 0.35, 0.35, ("uniform", 1, 2), (1, 2))
+    return Cell(lab, 1e-6, params)
+
+
+def _state(cell, seed):
+    rng = np.random.default_rng(seed)
+    u = cell.initial_state()
+    N = cell.N
+    u[:N] *= 1.0 + 0.02 * rng.standard_normal(N)
+    u[N:2 * N] += 0.004 * rng.standard_normal(N)
+    u[2 * N:] = 3e-5 * (rng.random(cell.F_pl) < 0.5)
+    gate = (rng.random(cell.F_pl) < 0.6).astype(float)
+    return u, gate
+
+
+def test_split_reproduces_full_order_residual(tiny):
+    """storage + A_lin + mu A_bnd + A_1c + s A_bv + A_ce + k A_pl = R (Eqs.
+    ap4:operator_decomposition and ap4:operator_subdecomposition)."""
+    cell = tiny
+    for seed in range(3):
+        u, gate = _state(cell, seed)
+        u_old, _ = _state(cell, seed + 10)
+        dt, mu, s, k = 0.7, -2.0 * cell.i_1c, 1.3, 0.4
+        r_full = cell.residual(u, u_old, dt, mu, gate, s, k)
+        r_split = R.full_residual_from_split(cell, u, u_old, dt, mu, gate, s, k)
+        scale = np.abs(cell.jacobian(u, u_old, dt, mu, gate, s, k)) @ np.abs(u) + np.abs(r_full)
+        assert np.all(np.abs(r_split - r_full) <= 64 * np.finfo(float).eps * scale + 1e-300)
+
+
+def test_boundary_term_is_the_current_derivative(tiny):
+    """A_bnd equals dR/dmu of the full-order residual (finite difference in mu
+    of an affine function is exact up to rounding)."""
+    cell = tiny
+    u, gate = _state(cell, 4)
+    r1 = cell.residual(u, u, 1.0, 5.0, gate)
+    r0 = cell.residual(u, u, 1.0, 0.0, gate)
+    bnd = R.suboperators(cell, u, gate)["bnd"]
+    tol = 16 * np.finfo(float).eps * (np.abs(r1) + np.abs(r0)) / 5.0
+    assert np.all(np.abs((r1 - r0) / 5.0 - bnd) <= tol + 1e-15 * np.max(np.abs(bnd)))
+    assert np.count_nonzero(bnd) == len(cell.bc_neu) > 0
+
+
+@pytest.fixture(scope="module")
+def trained(tiny):
+    cell = tiny
+    mu = -4.0 * cell.i_1c
+    u0 = cell.initial_state()
+    u0[2 * cell.N::4] = 2e-5          # seeded plated Li on every fourth face
+    snaps, trajs = R.snapshots(cell, [(mu, 1.0, 1.0)], 1.0, 4, u0=u0)
+    rom = R.build(cell, snaps, (10 ** 6, 10 ** 6, 10 ** 6, 10 ** 6), pod_tol=1e-15, ei_tol=1e-14)
+    return cell, mu, snaps, trajs[0], rom
+
+
+def test_ei_interpolation_identity(trained):
+    """I_M[O](x) agrees with O(x) at the interpolation points (Sec.
+    workflow:MOR) for states outside the training set."""
+    cell, mu, snaps, traj, rom = trained
+    for seed in range(2):
+        u, gate = _state(cell, 20 + seed)
+        so = R.suboperators(cell, u, gate)
+        for key, (Q, P) in (("bv", (rom.Qbv, rom.Pbv)), ("pl", (rom.Qbv, rom.Pbv)),
+                            ("c1", (rom.Q1c, rom.P1c))):
+            if len(P) == 0:
+                continue
+            vals = so[key][P]
+            interp = R.ei_interpolate(Q, P, vals)
+            assert np.allclose(interp[P], vals, rtol=1e-9, atol=1e-12 * np.max(np.abs(so[key])))
+
+
+def test_full_basis_rom_reproduces_the_training_trajectory(trained):
+    """With bases spanning every snapshot and EI spaces spanning every training
+    evaluation, the full-order states solve the fully reduced model (Eq.
+    ap4:fully_reduced): the reduced trajectory is the full-order one."""
+    cell, mu, snaps, traj, rom = trained
+    # start the reduced model from the seeded state the full-order run started from
+    rom.a0 = rom.U.T @ (R.weights(cell) * traj[0])
+    out = R.solve(rom, mu, 1.0, 1.0, 1.0, len(traj) - 1)
+    for n in range(len(traj)):
+        fom = cell.functionals(traj[n])
+        assert abs(out["V_cell"][n] - fom["V_cell"]) <= 1e-9 * abs(fom["V_cell"]), n
+        assert abs(out["s_ac"][n] - fom["mean_c_solid"]) <= 1e-9 * abs(fom["mean_c_solid"]), n
+        u_rom = rom.U @ out["a"][n]
+        for sl, tol in ((slice(0, cell.N), 1e-9), (slice(cell.N, 2 * cell.N), 1e-9),
+                        (slice(2 * cell.N, None), 1e-9)):
+            ref = traj[n][sl]
+            assert np.max(np.abs(u_rom[sl] - ref)) <= tol * np.max(np.abs(traj[:, sl])), n
+
+
+def test_rest_state_is_stationary(tiny):
+    """At zero current from the rest state the reduced model stays at rest."""
+    cell = tiny
+    snaps, trajs = R.snapshots(cell, [(-3.0 * cell.i_1c, 1.0, 1.0)], 1.0, 2)
+    rom = R.build(cell, snaps, (10 ** 6, 10 ** 6, 10 ** 6, 10 ** 6), pod_tol=1e-15, ei_tol=1e-14)
+    out = R.solve(rom, 0.0, 1.0, 1.0, 1.0, 3)
+    assert np.max(np.abs(out["V_cell"] - out["V_cell"][0])) <= 1e-12 * abs(out["V_cell"][0])
+    assert np.max(np.abs(out["a"] - out["a"][0])) <= 1e-10 * np.max(np.abs(out["a"][0]))
+
+
+def test_pod_bases_are_w_orthonormal(trained):
+    cell, mu, snaps, traj, rom = trained
+    w = R.weights(cell)
+    G = rom.U.T @ (w[:, None] * rom.U)
+    assert np.allclose(G, np.eye(G.shape[0]), atol=1e-10)
