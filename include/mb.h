@@ -171,6 +171,66 @@ int mb_launch_count(mb_cell* cell, int64_t* count);
  * host-pointer calls of this cell enqueue their work. */
 int mb_cell_stream(mb_cell* cell, void** stream);
 
+/* ---- reduced-order model (Sec. workflow:MOR, Eq. ap4:fully_reduced) ----
+ * The reduced model of a cell: reduced basis U (the POD spaces of c, n and phi
+ * in the full state layout), the empirical-interpolation points of the
+ * interface terms (Butler-Volmer, counter electrode, plating: one common
+ * basis, Eqs. ise_gr, ise_li, iplel) and of the migration term with 1/c (Eq.
+ * phiel), and the projected operators.  Residual of instance b at reduced
+ * coefficients a (N_r):
+ *   Ms (a - a_old)/dt + Alin a + mu bbnd + Pbv f_bv(a) + P1c f_1c(a)
+ * f_bv(a)[m] = s_i0 (BV rows) + (CE rows) + k_pl g (plating rows) of the
+ * full-order interface terms at point p_bv[m] of the reconstructed state U a,
+ * f_1c(a)[m] the migration term at p_1c[m]; the plating gate g follows the
+ * full-order rule on the reconstructed state.  Points index residual rows of
+ * the layout [R_c | R_phi | R_n]; the face rows are weighted by A.  All arrays
+ * are host, row-major, FP64, copied by mb_rom_create. */
+typedef struct {
+    int n_r;                 /* reduced dimension N_r */
+    int n_bv, n_1c;          /* interpolation points of the interface and migration terms */
+    const double* U;         /* n x n_r: basis in the full state layout (n = 2N + F) */
+    const int64_t* p_bv;     /* n_bv residual rows */
+    const int64_t* p_1c;     /* n_1c residual rows */
+    const double* Ms;        /* n_r x n_r projected storage */
+    const double* Alin;      /* n_r x n_r projected linear part */
+    const double* bbnd;      /* n_r projected boundary term (per unit I_app) */
+    const double* Pbv;       /* n_r x n_bv projected interpolation basis of the interface terms */
+    const double* P1c;       /* n_r x n_1c projected interpolation basis of the migration term */
+    const double* s_cp;      /* n_r: cell potential functional (mean phi of the last t-layer) */
+    const double* s_ac;      /* n_r: mean graphite concentration functional */
+    const double* a0;        /* n_r: initial coefficients */
+} mb_rom_data;
+
+typedef struct {
+    double I_app;            /* applied current density (A/m^2), the paper's mu */
+    double s_i0;             /* exchange-current scale */
+    double k_pl;             /* plating rate scale */
+} mb_rom_params;
+
+typedef struct {
+    int64_t newton_its;      /* reduced Newton iterations summed over instances and steps */
+    int64_t flips;           /* plating gate flips summed over instances and steps */
+    int     failed;          /* instances whose Newton iteration did not converge */
+} mb_rom_info;
+
+typedef struct mb_rom mb_rom;
+
+/* Build the reduced model of `cell` from the arrays of d (MB_EINVAL on
+ * inconsistent sizes or points outside the residual). */
+int mb_rom_create(mb_cell* cell, const mb_rom_data* d, mb_rom** out);
+int mb_rom_destroy(mb_rom* rom);
+/* Reduced trajectories of B instances from a0 with the instance parameters
+ * prm[B]: n_steps implicit Euler steps of size dt.  V_out and sac_out
+ * (host double[B * (n_steps + 1)], instance-major, entry 0 the initial
+ * state) receive s_cp and s_ac; a_final (host double[B * n_r]) the final
+ * coefficients (may be NULL).  Newton per step and instance: step length
+ * min(1, 0.25 / |U_loc delta|_s) on the stencil closure of the points,
+ * converged at lam |U_loc delta|_s <= 1e-12, at most 30 iterations;
+ * plating active-set passes as mb_step (at most 3).  Returns MB_ENOCONV if
+ * some instance failed (its outputs are then NaN from that step on). */
+int mb_rom_solve_batch(mb_rom* rom, int B, const mb_rom_params* prm, int n_steps, double dt, double* V_out,
+                       double* sac_out, double* a_final, mb_rom_info* info);
+
 /* ---- residual without allocation (no counterpart in the paper) ----
  * Same result as mb_residual_dev with gate == NULL (gates taken at u_old),
  * for callers that may not allocate memory at call time: a serving loop whose

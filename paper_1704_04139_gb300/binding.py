@@ -65,6 +65,20 @@ P_i32 = C.POINTER(C.c_int32)
 VP = C.c_void_p
 
 
+class RomData(C.Structure):
+    _fields_ = [("n_r", C.c_int), ("n_bv", C.c_int), ("n_1c", C.c_int), ("U", VP), ("p_bv", VP), ("p_1c", VP),
+                ("Ms", VP), ("Alin", VP), ("bbnd", VP), ("Pbv", VP), ("P1c", VP), ("s_cp", VP), ("s_ac", VP),
+                ("a0", VP)]
+
+
+class RomParams(C.Structure):
+    _fields_ = [("I_app", C.c_double), ("s_i0", C.c_double), ("k_pl", C.c_double)]
+
+
+class RomInfo(C.Structure):
+    _fields_ = [("newton_its", C.c_int64), ("flips", C.c_int64), ("failed", C.c_int)]
+
+
 def _declare(lib):
     def fn(name, res, args):
         f = getattr(lib, name)
@@ -85,6 +99,10 @@ def _declare(lib):
     fn("mb_residual", C.c_int, [VP, VP, VP, VP, C.c_double, C.c_double, VP])
     fn("mb_residual_dev", C.c_int, [VP, VP, VP, VP, C.c_double, C.c_double, VP, VP])
     fn("mb_residual_dev_noalloc", C.c_int, [VP, VP, VP, C.c_double, C.c_double, VP, VP])
+    fn("mb_rom_create", C.c_int, [VP, C.POINTER(RomData), C.POINTER(VP)])
+    fn("mb_rom_destroy", C.c_int, [VP])
+    fn("mb_rom_solve_batch", C.c_int, [VP, C.c_int, C.POINTER(RomParams), C.c_int, C.c_double, VP, VP, VP,
+                                        C.POINTER(RomInfo)])
     fn("mb_jvp", C.c_int, [VP, VP, VP, C.c_double, VP, VP])
     fn("mb_jvp_dev", C.c_int, [VP, VP, VP, C.c_double, VP, VP, VP])
     fn("mb_jvp_f32_dev", C.c_int, [VP, VP, VP, C.c_double, VP, VP, VP])
@@ -304,3 +322,51 @@ class Cell:
     def jvp_f32_dev(self, u, v, dt, out, gate):
         _check(lib().mb_jvp_f32_dev(self.h, VP(u.data_ptr()), VP(gate.data_ptr()), float(dt),
                                     VP(v.data_ptr()), VP(out.data_ptr()), _stream_of(u)))
+
+
+class Rom:
+    """Reduced model of a cell (mb_rom_create): arrays in the layout of
+    include/mb.h (row-major FP64; points as residual-row indices)."""
+
+    def __init__(self, cell, U, p_bv, p_1c, Ms, Alin, bbnd, Pbv, P1c, s_cp, s_ac, a0):
+        f64 = lambda a: np.ascontiguousarray(a, np.float64)
+        i64 = lambda a: np.ascontiguousarray(a, np.int64)
+        self._keep = [f64(U), i64(p_bv), i64(p_1c), f64(Ms), f64(Alin), f64(bbnd), f64(Pbv), f64(P1c),
+                      f64(s_cp), f64(s_ac), f64(a0)]
+        U_, pb, pc, Ms_, Al, bb, Pb, Pc, sc, sa, a0_ = self._keep
+        self.n_r = U_.shape[1]
+        d = RomData(self.n_r, len(pb), len(pc), _ptr(U_), _ptr(pb), _ptr(pc), _ptr(Ms_), _ptr(Al), _ptr(bb),
+                    _ptr(Pb), _ptr(Pc), _ptr(sc), _ptr(sa), _ptr(a0_))
+        h = VP()
+        _check(lib().mb_rom_create(cell.h, C.byref(d), C.byref(h)))
+        self.h = h
+        self.cell = cell
+
+    def solve(self, params, n_steps, dt):
+        """params: sequence of (I_app, s_i0, k_pl).  Returns dict V (B, n_steps+1),
+        s_ac, a (B, n_r) and the Newton/flip/failure counts."""
+        B = len(params)
+        prm = (RomParams * B)(*[RomParams(*map(float, p)) for p in params])
+        V = np.empty((B, n_steps + 1))
+        S = np.empty((B, n_steps + 1))
+        A = np.empty((B, self.n_r))
+        info = RomInfo()
+        rc = lib().mb_rom_solve_batch(self.h, B, prm, int(n_steps), float(dt), _ptr(V), _ptr(S), _ptr(A),
+                                      C.byref(info))
+        out = dict(V=V, s_ac=S, a=A, newton_its=int(info.newton_its), flips=int(info.flips),
+                   failed=int(info.failed))
+        if rc != 0 and rc != -4:
+            _check(rc)
+        out["ok"] = rc == 0
+        return out
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().mb_rom_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,844 @@
+// rom.cu -- online solve of the reduced model (Sec. workflow:MOR, Eq.
+// ap4:fully_reduced) for a batch of parameter instances.
+//
+// The reduced residual of an instance at coefficients a is
+//   Ms (a - a_old)/dt + Alin a + mu bbnd + Pbv f_bv(a) + P1c f_1c(a),
+// where f_bv, f_1c are the interface and migration terms of the full-order
+// residual at the empirical-interpolation points, evaluated on the
+// reconstruction u_loc = U_loc a over the stencil closure of the points (the
+// voxels and faces those rows depend on).  Each point is described on the
+// host by a short "term program": the faces that feed its row (interface
+// faces with their row weights for the Butler-Volmer / counter-electrode and
+// the plating current, electrolyte faces for the migration term) with the
+// closure slots of their unknowns.  Per Newton iteration and instance:
+//   gather u_loc = U_loc a; evaluate f and its sparse derivative rows G;
+//   GU = G U_loc; J = Ms/dt + Alin + P GU; r as above; solve J delta = -r by
+//   LU with partial pivoting after row/column equilibration; step length
+//   min(1, 0.25 / |U_loc delta|_s), converged at lam |U_loc delta|_s <= 1e-12.
+// Plating gates: the full-order rule on the reconstruction, with the
+// active-set passes of the full-order step.  All arithmetic FP64.
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include <algorithm>
+#include <map>
+#include <vector>
+
+#include "mb_internal.h"
+
+namespace mb {
+
+constexpr int TMAX = 6;          // face terms per interpolation point
+constexpr int GMAX = 32;         // closure slots one point depends on
+constexpr int ROM_NR_MAX = 512;  // largest reduced dimension
+constexpr int ROM_MAXIT = 30;
+constexpr int ROM_PASSES = 3;
+constexpr double ROM_DELTA_MAX = 0.25;
+constexpr double ROM_TOL = 1e-12;
+
+enum RomTerm : int8_t { T_NONE = 0, T_GE = 1, T_KE = 2, T_LE = 3, T_EE = 4 };
+
+struct RomDev {
+    int Nr = 0, Mbv = 0, M1c = 0, M = 0, nloc = 0, ngate = 0;
+    double* UlocC = nullptr;   // Nr x nloc (column j contiguous)
+    double* UlocR = nullptr;   // nloc x Nr
+    double* us = nullptr;      // nloc unknown scales
+    int8_t* ttype = nullptr;   // M x TMAX
+    int32_t* tidx = nullptr;   // M x TMAX x 5 closure slots (c_s, phi_s, c_e, phi_e, n), -1 unused
+    double* twbv = nullptr;    // M x TMAX row weight of the BV / CE current (or of the migration flux)
+    double* twpl = nullptr;    // M x TMAX row weight of the plating current
+    int32_t* tgate = nullptr;  // M x TMAX gate slot, -1 none
+    int8_t* tgpos = nullptr;   // M x TMAX x 5 position in the point's derivative list
+    int32_t* gidx = nullptr;   // M x GMAX closure slots of the derivative list, -1 unused
+    int32_t* gface = nullptr;  // ngate x 3 closure slots (phi_g, phi_e, n) of the gated faces
+    double* P = nullptr;       // Nr x M (Pbv | P1c)
+    double* Ms = nullptr;      // Nr x Nr
+    double* Alin = nullptr;    // Nr x Nr
+    double* bbnd = nullptr;    // Nr
+    double* scp = nullptr;     // Nr
+    double* sac = nullptr;     // Nr
+    double* a0 = nullptr;      // Nr
+};
+
+struct RomWork {
+    int B = 0;
+    double *a = nullptr, *a_old = nullptr, *delta = nullptr, *r = nullptr, *J = nullptr;
+    double *uloc = nullptr, *uloc_old = nullptr, *f = nullptr, *G = nullptr, *GU = nullptr;
+    double* prm = nullptr;
+    uint8_t *gate = nullptr, *gate2 = nullptr;
+    int *active = nullptr, *failed = nullptr, *pass_on = nullptr, *counts = nullptr;
+    long long* its = nullptr;
+    long long* flips = nullptr;
+    double *V = nullptr, *S = nullptr;
+    std::vector<void*> bufs;
+};
+
+}  // namespace mb
+
+struct mb_rom {
+    mb_cell* cell = nullptr;
+    mb::RomDev d;
+    std::vector<void*> owned;
+    mb::RomWork w;
+};
+
+namespace mb {
+
+static void rom_work_free(RomWork& w) {
+    for (void* p : w.bufs) cudaFree(p);
+    w = RomWork();
+}
+
+template <class T>
+static T* rom_alloc(std::vector<void*>& list, size_t n) {
+    void* p = nullptr;
+    if (cudaMalloc(&p, sizeof(T) * (n ? n : 1)) != cudaSuccess) return nullptr;
+    list.push_back(p);
+    return static_cast<T*>(p);
+}
+
+// ------------------------------------------------------------------ kernels
+// u_loc[b] = U_loc a[b]
+__global__ void k_rom_gather(RomDev d, const double* __restrict__ a, double* __restrict__ uloc) {
+    __shared__ double sa[ROM_NR_MAX];
+    const int b = blockIdx.y;
+    for (int j = threadIdx.x; j < d.Nr; j += blockDim.x) sa[j] = a[(int64_t)b * d.Nr + j];
+    __syncthreads();
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= d.nloc) return;
+    double acc = 0.0;
+    for (int j = 0; j < d.Nr; ++j) acc += d.UlocC[(int64_t)j * d.nloc + k] * sa[j];
+    uloc[(int64_t)b * d.nloc + k] = acc;
+}
+
+// gate of the gated faces: plated Li present or negative plating overpotential
+__global__ void k_rom_gate(RomDev d, int B, const double* __restrict__ uloc, const double* __restrict__ uloc_old,
+                           double n_thr, uint8_t* __restrict__ gate) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (int64_t)d.ngate * B) return;
+    const int b = (int)(i / d.ngate), g = (int)(i % d.ngate);
+    const double* u = uloc + (int64_t)b * d.nloc;
+    const double* uo = uloc_old + (int64_t)b * d.nloc;
+    const int32_t* s = d.gface + 3 * g;
+    const double etap = u[s[0]] - u[s[1]];
+    gate[i] = (uo[s[2]] > n_thr || etap < 0.0) ? 1 : 0;
+}
+
+// f and its derivative list at every point
+__global__ void k_rom_ei(RomDev d, DevParams P, int B, const double* __restrict__ uloc,
+                         const uint8_t* __restrict__ gate, const double* __restrict__ prm,
+                         const int* __restrict__ active, double* __restrict__ f, double* __restrict__ G) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (int64_t)d.M * B) return;
+    const int b = (int)(i / d.M), p = (int)(i % d.M);
+    if (!active[b]) return;
+    const double* u = uloc + (int64_t)b * d.nloc;
+    const double s_i0 = prm[3 * b + 1], k_pl = prm[3 * b + 2];
+    double g[GMAX];
+#pragma unroll
+    for (int e = 0; e < GMAX; ++e) g[e] = 0.0;
+    double fv = 0.0;
+    for (int t = 0; t < TMAX; ++t) {
+        const int q = p * TMAX + t;
+        const int type = d.ttype[q];
+        if (type == T_NONE) break;
+        const int32_t* sl = d.tidx + 5 * q;
+        const int8_t* gp = d.tgpos + 5 * q;
+        if (type == T_EE) {
+            // A j_m = -E_gm (c_w - c_v) / S, S = max(c_v, cmin) + max(c_w, cmin)
+            const double cv = u[sl[0]], cw = u[sl[2]], cmin = P.cmin[PE];
+            const double S = fmax(cv, cmin) + fmax(cw, cmin);
+            const double dc = cw - cv, gm = P.E_gm;
+            const double w = d.twbv[q];
+            fv += w * (-gm * dc / S);
+            g[gp[0]] += w * (gm / S + (cv >= cmin ? gm * dc / (S * S) : 0.0));
+            g[gp[2]] += w * (-gm / S + (cw >= cmin ? gm * dc / (S * S) : 0.0));
+        } else {
+            const int ls = type == T_GE ? PG : (type == T_KE ? PK : PL);
+            const double cs = sl[0] >= 0 ? u[sl[0]] : 0.0, ps = u[sl[1]];
+            const double ce = sl[2] >= 0 ? u[sl[2]] : 0.0, pe = u[sl[3]];
+            const double nf = sl[4] >= 0 ? u[sl[4]] : 0.0;
+            const bool gt = d.tgate[q] >= 0 && gate[(int64_t)b * d.ngate + d.tgate[q]] != 0;
+            double ibv, ipl, i_eta, i_cs, i_ce, ip_eta, ip_ce, ip_n;
+            interface_current<double>(P, ls, cs, ps, ce, pe, nf, gt, s_i0, k_pl, ibv, ipl);
+            interface_partials<double>(P, ls, cs, ps, ce, pe, nf, gt, s_i0, k_pl, i_eta, i_cs, i_ce, ip_eta, ip_ce,
+                                       ip_n);
+            const double wb = d.twbv[q], wp = d.twpl[q];
+            fv += wb * ibv + wp * ipl;
+            if (sl[0] >= 0) g[gp[0]] += wb * i_cs;
+            g[gp[1]] += wb * i_eta + wp * ip_eta;
+            if (sl[2] >= 0) g[gp[2]] += wb * i_ce + wp * ip_ce;
+            g[gp[3]] += -(wb * i_eta + wp * ip_eta);
+            if (sl[4] >= 0) g[gp[4]] += wp * ip_n;
+        }
+    }
+    f[(int64_t)b * d.M + p] = fv;
+    double* Gp = G + ((int64_t)b * d.M + p) * GMAX;
+#pragma unroll
+    for (int e = 0; e < GMAX; ++e) Gp[e] = g[e];
+}
+
+// GU[b][p][:] = sum_e G[b][p][e] U_loc[gidx[p][e]][:]
+__global__ void k_rom_gu(RomDev d, const double* __restrict__ G, const int* __restrict__ active,
+                         double* __restrict__ GU) {
+    const int p = blockIdx.x, b = blockIdx.y;
+    if (!active[b]) return;
+    const double* Gp = G + ((int64_t)b * d.M + p) * GMAX;
+    const int32_t* gi = d.gidx + (int64_t)p * GMAX;
+    for (int j = threadIdx.x; j < d.Nr; j += blockDim.x) {
+        double acc = 0.0;
+        for (int e = 0; e < GMAX; ++e) {
+            const int s = gi[e];
+            if (s < 0) break;
+            acc += Gp[e] * d.UlocR[(int64_t)s * d.Nr + j];
+        }
+        GU[((int64_t)b * d.M + p) * d.Nr + j] = acc;
+    }
+}
+
+// J[b] = Ms/dt + Alin + P GU[b]; row i of instance b per block
+__global__ void k_rom_jac(RomDev d, double dt_inv, const double* __restrict__ GU, const int* __restrict__ active,
+                          double* __restrict__ J) {
+    const int i = blockIdx.x, b = blockIdx.y;
+    if (!active[b]) return;
+    const double* Pi = d.P + (int64_t)i * d.M;
+    const double* GUb = GU + (int64_t)b * d.M * d.Nr;
+    for (int j = threadIdx.x; j < d.Nr; j += blockDim.x) {
+        double acc = d.Ms[(int64_t)i * d.Nr + j] * dt_inv + d.Alin[(int64_t)i * d.Nr + j];
+        for (int p = 0; p < d.M; ++p) acc += Pi[p] * GUb[(int64_t)p * d.Nr + j];
+        J[((int64_t)b * d.Nr + i) * d.Nr + j] = acc;
+    }
+}
+
+// r[b] = Ms (a - a_old)/dt + Alin a + mu bbnd + P f[b]
+__global__ void k_rom_resid(RomDev d, double dt_inv, const double* __restrict__ a, const double* __restrict__ a_old,
+                            const double* __restrict__ prm, const double* __restrict__ f,
+                            const int* __restrict__ active, double* __restrict__ r) {
+    const int b = blockIdx.x;
+    if (!active[b]) return;
+    const double* ab = a + (int64_t)b * d.Nr;
+    const double* aob = a_old + (int64_t)b * d.Nr;
+    const double* fb = f + (int64_t)b * d.M;
+    const double mu = prm[3 * b];
+    for (int i = threadIdx.x; i < d.Nr; i += blockDim.x) {
+        double acc = mu * d.bbnd[i];
+        for (int j = 0; j < d.Nr; ++j)
+            acc += d.Ms[(int64_t)i * d.Nr + j] * (ab[j] - aob[j]) * dt_inv + d.Alin[(int64_t)i * d.Nr + j] * ab[j];
+        for (int p = 0; p < d.M; ++p) acc += d.P[(int64_t)i * d.M + p] * fb[p];
+        r[(int64_t)b * d.Nr + i] = acc;
+    }
+}
+
+// block max / sum helpers (blockDim.x == 256)
+__device__ inline double block_max(double v, double* sh) {
+    sh[threadIdx.x] = v;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) sh[threadIdx.x] = fmax(sh[threadIdx.x], sh[threadIdx.x + s]);
+        __syncthreads();
+    }
+    double r = sh[0];
+    __syncthreads();
+    return r;
+}
+
+// delta[b] = -J[b]^-1 r[b]: row then column equilibration, LU with partial
+// pivoting (ties: lowest row), forward elimination of the right-hand side
+// during the factorisation, back substitution.  One block per instance,
+// J[b] overwritten.
+__global__ void __launch_bounds__(256)
+k_rom_lu(int Nr, double* __restrict__ J, const double* __restrict__ r, const int* __restrict__ active,
+         double* __restrict__ delta) {
+    const int b = blockIdx.x;
+    if (!active[b]) return;
+    __shared__ double sh[256];
+    __shared__ double rs[ROM_NR_MAX], cs[ROM_NR_MAX], rhs[ROM_NR_MAX], x[ROM_NR_MAX];
+    __shared__ int spiv;
+    double* A = J + (int64_t)b * Nr * Nr;
+    for (int i = threadIdx.x; i < Nr; i += blockDim.x) {
+        double m = 0.0;
+        for (int j = 0; j < Nr; ++j) m = fmax(m, fabs(A[(int64_t)i * Nr + j]));
+        rs[i] = m > 0.0 ? 1.0 / m : 1.0;
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < Nr; j += blockDim.x) {
+        double m = 0.0;
+        for (int i = 0; i < Nr; ++i) m = fmax(m, fabs(A[(int64_t)i * Nr + j] * rs[i]));
+        cs[j] = m > 0.0 ? 1.0 / m : 1.0;
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < Nr * Nr; idx += blockDim.x) {
+        const int i = idx / Nr, j = idx % Nr;
+        A[idx] *= rs[i] * cs[j];
+    }
+    for (int i = threadIdx.x; i < Nr; i += blockDim.x) rhs[i] = -r[(int64_t)b * Nr + i] * rs[i];
+    __syncthreads();
+    for (int k = 0; k < Nr; ++k) {
+        // pivot: largest |A[i][k]|, i >= k, lowest index on ties
+        double best = -1.0;
+        int bi = k;
+        for (int i = k + threadIdx.x; i < Nr; i += blockDim.x) {
+            double v = fabs(A[(int64_t)i * Nr + k]);
+            if (v > best) { best = v; bi = i; }
+        }
+        // reduce (value, index)
+        sh[threadIdx.x] = best;
+        __shared__ int shi[256];
+        shi[threadIdx.x] = bi;
+        __syncthreads();
+        for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+            if (threadIdx.x < s) {
+                double v2 = sh[threadIdx.x + s];
+                int i2 = shi[threadIdx.x + s];
+                if (v2 > sh[threadIdx.x] || (v2 == sh[threadIdx.x] && i2 < shi[threadIdx.x])) {
+                    sh[threadIdx.x] = v2;
+                    shi[threadIdx.x] = i2;
+                }
+            }
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) spiv = shi[0];
+        __syncthreads();
+        const int piv = spiv;
+        if (piv != k) {
+            for (int j = threadIdx.x; j < Nr; j += blockDim.x) {
+                double t = A[(int64_t)k * Nr + j];
+                A[(int64_t)k * Nr + j] = A[(int64_t)piv * Nr + j];
+                A[(int64_t)piv * Nr + j] = t;
+            }
+            if (threadIdx.x == 0) {
+                double t = rhs[k]; rhs[k] = rhs[piv]; rhs[piv] = t;
+            }
+        }
+        __syncthreads();
+        const double akk = A[(int64_t)k * Nr + k];
+        const double inv = akk != 0.0 ? 1.0 / akk : 0.0;
+        // multipliers and right-hand side
+        for (int i = k + 1 + threadIdx.x; i < Nr; i += blockDim.x) {
+            double l = A[(int64_t)i * Nr + k] * inv;
+            A[(int64_t)i * Nr + k] = l;
+            rhs[i] -= l * rhs[k];
+        }
+        __syncthreads();
+        const int m = Nr - k - 1;
+        for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x) {
+            const int i = k + 1 + idx / m, j = k + 1 + idx % m;
+            A[(int64_t)i * Nr + j] -= A[(int64_t)i * Nr + k] * A[(int64_t)k * Nr + j];
+        }
+        __syncthreads();
+    }
+    // back substitution
+    for (int k = Nr - 1; k >= 0; --k) {
+        double part = 0.0;
+        for (int j = k + 1 + threadIdx.x; j < Nr; j += blockDim.x) part += A[(int64_t)k * Nr + j] * x[j];
+        sh[threadIdx.x] = part;
+        __syncthreads();
+        for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+            if (threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) {
+            const double akk = A[(int64_t)k * Nr + k];
+            x[k] = akk != 0.0 ? (rhs[k] - sh[0]) / akk : 0.0;
+        }
+        __syncthreads();
+    }
+    for (int j = threadIdx.x; j < Nr; j += blockDim.x) delta[(int64_t)b * Nr + j] = x[j] * cs[j];
+}
+
+// step length and convergence of instance b (one block per instance)
+__global__ void __launch_bounds__(256)
+k_rom_update(RomDev d, double* __restrict__ a, const double* __restrict__ delta, int* __restrict__ active,
+             int* __restrict__ failed, long long* __restrict__ its) {
+    const int b = blockIdx.x;
+    if (!active[b]) return;
+    __shared__ double sd[ROM_NR_MAX];
+    __shared__ double sh[256];
+    for (int j = threadIdx.x; j < d.Nr; j += blockDim.x) sd[j] = delta[(int64_t)b * d.Nr + j];
+    __syncthreads();
+    double m = 0.0;
+    for (int k = threadIdx.x; k < d.nloc; k += blockDim.x) {
+        double acc = 0.0;
+        for (int j = 0; j < d.Nr; ++j) acc += d.UlocC[(int64_t)j * d.nloc + k] * sd[j];
+        double v = fabs(acc) / d.us[k];
+        m = (v == v) ? fmax(m, v) : INFINITY;
+    }
+    const double dn = block_max(m, sh);
+    if (!(dn < INFINITY)) {
+        if (threadIdx.x == 0) { failed[b] = 1; active[b] = 0; }
+        return;
+    }
+    const double lam = dn <= ROM_DELTA_MAX ? 1.0 : ROM_DELTA_MAX / dn;
+    for (int j = threadIdx.x; j < d.Nr; j += blockDim.x) a[(int64_t)b * d.Nr + j] += lam * sd[j];
+    if (threadIdx.x == 0) {
+        its[b] += 1;
+        if (lam * dn <= ROM_TOL) active[b] = 0;
+    }
+}
+
+__global__ void k_rom_init(RomDev d, int B, double* __restrict__ a) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < (int64_t)B * d.Nr) a[i] = d.a0[i % d.Nr];
+}
+
+// copy src -> dst for instances with mask[b] (all instances if mask is null)
+__global__ void k_rom_copy(int Nr, int B, const int* __restrict__ mask, const double* __restrict__ src,
+                           double* __restrict__ dst) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (int64_t)B * Nr) return;
+    if (mask && !mask[i / Nr]) return;
+    dst[i] = src[i];
+}
+
+__global__ void k_rom_set_active(int B, const int* __restrict__ on, const int* __restrict__ failed,
+                                 int* __restrict__ active) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b < B) active[b] = (on ? on[b] : 1) && !failed[b];
+}
+
+// flips of pass-active instances; instances with flips stay on for the next pass
+__global__ void k_rom_flips(int ngate, int B, const uint8_t* __restrict__ g1, uint8_t* __restrict__ g2,
+                            const int* __restrict__ failed, int* __restrict__ pass_on, long long* __restrict__ flips,
+                            uint8_t* __restrict__ gate, int last_pass) {
+    const int b = blockIdx.x;
+    __shared__ int cnt;
+    if (threadIdx.x == 0) cnt = 0;
+    __syncthreads();
+    if (!pass_on[b] || failed[b]) {
+        if (threadIdx.x == 0) pass_on[b] = 0;
+        return;
+    }
+    int c = 0;
+    for (int g = threadIdx.x; g < ngate; g += blockDim.x)
+        c += g1[(int64_t)b * ngate + g] != g2[(int64_t)b * ngate + g];
+    atomicAdd(&cnt, c);
+    __syncthreads();
+    if (cnt > 0 && !last_pass) {
+        for (int g = threadIdx.x; g < ngate; g += blockDim.x) gate[(int64_t)b * ngate + g] = g2[(int64_t)b * ngate + g];
+    }
+    if (threadIdx.x == 0) {
+        if (cnt > 0 && !last_pass) flips[b] += cnt;
+        pass_on[b] = (cnt > 0 && !last_pass) ? 1 : 0;
+    }
+}
+
+__global__ void k_rom_outputs(RomDev d, int B, const double* __restrict__ a, const int* __restrict__ failed,
+                              int col, int ncol, double* __restrict__ V, double* __restrict__ S) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= B) return;
+    double v = 0.0, s = 0.0;
+    for (int j = 0; j < d.Nr; ++j) {
+        v += d.scp[j] * a[(int64_t)b * d.Nr + j];
+        s += d.sac[j] * a[(int64_t)b * d.Nr + j];
+    }
+    V[(int64_t)b * ncol + col] = failed[b] ? NAN : v;
+    S[(int64_t)b * ncol + col] = failed[b] ? NAN : s;
+}
+
+__global__ void k_rom_count(int B, const int* __restrict__ flag, int* __restrict__ out) {
+    __shared__ int cnt;
+    if (threadIdx.x == 0) cnt = 0;
+    __syncthreads();
+    int c = 0;
+    for (int b = threadIdx.x; b < B; b += blockDim.x) c += flag[b] != 0;
+    atomicAdd(&cnt, c);
+    __syncthreads();
+    if (threadIdx.x == 0) *out = cnt;
+}
+
+// ------------------------------------------------------------- host build
+namespace {
+
+struct HostCell {
+    int nt, ny, nz;
+    int64_t N, F, syz;
+    std::vector<uint32_t> vc;
+    std::vector<int32_t> pg, pe;
+    int phase(int64_t v) const { return (int)(vc[v] & 7u); }
+    int64_t nb(int64_t v, int d) const {
+        int z = (int)(v % nz), y = (int)((v / nz) % ny), t = (int)(v / syz);
+        switch (d) {
+            case 0: return t > 0 ? v - syz : -1;
+            case 1: return t < nt - 1 ? v + syz : -1;
+            case 2: return y > 0 ? v - nz : -1;
+            case 3: return y < ny - 1 ? v + nz : -1;
+            case 4: return z > 0 ? v - 1 : -1;
+            default: return z < nz - 1 ? v + 1 : -1;
+        }
+    }
+    // interface face of solid s towards direction d
+    int64_t iface(int64_t s, int d) const {
+        uint32_t c = vc[s];
+        uint32_t m = (c >> 3) & 63u;
+        return (int64_t)(c >> VC_FBASE_SHIFT) + __builtin_popcount(m & ((1u << d) - 1u));
+    }
+};
+
+bool kinetic(int p) { return p == PG || p == PK || p == PL; }
+
+struct Term {
+    int type = T_NONE;
+    int64_t dof[5] = {-1, -1, -1, -1, -1};   // full-state indices
+    double wbv = 0.0, wpl = 0.0;
+    int64_t face = -1;                        // plating face (gate)
+};
+
+}  // namespace
+
+static int rom_build_host(mb_rom* R, const mb_rom_data* dd) {
+    mb_cell* c = R->cell;
+    const Dims& D = c->D;
+    HostCell H;
+    H.nt = D.nt; H.ny = D.ny; H.nz = D.nz; H.N = D.N; H.F = D.F; H.syz = D.syz;
+    H.vc.resize(D.N);
+    MB_CUDA(cudaMemcpy(H.vc.data(), c->vcode, 4 * D.N, cudaMemcpyDeviceToHost));
+    if (D.F) {
+        H.pg.resize(D.F); H.pe.resize(D.F);
+        MB_CUDA(cudaMemcpy(H.pg.data(), c->pf_g, 4 * D.F, cudaMemcpyDeviceToHost));
+        MB_CUDA(cudaMemcpy(H.pe.data(), c->pf_e, 4 * D.F, cudaMemcpyDeviceToHost));
+    }
+    const int64_t N = D.N, n = c->n;
+    const int Nr = dd->n_r, Mbv = dd->n_bv, M1c = dd->n_1c, M = Mbv + M1c;
+    const double A = c->P.A, invF = c->P.invF, tp = c->prm.E_tplus;
+    // plating faces touching each voxel (as graphite or electrolyte voxel)
+    std::vector<std::vector<int64_t>> vfaces(N);
+    for (int64_t f = 0; f < D.F; ++f) {
+        vfaces[H.pg[f]].push_back(f);
+        vfaces[H.pe[f]].push_back(f);
+    }
+    std::vector<std::vector<Term>> prog(M);
+    std::vector<int64_t> closure;
+    auto add_vox = [&](int64_t v) {
+        closure.push_back(v);
+        closure.push_back(N + v);
+    };
+    for (int m = 0; m < M; ++m) {
+        const bool bv = m < Mbv;
+        const int64_t p = bv ? dd->p_bv[m] : dd->p_1c[m - Mbv];
+        if (p < 0 || p >= n) return MB_EINVAL;
+        std::vector<Term>& T = prog[m];
+        if (p >= 2 * N) {                                 // face row of plating face f
+            const int64_t f = p - 2 * N;
+            closure.push_back(H.pg[f]); closure.push_back(N + H.pg[f]);
+            closure.push_back(H.pe[f]); closure.push_back(N + H.pe[f]);
+            closure.push_back(2 * N + f);
+            if (bv) {
+                Term t;
+                t.type = T_GE;
+                t.dof[0] = H.pg[f]; t.dof[1] = N + H.pg[f]; t.dof[2] = H.pe[f]; t.dof[3] = N + H.pe[f];
+                t.dof[4] = 2 * N + f;
+                t.wpl = invF;
+                t.face = f;
+                T.push_back(t);
+            }
+            continue;
+        }
+        const bool crow = p < N;
+        const int64_t v = crow ? p : p - N;
+        add_vox(v);
+        for (int d = 0; d < 6; ++d) {
+            int64_t w = H.nb(v, d);
+            if (w >= 0) add_vox(w);
+        }
+        for (int64_t f : vfaces[v]) closure.push_back(2 * N + f);
+        const int lv = H.phase(v);
+        for (int d = 0; d < 6; ++d) {
+            const int64_t w = H.nb(v, d);
+            if (w < 0) continue;
+            const int lw = H.phase(w);
+            if (!bv) {
+                if (lv == PE && lw == PE) {
+                    Term t;
+                    t.type = T_EE;
+                    t.dof[0] = v; t.dof[2] = w;
+                    t.wbv = crow ? tp * invF : 1.0;
+                    T.push_back(t);
+                }
+                continue;
+            }
+            int64_t s, e;
+            int dsol;
+            bool solid_row;
+            if (kinetic(lv) && lw == PE) { s = v; e = w; dsol = d; solid_row = true; }
+            else if (lv == PE && kinetic(lw)) { s = w; e = v; dsol = d ^ 1; solid_row = false; }
+            else continue;
+            const int ls = H.phase(s);
+            Term t;
+            t.type = ls == PG ? T_GE : (ls == PK ? T_KE : T_LE);
+            if (ls != PL) { t.dof[0] = s; t.dof[2] = e; }
+            t.dof[1] = N + s; t.dof[3] = N + e;
+            if (ls == PG) {
+                t.face = H.iface(s, dsol);
+                t.dof[4] = 2 * N + t.face;
+            }
+            if (crow) {
+                if (solid_row) t.wbv = ls == PL ? 0.0 : A * invF;
+                else { t.wbv = -A * invF; t.wpl = ls == PG ? -A * invF : 0.0; }
+            } else {
+                t.wbv = solid_row ? A : -A;
+                t.wpl = ls == PG ? t.wbv : 0.0;
+            }
+            T.push_back(t);
+        }
+        if ((int)T.size() > TMAX) return MB_EINVAL;
+    }
+    std::sort(closure.begin(), closure.end());
+    closure.erase(std::unique(closure.begin(), closure.end()), closure.end());
+    const int nloc = (int)closure.size();
+    std::map<int64_t, int> slot;
+    for (int k = 0; k < nloc; ++k) slot[closure[k]] = k;
+    // gated faces
+    std::map<int64_t, int> gslot;
+    std::vector<int32_t> gface;
+    // term arrays
+    std::vector<int8_t> ttype((size_t)M * TMAX, T_NONE), tgpos((size_t)M * TMAX * 5, 0);
+    std::vector<int32_t> tidx((size_t)M * TMAX * 5, -1), tgate((size_t)M * TMAX, -1), gidx((size_t)M * GMAX, -1);
+    std::vector<double> twbv((size_t)M * TMAX, 0.0), twpl((size_t)M * TMAX, 0.0);
+    for (int m = 0; m < M; ++m) {
+        std::vector<int32_t> glist;
+        for (size_t t = 0; t < prog[m].size(); ++t) {
+            const Term& T = prog[m][t];
+            const size_t q = (size_t)m * TMAX + t;
+            ttype[q] = (int8_t)T.type;
+            twbv[q] = T.wbv;
+            twpl[q] = T.wpl;
+            for (int k = 0; k < 5; ++k) {
+                if (T.dof[k] < 0) continue;
+                const int s = slot.at(T.dof[k]);
+                tidx[q * 5 + k] = s;
+                auto it = std::find(glist.begin(), glist.end(), s);
+                int pos = (int)(it - glist.begin());
+                if (it == glist.end()) glist.push_back(s);
+                if (pos >= GMAX) return MB_EINVAL;
+                tgpos[q * 5 + k] = (int8_t)pos;
+            }
+            if (T.face >= 0) {
+                auto it = gslot.find(T.face);
+                int gs;
+                if (it == gslot.end()) {
+                    gs = (int)gface.size() / 3;
+                    gslot[T.face] = gs;
+                    gface.push_back(slot.at(N + H.pg[T.face]));
+                    gface.push_back(slot.at(N + H.pe[T.face]));
+                    gface.push_back(slot.at(2 * N + T.face));
+                } else {
+                    gs = it->second;
+                }
+                tgate[q] = gs;
+            }
+        }
+        if ((int)glist.size() > GMAX) return MB_EINVAL;
+        for (size_t e = 0; e < glist.size(); ++e) gidx[(size_t)m * GMAX + e] = glist[e];
+    }
+    // basis at the closure
+    std::vector<double> UlocC((size_t)Nr * nloc), UlocR((size_t)nloc * Nr), us(nloc);
+    for (int k = 0; k < nloc; ++k) {
+        const int64_t dof = closure[k];
+        for (int j = 0; j < Nr; ++j) {
+            const double u = dd->U[(size_t)dof * Nr + j];
+            UlocC[(size_t)j * nloc + k] = u;
+            UlocR[(size_t)k * Nr + j] = u;
+        }
+        if (dof < N) us[k] = c->P.cref[H.phase(dof)];
+        else if (dof < 2 * N) us[k] = 1.0;
+        else us[k] = c->P.nc;
+    }
+    std::vector<double> P((size_t)Nr * M);
+    for (int i = 0; i < Nr; ++i) {
+        for (int m = 0; m < Mbv; ++m) P[(size_t)i * M + m] = dd->Pbv[(size_t)i * Mbv + m];
+        for (int m = 0; m < M1c; ++m) P[(size_t)i * M + Mbv + m] = dd->P1c[(size_t)i * M1c + m];
+    }
+    // upload
+    RomDev& d = R->d;
+    d.Nr = Nr; d.Mbv = Mbv; d.M1c = M1c; d.M = M; d.nloc = nloc; d.ngate = (int)gface.size() / 3;
+    auto up = [&](auto*& dst, const auto& src) -> bool {
+        using T = typename std::remove_reference<decltype(src[0])>::type;
+        using U = typename std::remove_const<T>::type;
+        dst = rom_alloc<U>(R->owned, src.size());
+        if (!dst) return false;
+        return cudaMemcpy(dst, src.data(), sizeof(U) * src.size(), cudaMemcpyHostToDevice) == cudaSuccess;
+    };
+    auto upr = [&](double*& dst, const double* src, size_t cnt) -> bool {
+        dst = rom_alloc<double>(R->owned, cnt);
+        if (!dst) return false;
+        return cudaMemcpy(dst, src, 8 * cnt, cudaMemcpyHostToDevice) == cudaSuccess;
+    };
+    bool ok = up(d.UlocC, UlocC) && up(d.UlocR, UlocR) && up(d.us, us) && up(d.ttype, ttype) &&
+              up(d.tidx, tidx) && up(d.twbv, twbv) && up(d.twpl, twpl) && up(d.tgate, tgate) &&
+              up(d.tgpos, tgpos) && up(d.gidx, gidx) && up(d.P, P) &&
+              upr(d.Ms, dd->Ms, (size_t)Nr * Nr) && upr(d.Alin, dd->Alin, (size_t)Nr * Nr) &&
+              upr(d.bbnd, dd->bbnd, Nr) && upr(d.scp, dd->s_cp, Nr) && upr(d.sac, dd->s_ac, Nr) &&
+              upr(d.a0, dd->a0, Nr);
+    if (ok && !gface.empty()) ok = up(d.gface, gface);
+    if (!ok) return cuda_fail(cudaGetLastError(), "rom upload");
+    return MB_OK;
+}
+
+static int rom_work_alloc(mb_rom* R, int B, int ncol) {
+    RomWork& w = R->w;
+    const RomDev& d = R->d;
+    rom_work_free(w);
+    w.B = B;
+    auto& L = w.bufs;
+    w.a = rom_alloc<double>(L, (size_t)B * d.Nr);
+    w.a_old = rom_alloc<double>(L, (size_t)B * d.Nr);
+    w.delta = rom_alloc<double>(L, (size_t)B * d.Nr);
+    w.r = rom_alloc<double>(L, (size_t)B * d.Nr);
+    w.J = rom_alloc<double>(L, (size_t)B * d.Nr * d.Nr);
+    w.uloc = rom_alloc<double>(L, (size_t)B * d.nloc);
+    w.uloc_old = rom_alloc<double>(L, (size_t)B * d.nloc);
+    w.f = rom_alloc<double>(L, (size_t)B * d.M);
+    w.G = rom_alloc<double>(L, (size_t)B * d.M * GMAX);
+    w.GU = rom_alloc<double>(L, (size_t)B * d.M * d.Nr);
+    w.prm = rom_alloc<double>(L, (size_t)B * 3);
+    w.gate = rom_alloc<uint8_t>(L, (size_t)B * (d.ngate ? d.ngate : 1));
+    w.gate2 = rom_alloc<uint8_t>(L, (size_t)B * (d.ngate ? d.ngate : 1));
+    w.active = rom_alloc<int>(L, B);
+    w.failed = rom_alloc<int>(L, B);
+    w.pass_on = rom_alloc<int>(L, B);
+    w.counts = rom_alloc<int>(L, 4);
+    w.its = rom_alloc<long long>(L, B);
+    w.flips = rom_alloc<long long>(L, B);
+    w.V = rom_alloc<double>(L, (size_t)B * ncol);
+    w.S = rom_alloc<double>(L, (size_t)B * ncol);
+    for (void* p : L)
+        if (!p) { rom_work_free(w); return MB_ENOMEM; }
+    return MB_OK;
+}
+
+}  // namespace mb
+
+using namespace mb;
+
+extern "C" int mb_rom_create(mb_cell* cell, const mb_rom_data* d, mb_rom** out) {
+    if (!cell || !d || !out || d->n_r < 1 || d->n_r > ROM_NR_MAX || d->n_bv < 0 || d->n_1c < 0 || !d->U ||
+        !d->Ms || !d->Alin || !d->bbnd || !d->s_cp || !d->s_ac || !d->a0 || (d->n_bv && (!d->p_bv || !d->Pbv)) ||
+        (d->n_1c && (!d->p_1c || !d->P1c))) {
+        set_error("mb_rom_create: invalid argument");
+        return MB_EINVAL;
+    }
+    mb_rom* R = new mb_rom();
+    R->cell = cell;
+    int rc = rom_build_host(R, d);
+    if (rc) {
+        if (rc == MB_EINVAL) set_error("mb_rom_create: point outside the residual or too many terms per point");
+        for (void* p : R->owned) cudaFree(p);
+        delete R;
+        return rc;
+    }
+    *out = R;
+    return MB_OK;
+}
+
+extern "C" int mb_rom_destroy(mb_rom* R) {
+    if (!R) return MB_EINVAL;
+    rom_work_free(R->w);
+    for (void* p : R->owned) cudaFree(p);
+    delete R;
+    return MB_OK;
+}
+
+extern "C" int mb_rom_solve_batch(mb_rom* R, int B, const mb_rom_params* prm, int n_steps, double dt, double* V_out,
+                                  double* sac_out, double* a_final, mb_rom_info* info) {
+    if (!R || B < 1 || !prm || n_steps < 0 || !(dt > 0) || !V_out || !sac_out) {
+        set_error("mb_rom_solve_batch: invalid argument");
+        return MB_EINVAL;
+    }
+    mb_cell* c = R->cell;
+    cudaStream_t s = c->stream;
+    const RomDev& d = R->d;
+    const int ncol = n_steps + 1;
+    int rc = rom_work_alloc(R, B, ncol);
+    if (rc) { set_error("mb_rom_solve_batch: device memory"); return rc; }
+    RomWork& w = R->w;
+    std::vector<double> hp((size_t)B * 3);
+    for (int b = 0; b < B; ++b) {
+        hp[3 * b] = prm[b].I_app;
+        hp[3 * b + 1] = prm[b].s_i0;
+        hp[3 * b + 2] = prm[b].k_pl;
+    }
+    MB_CUDA(cudaMemcpyAsync(w.prm, hp.data(), 8 * hp.size(), cudaMemcpyHostToDevice, s));
+    MB_CUDA(cudaMemsetAsync(w.failed, 0, 4 * B, s));
+    MB_CUDA(cudaMemsetAsync(w.its, 0, 8 * B, s));
+    MB_CUDA(cudaMemsetAsync(w.flips, 0, 8 * B, s));
+    MB_CUDA(cudaMemsetAsync(w.gate, 0, (size_t)B * (d.ngate ? d.ngate : 1), s));
+    const unsigned nb = (unsigned)(((int64_t)B * d.Nr + 255) / 256);
+    const unsigned bb = (unsigned)((B + 255) / 256);
+    k_rom_init<<<nb, 256, 0, s>>>(d, B, w.a), count_launch(c);
+    k_rom_outputs<<<bb, 256, 0, s>>>(d, B, w.a, w.failed, 0, ncol, w.V, w.S), count_launch(c);
+    const double dt_inv = 1.0 / dt;
+    const double n_thr = GATE_N_REL * c->P.nc;
+    const dim3 gg((unsigned)((d.nloc + 255) / 256), (unsigned)B);
+    const unsigned ge = (unsigned)(((int64_t)d.M * B + 127) / 128);
+    const unsigned gt = (unsigned)(((int64_t)(d.ngate ? d.ngate : 1) * B + 255) / 256);
+    int hcount = 0;
+    for (int step = 1; step <= n_steps; ++step) {
+        k_rom_copy<<<nb, 256, 0, s>>>(d.Nr, B, nullptr, w.a, w.a_old), count_launch(c);
+        k_rom_gather<<<gg, 256, 0, s>>>(d, w.a_old, w.uloc_old), count_launch(c);
+        if (d.ngate) k_rom_gate<<<gt, 256, 0, s>>>(d, B, w.uloc_old, w.uloc_old, n_thr, w.gate), count_launch(c);
+        k_rom_set_active<<<bb, 256, 0, s>>>(B, nullptr, w.failed, w.pass_on), count_launch(c);
+        for (int pass = 1; pass <= ROM_PASSES; ++pass) {
+            k_rom_copy<<<nb, 256, 0, s>>>(d.Nr, B, w.pass_on, w.a_old, w.a), count_launch(c);
+            k_rom_set_active<<<bb, 256, 0, s>>>(B, w.pass_on, w.failed, w.active), count_launch(c);
+            for (int it = 0; it < ROM_MAXIT; ++it) {
+                k_rom_gather<<<gg, 256, 0, s>>>(d, w.a, w.uloc), count_launch(c);
+                if (d.M) {
+                    k_rom_ei<<<ge, 128, 0, s>>>(d, c->P, B, w.uloc, w.gate, w.prm, w.active, w.f, w.G), count_launch(c);
+                    k_rom_gu<<<dim3((unsigned)d.M, (unsigned)B), 128, 0, s>>>(d, w.G, w.active, w.GU), count_launch(c);
+                }
+                k_rom_jac<<<dim3((unsigned)d.Nr, (unsigned)B), 128, 0, s>>>(d, dt_inv, w.GU, w.active, w.J), count_launch(c);
+                k_rom_resid<<<(unsigned)B, 128, 0, s>>>(d, dt_inv, w.a, w.a_old, w.prm, w.f, w.active, w.r), count_launch(c);
+                k_rom_lu<<<(unsigned)B, 256, 0, s>>>(d.Nr, w.J, w.r, w.active, w.delta), count_launch(c);
+                k_rom_update<<<(unsigned)B, 256, 0, s>>>(d, w.a, w.delta, w.active, w.failed, w.its), count_launch(c);
+                k_rom_count<<<1, 256, 0, s>>>(B, w.active, w.counts), count_launch(c);
+                MB_CUDA(cudaMemcpyAsync(&hcount, w.counts, 4, cudaMemcpyDeviceToHost, s));
+                MB_CUDA(cudaStreamSynchronize(s));
+                if (hcount == 0) break;
+            }
+            // instances still iterating after the iteration limit have failed
+            {
+                std::vector<int> act(B), fl(B);
+                MB_CUDA(cudaMemcpyAsync(act.data(), w.active, 4 * B, cudaMemcpyDeviceToHost, s));
+                MB_CUDA(cudaMemcpyAsync(fl.data(), w.failed, 4 * B, cudaMemcpyDeviceToHost, s));
+                MB_CUDA(cudaStreamSynchronize(s));
+                bool any = false;
+                for (int b = 0; b < B; ++b)
+                    if (act[b]) { fl[b] = 1; any = true; }
+                if (any) MB_CUDA(cudaMemcpyAsync(w.failed, fl.data(), 4 * B, cudaMemcpyHostToDevice, s));
+                MB_CUDA(cudaStreamSynchronize(s));
+            }
+            if (!d.ngate) break;
+            k_rom_gather<<<gg, 256, 0, s>>>(d, w.a, w.uloc), count_launch(c);
+            k_rom_gate<<<gt, 256, 0, s>>>(d, B, w.uloc, w.uloc_old, n_thr, w.gate2), count_launch(c);
+            k_rom_flips<<<(unsigned)B, 256, 0, s>>>(d.ngate, B, w.gate, w.gate2, w.failed, w.pass_on, w.flips, w.gate,
+                                                   pass == ROM_PASSES ? 1 : 0), count_launch(c);
+            k_rom_count<<<1, 256, 0, s>>>(B, w.pass_on, w.counts), count_launch(c);
+            MB_CUDA(cudaMemcpyAsync(&hcount, w.counts, 4, cudaMemcpyDeviceToHost, s));
+            MB_CUDA(cudaStreamSynchronize(s));
+            if (hcount == 0) break;
+        }
+        k_rom_outputs<<<bb, 256, 0, s>>>(d, B, w.a, w.failed, step, ncol, w.V, w.S), count_launch(c);
+    }
+    MB_CUDA_LAUNCH("rom_solve");
+    MB_CUDA(cudaMemcpyAsync(V_out, w.V, 8 * (size_t)B * ncol, cudaMemcpyDeviceToHost, s));
+    MB_CUDA(cudaMemcpyAsync(sac_out, w.S, 8 * (size_t)B * ncol, cudaMemcpyDeviceToHost, s));
+    if (a_final) MB_CUDA(cudaMemcpyAsync(a_final, w.a, 8 * (size_t)B * d.Nr, cudaMemcpyDeviceToHost, s));
+    std::vector<long long> its(B), flips(B);
+    std::vector<int> fl(B);
+    MB_CUDA(cudaMemcpyAsync(its.data(), w.its, 8 * B, cudaMemcpyDeviceToHost, s));
+    MB_CUDA(cudaMemcpyAsync(flips.data(), w.flips, 8 * B, cudaMemcpyDeviceToHost, s));
+    MB_CUDA(cudaMemcpyAsync(fl.data(), w.failed, 4 * B, cudaMemcpyDeviceToHost, s));
+    MB_CUDA(cudaStreamSynchronize(s));
+    mb_rom_info inf{0, 0, 0};
+    for (int b = 0; b < B; ++b) {
+        inf.newton_its += its[b];
+        inf.flips += flips[b];
+        inf.failed += fl[b] ? 1 : 0;
+    }
+    if (info) *info = inf;
+    if (inf.failed) {
+        set_error("mb_rom_solve_batch: reduced Newton did not converge for some instances");
+        return MB_ENOCONV;
+    }
+    return MB_OK;
+}

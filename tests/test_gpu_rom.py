@@ -1,0 +1,93 @@
+"""GPU reduced-model online solve (mb_rom_solve_batch) against the oracle's
+reduced Newton on the same reduced model (built by the oracle from full-order
+snapshots): cell potential and mean graphite concentration per step, FP64
+both sides; a batch gives every instance the result it has alone."""
+import numpy as np
+import pytest
+
+import synthetic as syn
+from oracle.fom import Cell as OCell
+from oracle import rom as R
+
+
+def _gpu():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1704_04139_gb300 import binding, build
+    import os
+    if not os.path.exists(binding.LIB_PATH):
+        build.build()
+    return binding
+
+
+@pytest.fixture(scope="module")
+def case(params):
+    lab = syn.full_cell(4, 4, 5, 3, 5, 0.35, 0.35, ("uniform", 1, 2), (1, 2))
+    oc = OCell(lab, 1e-6, params)
+    i1 = oc.i_1c
+    u0 = oc.initial_state()
+    u0[2 * oc.N::4] = 2e-5
+    snaps, _ = R.snapshots(oc, [(-2 * i1, 1.0, 1.0), (-5 * i1, 0.7, 3.0)], 1.0, 5, u0=u0)
+    rom = R.build(oc, snaps, (8, 6, 14, 10))
+    rom.a0 = rom.U.T @ (R.weights(oc) * u0)
+    return lab, oc, rom
+
+
+def _gpu_rom(B, lab, params, rom):
+    gc = B.Cell(lab, 1e-6, params)
+    g = B.Rom(gc, rom.U, rom.Pbv, rom.P1c, rom.Ms, rom.Alin, rom.bbnd, rom.Pbv_proj, rom.P1c_proj,
+              rom.s_cp, rom.s_ac, rom.a0)
+    return gc, g
+
+
+PRM = [(-3.5, 1.2, 0.5), (-1.0, 1.0, 1.0), (-4.5, 0.6, 4.0)]
+
+
+@pytest.mark.gpu
+def test_rom_solve_matches_oracle(params, case):
+    B = _gpu()
+    lab, oc, rom = case
+    gc, g = _gpu_rom(B, lab, params, rom)
+    prm = [(c * oc.i_1c, s, k) for (c, s, k) in PRM]
+    out = g.solve(prm, 5, 1.0)
+    assert out["ok"] and out["failed"] == 0
+    for b, p in enumerate(prm):
+        ref = R.solve(rom, p[0], p[1], p[2], 1.0, 5)
+        assert np.max(np.abs(out["V"][b] - ref["V_cell"])) <= 1e-9 * np.max(np.abs(ref["V_cell"])), b
+        assert np.max(np.abs(out["s_ac"][b] - ref["s_ac"])) <= 1e-9 * np.max(np.abs(ref["s_ac"])), b
+        # reconstructed state at the stencil closure (the values the model sees)
+        ug = rom.Uloc @ out["a"][b]
+        uo = rom.Uloc @ ref["a"][-1]
+        assert np.max(np.abs(ug - uo) / rom.us_loc) <= 1e-8, b
+    g.close()
+    gc.close()
+
+
+@pytest.mark.gpu
+def test_rom_batch_equals_alone(params, case):
+    B = _gpu()
+    lab, oc, rom = case
+    gc, g = _gpu_rom(B, lab, params, rom)
+    prm = [(c * oc.i_1c, s, k) for (c, s, k) in PRM]
+    mix = g.solve(prm, 4, 1.0)
+    for b, p in enumerate(prm):
+        alone = g.solve([p], 4, 1.0)
+        assert np.array_equal(alone["V"][0], mix["V"][b]), b
+        assert np.array_equal(alone["a"][0], mix["a"][b]), b
+    g.close()
+    gc.close()
+
+
+@pytest.mark.gpu
+def test_rom_zero_current_matches_oracle(params, case):
+    """Zero current (relaxation of the seeded plated Li) on the GPU and in the oracle."""
+    B = _gpu()
+    lab, oc, rom = case
+    gc, g = _gpu_rom(B, lab, params, rom)
+    out = g.solve([(0.0, 1.0, 1.0)], 3, 1.0)
+    ref = R.solve(rom, 0.0, 1.0, 1.0, 1.0, 3)
+    assert out["ok"]
+    assert np.max(np.abs(out["V"][0] - ref["V_cell"])) <= 1e-9 * np.max(np.abs(ref["V_cell"]))
+    g.close()
+    gc.close()
