@@ -215,6 +215,28 @@ typedef struct {
 
 typedef struct mb_rom mb_rom;
 
+/* Offline construction (Sec. workflow:MOR) from full-order solves of the
+ * cell: n_steps steps of size dt at every parameter point from the cell's
+ * current state (restored afterwards; it is also the reduced initial state),
+ * every Newton stage a snapshot; POD of c, plated Li n and phi separately in
+ * the L^2 inner product (at most n_c, n_n, n_phi modes, none below pod_tol of
+ * the largest singular value of the block; the Gram-matrix route resolves
+ * down to ~1e-7); EI-Greedy on the interface terms (at most m_bv points) and
+ * on the migration term (at most m_1c), stopping below ei_tol of the largest
+ * training entry; projections as in mb_rom_data. */
+typedef struct {
+    int n_params;                    /* snapshot parameter points */
+    const mb_rom_params* params;     /* n_params */
+    double dt;                       /* snapshot step */
+    int n_steps;                     /* steps per snapshot trajectory */
+    int n_c, n_n, n_phi;             /* POD dimension bounds */
+    int m_bv, m_1c;                  /* EI dimension bounds */
+    double pod_tol, ei_tol;          /* relative cut-offs */
+} mb_rom_build_opts;
+int mb_rom_build(mb_cell* cell, const mb_rom_build_opts* o, mb_rom** out);
+/* Dimensions of a reduced model: N_r and the two numbers of points. */
+int mb_rom_dims(mb_rom* rom, int* n_r, int* n_bv, int* n_1c);
+
 /* Build the reduced model of `cell` from the arrays of d (MB_EINVAL on
  * inconsistent sizes or points outside the residual). */
 int mb_rom_create(mb_cell* cell, const mb_rom_data* d, mb_rom** out);

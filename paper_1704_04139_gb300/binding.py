@@ -75,6 +75,12 @@ class RomParams(C.Structure):
     _fields_ = [("I_app", C.c_double), ("s_i0", C.c_double), ("k_pl", C.c_double)]
 
 
+class RomBuildOpts(C.Structure):
+    _fields_ = [("n_params", C.c_int), ("params", VP), ("dt", C.c_double), ("n_steps", C.c_int),
+                ("n_c", C.c_int), ("n_n", C.c_int), ("n_phi", C.c_int), ("m_bv", C.c_int), ("m_1c", C.c_int),
+                ("pod_tol", C.c_double), ("ei_tol", C.c_double)]
+
+
 class RomInfo(C.Structure):
     _fields_ = [("newton_its", C.c_int64), ("flips", C.c_int64), ("failed", C.c_int)]
 
@@ -101,6 +107,8 @@ def _declare(lib):
     fn("mb_residual_dev_noalloc", C.c_int, [VP, VP, VP, C.c_double, C.c_double, VP, VP])
     fn("mb_rom_create", C.c_int, [VP, C.POINTER(RomData), C.POINTER(VP)])
     fn("mb_rom_destroy", C.c_int, [VP])
+    fn("mb_rom_build", C.c_int, [VP, C.POINTER(RomBuildOpts), C.POINTER(VP)])
+    fn("mb_rom_dims", C.c_int, [VP, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)])
     fn("mb_rom_solve_batch", C.c_int, [VP, C.c_int, C.POINTER(RomParams), C.c_int, C.c_double, VP, VP, VP,
                                         C.POINTER(RomInfo)])
     fn("mb_jvp", C.c_int, [VP, VP, VP, C.c_double, VP, VP])
@@ -327,6 +335,23 @@ class Cell:
 class Rom:
     """Reduced model of a cell (mb_rom_create): arrays in the layout of
     include/mb.h (row-major FP64; points as residual-row indices)."""
+
+    @classmethod
+    def build(cls, cell, params, dt, n_steps, dims, pod_tol=1e-7, ei_tol=1e-12):
+        """mb_rom_build: params = [(I_app, s_i0, k_pl), ...], dims = (n_c, n_n, n_phi, m_bv, m_1c)."""
+        prm = (RomParams * len(params))(*[RomParams(*map(float, p)) for p in params])
+        o = RomBuildOpts(len(params), C.cast(prm, VP), float(dt), int(n_steps), *[int(x) for x in dims],
+                         float(pod_tol), float(ei_tol))
+        h = VP()
+        _check(lib().mb_rom_build(cell.h, C.byref(o), C.byref(h)))
+        self = cls.__new__(cls)
+        self.h = h
+        self.cell = cell
+        self._keep = []
+        nr, nb, n1 = C.c_int(), C.c_int(), C.c_int()
+        _check(lib().mb_rom_dims(h, C.byref(nr), C.byref(nb), C.byref(n1)))
+        self.n_r, self.n_bv, self.n_1c = nr.value, nb.value, n1.value
+        return self
 
     def __init__(self, cell, U, p_bv, p_1c, Ms, Alin, bbnd, Pbv, P1c, s_cp, s_ac, a0):
         f64 = lambda a: np.ascontiguousarray(a, np.float64)

@@ -121,6 +121,11 @@ struct mb_cell {
 
     mb::Prof prof;
     int64_t launches = 0;          // kernel launches issued by the library for this cell
+
+    // snapshot recording for the reduced-model build: when set, every Newton
+    // iterate and its plating gates are appended (host copies)
+    std::vector<std::vector<double>>* snap_u = nullptr;
+    std::vector<std::vector<uint8_t>>* snap_g = nullptr;
 };
 
 namespace mb {

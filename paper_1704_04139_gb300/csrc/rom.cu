@@ -730,6 +730,14 @@ extern "C" int mb_rom_create(mb_cell* cell, const mb_rom_data* d, mb_rom** out) 
     return MB_OK;
 }
 
+extern "C" int mb_rom_dims(mb_rom* R, int* n_r, int* n_bv, int* n_1c) {
+    if (!R) { set_error("mb_rom_dims: invalid argument"); return MB_EINVAL; }
+    if (n_r) *n_r = R->d.Nr;
+    if (n_bv) *n_bv = R->d.Mbv;
+    if (n_1c) *n_1c = R->d.M1c;
+    return MB_OK;
+}
+
 extern "C" int mb_rom_destroy(mb_rom* R) {
     if (!R) return MB_EINVAL;
     rom_work_free(R->w);

@@ -360,6 +360,13 @@ static int newton(mb_cell* c, double dt, double I_app, int* its_out, int* kits, 
                     dn, lam, ki, rr);
         k_axpy_d<<<nblk(n), 256, 0, s>>>(lam, c->du, c->u, n), ::mb::count_launch(c);
         MB_CUDA_LAUNCH("newton update");
+        if (c->snap_u) {   // record the Newton stage (reduced-model snapshots)
+            c->snap_u->emplace_back(n);
+            c->snap_g->emplace_back(c->D.F);
+            MB_CUDA(cudaMemcpyAsync(c->snap_u->back().data(), c->u, 8 * n, cudaMemcpyDeviceToHost, s));
+            if (c->D.F) MB_CUDA(cudaMemcpyAsync(c->snap_g->back().data(), c->gate, c->D.F, cudaMemcpyDeviceToHost, s));
+            MB_CUDA(cudaStreamSynchronize(s));
+        }
         // a small update only means convergence if the linear solve made progress
         if (lam * dn <= c->opt.newton_tol && rr <= 0.5) {
             *its_out = it;
