@@ -253,6 +253,57 @@ int mb_rom_destroy(mb_rom* rom);
 int mb_rom_solve_batch(mb_rom* rom, int B, const mb_rom_params* prm, int n_steps, double dt, double* V_out,
                        double* sac_out, double* a_final, mb_rom_info* info);
 
+/* ---- serving loop (parameter-study queries; no counterpart in the paper) ----
+ * Requests arrive at any time (mb_serve_submit never blocks).  Reduced-model
+ * requests are admitted into the free slots of one resident batch of the
+ * reduced model (mb_rom) at step boundaries and leave it when their protocol
+ * is done, so requests that arrive while others run join the same batched
+ * launches; each instance's arithmetic does not depend on the others in the
+ * batch, so a result is the same alone and in the mix.  Full-order
+ * requests (validation solves) run on their own cells, created from the
+ * server's cell template, on worker threads with their own streams, admitted
+ * while the device memory of the running ones stays within fom_budget_bytes;
+ * their work overlaps with the reduced batch on the device. */
+#define MB_REQ_ROM 0
+#define MB_REQ_FOM 1
+typedef struct {
+    mb_rom* rom;                     /* reduced model for MB_REQ_ROM (not owned; NULL: none) */
+    const uint8_t* fom_labels;       /* full-order cell template (copied; NULL: no MB_REQ_FOM) */
+    int nt, ny, nz;
+    double h;
+    const mb_params* params;         /* template parameters (copied) */
+    const mb_solver_opts* fom_opts;  /* NULL: defaults */
+    int rom_slots;                   /* slots of the resident reduced batch (>= 1) */
+    int64_t fom_budget_bytes;        /* device memory for concurrent full-order cells */
+    int fom_workers;                 /* threads running full-order requests (>= 1) */
+} mb_serve_opts;
+
+typedef struct {
+    int kind;                        /* MB_REQ_ROM or MB_REQ_FOM */
+    mb_rom_params prm;               /* current density, exchange-current scale, plating rate scale */
+    int n_steps;                     /* protocol length */
+    double dt;                       /* step (s) */
+} mb_request;
+
+typedef struct {
+    int status;                      /* MB_OK, MB_ENOCONV or another error of the request */
+    int n_steps;                     /* steps done */
+    double t_submit, t_start, t_done;/* server clock (s since mb_serve_create) */
+    double* V;                       /* caller-provided, n_steps + 1 cell potentials (may be NULL) */
+    double* s_ac;                    /* caller-provided, n_steps + 1 mean graphite concentrations (may be NULL) */
+} mb_result;
+
+typedef struct mb_server mb_server;
+
+int mb_serve_create(const mb_serve_opts* o, mb_server** out);
+/* Queue a request; *ticket identifies it.  Never blocks. */
+int mb_serve_submit(mb_server* srv, const mb_request* req, uint64_t* ticket);
+/* MB_EPENDING while the request runs; MB_OK once done (out filled, the
+ * ticket released); MB_EINVAL for an unknown ticket. */
+int mb_serve_poll(mb_server* srv, uint64_t ticket, mb_result* out);
+/* Stops the threads after the running work; pending requests are dropped. */
+int mb_serve_destroy(mb_server* srv);
+
 /* ---- residual without allocation (no counterpart in the paper) ----
  * Same result as mb_residual_dev with gate == NULL (gates taken at u_old),
  * for callers that may not allocate memory at call time: a serving loop whose

@@ -81,6 +81,23 @@ class RomBuildOpts(C.Structure):
                 ("pod_tol", C.c_double), ("ei_tol", C.c_double)]
 
 
+class ServeOpts(C.Structure):
+    _fields_ = [("rom", VP), ("fom_labels", VP), ("nt", C.c_int), ("ny", C.c_int), ("nz", C.c_int),
+                ("h", C.c_double), ("params", VP), ("fom_opts", VP), ("rom_slots", C.c_int),
+                ("fom_budget_bytes", C.c_int64), ("fom_workers", C.c_int)]
+
+
+
+
+class Result(C.Structure):
+    _fields_ = [("status", C.c_int), ("n_steps", C.c_int), ("t_submit", C.c_double), ("t_start", C.c_double),
+                ("t_done", C.c_double), ("V", VP), ("s_ac", VP)]
+
+
+class Request(C.Structure):
+    _fields_ = [("kind", C.c_int), ("prm", RomParams), ("n_steps", C.c_int), ("dt", C.c_double)]
+
+
 class RomInfo(C.Structure):
     _fields_ = [("newton_its", C.c_int64), ("flips", C.c_int64), ("failed", C.c_int)]
 
@@ -108,6 +125,10 @@ def _declare(lib):
     fn("mb_rom_create", C.c_int, [VP, C.POINTER(RomData), C.POINTER(VP)])
     fn("mb_rom_destroy", C.c_int, [VP])
     fn("mb_rom_build", C.c_int, [VP, C.POINTER(RomBuildOpts), C.POINTER(VP)])
+    fn("mb_serve_create", C.c_int, [C.POINTER(ServeOpts), C.POINTER(VP)])
+    fn("mb_serve_submit", C.c_int, [VP, C.POINTER(Request), C.POINTER(C.c_uint64)])
+    fn("mb_serve_poll", C.c_int, [VP, C.c_uint64, C.POINTER(Result)])
+    fn("mb_serve_destroy", C.c_int, [VP])
     fn("mb_rom_dims", C.c_int, [VP, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)])
     fn("mb_rom_solve_batch", C.c_int, [VP, C.c_int, C.POINTER(RomParams), C.c_int, C.c_double, VP, VP, VP,
                                         C.POINTER(RomInfo)])
@@ -388,6 +409,68 @@ class Rom:
     def close(self):
         if getattr(self, "h", None):
             lib().mb_rom_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+REQ_ROM, REQ_FOM = 0, 1
+
+
+class Server:
+    """Serving loop (mb_serve_*): reduced-model requests in a resident slot
+    batch, full-order requests on worker threads."""
+
+    def __init__(self, rom=None, labels=None, h=1e-6, params=None, fom_opts=None, rom_slots=64,
+                 fom_budget_bytes=8 << 30, fom_workers=1):
+        self._keep = []
+        lab = None
+        nt = ny = nz = 0
+        prm_p = None
+        fo_p = None
+        if labels is not None:
+            lab = np.ascontiguousarray(labels, np.uint8)
+            nt, ny, nz = lab.shape
+            pr = params_from_dict(params) if isinstance(params, dict) else params
+            self._keep += [lab, pr]
+            prm_p = C.cast(C.pointer(pr), VP)
+            if fom_opts is not None:
+                self._keep.append(fom_opts)
+                fo_p = C.cast(C.pointer(fom_opts), VP)
+        o = ServeOpts(rom.h if rom is not None else None, _ptr(lab) if lab is not None else None, nt, ny, nz,
+                      float(h), prm_p, fo_p, int(rom_slots), int(fom_budget_bytes), int(fom_workers))
+        hnd = VP()
+        _check(lib().mb_serve_create(C.byref(o), C.byref(hnd)))
+        self.h = hnd
+        self._n = {}
+
+    def submit(self, kind, I_app, s_i0, k_pl, n_steps, dt):
+        r = Request(int(kind), RomParams(float(I_app), float(s_i0), float(k_pl)), int(n_steps), float(dt))
+        t = C.c_uint64()
+        _check(lib().mb_serve_submit(self.h, C.byref(r), C.byref(t)))
+        self._n[t.value] = int(n_steps)
+        return t.value
+
+    def poll(self, ticket):
+        """None while pending, else dict(status, V, s_ac, t_submit, t_start, t_done)."""
+        n = self._n[ticket]
+        V = np.full(n + 1, np.nan)
+        S = np.full(n + 1, np.nan)
+        res = Result(0, 0, 0.0, 0.0, 0.0, _ptr(V), _ptr(S))
+        rc = lib().mb_serve_poll(self.h, C.c_uint64(ticket), C.byref(res))
+        if rc == -7:
+            return None
+        _check(rc)
+        del self._n[ticket]
+        return dict(status=res.status, V=V, s_ac=S, t_submit=res.t_submit, t_start=res.t_start, t_done=res.t_done)
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().mb_serve_destroy(self.h)
             self.h = None
 
     def __del__(self):

@@ -226,6 +226,14 @@ int precond_apply(mb_cell* c, const float* u32, const uint8_t* gate, double dt, 
 // add the kernel times of the last graph execution to the profile totals
 void precond_harvest(mb_cell* c);
 
+// ---- rom.cu: slot batch of the reduced model (one step per call) ----
+int rom_batch_alloc(mb_rom* R, int B);
+int rom_slot_start(mb_rom* R, int b, const mb_rom_params& p, double dt);
+int rom_slot_clear(mb_rom* R, int b);
+int rom_batch_step(mb_rom* R);
+int rom_batch_outputs(mb_rom* R, double* hV, double* hS, int* hfailed);
+int rom_slot_stats(mb_rom* R, int b, long long* its, long long* flips, double* a);
+
 // ---- solver.cu ----
 int newton_step(mb_cell* c, double dt, double I_app, mb_step_info* info);
 void krylov_destroy(mb_cell* c);   // frees the host structs; buffers stay owned by the cell

@@ -35,6 +35,7 @@ constexpr int ROM_MAXIT = 30;
 constexpr int ROM_PASSES = 3;
 constexpr double ROM_DELTA_MAX = 0.25;
 constexpr double ROM_TOL = 1e-12;
+constexpr int RP = 4;            // per-instance parameters: I_app, s_i0, k_pl, 1/dt
 
 enum RomTerm : int8_t { T_NONE = 0, T_GE = 1, T_KE = 2, T_LE = 3, T_EE = 4 };
 
@@ -133,7 +134,7 @@ __global__ void k_rom_ei(RomDev d, DevParams P, int B, const double* __restrict_
     const int b = (int)(i / d.M), p = (int)(i % d.M);
     if (!active[b]) return;
     const double* u = uloc + (int64_t)b * d.nloc;
-    const double s_i0 = prm[3 * b + 1], k_pl = prm[3 * b + 2];
+    const double s_i0 = prm[RP * b + 1], k_pl = prm[RP * b + 2];
     double g[GMAX];
 #pragma unroll
     for (int e = 0; e < GMAX; ++e) g[e] = 0.0;
@@ -197,10 +198,11 @@ __global__ void k_rom_gu(RomDev d, const double* __restrict__ G, const int* __re
 }
 
 // J[b] = Ms/dt + Alin + P GU[b]; row i of instance b per block
-__global__ void k_rom_jac(RomDev d, double dt_inv, const double* __restrict__ GU, const int* __restrict__ active,
-                          double* __restrict__ J) {
+__global__ void k_rom_jac(RomDev d, const double* __restrict__ prm, const double* __restrict__ GU,
+                          const int* __restrict__ active, double* __restrict__ J) {
     const int i = blockIdx.x, b = blockIdx.y;
     if (!active[b]) return;
+    const double dt_inv = prm[RP * b + 3];
     const double* Pi = d.P + (int64_t)i * d.M;
     const double* GUb = GU + (int64_t)b * d.M * d.Nr;
     for (int j = threadIdx.x; j < d.Nr; j += blockDim.x) {
@@ -211,15 +213,16 @@ __global__ void k_rom_jac(RomDev d, double dt_inv, const double* __restrict__ GU
 }
 
 // r[b] = Ms (a - a_old)/dt + Alin a + mu bbnd + P f[b]
-__global__ void k_rom_resid(RomDev d, double dt_inv, const double* __restrict__ a, const double* __restrict__ a_old,
+__global__ void k_rom_resid(RomDev d, const double* __restrict__ a, const double* __restrict__ a_old,
                             const double* __restrict__ prm, const double* __restrict__ f,
                             const int* __restrict__ active, double* __restrict__ r) {
     const int b = blockIdx.x;
     if (!active[b]) return;
+    const double dt_inv = prm[RP * b + 3];
     const double* ab = a + (int64_t)b * d.Nr;
     const double* aob = a_old + (int64_t)b * d.Nr;
     const double* fb = f + (int64_t)b * d.M;
-    const double mu = prm[3 * b];
+    const double mu = prm[RP * b];
     for (int i = threadIdx.x; i < d.Nr; i += blockDim.x) {
         double acc = mu * d.bbnd[i];
         for (int j = 0; j < d.Nr; ++j)
@@ -376,11 +379,6 @@ k_rom_update(RomDev d, double* __restrict__ a, const double* __restrict__ delta,
     }
 }
 
-__global__ void k_rom_init(RomDev d, int B, double* __restrict__ a) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < (int64_t)B * d.Nr) a[i] = d.a0[i % d.Nr];
-}
-
 // copy src -> dst for instances with mask[b] (all instances if mask is null)
 __global__ void k_rom_copy(int Nr, int B, const int* __restrict__ mask, const double* __restrict__ src,
                            double* __restrict__ dst) {
@@ -422,8 +420,8 @@ __global__ void k_rom_flips(int ngate, int B, const uint8_t* __restrict__ g1, ui
     }
 }
 
-__global__ void k_rom_outputs(RomDev d, int B, const double* __restrict__ a, const int* __restrict__ failed,
-                              int col, int ncol, double* __restrict__ V, double* __restrict__ S) {
+__global__ void k_rom_outputs(RomDev d, int B, const double* __restrict__ a, double* __restrict__ V,
+                              double* __restrict__ S) {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= B) return;
     double v = 0.0, s = 0.0;
@@ -431,8 +429,32 @@ __global__ void k_rom_outputs(RomDev d, int B, const double* __restrict__ a, con
         v += d.scp[j] * a[(int64_t)b * d.Nr + j];
         s += d.sac[j] * a[(int64_t)b * d.Nr + j];
     }
-    V[(int64_t)b * ncol + col] = failed[b] ? NAN : v;
-    S[(int64_t)b * ncol + col] = failed[b] ? NAN : s;
+    V[b] = v;
+    S[b] = s;
+}
+
+// start slot b: a = a0, parameters, counters zero, not failed
+__global__ void k_rom_slot_start(RomDev d, int b, double I_app, double s_i0, double k_pl, double dt_inv,
+                                 double* __restrict__ a, double* __restrict__ prm, int* __restrict__ failed,
+                                 long long* __restrict__ its, long long* __restrict__ flips) {
+    for (int j = threadIdx.x; j < d.Nr; j += blockDim.x) a[(int64_t)b * d.Nr + j] = d.a0[j];
+    if (threadIdx.x == 0) {
+        prm[RP * b] = I_app;
+        prm[RP * b + 1] = s_i0;
+        prm[RP * b + 2] = k_pl;
+        prm[RP * b + 3] = dt_inv;
+        failed[b] = 0;
+        its[b] = 0;
+        flips[b] = 0;
+    }
+}
+
+__global__ void k_rom_fail_active(int B, int* __restrict__ active, int* __restrict__ failed) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b < B && active[b]) {
+        failed[b] = 1;
+        active[b] = 0;
+    }
 }
 
 __global__ void k_rom_count(int B, const int* __restrict__ flag, int* __restrict__ out) {
@@ -674,7 +696,7 @@ static int rom_build_host(mb_rom* R, const mb_rom_data* dd) {
     return MB_OK;
 }
 
-static int rom_work_alloc(mb_rom* R, int B, int ncol) {
+static int rom_work_alloc(mb_rom* R, int B) {
     RomWork& w = R->w;
     const RomDev& d = R->d;
     rom_work_free(w);
@@ -690,7 +712,7 @@ static int rom_work_alloc(mb_rom* R, int B, int ncol) {
     w.f = rom_alloc<double>(L, (size_t)B * d.M);
     w.G = rom_alloc<double>(L, (size_t)B * d.M * GMAX);
     w.GU = rom_alloc<double>(L, (size_t)B * d.M * d.Nr);
-    w.prm = rom_alloc<double>(L, (size_t)B * 3);
+    w.prm = rom_alloc<double>(L, (size_t)B * RP);
     w.gate = rom_alloc<uint8_t>(L, (size_t)B * (d.ngate ? d.ngate : 1));
     w.gate2 = rom_alloc<uint8_t>(L, (size_t)B * (d.ngate ? d.ngate : 1));
     w.active = rom_alloc<int>(L, B);
@@ -699,10 +721,120 @@ static int rom_work_alloc(mb_rom* R, int B, int ncol) {
     w.counts = rom_alloc<int>(L, 4);
     w.its = rom_alloc<long long>(L, B);
     w.flips = rom_alloc<long long>(L, B);
-    w.V = rom_alloc<double>(L, (size_t)B * ncol);
-    w.S = rom_alloc<double>(L, (size_t)B * ncol);
+    w.V = rom_alloc<double>(L, (size_t)B);
+    w.S = rom_alloc<double>(L, (size_t)B);
     for (void* p : L)
         if (!p) { rom_work_free(w); return MB_ENOMEM; }
+    return MB_OK;
+}
+
+// ------------------------------------------------------------ slot batch
+// A batch of B slots; an empty slot is marked failed and skipped by every
+// kernel.  Each occupied slot advances one time step per rom_batch_step.
+int rom_batch_alloc(mb_rom* R, int B) {
+    int rc = rom_work_alloc(R, B);
+    if (rc) return rc;
+    RomWork& w = R->w;
+    cudaStream_t s = R->cell->stream;
+    std::vector<int> ones(B, 1);
+    MB_CUDA(cudaMemcpyAsync(w.failed, ones.data(), 4 * B, cudaMemcpyHostToDevice, s));
+    MB_CUDA(cudaMemsetAsync(w.a, 0, 8 * (size_t)B * R->d.Nr, s));
+    MB_CUDA(cudaMemsetAsync(w.prm, 0, 8 * (size_t)B * RP, s));
+    MB_CUDA(cudaMemsetAsync(w.gate, 0, (size_t)B * (R->d.ngate ? R->d.ngate : 1), s));
+    MB_CUDA(cudaMemsetAsync(w.its, 0, 8 * B, s));
+    MB_CUDA(cudaMemsetAsync(w.flips, 0, 8 * B, s));
+    MB_CUDA(cudaStreamSynchronize(s));
+    return MB_OK;
+}
+
+int rom_slot_start(mb_rom* R, int b, const mb_rom_params& p, double dt) {
+    RomWork& w = R->w;
+    k_rom_slot_start<<<1, 128, 0, R->cell->stream>>>(R->d, b, p.I_app, p.s_i0, p.k_pl, 1.0 / dt, w.a, w.prm,
+                                                     w.failed, w.its, w.flips), count_launch(R->cell);
+    MB_CUDA_LAUNCH("rom_slot_start");
+    return MB_OK;
+}
+
+int rom_slot_clear(mb_rom* R, int b) {
+    int one = 1;
+    MB_CUDA(cudaMemcpyAsync(R->w.failed + b, &one, 4, cudaMemcpyHostToDevice, R->cell->stream));
+    MB_CUDA(cudaStreamSynchronize(R->cell->stream));
+    return MB_OK;
+}
+
+// current outputs of every slot (host arrays of B)
+int rom_batch_outputs(mb_rom* R, double* hV, double* hS, int* hfailed) {
+    RomWork& w = R->w;
+    cudaStream_t s = R->cell->stream;
+    const int B = w.B;
+    k_rom_outputs<<<(unsigned)((B + 255) / 256), 256, 0, s>>>(R->d, B, w.a, w.V, w.S), count_launch(R->cell);
+    MB_CUDA(cudaMemcpyAsync(hV, w.V, 8 * B, cudaMemcpyDeviceToHost, s));
+    MB_CUDA(cudaMemcpyAsync(hS, w.S, 8 * B, cudaMemcpyDeviceToHost, s));
+    if (hfailed) MB_CUDA(cudaMemcpyAsync(hfailed, w.failed, 4 * B, cudaMemcpyDeviceToHost, s));
+    MB_CUDA(cudaStreamSynchronize(s));
+    return MB_OK;
+}
+
+int rom_slot_stats(mb_rom* R, int b, long long* its, long long* flips, double* a) {
+    cudaStream_t s = R->cell->stream;
+    if (its) MB_CUDA(cudaMemcpyAsync(its, R->w.its + b, 8, cudaMemcpyDeviceToHost, s));
+    if (flips) MB_CUDA(cudaMemcpyAsync(flips, R->w.flips + b, 8, cudaMemcpyDeviceToHost, s));
+    if (a) MB_CUDA(cudaMemcpyAsync(a, R->w.a + (size_t)b * R->d.Nr, 8 * R->d.Nr, cudaMemcpyDeviceToHost, s));
+    MB_CUDA(cudaStreamSynchronize(s));
+    return MB_OK;
+}
+
+// one implicit Euler step of every occupied slot (reduced Newton with the
+// plating active-set passes); a slot whose Newton iteration fails is marked
+// failed (and skipped from then on)
+int rom_batch_step(mb_rom* R) {
+    mb_cell* c = R->cell;
+    cudaStream_t s = c->stream;
+    const RomDev& d = R->d;
+    RomWork& w = R->w;
+    const int B = w.B;
+    const unsigned nb = (unsigned)(((int64_t)B * d.Nr + 255) / 256);
+    const unsigned bb = (unsigned)((B + 255) / 256);
+    const double n_thr = GATE_N_REL * c->P.nc;
+    const dim3 gg((unsigned)((d.nloc + 255) / 256), (unsigned)B);
+    const unsigned ge = (unsigned)(((int64_t)d.M * B + 127) / 128);
+    const unsigned gt = (unsigned)(((int64_t)(d.ngate ? d.ngate : 1) * B + 255) / 256);
+    int hcount = 0;
+    k_rom_copy<<<nb, 256, 0, s>>>(d.Nr, B, nullptr, w.a, w.a_old), count_launch(c);
+    k_rom_gather<<<gg, 256, 0, s>>>(d, w.a_old, w.uloc_old), count_launch(c);
+    if (d.ngate) k_rom_gate<<<gt, 256, 0, s>>>(d, B, w.uloc_old, w.uloc_old, n_thr, w.gate), count_launch(c);
+    k_rom_set_active<<<bb, 256, 0, s>>>(B, nullptr, w.failed, w.pass_on), count_launch(c);
+    for (int pass = 1; pass <= ROM_PASSES; ++pass) {
+        k_rom_copy<<<nb, 256, 0, s>>>(d.Nr, B, w.pass_on, w.a_old, w.a), count_launch(c);
+        k_rom_set_active<<<bb, 256, 0, s>>>(B, w.pass_on, w.failed, w.active), count_launch(c);
+        for (int it = 0; it < ROM_MAXIT; ++it) {
+            k_rom_gather<<<gg, 256, 0, s>>>(d, w.a, w.uloc), count_launch(c);
+            if (d.M) {
+                k_rom_ei<<<ge, 128, 0, s>>>(d, c->P, B, w.uloc, w.gate, w.prm, w.active, w.f, w.G), count_launch(c);
+                k_rom_gu<<<dim3((unsigned)d.M, (unsigned)B), 128, 0, s>>>(d, w.G, w.active, w.GU), count_launch(c);
+            }
+            k_rom_jac<<<dim3((unsigned)d.Nr, (unsigned)B), 128, 0, s>>>(d, w.prm, w.GU, w.active, w.J), count_launch(c);
+            k_rom_resid<<<(unsigned)B, 128, 0, s>>>(d, w.a, w.a_old, w.prm, w.f, w.active, w.r), count_launch(c);
+            k_rom_lu<<<(unsigned)B, 256, 0, s>>>(d.Nr, w.J, w.r, w.active, w.delta), count_launch(c);
+            k_rom_update<<<(unsigned)B, 256, 0, s>>>(d, w.a, w.delta, w.active, w.failed, w.its), count_launch(c);
+            k_rom_count<<<1, 256, 0, s>>>(B, w.active, w.counts), count_launch(c);
+            MB_CUDA(cudaMemcpyAsync(&hcount, w.counts, 4, cudaMemcpyDeviceToHost, s));
+            MB_CUDA(cudaStreamSynchronize(s));
+            if (hcount == 0) break;
+        }
+        // instances still iterating after the iteration limit have failed
+        k_rom_fail_active<<<bb, 256, 0, s>>>(B, w.active, w.failed), count_launch(c);
+        if (!d.ngate) break;
+        k_rom_gather<<<gg, 256, 0, s>>>(d, w.a, w.uloc), count_launch(c);
+        k_rom_gate<<<gt, 256, 0, s>>>(d, B, w.uloc, w.uloc_old, n_thr, w.gate2), count_launch(c);
+        k_rom_flips<<<(unsigned)B, 256, 0, s>>>(d.ngate, B, w.gate, w.gate2, w.failed, w.pass_on, w.flips, w.gate,
+                                               pass == ROM_PASSES ? 1 : 0), count_launch(c);
+        k_rom_count<<<1, 256, 0, s>>>(B, w.pass_on, w.counts), count_launch(c);
+        MB_CUDA(cudaMemcpyAsync(&hcount, w.counts, 4, cudaMemcpyDeviceToHost, s));
+        MB_CUDA(cudaStreamSynchronize(s));
+        if (hcount == 0) break;
+    }
+    MB_CUDA_LAUNCH("rom_step");
     return MB_OK;
 }
 
@@ -752,96 +884,28 @@ extern "C" int mb_rom_solve_batch(mb_rom* R, int B, const mb_rom_params* prm, in
         set_error("mb_rom_solve_batch: invalid argument");
         return MB_EINVAL;
     }
-    mb_cell* c = R->cell;
-    cudaStream_t s = c->stream;
-    const RomDev& d = R->d;
     const int ncol = n_steps + 1;
-    int rc = rom_work_alloc(R, B, ncol);
+    int rc = rom_batch_alloc(R, B);
     if (rc) { set_error("mb_rom_solve_batch: device memory"); return rc; }
-    RomWork& w = R->w;
-    std::vector<double> hp((size_t)B * 3);
-    for (int b = 0; b < B; ++b) {
-        hp[3 * b] = prm[b].I_app;
-        hp[3 * b + 1] = prm[b].s_i0;
-        hp[3 * b + 2] = prm[b].k_pl;
-    }
-    MB_CUDA(cudaMemcpyAsync(w.prm, hp.data(), 8 * hp.size(), cudaMemcpyHostToDevice, s));
-    MB_CUDA(cudaMemsetAsync(w.failed, 0, 4 * B, s));
-    MB_CUDA(cudaMemsetAsync(w.its, 0, 8 * B, s));
-    MB_CUDA(cudaMemsetAsync(w.flips, 0, 8 * B, s));
-    MB_CUDA(cudaMemsetAsync(w.gate, 0, (size_t)B * (d.ngate ? d.ngate : 1), s));
-    const unsigned nb = (unsigned)(((int64_t)B * d.Nr + 255) / 256);
-    const unsigned bb = (unsigned)((B + 255) / 256);
-    k_rom_init<<<nb, 256, 0, s>>>(d, B, w.a), count_launch(c);
-    k_rom_outputs<<<bb, 256, 0, s>>>(d, B, w.a, w.failed, 0, ncol, w.V, w.S), count_launch(c);
-    const double dt_inv = 1.0 / dt;
-    const double n_thr = GATE_N_REL * c->P.nc;
-    const dim3 gg((unsigned)((d.nloc + 255) / 256), (unsigned)B);
-    const unsigned ge = (unsigned)(((int64_t)d.M * B + 127) / 128);
-    const unsigned gt = (unsigned)(((int64_t)(d.ngate ? d.ngate : 1) * B + 255) / 256);
-    int hcount = 0;
-    for (int step = 1; step <= n_steps; ++step) {
-        k_rom_copy<<<nb, 256, 0, s>>>(d.Nr, B, nullptr, w.a, w.a_old), count_launch(c);
-        k_rom_gather<<<gg, 256, 0, s>>>(d, w.a_old, w.uloc_old), count_launch(c);
-        if (d.ngate) k_rom_gate<<<gt, 256, 0, s>>>(d, B, w.uloc_old, w.uloc_old, n_thr, w.gate), count_launch(c);
-        k_rom_set_active<<<bb, 256, 0, s>>>(B, nullptr, w.failed, w.pass_on), count_launch(c);
-        for (int pass = 1; pass <= ROM_PASSES; ++pass) {
-            k_rom_copy<<<nb, 256, 0, s>>>(d.Nr, B, w.pass_on, w.a_old, w.a), count_launch(c);
-            k_rom_set_active<<<bb, 256, 0, s>>>(B, w.pass_on, w.failed, w.active), count_launch(c);
-            for (int it = 0; it < ROM_MAXIT; ++it) {
-                k_rom_gather<<<gg, 256, 0, s>>>(d, w.a, w.uloc), count_launch(c);
-                if (d.M) {
-                    k_rom_ei<<<ge, 128, 0, s>>>(d, c->P, B, w.uloc, w.gate, w.prm, w.active, w.f, w.G), count_launch(c);
-                    k_rom_gu<<<dim3((unsigned)d.M, (unsigned)B), 128, 0, s>>>(d, w.G, w.active, w.GU), count_launch(c);
-                }
-                k_rom_jac<<<dim3((unsigned)d.Nr, (unsigned)B), 128, 0, s>>>(d, dt_inv, w.GU, w.active, w.J), count_launch(c);
-                k_rom_resid<<<(unsigned)B, 128, 0, s>>>(d, dt_inv, w.a, w.a_old, w.prm, w.f, w.active, w.r), count_launch(c);
-                k_rom_lu<<<(unsigned)B, 256, 0, s>>>(d.Nr, w.J, w.r, w.active, w.delta), count_launch(c);
-                k_rom_update<<<(unsigned)B, 256, 0, s>>>(d, w.a, w.delta, w.active, w.failed, w.its), count_launch(c);
-                k_rom_count<<<1, 256, 0, s>>>(B, w.active, w.counts), count_launch(c);
-                MB_CUDA(cudaMemcpyAsync(&hcount, w.counts, 4, cudaMemcpyDeviceToHost, s));
-                MB_CUDA(cudaStreamSynchronize(s));
-                if (hcount == 0) break;
-            }
-            // instances still iterating after the iteration limit have failed
-            {
-                std::vector<int> act(B), fl(B);
-                MB_CUDA(cudaMemcpyAsync(act.data(), w.active, 4 * B, cudaMemcpyDeviceToHost, s));
-                MB_CUDA(cudaMemcpyAsync(fl.data(), w.failed, 4 * B, cudaMemcpyDeviceToHost, s));
-                MB_CUDA(cudaStreamSynchronize(s));
-                bool any = false;
-                for (int b = 0; b < B; ++b)
-                    if (act[b]) { fl[b] = 1; any = true; }
-                if (any) MB_CUDA(cudaMemcpyAsync(w.failed, fl.data(), 4 * B, cudaMemcpyHostToDevice, s));
-                MB_CUDA(cudaStreamSynchronize(s));
-            }
-            if (!d.ngate) break;
-            k_rom_gather<<<gg, 256, 0, s>>>(d, w.a, w.uloc), count_launch(c);
-            k_rom_gate<<<gt, 256, 0, s>>>(d, B, w.uloc, w.uloc_old, n_thr, w.gate2), count_launch(c);
-            k_rom_flips<<<(unsigned)B, 256, 0, s>>>(d.ngate, B, w.gate, w.gate2, w.failed, w.pass_on, w.flips, w.gate,
-                                                   pass == ROM_PASSES ? 1 : 0), count_launch(c);
-            k_rom_count<<<1, 256, 0, s>>>(B, w.pass_on, w.counts), count_launch(c);
-            MB_CUDA(cudaMemcpyAsync(&hcount, w.counts, 4, cudaMemcpyDeviceToHost, s));
-            MB_CUDA(cudaStreamSynchronize(s));
-            if (hcount == 0) break;
+    for (int b = 0; b < B; ++b)
+        if ((rc = rom_slot_start(R, b, prm[b], dt))) return rc;
+    std::vector<double> hV(B), hS(B);
+    std::vector<int> hf(B);
+    for (int step = 0; step <= n_steps; ++step) {
+        if (step > 0 && (rc = rom_batch_step(R))) return rc;
+        if ((rc = rom_batch_outputs(R, hV.data(), hS.data(), hf.data()))) return rc;
+        for (int b = 0; b < B; ++b) {
+            V_out[(size_t)b * ncol + step] = hf[b] ? NAN : hV[b];
+            sac_out[(size_t)b * ncol + step] = hf[b] ? NAN : hS[b];
         }
-        k_rom_outputs<<<bb, 256, 0, s>>>(d, B, w.a, w.failed, step, ncol, w.V, w.S), count_launch(c);
     }
-    MB_CUDA_LAUNCH("rom_solve");
-    MB_CUDA(cudaMemcpyAsync(V_out, w.V, 8 * (size_t)B * ncol, cudaMemcpyDeviceToHost, s));
-    MB_CUDA(cudaMemcpyAsync(sac_out, w.S, 8 * (size_t)B * ncol, cudaMemcpyDeviceToHost, s));
-    if (a_final) MB_CUDA(cudaMemcpyAsync(a_final, w.a, 8 * (size_t)B * d.Nr, cudaMemcpyDeviceToHost, s));
-    std::vector<long long> its(B), flips(B);
-    std::vector<int> fl(B);
-    MB_CUDA(cudaMemcpyAsync(its.data(), w.its, 8 * B, cudaMemcpyDeviceToHost, s));
-    MB_CUDA(cudaMemcpyAsync(flips.data(), w.flips, 8 * B, cudaMemcpyDeviceToHost, s));
-    MB_CUDA(cudaMemcpyAsync(fl.data(), w.failed, 4 * B, cudaMemcpyDeviceToHost, s));
-    MB_CUDA(cudaStreamSynchronize(s));
     mb_rom_info inf{0, 0, 0};
     for (int b = 0; b < B; ++b) {
-        inf.newton_its += its[b];
-        inf.flips += flips[b];
-        inf.failed += fl[b] ? 1 : 0;
+        long long its = 0, flips = 0;
+        if ((rc = rom_slot_stats(R, b, &its, &flips, a_final ? a_final + (size_t)b * R->d.Nr : nullptr))) return rc;
+        inf.newton_its += its;
+        inf.flips += flips;
+        inf.failed += hf[b] ? 1 : 0;
     }
     if (info) *info = inf;
     if (inf.failed) {
