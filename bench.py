@@ -180,6 +180,115 @@ def run_reference(args):
     print(json.dumps(out))
 
 
+ROM_CELL = "cell16x16x48"
+ROM_DIMS = (60, 30, 30, 200, 150)     # POD c, plated Li, phi; EI interface, migration
+
+
+def _rom_params(rng, n, i1):
+    """Parameter instances of the reduced-model study: C-rate ~ U(0.5, 5) (charge),
+    exchange-current scale ~ LogU(0.5, 2), plating rate scale ~ LogU(0.1, 10)."""
+    c = rng.uniform(0.5, 5.0, n)
+    s = np.exp(rng.uniform(np.log(0.5), np.log(2.0), n))
+    k = np.exp(rng.uniform(np.log(0.1), np.log(10.0), n))
+    return [(-ci * i1, si, ki) for ci, si, ki in zip(c, s, k)]
+
+
+def rom_and_serve(B, params, args, torch):
+    """Reduced model built from the 16x16x48 cell (snapshots at three corners
+    of the parameter box over the --rom-steps horizon), a timed batched solve of
+    --rom-instances instances over --rom-steps steps, its cell-potential error
+    against full-order runs of two instances, and a serving run with Poisson
+    arrivals (95 % reduced requests of 20-100 steps, 5 % full-order 10-step
+    validation solves on the same cell) at 0.8 of the measured reduced capacity."""
+    labels = workload_labels(ROM_CELL)
+    opts = B.default_opts(precision=B.PREC_MIXED, newton_tol=1e-10, krylov_rtol=1e-5, max_halvings=3)
+    cell = B.Cell(labels, 1e-6, params, opts)
+    i1 = cell.i_1c
+    t0 = time.perf_counter()
+    snap = [(-0.5 * i1, 0.5, 0.1), (-5.0 * i1, 2.0, 10.0), (-2.0 * i1, 1.0, 1.0)]
+    rom = B.Rom.build(cell, snap, 1.0, args.rom_steps, ROM_DIMS, pod_tol=1e-7)
+    build_s = time.perf_counter() - t0
+    rng = np.random.default_rng(41)
+    prm = _rom_params(rng, args.rom_instances, i1)
+    rom.solve(prm[:8], 2, 1.0)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    out = rom.solve(prm, args.rom_steps, 1.0)
+    wall = time.perf_counter() - t0
+    inst_steps = args.rom_instances * args.rom_steps
+    # cell-potential error of two instances against full-order runs
+    errs = []
+    for b in range(2):
+        fc = B.Cell(labels, 1e-6, params, opts)
+        fc.set_scales(prm[b][1], prm[b][2])
+        V = []
+        for _ in range(args.rom_steps):
+            V.append(fc.step(1.0, prm[b][0])["V_cell"])
+        fc.close()
+        V = np.array(V)
+        errs.append(float(np.max(np.abs(out["V"][b][1:] - V)) / np.max(np.abs(V))))
+    rom_res = {"workload": "ROM of the %s cell, snapshots at (C-rate, i0 scale, k_pl) = (0.5, 0.5, 0.1), "
+                           "(5, 2, 10), (2, 1, 1), %d steps each" % (ROM_CELL, args.rom_steps),
+               "dims": {"n_r": rom.n_r, "ei_interface": rom.n_bv, "ei_migration": rom.n_1c,
+                        "requested": list(ROM_DIMS)},
+               "instances": args.rom_instances, "steps": args.rom_steps, "dt_s": 1.0, "precision": "f64",
+               "instance_steps_per_s": inst_steps / wall, "solves_per_s": args.rom_instances / wall,
+               "wall_s": wall, "build_s": build_s, "newton_its_per_instance_step": out["newton_its"] / inst_steps,
+               "failed": out["failed"], "V_rel_err_vs_full_order_2_instances": errs}
+    # serving at 0.8 of the reduced capacity (requests of 60 steps on average)
+    cap = inst_steps / wall / 60.0
+    rate = 0.8 * cap
+    srv = B.Server(rom=rom, labels=labels, params=params, fom_opts=opts, rom_slots=256, fom_workers=4)
+    rng = np.random.default_rng(51)
+    n_req = args.serve_requests
+    gaps = rng.exponential(1.0 / rate, n_req)
+    kinds = rng.random(n_req) < 0.95
+    lens = rng.integers(20, 101, n_req)
+    sprm = _rom_params(rng, n_req, i1)
+    tickets = []
+    t0 = time.perf_counter()
+    t_next = t0
+    pending = {}
+    done = {}
+    for k in range(n_req):
+        t_next += gaps[k]
+        while time.perf_counter() < t_next:
+            for t in list(pending):
+                r = srv.poll(t)
+                if r is not None:
+                    done[t] = (pending.pop(t), r)
+            time.sleep(0.0005)
+        if kinds[k]:
+            t = srv.submit(B.REQ_ROM, sprm[k][0], sprm[k][1], sprm[k][2], int(lens[k]), 1.0)
+            pending[t] = "rom"
+        else:
+            t = srv.submit(B.REQ_FOM, sprm[k][0], sprm[k][1], sprm[k][2], 10, 1.0)
+            pending[t] = "fom"
+    while pending:
+        for t in list(pending):
+            r = srv.poll(t)
+            if r is not None:
+                done[t] = (pending.pop(t), r)
+        time.sleep(0.0005)
+    total = time.perf_counter() - t0
+    srv.close()
+    lat = {"rom": [], "fom": []}
+    bad = 0
+    for kind, r in done.values():
+        lat[kind].append(1000.0 * (r["t_done"] - r["t_submit"]))
+        bad += r["status"] != 0
+    serve = {"requests": n_req, "rom_fraction": 0.95, "arrival_rate_per_s": rate,
+             "capacity_estimate_per_s": cap, "throughput_per_s": n_req / total, "wall_s": total,
+             "failed": int(bad), "rom_slots": 256, "fom_workers": 4,
+             "p50_ms": {k: float(np.percentile(v, 50)) if v else None for k, v in lat.items()},
+             "p99_ms": {k: float(np.percentile(v, 99)) if v else None for k, v in lat.items()},
+             "workload": "Poisson arrivals; reduced requests of U{20..100} steps with the study's parameter "
+                         "distribution; full-order requests: 10 steps on the %s cell" % ROM_CELL}
+    rom.close()
+    cell.close()
+    return rom_res, serve
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -190,6 +299,10 @@ def main():
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--no-rom", action="store_true", help="skip the reduced-model and serving measurements")
+    ap.add_argument("--rom-instances", type=int, default=1024)
+    ap.add_argument("--rom-steps", type=int, default=60)
+    ap.add_argument("--serve-requests", type=int, default=1000)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -282,6 +395,11 @@ def main():
                           "gbs": (v[2] / (v[1] / max(v[0], 1) / 1000.0) / 1e9) if v[0] else None}
                       for k, v in kinds.items()}}
 
+    cell.close()
+    rom = serve = None
+    if rank == 0 and ws == 1 and not args.no_rom:
+        rom, serve = rom_and_serve(B, params, args, torch)
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         v, wall, sample = oracle_sample(labels, params, np.sign(CRATE[args.workload]))
@@ -299,9 +417,9 @@ def main():
                "cpu_baseline": cpu,
                "solver": {"newton_its": [i["newton_its"] for i in infos], "krylov_its": [i["krylov_its"] for i in infos],
                           "V_cell": infos[-1]["V_cell"], "precond_ms": ms_pc, "precond_calls": n_pc,
-                          "residual_ms": ms_res, "residual_calls": n_res}}
+                          "residual_ms": ms_res, "residual_calls": n_res},
+               "rom": rom, "serve": serve}
         print(json.dumps(out))
-    cell.close()
     if dist is not None:
         dist.destroy_process_group()
 

@@ -331,8 +331,19 @@ inline unsigned nbk(int64_t n) { return (unsigned)((n + 255) / 256); }
 
 }  // namespace
 
+// D[:, k] = S[:, k] - S[:, 0]
+__global__ void k_sub_first(int64_t L, int K, const double* __restrict__ S, double* __restrict__ D) {
+    const int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int k = blockIdx.y;
+    if (l < L) D[(int64_t)k * L + l] = S[(int64_t)k * L + l] - S[l];
+}
+
 // W-orthonormal POD modes (column-major L x r on the device) of the snapshot
-// block S (column-major L x K on the device) with weights w (device, L).
+// block S (column-major L x K on the device, column 0 the initial state) with
+// weights w (device, L): the initial state's direction first, then the POD
+// modes of the snapshots' differences from it (the same span as the
+// snapshots; the differences' Gram matrix resolves their singular values,
+// which the large common part would push below the Gram route's precision).
 static int pod_block(mb_cell* c, Dev& dv, int64_t L, int K, const double* S, const double* w, int rmax, double tol,
                      double** modes, int* r_out) {
     cudaStream_t s = c->stream;
@@ -340,8 +351,22 @@ static int pod_block(mb_cell* c, Dev& dv, int64_t L, int K, const double* S, con
     *modes = nullptr;
     if (L == 0 || K == 0 || rmax <= 0) return MB_OK;
     double* G = dv.alloc<double>((size_t)K * K);
-    if (!G) return MB_ENOMEM;
+    double* Dif = dv.alloc<double>((size_t)L * K);
+    double* n0 = dv.alloc<double>(1);
+    if (!G || !Dif || !n0) return MB_ENOMEM;
     dim3 gb((K + GT - 1) / GT, (K + GT - 1) / GT), tb(GT, GT);
+    // is the initial state nonzero in this block?
+    k_atwb<<<dim3(1, 1), tb, 0, s>>>(L, 1, 1, S, S, w, n0), count_launch(c);
+    double h0 = 0.0;
+    MB_CUDA(cudaMemcpyAsync(&h0, n0, 8, cudaMemcpyDeviceToHost, s));
+    MB_CUDA(cudaStreamSynchronize(s));
+    const bool anchor = h0 > 0.0;
+    const double* S0 = S;   // column 0: the initial state
+    if (anchor) {
+        k_sub_first<<<dim3(nbk(L), K), 256, 0, s>>>(L, K, S, Dif), count_launch(c);
+        S = Dif;
+        rmax -= 1;
+    }
     k_atwb<<<gb, tb, 0, s>>>(L, K, K, S, S, w, G), count_launch(c);
     std::vector<double> hG((size_t)K * K);
     MB_CUDA(cudaMemcpyAsync(hG.data(), G, 8 * hG.size(), cudaMemcpyDeviceToHost, s));
@@ -352,21 +377,27 @@ static int pod_block(mb_cell* c, Dev& dv, int64_t L, int K, const double* S, con
     for (int i = 0; i < K; ++i) order[i] = i;
     std::sort(order.begin(), order.end(), [&](int a, int b) { return ev[a] > ev[b]; });
     const double l1 = ev[order[0]];
-    if (!(l1 > 0)) return MB_OK;
-    int r = 0;
-    while (r < rmax && r < K && ev[order[r]] > tol * tol * l1) ++r;
-    std::vector<double> X((size_t)K * r);
-    for (int j = 0; j < r; ++j) {
+    int rd = 0;
+    if (l1 > 0)
+        while (rd < rmax && rd < K && ev[order[rd]] > tol * tol * l1) ++rd;
+    const int a0 = anchor ? 1 : 0;
+    int r = rd + a0;
+    if (r == 0) return MB_OK;
+    std::vector<double> X((size_t)K * (rd ? rd : 1));
+    for (int j = 0; j < rd; ++j) {
         const double sc = 1.0 / sqrt(ev[order[j]]);
-        for (int k = 0; k < K; ++k) X[(size_t)k * r + j] = V[(size_t)k * K + order[j]] * sc;
+        for (int k = 0; k < K; ++k) X[(size_t)k * rd + j] = V[(size_t)k * K + order[j]] * sc;
     }
-    double* dX = dv.alloc<double>((size_t)K * r);
+    double* dX = dv.alloc<double>(X.size());
     double* Y = dv.alloc<double>((size_t)L * r);
     double* Y2 = dv.alloc<double>((size_t)L * r);
     double* Gm = dv.alloc<double>((size_t)r * r);
     if (!dX || !Y || !Y2 || !Gm) return MB_ENOMEM;
-    MB_CUDA(cudaMemcpyAsync(dX, X.data(), 8 * X.size(), cudaMemcpyHostToDevice, s));
-    k_sx<<<dim3(nbk(L), r), 256, 0, s>>>(L, K, r, S, dX, Y), count_launch(c);
+    if (anchor) MB_CUDA(cudaMemcpyAsync(Y, S0, 8 * L, cudaMemcpyDeviceToDevice, s));
+    if (rd) {
+        MB_CUDA(cudaMemcpyAsync(dX, X.data(), 8 * X.size(), cudaMemcpyHostToDevice, s));
+        k_sx<<<dim3(nbk(L), rd), 256, 0, s>>>(L, K, rd, S, dX, Y + (size_t)a0 * L), count_launch(c);
+    }
     // two Cholesky passes: Y <- Y L^-T with L L^T = Y^T W Y
     for (int pass = 0; pass < 2; ++pass) {
         dim3 gr((r + GT - 1) / GT, (r + GT - 1) / GT);
