@@ -124,10 +124,10 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
-def jvp_traffic(workload, mode):
-    """DRAM bytes per launch of the JVP in the given mode from the committed
-    ncu summary, or None."""
-    path = os.path.join(ROOT, "profiles", "k_jvp_lin__%s.json" % workload)
+def kernel_traffic(kernel, workload, mode):
+    """DRAM bytes per launch of a kernel in the given mode from the committed
+    ncu summary (profiles/<kernel>__<workload>.json), or None."""
+    path = os.path.join(ROOT, "profiles", "%s__%s.json" % (kernel, workload))
     try:
         with open(path) as f:
             return float(json.load(f)["dram_bytes_per_launch"][mode])
@@ -298,6 +298,8 @@ def main():
     ap.add_argument("--workload", default="cell128x128x256")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--fp32-coarse", action="store_true",
+                    help="coarse-level products from FP32 operators instead of their BF16 copies")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-rom", action="store_true", help="skip the reduced-model and serving measurements")
     ap.add_argument("--rom-instances", type=int, default=1024)
@@ -319,7 +321,8 @@ def main():
     labels = workload_labels(args.workload)
     prec = B.PREC_MIXED if args.precision == "mixed" else B.PREC_FP64
     opts = B.default_opts(precision=prec, newton_tol=1e-9, krylov_rtol=1e-4 if prec else 1e-6,
-                          newton_maxit=20, krylov_maxit=300, max_halvings=3)
+                          newton_maxit=20, krylov_maxit=300, max_halvings=3,
+                          mg_bf16=0 if args.fp32_coarse else 1)
     cell = B.Cell(labels, 1e-6, params, opts)
     I = CRATE[args.workload] * cell.i_1c
     dt = 1.0
@@ -350,6 +353,7 @@ def main():
     n_res, ms_res = cell.prof_read(B.Cell.PROF_RESIDUAL)
     n_pc, ms_pc = cell.prof_read(B.Cell.PROF_PRECOND)
     n_sm, ms_sm = cell.prof_read(B.Cell.PROF_SMOOTH)
+    n_ls, ms_ls = cell.prof_read(B.Cell.PROF_LSMOOTH)
     cell.prof_enable(False)
     if dist is not None:
         t = torch.tensor([ms], device="cuda", dtype=torch.float64)
@@ -373,22 +377,37 @@ def main():
     e2e = {"value": ws * args.e2e_steps * dt / e2e_wall, "unit": UNIT,
            "h2d_bytes_per_step": 8 * cell.n, "d2h_bytes_per_step": 8 * cell.n}
 
-    # roofline of the dominant kernel: the stencil JVP k_jvp_lin, launched as
-    # the fine smoother's S z (mode 1) and as the Krylov operator (mode 2)
+    # roofline of the dominant timed kernel: the stencil JVP k_jvp_lin, launched as
+    # the fine smoother's S z (mode 1) and as the Krylov operator (mode 2), or the
+    # level-1 smoothing sweep k_lvl_smooth of the K-cycle
     peak, peak_kind = measured_peaks()
     N, F, NI = cell.N, cell.F, cell.NI
+    cell_levels = cell.debug_levels()
     # algorithmic bytes per launch.  Per voxel: vcode 4 + FP32 c 4 + float-float direction (c, phi) 16
     # + FP32 result (c, phi) 8 (+ FP32 row scales (c, phi) 8 in mode 2).  Per interface face: six FP32
     # partials 24.  Per plating face: float-float direction 8 (+ FP32 result 4 + row scale 4 in mode 2).
-    kinds = {"smoother": (n_sm, ms_sm, 32.0 * N + 24.0 * NI + 8.0 * F, "k_jvp_lin<1> (fine smoother S z)"),
-             "operator": (n_jvp, ms_jvp, 40.0 * N + 24.0 * NI + 16.0 * F, "k_jvp_lin<2> (Krylov operator)")}
+    # Level-1 post-smoothing sweep, per coarse cell: the operator rows (six 4x4 couplings, the
+    # difference-form self block and the block inverse: 32 rows of four BF16 = 256 B, or 512 B in
+    # FP32) + right-hand side 16 + float-float iterate in 32 and out 32; one sweep in two also reads
+    # the prolonged level-2 correction (32 B per level-2 cell).
+    lv = cell_levels
+    c1 = lv[0][0] * lv[0][1] * lv[0][2]
+    c2 = lv[1][0] * lv[1][1] * lv[1][2] if len(lv) > 1 else 0
+    op_b = 256.0 if opts.mg_bf16 else 512.0
+    kinds = {"smoother": (n_sm, ms_sm, 32.0 * N + 24.0 * NI + 8.0 * F, "k_jvp_lin<1> (fine smoother S z)",
+                          "k_jvp_lin"),
+             "operator": (n_jvp, ms_jvp, 40.0 * N + 24.0 * NI + 16.0 * F, "k_jvp_lin<2> (Krylov operator)",
+                          "k_jvp_lin"),
+             "level1_smoother": (n_ls, ms_ls, (op_b + 80.0) * c1 + 32.0 * c2 / 2.0,
+                                 "k_lvl_smooth<%s> (level-1 post-smoothing sweep)" % ("true" if opts.mg_bf16 else "false"),
+                                 "k_lvl_smooth")}
     dom = max(kinds, key=lambda k: kinds[k][1])
-    n_k, ms_k, bytes_per_launch, kname = kinds[dom]
+    n_k, ms_k, bytes_per_launch, kname, kfile = kinds[dom]
     avg_ms = ms_k / max(n_k, 1)
     achieved = bytes_per_launch / (avg_ms / 1000.0) / 1e9 if n_k else None
     roof = {"kernel": kname, "bound": "hbm",
             "achieved": achieved, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
-            "frac": (achieved / peak) if achieved else None, "traffic": jvp_traffic(args.workload, dom),
+            "frac": (achieved / peak) if achieved else None, "traffic": kernel_traffic(kfile, args.workload, dom),
             "bytes_per_launch": bytes_per_launch, "launches": n_k, "avg_launch_ms": avg_ms,
             "share_of_step": ms_k / ms if ms else None,
             "other": {k: {"launches": v[0], "avg_launch_ms": v[1] / max(v[0], 1),
@@ -412,6 +431,7 @@ def main():
                "config": {"workload": args.workload, "voxels": int(cell.N), "plating_faces": int(cell.F),
                           "device_bytes": int(cell.device_bytes),
                           "dt_s": dt, "crate": CRATE[args.workload], "precision": args.precision,
+                          "coarse_operators": "fp32" if args.fp32_coarse else "bf16",
                           "l2": "working set > 129 MB L2, no flush", "parallelism": "replicas" if ws > 1 else "1 GPU"},
                "clocks": clk, "e2e": e2e, "gpu_launches": int(launches), "roofline": roof,
                "cpu_baseline": cpu,

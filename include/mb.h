@@ -78,6 +78,8 @@ typedef struct {
     int    mg_coarse_cells;/* multigrid: coarsen until at most this many cells */
     int    mg_smooth;      /* fine-level block-Jacobi sweeps before and after the coarse correction (1..8) */
     int    mg_kcycle;      /* FGMRES iterations of the level-1 K-cycle (1..16) */
+    int    mg_bf16;        /* 1: coarse-level smoothing, residuals and K-cycle products read BF16
+                              copies of the level operators (FP32 arithmetic); 0: FP32 operators */
 } mb_solver_opts;
 
 typedef struct {
@@ -163,6 +165,7 @@ int mb_jvp_f32_dev(mb_cell* cell, const float* u, const uint8_t* gate, double dt
 #define MB_PROF_RESIDUAL 1   /* FP64 residual kernel */
 #define MB_PROF_PRECOND  2   /* one whole preconditioner application (many kernels) */
 #define MB_PROF_SMOOTH   3   /* Jacobian-vector product kernel inside the fine-level smoother */
+#define MB_PROF_LSMOOTH  4   /* level-1 post-smoothing sweep (two per V-cycle of the K-cycle) */
 int mb_prof_enable(mb_cell* cell, int on);
 int mb_prof_read(mb_cell* cell, int kind, int64_t* count, double* total_ms);
 int mb_prof_reset(mb_cell* cell);

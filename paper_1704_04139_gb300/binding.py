@@ -38,7 +38,7 @@ class SolverOpts(C.Structure):
     _fields_ = [("precision", C.c_int), ("newton_tol", C.c_double), ("newton_maxit", C.c_int),
                 ("gmres_m", C.c_int), ("krylov_maxit", C.c_int), ("krylov_rtol", C.c_double),
                 ("max_passes", C.c_int), ("max_halvings", C.c_int), ("mg_coarse_cells", C.c_int),
-                ("mg_smooth", C.c_int), ("mg_kcycle", C.c_int)]
+                ("mg_smooth", C.c_int), ("mg_kcycle", C.c_int), ("mg_bf16", C.c_int)]
 
 
 class StepInfo(C.Structure):
@@ -282,7 +282,7 @@ class Cell:
         return out
 
     # kernel timing (CUDA events on the launching stream) and launch counting
-    PROF_JVP, PROF_RESIDUAL, PROF_PRECOND, PROF_SMOOTH = 0, 1, 2, 3
+    PROF_JVP, PROF_RESIDUAL, PROF_PRECOND, PROF_SMOOTH, PROF_LSMOOTH = 0, 1, 2, 3, 4
 
     def prof_enable(self, on=True):
         _check(lib().mb_prof_enable(self.h, 1 if on else 0))

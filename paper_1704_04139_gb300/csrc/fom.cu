@@ -601,7 +601,7 @@ template int launch_lin_setup<double>(mb_cell*, const double*, const uint8_t*, c
 // phases pays little for divergence.  scal: [0] 1/dt, [1 + phase]
 // 1/(V c_ref/dt), [7] 1/A, [8] dt/n_c.
 template <int MODE>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 4)
 k_jvp_lin(ParT<float> P, Dims D, const uint32_t* __restrict__ vc, const float* __restrict__ c32,
           const float* __restrict__ icoef, const float* __restrict__ rowinv, const float* __restrict__ scal,
           const float2* __restrict__ x, float* __restrict__ y_out) {

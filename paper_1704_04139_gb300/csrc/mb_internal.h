@@ -39,7 +39,8 @@ struct Krylov;    // FGMRES workspace (solver.cu)
 // launches of the timed kernel classes are bracketed by CUDA events recorded
 // on the launching stream; every kernel launch of the library increments the
 // cell's launch counter whether or not timing is enabled.
-enum ProfKernel { PROF_JVP = 0, PROF_RESIDUAL = 1, PROF_PRECOND = 2, PROF_SMOOTH = 3, PROF_NKERNELS = 4 };
+enum ProfKernel { PROF_JVP = 0, PROF_RESIDUAL = 1, PROF_PRECOND = 2, PROF_SMOOTH = 3, PROF_LSMOOTH = 4,
+                  PROF_NKERNELS = 5 };
 struct ProfPair {
     cudaEvent_t e0, e1;
     int kind;

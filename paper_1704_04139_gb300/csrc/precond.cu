@@ -25,7 +25,13 @@
 //    explicit FP64 inverse.
 // Precision: all arithmetic of the application is FP32; iterates and
 // corrections (z, coarse x, K-cycle directions) are float-float, residuals and
-// Krylov bases FP32, operators FP32.
+// Krylov bases FP32.  Coarse operators are assembled in FP32; with mg_bf16 the
+// smoothing, residual and K-cycle products read a BF16 copy (each 4x4 block
+// row packed as four BF16 in 8 bytes), which halves the dominant byte stream
+// of the coarse levels.  The difference form keeps their null space exact
+// under this rounding: constants per class are annihilated whatever the
+// couplings' values.
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdio.h>
@@ -94,6 +100,7 @@ struct Level {
     float* aself = nullptr;   // 16 x cells  self block ex - sum_d off_d (absent classes fixed up)
     float* sinv = nullptr;    // 16 x cells  inverse of the self block
     uint8_t* mask = nullptr;  // cells: classes present
+    uint2* pk = nullptr;      // 32 x cells  BF16 copy: rows of off_0..off_5, exd, sinv (4 BF16 per row)
     DF4* x = nullptr;         // cells
     DF4* x2 = nullptr;        // cells
     float4* b = nullptr;      // cells
@@ -125,6 +132,7 @@ struct Precond {
     double* cinv = nullptr;
     int* cstat = nullptr;
     int kcyc = 0;              // level-1 K-cycle length
+    bool b16 = false;          // applications read the BF16 operator copies
     int nu_fine = 0;           // fine-level block-Jacobi sweeps before and after the coarse correction
     // level-1 K-cycle workspace
     float* kV = nullptr;       // (KCYC_MAX+1) x m4  FP32 basis
@@ -516,6 +524,16 @@ __global__ void k_finalize(Level L) {
     }
     for (int k = 0; k < NCLS; ++k)
         for (int kk = 0; kk < NCLS; ++kk) L.sinv[(int64_t)(k * NCLS + kk) * L.cells + cell] = (float)a[k][NCLS + kk];
+    // BF16 copy, block q (0..5 off_d, 6 exd, 7 sinv), row k: pk[(4q + k) * cells + cell]
+    for (int q = 0; q < 8; ++q) {
+        const float* src = q < 6 ? L.off + (int64_t)q * BLK * L.cells : (q == 6 ? L.exd : L.sinv);
+        for (int k = 0; k < NCLS; ++k) {
+            uint32_t h[NCLS];
+            for (int kk = 0; kk < NCLS; ++kk)
+                h[kk] = __bfloat16_as_ushort(__float2bfloat16_rn(src[(int64_t)(k * NCLS + kk) * L.cells + cell]));
+            L.pk[(int64_t)(4 * q + k) * L.cells + cell] = make_uint2(h[0] | (h[1] << 16), h[2] | (h[3] << 16));
+        }
+    }
 }
 
 // ----------------------------------------------------- coarsest dense solve
@@ -597,7 +615,8 @@ __global__ void k_coarse_invert(int n, double* __restrict__ A, double* __restric
     }
 }
 
-// x = Ainv b (FP64 accumulation), one block; x stored float-float
+// x = Ainv b (FP64 accumulation), one block; x stored float-float.  One warp
+// per row (coalesced loads of Ainv), lane partial sums combined by shuffles.
 __global__ void k_coarse_solve(int n, const double* __restrict__ Ainv, const float4* __restrict__ b,
                                DF4* __restrict__ x) {
     __shared__ double sb[COARSE_MAX];
@@ -605,10 +624,12 @@ __global__ void k_coarse_solve(int n, const double* __restrict__ Ainv, const flo
     const float* bf = reinterpret_cast<const float*>(b);
     for (int i = threadIdx.x; i < n; i += blockDim.x) sb[i] = (double)bf[i];
     __syncthreads();
-    for (int r = threadIdx.x; r < n; r += blockDim.x) {
+    const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int r = threadIdx.x >> 5; r < n; r += nw) {
         double acc = 0.0;
-        for (int j = 0; j < n; ++j) acc += Ainv[(int64_t)r * n + j] * sb[j];
-        sx[r] = acc;
+        for (int j = lane; j < n; j += 32) acc += Ainv[(int64_t)r * n + j] * sb[j];
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+        if (lane == 0) sx[r] = acc;
     }
     __syncthreads();
     for (int cell = threadIdx.x; cell < n / NCLS; cell += blockDim.x)
@@ -625,6 +646,22 @@ __device__ inline float4 mv4(const float* __restrict__ m, int64_t st, float4 x) 
                        m[8 * st] * x.x + m[9 * st] * x.y + m[10 * st] * x.z + m[11 * st] * x.w,
                        m[12 * st] * x.x + m[13 * st] * x.y + m[14 * st] * x.z + m[15 * st] * x.w);
 }
+// the same product from the BF16 copy: row k of block q is one 8-byte word
+__device__ inline float bf_lo(uint32_t w) { return __uint_as_float(w << 16); }
+__device__ inline float bf_hi(uint32_t w) { return __uint_as_float(w & 0xffff0000u); }
+__device__ inline float bf_row(uint2 w, float4 x) {
+    return bf_lo(w.x) * x.x + bf_hi(w.x) * x.y + bf_lo(w.y) * x.z + bf_hi(w.y) * x.w;
+}
+__device__ inline float4 mv4b(const uint2* __restrict__ m, int64_t st, float4 x) {
+    return make_float4(bf_row(m[0], x), bf_row(m[st], x), bf_row(m[2 * st], x), bf_row(m[3 * st], x));
+}
+// block q of the level operator (0..5 off_d, 6 exd, 7 sinv) times x
+template <bool B16>
+__device__ inline float4 lvl_mv(const Level& L, int q, int64_t cell, float4 x) {
+    if (B16) return mv4b(L.pk + (int64_t)4 * q * L.cells + cell, L.cells, x);
+    const float* m = q < 6 ? L.off + (int64_t)q * BLK * L.cells : (q == 6 ? L.exd : L.sinv);
+    return mv4(m + cell, L.cells, x);
+}
 __device__ inline float4 f4add(float4 a, float4 b) { return make_float4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w); }
 __device__ inline float4 f4sub(float4 a, float4 b) { return make_float4(a.x - b.x, a.y - b.y, a.z - b.z, a.w - b.w); }
 __device__ inline float4 f4scale(float s, float4 a) { return make_float4(s * a.x, s * a.y, s * a.z, s * a.w); }
@@ -636,20 +673,40 @@ __device__ inline DF4 xeff(const DF4* x, const DF4* ec, int ccny, int ccnz, int 
     return r;
 }
 
-// A xe at one cell of level L in difference form (xe_i given)
-__device__ inline float4 cell_apply(const Level& L, const DF4* x, const DF4* ec, int ccny, int ccnz, int t, int y,
-                                    int z, int64_t cell, const DF4& xi) {
-    float4 acc = mv4(L.exd + cell, L.cells, df4_val(xi));
+// A xe at one cell of level L in difference form (xe_i given; xf(t, y, z, cell)
+// gives the neighbours' iterates).  Branch-free: a neighbour outside the
+// level is replaced by the cell itself, whose difference is exactly zero
+// (and whose coupling is zero: no face leaves the domain), so that all loads
+// of the cell can be in flight together.
+template <bool B16, class XF>
+__device__ inline float4 cell_apply_g(const Level& L, int t, int y, int z, int64_t cell, const DF4& xi, XF xf) {
+    float4 acc = lvl_mv<B16>(L, 6, cell, df4_val(xi));
+    const int64_t syz = (int64_t)L.ny * L.nz;
+    const bool inb[6] = {t > 0, t < L.nt - 1, y > 0, y < L.ny - 1, z > 0, z < L.nz - 1};
+    const int64_t st[6] = {-syz, syz, -(int64_t)L.nz, (int64_t)L.nz, -1, 1};
     const int dt_[6] = {-1, 1, 0, 0, 0, 0}, dy_[6] = {0, 0, -1, 1, 0, 0}, dz_[6] = {0, 0, 0, 0, -1, 1};
 #pragma unroll
     for (int d = 0; d < 6; ++d) {
-        int tt = t + dt_[d], yy = y + dy_[d], zz = z + dz_[d];
-        if (tt < 0 || tt >= L.nt || yy < 0 || yy >= L.ny || zz < 0 || zz >= L.nz) continue;
-        int64_t nb = ((int64_t)tt * L.ny + yy) * L.nz + zz;
-        acc = f4add(acc, mv4(L.off + (int64_t)d * BLK * L.cells + cell, L.cells,
-                                 df4_diff(xeff(x, ec, ccny, ccnz, tt, yy, zz, nb), xi)));
+        const int tt = inb[d] ? t + dt_[d] : t, yy = inb[d] ? y + dy_[d] : y, zz = inb[d] ? z + dz_[d] : z;
+        const int64_t nb = inb[d] ? cell + st[d] : cell;
+        acc = f4add(acc, lvl_mv<B16>(L, d, cell, df4_diff(xf(tt, yy, zz, nb), xi)));
     }
     return acc;
+}
+template <bool B16>
+__device__ inline float4 cell_apply(const Level& L, const DF4* x, const DF4* ec, int ccny, int ccnz, int t, int y,
+                                    int z, int64_t cell, const DF4& xi) {
+    return cell_apply_g<B16>(L, t, y, z, cell, xi, [&](int tt, int yy, int zz, int64_t nb) {
+        return xeff(x, ec, ccny, ccnz, tt, yy, zz, nb);
+    });
+}
+// the first sweep from zero, x1 = omega Sinv b, at one cell (float-float with a zero tail)
+template <bool B16>
+__device__ inline DF4 first_sweep(const Level& L, int64_t cell, float omega) {
+    DF4 o;
+    o.h = f4scale(omega, lvl_mv<B16>(L, 7, cell, L.b[cell]));
+    o.l = make_float4(0.f, 0.f, 0.f, 0.f);
+    return o;
 }
 
 __device__ inline void cell_coords(const Level& L, int64_t cell, int& t, int& y, int& z) {
@@ -659,6 +716,7 @@ __device__ inline void cell_coords(const Level& L, int64_t cell, int& t, int& y,
 }
 
 // x_out = xe + omega Sinv (b - A xe), xe = x_in (+ prolonged ec); both absent: x_out = omega Sinv b
+template <bool B16>
 __global__ void k_lvl_smooth(Level L, const DF4* __restrict__ x_in, const DF4* __restrict__ ec, int ccny,
                              int ccnz, float omega, DF4* __restrict__ x_out) {
     int64_t cell = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -666,7 +724,7 @@ __global__ void k_lvl_smooth(Level L, const DF4* __restrict__ x_in, const DF4* _
     int t, y, z;
     cell_coords(L, cell, t, y, z);
     if (!x_in && !ec) {
-        float4 c = f4scale(omega, mv4(L.sinv + cell, L.cells, L.b[cell]));
+        float4 c = f4scale(omega, lvl_mv<B16>(L, 7, cell, L.b[cell]));
         DF4 o;
         o.h = c;
         o.l = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -674,20 +732,38 @@ __global__ void k_lvl_smooth(Level L, const DF4* __restrict__ x_in, const DF4* _
         return;
     }
     DF4 xe = xeff(x_in, ec, ccny, ccnz, t, y, z, cell);
-    float4 r = f4sub(L.b[cell], cell_apply(L, x_in, ec, ccny, ccnz, t, y, z, cell, xe));
-    x_out[cell] = df4_add_f(xe, f4scale(omega, mv4(L.sinv + cell, L.cells, r)));
+    float4 r = f4sub(L.b[cell], cell_apply<B16>(L, x_in, ec, ccny, ccnz, t, y, z, cell, xe));
+    x_out[cell] = df4_add_f(xe, f4scale(omega, lvl_mv<B16>(L, 7, cell, r)));
 }
 
+// the first two sweeps from zero in one pass: x2 = x1 + omega Sinv (b - A x1)
+// with x1 = omega Sinv b evaluated where it is needed (the cell and its
+// neighbours), bit-identical to two k_lvl_smooth launches
+template <bool B16>
+__global__ void k_lvl_smooth2(Level L, float omega, DF4* __restrict__ x_out) {
+    int64_t cell = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (cell >= L.cells) return;
+    int t, y, z;
+    cell_coords(L, cell, t, y, z);
+    const DF4 x1 = first_sweep<B16>(L, cell, omega);
+    float4 r = f4sub(L.b[cell], cell_apply_g<B16>(L, t, y, z, cell, x1, [&](int, int, int, int64_t nb) {
+                         return first_sweep<B16>(L, nb, omega);
+                     }));
+    x_out[cell] = df4_add_f(x1, f4scale(omega, lvl_mv<B16>(L, 7, cell, r)));
+}
+
+template <bool B16>
 __global__ void k_lvl_matvec(Level L, const DF4* __restrict__ x, float4* __restrict__ y_out) {
     int64_t cell = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (cell >= L.cells) return;
     int t, y, z;
     cell_coords(L, cell, t, y, z);
-    y_out[cell] = cell_apply(L, x, nullptr, 0, 0, t, y, z, cell, x[cell]);
+    y_out[cell] = cell_apply<B16>(L, x, nullptr, 0, 0, t, y, z, cell, x[cell]);
 }
 
 // bc(parent) = sum over children of (b - A x): one thread per child (eight
 // consecutive threads per parent), summed by shuffles within the octet
+template <bool B16>
 __global__ void k_lvl_restrict(Level L, const DF4* __restrict__ x, Level C) {
     const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t cell = tid >> 3;
@@ -699,7 +775,7 @@ __global__ void k_lvl_restrict(Level L, const DF4* __restrict__ x, Level C) {
         int t = 2 * ct + (k >> 2), y = 2 * cy + ((k >> 1) & 1), z = 2 * cz + (k & 1);
         if (t < L.nt && y < L.ny && z < L.nz) {
             int64_t ch = ((int64_t)t * L.ny + y) * L.nz + z;
-            r = f4sub(L.b[ch], cell_apply(L, x, nullptr, 0, 0, t, y, z, ch, x[ch]));
+            r = f4sub(L.b[ch], cell_apply<B16>(L, x, nullptr, 0, 0, t, y, z, ch, x[ch]));
         }
     }
 #pragma unroll
@@ -779,6 +855,44 @@ __global__ void k_kupdate(const float* __restrict__ V, int64_t stride, int cnt, 
     float acc = 0.f;
     for (int j = 0; j < cnt; ++j) acc = fmaf(hs[j], V[j * stride + i], acc);
     w[i] = fmaf(sign, acc, w[i]);
+}
+
+// The two passes of classical Gram-Schmidt fused with the products that
+// follow them: w -= sum_j h[j] V_j (as k_kupdate), then the block partials of
+// the updated w against V_j, j < cnt (the second pass's coefficients) or, NORM,
+// against itself.  Same grid and summation order as k_kdot, so the results
+// equal the unfused sequence bit for bit.  cnt <= 8.
+template <bool NORM>
+__global__ void __launch_bounds__(RED_THREADS)
+k_kupd_dot(const float* __restrict__ V, int64_t stride, int cnt, const double* __restrict__ h,
+           float* __restrict__ w, int64_t n, double* partials) {
+    constexpr int K = NORM ? 1 : 8;
+    __shared__ float hs[8];
+    if (threadIdx.x < cnt) hs[threadIdx.x] = (float)h[threadIdx.x];
+    __syncthreads();
+    float acc32[K];
+#pragma unroll
+    for (int j = 0; j < K; ++j) acc32[j] = 0.f;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        float v[8];
+        float a = 0.f;
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+            if (j < cnt) {
+                v[j] = V[j * stride + i];
+                a = fmaf(hs[j], v[j], a);
+            }
+        const float wi = fmaf(-1.f, a, w[i]);
+        w[i] = wi;
+        if (NORM) {
+            acc32[0] = fmaf(wi, wi, acc32[0]);
+        } else {
+#pragma unroll
+            for (int j = 0; j < K; ++j)
+                if (j < cnt) acc32[j] = fmaf(v[j], wi, acc32[j]);
+        }
+    }
+    block_reduce_store_f32<K>(acc32, partials);
 }
 
 // out = a / sqrt(max(d2, tiny)) (the scale computed once per block)
@@ -880,7 +994,9 @@ int precond_create(mb_cell* c) {
         L.x = (DF4*)cell_alloc(c, sizeof(DF4) * (size_t)L.cells);
         L.x2 = (DF4*)cell_alloc(c, sizeof(DF4) * (size_t)L.cells);
         L.b = (float4*)cell_alloc(c, 16 * (size_t)L.cells);
-        if (!L.off || !L.ex || !L.exd || !L.aself || !L.sinv || !L.mask || !L.x || !L.x2 || !L.b) return MB_ENOMEM;
+        L.pk = (uint2*)cell_alloc(c, 8 * 32 * (size_t)L.cells);
+        if (!L.off || !L.ex || !L.exd || !L.aself || !L.sinv || !L.mask || !L.x || !L.x2 || !L.b || !L.pk)
+            return MB_ENOMEM;
         if (L.cells <= coarse_cells) break;
         if (nt == 1 && ny == 1 && nz == 1) break;
     }
@@ -925,6 +1041,7 @@ int precond_setup(mb_cell* c, const float* u32, const uint8_t* gate, double dt) 
     Precond* p = c->pc;
     p->kcyc = c->opt.mg_kcycle < 1 ? 1 : (c->opt.mg_kcycle > KCYC_MAX ? KCYC_MAX : c->opt.mg_kcycle);
     p->nu_fine = c->opt.mg_smooth < 1 ? 1 : (c->opt.mg_smooth > 8 ? 8 : c->opt.mg_smooth);
+    p->b16 = c->opt.mg_bf16 != 0;
     const Dims& D = c->D;
     cudaStream_t s = c->stream;
     k_bj_setup<<<pgrid(D.nt, D.ny, D.nz), PB, 0, s>>>(c->Pf, D, c->vcode, u32, gate, dt, c->s_i0, c->k_pl,
@@ -944,6 +1061,49 @@ int precond_setup(mb_cell* c, const float* u32, const uint8_t* gate, double dt) 
     return MB_OK;
 }
 
+// launches of the level kernels with the operator storage chosen at set-up
+static void lvl_smooth(mb_cell* c, Level& L, const DF4* xin, const DF4* ec, int ccny, int ccnz, DF4* xout,
+                       bool timed = false) {
+    cudaStream_t s = c->stream;
+    unsigned g = nblk(L.cells);
+    cudaEvent_t ev = nullptr;
+    timed = timed && (xin || ec);
+    if (timed) prof_begin(c, s, &ev);
+    if (c->pc->b16)
+        k_lvl_smooth<true><<<g, 256, 0, s>>>(L, xin, ec, ccny, ccnz, OMEGA_COARSE, xout);
+    else
+        k_lvl_smooth<false><<<g, 256, 0, s>>>(L, xin, ec, ccny, ccnz, OMEGA_COARSE, xout);
+    ::mb::count_launch(c);
+    if (timed) prof_end(c, s, PROF_LSMOOTH, ev);
+}
+static void lvl_smooth2(mb_cell* c, Level& L, DF4* xout) {
+    cudaStream_t s = c->stream;
+    unsigned g = nblk(L.cells);
+    if (c->pc->b16)
+        k_lvl_smooth2<true><<<g, 256, 0, s>>>(L, OMEGA_COARSE, xout);
+    else
+        k_lvl_smooth2<false><<<g, 256, 0, s>>>(L, OMEGA_COARSE, xout);
+    ::mb::count_launch(c);
+}
+static void lvl_restrict(mb_cell* c, Level& L, const DF4* x, Level& C) {
+    cudaStream_t s = c->stream;
+    unsigned g = nblk(8 * C.cells);
+    if (c->pc->b16)
+        k_lvl_restrict<true><<<g, 256, 0, s>>>(L, x, C);
+    else
+        k_lvl_restrict<false><<<g, 256, 0, s>>>(L, x, C);
+    ::mb::count_launch(c);
+}
+static void lvl_matvec(mb_cell* c, Level& L, const DF4* x, float* y) {
+    cudaStream_t s = c->stream;
+    unsigned g = nblk(L.cells);
+    if (c->pc->b16)
+        k_lvl_matvec<true><<<g, 256, 0, s>>>(L, x, reinterpret_cast<float4*>(y));
+    else
+        k_lvl_matvec<false><<<g, 256, 0, s>>>(L, x, reinterpret_cast<float4*>(y));
+    ::mb::count_launch(c);
+}
+
 // V-cycle on levels l..nlev with right-hand side lv[l].b; result in lv[l].x
 static void vcycle(mb_cell* c, int l) {
     Precond* p = c->pc;
@@ -954,19 +1114,23 @@ static void vcycle(mb_cell* c, int l) {
         return;
     }
     Level& C = p->lv[l + 1];
-    unsigned g = nblk(L.cells);
-    k_lvl_smooth<<<g, 256, 0, s>>>(L, nullptr, nullptr, 0, 0, OMEGA_COARSE, L.x), ::mb::count_launch(c);
-    for (int k = 1; k < NU; ++k) {
-        k_lvl_smooth<<<g, 256, 0, s>>>(L, L.x, nullptr, 0, 0, OMEGA_COARSE, L.x2), ::mb::count_launch(c);
+    const bool timed = l == 1;
+    // pre-smoothing from zero; the first two sweeps fused
+    if (NU >= 2)
+        lvl_smooth2(c, L, L.x);
+    else
+        lvl_smooth(c, L, nullptr, nullptr, 0, 0, L.x);
+    for (int k = 2; k < NU; ++k) {
+        lvl_smooth(c, L, L.x, nullptr, 0, 0, L.x2);
         std::swap(L.x, L.x2);
     }
-    k_lvl_restrict<<<nblk(8 * C.cells), 256, 0, s>>>(L, L.x, C), ::mb::count_launch(c);
+    lvl_restrict(c, L, L.x, C);
     vcycle(c, l + 1);
     // post-smoothing, the first sweep applied to x + P e
-    k_lvl_smooth<<<g, 256, 0, s>>>(L, L.x, C.x, C.ny, C.nz, OMEGA_COARSE, L.x2), ::mb::count_launch(c);
+    lvl_smooth(c, L, L.x, C.x, C.ny, C.nz, L.x2, timed);
     std::swap(L.x, L.x2);
     for (int k = 1; k < NU; ++k) {
-        k_lvl_smooth<<<g, 256, 0, s>>>(L, L.x, nullptr, 0, 0, OMEGA_COARSE, L.x2), ::mb::count_launch(c);
+        lvl_smooth(c, L, L.x, nullptr, 0, 0, L.x2, timed);
         std::swap(L.x, L.x2);
     }
 }
@@ -1013,12 +1177,22 @@ static void kcycle_l1(mb_cell* c) {
         L.b = reinterpret_cast<float4*>(Vj);
         vcycle(c, 1);
         cudaMemcpyAsync(Zj, L.x, sizeof(DF4) * L.cells, cudaMemcpyDeviceToDevice, s);
-        k_lvl_matvec<<<nblk(L.cells), 256, 0, s>>>(L, Zj, reinterpret_cast<float4*>(p->kw)), ::mb::count_launch(c);
+        lvl_matvec(c, L, Zj, p->kw);
         kdots(c, p->kV, m4, j + 1, p->kw, m4, h1);
-        k_kupdate<<<g, 256, 0, s>>>(p->kV, m4, j + 1, h1, -1.f, p->kw, m4), ::mb::count_launch(c);
-        kdots(c, p->kV, m4, j + 1, p->kw, m4, h2);
-        k_kupdate<<<g, 256, 0, s>>>(p->kV, m4, j + 1, h2, -1.f, p->kw, m4), ::mb::count_launch(c);
-        kdots(c, p->kw, 0, 1, p->kw, m4, wn2);
+        if (j + 1 <= 8) {
+            // CGS2 with each update fused into the products that follow it
+            k_kupd_dot<false><<<RED_BLOCKS, RED_THREADS, 0, s>>>(p->kV, m4, j + 1, h1, p->kw, m4, p->kred),
+                ::mb::count_launch(c);
+            k_reduce_final<false><<<j + 1, RED_THREADS, 0, s>>>(p->kred, j + 1, h2), ::mb::count_launch(c);
+            k_kupd_dot<true><<<RED_BLOCKS, RED_THREADS, 0, s>>>(p->kV, m4, j + 1, h2, p->kw, m4, p->kred),
+                ::mb::count_launch(c);
+            k_reduce_final<false><<<1, RED_THREADS, 0, s>>>(p->kred, 1, wn2), ::mb::count_launch(c);
+        } else {
+            k_kupdate<<<g, 256, 0, s>>>(p->kV, m4, j + 1, h1, -1.f, p->kw, m4), ::mb::count_launch(c);
+            kdots(c, p->kV, m4, j + 1, p->kw, m4, h2);
+            k_kupdate<<<g, 256, 0, s>>>(p->kV, m4, j + 1, h2, -1.f, p->kw, m4), ::mb::count_launch(c);
+            kdots(c, p->kw, 0, 1, p->kw, m4, wn2);
+        }
         k_kcol<<<1, 32, 0, s>>>(H, j, h1, h2, wn2), ::mb::count_launch(c);
         k_knormalize<<<g, 256, 0, s>>>(p->kw, wn2, p->kV + (j + 1) * m4, m4), ::mb::count_launch(c);
     }
@@ -1086,7 +1260,7 @@ static int apply_body(mb_cell* c, const float* r, float2* z) {
                 dbg_norm(c, reinterpret_cast<const float*>(L1.b), 4 * L1.cells));
     kcycle_l1(c);
     if (debug_level() >= 2) {
-        k_lvl_matvec<<<nblk(L1.cells), 256, 0, s>>>(L1, L1.x, reinterpret_cast<float4*>(p->kw)), ::mb::count_launch(c);
+        lvl_matvec(c, L1, L1.x, p->kw);
         fprintf(stderr, "[mb-pc] |x1| %.3e |A1 x1| %.3e\n",
                 dbg_norm(c, reinterpret_cast<const float2*>(L1.x), 4 * L1.cells), dbg_norm(c, p->kw, 4 * L1.cells));
     }

@@ -242,11 +242,15 @@ class _Emulation:
         return np.concatenate([z, zn])
 
 
-def test_precond_matches_emulation(params):
+@pytest.mark.parametrize("bf16", [0, 1])
+def test_precond_matches_emulation(params, bf16):
+    """FP64 emulation of the whole application; with mg_bf16 the coarse
+    levels apply BF16-rounded operators (relative rounding 2^-9), which the
+    same bound covers."""
     B = _gpu()
     lab, oc, u, u_old, gate = _case(params)
     dt = 1.0
-    gc = B.Cell(lab, 1e-6, params, B.default_opts(mg_kcycle=KCYCLE, mg_smooth=4))
+    gc = B.Cell(lab, 1e-6, params, B.default_opts(mg_kcycle=KCYCLE, mg_smooth=4, mg_bf16=bf16))
     A, S, Ann = _reference(oc, u, u_old, gate, dt)
     gc.debug_precond(u, gate, dt, np.ones(gc.n))
     rowdiag = gc.debug_fine()[2].astype(np.float64)
