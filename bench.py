@@ -377,15 +377,17 @@ def main():
     e2e = {"value": ws * args.e2e_steps * dt / e2e_wall, "unit": UNIT,
            "h2d_bytes_per_step": 8 * cell.n, "d2h_bytes_per_step": 8 * cell.n}
 
-    # roofline of the dominant timed kernel: the stencil JVP k_jvp_lin, launched as
-    # the fine smoother's S z (mode 1) and as the Krylov operator (mode 2), or the
-    # level-1 smoothing sweep k_lvl_smooth of the K-cycle
+    # roofline of the dominant timed kernel: the fine smoothing sweep k_fine_stencil,
+    # the Krylov operator's stencil JVP k_jvp_lin, or the level-1 smoothing sweep
+    # k_lvl_smooth of the K-cycle
     peak, peak_kind = measured_peaks()
     N, F, NI = cell.N, cell.F, cell.NI
     cell_levels = cell.debug_levels()
-    # algorithmic bytes per launch.  Per voxel: vcode 4 + FP32 c 4 + float-float direction (c, phi) 16
-    # + FP32 result (c, phi) 8 (+ FP32 row scales (c, phi) 8 in mode 2).  Per interface face: six FP32
-    # partials 24.  Per plating face: float-float direction 8 (+ FP32 result 4 + row scale 4 in mode 2).
+    # algorithmic bytes per launch.  Fine sweep, per voxel: the assembled stencil (14 row blocks of
+    # two BF16 = 56 B, or two FP32 = 112 B) + float-float iterate (c, phi) in 16 and out 16 + FP32
+    # right-hand side 8 + 2x2 block inverse 16.  Krylov JVP, per voxel: vcode 4 + FP32 c 4 +
+    # float-float direction (c, phi) 16 + FP32 result 8 + FP32 row scales 8; per interface face six
+    # FP32 partials 24; per plating face float-float direction 8 + result 4 + row scale 4.
     # Level-1 post-smoothing sweep, per coarse cell: the operator rows (six 4x4 couplings, the
     # difference-form self block and the block inverse: 32 rows of four BF16 = 256 B, or 512 B in
     # FP32) + right-hand side 16 + float-float iterate in 32 and out 32; one sweep in two also reads
@@ -394,9 +396,11 @@ def main():
     c1 = lv[0][0] * lv[0][1] * lv[0][2]
     c2 = lv[1][0] * lv[1][1] * lv[1][2] if len(lv) > 1 else 0
     op_b = 256.0 if opts.mg_bf16 else 512.0
-    kinds = {"smoother": (n_sm, ms_sm, 32.0 * N + 24.0 * NI + 8.0 * F, "k_jvp_lin<1> (fine smoother S z)",
-                          "k_jvp_lin"),
-             "operator": (n_jvp, ms_jvp, 40.0 * N + 24.0 * NI + 16.0 * F, "k_jvp_lin<2> (Krylov operator)",
+    st_b = 56.0 if opts.mg_bf16 else 112.0
+    kinds = {"smoother": (n_sm, ms_sm, (st_b + 56.0) * N,
+                          "k_fine_stencil<%s,sweep> (fine smoothing sweep)" % ("bf16" if opts.mg_bf16 else "fp32"),
+                          "k_fine_stencil"),
+             "operator": (n_jvp, ms_jvp, 40.0 * N + 24.0 * NI + 16.0 * F, "k_jvp_lin (Krylov operator)",
                           "k_jvp_lin"),
              "level1_smoother": (n_ls, ms_ls, (op_b + 80.0) * c1 + 32.0 * c2 / 2.0,
                                  "k_lvl_smooth<%s> (level-1 post-smoothing sweep)" % ("true" if opts.mg_bf16 else "false"),

@@ -164,7 +164,8 @@ int mb_jvp_f32_dev(mb_cell* cell, const float* u, const uint8_t* gate, double dt
 #define MB_PROF_JVP      0   /* Jacobian-vector product kernel (Krylov operator) */
 #define MB_PROF_RESIDUAL 1   /* FP64 residual kernel */
 #define MB_PROF_PRECOND  2   /* one whole preconditioner application (many kernels) */
-#define MB_PROF_SMOOTH   3   /* Jacobian-vector product kernel inside the fine-level smoother */
+#define MB_PROF_SMOOTH   3   /* fine-level smoothing sweep (assembled stencil; 2 mg_smooth - 1 per
+                                preconditioner application) */
 #define MB_PROF_LSMOOTH  4   /* level-1 post-smoothing sweep (two per V-cycle of the K-cycle) */
 int mb_prof_enable(mb_cell* cell, int on);
 int mb_prof_read(mb_cell* cell, int kind, int64_t* count, double* total_ms);

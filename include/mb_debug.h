@@ -38,6 +38,11 @@ int mb_debug_level_op(mb_cell* cell, int level, float* aself, float* off, uint8_
  * by which the Krylov rows are divided; mb_debug_precond's r and z are in
  * those row-equilibrated units on input). */
 int mb_debug_fine(mb_cell* cell, float* dinv, float* fc, float* rowdiag);
+/* The assembled fine smoother stencil of the last mb_debug_precond, as FP32:
+ * out[(k * N + v) * 2 + col] for row block k = 2q + r (q = 0 self block of the
+ * difference form, 1 + d coupling in direction d; r = 0 c row, 1 phi row),
+ * col = 0 c, 1 phi; 14 x N x 2 floats. */
+int mb_debug_fine_stencil(mb_cell* cell, float* out);
 
 /* The solver's own Newton residual (interface currents evaluated once per
  * face, then the voxel rows) at u, u_old with gates gate (uint8[F]); the

@@ -146,6 +146,7 @@ def _declare(lib):
     fn("mb_debug_level_dims", C.c_int, [VP, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)])
     fn("mb_debug_level_op", C.c_int, [VP, C.c_int, VP, VP, VP])
     fn("mb_debug_fine", C.c_int, [VP, VP, VP, VP])
+    fn("mb_debug_fine_stencil", C.c_int, [VP, VP])
     fn("mb_debug_residual_split", C.c_int, [VP, VP, VP, VP, C.c_double, C.c_double, VP])
     return lib
 
@@ -333,6 +334,11 @@ class Cell:
         rowdiag = np.empty(self.n, np.float32)
         _check(lib().mb_debug_fine(self.h, _ptr(dinv), _ptr(fc), _ptr(rowdiag)))
         return dinv, fc[:self.F], rowdiag
+
+    def debug_fine_stencil(self):
+        out = np.empty((14, self.N, 2), np.float32)
+        _check(lib().mb_debug_fine_stencil(self.h, _ptr(out)))
+        return out
 
     # device-pointer variants (torch CUDA tensors)
     def residual_dev(self, u, u_old, dt, I_app, r, gate=None):

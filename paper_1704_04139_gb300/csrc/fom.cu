@@ -591,16 +591,14 @@ int launch_lin_setup(mb_cell* c, const TC* u, const uint8_t* gate, cudaStream_t 
 template int launch_lin_setup<float>(mb_cell*, const float*, const uint8_t*, cudaStream_t);
 template int launch_lin_setup<double>(mb_cell*, const double*, const uint8_t*, cudaStream_t);
 
-// J v on a float-float direction in scaled units: MODE 1 output rows divided
-// by the residual scale s_r (the smoother's S z; face rows not written),
-// MODE 2 further multiplied by the inverse row scale rowinv (the Krylov
-// operator, face rows written).  FP32 arithmetic; differences taken before
+// J v on a float-float direction in scaled units: output rows divided by the
+// residual scale s_r and by the row equilibration (multiplied by rowinv): the
+// Krylov operator, face rows written.  FP32 arithmetic; differences taken before
 // rounding (see face_jvp).  Each face first selects its coefficients on
 // (dphi_w - dphi_v, dc_w - dc_v, dc_v, dc_w, dn_f) for the phi and c rows in a
 // short branch, then all faces share one update, so that a warp of mixed
 // phases pays little for divergence.  scal: [0] 1/dt, [1 + phase]
 // 1/(V c_ref/dt), [7] 1/A, [8] dt/n_c.
-template <int MODE>
 __global__ void __launch_bounds__(256, 4)
 k_jvp_lin(ParT<float> P, Dims D, const uint32_t* __restrict__ vc, const float* __restrict__ c32,
           const float* __restrict__ icoef, const float* __restrict__ rowinv, const float* __restrict__ scal,
@@ -608,7 +606,6 @@ k_jvp_lin(ParT<float> P, Dims D, const uint32_t* __restrict__ vc, const float* _
     int z, y, t;
     vox_coords(D, z, y, t);
     if (z >= D.nz || y >= D.ny) return;
-    constexpr bool EQUIL = MODE == 2;
     const int syz = (int)D.syz, nz = D.nz;
     const int NI = (int)D.NI;
     const int v = t * syz + y * nz + z;
@@ -684,7 +681,7 @@ k_jvp_lin(ParT<float> P, Dims D, const uint32_t* __restrict__ vc, const float* _
                 q3 = AF * i_cs;
                 q4 = AF * i_ce;
             }
-            if (EQUIL && lv == PG) {
+            if (lv == PG) {
                 const float dipl = -ip_eta * ddp + ip_ce * dcw + ip_n * dnf;
                 y_out[2 * D.N + i] = (P.invF * dipl + dnf * dt_inv) * scal[8] * rowinv[2 * D.N + i];
             }
@@ -711,10 +708,8 @@ k_jvp_lin(ParT<float> P, Dims D, const uint32_t* __restrict__ vc, const float* _
     if (has_c(lv)) jc = (jc + P.V * dt_inv * dcv) * scal[1 + lv];
     else jc = dcv;
     jp *= scal[7];
-    if (EQUIL) {
-        jc *= rowinv[v];
-        jp *= rowinv[D.N + v];
-    }
+    jc *= rowinv[v];
+    jp *= rowinv[D.N + v];
     y_out[v] = jc;
     y_out[D.N + v] = jp;
 }
@@ -734,17 +729,14 @@ int set_dt(mb_cell* c, double dt, cudaStream_t s) {
     return MB_OK;
 }
 
-int launch_jvp_lin(mb_cell* c, const float2* v, float* jv, cudaStream_t s, int mode) {
+int launch_jvp_lin(mb_cell* c, const float2* v, float* jv, cudaStream_t s) {
     const Dims& D = c->D;
     const dim3 g = vox_grid(D, VOX_BLOCK);
     const float* sc = c->d_dtinv;
     cudaEvent_t ev;
     prof_begin(c, s, &ev);
-    if (mode == 2)
-        k_jvp_lin<2><<<g, VOX_BLOCK, 0, s>>>(c->Pf, D, c->vcode, c->u32, c->icoef, c->rowinv, sc, v, jv), ::mb::count_launch(c);
-    else
-        k_jvp_lin<1><<<g, VOX_BLOCK, 0, s>>>(c->Pf, D, c->vcode, c->u32, c->icoef, c->rowinv, sc, v, jv), ::mb::count_launch(c);
-    prof_end(c, s, mode == 2 ? PROF_JVP : PROF_SMOOTH, ev);
+    k_jvp_lin<<<g, VOX_BLOCK, 0, s>>>(c->Pf, D, c->vcode, c->u32, c->icoef, c->rowinv, sc, v, jv), ::mb::count_launch(c);
+    prof_end(c, s, PROF_JVP, ev);
     MB_CUDA_LAUNCH("jvp_lin");
     return MB_OK;
 }

@@ -191,10 +191,9 @@ template <class TC>
 int launch_lin_setup(mb_cell* c, const TC* u, const uint8_t* gate, cudaStream_t s);
 // J v from the stored interface partials (c->icoef), the FP32 concentrations
 // c->u32, the row scales c->rowdiag and 1/dt from c->d_dtinv, on a float-float
-// direction v in scaled units, FP32 result; mode 1: rows divided by the
-// residual scale (the smoother's S z), mode 2: further divided by the row
-// scale (the row-equilibrated Krylov operator)
-int launch_jvp_lin(mb_cell* c, const float2* v, float* jv, cudaStream_t s, int mode);
+// direction v in scaled units, FP32 result; rows divided by the residual scale
+// and by the row equilibration (the Krylov operator)
+int launch_jvp_lin(mb_cell* c, const float2* v, float* jv, cudaStream_t s);
 // c->d_dtinv = 1/dt (stream-ordered)
 int set_dt(mb_cell* c, double dt, cudaStream_t s);
 int launch_gate(mb_cell* c, const double* u, const double* n_old, uint8_t* gate, cudaStream_t s);
@@ -218,8 +217,11 @@ int precond_create(mb_cell* c);
 void precond_destroy(mb_cell* c);
 // build at linearisation point u32 (float) for time step dt with gates
 int precond_setup(mb_cell* c, const float* u32, const uint8_t* gate, double dt);
+// assemble the fine smoother's stencil; after launch_lin_setup and set_dt of
+// the same linearisation (it reads the interface partials and 1/dt)
+int precond_setup_fine(mb_cell* c);
 // z = M^{-1} r (length n, row-equilibrated Krylov units; r FP32, z float-float);
-// uses the stencil JVP at the current linearisation.  With graph = true the
+// uses the assembled fine stencil of the current linearisation.  With graph = true the
 // whole application is replayed from a CUDA graph captured once per (r, z)
 // buffer pair.
 int precond_apply(mb_cell* c, const float* u32, const uint8_t* gate, double dt, const float* r, float2* z,

@@ -7,11 +7,14 @@
 //    S z_v = r_v - J_vn D_n^-1 r_n approximately and back-substitutes
 //    z_n = D_n^-1 (r_n - J_nv z_v).
 // 2. Fine level: nu_fine (mg_smooth) damped 2x2 (c, phi) block-Jacobi sweeps of S before
-//    and after the coarse correction; S z is applied as the matrix-free JVP
-//    of [z_v, -D_n^-1 J_nv z_v].  Several post-sweeps are needed: with a
-//    current source the correction carries a large, weakly pinned potential
-//    component, and the jumps its piecewise-constant prolongation leaves at
-//    aggregate boundaries otherwise dominate the residual.
+//    and after the coarse correction.  S is assembled once per linear solve
+//    as a seven-point stencil of 2x2 blocks in difference form (from the same
+//    interface partials as the Krylov operator, with the plating rows
+//    eliminated face by face), and each sweep is one streaming kernel:
+//    product, residual and block update.  Several post-sweeps are needed:
+//    with a current source the correction carries a large, weakly pinned
+//    potential component, and the jumps its piecewise-constant prolongation
+//    leaves at aggregate boundaries otherwise dominate the residual.
 // 3. Coarse levels: aggregation of 2x2x2 blocks split by class
 //    (0 electrolyte c, 1 electrolyte phi, 2 anode-side phi: G, CN,
 //    3 cathode-side phi: K, CP, L); Galerkin operators with piecewise-constant
@@ -53,6 +56,7 @@ constexpr int KCYC_MAX = 16;              // longest level-1 K-cycle (FGMRES ite
 constexpr int MAX_LEVELS = 16;
 constexpr int COARSE_MAX = 256;           // dense coarsest system size bound (4 x cells)
 constexpr int FCW = 8;                    // floats of condensation coefficients per face
+constexpr int FSTK = 14;                  // row blocks of the assembled fine stencil per voxel
 
 // float-float 4-vector of one coarse cell
 struct alignas(32) DF4 {
@@ -125,6 +129,8 @@ struct Precond {
     float* fc = nullptr;       // FCW per plating face: condensation coefficients (scaled)
     float* rv = nullptr;       // 2N: condensed right-hand side
     float* t = nullptr;        // 2N: S z
+    void* fst = nullptr;       // FSTK x N: assembled fine stencil (float2, or two BF16 per word)
+    float2* zs = nullptr;      // 2N: second fine iterate (sweeps alternate between it and z)
     int nlev = 0;              // coarse levels (index 1..nlev; lv[0] unused)
     Level lv[MAX_LEVELS + 1];
     int ncoarse = 0;
@@ -637,6 +643,205 @@ __global__ void k_coarse_solve(int n, const double* __restrict__ Ainv, const flo
                            df_from_double(sx[4 * cell + 2]), df_from_double(sx[4 * cell + 3]));
 }
 
+// ------------------------------------------------ assembled fine smoother
+// The condensed scaled operator S (the smoother's units: rows over the
+// residual scale, unknowns in Krylov units) per voxel in difference form,
+//   (S z)_v = Dv z_v + sum_d O_d (z_nb - z_v),
+// 2x2 blocks with rows and columns (c, phi).  Row block k = 2q + r (q = 0
+// self, 1 + d direction d; r = 0 c row, 1 phi row) holds the row's two
+// column entries at [k * N + v]: a float2, or two BF16 in one word.
+template <bool B16>
+__device__ inline float2 fst_ld(const void* fst, int k, int64_t N, int64_t v) {
+    if (B16) {
+        const uint32_t w = static_cast<const uint32_t*>(fst)[k * N + v];
+        return make_float2(__uint_as_float(w << 16), __uint_as_float(w & 0xffff0000u));
+    }
+    return static_cast<const float2*>(fst)[k * N + v];
+}
+template <bool B16>
+__device__ inline void fst_st(void* fst, int k, int64_t N, int64_t v, float a, float b) {
+    if (B16) {
+        const uint32_t lo = __bfloat16_as_ushort(__float2bfloat16_rn(a));
+        const uint32_t hi = __bfloat16_as_ushort(__float2bfloat16_rn(b));
+        static_cast<uint32_t*>(fst)[k * N + v] = lo | (hi << 16);
+    } else {
+        static_cast<float2*>(fst)[k * N + v] = make_float2(a, b);
+    }
+}
+
+// Assembly, one thread per voxel.  Per face the coefficients of the
+// linearised fluxes on (dphi_w - dphi_v, dc_w - dc_v, dc_v, dc_w, dn_f) are
+// those of the Krylov operator's stencil (same interface partials icoef, same
+// FP32 concentrations); a plating face's dn_f is eliminated with its own row
+// (F dn/dt + i_pl linearised = 0), and the absolute c_w terms are moved into
+// difference form: p dc_w = p c_ref,w ((z_c,w - z_c,v) + z_c,v).
+template <bool B16>
+__global__ void __launch_bounds__(256)
+k_assemble_fine(ParT<float> P, Dims D, const uint32_t* __restrict__ vc, const float* __restrict__ c32,
+                const float* __restrict__ icoef, const float* __restrict__ scal, void* __restrict__ fst) {
+    const int z = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int t = blockIdx.z;
+    if (z >= D.nz || y >= D.ny) return;
+    const int64_t N = D.N, NI = D.NI;
+    const int64_t v = (int64_t)t * D.syz + (int64_t)y * D.nz + z;
+    const uint32_t code = vc[v];
+    const int lv = vc_phase(code);
+    const float crv = P.cref[lv], crE = P.cref[PE];
+    const float A = P.A, AF = P.A * P.invF;
+    const float dt_inv = scal[0];
+    const float Fdt = dt_inv / P.invF;   // F / dt
+    const bool vkin = lv == PG || lv == PK || lv == PL;
+    const int64_t off[6] = {-D.syz, D.syz, -(int64_t)D.nz, (int64_t)D.nz, -1, 1};
+    const bool inb[6] = {t > 0, t < D.nt - 1, y > 0, y < D.ny - 1, z > 0, z < D.nz - 1};
+    float Dcc = 0.f, Dcp = 0.f, Dpc = 0.f, Dpp = 0.f;
+    float Occ[6], Ocp[6], Opc[6], Opp[6];
+    int64_t ibase = (int64_t)vc_fbase(code);
+#pragma unroll
+    for (int d = 0; d < 6; ++d) {
+        Occ[d] = Ocp[d] = Opc[d] = Opp[d] = 0.f;
+        if (!inb[d]) continue;
+        const int64_t w = v + off[d];
+        const uint32_t cw_code = vc[w];
+        const int lw = vc_phase(cw_code);
+        float p1 = 0.f, p2 = 0.f, p3 = 0.f, p4 = 0.f;   // phi row on (ddp, ddc, dcv, dcw)
+        float q1 = 0.f, q2 = 0.f, q3 = 0.f, q4 = 0.f;   // c row
+        float crd = 0.f, crw = 0.f;                     // c_ref of the ddc and dcw terms
+        if (lv == PE && lw == PE) {
+            crd = crE;
+            crw = crE;
+            const float cv = c32[v], cw = c32[w], cmin = P.cmin[PE];
+            const float iS = __frcp_rn(fmaxf(cv, cmin) + fmaxf(cw, cmin));
+            const float gr = P.E_gm * (cw - cv) * iS * iS;
+            p1 = -P.E_gk;
+            p2 = -P.E_gm * iS;
+            p3 = cv >= cmin ? gr : 0.f;
+            p4 = cw >= cmin ? gr : 0.f;
+            q1 = P.E_tF * p1;
+            q2 = -P.E_gD + P.E_tF * p2;
+            q3 = P.E_tF * p3;
+            q4 = P.E_tF * p4;
+        } else if (lv == lw && (lv == PG || lv == PK)) {
+            crd = crv;
+            q2 = -P.gD[lv];
+            p1 = -P.gsig[lv][lw];
+        } else if (lv != PE && lw != PE) {
+            p1 = -P.gsig[lv][lw];
+        } else if (vkin && lw == PE) {
+            const int64_t i = ibase++;
+            const float i_eta = icoef[i], ip_eta = icoef[NI + i], i_cs = icoef[2 * NI + i];
+            const float i_ce = icoef[3 * NI + i], ip_ce = icoef[4 * NI + i], ip_n = icoef[5 * NI + i];
+            crw = crE;
+            p1 = -A * (i_eta + ip_eta);
+            p3 = A * i_cs;
+            p4 = A * (i_ce + ip_ce);
+            if (lv != PL) {
+                q1 = -AF * i_eta;
+                q3 = AF * i_cs;
+                q4 = AF * i_ce;
+            }
+            if (lv == PG) {   // dn_f = (ip_eta ddp - ip_ce dcw) / (ip_n + F/dt)
+                const float p5 = A * ip_n, k = 1.f / (ip_n + Fdt);
+                p1 += p5 * k * ip_eta;
+                p4 -= p5 * k * ip_ce;
+            }
+        } else if (lv == PE && (lw == PG || lw == PK || lw == PL)) {
+            const int64_t i = (int64_t)vc_fbase(cw_code) + __popc(vc_emask(cw_code) & ((1u << opp_dir(d)) - 1u));
+            const float i_eta = icoef[i], ip_eta = icoef[NI + i], i_cs = icoef[2 * NI + i];
+            const float i_ce = icoef[3 * NI + i], ip_ce = icoef[4 * NI + i], ip_n = icoef[5 * NI + i];
+            crw = P.cref[lw];
+            p1 = -A * (i_eta + ip_eta);
+            p3 = -A * (i_ce + ip_ce);
+            p4 = -A * i_cs;
+            q1 = -AF * (i_eta + ip_eta);
+            q3 = -AF * (i_ce + ip_ce);
+            q4 = -AF * i_cs;
+            if (lw == PG) {   // dn_f = (-ip_eta ddp - ip_ce dcv) / (ip_n + F/dt) from this side
+                const float p5 = -A * ip_n, q5 = -AF * ip_n, k = 1.f / (ip_n + Fdt);
+                p1 -= p5 * k * ip_eta;
+                p3 -= p5 * k * ip_ce;
+                q1 -= q5 * k * ip_eta;
+                q3 -= q5 * k * ip_ce;
+            }
+        }
+        Opp[d] = p1;
+        Opc[d] = p2 * crd + p4 * crw;
+        Dpc += p3 * crv + p4 * crw;
+        Ocp[d] = q1;
+        Occ[d] = q2 * crd + q4 * crw;
+        Dcc += q3 * crv + q4 * crw;
+    }
+    if (t == 0 && lv == PCN) Dpp += P.g_dir;
+    if (has_c(lv)) {
+        const float sc = scal[1 + lv];
+        Dcc = (Dcc + P.V * dt_inv * crv) * sc;
+        Dcp *= sc;
+#pragma unroll
+        for (int d = 0; d < 6; ++d) { Occ[d] *= sc; Ocp[d] *= sc; }
+    } else {   // identity row of a phase without concentration
+        Dcc = crv;
+        Dcp = 0.f;
+#pragma unroll
+        for (int d = 0; d < 6; ++d) { Occ[d] = 0.f; Ocp[d] = 0.f; }
+    }
+    const float sp = scal[7];
+    fst_st<B16>(fst, 0, N, v, Dcc, Dcp);
+    fst_st<B16>(fst, 1, N, v, Dpc * sp, Dpp * sp);
+#pragma unroll
+    for (int d = 0; d < 6; ++d) {
+        fst_st<B16>(fst, 2 + 2 * d, N, v, Occ[d], Ocp[d]);
+        fst_st<B16>(fst, 3 + 2 * d, N, v, Opc[d] * sp, Opp[d] * sp);
+    }
+}
+
+// S z at one voxel from the assembled stencil, differences from the
+// float-float iterate; a neighbour outside the grid is replaced by the voxel
+// itself (zero difference, zero coupling)
+template <bool B16>
+__device__ inline float2 fine_Sz(const Dims& D, const void* __restrict__ fst, const float2* __restrict__ zin, int t,
+                                 int y, int z, int64_t v, float2 zc, float2 zp) {
+    const int64_t N = D.N;
+    const float2 s0 = fst_ld<B16>(fst, 0, N, v), s1 = fst_ld<B16>(fst, 1, N, v);
+    const float vc = df_val(zc), vp = df_val(zp);
+    float yc = s0.x * vc + s0.y * vp, yp = s1.x * vc + s1.y * vp;
+    const int64_t off[6] = {-D.syz, D.syz, -(int64_t)D.nz, (int64_t)D.nz, -1, 1};
+    const bool inb[6] = {t > 0, t < D.nt - 1, y > 0, y < D.ny - 1, z > 0, z < D.nz - 1};
+#pragma unroll
+    for (int d = 0; d < 6; ++d) {
+        const int64_t nb = inb[d] ? v + off[d] : v;
+        const float dc = df_diff(zin[nb], zc), dp = df_diff(zin[N + nb], zp);
+        const float2 o0 = fst_ld<B16>(fst, 2 + 2 * d, N, v), o1 = fst_ld<B16>(fst, 3 + 2 * d, N, v);
+        yc += o0.x * dc + o0.y * dp;
+        yp += o1.x * dc + o1.y * dp;
+    }
+    return make_float2(yc, yp);
+}
+
+// one damped block-Jacobi sweep, zout = zin + omega Dinv (rv - S zin) (SWEEP),
+// or the product tout = S zin; voxel rows only
+template <bool B16, bool SWEEP>
+__global__ void __launch_bounds__(256)
+k_fine_stencil(Dims D, const void* __restrict__ fst, const float* __restrict__ dinv, const float* __restrict__ rv,
+               const float2* __restrict__ zin, float omega, float2* __restrict__ zout, float* __restrict__ tout) {
+    const int z = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int t = blockIdx.z;
+    if (z >= D.nz || y >= D.ny) return;
+    const int64_t N = D.N;
+    const int64_t v = (int64_t)t * D.syz + (int64_t)y * D.nz + z;
+    const float2 zc = zin[v], zp = zin[N + v];
+    const float2 sz = fine_Sz<B16>(D, fst, zin, t, y, z, v, zc, zp);
+    if (!SWEEP) {
+        tout[v] = sz.x;
+        tout[N + v] = sz.y;
+        return;
+    }
+    const float rc = rv[v] - sz.x, rp = rv[N + v] - sz.y;
+    const float4 m = reinterpret_cast<const float4*>(dinv)[v];
+    zout[v] = df_add_f(zc, omega * (m.x * rc + m.y * rp));
+    zout[N + v] = df_add_f(zp, omega * (m.z * rc + m.w * rp));
+}
+
 // --------------------------------------------------------- coarse smoothing
 // 4x4 block (row-major entries k*4+kk stored st apart: structure-of-arrays
 // over the cells, so that a warp's loads of one entry are contiguous) times x
@@ -971,6 +1176,10 @@ int precond_create(mb_cell* c) {
     p->fc = (float*)cell_alloc(c, 4 * FCW * (D.F ? D.F : 1));
     p->rv = (float*)cell_alloc(c, 8 * D.N);
     p->t = (float*)cell_alloc(c, 8 * D.N);
+    p->b16 = c->opt.mg_bf16 != 0;
+    p->fst = cell_alloc(c, (p->b16 ? 4 : 8) * (size_t)FSTK * D.N);
+    p->zs = (float2*)cell_alloc(c, 16 * (size_t)D.N);
+    if (!p->fst || !p->zs) return MB_ENOMEM;
     c->rowdiag = (float*)cell_alloc(c, 4 * c->n);
     c->rowinv = (float*)cell_alloc(c, 4 * c->n);
     if (!p->dinv || !p->fc || !p->rv || !p->t || !c->rowdiag || !c->rowinv) return MB_ENOMEM;
@@ -1041,7 +1250,6 @@ int precond_setup(mb_cell* c, const float* u32, const uint8_t* gate, double dt) 
     Precond* p = c->pc;
     p->kcyc = c->opt.mg_kcycle < 1 ? 1 : (c->opt.mg_kcycle > KCYC_MAX ? KCYC_MAX : c->opt.mg_kcycle);
     p->nu_fine = c->opt.mg_smooth < 1 ? 1 : (c->opt.mg_smooth > 8 ? 8 : c->opt.mg_smooth);
-    p->b16 = c->opt.mg_bf16 != 0;
     const Dims& D = c->D;
     cudaStream_t s = c->stream;
     k_bj_setup<<<pgrid(D.nt, D.ny, D.nz), PB, 0, s>>>(c->Pf, D, c->vcode, u32, gate, dt, c->s_i0, c->k_pl,
@@ -1229,6 +1437,47 @@ int debug_level();
 
 // the kernel sequence of one application (stream-ordered, no host synchronisation
 // unless MB_DEBUG >= 2)
+// fine stencil launches with the storage chosen at creation
+static void fine_sweep(mb_cell* c, const float2* zin, float2* zout) {
+    Precond* p = c->pc;
+    const Dims& D = c->D;
+    cudaStream_t s = c->stream;
+    const dim3 vg = pgrid(D.nt, D.ny, D.nz);
+    cudaEvent_t ev;
+    prof_begin(c, s, &ev);
+    if (p->b16)
+        k_fine_stencil<true, true><<<vg, PB, 0, s>>>(D, p->fst, p->dinv, p->rv, zin, OMEGA_FINE, zout, nullptr);
+    else
+        k_fine_stencil<false, true><<<vg, PB, 0, s>>>(D, p->fst, p->dinv, p->rv, zin, OMEGA_FINE, zout, nullptr);
+    ::mb::count_launch(c);
+    prof_end(c, s, PROF_SMOOTH, ev);
+}
+static void fine_product(mb_cell* c, const float2* zin, float* tout) {
+    Precond* p = c->pc;
+    const Dims& D = c->D;
+    cudaStream_t s = c->stream;
+    const dim3 vg = pgrid(D.nt, D.ny, D.nz);
+    if (p->b16)
+        k_fine_stencil<true, false><<<vg, PB, 0, s>>>(D, p->fst, nullptr, nullptr, zin, 0.f, nullptr, tout);
+    else
+        k_fine_stencil<false, false><<<vg, PB, 0, s>>>(D, p->fst, nullptr, nullptr, zin, 0.f, nullptr, tout);
+    ::mb::count_launch(c);
+}
+
+int precond_setup_fine(mb_cell* c) {
+    Precond* p = c->pc;
+    const Dims& D = c->D;
+    cudaStream_t s = c->stream;
+    const dim3 vg = pgrid(D.nt, D.ny, D.nz);
+    if (p->b16)
+        k_assemble_fine<true><<<vg, PB, 0, s>>>(c->Pf, D, c->vcode, c->u32, c->icoef, c->d_dtinv, p->fst);
+    else
+        k_assemble_fine<false><<<vg, PB, 0, s>>>(c->Pf, D, c->vcode, c->u32, c->icoef, c->d_dtinv, p->fst);
+    ::mb::count_launch(c);
+    MB_CUDA_LAUNCH("precond_setup_fine");
+    return MB_OK;
+}
+
 static int apply_body(mb_cell* c, const float* r, float2* z) {
     Precond* p = c->pc;
     const Dims& D = c->D;
@@ -1238,20 +1487,19 @@ static int apply_body(mb_cell* c, const float* r, float2* z) {
                 dbg_norm(c, r, c->n), dbg_norm(c, c->rowdiag, c->n));
     const dim3 vg = pgrid(D.nt, D.ny, D.nz);
     const unsigned fg = nblk(D.F ? D.F : 1);
-    // condensed right-hand side, then nu_fine damped block-Jacobi sweeps from zero
+    // condensed right-hand side, then nu_fine damped block-Jacobi sweeps from
+    // zero; the sweeps alternate between zs and z, and the first one (from
+    // zero) writes where the last one must end up in z
     k_condense_rhs<<<vg, PB, 0, s>>>(D, c->vcode, p->fc, r, c->rowdiag, p->rv), ::mb::count_launch(c);
-    k_bj_apply<<<nblk(D.N), 256, 0, s>>>(D, p->dinv, p->rv, nullptr, OMEGA_FINE, false, z), ::mb::count_launch(c);
-    // t = S z_v  (S applied as the JVP of [z_v, -D_n^-1 J_nv z_v])
-    auto apply_S = [&]() -> int {
-        if (D.F) k_face_solve<<<fg, 256, 0, s>>>(D, c->pf_g, c->pf_e, p->fc, nullptr, c->rowdiag, z), ::mb::count_launch(c);
-        return launch_jvp_lin(c, z, p->t, s, 1);
-    };
-    int rc;
+    float2* za = (p->nu_fine - 1) % 2 == 0 ? z : p->zs;
+    float2* zb = za == z ? p->zs : z;
+    k_bj_apply<<<nblk(D.N), 256, 0, s>>>(D, p->dinv, p->rv, nullptr, OMEGA_FINE, false, za), ::mb::count_launch(c);
     for (int k = 1; k < p->nu_fine; ++k) {
-        if ((rc = apply_S())) return rc;
-        k_bj_apply<<<nblk(D.N), 256, 0, s>>>(D, p->dinv, p->rv, p->t, OMEGA_FINE, true, z), ::mb::count_launch(c);
+        fine_sweep(c, za, zb);
+        std::swap(za, zb);
     }
-    if ((rc = apply_S())) return rc;
+    // t = S z for the restricted residual
+    fine_product(c, z, p->t);
     Level& L1 = p->lv[1];
     k_restrict_fine<<<nblk(L1.cells), 256, 0, s>>>(D, c->vcode, p->rv, p->t, L1), ::mb::count_launch(c);
     if (debug_level() >= 2)
@@ -1266,10 +1514,13 @@ static int apply_body(mb_cell* c, const float* r, float2* z) {
     }
     k_prolong_fine<<<vg, PB, 0, s>>>(D, c->vcode, L1, L1.x, z), ::mb::count_launch(c);
     // nu_fine post-smoothing sweeps (they remove the jumps of the piecewise-constant prolongation)
+    za = z;
+    zb = p->zs;
     for (int k = 0; k < p->nu_fine; ++k) {
-        if ((rc = apply_S())) return rc;
-        k_bj_apply<<<nblk(D.N), 256, 0, s>>>(D, p->dinv, p->rv, p->t, OMEGA_FINE, true, z), ::mb::count_launch(c);
+        fine_sweep(c, za, zb);
+        std::swap(za, zb);
     }
+    if (za != z) MB_CUDA(cudaMemcpyAsync(z, za, 16 * (size_t)D.N, cudaMemcpyDeviceToDevice, s));
     // back-substitution of the plating rows
     if (D.F) k_face_solve<<<fg, 256, 0, s>>>(D, c->pf_g, c->pf_e, p->fc, r, c->rowdiag, z), ::mb::count_launch(c);
     if (debug_level() >= 2) fprintf(stderr, "[mb-pc] |z| %.3e\n", dbg_norm(c, z, c->n));
@@ -1401,6 +1652,7 @@ int mb_debug_precond(mb_cell* c, const double* u, const uint8_t* gate, double dt
     int rc = precond_setup(c, c->u32, c->gate2, dt);
     if (!rc) rc = launch_lin_setup<float>(c, c->u32, c->gate2, s);
     if (!rc) rc = set_dt(c, dt, s);
+    if (!rc) rc = precond_setup_fine(c);
     if (!rc) rc = precond_apply(c, c->u32, c->gate2, dt, r32, zdf, false);
     if (!rc) {
         k_df_to_double<<<nblk(n), 256, 0, s>>>(zdf, z64, n), ::mb::count_launch(c);
@@ -1458,6 +1710,28 @@ int mb_debug_level_op(mb_cell* c, int level, float* aself, float* off, uint8_t* 
             for (int e = 0; e < OFFW; ++e) off[i * OFFW + e] = tmp[(size_t)e * L.cells + i];
     }
     if (mask) MB_CUDA(cudaMemcpy(mask, L.mask, L.cells, cudaMemcpyDeviceToHost));
+    return MB_OK;
+}
+
+__global__ void k_fst_to_f32(const uint32_t* __restrict__ a, float2* __restrict__ b, int64_t n) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) b[i] = make_float2(__uint_as_float(a[i] << 16), __uint_as_float(a[i] & 0xffff0000u));
+}
+
+int mb_debug_fine_stencil(mb_cell* c, float* out) {
+    if (!c || !out) { set_error("mb_debug_fine_stencil: invalid argument"); return MB_EINVAL; }
+    const int64_t m = (int64_t)FSTK * c->D.N;
+    if (!c->pc->b16) {
+        MB_CUDA(cudaMemcpy(out, c->pc->fst, 8 * m, cudaMemcpyDeviceToHost));
+        return MB_OK;
+    }
+    float2* tmp = nullptr;
+    MB_CUDA(cudaMalloc(&tmp, 8 * m));
+    k_fst_to_f32<<<nblk(m), 256, 0, c->stream>>>(static_cast<const uint32_t*>(c->pc->fst), tmp, m);
+    cudaError_t e = cudaMemcpyAsync(out, tmp, 8 * m, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    cudaFree(tmp);
+    if (e != cudaSuccess) return cuda_fail(e, "debug_fine_stencil");
     return MB_OK;
 }
 

@@ -174,7 +174,7 @@ struct OpCtx {
 
 static int apply_op(mb_cell* c, const OpCtx& o, const float2* x, float* y) {
     (void)o;
-    return launch_jvp_lin(c, x, y, c->stream, 2);
+    return launch_jvp_lin(c, x, y, c->stream);
 }
 
 // Flexible GMRES(m) on A x = b (x starts at zero), stopping at
@@ -314,6 +314,7 @@ static int linear_solve(mb_cell* c, double dt, int* its, double* relres) {
     rc = c->opt.precision == MB_PREC_MIXED ? launch_lin_setup<float>(c, c->u32, c->gate, s)
                                            : launch_lin_setup<double>(c, c->u, c->gate, s);
     if (rc) return rc;
+    if ((rc = precond_setup_fine(c))) return rc;
     if (!c->kd && (rc = krylov_create(c, &c->kd))) return rc;
     Krylov* K = c->kd;
     k_scale_rhs<<<nblk(n), 256, 0, s>>>(c->D, c->vcode, c->r, inv_scales(c, 1, dt), c->rowinv, K->b), ::mb::count_launch(c);

@@ -150,6 +150,54 @@ def test_precond_stages_match_reference(params):
             Aref = (Pu.T @ Aref @ Pu).tocsr()
 
 
+def _stencil_matrix(st, dims):
+    """2N x 2N matrix of the assembled fine stencil: row block k = 2q + r holds
+    (c, phi) column entries; q = 0 the difference-form self block, q = 1 + d the
+    coupling towards direction d (-t, +t, -y, +y, -z, +z)."""
+    nt, ny, nz = dims
+    N = nt * ny * nz
+    t, y, z = np.unravel_index(np.arange(N), dims)
+    rows, cols, vals = [], [], []
+    self_blk = st[0:2].astype(np.float64).copy()    # (row, N, col)
+    steps = [(-1, 0, 0), (1, 0, 0), (0, -1, 0), (0, 1, 0), (0, 0, -1), (0, 0, 1)]
+    for d, (a, b, c) in enumerate(steps):
+        tt, yy, zz = t + a, y + b, z + c
+        ok = (tt >= 0) & (tt < nt) & (yy >= 0) & (yy < ny) & (zz >= 0) & (zz < nz)
+        v = np.nonzero(ok)[0]
+        nb = (tt[v] * ny + yy[v]) * nz + zz[v]
+        o = st[2 + 2 * d: 4 + 2 * d].astype(np.float64)
+        # outside the grid the coupling must be zero
+        assert np.all(o[:, ~ok, :] == 0)
+        for r in range(2):
+            for col in range(2):
+                rows.append(r * N + v); cols.append(col * N + nb); vals.append(o[r, v, col])
+                self_blk[r, v, col] -= o[r, v, col]
+    v = np.arange(N)
+    for r in range(2):
+        for col in range(2):
+            rows.append(r * N + v); cols.append(col * N + v); vals.append(self_blk[r, :, col])
+    return sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))), shape=(2 * N, 2 * N))
+
+
+@pytest.mark.parametrize("bf16", [0, 1])
+def test_fine_stencil_matches_condensed_operator(params, bf16):
+    """The smoother's assembled stencil equals the condensed scaled operator
+    S = A_vv - A_vn A_nn^-1 A_nv of the oracle's Jacobian (FP32: 2e-3 of the
+    row's largest entry; BF16 entries: 2^-9 each, the self block rebuilt from
+    up to seven of them: 2e-2)."""
+    B = _gpu()
+    lab, oc, u, u_old, gate = _case(params)
+    dt = 1.0
+    gc = B.Cell(lab, 1e-6, params, B.default_opts(mg_bf16=bf16))
+    A, S, Ann = _reference(oc, u, u_old, gate, dt)
+    gc.debug_precond(u, gate, dt, np.ones(gc.n))
+    M = _stencil_matrix(gc.debug_fine_stencil(), lab.shape)
+    diff = abs(M - S).tocsr()
+    rowmax = np.asarray(abs(S).max(axis=1).todense()).ravel() + 1e-30
+    err = np.asarray(diff.max(axis=1).todense()).ravel() / rowmax
+    assert err.max() < (2e-2 if bf16 else 2e-3), float(err.max())
+
+
 KCYCLE = 6   # level-1 K-cycle length used by the emulation test
 
 

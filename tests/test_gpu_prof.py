@@ -33,8 +33,8 @@ def test_profiling_counters_across_steps(params):
     n_r, ms_r = cell.prof_read(B.Cell.PROF_RESIDUAL)
     assert info["krylov_its"] > 0
     assert n_pc >= info["krylov_its"] and ms_pc > 0
-    # every preconditioner application runs 2 * mg_smooth smoother products
-    assert n_sm == 2 * B.default_opts().mg_smooth * n_pc and ms_sm > 0
+    # every preconditioner application runs 2 * mg_smooth - 1 fine sweeps with a product
+    assert n_sm == (2 * B.default_opts().mg_smooth - 1) * n_pc and ms_sm > 0
     # and per level-1 V-cycle (one per K-cycle iteration) 2 timed post-smoothing sweeps
     n_ls, ms_ls = cell.prof_read(B.Cell.PROF_LSMOOTH)
     if len(cell.debug_levels()) > 1:
