@@ -264,10 +264,12 @@ int mb_rom_solve_batch(mb_rom* rom, int B, const mb_rom_params* prm, int n_steps
  * is done, so requests that arrive while others run join the same batched
  * launches; each instance's arithmetic does not depend on the others in the
  * batch, so a result is the same alone and in the mix.  Full-order
- * requests (validation solves) run on their own cells, created from the
- * server's cell template, on worker threads with their own streams, admitted
- * while the device memory of the running ones stays within fom_budget_bytes;
- * their work overlaps with the reduced batch on the device. */
+ * requests (validation solves) run on worker threads with their own streams
+ * and cells (created from the server's cell template on a worker's first
+ * request, kept and reset to the initial state for the next ones; a worker
+ * creates its cell while the device memory of the existing ones stays within
+ * fom_budget_bytes); their work overlaps with the reduced batch on the
+ * device. */
 #define MB_REQ_ROM 0
 #define MB_REQ_FOM 1
 typedef struct {

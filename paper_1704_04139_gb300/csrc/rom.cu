@@ -16,7 +16,12 @@
 //   LU with partial pivoting after row/column equilibration; step length
 //   min(1, 0.25 / |U_loc delta|_s), converged at lam |U_loc delta|_s <= 1e-12.
 // Plating gates: the full-order rule on the reconstruction, with the
-// active-set passes of the full-order step.  All arithmetic FP64.
+// active-set passes of the full-order step.
+// Precision: the state a, the reconstruction, the interpolated terms f and
+// the residual are FP64, so the converged solution is the FP64 one; the
+// Newton matrix (GU, the contraction P GU as one GEMM over all instances,
+// its LU) and the step-length norm are FP32 (an inexact Newton iteration:
+// GB300's FP64 rate is a small fraction of its FP32 rate).
 #include <cuda_runtime.h>
 #include <math.h>
 
@@ -55,6 +60,12 @@ struct RomDev {
     double* P = nullptr;       // Nr x M (Pbv | P1c)
     double* Ms = nullptr;      // Nr x Nr
     double* Alin = nullptr;    // Nr x Nr
+    float* Pf = nullptr;       // FP32 copies for the Newton matrix: P, Ms, Alin, UlocR, UlocC, us
+    float* Msf = nullptr;
+    float* Alinf = nullptr;
+    float* UlocRf = nullptr;
+    float* UlocCf = nullptr;
+    float* usf = nullptr;
     double* bbnd = nullptr;    // Nr
     double* scp = nullptr;     // Nr
     double* sac = nullptr;     // Nr
@@ -63,8 +74,10 @@ struct RomDev {
 
 struct RomWork {
     int B = 0;
-    double *a = nullptr, *a_old = nullptr, *delta = nullptr, *r = nullptr, *J = nullptr;
-    double *uloc = nullptr, *uloc_old = nullptr, *f = nullptr, *G = nullptr, *GU = nullptr;
+    double *a = nullptr, *a_old = nullptr, *delta = nullptr, *r = nullptr;
+    float* J = nullptr;        // B x Nr x Nr, instance-major
+    float* GU = nullptr;       // M x B x Nr: row p of every instance's G U_loc (the GEMM's right operand)
+    double *uloc = nullptr, *uloc_old = nullptr, *f = nullptr, *G = nullptr;
     double* prm = nullptr;
     uint8_t *gate = nullptr, *gate2 = nullptr;
     int *active = nullptr, *failed = nullptr, *pass_on = nullptr, *counts = nullptr;
@@ -180,35 +193,101 @@ __global__ void k_rom_ei(RomDev d, DevParams P, int B, const double* __restrict_
 }
 
 // GU[b][p][:] = sum_e G[b][p][e] U_loc[gidx[p][e]][:]
-__global__ void k_rom_gu(RomDev d, const double* __restrict__ G, const int* __restrict__ active,
-                         double* __restrict__ GU) {
+// GU[p][b][j] = sum_e G[b][p][e] U_loc[gidx[p][e]][j] (FP32); inactive
+// instances write zeros so that the GEMM below reads defined values
+__global__ void k_rom_gu(RomDev d, int B, const double* __restrict__ G, const int* __restrict__ active,
+                         float* __restrict__ GU) {
     const int p = blockIdx.x, b = blockIdx.y;
-    if (!active[b]) return;
+    float* out = GU + ((int64_t)p * B + b) * d.Nr;
+    if (!active[b]) {
+        for (int j = threadIdx.x; j < d.Nr; j += blockDim.x) out[j] = 0.f;
+        return;
+    }
     const double* Gp = G + ((int64_t)b * d.M + p) * GMAX;
     const int32_t* gi = d.gidx + (int64_t)p * GMAX;
     for (int j = threadIdx.x; j < d.Nr; j += blockDim.x) {
-        double acc = 0.0;
+        float acc = 0.f;
         for (int e = 0; e < GMAX; ++e) {
             const int s = gi[e];
             if (s < 0) break;
-            acc += Gp[e] * d.UlocR[(int64_t)s * d.Nr + j];
+            acc = fmaf((float)Gp[e], d.UlocRf[(int64_t)s * d.Nr + j], acc);
         }
-        GU[((int64_t)b * d.M + p) * d.Nr + j] = acc;
+        out[j] = acc;
     }
 }
 
-// J[b] = Ms/dt + Alin + P GU[b]; row i of instance b per block
-__global__ void k_rom_jac(RomDev d, const double* __restrict__ prm, const double* __restrict__ GU,
-                          const int* __restrict__ active, double* __restrict__ J) {
+// Newton matrices of all instances as one FP32 GEMM, C = P [GU_0 | GU_1 | ...]
+// (Nr x M times M x B Nr), plus Ms/dt_b + Alin, written instance-major
+// J[b][i][j].  Tile: all Nr <= 64 rows x 128 columns per block of 256
+// threads, each thread 4 rows x 8 columns in registers, K in chunks of 16
+// staged in shared memory.  Column c = b Nr + j.
+constexpr int JT_ROWS = 64, JT_COLS = 128, JT_K = 16;
+__global__ void __launch_bounds__(256)
+k_rom_jac(RomDev d, int B, const double* __restrict__ prm, const float* __restrict__ GU, float* __restrict__ J) {
+    __shared__ float As[JT_K][JT_ROWS];
+    __shared__ float Bs[JT_K][JT_COLS];
+    const int Nr = d.Nr, M = d.M;
+    const int64_t ncol = (int64_t)B * Nr;
+    const int64_t c0 = (int64_t)blockIdx.x * JT_COLS;
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    float acc[4][8];
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int q = 0; q < 8; ++q) acc[r][q] = 0.f;
+    for (int k0 = 0; k0 < M; k0 += JT_K) {
+        for (int e = threadIdx.x; e < JT_K * JT_ROWS; e += 256) {
+            const int k = e / JT_ROWS, i = e % JT_ROWS;
+            As[k][i] = (i < Nr && k0 + k < M) ? d.Pf[(int64_t)i * M + k0 + k] : 0.f;
+        }
+        for (int e = threadIdx.x; e < JT_K * JT_COLS; e += 256) {
+            const int k = e / JT_COLS, q = e % JT_COLS;
+            const int64_t c = c0 + q;
+            Bs[k][q] = (c < ncol && k0 + k < M) ? GU[(int64_t)(k0 + k) * ncol + c] : 0.f;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < JT_K; ++k) {
+            float a[4], bq[8];
+#pragma unroll
+            for (int r = 0; r < 4; ++r) a[r] = As[k][ty * 4 + r];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) bq[q] = Bs[k][tx * 8 + q];
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+#pragma unroll
+                for (int q = 0; q < 8; ++q) acc[r][q] = fmaf(a[r], bq[q], acc[r][q]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        const int64_t c = c0 + tx * 8 + q;
+        if (c >= ncol) continue;
+        const int b = (int)(c / Nr), j = (int)(c % Nr);
+        const float dt_inv = (float)prm[RP * b + 3];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const int i = ty * 4 + r;
+            if (i >= Nr) continue;
+            J[((int64_t)b * Nr + i) * Nr + j] =
+                acc[r][q] + d.Msf[(int64_t)i * Nr + j] * dt_inv + d.Alinf[(int64_t)i * Nr + j];
+        }
+    }
+}
+
+// the same product for Nr > 64: row i of instance b per block
+__global__ void k_rom_jac_wide(RomDev d, int B, const double* __restrict__ prm, const float* __restrict__ GU,
+                               const int* __restrict__ active, float* __restrict__ J) {
     const int i = blockIdx.x, b = blockIdx.y;
     if (!active[b]) return;
-    const double dt_inv = prm[RP * b + 3];
-    const double* Pi = d.P + (int64_t)i * d.M;
-    const double* GUb = GU + (int64_t)b * d.M * d.Nr;
-    for (int j = threadIdx.x; j < d.Nr; j += blockDim.x) {
-        double acc = d.Ms[(int64_t)i * d.Nr + j] * dt_inv + d.Alin[(int64_t)i * d.Nr + j];
-        for (int p = 0; p < d.M; ++p) acc += Pi[p] * GUb[(int64_t)p * d.Nr + j];
-        J[((int64_t)b * d.Nr + i) * d.Nr + j] = acc;
+    const int Nr = d.Nr;
+    const float dt_inv = (float)prm[RP * b + 3];
+    const float* Pi = d.Pf + (int64_t)i * d.M;
+    for (int j = threadIdx.x; j < Nr; j += blockDim.x) {
+        float acc = 0.f;
+        for (int p = 0; p < d.M; ++p) acc = fmaf(Pi[p], GU[((int64_t)p * B + b) * Nr + j], acc);
+        J[((int64_t)b * Nr + i) * Nr + j] = acc + d.Msf[(int64_t)i * Nr + j] * dt_inv + d.Alinf[(int64_t)i * Nr + j];
     }
 }
 
@@ -233,6 +312,17 @@ __global__ void k_rom_resid(RomDev d, const double* __restrict__ a, const double
 }
 
 // block max / sum helpers (blockDim.x == 256)
+__device__ inline float block_maxf(float v, float* sh) {
+    sh[threadIdx.x] = v;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) sh[threadIdx.x] = fmaxf(sh[threadIdx.x], sh[threadIdx.x + s]);
+        __syncthreads();
+    }
+    float r = sh[0];
+    __syncthreads();
+    return r;
+}
 __device__ inline double block_max(double v, double* sh) {
     sh[threadIdx.x] = v;
     __syncthreads();
@@ -245,43 +335,43 @@ __device__ inline double block_max(double v, double* sh) {
     return r;
 }
 
-// delta[b] = -J[b]^-1 r[b]: row then column equilibration, LU with partial
-// pivoting (ties: lowest row), forward elimination of the right-hand side
-// during the factorisation, back substitution.  One block per instance,
-// J[b] overwritten.
+// delta[b] = -J[b]^-1 r[b] in FP32 (r FP64 on input, delta FP64 on output):
+// row then column equilibration, LU with partial pivoting (ties: lowest
+// row), forward elimination of the right-hand side during the
+// factorisation, back substitution.  One block per instance, J[b] overwritten.
 __global__ void __launch_bounds__(256)
-k_rom_lu(int Nr, double* __restrict__ J, const double* __restrict__ r, const int* __restrict__ active,
+k_rom_lu(int Nr, float* __restrict__ J, const double* __restrict__ r, const int* __restrict__ active,
          double* __restrict__ delta) {
     const int b = blockIdx.x;
     if (!active[b]) return;
-    __shared__ double sh[256];
-    __shared__ double rs[ROM_NR_MAX], cs[ROM_NR_MAX], rhs[ROM_NR_MAX], x[ROM_NR_MAX];
+    __shared__ float sh[256];
+    __shared__ float rs[ROM_NR_MAX], cs[ROM_NR_MAX], rhs[ROM_NR_MAX], x[ROM_NR_MAX];
     __shared__ int spiv;
-    double* A = J + (int64_t)b * Nr * Nr;
+    float* A = J + (int64_t)b * Nr * Nr;
     for (int i = threadIdx.x; i < Nr; i += blockDim.x) {
-        double m = 0.0;
-        for (int j = 0; j < Nr; ++j) m = fmax(m, fabs(A[(int64_t)i * Nr + j]));
-        rs[i] = m > 0.0 ? 1.0 / m : 1.0;
+        float m = 0.f;
+        for (int j = 0; j < Nr; ++j) m = fmaxf(m, fabsf(A[(int64_t)i * Nr + j]));
+        rs[i] = m > 0.f ? 1.f / m : 1.f;
     }
     __syncthreads();
     for (int j = threadIdx.x; j < Nr; j += blockDim.x) {
-        double m = 0.0;
-        for (int i = 0; i < Nr; ++i) m = fmax(m, fabs(A[(int64_t)i * Nr + j] * rs[i]));
-        cs[j] = m > 0.0 ? 1.0 / m : 1.0;
+        float m = 0.f;
+        for (int i = 0; i < Nr; ++i) m = fmaxf(m, fabsf(A[(int64_t)i * Nr + j] * rs[i]));
+        cs[j] = m > 0.f ? 1.f / m : 1.f;
     }
     __syncthreads();
     for (int idx = threadIdx.x; idx < Nr * Nr; idx += blockDim.x) {
         const int i = idx / Nr, j = idx % Nr;
         A[idx] *= rs[i] * cs[j];
     }
-    for (int i = threadIdx.x; i < Nr; i += blockDim.x) rhs[i] = -r[(int64_t)b * Nr + i] * rs[i];
+    for (int i = threadIdx.x; i < Nr; i += blockDim.x) rhs[i] = (float)(-r[(int64_t)b * Nr + i]) * rs[i];
     __syncthreads();
     for (int k = 0; k < Nr; ++k) {
         // pivot: largest |A[i][k]|, i >= k, lowest index on ties
-        double best = -1.0;
+        float best = -1.f;
         int bi = k;
         for (int i = k + threadIdx.x; i < Nr; i += blockDim.x) {
-            double v = fabs(A[(int64_t)i * Nr + k]);
+            float v = fabsf(A[(int64_t)i * Nr + k]);
             if (v > best) { best = v; bi = i; }
         }
         // reduce (value, index)
@@ -291,7 +381,7 @@ k_rom_lu(int Nr, double* __restrict__ J, const double* __restrict__ r, const int
         __syncthreads();
         for (int s = blockDim.x / 2; s > 0; s >>= 1) {
             if (threadIdx.x < s) {
-                double v2 = sh[threadIdx.x + s];
+                float v2 = sh[threadIdx.x + s];
                 int i2 = shi[threadIdx.x + s];
                 if (v2 > sh[threadIdx.x] || (v2 == sh[threadIdx.x] && i2 < shi[threadIdx.x])) {
                     sh[threadIdx.x] = v2;
@@ -305,20 +395,20 @@ k_rom_lu(int Nr, double* __restrict__ J, const double* __restrict__ r, const int
         const int piv = spiv;
         if (piv != k) {
             for (int j = threadIdx.x; j < Nr; j += blockDim.x) {
-                double t = A[(int64_t)k * Nr + j];
+                float t = A[(int64_t)k * Nr + j];
                 A[(int64_t)k * Nr + j] = A[(int64_t)piv * Nr + j];
                 A[(int64_t)piv * Nr + j] = t;
             }
             if (threadIdx.x == 0) {
-                double t = rhs[k]; rhs[k] = rhs[piv]; rhs[piv] = t;
+                float t = rhs[k]; rhs[k] = rhs[piv]; rhs[piv] = t;
             }
         }
         __syncthreads();
-        const double akk = A[(int64_t)k * Nr + k];
-        const double inv = akk != 0.0 ? 1.0 / akk : 0.0;
+        const float akk = A[(int64_t)k * Nr + k];
+        const float inv = akk != 0.f ? 1.f / akk : 0.f;
         // multipliers and right-hand side
         for (int i = k + 1 + threadIdx.x; i < Nr; i += blockDim.x) {
-            double l = A[(int64_t)i * Nr + k] * inv;
+            float l = A[(int64_t)i * Nr + k] * inv;
             A[(int64_t)i * Nr + k] = l;
             rhs[i] -= l * rhs[k];
         }
@@ -332,7 +422,7 @@ k_rom_lu(int Nr, double* __restrict__ J, const double* __restrict__ r, const int
     }
     // back substitution
     for (int k = Nr - 1; k >= 0; --k) {
-        double part = 0.0;
+        float part = 0.f;
         for (int j = k + 1 + threadIdx.x; j < Nr; j += blockDim.x) part += A[(int64_t)k * Nr + j] * x[j];
         sh[threadIdx.x] = part;
         __syncthreads();
@@ -341,12 +431,12 @@ k_rom_lu(int Nr, double* __restrict__ J, const double* __restrict__ r, const int
             __syncthreads();
         }
         if (threadIdx.x == 0) {
-            const double akk = A[(int64_t)k * Nr + k];
-            x[k] = akk != 0.0 ? (rhs[k] - sh[0]) / akk : 0.0;
+            const float akk = A[(int64_t)k * Nr + k];
+            x[k] = akk != 0.f ? (rhs[k] - sh[0]) / akk : 0.f;
         }
         __syncthreads();
     }
-    for (int j = threadIdx.x; j < Nr; j += blockDim.x) delta[(int64_t)b * Nr + j] = x[j] * cs[j];
+    for (int j = threadIdx.x; j < Nr; j += blockDim.x) delta[(int64_t)b * Nr + j] = (double)(x[j] * cs[j]);
 }
 
 // step length and convergence of instance b (one block per instance)
@@ -356,17 +446,22 @@ k_rom_update(RomDev d, double* __restrict__ a, const double* __restrict__ delta,
     const int b = blockIdx.x;
     if (!active[b]) return;
     __shared__ double sd[ROM_NR_MAX];
-    __shared__ double sh[256];
-    for (int j = threadIdx.x; j < d.Nr; j += blockDim.x) sd[j] = delta[(int64_t)b * d.Nr + j];
-    __syncthreads();
-    double m = 0.0;
-    for (int k = threadIdx.x; k < d.nloc; k += blockDim.x) {
-        double acc = 0.0;
-        for (int j = 0; j < d.Nr; ++j) acc += d.UlocC[(int64_t)j * d.nloc + k] * sd[j];
-        double v = fabs(acc) / d.us[k];
-        m = (v == v) ? fmax(m, v) : INFINITY;
+    __shared__ float sdf[ROM_NR_MAX];
+    __shared__ float sh[256];
+    for (int j = threadIdx.x; j < d.Nr; j += blockDim.x) {
+        sd[j] = delta[(int64_t)b * d.Nr + j];
+        sdf[j] = (float)sd[j];
     }
-    const double dn = block_max(m, sh);
+    __syncthreads();
+    // scaled max-norm of the reconstructed update (FP32: it only sets the step length and the stop)
+    float m = 0.f;
+    for (int k = threadIdx.x; k < d.nloc; k += blockDim.x) {
+        float acc = 0.f;
+        for (int j = 0; j < d.Nr; ++j) acc = fmaf(d.UlocCf[(int64_t)j * d.nloc + k], sdf[j], acc);
+        float v = fabsf(acc) / d.usf[k];
+        m = (v == v) ? fmaxf(m, v) : INFINITY;
+    }
+    const double dn = (double)block_maxf(m, sh);
     if (!(dn < INFINITY)) {
         if (threadIdx.x == 0) { failed[b] = 1; active[b] = 0; }
         return;
@@ -692,6 +787,17 @@ static int rom_build_host(mb_rom* R, const mb_rom_data* dd) {
               upr(d.bbnd, dd->bbnd, Nr) && upr(d.scp, dd->s_cp, Nr) && upr(d.sac, dd->s_ac, Nr) &&
               upr(d.a0, dd->a0, Nr);
     if (ok && !gface.empty()) ok = up(d.gface, gface);
+    // FP32 copies for the Newton matrix and the step-length norm
+    auto upf = [&](float*& dst, const double* src, size_t cnt) -> bool {
+        std::vector<float> h(src, src + cnt);
+        dst = rom_alloc<float>(R->owned, cnt);
+        if (!dst) return false;
+        return cudaMemcpy(dst, h.data(), 4 * (cnt ? cnt : 1), cudaMemcpyHostToDevice) == cudaSuccess;
+    };
+    if (ok)
+        ok = upf(d.Pf, P.data(), P.size()) && upf(d.Msf, dd->Ms, (size_t)Nr * Nr) &&
+             upf(d.Alinf, dd->Alin, (size_t)Nr * Nr) && upf(d.UlocRf, UlocR.data(), UlocR.size()) &&
+             upf(d.UlocCf, UlocC.data(), UlocC.size()) && upf(d.usf, us.data(), us.size());
     if (!ok) return cuda_fail(cudaGetLastError(), "rom upload");
     return MB_OK;
 }
@@ -706,12 +812,12 @@ static int rom_work_alloc(mb_rom* R, int B) {
     w.a_old = rom_alloc<double>(L, (size_t)B * d.Nr);
     w.delta = rom_alloc<double>(L, (size_t)B * d.Nr);
     w.r = rom_alloc<double>(L, (size_t)B * d.Nr);
-    w.J = rom_alloc<double>(L, (size_t)B * d.Nr * d.Nr);
+    w.J = rom_alloc<float>(L, (size_t)B * d.Nr * d.Nr);
     w.uloc = rom_alloc<double>(L, (size_t)B * d.nloc);
     w.uloc_old = rom_alloc<double>(L, (size_t)B * d.nloc);
     w.f = rom_alloc<double>(L, (size_t)B * d.M);
     w.G = rom_alloc<double>(L, (size_t)B * d.M * GMAX);
-    w.GU = rom_alloc<double>(L, (size_t)B * d.M * d.Nr);
+    w.GU = rom_alloc<float>(L, (size_t)B * (d.M ? d.M : 1) * d.Nr);
     w.prm = rom_alloc<double>(L, (size_t)B * RP);
     w.gate = rom_alloc<uint8_t>(L, (size_t)B * (d.ngate ? d.ngate : 1));
     w.gate2 = rom_alloc<uint8_t>(L, (size_t)B * (d.ngate ? d.ngate : 1));
@@ -811,9 +917,14 @@ int rom_batch_step(mb_rom* R) {
             k_rom_gather<<<gg, 256, 0, s>>>(d, w.a, w.uloc), count_launch(c);
             if (d.M) {
                 k_rom_ei<<<ge, 128, 0, s>>>(d, c->P, B, w.uloc, w.gate, w.prm, w.active, w.f, w.G), count_launch(c);
-                k_rom_gu<<<dim3((unsigned)d.M, (unsigned)B), 128, 0, s>>>(d, w.G, w.active, w.GU), count_launch(c);
+                k_rom_gu<<<dim3((unsigned)d.M, (unsigned)B), 64, 0, s>>>(d, B, w.G, w.active, w.GU), count_launch(c);
             }
-            k_rom_jac<<<dim3((unsigned)d.Nr, (unsigned)B), 128, 0, s>>>(d, w.prm, w.GU, w.active, w.J), count_launch(c);
+            if (d.Nr <= JT_ROWS)
+                k_rom_jac<<<(unsigned)(((int64_t)B * d.Nr + JT_COLS - 1) / JT_COLS), 256, 0, s>>>(d, B, w.prm, w.GU,
+                                                                                                   w.J), count_launch(c);
+            else
+                k_rom_jac_wide<<<dim3((unsigned)d.Nr, (unsigned)B), 128, 0, s>>>(d, B, w.prm, w.GU, w.active, w.J),
+                    count_launch(c);
             k_rom_resid<<<(unsigned)B, 128, 0, s>>>(d, w.a, w.a_old, w.prm, w.f, w.active, w.r), count_launch(c);
             k_rom_lu<<<(unsigned)B, 256, 0, s>>>(d.Nr, w.J, w.r, w.active, w.delta), count_launch(c);
             k_rom_update<<<(unsigned)B, 256, 0, s>>>(d, w.a, w.delta, w.active, w.failed, w.its), count_launch(c);

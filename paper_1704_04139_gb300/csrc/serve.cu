@@ -142,33 +142,53 @@ double cell_potential(mb_cell* c) {
     return s / (double)(N - last0);
 }
 
+// A worker keeps the cell it created for its first request and resets its
+// state for the next ones (no device allocation or release, which would
+// synchronise the device, in steady state).  A worker without a cell is
+// admitted while the cells' device memory stays within the budget.
 void fom_loop(mb_server* S) {
     cudaSetDevice(S->device);
+    mb_cell* c = nullptr;
+    int64_t charged = 0;   // this worker's share of fom_bytes
     for (;;) {
         std::shared_ptr<Req> q;
         {
             std::unique_lock<std::mutex> lk(S->m);
             S->cv.wait(lk, [&]() {
                 return S->stop || (!S->fom_q.empty() &&
-                                   (S->fom_bytes == 0 || S->fom_bytes + S->fom_cell_bytes <= S->o.fom_budget_bytes));
+                                   (c || S->fom_bytes == 0 || S->fom_bytes + S->fom_cell_bytes <= S->o.fom_budget_bytes));
             });
             if (S->stop) break;
             q = S->fom_q.front();
             S->fom_q.pop_front();
-            S->fom_bytes += S->fom_cell_bytes;
+            if (!c) {
+                charged = S->fom_cell_bytes;
+                S->fom_bytes += charged;
+            }
             q->t_start = S->now();
         }
-        mb_cell* c = nullptr;
-        int rc = mb_cell_create(S->labels.data(), S->o.nt, S->o.ny, S->o.nz, S->o.h, &S->prm, &S->fopts, &c);
-        if (!rc) rc = mb_cell_set_scales(c, q->r.prm.s_i0, q->r.prm.k_pl);
-        int64_t bytes = 0;
-        if (!rc) {
-            mb_cell_info info;
-            mb_cell_info_get(c, &info);
-            bytes = info.device_bytes;
-            std::lock_guard<std::mutex> lk(S->m);
-            if (!S->fom_cell_bytes) S->fom_cell_bytes = bytes;
+        int rc = MB_OK;
+        if (!c) {
+            rc = mb_cell_create(S->labels.data(), S->o.nt, S->o.ny, S->o.nz, S->o.h, &S->prm, &S->fopts, &c);
+            if (!rc) {
+                mb_cell_info info;
+                mb_cell_info_get(c, &info);
+                std::lock_guard<std::mutex> lk(S->m);
+                if (!S->fom_cell_bytes) S->fom_cell_bytes = info.device_bytes;
+                S->fom_bytes += info.device_bytes - charged;
+                charged = info.device_bytes;
+            } else {
+                c = nullptr;
+                std::lock_guard<std::mutex> lk(S->m);
+                S->fom_bytes -= charged;
+                charged = 0;
+            }
+        } else {
+            rc = mb::launch_init_state(c, c->u);
+            if (!rc && cudaStreamSynchronize(c->stream) != cudaSuccess)
+                rc = mb::cuda_fail(cudaGetLastError(), "fom reset");
         }
+        if (!rc) rc = mb_cell_set_scales(c, q->r.prm.s_i0, q->r.prm.k_pl);
         if (!rc) {
             q->V.push_back(cell_potential(c));
             q->S.push_back(NAN);
@@ -181,13 +201,16 @@ void fom_loop(mb_server* S) {
                 q->S.push_back(info.mean_c_solid);
             }
         }
-        if (c) mb_cell_destroy(c);
         {
             std::lock_guard<std::mutex> lk(S->m);
-            S->fom_bytes -= S->fom_cell_bytes;
             finish(S, q, rc);
         }
         S->cv.notify_all();
+    }
+    if (c) {
+        mb_cell_destroy(c);
+        std::lock_guard<std::mutex> lk(S->m);
+        S->fom_bytes -= charged;
     }
 }
 

@@ -60,9 +60,16 @@ def test_serving_mix_equals_alone(params):
     for _ in range(3):
         V_fom.append(fom_ref.step(1.0, -2.0 * i1)["V_cell"])
     fom_ref.close()
+    # a second full-order request with other scales: the worker reuses its cell, reset to the
+    # initial state, and must give what a fresh cell gives
+    fom_ref2 = B.Cell(lab, 1e-6, params)
+    fom_ref2.set_scales(0.7, 3.0)
+    V_fom2 = [fom_ref2.step(1.0, -4.0 * i1)["V_cell"] for _ in range(2)]
+    fom_ref2.close()
     srv = B.Server(rom=g, labels=lab, params=params, rom_slots=3, fom_workers=1)
     tk = {}
     tk["fom"] = srv.submit(B.REQ_FOM, -2.0 * i1, 1.0, 1.0, 3, 1.0)
+    tk["fom2"] = srv.submit(B.REQ_FOM, -4.0 * i1, 0.7, 3.0, 2, 1.0)
     for k in range(3):
         c, s, kp, n = reqs[k]
         tk[k] = srv.submit(B.REQ_ROM, c * i1, s, kp, n, 1.0)
@@ -81,5 +88,8 @@ def test_serving_mix_equals_alone(params):
     assert rf["status"] == 0
     assert np.array_equal(rf["V"][1:], np.array(V_fom[1:]))          # same kernels, same order
     assert abs(rf["V"][0] - V_fom[0]) <= 1e-14 * abs(V_fom[0])         # host means, different summation order
+    rf2 = res[tk["fom2"]]
+    assert rf2["status"] == 0 and rf2["t_start"] >= rf["t_done"]
+    assert np.array_equal(rf2["V"][1:], np.array(V_fom2))
     g.close()
     gc.close()
