@@ -316,7 +316,9 @@ def main():
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fp32-coarse", action="store_true",
-                    help="coarse-level products from FP32 operators instead of their BF16 copies")
+                    help="smoother and coarse-level products from FP32 operators instead of their BF16 copies")
+    ap.add_argument("--mg-stream", type=int, default=0, choices=[0, 1, 2],
+                    help="operator fetch of the BF16 coarse sweeps: 0 plain, 1 L2 prefetch, 2 staged in shared memory")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-rom", action="store_true", help="skip the reduced-model and serving measurements")
     ap.add_argument("--rom-instances", type=int, default=1024)
@@ -339,7 +341,7 @@ def main():
     prec = B.PREC_MIXED if args.precision == "mixed" else B.PREC_FP64
     opts = B.default_opts(precision=prec, newton_tol=1e-9, krylov_rtol=1e-4 if prec else 1e-6,
                           newton_maxit=20, krylov_maxit=300, max_halvings=3,
-                          mg_bf16=0 if args.fp32_coarse else 1)
+                          mg_bf16=0 if args.fp32_coarse else 1, mg_stream=args.mg_stream)
     cell = B.Cell(labels, 1e-6, params, opts)
     I = CRATE[args.workload] * cell.i_1c
     dt = 1.0
@@ -452,7 +454,7 @@ def main():
                "config": {"workload": args.workload, "voxels": int(cell.N), "plating_faces": int(cell.F),
                           "device_bytes": int(cell.device_bytes),
                           "dt_s": dt, "crate": CRATE[args.workload], "precision": args.precision,
-                          "coarse_operators": "fp32" if args.fp32_coarse else "bf16",
+                          "coarse_operators": "fp32" if args.fp32_coarse else "bf16", "mg_stream": args.mg_stream,
                           "l2": "working set > 129 MB L2, no flush", "parallelism": "replicas" if ws > 1 else "1 GPU"},
                "clocks": clk, "e2e": e2e, "gpu_launches": int(launches), "roofline": roof,
                "cpu_baseline": cpu,

@@ -78,8 +78,16 @@ typedef struct {
     int    mg_coarse_cells;/* multigrid: coarsen until at most this many cells */
     int    mg_smooth;      /* fine-level block-Jacobi sweeps before and after the coarse correction (1..8) */
     int    mg_kcycle;      /* FGMRES iterations of the level-1 K-cycle (1..16) */
-    int    mg_bf16;        /* 1: coarse-level smoothing, residuals and K-cycle products read BF16
-                              copies of the level operators (FP32 arithmetic); 0: FP32 operators */
+    int    mg_bf16;        /* 1: the fine smoother's stencil and the coarse-level operators are
+                              applied from BF16 copies (FP32 arithmetic); 0: FP32 operators */
+    int    mg_stream;      /* how the BF16 coarse sweeps and products fetch their operator rows
+                              (same results in every mode): 0 plain loads (default; the fastest
+                              measured on GB300: 50 % occupancy hides the latency); 1 each block first
+                              prefetches into L2 the rows of the block one resident wave ahead
+                              (bulk asynchronous prefetch); 2 post-smoothing sweeps of levels with
+                              at least one tile of 256 cells per SM stage rows, right-hand side and
+                              iterate in shared memory by bulk asynchronous copies (persistent,
+                              double-buffered) */
 } mb_solver_opts;
 
 typedef struct {

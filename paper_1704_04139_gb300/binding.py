@@ -38,7 +38,7 @@ class SolverOpts(C.Structure):
     _fields_ = [("precision", C.c_int), ("newton_tol", C.c_double), ("newton_maxit", C.c_int),
                 ("gmres_m", C.c_int), ("krylov_maxit", C.c_int), ("krylov_rtol", C.c_double),
                 ("max_passes", C.c_int), ("max_halvings", C.c_int), ("mg_coarse_cells", C.c_int),
-                ("mg_smooth", C.c_int), ("mg_kcycle", C.c_int), ("mg_bf16", C.c_int)]
+                ("mg_smooth", C.c_int), ("mg_kcycle", C.c_int), ("mg_bf16", C.c_int), ("mg_stream", C.c_int)]
 
 
 class StepInfo(C.Structure):

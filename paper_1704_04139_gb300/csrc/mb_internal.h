@@ -228,6 +228,8 @@ int precond_apply(mb_cell* c, const float* u32, const uint8_t* gate, double dt, 
                   bool graph = true);
 // add the kernel times of the last graph execution to the profile totals
 void precond_harvest(mb_cell* c);
+// MB_ETIMEOUT if a staged coarse sweep gave up waiting for its copies (synchronises the stream)
+int precond_check(mb_cell* c);
 
 // ---- rom.cu: slot batch of the reduced model (one step per call) ----
 int rom_batch_alloc(mb_rom* R, int B);

@@ -57,6 +57,7 @@ constexpr int MAX_LEVELS = 16;
 constexpr int COARSE_MAX = 256;           // dense coarsest system size bound (4 x cells)
 constexpr int FCW = 8;                    // floats of condensation coefficients per face
 constexpr int FSTK = 14;                  // row blocks of the assembled fine stencil per voxel
+constexpr int SWT = 256;                  // cells per tile of the staged coarse sweep (= its threads)
 
 // float-float 4-vector of one coarse cell
 struct alignas(32) DF4 {
@@ -104,7 +105,8 @@ struct Level {
     float* aself = nullptr;   // 16 x cells  self block ex - sum_d off_d (absent classes fixed up)
     float* sinv = nullptr;    // 16 x cells  inverse of the self block
     uint8_t* mask = nullptr;  // cells: classes present
-    uint2* pk = nullptr;      // 32 x cells  BF16 copy: rows of off_0..off_5, exd, sinv (4 BF16 per row)
+    uint2* pk = nullptr;      // 32 x pst  BF16 copy: rows of off_0..off_5, exd, sinv (4 BF16 per row)
+    int64_t pst = 0;          // row stride of pk: cells rounded up to a whole tile of the staged sweep
     DF4* x = nullptr;         // cells
     DF4* x2 = nullptr;        // cells
     float4* b = nullptr;      // cells
@@ -139,6 +141,10 @@ struct Precond {
     int* cstat = nullptr;
     int kcyc = 0;              // level-1 K-cycle length
     bool b16 = false;          // applications read the BF16 operator copies
+    int nsm = 0;               // SMs of the device (grid of the persistent staged sweep)
+    int pf[3] = {0, 0, 0};     // L2 prefetch distance (blocks of one resident wave) of the BF16
+                               // sweep, fused first sweeps and product
+    int* err = nullptr;        // device flag: a bounded wait of a staged sweep gave up
     int nu_fine = 0;           // fine-level block-Jacobi sweeps before and after the coarse correction
     // level-1 K-cycle workspace
     float* kV = nullptr;       // (KCYC_MAX+1) x m4  FP32 basis
@@ -537,7 +543,7 @@ __global__ void k_finalize(Level L) {
             uint32_t h[NCLS];
             for (int kk = 0; kk < NCLS; ++kk)
                 h[kk] = __bfloat16_as_ushort(__float2bfloat16_rn(src[(int64_t)(k * NCLS + kk) * L.cells + cell]));
-            L.pk[(int64_t)(4 * q + k) * L.cells + cell] = make_uint2(h[0] | (h[1] << 16), h[2] | (h[3] << 16));
+            L.pk[(int64_t)(4 * q + k) * L.pst + cell] = make_uint2(h[0] | (h[1] << 16), h[2] | (h[3] << 16));
         }
     }
 }
@@ -863,7 +869,7 @@ __device__ inline float4 mv4b(const uint2* __restrict__ m, int64_t st, float4 x)
 // block q of the level operator (0..5 off_d, 6 exd, 7 sinv) times x
 template <bool B16>
 __device__ inline float4 lvl_mv(const Level& L, int q, int64_t cell, float4 x) {
-    if (B16) return mv4b(L.pk + (int64_t)4 * q * L.cells + cell, L.cells, x);
+    if (B16) return mv4b(L.pk + (int64_t)4 * q * L.pst + cell, L.pst, x);
     const float* m = q < 6 ? L.off + (int64_t)q * BLK * L.cells : (q == 6 ? L.exd : L.sinv);
     return mv4(m + cell, L.cells, x);
 }
@@ -920,10 +926,70 @@ __device__ inline void cell_coords(const Level& L, int64_t cell, int& t, int& y,
     t = (int)(cell / ((int64_t)L.nz * L.ny));
 }
 
+// --------------------------------------- bulk asynchronous copies (PTX)
+constexpr int SW_OP = 32 * SWT * 8;                    // operator rows of a tile
+constexpr int SW_STAGE = SW_OP + SWT * 16 + SWT * 32;   // + rhs + iterate
+constexpr int SW_SMEM = 2 * SW_STAGE;
+constexpr int SW_SPIN = 1 << 22;
+
+__device__ inline uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ inline void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ inline void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    uint64_t state;
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 %0, [%1], %2;"
+                 : "=l"(state)
+                 : "r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+    (void)state;
+}
+__device__ inline bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ inline bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+    for (int i = 0; i < SW_SPIN; ++i)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+// global -> shared bulk copy (16-byte aligned addresses, size a multiple of 16)
+__device__ inline void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(smem_addr(dst)), "l"(src), "r"(bytes), "r"(smem_addr(bar))
+                 : "memory");
+}
+
+// L2 prefetch of a global range (16-byte aligned, size a multiple of 16)
+__device__ inline void bulk_prefetch_l2(const void* src, uint32_t bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
+}
+// one thread: L2 prefetch of the operator rows [r0, r1) of the block of SWT
+// cells `blk` (and its right-hand side and iterate when given)
+__device__ inline void lvl_prefetch(const Level& L, int64_t blk, int r0, int r1, const void* x) {
+    const int64_t c0 = blk * SWT;
+    if (c0 >= L.cells) return;
+    const int nv = (int)(L.cells - c0 < SWT ? L.cells - c0 : SWT);
+    for (int r = r0; r < r1; ++r) bulk_prefetch_l2(L.pk + (int64_t)r * L.pst + c0, SWT * 8);
+    if (L.b) bulk_prefetch_l2(L.b + c0, (uint32_t)nv * 16);
+    if (x) bulk_prefetch_l2(static_cast<const DF4*>(x) + c0, (uint32_t)nv * 32);
+}
+
 // x_out = xe + omega Sinv (b - A xe), xe = x_in (+ prolonged ec); both absent: x_out = omega Sinv b
+// pf > 0 (BF16 operators, blocks of SWT threads): the block's thread 0 first
+// prefetches into L2 the operator rows, right-hand side and iterate of block
+// blockIdx.x + pf, about one resident wave ahead
 template <bool B16>
 __global__ void k_lvl_smooth(Level L, const DF4* __restrict__ x_in, const DF4* __restrict__ ec, int ccny,
-                             int ccnz, float omega, DF4* __restrict__ x_out) {
+                             int ccnz, float omega, DF4* __restrict__ x_out, int pf) {
+    if (B16 && pf > 0 && threadIdx.x == 0) lvl_prefetch(L, (int64_t)blockIdx.x + pf, 0, 32, x_in);
     int64_t cell = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (cell >= L.cells) return;
     int t, y, z;
@@ -941,11 +1007,99 @@ __global__ void k_lvl_smooth(Level L, const DF4* __restrict__ x_in, const DF4* _
     x_out[cell] = df4_add_f(xe, f4scale(omega, lvl_mv<B16>(L, 7, cell, r)));
 }
 
+// ---------------------------------------- staged sweep (bulk async copies)
+// The same sweep as k_lvl_smooth<true> from an iterate, with the tile's
+// operator rows, right-hand side and iterate moved into shared memory by
+// cp.async.bulk (completion counted on an mbarrier) while the previous tile
+// is computed: a persistent grid, one CTA of SWT threads per SM, two stages.
+// The neighbours' iterates (and the prolonged correction) are read from
+// global memory (L1/L2).  Every wait is bounded; on a timeout the CTA sets
+// *err, waits (bounded) for its copies in flight and returns.
+// one thread: copies of tile `tile` into stage buffer sb
+__device__ inline void sw_issue(const Level& L, const DF4* x_in, int64_t tile, uint8_t* sb, uint64_t* bar) {
+    const int64_t c0 = tile * SWT;
+    const int nv = (int)(L.cells - c0 < SWT ? L.cells - c0 : SWT);
+    mbar_expect_tx(bar, (uint32_t)(SW_OP + nv * 16 + nv * 32));
+    for (int r = 0; r < 32; ++r)
+        bulk_g2s(sb + (size_t)r * SWT * 8, L.pk + (int64_t)r * L.pst + c0, SWT * 8, bar);
+    bulk_g2s(sb + SW_OP, L.b + c0, (uint32_t)nv * 16, bar);
+    bulk_g2s(sb + SW_OP + SWT * 16, x_in + c0, (uint32_t)nv * 32, bar);
+}
+
+__global__ void __launch_bounds__(SWT, 1)
+k_lvl_smooth_staged(Level L, const DF4* __restrict__ x_in, const DF4* __restrict__ ec, int ccny, int ccnz,
+                    float omega, DF4* __restrict__ x_out, int* __restrict__ err) {
+    extern __shared__ __align__(128) uint8_t sw_smem[];
+    __shared__ __align__(8) uint64_t bar[2];
+    const int tid = threadIdx.x;
+    const int64_t ntiles = (L.cells + SWT - 1) / SWT;
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    int64_t tile = blockIdx.x;
+    if (tid == 0 && tile < ntiles) sw_issue(L, x_in, tile, sw_smem, &bar[0]);
+    uint32_t parity[2] = {0u, 0u};
+    bool pending[2] = {tile < ntiles, false};
+    int st = 0;
+    for (; tile < ntiles; tile += gridDim.x) {
+        const int64_t next = tile + gridDim.x;
+        if (next < ntiles) {
+            // the other stage was released by the barrier at the end of the previous tile
+            if (tid == 0) {
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                sw_issue(L, x_in, next, sw_smem + (st ^ 1) * SW_STAGE, &bar[st ^ 1]);
+            }
+            pending[st ^ 1] = true;
+        }
+        const bool ok = __syncthreads_and(mbar_wait_bounded(&bar[st], parity[st]));
+        if (!ok) {
+            if (tid == 0) {
+                atomicOr(err, 1);
+                for (int k = 0; k < 2; ++k)
+                    if (pending[k]) mbar_wait_bounded(&bar[k], parity[k]);
+            }
+            return;
+        }
+        pending[st] = false;
+        parity[st] ^= 1u;
+        const int64_t cell = tile * SWT + tid;
+        if (cell < L.cells) {
+            const uint8_t* sb = sw_smem + st * SW_STAGE;
+            const uint2* op = reinterpret_cast<const uint2*>(sb);
+            int t, y, z;
+            cell_coords(L, cell, t, y, z);
+            DF4 xe = reinterpret_cast<const DF4*>(sb + SW_OP + SWT * 16)[tid];
+            if (ec) xe = df4_add(xe, ec[((int64_t)(t >> 1) * ccny + (y >> 1)) * ccnz + (z >> 1)]);
+            float4 acc = mv4b(op + 24 * SWT + tid, SWT, df4_val(xe));
+            const int64_t syz = (int64_t)L.ny * L.nz;
+            const bool inb[6] = {t > 0, t < L.nt - 1, y > 0, y < L.ny - 1, z > 0, z < L.nz - 1};
+            const int64_t stp[6] = {-syz, syz, -(int64_t)L.nz, (int64_t)L.nz, -1, 1};
+            const int dt_[6] = {-1, 1, 0, 0, 0, 0}, dy_[6] = {0, 0, -1, 1, 0, 0}, dz_[6] = {0, 0, 0, 0, -1, 1};
+#pragma unroll
+            for (int d = 0; d < 6; ++d) {
+                const int tt = inb[d] ? t + dt_[d] : t, yy = inb[d] ? y + dy_[d] : y, zz = inb[d] ? z + dz_[d] : z;
+                const int64_t nb = inb[d] ? cell + stp[d] : cell;
+                acc = f4add(acc, mv4b(op + 4 * d * SWT + tid, SWT,
+                                      df4_diff(xeff(x_in, ec, ccny, ccnz, tt, yy, zz, nb), xe)));
+            }
+            const float4 b = reinterpret_cast<const float4*>(sb + SW_OP)[tid];
+            const float4 r = f4sub(b, acc);
+            x_out[cell] = df4_add_f(xe, f4scale(omega, mv4b(op + 28 * SWT + tid, SWT, r)));
+        }
+        __syncthreads();
+        st ^= 1;
+    }
+}
+
 // the first two sweeps from zero in one pass: x2 = x1 + omega Sinv (b - A x1)
 // with x1 = omega Sinv b evaluated where it is needed (the cell and its
 // neighbours), bit-identical to two k_lvl_smooth launches
 template <bool B16>
-__global__ void k_lvl_smooth2(Level L, float omega, DF4* __restrict__ x_out) {
+__global__ void k_lvl_smooth2(Level L, float omega, DF4* __restrict__ x_out, int pf) {
+    if (B16 && pf > 0 && threadIdx.x == 0) lvl_prefetch(L, (int64_t)blockIdx.x + pf, 0, 32, nullptr);
     int64_t cell = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (cell >= L.cells) return;
     int t, y, z;
@@ -958,7 +1112,8 @@ __global__ void k_lvl_smooth2(Level L, float omega, DF4* __restrict__ x_out) {
 }
 
 template <bool B16>
-__global__ void k_lvl_matvec(Level L, const DF4* __restrict__ x, float4* __restrict__ y_out) {
+__global__ void k_lvl_matvec(Level L, const DF4* __restrict__ x, float4* __restrict__ y_out, int pf) {
+    if (B16 && pf > 0 && threadIdx.x == 0) lvl_prefetch(L, (int64_t)blockIdx.x + pf, 0, 28, x);
     int64_t cell = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (cell >= L.cells) return;
     int t, y, z;
@@ -1177,6 +1332,24 @@ int precond_create(mb_cell* c) {
     p->rv = (float*)cell_alloc(c, 8 * D.N);
     p->t = (float*)cell_alloc(c, 8 * D.N);
     p->b16 = c->opt.mg_bf16 != 0;
+    {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&p->nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || p->nsm < 1)
+            return cuda_fail(cudaGetLastError(), "multiprocessor count");
+        if (cudaFuncSetAttribute(k_lvl_smooth_staged, cudaFuncAttributeMaxDynamicSharedMemorySize, SW_SMEM) !=
+            cudaSuccess)
+            return cuda_fail(cudaGetLastError(), "staged sweep shared memory");
+        int nb[3] = {0, 0, 0};
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb[0], k_lvl_smooth<true>, 256, 0) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb[1], k_lvl_smooth2<true>, 256, 0) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb[2], k_lvl_matvec<true>, 256, 0) != cudaSuccess)
+            return cuda_fail(cudaGetLastError(), "occupancy");
+        for (int k = 0; k < 3; ++k) p->pf[k] = (nb[k] > 0 ? nb[k] : 1) * p->nsm;
+    }
+    p->err = (int*)cell_alloc(c, 16);
+    if (!p->err) return MB_ENOMEM;
+    MB_CUDA(cudaMemsetAsync(p->err, 0, 16, c->stream));
     p->fst = cell_alloc(c, (p->b16 ? 4 : 8) * (size_t)FSTK * D.N);
     p->zs = (float2*)cell_alloc(c, 16 * (size_t)D.N);
     if (!p->fst || !p->zs) return MB_ENOMEM;
@@ -1203,7 +1376,8 @@ int precond_create(mb_cell* c) {
         L.x = (DF4*)cell_alloc(c, sizeof(DF4) * (size_t)L.cells);
         L.x2 = (DF4*)cell_alloc(c, sizeof(DF4) * (size_t)L.cells);
         L.b = (float4*)cell_alloc(c, 16 * (size_t)L.cells);
-        L.pk = (uint2*)cell_alloc(c, 8 * 32 * (size_t)L.cells);
+        L.pst = (L.cells + SWT - 1) / SWT * SWT;
+        L.pk = (uint2*)cell_alloc(c, 8 * 32 * (size_t)L.pst);
         if (!L.off || !L.ex || !L.exd || !L.aself || !L.sinv || !L.mask || !L.x || !L.x2 || !L.b || !L.pk)
             return MB_ENOMEM;
         if (L.cells <= coarse_cells) break;
@@ -1277,10 +1451,15 @@ static void lvl_smooth(mb_cell* c, Level& L, const DF4* xin, const DF4* ec, int 
     cudaEvent_t ev = nullptr;
     timed = timed && (xin || ec);
     if (timed) prof_begin(c, s, &ev);
-    if (c->pc->b16)
-        k_lvl_smooth<true><<<g, 256, 0, s>>>(L, xin, ec, ccny, ccnz, OMEGA_COARSE, xout);
+    const Precond* p = c->pc;
+    const int64_t ntiles = (L.cells + SWT - 1) / SWT;
+    if (p->b16 && c->opt.mg_stream == 2 && xin && ntiles >= p->nsm)
+        k_lvl_smooth_staged<<<p->nsm, SWT, SW_SMEM, s>>>(L, xin, ec, ccny, ccnz, OMEGA_COARSE, xout, p->err);
+    else if (p->b16)
+        k_lvl_smooth<true><<<g, 256, 0, s>>>(L, xin, ec, ccny, ccnz, OMEGA_COARSE, xout,
+                                             c->opt.mg_stream == 1 ? p->pf[0] : 0);
     else
-        k_lvl_smooth<false><<<g, 256, 0, s>>>(L, xin, ec, ccny, ccnz, OMEGA_COARSE, xout);
+        k_lvl_smooth<false><<<g, 256, 0, s>>>(L, xin, ec, ccny, ccnz, OMEGA_COARSE, xout, 0);
     ::mb::count_launch(c);
     if (timed) prof_end(c, s, PROF_LSMOOTH, ev);
 }
@@ -1288,9 +1467,9 @@ static void lvl_smooth2(mb_cell* c, Level& L, DF4* xout) {
     cudaStream_t s = c->stream;
     unsigned g = nblk(L.cells);
     if (c->pc->b16)
-        k_lvl_smooth2<true><<<g, 256, 0, s>>>(L, OMEGA_COARSE, xout);
+        k_lvl_smooth2<true><<<g, 256, 0, s>>>(L, OMEGA_COARSE, xout, c->opt.mg_stream == 1 ? c->pc->pf[1] : 0);
     else
-        k_lvl_smooth2<false><<<g, 256, 0, s>>>(L, OMEGA_COARSE, xout);
+        k_lvl_smooth2<false><<<g, 256, 0, s>>>(L, OMEGA_COARSE, xout, 0);
     ::mb::count_launch(c);
 }
 static void lvl_restrict(mb_cell* c, Level& L, const DF4* x, Level& C) {
@@ -1306,9 +1485,10 @@ static void lvl_matvec(mb_cell* c, Level& L, const DF4* x, float* y) {
     cudaStream_t s = c->stream;
     unsigned g = nblk(L.cells);
     if (c->pc->b16)
-        k_lvl_matvec<true><<<g, 256, 0, s>>>(L, x, reinterpret_cast<float4*>(y));
+        k_lvl_matvec<true><<<g, 256, 0, s>>>(L, x, reinterpret_cast<float4*>(y),
+                                             c->opt.mg_stream == 1 ? c->pc->pf[2] : 0);
     else
-        k_lvl_matvec<false><<<g, 256, 0, s>>>(L, x, reinterpret_cast<float4*>(y));
+        k_lvl_matvec<false><<<g, 256, 0, s>>>(L, x, reinterpret_cast<float4*>(y), 0);
     ::mb::count_launch(c);
 }
 
@@ -1462,6 +1642,17 @@ static void fine_product(mb_cell* c, const float2* zin, float* tout) {
     else
         k_fine_stencil<false, false><<<vg, PB, 0, s>>>(D, p->fst, nullptr, nullptr, zin, 0.f, nullptr, tout);
     ::mb::count_launch(c);
+}
+
+int precond_check(mb_cell* c) {
+    int h = 0;
+    MB_CUDA(cudaMemcpyAsync(&h, c->pc->err, 4, cudaMemcpyDeviceToHost, c->stream));
+    MB_CUDA(cudaStreamSynchronize(c->stream));
+    if (h) {
+        set_error("preconditioner: a bounded wait for staged operator data gave up");
+        return MB_ETIMEOUT;
+    }
+    return MB_OK;
 }
 
 int precond_setup_fine(mb_cell* c) {

@@ -320,6 +320,7 @@ static int linear_solve(mb_cell* c, double dt, int* its, double* relres) {
     k_scale_rhs<<<nblk(n), 256, 0, s>>>(c->D, c->vcode, c->r, inv_scales(c, 1, dt), c->rowinv, K->b), ::mb::count_launch(c);
     OpCtx o{c->u32, c->gate, dt};
     rc = fgmres(c, K, o, c->opt.krylov_rtol, c->opt.krylov_maxit, its, relres);
+    if (!rc) rc = precond_check(c);
     if (rc) return rc;
     k_unscale<<<nblk(n), 256, 0, s>>>(c->P, c->D, c->vcode, K->x, c->du), ::mb::count_launch(c);
     MB_CUDA_LAUNCH("linear_solve");
