@@ -77,7 +77,7 @@ typedef struct {
     int    max_halvings;   /* dt halvings on Newton failure */
     int    mg_coarse_cells;/* multigrid: coarsen until at most this many cells */
     int    mg_smooth;      /* fine-level block-Jacobi sweeps before and after the coarse correction (1..8) */
-    int    mg_kcycle;      /* FGMRES iterations of the level-1 K-cycle (1..16) */
+    int    mg_kcycle;      /* FGMRES iterations of the level-1 K-cycle (1..16; default 5) */
     int    mg_bf16;        /* 1: the fine smoother's stencil and the coarse-level operators are
                               applied from BF16 copies (FP32 arithmetic); 0: FP32 operators */
     int    mg_stream;      /* how the BF16 coarse sweeps and products fetch their operator rows

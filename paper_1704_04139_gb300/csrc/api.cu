@@ -109,7 +109,7 @@ void mb_opts_default(mb_solver_opts* o) {
     o->max_halvings = 6;
     o->mg_coarse_cells = 32;
     o->mg_smooth = 2;
-    o->mg_kcycle = 6;
+    o->mg_kcycle = 5;
     o->mg_bf16 = 1;
     o->mg_stream = 0;
 }

@@ -580,22 +580,35 @@ __global__ void k_coarse_dense(Level L, int n, double* __restrict__ Ad) {
     }
 }
 
-// Gauss-Jordan inverse with partial pivoting, one block.
+// Gauss-Jordan inverse with partial pivoting (largest magnitude, lowest row
+// on ties), one block; the pivot search is a block reduction.
 __global__ void k_coarse_invert(int n, double* __restrict__ A, double* __restrict__ Ainv, int* __restrict__ stat) {
     __shared__ int piv;
     __shared__ double pval;
+    __shared__ double wv[32];
+    __shared__ int wi[32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
     for (int i = threadIdx.x; i < n * n; i += blockDim.x) Ainv[i] = (i / n == i % n) ? 1.0 : 0.0;
     __syncthreads();
     for (int col = 0; col < n; ++col) {
+        double best = -1.0;
+        int bi = n;
+        for (int r = col + threadIdx.x; r < n; r += blockDim.x) {
+            const double v = fabs(A[(int64_t)r * n + col]);
+            if (v > best) { best = v; bi = r; }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            const double v2 = __shfl_down_sync(0xffffffffu, best, o);
+            const int i2 = __shfl_down_sync(0xffffffffu, bi, o);
+            if (v2 > best || (v2 == best && i2 < bi)) { best = v2; bi = i2; }
+        }
+        if (lane == 0) { wv[wid] = best; wi[wid] = bi; }
+        __syncthreads();
         if (threadIdx.x == 0) {
-            int p = col;
-            double best = fabs(A[(int64_t)col * n + col]);
-            for (int r = col + 1; r < n; ++r) {
-                double v = fabs(A[(int64_t)r * n + col]);
-                if (v > best) { best = v; p = r; }
-            }
-            piv = p;
-            pval = A[(int64_t)p * n + col];
+            for (int w = 1; w < nw; ++w)
+                if (wv[w] > best || (wv[w] == best && wi[w] < bi)) { best = wv[w]; bi = wi[w]; }
+            piv = bi;
+            pval = A[(int64_t)bi * n + col];
             if (pval == 0.0) *stat = 1;
         }
         __syncthreads();

@@ -75,6 +75,40 @@ __global__ void k_mupdate(const float* __restrict__ V, int64_t stride, int cnt, 
     w[i] = fmaf(sign, acc, w[i]);
 }
 
+// w -= sum_j h[j] V_j (as k_mupdate with sign -1), then the block partials
+// of the updated w against V_j, j < cnt <= MDOT_G (NORM: against itself), in
+// the grid and summation order of k_mdot: one pass of classical Gram-Schmidt
+// fused with the products that follow it
+template <bool NORM>
+__global__ void __launch_bounds__(RED_THREADS)
+k_mupd_dot(const float* __restrict__ V, int64_t stride, int cnt, HParam hp, float* __restrict__ w, int64_t n,
+           double* partials) {
+    constexpr int K = NORM ? 1 : MDOT_G;
+    float a32[K];
+#pragma unroll
+    for (int j = 0; j < K; ++j) a32[j] = 0.f;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        float v[MDOT_G];
+        float acc = 0.f;
+#pragma unroll
+        for (int j = 0; j < MDOT_G; ++j)
+            if (j < cnt) {
+                v[j] = V[j * stride + i];
+                acc = fmaf(hp.h[j], v[j], acc);
+            }
+        const float wi = fmaf(-1.f, acc, w[i]);
+        w[i] = wi;
+        if (NORM) {
+            a32[0] = fmaf(wi, wi, a32[0]);
+        } else {
+#pragma unroll
+            for (int j = 0; j < K; ++j)
+                if (j < cnt) a32[j] = fmaf(v[j], wi, a32[j]);
+        }
+    }
+    block_reduce_store_f32<K>(a32, partials);
+}
+
 // x += sum_j y[j] Z_j in float-float arithmetic
 __global__ void k_combine(const float2* __restrict__ Z, int64_t stride, int cnt, HParamDF hp,
                           float2* __restrict__ x, int64_t n) {
@@ -147,6 +181,26 @@ static int mdot(mb_cell* c, const float* V, int64_t stride, int cnt, const float
     MB_CUDA(cudaMemcpyAsync(c->h_red, c->red_out, 8 * cnt, cudaMemcpyDeviceToHost, s));
     MB_CUDA(cudaStreamSynchronize(s));
     memcpy(out, c->h_red, 8 * cnt);
+    return MB_OK;
+}
+
+// w -= sum_j h[j] V_j, then out[j] = <V_j, w> (j < cnt) or, norm, out[0] = <w, w>;
+// cnt <= MDOT_G
+static int mupdate_dot(mb_cell* c, const float* V, int64_t stride, int cnt, const double* h, float* w, int64_t n,
+                       bool norm, double* out) {
+    cudaStream_t s = c->stream;
+    HParam hp;
+    for (int j = 0; j < cnt; ++j) hp.h[j] = (float)h[j];
+    const int k = norm ? 1 : cnt;
+    if (norm)
+        k_mupd_dot<true><<<RED_BLOCKS, RED_THREADS, 0, s>>>(V, stride, cnt, hp, w, n, c->red), ::mb::count_launch(c);
+    else
+        k_mupd_dot<false><<<RED_BLOCKS, RED_THREADS, 0, s>>>(V, stride, cnt, hp, w, n, c->red), ::mb::count_launch(c);
+    k_reduce_final<false><<<k, RED_THREADS, 0, s>>>(c->red, k, c->red_out), ::mb::count_launch(c);
+    MB_CUDA_LAUNCH("mupdate_dot");
+    MB_CUDA(cudaMemcpyAsync(c->h_red, c->red_out, 8 * k, cudaMemcpyDeviceToHost, s));
+    MB_CUDA(cudaStreamSynchronize(s));
+    memcpy(out, c->h_red, 8 * k);
     return MB_OK;
 }
 
@@ -228,19 +282,26 @@ static int fgmres(mb_cell* c, Krylov* K, const OpCtx& o, double rtol, int maxit,
             if (rc) return rc;
             rc = apply_op(c, o, Zj, K->w);
             if (rc) return rc;
-            // CGS2
+            // CGS2 (for up to MDOT_G basis vectors each update fused with the products after it)
             rc = mdot(c, K->V, n, j + 1, K->w, n, hv.data());
             if (rc) return rc;
-            rc = mupdate(c, K->V, n, j + 1, hv.data(), K->w, n, -1.f);
-            if (rc) return rc;
-            rc = mdot(c, K->V, n, j + 1, K->w, n, h2.data());
-            if (rc) return rc;
-            rc = mupdate(c, K->V, n, j + 1, h2.data(), K->w, n, -1.f);
-            if (rc) return rc;
-            for (int i = 0; i <= j; ++i) hv[i] += h2[i];
             double d;
-            rc = mdot(c, K->w, 0, 1, K->w, n, &d);
-            if (rc) return rc;
+            if (j + 1 <= MDOT_G) {
+                rc = mupdate_dot(c, K->V, n, j + 1, hv.data(), K->w, n, false, h2.data());
+                if (rc) return rc;
+                rc = mupdate_dot(c, K->V, n, j + 1, h2.data(), K->w, n, true, &d);
+                if (rc) return rc;
+            } else {
+                rc = mupdate(c, K->V, n, j + 1, hv.data(), K->w, n, -1.f);
+                if (rc) return rc;
+                rc = mdot(c, K->V, n, j + 1, K->w, n, h2.data());
+                if (rc) return rc;
+                rc = mupdate(c, K->V, n, j + 1, h2.data(), K->w, n, -1.f);
+                if (rc) return rc;
+                rc = mdot(c, K->w, 0, 1, K->w, n, &d);
+                if (rc) return rc;
+            }
+            for (int i = 0; i <= j; ++i) hv[i] += h2[i];
             double hn = sqrt(d);
             hv[j + 1] = hn;
             if (hn > 0) k_scale<<<nblk(n), 256, 0, s>>>(K->w, (float)(1.0 / hn), K->V + (j + 1) * n, n), ::mb::count_launch(c);
