@@ -77,7 +77,9 @@ struct RomWork {
     double *a = nullptr, *a_old = nullptr, *delta = nullptr, *r = nullptr;
     float* J = nullptr;        // B x Nr x Nr, instance-major
     float* GU = nullptr;       // M x B x Nr: row p of every instance's G U_loc (the GEMM's right operand)
-    double *uloc = nullptr, *uloc_old = nullptr, *f = nullptr, *G = nullptr;
+    double *uloc = nullptr, *uloc_old = nullptr, *f = nullptr;
+    float* G = nullptr;        // B x M x GMAX derivative lists (FP32: they only feed the Newton matrix)
+    float* dpart = nullptr;    // B x ceil(nloc / UN_K): partial maxima of the step-length norm
     double* prm = nullptr;
     uint8_t *gate = nullptr, *gate2 = nullptr;
     int *active = nullptr, *failed = nullptr, *pass_on = nullptr, *counts = nullptr;
@@ -138,19 +140,19 @@ __global__ void k_rom_gate(RomDev d, int B, const double* __restrict__ uloc, con
     gate[i] = (uo[s[2]] > n_thr || etap < 0.0) ? 1 : 0;
 }
 
-// f and its derivative list at every point
-__global__ void k_rom_ei(RomDev d, DevParams P, int B, const double* __restrict__ uloc,
+// f (FP64) and its derivative list (FP32) at every point
+__global__ void k_rom_ei(RomDev d, DevParams P, ParT<float> Pf, int B, const double* __restrict__ uloc,
                          const uint8_t* __restrict__ gate, const double* __restrict__ prm,
-                         const int* __restrict__ active, double* __restrict__ f, double* __restrict__ G) {
+                         const int* __restrict__ active, double* __restrict__ f, float* __restrict__ G) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= (int64_t)d.M * B) return;
     const int b = (int)(i / d.M), p = (int)(i % d.M);
     if (!active[b]) return;
     const double* u = uloc + (int64_t)b * d.nloc;
     const double s_i0 = prm[RP * b + 1], k_pl = prm[RP * b + 2];
-    double g[GMAX];
+    float g[GMAX];
 #pragma unroll
-    for (int e = 0; e < GMAX; ++e) g[e] = 0.0;
+    for (int e = 0; e < GMAX; ++e) g[e] = 0.f;
     double fv = 0.0;
     for (int t = 0; t < TMAX; ++t) {
         const int q = p * TMAX + t;
@@ -165,20 +167,22 @@ __global__ void k_rom_ei(RomDev d, DevParams P, int B, const double* __restrict_
             const double dc = cw - cv, gm = P.E_gm;
             const double w = d.twbv[q];
             fv += w * (-gm * dc / S);
-            g[gp[0]] += w * (gm / S + (cv >= cmin ? gm * dc / (S * S) : 0.0));
-            g[gp[2]] += w * (-gm / S + (cw >= cmin ? gm * dc / (S * S) : 0.0));
+            g[gp[0]] += (float)(w * (gm / S + (cv >= cmin ? gm * dc / (S * S) : 0.0)));
+            g[gp[2]] += (float)(w * (-gm / S + (cw >= cmin ? gm * dc / (S * S) : 0.0)));
         } else {
             const int ls = type == T_GE ? PG : (type == T_KE ? PK : PL);
             const double cs = sl[0] >= 0 ? u[sl[0]] : 0.0, ps = u[sl[1]];
             const double ce = sl[2] >= 0 ? u[sl[2]] : 0.0, pe = u[sl[3]];
             const double nf = sl[4] >= 0 ? u[sl[4]] : 0.0;
             const bool gt = d.tgate[q] >= 0 && gate[(int64_t)b * d.ngate + d.tgate[q]] != 0;
-            double ibv, ipl, i_eta, i_cs, i_ce, ip_eta, ip_ce, ip_n;
+            double ibv, ipl;
             interface_current<double>(P, ls, cs, ps, ce, pe, nf, gt, s_i0, k_pl, ibv, ipl);
-            interface_partials<double>(P, ls, cs, ps, ce, pe, nf, gt, s_i0, k_pl, i_eta, i_cs, i_ce, ip_eta, ip_ce,
-                                       ip_n);
-            const double wb = d.twbv[q], wp = d.twpl[q];
-            fv += wb * ibv + wp * ipl;
+            float i_eta, i_cs, i_ce, ip_eta, ip_ce, ip_n;
+            interface_partials<float>(Pf, ls, (float)cs, (float)ps, (float)ce, (float)pe, (float)nf, gt, (float)s_i0,
+                                      (float)k_pl, i_eta, i_cs, i_ce, ip_eta, ip_ce, ip_n);
+            const double wbd = d.twbv[q], wpd = d.twpl[q];
+            fv += wbd * ibv + wpd * ipl;
+            const float wb = (float)wbd, wp = (float)wpd;
             if (sl[0] >= 0) g[gp[0]] += wb * i_cs;
             g[gp[1]] += wb * i_eta + wp * ip_eta;
             if (sl[2] >= 0) g[gp[2]] += wb * i_ce + wp * ip_ce;
@@ -187,7 +191,7 @@ __global__ void k_rom_ei(RomDev d, DevParams P, int B, const double* __restrict_
         }
     }
     f[(int64_t)b * d.M + p] = fv;
-    double* Gp = G + ((int64_t)b * d.M + p) * GMAX;
+    float* Gp = G + ((int64_t)b * d.M + p) * GMAX;
 #pragma unroll
     for (int e = 0; e < GMAX; ++e) Gp[e] = g[e];
 }
@@ -195,22 +199,26 @@ __global__ void k_rom_ei(RomDev d, DevParams P, int B, const double* __restrict_
 // GU[b][p][:] = sum_e G[b][p][e] U_loc[gidx[p][e]][:]
 // GU[p][b][j] = sum_e G[b][p][e] U_loc[gidx[p][e]][j] (FP32); inactive
 // instances write zeros so that the GEMM below reads defined values
-__global__ void k_rom_gu(RomDev d, int B, const double* __restrict__ G, const int* __restrict__ active,
+// one warp per (point, instance): lanes over j
+__global__ void k_rom_gu(RomDev d, int B, const float* __restrict__ G, const int* __restrict__ active,
                          float* __restrict__ GU) {
-    const int p = blockIdx.x, b = blockIdx.y;
+    const int64_t wg = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (wg >= (int64_t)d.M * B) return;
+    const int b = (int)(wg / d.M), p = (int)(wg % d.M);
     float* out = GU + ((int64_t)p * B + b) * d.Nr;
     if (!active[b]) {
-        for (int j = threadIdx.x; j < d.Nr; j += blockDim.x) out[j] = 0.f;
+        for (int j = lane; j < d.Nr; j += 32) out[j] = 0.f;
         return;
     }
-    const double* Gp = G + ((int64_t)b * d.M + p) * GMAX;
+    const float* Gp = G + ((int64_t)b * d.M + p) * GMAX;
     const int32_t* gi = d.gidx + (int64_t)p * GMAX;
-    for (int j = threadIdx.x; j < d.Nr; j += blockDim.x) {
+    for (int j = lane; j < d.Nr; j += 32) {
         float acc = 0.f;
         for (int e = 0; e < GMAX; ++e) {
             const int s = gi[e];
             if (s < 0) break;
-            acc = fmaf((float)Gp[e], d.UlocRf[(int64_t)s * d.Nr + j], acc);
+            acc = fmaf(Gp[e], d.UlocRf[(int64_t)s * d.Nr + j], acc);
         }
         out[j] = acc;
     }
@@ -218,10 +226,10 @@ __global__ void k_rom_gu(RomDev d, int B, const double* __restrict__ G, const in
 
 // Newton matrices of all instances as one FP32 GEMM, C = P [GU_0 | GU_1 | ...]
 // (Nr x M times M x B Nr), plus Ms/dt_b + Alin, written instance-major
-// J[b][i][j].  Tile: all Nr <= 64 rows x 128 columns per block of 256
-// threads, each thread 4 rows x 8 columns in registers, K in chunks of 16
+// J[b][i][j].  Tile: all Nr <= 64 rows x 64 columns per block of 256
+// threads, each thread 4 rows x 4 columns in registers, K in chunks of 16
 // staged in shared memory.  Column c = b Nr + j.
-constexpr int JT_ROWS = 64, JT_COLS = 128, JT_K = 16;
+constexpr int JT_ROWS = 64, JT_COLS = 64, JT_K = 16;
 __global__ void __launch_bounds__(256)
 k_rom_jac(RomDev d, int B, const double* __restrict__ prm, const float* __restrict__ GU, float* __restrict__ J) {
     __shared__ float As[JT_K][JT_ROWS];
@@ -230,11 +238,11 @@ k_rom_jac(RomDev d, int B, const double* __restrict__ prm, const float* __restri
     const int64_t ncol = (int64_t)B * Nr;
     const int64_t c0 = (int64_t)blockIdx.x * JT_COLS;
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-    float acc[4][8];
+    float acc[4][4];
 #pragma unroll
     for (int r = 0; r < 4; ++r)
 #pragma unroll
-        for (int q = 0; q < 8; ++q) acc[r][q] = 0.f;
+        for (int q = 0; q < 4; ++q) acc[r][q] = 0.f;
     for (int k0 = 0; k0 < M; k0 += JT_K) {
         for (int e = threadIdx.x; e < JT_K * JT_ROWS; e += 256) {
             const int k = e / JT_ROWS, i = e % JT_ROWS;
@@ -248,21 +256,21 @@ k_rom_jac(RomDev d, int B, const double* __restrict__ prm, const float* __restri
         __syncthreads();
 #pragma unroll
         for (int k = 0; k < JT_K; ++k) {
-            float a[4], bq[8];
+            float a[4], bq[4];
 #pragma unroll
             for (int r = 0; r < 4; ++r) a[r] = As[k][ty * 4 + r];
 #pragma unroll
-            for (int q = 0; q < 8; ++q) bq[q] = Bs[k][tx * 8 + q];
+            for (int q = 0; q < 4; ++q) bq[q] = Bs[k][tx * 4 + q];
 #pragma unroll
             for (int r = 0; r < 4; ++r)
 #pragma unroll
-                for (int q = 0; q < 8; ++q) acc[r][q] = fmaf(a[r], bq[q], acc[r][q]);
+                for (int q = 0; q < 4; ++q) acc[r][q] = fmaf(a[r], bq[q], acc[r][q]);
         }
         __syncthreads();
     }
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
-        const int64_t c = c0 + tx * 8 + q;
+    for (int q = 0; q < 4; ++q) {
+        const int64_t c = c0 + tx * 4 + q;
         if (c >= ncol) continue;
         const int b = (int)(c / Nr), j = (int)(c % Nr);
         const float dt_inv = (float)prm[RP * b + 3];
@@ -291,48 +299,28 @@ __global__ void k_rom_jac_wide(RomDev d, int B, const double* __restrict__ prm, 
     }
 }
 
-// r[b] = Ms (a - a_old)/dt + Alin a + mu bbnd + P f[b]
-__global__ void k_rom_resid(RomDev d, const double* __restrict__ a, const double* __restrict__ a_old,
-                            const double* __restrict__ prm, const double* __restrict__ f,
-                            const int* __restrict__ active, double* __restrict__ r) {
+// r[b] = Ms (a - a_old)/dt + Alin a + mu bbnd + P f[b] (FP64); one block per
+// instance, one warp per row, lanes over the columns, a fixed shuffle tree
+__global__ void __launch_bounds__(256)
+k_rom_resid(RomDev d, const double* __restrict__ a, const double* __restrict__ a_old,
+            const double* __restrict__ prm, const double* __restrict__ f, const int* __restrict__ active,
+            double* __restrict__ r) {
     const int b = blockIdx.x;
     if (!active[b]) return;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const double dt_inv = prm[RP * b + 3];
     const double* ab = a + (int64_t)b * d.Nr;
     const double* aob = a_old + (int64_t)b * d.Nr;
     const double* fb = f + (int64_t)b * d.M;
     const double mu = prm[RP * b];
-    for (int i = threadIdx.x; i < d.Nr; i += blockDim.x) {
-        double acc = mu * d.bbnd[i];
-        for (int j = 0; j < d.Nr; ++j)
+    for (int i = wid; i < d.Nr; i += nw) {
+        double acc = 0.0;
+        for (int j = lane; j < d.Nr; j += 32)
             acc += d.Ms[(int64_t)i * d.Nr + j] * (ab[j] - aob[j]) * dt_inv + d.Alin[(int64_t)i * d.Nr + j] * ab[j];
-        for (int p = 0; p < d.M; ++p) acc += d.P[(int64_t)i * d.M + p] * fb[p];
-        r[(int64_t)b * d.Nr + i] = acc;
+        for (int p = lane; p < d.M; p += 32) acc += d.P[(int64_t)i * d.M + p] * fb[p];
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+        if (lane == 0) r[(int64_t)b * d.Nr + i] = acc + mu * d.bbnd[i];
     }
-}
-
-// block max / sum helpers (blockDim.x == 256)
-__device__ inline float block_maxf(float v, float* sh) {
-    sh[threadIdx.x] = v;
-    __syncthreads();
-    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-        if (threadIdx.x < s) sh[threadIdx.x] = fmaxf(sh[threadIdx.x], sh[threadIdx.x + s]);
-        __syncthreads();
-    }
-    float r = sh[0];
-    __syncthreads();
-    return r;
-}
-__device__ inline double block_max(double v, double* sh) {
-    sh[threadIdx.x] = v;
-    __syncthreads();
-    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-        if (threadIdx.x < s) sh[threadIdx.x] = fmax(sh[threadIdx.x], sh[threadIdx.x + s]);
-        __syncthreads();
-    }
-    double r = sh[0];
-    __syncthreads();
-    return r;
 }
 
 // delta[b] = -J[b]^-1 r[b] in FP32 (r FP64 on input, delta FP64 on output):
@@ -439,36 +427,177 @@ k_rom_lu(int Nr, float* __restrict__ J, const double* __restrict__ r, const int*
     for (int j = threadIdx.x; j < Nr; j += blockDim.x) delta[(int64_t)b * Nr + j] = (double)(x[j] * cs[j]);
 }
 
-// step length and convergence of instance b (one block per instance)
-__global__ void __launch_bounds__(256)
-k_rom_update(RomDev d, double* __restrict__ a, const double* __restrict__ delta, int* __restrict__ active,
-             int* __restrict__ failed, long long* __restrict__ its) {
+// The same factorisation and solve with one warp per instance, the matrix in
+// shared memory (Nr <= ROM_LU_WARP_NR): lanes over rows for the pivot search
+// and the multipliers, over columns for the row swap and the update; the
+// pivot is the largest magnitude, the lowest row on ties.
+constexpr int ROM_LU_WARP_NR = 64;
+__global__ void __launch_bounds__(32)
+k_rom_lu_warp(int Nr, float* __restrict__ J, const double* __restrict__ r, const int* __restrict__ active,
+              double* __restrict__ delta) {
     const int b = blockIdx.x;
     if (!active[b]) return;
-    __shared__ double sd[ROM_NR_MAX];
-    __shared__ float sdf[ROM_NR_MAX];
-    __shared__ float sh[256];
-    for (int j = threadIdx.x; j < d.Nr; j += blockDim.x) {
-        sd[j] = delta[(int64_t)b * d.Nr + j];
-        sdf[j] = (float)sd[j];
+    extern __shared__ float lu_sm[];
+    float* A = lu_sm;                 // Nr x Nr
+    float* rs = A + Nr * Nr;          // row scales
+    float* cs = rs + Nr;              // column scales
+    float* rhs = cs + Nr;
+    float* x = rhs + Nr;
+    const int lane = threadIdx.x;
+    const float* Jb = J + (int64_t)b * Nr * Nr;
+    for (int e = lane; e < Nr * Nr; e += 32) A[e] = Jb[e];
+    __syncwarp();
+    for (int i = lane; i < Nr; i += 32) {
+        float m = 0.f;
+        for (int j = 0; j < Nr; ++j) m = fmaxf(m, fabsf(A[i * Nr + j]));
+        rs[i] = m > 0.f ? 1.f / m : 1.f;
     }
-    __syncthreads();
-    // scaled max-norm of the reconstructed update (FP32: it only sets the step length and the stop)
+    __syncwarp();
+    for (int j = lane; j < Nr; j += 32) {
+        float m = 0.f;
+        for (int i = 0; i < Nr; ++i) m = fmaxf(m, fabsf(A[i * Nr + j] * rs[i]));
+        cs[j] = m > 0.f ? 1.f / m : 1.f;
+    }
+    __syncwarp();
+    for (int e = lane; e < Nr * Nr; e += 32) A[e] *= rs[e / Nr] * cs[e % Nr];
+    for (int i = lane; i < Nr; i += 32) rhs[i] = (float)(-r[(int64_t)b * Nr + i]) * rs[i];
+    __syncwarp();
+    for (int k = 0; k < Nr; ++k) {
+        float best = -1.f;
+        int bi = k;
+        for (int i = k + lane; i < Nr; i += 32) {
+            const float v = fabsf(A[i * Nr + k]);
+            if (v > best) { best = v; bi = i; }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            const float v2 = __shfl_xor_sync(0xffffffffu, best, o);
+            const int i2 = __shfl_xor_sync(0xffffffffu, bi, o);
+            if (v2 > best || (v2 == best && i2 < bi)) { best = v2; bi = i2; }
+        }
+        const int piv = bi;
+        if (piv != k) {
+            for (int j = lane; j < Nr; j += 32) {
+                const float t = A[k * Nr + j];
+                A[k * Nr + j] = A[piv * Nr + j];
+                A[piv * Nr + j] = t;
+            }
+            if (lane == 0) {
+                const float t = rhs[k];
+                rhs[k] = rhs[piv];
+                rhs[piv] = t;
+            }
+        }
+        __syncwarp();
+        const float akk = A[k * Nr + k];
+        const float inv = akk != 0.f ? 1.f / akk : 0.f;
+        for (int i = k + 1 + lane; i < Nr; i += 32) {
+            const float l = A[i * Nr + k] * inv;
+            A[i * Nr + k] = l;
+            rhs[i] -= l * rhs[k];
+        }
+        __syncwarp();
+        for (int i = k + 1; i < Nr; ++i) {
+            const float l = A[i * Nr + k];
+            for (int j = k + 1 + lane; j < Nr; j += 32) A[i * Nr + j] -= l * A[k * Nr + j];
+        }
+        __syncwarp();
+    }
+    for (int k = Nr - 1; k >= 0; --k) {
+        float part = 0.f;
+        for (int j = k + 1 + lane; j < Nr; j += 32) part += A[k * Nr + j] * x[j];
+        for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+        if (lane == 0) {
+            const float akk = A[k * Nr + k];
+            x[k] = akk != 0.f ? (rhs[k] - part) / akk : 0.f;
+        }
+        __syncwarp();
+    }
+    for (int j = lane; j < Nr; j += 32) delta[(int64_t)b * Nr + j] = (double)(x[j] * cs[j]);
+}
+
+// Step length of all instances: the scaled max-norm of the reconstructed
+// update U_loc delta over the closure (FP32; it only sets the step length
+// and the stop), as a tiled product U_loc [delta_0 | delta_1 | ...]: a block
+// takes UN_K closure slots x UN_B instances, K (the reduced coordinates) in
+// chunks of 16 staged in shared memory, each thread 4 x 4 results; per
+// instance and tile the maximum goes to dpart (NaN counts as infinite).
+constexpr int UN_K = 128, UN_B = 32, UN_C = 16;
+__global__ void __launch_bounds__(256)
+k_rom_unorm(RomDev d, int B, const double* __restrict__ delta, const int* __restrict__ active,
+            float* __restrict__ dpart) {
+    __shared__ float Us[UN_C][UN_K];
+    __shared__ float Ds[UN_C][UN_B];
+    const int k0 = blockIdx.x * UN_K, b0 = blockIdx.y * UN_B;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 32 slot groups x 8 instance groups
+    float acc[4][4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[u][q] = 0.f;
+    for (int j0 = 0; j0 < d.Nr; j0 += UN_C) {
+        for (int e = threadIdx.x; e < UN_C * UN_K; e += 256) {
+            const int j = e / UN_K, k = e % UN_K;
+            Us[j][k] = (j0 + j < d.Nr && k0 + k < d.nloc) ? d.UlocCf[(int64_t)(j0 + j) * d.nloc + k0 + k] : 0.f;
+        }
+        for (int e = threadIdx.x; e < UN_C * UN_B; e += 256) {
+            const int j = e / UN_B, q = e % UN_B;
+            const int b = b0 + q;
+            Ds[j][q] = (j0 + j < d.Nr && b < B) ? (float)delta[(int64_t)b * d.Nr + j0 + j] : 0.f;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < UN_C; ++j) {
+            float u[4], v[4];
+#pragma unroll
+            for (int s = 0; s < 4; ++s) u[s] = Us[j][tx + 32 * s];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) v[q] = Ds[j][ty * 4 + q];
+#pragma unroll
+            for (int s = 0; s < 4; ++s)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) acc[s][q] = fmaf(u[s], v[q], acc[s][q]);
+        }
+        __syncthreads();
+    }
+    // per instance: max over this thread's 4 slots, then over the warp's 32 threads
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        float m = 0.f;
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+            const int k = k0 + tx + 32 * s;
+            if (k < d.nloc) {
+                const float v = fabsf(acc[s][q]) / d.usf[k];
+                m = (v == v) ? fmaxf(m, v) : INFINITY;
+            }
+        }
+        for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+        const int b = b0 + ty * 4 + q;
+        if (tx == 0 && b < B) dpart[(int64_t)b * gridDim.x + blockIdx.x] = m;
+    }
+}
+
+// step length and convergence of instance b from the partial maxima (one warp per instance)
+__global__ void __launch_bounds__(32)
+k_rom_apply(RomDev d, int nkt, double* __restrict__ a, const double* __restrict__ delta,
+            const float* __restrict__ dpart, int* __restrict__ active, int* __restrict__ failed,
+            long long* __restrict__ its) {
+    const int b = blockIdx.x, lane = threadIdx.x;
+    if (!active[b]) return;
     float m = 0.f;
-    for (int k = threadIdx.x; k < d.nloc; k += blockDim.x) {
-        float acc = 0.f;
-        for (int j = 0; j < d.Nr; ++j) acc = fmaf(d.UlocCf[(int64_t)j * d.nloc + k], sdf[j], acc);
-        float v = fabsf(acc) / d.usf[k];
+    for (int t = lane; t < nkt; t += 32) {
+        const float v = dpart[(int64_t)b * nkt + t];
         m = (v == v) ? fmaxf(m, v) : INFINITY;
     }
-    const double dn = (double)block_maxf(m, sh);
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    const double dn = (double)m;
     if (!(dn < INFINITY)) {
-        if (threadIdx.x == 0) { failed[b] = 1; active[b] = 0; }
+        if (lane == 0) { failed[b] = 1; active[b] = 0; }
         return;
     }
     const double lam = dn <= ROM_DELTA_MAX ? 1.0 : ROM_DELTA_MAX / dn;
-    for (int j = threadIdx.x; j < d.Nr; j += blockDim.x) a[(int64_t)b * d.Nr + j] += lam * sd[j];
-    if (threadIdx.x == 0) {
+    for (int j = lane; j < d.Nr; j += 32) a[(int64_t)b * d.Nr + j] += lam * delta[(int64_t)b * d.Nr + j];
+    if (lane == 0) {
         its[b] += 1;
         if (lam * dn <= ROM_TOL) active[b] = 0;
     }
@@ -816,7 +945,8 @@ static int rom_work_alloc(mb_rom* R, int B) {
     w.uloc = rom_alloc<double>(L, (size_t)B * d.nloc);
     w.uloc_old = rom_alloc<double>(L, (size_t)B * d.nloc);
     w.f = rom_alloc<double>(L, (size_t)B * d.M);
-    w.G = rom_alloc<double>(L, (size_t)B * d.M * GMAX);
+    w.G = rom_alloc<float>(L, (size_t)B * (d.M ? d.M : 1) * GMAX);
+    w.dpart = rom_alloc<float>(L, (size_t)B * ((d.nloc + UN_K - 1) / UN_K));
     w.GU = rom_alloc<float>(L, (size_t)B * (d.M ? d.M : 1) * d.Nr);
     w.prm = rom_alloc<double>(L, (size_t)B * RP);
     w.gate = rom_alloc<uint8_t>(L, (size_t)B * (d.ngate ? d.ngate : 1));
@@ -916,8 +1046,10 @@ int rom_batch_step(mb_rom* R) {
         for (int it = 0; it < ROM_MAXIT; ++it) {
             k_rom_gather<<<gg, 256, 0, s>>>(d, w.a, w.uloc), count_launch(c);
             if (d.M) {
-                k_rom_ei<<<ge, 128, 0, s>>>(d, c->P, B, w.uloc, w.gate, w.prm, w.active, w.f, w.G), count_launch(c);
-                k_rom_gu<<<dim3((unsigned)d.M, (unsigned)B), 64, 0, s>>>(d, B, w.G, w.active, w.GU), count_launch(c);
+                k_rom_ei<<<ge, 128, 0, s>>>(d, c->P, c->Pf, B, w.uloc, w.gate, w.prm, w.active, w.f, w.G),
+                    count_launch(c);
+                k_rom_gu<<<(unsigned)(((int64_t)d.M * B * 32 + 255) / 256), 256, 0, s>>>(d, B, w.G, w.active, w.GU),
+                    count_launch(c);
             }
             if (d.Nr <= JT_ROWS)
                 k_rom_jac<<<(unsigned)(((int64_t)B * d.Nr + JT_COLS - 1) / JT_COLS), 256, 0, s>>>(d, B, w.prm, w.GU,
@@ -926,8 +1058,19 @@ int rom_batch_step(mb_rom* R) {
                 k_rom_jac_wide<<<dim3((unsigned)d.Nr, (unsigned)B), 128, 0, s>>>(d, B, w.prm, w.GU, w.active, w.J),
                     count_launch(c);
             k_rom_resid<<<(unsigned)B, 128, 0, s>>>(d, w.a, w.a_old, w.prm, w.f, w.active, w.r), count_launch(c);
-            k_rom_lu<<<(unsigned)B, 256, 0, s>>>(d.Nr, w.J, w.r, w.active, w.delta), count_launch(c);
-            k_rom_update<<<(unsigned)B, 256, 0, s>>>(d, w.a, w.delta, w.active, w.failed, w.its), count_launch(c);
+            if (d.Nr <= ROM_LU_WARP_NR)
+                k_rom_lu_warp<<<(unsigned)B, 32, (size_t)4 * ((size_t)d.Nr * d.Nr + 4 * d.Nr), s>>>(d.Nr, w.J, w.r,
+                                                                                                    w.active, w.delta),
+                    count_launch(c);
+            else
+                k_rom_lu<<<(unsigned)B, 256, 0, s>>>(d.Nr, w.J, w.r, w.active, w.delta), count_launch(c);
+            {
+                const unsigned nkt = (unsigned)((d.nloc + UN_K - 1) / UN_K);
+                k_rom_unorm<<<dim3(nkt, (unsigned)((B + UN_B - 1) / UN_B)), 256, 0, s>>>(d, B, w.delta, w.active,
+                                                                                         w.dpart), count_launch(c);
+                k_rom_apply<<<(unsigned)B, 32, 0, s>>>(d, (int)nkt, w.a, w.delta, w.dpart, w.active, w.failed,
+                                                       w.its), count_launch(c);
+            }
             k_rom_count<<<1, 256, 0, s>>>(B, w.active, w.counts), count_launch(c);
             MB_CUDA(cudaMemcpyAsync(&hcount, w.counts, 4, cudaMemcpyDeviceToHost, s));
             MB_CUDA(cudaStreamSynchronize(s));
