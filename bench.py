@@ -391,7 +391,7 @@ def main():
     for _ in range(args.e2e_steps):
         cell.set_state(u_host)
         cell.step(dt, I)
-        u_host[:] = cell.state()
+        cell.state(out=u_host)
     e2e_wall = time.perf_counter() - t0
     e2e = {"value": ws * args.e2e_steps * dt / e2e_wall, "unit": UNIT,
            "h2d_bytes_per_step": 8 * cell.n, "d2h_bytes_per_step": 8 * cell.n}

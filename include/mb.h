@@ -78,6 +78,9 @@ typedef struct {
     int    mg_coarse_cells;/* multigrid: coarsen until at most this many cells */
     int    mg_smooth;      /* fine-level block-Jacobi sweeps before and after the coarse correction (1..8) */
     int    mg_kcycle;      /* FGMRES iterations of the level-1 K-cycle (1..16; default 5) */
+    int    mg_coarse_pre;  /* damped block-Jacobi sweeps before the coarse correction on levels >= 1
+                              (1..4; default 2) */
+    int    mg_coarse_post; /* ... and after it (1..4; default 2) */
     int    mg_bf16;        /* 1: the fine smoother's stencil and the coarse-level operators are
                               applied from BF16 copies (FP32 arithmetic); 0: FP32 operators */
     int    mg_stream;      /* how the BF16 coarse sweeps and products fetch their operator rows
@@ -174,7 +177,7 @@ int mb_jvp_f32_dev(mb_cell* cell, const float* u, const uint8_t* gate, double dt
 #define MB_PROF_PRECOND  2   /* one whole preconditioner application (many kernels) */
 #define MB_PROF_SMOOTH   3   /* fine-level smoothing sweep (assembled stencil; 2 mg_smooth - 1 per
                                 preconditioner application) */
-#define MB_PROF_LSMOOTH  4   /* level-1 post-smoothing sweep (two per V-cycle of the K-cycle) */
+#define MB_PROF_LSMOOTH  4   /* level-1 post-smoothing sweep (mg_coarse_post per V-cycle of the K-cycle) */
 int mb_prof_enable(mb_cell* cell, int on);
 int mb_prof_read(mb_cell* cell, int kind, int64_t* count, double* total_ms);
 int mb_prof_reset(mb_cell* cell);

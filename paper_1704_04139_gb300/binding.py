@@ -38,7 +38,8 @@ class SolverOpts(C.Structure):
     _fields_ = [("precision", C.c_int), ("newton_tol", C.c_double), ("newton_maxit", C.c_int),
                 ("gmres_m", C.c_int), ("krylov_maxit", C.c_int), ("krylov_rtol", C.c_double),
                 ("max_passes", C.c_int), ("max_halvings", C.c_int), ("mg_coarse_cells", C.c_int),
-                ("mg_smooth", C.c_int), ("mg_kcycle", C.c_int), ("mg_bf16", C.c_int), ("mg_stream", C.c_int)]
+                ("mg_smooth", C.c_int), ("mg_kcycle", C.c_int), ("mg_coarse_pre", C.c_int),
+                ("mg_coarse_post", C.c_int), ("mg_bf16", C.c_int), ("mg_stream", C.c_int)]
 
 
 class StepInfo(C.Structure):
@@ -245,8 +246,11 @@ class Cell:
         _check(lib().mb_plating_faces(self.h, _ptr(g), _ptr(e), _ptr(d)))
         return g, e, d
 
-    def state(self):
-        u = np.empty(self.n)
+    def state(self, out=None):
+        """The FP64 state; into `out` (a contiguous float64 array of n entries,
+        e.g. in pinned memory) when given."""
+        u = np.empty(self.n) if out is None else out
+        assert u.dtype == np.float64 and u.shape == (self.n,) and u.flags["C_CONTIGUOUS"]
         _check(lib().mb_state_get(self.h, _ptr(u)))
         return u
 

@@ -110,6 +110,8 @@ void mb_opts_default(mb_solver_opts* o) {
     o->mg_coarse_cells = 32;
     o->mg_smooth = 2;
     o->mg_kcycle = 5;
+    o->mg_coarse_pre = 2;
+    o->mg_coarse_post = 2;
     o->mg_bf16 = 1;
     o->mg_stream = 0;
 }
@@ -120,7 +122,8 @@ static int check_opts(const mb_solver_opts* o) {
     if (o->gmres_m < 1 || o->gmres_m > 63 || o->newton_maxit < 1 || o->krylov_maxit < 1 ||
         o->max_passes < 1 || o->max_halvings < 0 || o->max_halvings > 20 || !(o->newton_tol > 0) ||
         !(o->krylov_rtol > 0) || o->mg_kcycle < 1 || o->mg_kcycle > 16 || o->mg_smooth < 1 || o->mg_smooth > 8 ||
-        (o->mg_bf16 != 0 && o->mg_bf16 != 1) || o->mg_stream < 0 || o->mg_stream > 2)
+        (o->mg_bf16 != 0 && o->mg_bf16 != 1) || o->mg_coarse_pre < 1 || o->mg_coarse_pre > 4 ||
+        o->mg_coarse_post < 1 || o->mg_coarse_post > 4 || o->mg_stream < 0 || o->mg_stream > 2)
         return MB_EINVAL;
     return MB_OK;
 }

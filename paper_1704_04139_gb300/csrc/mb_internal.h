@@ -215,7 +215,8 @@ int count_diff_u8(mb_cell* c, const uint8_t* a, const uint8_t* b, int64_t n, int
 // ---- precond.cu ----
 int precond_create(mb_cell* c);
 void precond_destroy(mb_cell* c);
-// build at linearisation point u32 (float) for time step dt with gates
+// build at linearisation point u32 (float) for time step dt; after launch_lin_setup and set_dt of the
+// same linearisation (the interface partials c->icoef carry the gates and the plated Li)
 int precond_setup(mb_cell* c, const float* u32, const uint8_t* gate, double dt);
 // assemble the fine smoother's stencil; after launch_lin_setup and set_dt of
 // the same linearisation (it reads the interface partials and 1/dt)

@@ -190,6 +190,76 @@ __device__ inline void interface_partials(const ParT<T>& P, int ls, T cs, T ps, 
     }
 }
 
+// interface-face entries of J from the six partials; solid_side: v is the
+// solid voxel (x = (c_s, phi_s, c_e, phi_e, n)), else the electrolyte voxel
+// (x = (c_e, phi_e, c_s, phi_s, n))
+template <class T>
+__device__ inline void face_jacobian_iface(const ParT<T>& P, bool solid_side, bool solid_has_c, T i_eta, T i_cs,
+                                           T i_ce, T ip_eta, T ip_ce, T ip_n, FaceJac<T>& J) {
+    T A = T(P.A), AF = T(P.A) * T(P.invF), iF = T(P.invF);
+    if (solid_side) {
+        if (solid_has_c) {
+            J.c[0] = AF * i_cs; J.c[1] = AF * i_eta; J.c[2] = AF * i_ce; J.c[3] = -AF * i_eta;
+        }
+        J.p[0] = A * i_cs; J.p[1] = A * (i_eta + ip_eta); J.p[2] = A * (i_ce + ip_ce);
+        J.p[3] = -A * (i_eta + ip_eta); J.p[4] = A * ip_n;
+        J.n[1] = iF * ip_eta; J.n[2] = iF * ip_ce; J.n[3] = -iF * ip_eta; J.n[4] = iF * ip_n;
+    } else {
+        T te = i_eta + ip_eta;
+        J.c[0] = -AF * (i_ce + ip_ce); J.c[1] = AF * te; J.c[2] = -AF * i_cs; J.c[3] = -AF * te;
+        J.c[4] = -AF * ip_n;
+        J.p[0] = -A * (i_ce + ip_ce); J.p[1] = A * te; J.p[2] = -A * i_cs; J.p[3] = -A * te;
+        J.p[4] = -A * ip_n;
+        // face row i_pl/F seen from the electrolyte side: x = (c_e, phi_e, c_g, phi_g, n)
+        J.n[0] = iF * ip_ce; J.n[1] = -iF * ip_eta; J.n[3] = iF * ip_eta; J.n[4] = iF * ip_n;
+    }
+}
+
+// the face types without interface kinetics; false for an interface face (J untouched then)
+template <class T>
+__device__ inline bool face_jacobian_bulk(const ParT<T>& P, int lv, int lw, T cv, T cw, FaceJac<T>& J) {
+    if (lv == PE && lw == PE) {
+        T cmin = T(P.cmin[PE]);
+        T mv = cv >= cmin ? T(1) : T(0), mw = cw >= cmin ? T(1) : T(0);
+        T S = tmax(cv, cmin) + tmax(cw, cmin);
+        T iS = T(1) / S;
+        T dc = cw - cv;
+        T r = dc * iS * iS;
+        T gm = T(P.E_gm), gk = T(P.E_gk), tF = T(P.E_tF), gD = T(P.E_gD);
+        T jcv = gm * (iS + r * mv);       // d j / d c_v
+        T jcw = -gm * (iS - r * mw);      // d j / d c_w
+        J.p[0] = jcv; J.p[1] = gk; J.p[2] = jcw; J.p[3] = -gk;
+        J.c[0] = gD + tF * jcv; J.c[1] = tF * gk; J.c[2] = -gD + tF * jcw; J.c[3] = -tF * gk;
+        return true;
+    }
+    if (lv == lw && (lv == PG || lv == PK)) {
+        T gD = T(P.gD[lv]), gs = T(P.gsig[lv][lw]);
+        J.c[0] = gD; J.c[2] = -gD;
+        J.p[1] = gs; J.p[3] = -gs;
+        return true;
+    }
+    if (is_conductor(lv) && is_conductor(lw)) {
+        T gs = T(P.gsig[lv][lw]);
+        J.p[1] = gs; J.p[3] = -gs;
+        return true;
+    }
+    return !((lw == PE && (lv == PG || lv == PK || lv == PL)) || (lv == PE && (lw == PG || lw == PK || lw == PL)));
+}
+
+// J of one face with the interface partials of face i taken from the stored
+// linearisation icoef[6][NI] (i_eta, ip_eta, i_cs, i_ce, ip_ce, ip_n)
+template <class T>
+__device__ inline void face_jacobian_lin(const ParT<T>& P, int lv, int lw, T cv, T cw, const float* __restrict__ icoef,
+                                         int64_t NI, int64_t i, FaceJac<T>& J) {
+#pragma unroll
+    for (int k = 0; k < 5; ++k) { J.c[k] = T(0); J.p[k] = T(0); J.n[k] = T(0); }
+    if (face_jacobian_bulk<T>(P, lv, lw, cv, cw, J)) return;
+    const T i_eta = T(icoef[i]), ip_eta = T(icoef[NI + i]), i_cs = T(icoef[2 * NI + i]);
+    const T i_ce = T(icoef[3 * NI + i]), ip_ce = T(icoef[4 * NI + i]), ip_n = T(icoef[5 * NI + i]);
+    const bool solid_side = lw == PE;
+    face_jacobian_iface<T>(P, solid_side, (solid_side ? lv : lw) != PL, i_eta, i_cs, i_ce, ip_eta, ip_ce, ip_n, J);
+}
+
 template <class T>
 __device__ inline void face_jacobian(const ParT<T>& P, int lv, int lw, T cv, T pv, T cw, T pw,
                                      T nf, bool gate, T s_i0, T k_pl, FaceJac<T>& J) {

@@ -23,8 +23,8 @@
 //    A x = ex x_i + sum_d off_d (x_nb - x_i), so that the large intra-phase
 //    conductances never meet the iterate's large near-null components.
 //    Level 1 is solved by a K-cycle: FGMRES(KCYC) run entirely on the device,
-//    preconditioned by a V-cycle (NU damped 4x4 block-Jacobi sweeps before and
-//    after each coarse correction); the coarsest level is solved with an
+//    preconditioned by a V-cycle (mg_coarse_pre / mg_coarse_post damped 4x4
+//    block-Jacobi sweeps before / after each coarse correction); the coarsest level is solved with an
 //    explicit FP64 inverse.
 // Precision: all arithmetic of the application is FP32; iterates and
 // corrections (z, coarse x, K-cycle directions) are float-float, residuals and
@@ -51,7 +51,6 @@ constexpr int BLK = NCLS * NCLS;          // 16 floats per 4x4 block
 constexpr int OFFW = 6 * BLK;             // 96 floats of outgoing couplings per cell
 constexpr float OMEGA_FINE = 0.8f;
 constexpr float OMEGA_COARSE = 0.7f;
-constexpr int NU = 2;                     // smoothing sweeps per coarse level (pre and post)
 constexpr int KCYC_MAX = 16;              // longest level-1 K-cycle (FGMRES iterations)
 constexpr int MAX_LEVELS = 16;
 constexpr int COARSE_MAX = 256;           // dense coarsest system size bound (4 x cells)
@@ -170,12 +169,20 @@ __device__ inline int64_t face_of(int lv, int lw, uint32_t code, uint32_t cw_cod
     return -1;
 }
 
+// interface face (index into the stored partials) of voxel v in direction d
+// towards w, -1 for the other face types; irank counts v's own interface faces
+__device__ inline int64_t iface_of(int lv, int lw, uint32_t code, uint32_t cw_code, int d, int& irank) {
+    if ((lv == PG || lv == PK || lv == PL) && lw == PE) return (int64_t)vc_fbase(code) + irank++;
+    if (lv == PE && (lw == PG || lw == PK || lw == PL))
+        return (int64_t)vc_fbase(cw_code) + __popc(vc_emask(cw_code) & ((1u << opp_dir(d)) - 1u));
+    return -1;
+}
+
 // ------------------------------------------------------------ fine level
 __global__ void __launch_bounds__(256)
 k_bj_setup(ParT<float> P, Dims D, const uint32_t* __restrict__ vc, const float* __restrict__ u,
-           const uint8_t* __restrict__ gate, double dt, double s_i0d, double k_pld,
-           float* __restrict__ dinv, float* __restrict__ fc, float* __restrict__ rowdiag,
-           float* __restrict__ rowinv) {
+           const float* __restrict__ icoef, double dt, float* __restrict__ dinv, float* __restrict__ fc,
+           float* __restrict__ rowdiag, float* __restrict__ rowinv) {
     int z = blockIdx.x * blockDim.x + threadIdx.x;
     int y = blockIdx.y * blockDim.y + threadIdx.y;
     int t = blockIdx.z;
@@ -183,34 +190,25 @@ k_bj_setup(ParT<float> P, Dims D, const uint32_t* __restrict__ vc, const float* 
     const int64_t N = D.N;
     int64_t v = (int64_t)t * D.syz + (int64_t)y * D.nz + z;
     const float* cc = u;
-    const float* ph = u + N;
-    const float* nn = u + 2 * N;
-    const float s_i0 = float(s_i0d), k_pl = float(k_pld);
     const float dtf = float(dt), idt = float(1.0 / dt);
     const float nc = P.nc;
     const float A = float(P.A), c0 = float(P.cref[PE]);
     uint32_t code = vc[v];
     int lv = vc_phase(code);
-    float cv = cc[v], pv = ph[v];
+    float cv = cc[v];
     float d00 = 0.f, d01 = 0.f, d10 = 0.f, d11 = 0.f;
     float dgc = 0.f, dgp = 0.f;   // uncondensed diagonal entries
     const int64_t off[6] = {-D.syz, D.syz, -(int64_t)D.nz, (int64_t)D.nz, -1, 1};
     const bool inb[6] = {t > 0, t < D.nt - 1, y > 0, y < D.ny - 1, z > 0, z < D.nz - 1};
-    int rank = 0;
+    int rank = 0, irank = 0;
     for (int d = 0; d < 6; ++d) {
         if (!inb[d]) continue;
         int64_t w = v + off[d];
         uint32_t cw_code = vc[w];
         int lw = vc_phase(cw_code);
         int64_t f = face_of(lv, lw, code, cw_code, d, rank);
-        float nf = 0.f;
-        bool g = false;
-        if (f >= 0) {
-            nf = nn[f];
-            g = gate[f] != 0;
-        }
         FaceJac<float> J;
-        face_jacobian<float>(P, lv, lw, cv, pv, cc[w], ph[w], nf, g, s_i0, k_pl, J);
+        face_jacobian_lin<float>(P, lv, lw, cv, cc[w], icoef, D.NI, iface_of(lv, lw, code, cw_code, d, irank), J);
         d00 += J.c[0]; d01 += J.c[1]; d10 += J.p[0]; d11 += J.p[1];
         dgc += J.c[0]; dgp += J.p[1];
         if (f >= 0) {
@@ -330,7 +328,7 @@ __device__ inline void acc_blk(float* blk, int k, int kk, float v) { blk[k * NCL
 
 __global__ void __launch_bounds__(128)
 k_assemble_l1(ParT<float> P, Dims D, const uint32_t* __restrict__ vc, const float* __restrict__ u,
-              const uint8_t* __restrict__ gate, double dt, double s_i0d, double k_pld, Level L1) {
+              const float* __restrict__ icoef, double dt, Level L1) {
     int64_t cell = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (cell >= L1.cells) return;
     int cz = (int)(cell % L1.nz);
@@ -338,9 +336,6 @@ k_assemble_l1(ParT<float> P, Dims D, const uint32_t* __restrict__ vc, const floa
     int ct = (int)(cell / ((int64_t)L1.nz * L1.ny));
     const int64_t N = D.N;
     const float* cc = u;
-    const float* ph = u + N;
-    const float* nn = u + 2 * N;
-    const float s_i0 = float(s_i0d), k_pl = float(k_pld);
     const float A = float(P.A);
     const float c0 = float(P.cref[PE]);
     const float idt = float(1.0 / dt);
@@ -369,11 +364,11 @@ k_assemble_l1(ParT<float> P, Dims D, const uint32_t* __restrict__ vc, const floa
                     acc_blk(ex, 0, 0, 1.f);   // storage V/dt, scaled
                 }
                 if (t == 0 && lv == PCN) acc_blk(ex, kv, kv, float(P.g_dir) * sc_pp);
-                float cv = cc[v], pv = ph[v];
+                float cv = cc[v];
                 const int64_t offs[6] = {-D.syz, D.syz, -(int64_t)D.nz, (int64_t)D.nz, -1, 1};
                 const bool inb[6] = {t > 0, t < D.nt - 1, y > 0, y < D.ny - 1, z > 0, z < D.nz - 1};
                 const int loc[6] = {a, a, b, b, e, e};
-                int rank = 0;
+                int rank = 0, irank = 0;
                 for (int d = 0; d < 6; ++d) {
                     if (!inb[d]) continue;
                     int64_t w = v + offs[d];
@@ -384,15 +379,10 @@ k_assemble_l1(ParT<float> P, Dims D, const uint32_t* __restrict__ vc, const floa
                     bool other = (d & 1) ? (loc[d] == 1) : (loc[d] == 0);
                     float* od = off + d * BLK;
                     int64_t f = face_of(lv, lw, code, cw_code, d, rank);
-                    float nf = 0.f;
-                    bool g = false;
-                    if (f >= 0) {
-                        nf = nn[f];
-                        g = gate[f] != 0;
-                    }
-                    float cw = cc[w], pw = ph[w];
+                    float cw = cc[w];
                     FaceJac<float> J;
-                    face_jacobian<float>(P, lv, lw, cv, pv, cw, pw, nf, g, s_i0, k_pl, J);
+                    face_jacobian_lin<float>(P, lv, lw, cv, cw, icoef, D.NI, iface_of(lv, lw, code, cw_code, d, irank),
+                                             J);
                     if (lv == PE && lw == PE) {
                         // row sums of the face terms without cancellation:
                         // dj/dc_v + dj/dc_w = gm dc/S^2 (m_v + m_w); the conduction parts cancel exactly
@@ -495,47 +485,55 @@ __global__ void k_assemble_up(Level F, Level C) {
 
 // self block = row sums - outgoing couplings; absent classes get an identity
 // row (and zero columns); the block inverse by Gauss-Jordan with partial
-// pivoting (FP64).  exd is the self block of the difference form:
+// pivoting (FP32: it only serves the smoother).  exd is the self block of the difference form:
 // ex for present classes, the fixed-up self block plus the outgoing sums
 // elsewhere, so that exd x_i + sum_d off_d (x_nb - x_i) = aself x_i + sum_d off_d x_nb.
 __global__ void k_finalize(Level L) {
     int64_t cell = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (cell >= L.cells) return;
-    double a[NCLS][2 * NCLS];
+    float a[NCLS][2 * NCLS];
     uint32_t mask = L.mask[cell];
+#pragma unroll
     for (int k = 0; k < NCLS; ++k)
+#pragma unroll
         for (int kk = 0; kk < NCLS; ++kk) {
-            double so = 0.0;
+            float so = 0.f;
             for (int d = 0; d < 6; ++d) so += L.off[(int64_t)(d * BLK + k * NCLS + kk) * L.cells + cell];
-            double s = L.ex[(int64_t)(k * NCLS + kk) * L.cells + cell] - so;
-            double sd = L.ex[(int64_t)(k * NCLS + kk) * L.cells + cell];
+            const float ex = L.ex[(int64_t)(k * NCLS + kk) * L.cells + cell];
+            float s = ex - so;
+            float sd = ex;
             if (!((mask >> k) & 1u) || !((mask >> kk) & 1u)) {
-                s = (k == kk && !((mask >> k) & 1u)) ? 1.0 : 0.0;
+                s = (k == kk && !((mask >> k) & 1u)) ? 1.f : 0.f;
                 sd = s + so;
             }
             a[k][kk] = s;
-            a[k][NCLS + kk] = (k == kk) ? 1.0 : 0.0;
-            L.aself[(int64_t)(k * NCLS + kk) * L.cells + cell] = (float)s;
-            L.exd[(int64_t)(k * NCLS + kk) * L.cells + cell] = (float)sd;
+            a[k][NCLS + kk] = (k == kk) ? 1.f : 0.f;
+            L.aself[(int64_t)(k * NCLS + kk) * L.cells + cell] = s;
+            L.exd[(int64_t)(k * NCLS + kk) * L.cells + cell] = sd;
         }
+#pragma unroll
     for (int col = 0; col < NCLS; ++col) {
         int piv = col;
+#pragma unroll
         for (int r = col + 1; r < NCLS; ++r)
-            if (fabs(a[r][col]) > fabs(a[piv][col])) piv = r;
+            if (fabsf(a[r][col]) > fabsf(a[piv][col])) piv = r;
         if (piv != col)
-            for (int j = 0; j < 2 * NCLS; ++j) { double tmp = a[col][j]; a[col][j] = a[piv][j]; a[piv][j] = tmp; }
-        double p = a[col][col];
-        double ip = p != 0.0 ? 1.0 / p : 0.0;
+#pragma unroll
+            for (int j = 0; j < 2 * NCLS; ++j) { float tmp = a[col][j]; a[col][j] = a[piv][j]; a[piv][j] = tmp; }
+        const float p = a[col][col];
+        const float ip = p != 0.f ? 1.f / p : 0.f;
+#pragma unroll
         for (int j = 0; j < 2 * NCLS; ++j) a[col][j] *= ip;
+#pragma unroll
         for (int r = 0; r < NCLS; ++r) {
             if (r == col) continue;
-            double fct = a[r][col];
-            if (fct != 0.0)
-                for (int j = 0; j < 2 * NCLS; ++j) a[r][j] -= fct * a[col][j];
+            const float fct = a[r][col];
+#pragma unroll
+            for (int j = 0; j < 2 * NCLS; ++j) a[r][j] -= fct * a[col][j];
         }
     }
     for (int k = 0; k < NCLS; ++k)
-        for (int kk = 0; kk < NCLS; ++kk) L.sinv[(int64_t)(k * NCLS + kk) * L.cells + cell] = (float)a[k][NCLS + kk];
+        for (int kk = 0; kk < NCLS; ++kk) L.sinv[(int64_t)(k * NCLS + kk) * L.cells + cell] = a[k][NCLS + kk];
     // BF16 copy, block q (0..5 off_d, 6 exd, 7 sinv), row k: pk[(4q + k) * cells + cell]
     for (int q = 0; q < 8; ++q) {
         const float* src = q < 6 ? L.off + (int64_t)q * BLK * L.cells : (q == 6 ? L.exd : L.sinv);
@@ -1439,11 +1437,12 @@ int precond_setup(mb_cell* c, const float* u32, const uint8_t* gate, double dt) 
     p->nu_fine = c->opt.mg_smooth < 1 ? 1 : (c->opt.mg_smooth > 8 ? 8 : c->opt.mg_smooth);
     const Dims& D = c->D;
     cudaStream_t s = c->stream;
-    k_bj_setup<<<pgrid(D.nt, D.ny, D.nz), PB, 0, s>>>(c->Pf, D, c->vcode, u32, gate, dt, c->s_i0, c->k_pl,
-                                                       p->dinv, p->fc, c->rowdiag, c->rowinv), ::mb::count_launch(c);
+    (void)gate;
+    k_bj_setup<<<pgrid(D.nt, D.ny, D.nz), PB, 0, s>>>(c->Pf, D, c->vcode, u32, c->icoef, dt, p->dinv, p->fc,
+                                                       c->rowdiag, c->rowinv), ::mb::count_launch(c);
     Level& L1 = p->lv[1];
-    k_assemble_l1<<<(unsigned)((L1.cells + 127) / 128), 128, 0, s>>>(c->Pf, D, c->vcode, u32, gate, dt, c->s_i0,
-                                                                      c->k_pl, L1), ::mb::count_launch(c);
+    k_assemble_l1<<<(unsigned)((L1.cells + 127) / 128), 128, 0, s>>>(c->Pf, D, c->vcode, u32, c->icoef, dt, L1),
+        ::mb::count_launch(c);
     for (int l = 2; l <= p->nlev; ++l)
         k_assemble_up<<<nblk(p->lv[l].cells), 256, 0, s>>>(p->lv[l - 1], p->lv[l]), ::mb::count_launch(c);
     for (int l = 1; l <= p->nlev; ++l) k_finalize<<<nblk(p->lv[l].cells), 256, 0, s>>>(p->lv[l]), ::mb::count_launch(c);
@@ -1516,12 +1515,13 @@ static void vcycle(mb_cell* c, int l) {
     }
     Level& C = p->lv[l + 1];
     const bool timed = l == 1;
+    const int nu_pre = c->opt.mg_coarse_pre, nu_post = c->opt.mg_coarse_post;
     // pre-smoothing from zero; the first two sweeps fused
-    if (NU >= 2)
+    if (nu_pre >= 2)
         lvl_smooth2(c, L, L.x);
     else
         lvl_smooth(c, L, nullptr, nullptr, 0, 0, L.x);
-    for (int k = 2; k < NU; ++k) {
+    for (int k = 2; k < nu_pre; ++k) {
         lvl_smooth(c, L, L.x, nullptr, 0, 0, L.x2);
         std::swap(L.x, L.x2);
     }
@@ -1530,7 +1530,7 @@ static void vcycle(mb_cell* c, int l) {
     // post-smoothing, the first sweep applied to x + P e
     lvl_smooth(c, L, L.x, C.x, C.ny, C.nz, L.x2, timed);
     std::swap(L.x, L.x2);
-    for (int k = 1; k < NU; ++k) {
+    for (int k = 1; k < nu_post; ++k) {
         lvl_smooth(c, L, L.x, nullptr, 0, 0, L.x2, timed);
         std::swap(L.x, L.x2);
     }
@@ -1853,9 +1853,9 @@ int mb_debug_precond(mb_cell* c, const double* u, const uint8_t* gate, double dt
     if (F) MB_CUDA(cudaMemcpyAsync(c->gate2, gate, F, cudaMemcpyHostToDevice, s));
     MB_CUDA(cudaMemcpyAsync(r64, r, 8 * n, cudaMemcpyHostToDevice, s));
     k_cvt<double, float><<<nblk(n), 256, 0, s>>>(r64, r32, n), ::mb::count_launch(c);
-    int rc = precond_setup(c, c->u32, c->gate2, dt);
-    if (!rc) rc = launch_lin_setup<float>(c, c->u32, c->gate2, s);
+    int rc = launch_lin_setup<float>(c, c->u32, c->gate2, s);
     if (!rc) rc = set_dt(c, dt, s);
+    if (!rc) rc = precond_setup(c, c->u32, c->gate2, dt);
     if (!rc) rc = precond_setup_fine(c);
     if (!rc) rc = precond_apply(c, c->u32, c->gate2, dt, r32, zdf, false);
     if (!rc) {

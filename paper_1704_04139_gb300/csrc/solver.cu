@@ -369,12 +369,12 @@ static int linear_solve(mb_cell* c, double dt, int* its, double* relres) {
     cudaStream_t s = c->stream;
     k_convert<double, float><<<nblk(n), 256, 0, s>>>(c->u, c->u32, n), ::mb::count_launch(c);
     MB_CUDA_LAUNCH("u32");
-    int rc = precond_setup(c, c->u32, c->gate, dt);
+    int rc = set_dt(c, dt, s);
     if (rc) return rc;
-    if ((rc = set_dt(c, dt, s))) return rc;
     rc = c->opt.precision == MB_PREC_MIXED ? launch_lin_setup<float>(c, c->u32, c->gate, s)
                                            : launch_lin_setup<double>(c, c->u, c->gate, s);
     if (rc) return rc;
+    if ((rc = precond_setup(c, c->u32, c->gate, dt))) return rc;
     if ((rc = precond_setup_fine(c))) return rc;
     if (!c->kd && (rc = krylov_create(c, &c->kd))) return rc;
     Krylov* K = c->kd;

@@ -35,10 +35,11 @@ def test_profiling_counters_across_steps(params):
     assert n_pc >= info["krylov_its"] and ms_pc > 0
     # every preconditioner application runs 2 * mg_smooth - 1 fine sweeps with a product
     assert n_sm == (2 * B.default_opts().mg_smooth - 1) * n_pc and ms_sm > 0
-    # and per level-1 V-cycle (one per K-cycle iteration) 2 timed post-smoothing sweeps
+    # and per level-1 V-cycle (one per K-cycle iteration) mg_coarse_post timed post-smoothing sweeps
     n_ls, ms_ls = cell.prof_read(B.Cell.PROF_LSMOOTH)
     if len(cell.debug_levels()) > 1:
-        assert n_ls == 2 * B.default_opts().mg_kcycle * n_pc and 0 < ms_ls < ms_pc
+        o = B.default_opts()
+        assert n_ls == o.mg_coarse_post * o.mg_kcycle * n_pc and 0 < ms_ls < ms_pc
     else:
         assert n_ls == 0
     assert n_op >= info["krylov_its"] and n_r >= info["newton_its"]
