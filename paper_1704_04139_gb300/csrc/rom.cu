@@ -427,14 +427,15 @@ k_rom_lu(int Nr, float* __restrict__ J, const double* __restrict__ r, const int*
     for (int j = threadIdx.x; j < Nr; j += blockDim.x) delta[(int64_t)b * Nr + j] = (double)(x[j] * cs[j]);
 }
 
-// The same factorisation and solve with one warp per instance, the matrix in
-// shared memory (Nr <= ROM_LU_WARP_NR): lanes over rows for the pivot search
-// and the multipliers, over columns for the row swap and the update; the
-// pivot is the largest magnitude, the lowest row on ties.
-constexpr int ROM_LU_WARP_NR = 64;
-__global__ void __launch_bounds__(32)
-k_rom_lu_warp(int Nr, float* __restrict__ J, const double* __restrict__ r, const int* __restrict__ active,
-              double* __restrict__ delta) {
+// The same factorisation and solve with four warps per instance, the matrix
+// in shared memory (Nr <= ROM_LU4_NR): per column one warp finds the pivot,
+// then all threads swap, form the multipliers and update the trailing block
+// (four barriers per column); warp 0 does the back substitution.
+constexpr int ROM_LU4_NR = 96;
+constexpr int LU4_T = 128;
+__global__ void __launch_bounds__(LU4_T)
+k_rom_lu4(int Nr, float* __restrict__ J, const double* __restrict__ r, const int* __restrict__ active,
+          double* __restrict__ delta) {
     const int b = blockIdx.x;
     if (!active[b]) return;
     extern __shared__ float lu_sm[];
@@ -443,76 +444,85 @@ k_rom_lu_warp(int Nr, float* __restrict__ J, const double* __restrict__ r, const
     float* cs = rs + Nr;              // column scales
     float* rhs = cs + Nr;
     float* x = rhs + Nr;
-    const int lane = threadIdx.x;
+    __shared__ int spiv;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const float* Jb = J + (int64_t)b * Nr * Nr;
-    for (int e = lane; e < Nr * Nr; e += 32) A[e] = Jb[e];
-    __syncwarp();
-    for (int i = lane; i < Nr; i += 32) {
+    for (int e = tid; e < Nr * Nr; e += LU4_T) A[e] = Jb[e];
+    __syncthreads();
+    for (int i = tid; i < Nr; i += LU4_T) {
         float m = 0.f;
         for (int j = 0; j < Nr; ++j) m = fmaxf(m, fabsf(A[i * Nr + j]));
         rs[i] = m > 0.f ? 1.f / m : 1.f;
     }
-    __syncwarp();
-    for (int j = lane; j < Nr; j += 32) {
+    __syncthreads();
+    for (int j = tid; j < Nr; j += LU4_T) {
         float m = 0.f;
         for (int i = 0; i < Nr; ++i) m = fmaxf(m, fabsf(A[i * Nr + j] * rs[i]));
         cs[j] = m > 0.f ? 1.f / m : 1.f;
     }
-    __syncwarp();
-    for (int e = lane; e < Nr * Nr; e += 32) A[e] *= rs[e / Nr] * cs[e % Nr];
-    for (int i = lane; i < Nr; i += 32) rhs[i] = (float)(-r[(int64_t)b * Nr + i]) * rs[i];
-    __syncwarp();
+    __syncthreads();
+    for (int e = tid; e < Nr * Nr; e += LU4_T) A[e] *= rs[e / Nr] * cs[e % Nr];
+    for (int i = tid; i < Nr; i += LU4_T) rhs[i] = (float)(-r[(int64_t)b * Nr + i]) * rs[i];
+    __syncthreads();
     for (int k = 0; k < Nr; ++k) {
-        float best = -1.f;
-        int bi = k;
-        for (int i = k + lane; i < Nr; i += 32) {
-            const float v = fabsf(A[i * Nr + k]);
-            if (v > best) { best = v; bi = i; }
+        if (wid == 0) {
+            float best = -1.f;
+            int bi = k;
+            for (int i = k + lane; i < Nr; i += 32) {
+                const float v = fabsf(A[i * Nr + k]);
+                if (v > best) { best = v; bi = i; }
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                const float v2 = __shfl_xor_sync(0xffffffffu, best, o);
+                const int i2 = __shfl_xor_sync(0xffffffffu, bi, o);
+                if (v2 > best || (v2 == best && i2 < bi)) { best = v2; bi = i2; }
+            }
+            if (lane == 0) spiv = bi;
         }
-        for (int o = 16; o > 0; o >>= 1) {
-            const float v2 = __shfl_xor_sync(0xffffffffu, best, o);
-            const int i2 = __shfl_xor_sync(0xffffffffu, bi, o);
-            if (v2 > best || (v2 == best && i2 < bi)) { best = v2; bi = i2; }
-        }
-        const int piv = bi;
+        __syncthreads();
+        const int piv = spiv;
         if (piv != k) {
-            for (int j = lane; j < Nr; j += 32) {
+            for (int j = tid; j < Nr; j += LU4_T) {
                 const float t = A[k * Nr + j];
                 A[k * Nr + j] = A[piv * Nr + j];
                 A[piv * Nr + j] = t;
             }
-            if (lane == 0) {
+            if (tid == 0) {
                 const float t = rhs[k];
                 rhs[k] = rhs[piv];
                 rhs[piv] = t;
             }
         }
-        __syncwarp();
+        __syncthreads();
         const float akk = A[k * Nr + k];
         const float inv = akk != 0.f ? 1.f / akk : 0.f;
-        for (int i = k + 1 + lane; i < Nr; i += 32) {
+        for (int i = k + 1 + tid; i < Nr; i += LU4_T) {
             const float l = A[i * Nr + k] * inv;
             A[i * Nr + k] = l;
             rhs[i] -= l * rhs[k];
         }
-        __syncwarp();
-        for (int i = k + 1; i < Nr; ++i) {
-            const float l = A[i * Nr + k];
-            for (int j = k + 1 + lane; j < Nr; j += 32) A[i * Nr + j] -= l * A[k * Nr + j];
+        __syncthreads();
+        const int m = Nr - k - 1;
+        for (int e = tid; e < m * m; e += LU4_T) {
+            const int i = k + 1 + e / m, j = k + 1 + e % m;
+            A[i * Nr + j] -= A[i * Nr + k] * A[k * Nr + j];
         }
-        __syncwarp();
+        __syncthreads();
     }
-    for (int k = Nr - 1; k >= 0; --k) {
-        float part = 0.f;
-        for (int j = k + 1 + lane; j < Nr; j += 32) part += A[k * Nr + j] * x[j];
-        for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
-        if (lane == 0) {
-            const float akk = A[k * Nr + k];
-            x[k] = akk != 0.f ? (rhs[k] - part) / akk : 0.f;
+    if (wid == 0) {
+        for (int k = Nr - 1; k >= 0; --k) {
+            float part = 0.f;
+            for (int j = k + 1 + lane; j < Nr; j += 32) part += A[k * Nr + j] * x[j];
+            for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+            if (lane == 0) {
+                const float a_kk = A[k * Nr + k];
+                x[k] = a_kk != 0.f ? (rhs[k] - part) / a_kk : 0.f;
+            }
+            __syncwarp();
         }
-        __syncwarp();
     }
-    for (int j = lane; j < Nr; j += 32) delta[(int64_t)b * Nr + j] = (double)(x[j] * cs[j]);
+    __syncthreads();
+    for (int j = tid; j < Nr; j += LU4_T) delta[(int64_t)b * Nr + j] = (double)(x[j] * cs[j]);
 }
 
 // Step length of all instances: the scaled max-norm of the reconstructed
@@ -1058,9 +1068,9 @@ int rom_batch_step(mb_rom* R) {
                 k_rom_jac_wide<<<dim3((unsigned)d.Nr, (unsigned)B), 128, 0, s>>>(d, B, w.prm, w.GU, w.active, w.J),
                     count_launch(c);
             k_rom_resid<<<(unsigned)B, 128, 0, s>>>(d, w.a, w.a_old, w.prm, w.f, w.active, w.r), count_launch(c);
-            if (d.Nr <= ROM_LU_WARP_NR)
-                k_rom_lu_warp<<<(unsigned)B, 32, (size_t)4 * ((size_t)d.Nr * d.Nr + 4 * d.Nr), s>>>(d.Nr, w.J, w.r,
-                                                                                                    w.active, w.delta),
+            if (d.Nr <= ROM_LU4_NR)
+                k_rom_lu4<<<(unsigned)B, LU4_T, (size_t)4 * ((size_t)d.Nr * d.Nr + 4 * d.Nr), s>>>(d.Nr, w.J, w.r,
+                                                                                                   w.active, w.delta),
                     count_launch(c);
             else
                 k_rom_lu<<<(unsigned)B, 256, 0, s>>>(d.Nr, w.J, w.r, w.active, w.delta), count_launch(c);
