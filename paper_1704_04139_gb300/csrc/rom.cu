@@ -21,11 +21,18 @@
 // the residual are FP64, so the converged solution is the FP64 one; the
 // Newton matrix (GU, the contraction P GU as one GEMM over all instances,
 // its LU) and the step-length norm are FP32 (an inexact Newton iteration:
-// GB300's FP64 rate is a small fraction of its FP32 rate).
+// GB300's FP64 rate is a small fraction of its FP32 rate).  An instance
+// switches to an FP64 Newton matrix (FP64 derivatives, G U_loc, contraction
+// and LU) for the rest of its time step when its iteration stagnates (a full
+// step whose norm fell by less than 10 %, from the third iteration of a
+// pass) or has not converged after ROM_HP_AFTER iterations: an FP32 matrix
+// cannot converge when the equilibrated reduced Jacobian's condition number
+// approaches 1/eps_32 (POD modes kept down to tiny singular values).
 #include <cuda_runtime.h>
 #include <math.h>
 
 #include <algorithm>
+#include <type_traits>
 #include <map>
 #include <vector>
 
@@ -41,6 +48,7 @@ constexpr int ROM_PASSES = 3;
 constexpr double ROM_DELTA_MAX = 0.25;
 constexpr double ROM_TOL = 1e-12;
 constexpr int RP = 4;            // per-instance parameters: I_app, s_i0, k_pl, 1/dt
+constexpr int ROM_HP_AFTER = 8;  // FP32-matrix iterations of a pass before an instance switches to FP64
 
 enum RomTerm : int8_t { T_NONE = 0, T_GE = 1, T_KE = 2, T_LE = 3, T_EE = 4 };
 
@@ -80,6 +88,13 @@ struct RomWork {
     double *uloc = nullptr, *uloc_old = nullptr, *f = nullptr;
     float* G = nullptr;        // B x M x GMAX derivative lists (FP32: they only feed the Newton matrix)
     float* dpart = nullptr;    // B x ceil(nloc / UN_K): partial maxima of the step-length norm
+    int* hp = nullptr;         // B: instance uses the FP64 Newton matrix (for the rest of the time step)
+    int* pit = nullptr;        // B: iterations in the current pass
+    float* dnprev = nullptr;   // B: step norm of the previous iteration
+    double* G64 = nullptr;     // B x M x GMAX   FP64 derivative lists of the hp instances
+    double* GU64 = nullptr;    // B x M x Nr     their G U_loc
+    double* J64 = nullptr;     // B x Nr x Nr    their Newton matrices
+    int hp_any = 0;            // host: some instance used the FP64 matrix at the last count
     double* prm = nullptr;
     uint8_t *gate = nullptr, *gate2 = nullptr;
     int *active = nullptr, *failed = nullptr, *pass_on = nullptr, *counts = nullptr;
@@ -140,19 +155,24 @@ __global__ void k_rom_gate(RomDev d, int B, const double* __restrict__ uloc, con
     gate[i] = (uo[s[2]] > n_thr || etap < 0.0) ? 1 : 0;
 }
 
-// f (FP64) and its derivative list (FP32) at every point
+// f (FP64) and its derivative list at every point, for the instances whose
+// Newton-matrix precision matches HP (FP64 derivatives to G64 when HP, FP32
+// to G otherwise)
+template <bool HP>
 __global__ void k_rom_ei(RomDev d, DevParams P, ParT<float> Pf, int B, const double* __restrict__ uloc,
                          const uint8_t* __restrict__ gate, const double* __restrict__ prm,
-                         const int* __restrict__ active, double* __restrict__ f, float* __restrict__ G) {
+                         const int* __restrict__ active, const int* __restrict__ hp, double* __restrict__ f,
+                         float* __restrict__ G, double* __restrict__ G64) {
+    using TG = typename std::conditional<HP, double, float>::type;
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= (int64_t)d.M * B) return;
     const int b = (int)(i / d.M), p = (int)(i % d.M);
-    if (!active[b]) return;
+    if (!active[b] || (hp[b] != 0) != HP) return;
     const double* u = uloc + (int64_t)b * d.nloc;
     const double s_i0 = prm[RP * b + 1], k_pl = prm[RP * b + 2];
-    float g[GMAX];
+    TG g[GMAX];
 #pragma unroll
-    for (int e = 0; e < GMAX; ++e) g[e] = 0.f;
+    for (int e = 0; e < GMAX; ++e) g[e] = TG(0);
     double fv = 0.0;
     for (int t = 0; t < TMAX; ++t) {
         const int q = p * TMAX + t;
@@ -167,8 +187,8 @@ __global__ void k_rom_ei(RomDev d, DevParams P, ParT<float> Pf, int B, const dou
             const double dc = cw - cv, gm = P.E_gm;
             const double w = d.twbv[q];
             fv += w * (-gm * dc / S);
-            g[gp[0]] += (float)(w * (gm / S + (cv >= cmin ? gm * dc / (S * S) : 0.0)));
-            g[gp[2]] += (float)(w * (-gm / S + (cw >= cmin ? gm * dc / (S * S) : 0.0)));
+            g[gp[0]] += (TG)(w * (gm / S + (cv >= cmin ? gm * dc / (S * S) : 0.0)));
+            g[gp[2]] += (TG)(w * (-gm / S + (cw >= cmin ? gm * dc / (S * S) : 0.0)));
         } else {
             const int ls = type == T_GE ? PG : (type == T_KE ? PK : PL);
             const double cs = sl[0] >= 0 ? u[sl[0]] : 0.0, ps = u[sl[1]];
@@ -177,12 +197,16 @@ __global__ void k_rom_ei(RomDev d, DevParams P, ParT<float> Pf, int B, const dou
             const bool gt = d.tgate[q] >= 0 && gate[(int64_t)b * d.ngate + d.tgate[q]] != 0;
             double ibv, ipl;
             interface_current<double>(P, ls, cs, ps, ce, pe, nf, gt, s_i0, k_pl, ibv, ipl);
-            float i_eta, i_cs, i_ce, ip_eta, ip_ce, ip_n;
-            interface_partials<float>(Pf, ls, (float)cs, (float)ps, (float)ce, (float)pe, (float)nf, gt, (float)s_i0,
-                                      (float)k_pl, i_eta, i_cs, i_ce, ip_eta, ip_ce, ip_n);
+            TG i_eta, i_cs, i_ce, ip_eta, ip_ce, ip_n;
+            if constexpr (HP)
+                interface_partials<double>(P, ls, cs, ps, ce, pe, nf, gt, s_i0, k_pl, i_eta, i_cs, i_ce, ip_eta, ip_ce,
+                                           ip_n);
+            else
+                interface_partials<float>(Pf, ls, (float)cs, (float)ps, (float)ce, (float)pe, (float)nf, gt,
+                                          (float)s_i0, (float)k_pl, i_eta, i_cs, i_ce, ip_eta, ip_ce, ip_n);
             const double wbd = d.twbv[q], wpd = d.twpl[q];
             fv += wbd * ibv + wpd * ipl;
-            const float wb = (float)wbd, wp = (float)wpd;
+            const TG wb = (TG)wbd, wp = (TG)wpd;
             if (sl[0] >= 0) g[gp[0]] += wb * i_cs;
             g[gp[1]] += wb * i_eta + wp * ip_eta;
             if (sl[2] >= 0) g[gp[2]] += wb * i_ce + wp * ip_ce;
@@ -191,7 +215,11 @@ __global__ void k_rom_ei(RomDev d, DevParams P, ParT<float> Pf, int B, const dou
         }
     }
     f[(int64_t)b * d.M + p] = fv;
-    float* Gp = G + ((int64_t)b * d.M + p) * GMAX;
+    TG* Gp;
+    if constexpr (HP)
+        Gp = G64 + ((int64_t)b * d.M + p) * GMAX;
+    else
+        Gp = G + ((int64_t)b * d.M + p) * GMAX;
 #pragma unroll
     for (int e = 0; e < GMAX; ++e) Gp[e] = g[e];
 }
@@ -201,13 +229,13 @@ __global__ void k_rom_ei(RomDev d, DevParams P, ParT<float> Pf, int B, const dou
 // instances write zeros so that the GEMM below reads defined values
 // one warp per (point, instance): lanes over j
 __global__ void k_rom_gu(RomDev d, int B, const float* __restrict__ G, const int* __restrict__ active,
-                         float* __restrict__ GU) {
+                         const int* __restrict__ hp, float* __restrict__ GU) {
     const int64_t wg = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (wg >= (int64_t)d.M * B) return;
     const int b = (int)(wg / d.M), p = (int)(wg % d.M);
     float* out = GU + ((int64_t)p * B + b) * d.Nr;
-    if (!active[b]) {
+    if (!active[b] || hp[b]) {
         for (int j = lane; j < d.Nr; j += 32) out[j] = 0.f;
         return;
     }
@@ -231,7 +259,8 @@ __global__ void k_rom_gu(RomDev d, int B, const float* __restrict__ G, const int
 // staged in shared memory.  Column c = b Nr + j.
 constexpr int JT_ROWS = 64, JT_COLS = 64, JT_K = 16;
 __global__ void __launch_bounds__(256)
-k_rom_jac(RomDev d, int B, const double* __restrict__ prm, const float* __restrict__ GU, float* __restrict__ J) {
+k_rom_jac(RomDev d, int B, const double* __restrict__ prm, const float* __restrict__ GU,
+          const int* __restrict__ hp, float* __restrict__ J) {
     __shared__ float As[JT_K][JT_ROWS];
     __shared__ float Bs[JT_K][JT_COLS];
     const int Nr = d.Nr, M = d.M;
@@ -273,6 +302,7 @@ k_rom_jac(RomDev d, int B, const double* __restrict__ prm, const float* __restri
         const int64_t c = c0 + tx * 4 + q;
         if (c >= ncol) continue;
         const int b = (int)(c / Nr), j = (int)(c % Nr);
+        if (hp[b]) continue;   // its Newton matrix is the FP64 one
         const float dt_inv = (float)prm[RP * b + 3];
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
@@ -286,9 +316,9 @@ k_rom_jac(RomDev d, int B, const double* __restrict__ prm, const float* __restri
 
 // the same product for Nr > 64: row i of instance b per block
 __global__ void k_rom_jac_wide(RomDev d, int B, const double* __restrict__ prm, const float* __restrict__ GU,
-                               const int* __restrict__ active, float* __restrict__ J) {
+                               const int* __restrict__ active, const int* __restrict__ hp, float* __restrict__ J) {
     const int i = blockIdx.x, b = blockIdx.y;
-    if (!active[b]) return;
+    if (!active[b] || hp[b]) return;
     const int Nr = d.Nr;
     const float dt_inv = (float)prm[RP * b + 3];
     const float* Pi = d.Pf + (int64_t)i * d.M;
@@ -296,6 +326,39 @@ __global__ void k_rom_jac_wide(RomDev d, int B, const double* __restrict__ prm, 
         float acc = 0.f;
         for (int p = 0; p < d.M; ++p) acc = fmaf(Pi[p], GU[((int64_t)p * B + b) * Nr + j], acc);
         J[((int64_t)b * Nr + i) * Nr + j] = acc + d.Msf[(int64_t)i * Nr + j] * dt_inv + d.Alinf[(int64_t)i * Nr + j];
+    }
+}
+
+// FP64 Newton matrix of the instances with hp[b]: GU64[b][p][:] = G64[b][p] U_loc
+// (one block per point and instance), then J64[b] = Ms/dt + Alin + P GU64[b]
+// (one block per row and instance)
+__global__ void k_rom_gu64(RomDev d, const double* __restrict__ G, const int* __restrict__ active,
+                           const int* __restrict__ hp, double* __restrict__ GU) {
+    const int p = blockIdx.x, b = blockIdx.y;
+    if (!active[b] || !hp[b]) return;
+    const double* Gp = G + ((int64_t)b * d.M + p) * GMAX;
+    const int32_t* gi = d.gidx + (int64_t)p * GMAX;
+    for (int j = threadIdx.x; j < d.Nr; j += blockDim.x) {
+        double acc = 0.0;
+        for (int e = 0; e < GMAX; ++e) {
+            const int s = gi[e];
+            if (s < 0) break;
+            acc += Gp[e] * d.UlocR[(int64_t)s * d.Nr + j];
+        }
+        GU[((int64_t)b * d.M + p) * d.Nr + j] = acc;
+    }
+}
+__global__ void k_rom_jac64(RomDev d, const double* __restrict__ prm, const double* __restrict__ GU,
+                            const int* __restrict__ active, const int* __restrict__ hp, double* __restrict__ J) {
+    const int i = blockIdx.x, b = blockIdx.y;
+    if (!active[b] || !hp[b]) return;
+    const double dt_inv = prm[RP * b + 3];
+    const double* Pi = d.P + (int64_t)i * d.M;
+    const double* GUb = GU + (int64_t)b * d.M * d.Nr;
+    for (int j = threadIdx.x; j < d.Nr; j += blockDim.x) {
+        double acc = d.Ms[(int64_t)i * d.Nr + j] * dt_inv + d.Alin[(int64_t)i * d.Nr + j];
+        for (int p = 0; p < d.M; ++p) acc += Pi[p] * GUb[(int64_t)p * d.Nr + j];
+        J[((int64_t)b * d.Nr + i) * d.Nr + j] = acc;
     }
 }
 
@@ -327,39 +390,40 @@ k_rom_resid(RomDev d, const double* __restrict__ a, const double* __restrict__ a
 // row then column equilibration, LU with partial pivoting (ties: lowest
 // row), forward elimination of the right-hand side during the
 // factorisation, back substitution.  One block per instance, J[b] overwritten.
+template <class T>
 __global__ void __launch_bounds__(256)
-k_rom_lu(int Nr, float* __restrict__ J, const double* __restrict__ r, const int* __restrict__ active,
-         double* __restrict__ delta) {
+k_rom_lu(int Nr, T* __restrict__ J, const double* __restrict__ r, const int* __restrict__ active,
+         const int* __restrict__ hp, int want_hp, double* __restrict__ delta) {
     const int b = blockIdx.x;
-    if (!active[b]) return;
-    __shared__ float sh[256];
-    __shared__ float rs[ROM_NR_MAX], cs[ROM_NR_MAX], rhs[ROM_NR_MAX], x[ROM_NR_MAX];
+    if (!active[b] || (hp[b] != 0) != (want_hp != 0)) return;
+    __shared__ T sh[256];
+    __shared__ T rs[ROM_NR_MAX], cs[ROM_NR_MAX], rhs[ROM_NR_MAX], x[ROM_NR_MAX];
     __shared__ int spiv;
-    float* A = J + (int64_t)b * Nr * Nr;
+    T* A = J + (int64_t)b * Nr * Nr;
     for (int i = threadIdx.x; i < Nr; i += blockDim.x) {
-        float m = 0.f;
-        for (int j = 0; j < Nr; ++j) m = fmaxf(m, fabsf(A[(int64_t)i * Nr + j]));
-        rs[i] = m > 0.f ? 1.f / m : 1.f;
+        T m = T(0);
+        for (int j = 0; j < Nr; ++j) m = fmax(m, fabs(A[(int64_t)i * Nr + j]));
+        rs[i] = m > T(0) ? T(1) / m : T(1);
     }
     __syncthreads();
     for (int j = threadIdx.x; j < Nr; j += blockDim.x) {
-        float m = 0.f;
-        for (int i = 0; i < Nr; ++i) m = fmaxf(m, fabsf(A[(int64_t)i * Nr + j] * rs[i]));
-        cs[j] = m > 0.f ? 1.f / m : 1.f;
+        T m = T(0);
+        for (int i = 0; i < Nr; ++i) m = fmax(m, fabs(A[(int64_t)i * Nr + j] * rs[i]));
+        cs[j] = m > T(0) ? T(1) / m : T(1);
     }
     __syncthreads();
     for (int idx = threadIdx.x; idx < Nr * Nr; idx += blockDim.x) {
         const int i = idx / Nr, j = idx % Nr;
         A[idx] *= rs[i] * cs[j];
     }
-    for (int i = threadIdx.x; i < Nr; i += blockDim.x) rhs[i] = (float)(-r[(int64_t)b * Nr + i]) * rs[i];
+    for (int i = threadIdx.x; i < Nr; i += blockDim.x) rhs[i] = (T)(-r[(int64_t)b * Nr + i]) * rs[i];
     __syncthreads();
     for (int k = 0; k < Nr; ++k) {
         // pivot: largest |A[i][k]|, i >= k, lowest index on ties
-        float best = -1.f;
+        T best = T(-1);
         int bi = k;
         for (int i = k + threadIdx.x; i < Nr; i += blockDim.x) {
-            float v = fabsf(A[(int64_t)i * Nr + k]);
+            T v = fabs(A[(int64_t)i * Nr + k]);
             if (v > best) { best = v; bi = i; }
         }
         // reduce (value, index)
@@ -369,7 +433,7 @@ k_rom_lu(int Nr, float* __restrict__ J, const double* __restrict__ r, const int*
         __syncthreads();
         for (int s = blockDim.x / 2; s > 0; s >>= 1) {
             if (threadIdx.x < s) {
-                float v2 = sh[threadIdx.x + s];
+                T v2 = sh[threadIdx.x + s];
                 int i2 = shi[threadIdx.x + s];
                 if (v2 > sh[threadIdx.x] || (v2 == sh[threadIdx.x] && i2 < shi[threadIdx.x])) {
                     sh[threadIdx.x] = v2;
@@ -383,20 +447,20 @@ k_rom_lu(int Nr, float* __restrict__ J, const double* __restrict__ r, const int*
         const int piv = spiv;
         if (piv != k) {
             for (int j = threadIdx.x; j < Nr; j += blockDim.x) {
-                float t = A[(int64_t)k * Nr + j];
+                T t = A[(int64_t)k * Nr + j];
                 A[(int64_t)k * Nr + j] = A[(int64_t)piv * Nr + j];
                 A[(int64_t)piv * Nr + j] = t;
             }
             if (threadIdx.x == 0) {
-                float t = rhs[k]; rhs[k] = rhs[piv]; rhs[piv] = t;
+                T t = rhs[k]; rhs[k] = rhs[piv]; rhs[piv] = t;
             }
         }
         __syncthreads();
-        const float akk = A[(int64_t)k * Nr + k];
-        const float inv = akk != 0.f ? 1.f / akk : 0.f;
+        const T akk = A[(int64_t)k * Nr + k];
+        const T inv = akk != T(0) ? T(1) / akk : T(0);
         // multipliers and right-hand side
         for (int i = k + 1 + threadIdx.x; i < Nr; i += blockDim.x) {
-            float l = A[(int64_t)i * Nr + k] * inv;
+            T l = A[(int64_t)i * Nr + k] * inv;
             A[(int64_t)i * Nr + k] = l;
             rhs[i] -= l * rhs[k];
         }
@@ -410,7 +474,7 @@ k_rom_lu(int Nr, float* __restrict__ J, const double* __restrict__ r, const int*
     }
     // back substitution
     for (int k = Nr - 1; k >= 0; --k) {
-        float part = 0.f;
+        T part = T(0);
         for (int j = k + 1 + threadIdx.x; j < Nr; j += blockDim.x) part += A[(int64_t)k * Nr + j] * x[j];
         sh[threadIdx.x] = part;
         __syncthreads();
@@ -419,8 +483,8 @@ k_rom_lu(int Nr, float* __restrict__ J, const double* __restrict__ r, const int*
             __syncthreads();
         }
         if (threadIdx.x == 0) {
-            const float akk = A[(int64_t)k * Nr + k];
-            x[k] = akk != 0.f ? (rhs[k] - sh[0]) / akk : 0.f;
+            const T akk = A[(int64_t)k * Nr + k];
+            x[k] = akk != T(0) ? (rhs[k] - sh[0]) / akk : T(0);
         }
         __syncthreads();
     }
@@ -431,49 +495,51 @@ k_rom_lu(int Nr, float* __restrict__ J, const double* __restrict__ r, const int*
 // in shared memory (Nr <= ROM_LU4_NR): per column one warp finds the pivot,
 // then all threads swap, form the multipliers and update the trailing block
 // (four barriers per column); warp 0 does the back substitution.
-constexpr int ROM_LU4_NR = 96;
+constexpr int ROM_LU4_NR = 96;    // FP32 (FP64: 64, the shared-memory limit)
+constexpr int ROM_LU4_NR64 = 64;
 constexpr int LU4_T = 128;
+template <class T>
 __global__ void __launch_bounds__(LU4_T)
-k_rom_lu4(int Nr, float* __restrict__ J, const double* __restrict__ r, const int* __restrict__ active,
-          double* __restrict__ delta) {
+k_rom_lu4(int Nr, T* __restrict__ J, const double* __restrict__ r, const int* __restrict__ active,
+          const int* __restrict__ hp, int want_hp, double* __restrict__ delta) {
     const int b = blockIdx.x;
-    if (!active[b]) return;
-    extern __shared__ float lu_sm[];
-    float* A = lu_sm;                 // Nr x Nr
-    float* rs = A + Nr * Nr;          // row scales
-    float* cs = rs + Nr;              // column scales
-    float* rhs = cs + Nr;
-    float* x = rhs + Nr;
+    if (!active[b] || (hp[b] != 0) != (want_hp != 0)) return;
+    extern __shared__ __align__(16) unsigned char lu_raw[];
+    T* A = reinterpret_cast<T*>(lu_raw);   // Nr x Nr
+    T* rs = A + Nr * Nr;          // row scales
+    T* cs = rs + Nr;              // column scales
+    T* rhs = cs + Nr;
+    T* x = rhs + Nr;
     __shared__ int spiv;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    const float* Jb = J + (int64_t)b * Nr * Nr;
+    const T* Jb = J + (int64_t)b * Nr * Nr;
     for (int e = tid; e < Nr * Nr; e += LU4_T) A[e] = Jb[e];
     __syncthreads();
     for (int i = tid; i < Nr; i += LU4_T) {
-        float m = 0.f;
-        for (int j = 0; j < Nr; ++j) m = fmaxf(m, fabsf(A[i * Nr + j]));
-        rs[i] = m > 0.f ? 1.f / m : 1.f;
+        T m = T(0);
+        for (int j = 0; j < Nr; ++j) m = fmax(m, fabs(A[i * Nr + j]));
+        rs[i] = m > T(0) ? T(1) / m : T(1);
     }
     __syncthreads();
     for (int j = tid; j < Nr; j += LU4_T) {
-        float m = 0.f;
-        for (int i = 0; i < Nr; ++i) m = fmaxf(m, fabsf(A[i * Nr + j] * rs[i]));
-        cs[j] = m > 0.f ? 1.f / m : 1.f;
+        T m = T(0);
+        for (int i = 0; i < Nr; ++i) m = fmax(m, fabs(A[i * Nr + j] * rs[i]));
+        cs[j] = m > T(0) ? T(1) / m : T(1);
     }
     __syncthreads();
     for (int e = tid; e < Nr * Nr; e += LU4_T) A[e] *= rs[e / Nr] * cs[e % Nr];
-    for (int i = tid; i < Nr; i += LU4_T) rhs[i] = (float)(-r[(int64_t)b * Nr + i]) * rs[i];
+    for (int i = tid; i < Nr; i += LU4_T) rhs[i] = (T)(-r[(int64_t)b * Nr + i]) * rs[i];
     __syncthreads();
     for (int k = 0; k < Nr; ++k) {
         if (wid == 0) {
-            float best = -1.f;
+            T best = T(-1);
             int bi = k;
             for (int i = k + lane; i < Nr; i += 32) {
-                const float v = fabsf(A[i * Nr + k]);
+                const T v = fabs(A[i * Nr + k]);
                 if (v > best) { best = v; bi = i; }
             }
             for (int o = 16; o > 0; o >>= 1) {
-                const float v2 = __shfl_xor_sync(0xffffffffu, best, o);
+                const T v2 = __shfl_xor_sync(0xffffffffu, best, o);
                 const int i2 = __shfl_xor_sync(0xffffffffu, bi, o);
                 if (v2 > best || (v2 == best && i2 < bi)) { best = v2; bi = i2; }
             }
@@ -483,21 +549,21 @@ k_rom_lu4(int Nr, float* __restrict__ J, const double* __restrict__ r, const int
         const int piv = spiv;
         if (piv != k) {
             for (int j = tid; j < Nr; j += LU4_T) {
-                const float t = A[k * Nr + j];
+                const T t = A[k * Nr + j];
                 A[k * Nr + j] = A[piv * Nr + j];
                 A[piv * Nr + j] = t;
             }
             if (tid == 0) {
-                const float t = rhs[k];
+                const T t = rhs[k];
                 rhs[k] = rhs[piv];
                 rhs[piv] = t;
             }
         }
         __syncthreads();
-        const float akk = A[k * Nr + k];
-        const float inv = akk != 0.f ? 1.f / akk : 0.f;
+        const T akk = A[k * Nr + k];
+        const T inv = akk != T(0) ? T(1) / akk : T(0);
         for (int i = k + 1 + tid; i < Nr; i += LU4_T) {
-            const float l = A[i * Nr + k] * inv;
+            const T l = A[i * Nr + k] * inv;
             A[i * Nr + k] = l;
             rhs[i] -= l * rhs[k];
         }
@@ -511,12 +577,12 @@ k_rom_lu4(int Nr, float* __restrict__ J, const double* __restrict__ r, const int
     }
     if (wid == 0) {
         for (int k = Nr - 1; k >= 0; --k) {
-            float part = 0.f;
+            T part = T(0);
             for (int j = k + 1 + lane; j < Nr; j += 32) part += A[k * Nr + j] * x[j];
             for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
             if (lane == 0) {
-                const float a_kk = A[k * Nr + k];
-                x[k] = a_kk != 0.f ? (rhs[k] - part) / a_kk : 0.f;
+                const T a_kk = A[k * Nr + k];
+                x[k] = a_kk != T(0) ? (rhs[k] - part) / a_kk : T(0);
             }
             __syncwarp();
         }
@@ -591,7 +657,7 @@ k_rom_unorm(RomDev d, int B, const double* __restrict__ delta, const int* __rest
 __global__ void __launch_bounds__(32)
 k_rom_apply(RomDev d, int nkt, double* __restrict__ a, const double* __restrict__ delta,
             const float* __restrict__ dpart, int* __restrict__ active, int* __restrict__ failed,
-            long long* __restrict__ its) {
+            long long* __restrict__ its, int* __restrict__ pit, int* __restrict__ hp, float* __restrict__ dnprev) {
     const int b = blockIdx.x, lane = threadIdx.x;
     if (!active[b]) return;
     float m = 0.f;
@@ -610,7 +676,27 @@ k_rom_apply(RomDev d, int nkt, double* __restrict__ a, const double* __restrict_
     if (lane == 0) {
         its[b] += 1;
         if (lam * dn <= ROM_TOL) active[b] = 0;
+        const int k = ++pit[b];
+        if (k >= ROM_HP_AFTER || (k >= 3 && lam == 1.0 && m > 0.9f * dnprev[b])) hp[b] = 1;
+        dnprev[b] = m;
     }
+}
+
+// out[0] = active instances, out[1] = instances on the FP64 Newton matrix (active or not)
+__global__ void k_rom_count_hp(int B, const int* __restrict__ active, const int* __restrict__ hp,
+                               int* __restrict__ out) {
+    __shared__ int c0, c1;
+    if (threadIdx.x == 0) { c0 = 0; c1 = 0; }
+    __syncthreads();
+    int a = 0, h = 0;
+    for (int b = threadIdx.x; b < B; b += blockDim.x) {
+        a += active[b] != 0;
+        h += hp[b] != 0;
+    }
+    atomicAdd(&c0, a);
+    atomicAdd(&c1, h);
+    __syncthreads();
+    if (threadIdx.x == 0) { out[0] = c0; out[1] = c1; }
 }
 
 // copy src -> dst for instances with mask[b] (all instances if mask is null)
@@ -622,10 +708,14 @@ __global__ void k_rom_copy(int Nr, int B, const int* __restrict__ mask, const do
     dst[i] = src[i];
 }
 
+// active = on && !failed; pit (if given) = 0; hp (if given) = 0
 __global__ void k_rom_set_active(int B, const int* __restrict__ on, const int* __restrict__ failed,
-                                 int* __restrict__ active) {
+                                 int* __restrict__ active, int* __restrict__ pit, int* __restrict__ hp) {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b < B) active[b] = (on ? on[b] : 1) && !failed[b];
+    if (b >= B) return;
+    active[b] = (on ? on[b] : 1) && !failed[b];
+    if (pit) pit[b] = 0;
+    if (hp) hp[b] = 0;
 }
 
 // flips of pass-active instances; instances with flips stay on for the next pass
@@ -670,7 +760,7 @@ __global__ void k_rom_outputs(RomDev d, int B, const double* __restrict__ a, dou
 // start slot b: a = a0, parameters, counters zero, not failed
 __global__ void k_rom_slot_start(RomDev d, int b, double I_app, double s_i0, double k_pl, double dt_inv,
                                  double* __restrict__ a, double* __restrict__ prm, int* __restrict__ failed,
-                                 long long* __restrict__ its, long long* __restrict__ flips) {
+                                 long long* __restrict__ its, long long* __restrict__ flips, int* __restrict__ hp) {
     for (int j = threadIdx.x; j < d.Nr; j += blockDim.x) a[(int64_t)b * d.Nr + j] = d.a0[j];
     if (threadIdx.x == 0) {
         prm[RP * b] = I_app;
@@ -680,6 +770,7 @@ __global__ void k_rom_slot_start(RomDev d, int b, double I_app, double s_i0, dou
         failed[b] = 0;
         its[b] = 0;
         flips[b] = 0;
+        hp[b] = 0;
     }
 }
 
@@ -957,6 +1048,12 @@ static int rom_work_alloc(mb_rom* R, int B) {
     w.f = rom_alloc<double>(L, (size_t)B * d.M);
     w.G = rom_alloc<float>(L, (size_t)B * (d.M ? d.M : 1) * GMAX);
     w.dpart = rom_alloc<float>(L, (size_t)B * ((d.nloc + UN_K - 1) / UN_K));
+    w.hp = rom_alloc<int>(L, B);
+    w.pit = rom_alloc<int>(L, B);
+    w.dnprev = rom_alloc<float>(L, B);
+    w.G64 = rom_alloc<double>(L, (size_t)B * (d.M ? d.M : 1) * GMAX);
+    w.GU64 = rom_alloc<double>(L, (size_t)B * (d.M ? d.M : 1) * d.Nr);
+    w.J64 = rom_alloc<double>(L, (size_t)B * d.Nr * d.Nr);
     w.GU = rom_alloc<float>(L, (size_t)B * (d.M ? d.M : 1) * d.Nr);
     w.prm = rom_alloc<double>(L, (size_t)B * RP);
     w.gate = rom_alloc<uint8_t>(L, (size_t)B * (d.ngate ? d.ngate : 1));
@@ -989,14 +1086,17 @@ int rom_batch_alloc(mb_rom* R, int B) {
     MB_CUDA(cudaMemsetAsync(w.gate, 0, (size_t)B * (R->d.ngate ? R->d.ngate : 1), s));
     MB_CUDA(cudaMemsetAsync(w.its, 0, 8 * B, s));
     MB_CUDA(cudaMemsetAsync(w.flips, 0, 8 * B, s));
+    MB_CUDA(cudaMemsetAsync(w.hp, 0, 4 * B, s));
+    MB_CUDA(cudaMemsetAsync(w.pit, 0, 4 * B, s));
     MB_CUDA(cudaStreamSynchronize(s));
+    w.hp_any = 0;
     return MB_OK;
 }
 
 int rom_slot_start(mb_rom* R, int b, const mb_rom_params& p, double dt) {
     RomWork& w = R->w;
     k_rom_slot_start<<<1, 128, 0, R->cell->stream>>>(R->d, b, p.I_app, p.s_i0, p.k_pl, 1.0 / dt, w.a, w.prm,
-                                                     w.failed, w.its, w.flips), count_launch(R->cell);
+                                                     w.failed, w.its, w.flips, w.hp), count_launch(R->cell);
     MB_CUDA_LAUNCH("rom_slot_start");
     return MB_OK;
 }
@@ -1049,42 +1149,64 @@ int rom_batch_step(mb_rom* R) {
     k_rom_copy<<<nb, 256, 0, s>>>(d.Nr, B, nullptr, w.a, w.a_old), count_launch(c);
     k_rom_gather<<<gg, 256, 0, s>>>(d, w.a_old, w.uloc_old), count_launch(c);
     if (d.ngate) k_rom_gate<<<gt, 256, 0, s>>>(d, B, w.uloc_old, w.uloc_old, n_thr, w.gate), count_launch(c);
-    k_rom_set_active<<<bb, 256, 0, s>>>(B, nullptr, w.failed, w.pass_on), count_launch(c);
+    k_rom_set_active<<<bb, 256, 0, s>>>(B, nullptr, w.failed, w.pass_on, nullptr, w.hp), count_launch(c);
+    w.hp_any = 0;
     for (int pass = 1; pass <= ROM_PASSES; ++pass) {
         k_rom_copy<<<nb, 256, 0, s>>>(d.Nr, B, w.pass_on, w.a_old, w.a), count_launch(c);
-        k_rom_set_active<<<bb, 256, 0, s>>>(B, w.pass_on, w.failed, w.active), count_launch(c);
+        k_rom_set_active<<<bb, 256, 0, s>>>(B, w.pass_on, w.failed, w.active, w.pit, nullptr), count_launch(c);
         for (int it = 0; it < ROM_MAXIT; ++it) {
+            // FP64 Newton-matrix kernels only while some instance uses them (hp only turns on
+            // within a step, so the count of the previous iteration covers this one)
+            const bool hp_any = w.hp_any > 0;
             k_rom_gather<<<gg, 256, 0, s>>>(d, w.a, w.uloc), count_launch(c);
             if (d.M) {
-                k_rom_ei<<<ge, 128, 0, s>>>(d, c->P, c->Pf, B, w.uloc, w.gate, w.prm, w.active, w.f, w.G),
-                    count_launch(c);
-                k_rom_gu<<<(unsigned)(((int64_t)d.M * B * 32 + 255) / 256), 256, 0, s>>>(d, B, w.G, w.active, w.GU),
-                    count_launch(c);
+                k_rom_ei<false><<<ge, 128, 0, s>>>(d, c->P, c->Pf, B, w.uloc, w.gate, w.prm, w.active, w.hp, w.f,
+                                                   w.G, w.G64), count_launch(c);
+                if (hp_any) {
+                    k_rom_ei<true><<<ge, 128, 0, s>>>(d, c->P, c->Pf, B, w.uloc, w.gate, w.prm, w.active, w.hp, w.f,
+                                                      w.G, w.G64), count_launch(c);
+                    k_rom_gu64<<<dim3((unsigned)d.M, (unsigned)B), 64, 0, s>>>(d, w.G64, w.active, w.hp, w.GU64),
+                        count_launch(c);
+                }
+                k_rom_gu<<<(unsigned)(((int64_t)d.M * B * 32 + 255) / 256), 256, 0, s>>>(d, B, w.G, w.active, w.hp,
+                                                                                           w.GU), count_launch(c);
             }
             if (d.Nr <= JT_ROWS)
                 k_rom_jac<<<(unsigned)(((int64_t)B * d.Nr + JT_COLS - 1) / JT_COLS), 256, 0, s>>>(d, B, w.prm, w.GU,
-                                                                                                   w.J), count_launch(c);
+                                                                                                   w.hp, w.J),
+                    count_launch(c);
             else
-                k_rom_jac_wide<<<dim3((unsigned)d.Nr, (unsigned)B), 128, 0, s>>>(d, B, w.prm, w.GU, w.active, w.J),
+                k_rom_jac_wide<<<dim3((unsigned)d.Nr, (unsigned)B), 128, 0, s>>>(d, B, w.prm, w.GU, w.active, w.hp,
+                                                                                  w.J), count_launch(c);
+            if (hp_any)
+                k_rom_jac64<<<dim3((unsigned)d.Nr, (unsigned)B), 128, 0, s>>>(d, w.prm, w.GU64, w.active, w.hp, w.J64),
                     count_launch(c);
             k_rom_resid<<<(unsigned)B, 128, 0, s>>>(d, w.a, w.a_old, w.prm, w.f, w.active, w.r), count_launch(c);
             if (d.Nr <= ROM_LU4_NR)
-                k_rom_lu4<<<(unsigned)B, LU4_T, (size_t)4 * ((size_t)d.Nr * d.Nr + 4 * d.Nr), s>>>(d.Nr, w.J, w.r,
-                                                                                                   w.active, w.delta),
-                    count_launch(c);
+                k_rom_lu4<float><<<(unsigned)B, LU4_T, (size_t)4 * ((size_t)d.Nr * d.Nr + 4 * d.Nr), s>>>(
+                    d.Nr, w.J, w.r, w.active, w.hp, 0, w.delta), count_launch(c);
             else
-                k_rom_lu<<<(unsigned)B, 256, 0, s>>>(d.Nr, w.J, w.r, w.active, w.delta), count_launch(c);
+                k_rom_lu<float><<<(unsigned)B, 256, 0, s>>>(d.Nr, w.J, w.r, w.active, w.hp, 0, w.delta),
+                    count_launch(c);
+            if (hp_any && d.Nr <= ROM_LU4_NR64)
+                k_rom_lu4<double><<<(unsigned)B, LU4_T, (size_t)8 * ((size_t)d.Nr * d.Nr + 4 * d.Nr), s>>>(
+                    d.Nr, w.J64, w.r, w.active, w.hp, 1, w.delta), count_launch(c);
+            else if (hp_any)
+                k_rom_lu<double><<<(unsigned)B, 256, 0, s>>>(d.Nr, w.J64, w.r, w.active, w.hp, 1, w.delta),
+                    count_launch(c);
             {
                 const unsigned nkt = (unsigned)((d.nloc + UN_K - 1) / UN_K);
                 k_rom_unorm<<<dim3(nkt, (unsigned)((B + UN_B - 1) / UN_B)), 256, 0, s>>>(d, B, w.delta, w.active,
                                                                                          w.dpart), count_launch(c);
                 k_rom_apply<<<(unsigned)B, 32, 0, s>>>(d, (int)nkt, w.a, w.delta, w.dpart, w.active, w.failed,
-                                                       w.its), count_launch(c);
+                                                       w.its, w.pit, w.hp, w.dnprev), count_launch(c);
             }
-            k_rom_count<<<1, 256, 0, s>>>(B, w.active, w.counts), count_launch(c);
-            MB_CUDA(cudaMemcpyAsync(&hcount, w.counts, 4, cudaMemcpyDeviceToHost, s));
+            int hc[2] = {0, 0};
+            k_rom_count_hp<<<1, 256, 0, s>>>(B, w.active, w.hp, w.counts), count_launch(c);
+            MB_CUDA(cudaMemcpyAsync(hc, w.counts, 8, cudaMemcpyDeviceToHost, s));
             MB_CUDA(cudaStreamSynchronize(s));
-            if (hcount == 0) break;
+            w.hp_any = hc[1];
+            if (hc[0] == 0) break;
         }
         // instances still iterating after the iteration limit have failed
         k_rom_fail_active<<<bb, 256, 0, s>>>(B, w.active, w.failed), count_launch(c);

@@ -91,3 +91,39 @@ def test_rom_zero_current_matches_oracle(params, case):
     assert np.max(np.abs(out["V"][0] - ref["V_cell"])) <= 1e-9 * np.max(np.abs(ref["V_cell"]))
     g.close()
     gc.close()
+
+
+@pytest.fixture(scope="module")
+def wide_case(params):
+    """A reduced model with more than 96 modes (the paper's ROMs have 252), so
+    that the GPU takes its paths for large N_r (row-per-block Newton matrix,
+    block LU in global memory): six trajectories of 12 steps on a 5x5x17
+    cell."""
+    lab = syn.full_cell(5, 5, 6, 3, 6, 0.35, 0.35, ("uniform", 1, 2), (1, 2))
+    oc = OCell(lab, 1e-6, params)
+    i1 = oc.i_1c
+    u0 = oc.initial_state()
+    u0[2 * oc.N::4] = 2e-5
+    pts = [(-2 * i1, 1.0, 1.0), (-5 * i1, 0.7, 3.0), (-0.5 * i1, 1.5, 0.3), (-3.5 * i1, 0.5, 8.0),
+           (-1.0 * i1, 2.0, 1.5), (-4.0 * i1, 1.2, 0.1)]
+    snaps, _ = R.snapshots(oc, pts, 1.0, 12, u0=u0)
+    rom = R.build(oc, snaps, (70, 60, 40, 30), pod_tol=1e-12)
+    rom.a0 = rom.U.T @ (R.weights(oc) * u0)
+    return lab, oc, rom
+
+
+@pytest.mark.gpu
+def test_rom_wide_matches_oracle(params, wide_case):
+    B = _gpu()
+    lab, oc, rom = wide_case
+    assert rom.U.shape[1] > 96
+    gc, g = _gpu_rom(B, lab, params, rom)
+    prm = [(c * oc.i_1c, s, k) for (c, s, k) in [(-3.0, 1.1, 0.7), (-1.5, 0.8, 2.0)]]
+    out = g.solve(prm, 3, 1.0)
+    assert out["ok"] and out["failed"] == 0
+    for b, p in enumerate(prm):
+        ref = R.solve(rom, p[0], p[1], p[2], 1.0, 3)
+        assert np.max(np.abs(out["V"][b] - ref["V_cell"])) <= 1e-9 * np.max(np.abs(ref["V_cell"])), b
+        assert np.max(np.abs(out["s_ac"][b] - ref["s_ac"])) <= 1e-9 * np.max(np.abs(ref["s_ac"])), b
+    g.close()
+    gc.close()
