@@ -54,6 +54,22 @@ def workload_labels(name):
 CRATE = {"cell128x128x256": -2.0, "cell16x16x48": -1.0, "cell64x64x128": -2.0}
 
 
+def max_over_ranks(x, dist, device):
+    """The largest x over the ranks of the process group (x without one)."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(ws, steps, dt, ms):
+    """Simulated seconds of all replicas per wall second: every rank advances its
+    own cell by steps * dt in the (slowest rank's) ms."""
+    return ws * steps * dt / (ms / 1000.0)
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     if ws <= 1:
@@ -374,13 +390,10 @@ def main():
     n_sm, ms_sm = cell.prof_read(B.Cell.PROF_SMOOTH)
     n_ls, ms_ls = cell.prof_read(B.Cell.PROF_LSMOOTH)
     cell.prof_enable(False)
+    ms = max_over_ranks(ms, dist, "cuda")
     if dist is not None:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
         dist.barrier()
-    sim_s = args.steps * dt
-    value = ws * sim_s / (ms / 1000.0)
+    value = whole_job_value(ws, args.steps, dt, ms)
 
     # end to end through the C-ABI with host buffers: state uploaded from
     # pinned host memory before and read back after every step
