@@ -334,7 +334,6 @@ k_assemble_l1(ParT<float> P, Dims D, const uint32_t* __restrict__ vc, const floa
     int cz = (int)(cell % L1.nz);
     int cy = (int)((cell / L1.nz) % L1.ny);
     int ct = (int)(cell / ((int64_t)L1.nz * L1.ny));
-    const int64_t N = D.N;
     const float* cc = u;
     const float A = float(P.A);
     const float c0 = float(P.cref[PE]);

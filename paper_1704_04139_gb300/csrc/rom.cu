@@ -94,7 +94,8 @@ struct RomWork {
     double* G64 = nullptr;     // B x M x GMAX   FP64 derivative lists of the hp instances
     double* GU64 = nullptr;    // B x M x Nr     their G U_loc
     double* J64 = nullptr;     // B x Nr x Nr    their Newton matrices
-    int hp_any = 0;            // host: some instance used the FP64 matrix at the last count
+    int* hplist = nullptr;     // B: the instances with hp (compacted at each count; order irrelevant)
+    int hp_any = 0;            // host: number of instances with hp at the last count
     double* prm = nullptr;
     uint8_t *gate = nullptr, *gate2 = nullptr;
     int *active = nullptr, *failed = nullptr, *pass_on = nullptr, *counts = nullptr;
@@ -161,12 +162,15 @@ __global__ void k_rom_gate(RomDev d, int B, const double* __restrict__ uloc, con
 template <bool HP>
 __global__ void k_rom_ei(RomDev d, DevParams P, ParT<float> Pf, int B, const double* __restrict__ uloc,
                          const uint8_t* __restrict__ gate, const double* __restrict__ prm,
-                         const int* __restrict__ active, const int* __restrict__ hp, double* __restrict__ f,
-                         float* __restrict__ G, double* __restrict__ G64) {
+                         const int* __restrict__ active, const int* __restrict__ hp,
+                         const int* __restrict__ hplist, double* __restrict__ f, float* __restrict__ G,
+                         double* __restrict__ G64) {
     using TG = typename std::conditional<HP, double, float>::type;
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= (int64_t)d.M * B) return;
-    const int b = (int)(i / d.M), p = (int)(i % d.M);
+    if (i >= (int64_t)d.M * B) return;   // HP: B = length of hplist
+    int b = (int)(i / d.M);
+    const int p = (int)(i % d.M);
+    if (HP) b = hplist[b];
     if (!active[b] || (hp[b] != 0) != HP) return;
     const double* u = uloc + (int64_t)b * d.nloc;
     const double s_i0 = prm[RP * b + 1], k_pl = prm[RP * b + 2];
@@ -333,8 +337,8 @@ __global__ void k_rom_jac_wide(RomDev d, int B, const double* __restrict__ prm, 
 // (one block per point and instance), then J64[b] = Ms/dt + Alin + P GU64[b]
 // (one block per row and instance)
 __global__ void k_rom_gu64(RomDev d, const double* __restrict__ G, const int* __restrict__ active,
-                           const int* __restrict__ hp, double* __restrict__ GU) {
-    const int p = blockIdx.x, b = blockIdx.y;
+                           const int* __restrict__ hp, const int* __restrict__ hplist, double* __restrict__ GU) {
+    const int p = blockIdx.x, b = hplist[blockIdx.y];
     if (!active[b] || !hp[b]) return;
     const double* Gp = G + ((int64_t)b * d.M + p) * GMAX;
     const int32_t* gi = d.gidx + (int64_t)p * GMAX;
@@ -349,8 +353,9 @@ __global__ void k_rom_gu64(RomDev d, const double* __restrict__ G, const int* __
     }
 }
 __global__ void k_rom_jac64(RomDev d, const double* __restrict__ prm, const double* __restrict__ GU,
-                            const int* __restrict__ active, const int* __restrict__ hp, double* __restrict__ J) {
-    const int i = blockIdx.x, b = blockIdx.y;
+                            const int* __restrict__ active, const int* __restrict__ hp,
+                            const int* __restrict__ hplist, double* __restrict__ J) {
+    const int i = blockIdx.x, b = hplist[blockIdx.y];
     if (!active[b] || !hp[b]) return;
     const double dt_inv = prm[RP * b + 3];
     const double* Pi = d.P + (int64_t)i * d.M;
@@ -393,8 +398,8 @@ k_rom_resid(RomDev d, const double* __restrict__ a, const double* __restrict__ a
 template <class T>
 __global__ void __launch_bounds__(256)
 k_rom_lu(int Nr, T* __restrict__ J, const double* __restrict__ r, const int* __restrict__ active,
-         const int* __restrict__ hp, int want_hp, double* __restrict__ delta) {
-    const int b = blockIdx.x;
+         const int* __restrict__ hp, int want_hp, const int* __restrict__ list, double* __restrict__ delta) {
+    const int b = list ? list[blockIdx.x] : blockIdx.x;
     if (!active[b] || (hp[b] != 0) != (want_hp != 0)) return;
     __shared__ T sh[256];
     __shared__ T rs[ROM_NR_MAX], cs[ROM_NR_MAX], rhs[ROM_NR_MAX], x[ROM_NR_MAX];
@@ -501,8 +506,8 @@ constexpr int LU4_T = 128;
 template <class T>
 __global__ void __launch_bounds__(LU4_T)
 k_rom_lu4(int Nr, T* __restrict__ J, const double* __restrict__ r, const int* __restrict__ active,
-          const int* __restrict__ hp, int want_hp, double* __restrict__ delta) {
-    const int b = blockIdx.x;
+          const int* __restrict__ hp, int want_hp, const int* __restrict__ list, double* __restrict__ delta) {
+    const int b = list ? list[blockIdx.x] : blockIdx.x;
     if (!active[b] || (hp[b] != 0) != (want_hp != 0)) return;
     extern __shared__ __align__(16) unsigned char lu_raw[];
     T* A = reinterpret_cast<T*>(lu_raw);   // Nr x Nr
@@ -682,19 +687,20 @@ k_rom_apply(RomDev d, int nkt, double* __restrict__ a, const double* __restrict_
     }
 }
 
-// out[0] = active instances, out[1] = instances on the FP64 Newton matrix (active or not)
+// out[0] = active instances, out[1] = instances on the FP64 Newton matrix
+// (active or not), listed in list[0, out[1]) (one block; the list's order
+// does not matter: every instance's arithmetic is its own)
 __global__ void k_rom_count_hp(int B, const int* __restrict__ active, const int* __restrict__ hp,
-                               int* __restrict__ out) {
+                               int* __restrict__ out, int* __restrict__ list) {
     __shared__ int c0, c1;
     if (threadIdx.x == 0) { c0 = 0; c1 = 0; }
     __syncthreads();
-    int a = 0, h = 0;
+    int a = 0;
     for (int b = threadIdx.x; b < B; b += blockDim.x) {
         a += active[b] != 0;
-        h += hp[b] != 0;
+        if (hp[b]) list[atomicAdd(&c1, 1)] = b;
     }
     atomicAdd(&c0, a);
-    atomicAdd(&c1, h);
     __syncthreads();
     if (threadIdx.x == 0) { out[0] = c0; out[1] = c1; }
 }
@@ -719,9 +725,10 @@ __global__ void k_rom_set_active(int B, const int* __restrict__ on, const int* _
 }
 
 // flips of pass-active instances; instances with flips stay on for the next pass
-__global__ void k_rom_flips(int ngate, int B, const uint8_t* __restrict__ g1, uint8_t* __restrict__ g2,
+// (g1 and gate may be the same buffer: g1 is read before the barrier, gate written after it)
+__global__ void k_rom_flips(int ngate, int B, const uint8_t* g1, const uint8_t* __restrict__ g2,
                             const int* __restrict__ failed, int* __restrict__ pass_on, long long* __restrict__ flips,
-                            uint8_t* __restrict__ gate, int last_pass) {
+                            uint8_t* gate, int last_pass) {
     const int b = blockIdx.x;
     __shared__ int cnt;
     if (threadIdx.x == 0) cnt = 0;
@@ -1049,6 +1056,7 @@ static int rom_work_alloc(mb_rom* R, int B) {
     w.G = rom_alloc<float>(L, (size_t)B * (d.M ? d.M : 1) * GMAX);
     w.dpart = rom_alloc<float>(L, (size_t)B * ((d.nloc + UN_K - 1) / UN_K));
     w.hp = rom_alloc<int>(L, B);
+    w.hplist = rom_alloc<int>(L, B);
     w.pit = rom_alloc<int>(L, B);
     w.dnprev = rom_alloc<float>(L, B);
     w.G64 = rom_alloc<double>(L, (size_t)B * (d.M ? d.M : 1) * GMAX);
@@ -1157,16 +1165,18 @@ int rom_batch_step(mb_rom* R) {
         for (int it = 0; it < ROM_MAXIT; ++it) {
             // FP64 Newton-matrix kernels only while some instance uses them (hp only turns on
             // within a step, so the count of the previous iteration covers this one)
-            const bool hp_any = w.hp_any > 0;
+            const int nhp = w.hp_any;
+            const bool hp_any = nhp > 0;
             k_rom_gather<<<gg, 256, 0, s>>>(d, w.a, w.uloc), count_launch(c);
             if (d.M) {
-                k_rom_ei<false><<<ge, 128, 0, s>>>(d, c->P, c->Pf, B, w.uloc, w.gate, w.prm, w.active, w.hp, w.f,
-                                                   w.G, w.G64), count_launch(c);
+                k_rom_ei<false><<<ge, 128, 0, s>>>(d, c->P, c->Pf, B, w.uloc, w.gate, w.prm, w.active, w.hp,
+                                                   w.hplist, w.f, w.G, w.G64), count_launch(c);
                 if (hp_any) {
-                    k_rom_ei<true><<<ge, 128, 0, s>>>(d, c->P, c->Pf, B, w.uloc, w.gate, w.prm, w.active, w.hp, w.f,
-                                                      w.G, w.G64), count_launch(c);
-                    k_rom_gu64<<<dim3((unsigned)d.M, (unsigned)B), 64, 0, s>>>(d, w.G64, w.active, w.hp, w.GU64),
+                    k_rom_ei<true><<<(unsigned)(((int64_t)d.M * nhp + 127) / 128), 128, 0, s>>>(
+                        d, c->P, c->Pf, nhp, w.uloc, w.gate, w.prm, w.active, w.hp, w.hplist, w.f, w.G, w.G64),
                         count_launch(c);
+                    k_rom_gu64<<<dim3((unsigned)d.M, (unsigned)nhp), 64, 0, s>>>(d, w.G64, w.active, w.hp, w.hplist,
+                                                                                  w.GU64), count_launch(c);
                 }
                 k_rom_gu<<<(unsigned)(((int64_t)d.M * B * 32 + 255) / 256), 256, 0, s>>>(d, B, w.G, w.active, w.hp,
                                                                                            w.GU), count_launch(c);
@@ -1179,21 +1189,21 @@ int rom_batch_step(mb_rom* R) {
                 k_rom_jac_wide<<<dim3((unsigned)d.Nr, (unsigned)B), 128, 0, s>>>(d, B, w.prm, w.GU, w.active, w.hp,
                                                                                   w.J), count_launch(c);
             if (hp_any)
-                k_rom_jac64<<<dim3((unsigned)d.Nr, (unsigned)B), 128, 0, s>>>(d, w.prm, w.GU64, w.active, w.hp, w.J64),
-                    count_launch(c);
+                k_rom_jac64<<<dim3((unsigned)d.Nr, (unsigned)nhp), 128, 0, s>>>(d, w.prm, w.GU64, w.active, w.hp,
+                                                                                 w.hplist, w.J64), count_launch(c);
             k_rom_resid<<<(unsigned)B, 128, 0, s>>>(d, w.a, w.a_old, w.prm, w.f, w.active, w.r), count_launch(c);
             if (d.Nr <= ROM_LU4_NR)
                 k_rom_lu4<float><<<(unsigned)B, LU4_T, (size_t)4 * ((size_t)d.Nr * d.Nr + 4 * d.Nr), s>>>(
-                    d.Nr, w.J, w.r, w.active, w.hp, 0, w.delta), count_launch(c);
+                    d.Nr, w.J, w.r, w.active, w.hp, 0, nullptr, w.delta), count_launch(c);
             else
-                k_rom_lu<float><<<(unsigned)B, 256, 0, s>>>(d.Nr, w.J, w.r, w.active, w.hp, 0, w.delta),
+                k_rom_lu<float><<<(unsigned)B, 256, 0, s>>>(d.Nr, w.J, w.r, w.active, w.hp, 0, nullptr, w.delta),
                     count_launch(c);
             if (hp_any && d.Nr <= ROM_LU4_NR64)
-                k_rom_lu4<double><<<(unsigned)B, LU4_T, (size_t)8 * ((size_t)d.Nr * d.Nr + 4 * d.Nr), s>>>(
-                    d.Nr, w.J64, w.r, w.active, w.hp, 1, w.delta), count_launch(c);
+                k_rom_lu4<double><<<(unsigned)nhp, LU4_T, (size_t)8 * ((size_t)d.Nr * d.Nr + 4 * d.Nr), s>>>(
+                    d.Nr, w.J64, w.r, w.active, w.hp, 1, w.hplist, w.delta), count_launch(c);
             else if (hp_any)
-                k_rom_lu<double><<<(unsigned)B, 256, 0, s>>>(d.Nr, w.J64, w.r, w.active, w.hp, 1, w.delta),
-                    count_launch(c);
+                k_rom_lu<double><<<(unsigned)nhp, 256, 0, s>>>(d.Nr, w.J64, w.r, w.active, w.hp, 1, w.hplist,
+                                                               w.delta), count_launch(c);
             {
                 const unsigned nkt = (unsigned)((d.nloc + UN_K - 1) / UN_K);
                 k_rom_unorm<<<dim3(nkt, (unsigned)((B + UN_B - 1) / UN_B)), 256, 0, s>>>(d, B, w.delta, w.active,
@@ -1202,7 +1212,7 @@ int rom_batch_step(mb_rom* R) {
                                                        w.its, w.pit, w.hp, w.dnprev), count_launch(c);
             }
             int hc[2] = {0, 0};
-            k_rom_count_hp<<<1, 256, 0, s>>>(B, w.active, w.hp, w.counts), count_launch(c);
+            k_rom_count_hp<<<1, 256, 0, s>>>(B, w.active, w.hp, w.counts, w.hplist), count_launch(c);
             MB_CUDA(cudaMemcpyAsync(hc, w.counts, 8, cudaMemcpyDeviceToHost, s));
             MB_CUDA(cudaStreamSynchronize(s));
             w.hp_any = hc[1];
