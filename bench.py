@@ -197,7 +197,55 @@ def run_reference(args):
 
 
 ROM_CELL = "cell16x16x48"
-ROM_DIMS = (60, 30, 30, 200, 150)     # POD c, plated Li, phi; EI interface, migration
+ROM_DIMS = (60, 30, 30, 200, 150)     # POD c, plated Li, phi; EI interface, migration (serving model)
+ROM_DIMS_PAPER = (183, 40, 69, 952, 1027)   # the paper's 183 c / 69 phi modes, 952 BV / 1027 lambda points
+
+
+def rom_paper_dims(B, params, args, torch):
+    """The reduced model at the paper's dimensions (as far as the 16x16x48
+    cell's snapshots support them): snapshots at four parameter points
+    (C-rate 0.5, 5, 2, 1) over 60 steps, POD to 1e-9; a timed batch of
+    --rom-instances instances over a bounded sample of the 600-step protocol
+    (--rom-paper-steps steps), and the cell-potential error of two instances
+    against full-order runs over that sample."""
+    labels = workload_labels(ROM_CELL)
+    opts = B.default_opts(precision=B.PREC_MIXED, newton_tol=1e-10, krylov_rtol=1e-5, max_halvings=3)
+    cell = B.Cell(labels, 1e-6, params, opts)
+    i1 = cell.i_1c
+    t0 = time.perf_counter()
+    snap = [(-0.5 * i1, 0.5, 0.1), (-5.0 * i1, 2.0, 10.0), (-2.0 * i1, 1.0, 1.0), (-1.0 * i1, 1.0, 1.0)]
+    rom = B.Rom.build(cell, snap, 1.0, 60, ROM_DIMS_PAPER, pod_tol=1e-9)
+    build_s = time.perf_counter() - t0
+    rng = np.random.default_rng(43)
+    prm = _rom_params(rng, args.rom_instances, i1)
+    steps = args.rom_paper_steps
+    rom.solve(prm[:8], 1, 1.0)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    out = rom.solve(prm, steps, 1.0)
+    wall = time.perf_counter() - t0
+    inst_steps = args.rom_instances * steps
+    errs = []
+    for b in range(2):
+        fc = B.Cell(labels, 1e-6, params, opts)
+        fc.set_scales(prm[b][1], prm[b][2])
+        V = np.array([fc.step(1.0, prm[b][0])["V_cell"] for _ in range(steps)])
+        fc.close()
+        errs.append(float(np.max(np.abs(out["V"][b][1:] - V)) / np.max(np.abs(V))))
+    res = {"workload": "ROM of the %s cell at the paper's dimensions, snapshots at (C-rate, i0 scale, k_pl) = "
+                       "(0.5, 0.5, 0.1), (5, 2, 10), (2, 1, 1), (1, 1, 1), 60 steps each; %d of the 600 steps "
+                       "timed" % (ROM_CELL, steps),
+           "dims": {"n_r": rom.n_r, "ei_interface": rom.n_bv, "ei_migration": rom.n_1c,
+                    "requested": list(ROM_DIMS_PAPER)},
+           "instances": args.rom_instances, "steps": steps, "dt_s": 1.0,
+           "precision": "f64 state and residual; float-float reconstruction; f32 Newton matrix and LU with "
+                        "per-instance escalation to f64",
+           "instance_steps_per_s": inst_steps / wall, "solves_per_s": args.rom_instances / wall, "wall_s": wall,
+           "build_s": build_s, "newton_its_per_instance_step": out["newton_its"] / inst_steps,
+           "failed": out["failed"], "V_rel_err_vs_full_order_2_instances": errs}
+    rom.close()
+    cell.close()
+    return res
 
 
 def _rom_params(rng, n, i1):
@@ -210,8 +258,9 @@ def _rom_params(rng, n, i1):
 
 
 def rom_and_serve(B, params, args, torch):
-    """Reduced model built from the 16x16x48 cell (snapshots at three corners
-    of the parameter box over the --rom-steps horizon), a timed batched solve of
+    """A smaller reduced model of the 16x16x48 cell (the serving model;
+    snapshots at three corners of the parameter box over the --rom-steps
+    horizon, POD to 1e-7), a timed batched solve of
     --rom-instances instances over --rom-steps steps, its cell-potential error
     against full-order runs of two instances, and a serving run with Poisson
     arrivals (95 % reduced requests of 20-100 steps, 5 % full-order 10-step
@@ -339,6 +388,8 @@ def main():
     ap.add_argument("--no-rom", action="store_true", help="skip the reduced-model and serving measurements")
     ap.add_argument("--rom-instances", type=int, default=1024)
     ap.add_argument("--rom-steps", type=int, default=60)
+    ap.add_argument("--rom-paper-steps", type=int, default=3,
+                    help="timed steps of the paper-size reduced model (a sample of its 600-step protocol)")
     ap.add_argument("--serve-requests", type=int, default=1000)
     args = ap.parse_args()
     if args.impl == "reference":
@@ -451,9 +502,10 @@ def main():
                       for k, v in kinds.items()}}
 
     cell.close()
-    rom = serve = None
+    rom = rom_small = serve = None
     if rank == 0 and ws == 1 and not args.no_rom:
-        rom, serve = rom_and_serve(B, params, args, torch)
+        rom = rom_paper_dims(B, params, args, torch)
+        rom_small, serve = rom_and_serve(B, params, args, torch)
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -474,7 +526,7 @@ def main():
                "solver": {"newton_its": [i["newton_its"] for i in infos], "krylov_its": [i["krylov_its"] for i in infos],
                           "V_cell": infos[-1]["V_cell"], "precond_ms": ms_pc, "precond_calls": n_pc,
                           "residual_ms": ms_res, "residual_calls": n_res},
-               "rom": rom, "serve": serve}
+               "rom": rom, "rom_small": rom_small, "serve": serve}
         print(json.dumps(out))
     if dist is not None:
         dist.destroy_process_group()

@@ -266,9 +266,9 @@ __global__ void k_rom_gu(RomDev d, int B, const float* __restrict__ G, const int
 
 // Newton matrices of all instances as one FP32 GEMM, C = P [GU_0 | GU_1 | ...]
 // (Nr x M times M x B Nr), plus Ms/dt_b + Alin, written instance-major
-// J[b][i][j].  Tile: all Nr <= 64 rows x 64 columns per block of 256
-// threads, each thread 4 rows x 4 columns in registers, K in chunks of 16
-// staged in shared memory.  Column c = b Nr + j.
+// J[b][i][j].  Tile: 64 rows (blockIdx.y) x 64 columns (blockIdx.x) per block
+// of 256 threads, each thread 4 rows x 4 columns in registers, K in chunks of
+// 16 staged in shared memory.  Column c = b Nr + j.
 constexpr int JT_ROWS = 64, JT_COLS = 64, JT_K = 16;
 __global__ void __launch_bounds__(256)
 k_rom_jac(RomDev d, int B, const double* __restrict__ prm, const float* __restrict__ GU,
@@ -278,6 +278,7 @@ k_rom_jac(RomDev d, int B, const double* __restrict__ prm, const float* __restri
     const int Nr = d.Nr, M = d.M;
     const int64_t ncol = (int64_t)B * Nr;
     const int64_t c0 = (int64_t)blockIdx.x * JT_COLS;
+    const int i0 = blockIdx.y * JT_ROWS;
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
     float acc[4][4];
 #pragma unroll
@@ -287,7 +288,7 @@ k_rom_jac(RomDev d, int B, const double* __restrict__ prm, const float* __restri
     for (int k0 = 0; k0 < M; k0 += JT_K) {
         for (int e = threadIdx.x; e < JT_K * JT_ROWS; e += 256) {
             const int k = e / JT_ROWS, i = e % JT_ROWS;
-            As[k][i] = (i < Nr && k0 + k < M) ? d.Pf[(int64_t)i * M + k0 + k] : 0.f;
+            As[k][i] = (i0 + i < Nr && k0 + k < M) ? d.Pf[(int64_t)(i0 + i) * M + k0 + k] : 0.f;
         }
         for (int e = threadIdx.x; e < JT_K * JT_COLS; e += 256) {
             const int k = e / JT_COLS, q = e % JT_COLS;
@@ -318,7 +319,7 @@ k_rom_jac(RomDev d, int B, const double* __restrict__ prm, const float* __restri
         const float dt_inv = (float)prm[RP * b + 3];
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
-            const int i = ty * 4 + r;
+            const int i = i0 + ty * 4 + r;
             if (i >= Nr) continue;
             J[((int64_t)b * Nr + i) * Nr + j] =
                 acc[r][q] + d.Msf[(int64_t)i * Nr + j] * dt_inv + d.Alinf[(int64_t)i * Nr + j];
@@ -326,20 +327,6 @@ k_rom_jac(RomDev d, int B, const double* __restrict__ prm, const float* __restri
     }
 }
 
-// the same product for Nr > 64: row i of instance b per block
-__global__ void k_rom_jac_wide(RomDev d, int B, const double* __restrict__ prm, const float* __restrict__ GU,
-                               const int* __restrict__ active, const int* __restrict__ hp, float* __restrict__ J) {
-    const int i = blockIdx.x, b = blockIdx.y;
-    if (!active[b] || hp[b]) return;
-    const int Nr = d.Nr;
-    const float dt_inv = (float)prm[RP * b + 3];
-    const float* Pi = d.Pf + (int64_t)i * d.M;
-    for (int j = threadIdx.x; j < Nr; j += blockDim.x) {
-        float acc = 0.f;
-        for (int p = 0; p < d.M; ++p) acc = fmaf(Pi[p], GU[((int64_t)p * B + b) * Nr + j], acc);
-        J[((int64_t)b * Nr + i) * Nr + j] = acc + d.Msf[(int64_t)i * Nr + j] * dt_inv + d.Alinf[(int64_t)i * Nr + j];
-    }
-}
 
 // FP64 Newton matrix of the instances with hp[b]: GU64[b][p][:] = G64[b][p] U_loc
 // (one block per point and instance), then J64[b] = Ms/dt + Alin + P GU64[b]
@@ -504,15 +491,17 @@ k_rom_lu(int Nr, T* __restrict__ J, const double* __restrict__ r, const int* __r
     for (int j = threadIdx.x; j < Nr; j += blockDim.x) delta[(int64_t)b * Nr + j] = (double)(x[j] * cs[j]);
 }
 
-// The same factorisation and solve with four warps per instance, the matrix
-// in shared memory (Nr <= ROM_LU4_NR): per column one warp finds the pivot,
+// The same factorisation and solve with four or eight warps per instance, the
+// matrix in shared memory (lu4_smem(Nr) <= ROM_LU4_SMEM): per column one warp finds the pivot,
 // then all threads swap, form the multipliers and update the trailing block
 // (four barriers per column); warp 0 does the back substitution.
-constexpr int ROM_LU4_NR = 96;    // FP32 (FP64: 64, the shared-memory limit)
-constexpr int ROM_LU4_NR64 = 64;
+// Matrix sizes held in shared memory: up to ROM_LU4_SMEM bytes (opt-in above
+// 48 KB, set at mb_rom_create); 128 threads up to Nr 96, 256 beyond.
+constexpr int ROM_LU4_SMEM = 220 * 1024;
 constexpr int LU4_T = 128;
+__host__ __device__ constexpr size_t lu4_smem(int Nr, size_t elem) { return elem * ((size_t)Nr * Nr + 4 * (size_t)Nr); }
 template <class T>
-__global__ void __launch_bounds__(LU4_T)
+__global__ void __launch_bounds__(256)
 k_rom_lu4(int Nr, T* __restrict__ J, const double* __restrict__ r, const int* __restrict__ active,
           const int* __restrict__ hp, int want_hp, const int* __restrict__ list, double* __restrict__ delta) {
     const int b = list ? list[blockIdx.x] : blockIdx.x;
@@ -526,22 +515,22 @@ k_rom_lu4(int Nr, T* __restrict__ J, const double* __restrict__ r, const int* __
     __shared__ int spiv;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const T* Jb = J + (int64_t)b * Nr * Nr;
-    for (int e = tid; e < Nr * Nr; e += LU4_T) A[e] = Jb[e];
+    for (int e = tid; e < Nr * Nr; e += blockDim.x) A[e] = Jb[e];
     __syncthreads();
-    for (int i = tid; i < Nr; i += LU4_T) {
+    for (int i = tid; i < Nr; i += blockDim.x) {
         T m = T(0);
         for (int j = 0; j < Nr; ++j) m = fmax(m, fabs(A[i * Nr + j]));
         rs[i] = m > T(0) ? T(1) / m : T(1);
     }
     __syncthreads();
-    for (int j = tid; j < Nr; j += LU4_T) {
+    for (int j = tid; j < Nr; j += blockDim.x) {
         T m = T(0);
         for (int i = 0; i < Nr; ++i) m = fmax(m, fabs(A[i * Nr + j] * rs[i]));
         cs[j] = m > T(0) ? T(1) / m : T(1);
     }
     __syncthreads();
-    for (int e = tid; e < Nr * Nr; e += LU4_T) A[e] *= rs[e / Nr] * cs[e % Nr];
-    for (int i = tid; i < Nr; i += LU4_T) rhs[i] = (T)(-r[(int64_t)b * Nr + i]) * rs[i];
+    for (int e = tid; e < Nr * Nr; e += blockDim.x) A[e] *= rs[e / Nr] * cs[e % Nr];
+    for (int i = tid; i < Nr; i += blockDim.x) rhs[i] = (T)(-r[(int64_t)b * Nr + i]) * rs[i];
     __syncthreads();
     for (int k = 0; k < Nr; ++k) {
         if (wid == 0) {
@@ -561,7 +550,7 @@ k_rom_lu4(int Nr, T* __restrict__ J, const double* __restrict__ r, const int* __
         __syncthreads();
         const int piv = spiv;
         if (piv != k) {
-            for (int j = tid; j < Nr; j += LU4_T) {
+            for (int j = tid; j < Nr; j += blockDim.x) {
                 const T t = A[k * Nr + j];
                 A[k * Nr + j] = A[piv * Nr + j];
                 A[piv * Nr + j] = t;
@@ -575,14 +564,14 @@ k_rom_lu4(int Nr, T* __restrict__ J, const double* __restrict__ r, const int* __
         __syncthreads();
         const T akk = A[k * Nr + k];
         const T inv = akk != T(0) ? T(1) / akk : T(0);
-        for (int i = k + 1 + tid; i < Nr; i += LU4_T) {
+        for (int i = k + 1 + tid; i < Nr; i += blockDim.x) {
             const T l = A[i * Nr + k] * inv;
             A[i * Nr + k] = l;
             rhs[i] -= l * rhs[k];
         }
         __syncthreads();
         const int m = Nr - k - 1;
-        for (int e = tid; e < m * m; e += LU4_T) {
+        for (int e = tid; e < m * m; e += blockDim.x) {
             const int i = k + 1 + e / m, j = k + 1 + e % m;
             A[i * Nr + j] -= A[i * Nr + k] * A[k * Nr + j];
         }
@@ -601,7 +590,7 @@ k_rom_lu4(int Nr, T* __restrict__ J, const double* __restrict__ r, const int* __
         }
     }
     __syncthreads();
-    for (int j = tid; j < Nr; j += LU4_T) delta[(int64_t)b * Nr + j] = (double)(x[j] * cs[j]);
+    for (int j = tid; j < Nr; j += blockDim.x) delta[(int64_t)b * Nr + j] = (double)(x[j] * cs[j]);
 }
 
 // Step length of all instances: the scaled max-norm of the reconstructed
@@ -1050,6 +1039,12 @@ static int rom_build_host(mb_rom* R, const mb_rom_data* dd) {
         ok = upf(d.Pf, P.data(), P.size()) && upf(d.Msf, dd->Ms, (size_t)Nr * Nr) &&
              upf(d.Alinf, dd->Alin, (size_t)Nr * Nr) && upf(d.UlocRf, UlocR.data(), UlocR.size()) &&
              upf(d.UlocCf, UlocC.data(), UlocC.size()) && upf(d.usf, us.data(), us.size());
+    // shared memory of the LU kernels beyond the default 48 KB
+    if (ok)
+        ok = cudaFuncSetAttribute(k_rom_lu4<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, ROM_LU4_SMEM) ==
+                 cudaSuccess &&
+             cudaFuncSetAttribute(k_rom_lu4<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, ROM_LU4_SMEM) ==
+                 cudaSuccess;
     if (!ok) return cuda_fail(cudaGetLastError(), "rom upload");
     return MB_OK;
 }
@@ -1196,29 +1191,29 @@ int rom_batch_step(mb_rom* R) {
                 k_rom_gu<<<(unsigned)(((int64_t)d.M * B * 32 + 255) / 256), 256, 0, s>>>(d, B, w.G, w.active, w.hp,
                                                                                            w.GU), count_launch(c);
             }
-            if (d.Nr <= JT_ROWS)
-                k_rom_jac<<<(unsigned)(((int64_t)B * d.Nr + JT_COLS - 1) / JT_COLS), 256, 0, s>>>(d, B, w.prm, w.GU,
-                                                                                                   w.hp, w.J),
-                    count_launch(c);
-            else
-                k_rom_jac_wide<<<dim3((unsigned)d.Nr, (unsigned)B), 128, 0, s>>>(d, B, w.prm, w.GU, w.active, w.hp,
-                                                                                  w.J), count_launch(c);
+            k_rom_jac<<<dim3((unsigned)(((int64_t)B * d.Nr + JT_COLS - 1) / JT_COLS),
+                             (unsigned)((d.Nr + JT_ROWS - 1) / JT_ROWS)),
+                        256, 0, s>>>(d, B, w.prm, w.GU, w.hp, w.J), count_launch(c);
             if (hp_any)
                 k_rom_jac64<<<dim3((unsigned)d.Nr, (unsigned)nhp), 128, 0, s>>>(d, w.prm, w.GU64, w.active, w.hp,
                                                                                  w.hplist, w.J64), count_launch(c);
             k_rom_resid<<<(unsigned)B, 128, 0, s>>>(d, w.a, w.a_old, w.prm, w.f, w.active, w.r), count_launch(c);
-            if (d.Nr <= ROM_LU4_NR)
-                k_rom_lu4<float><<<(unsigned)B, LU4_T, (size_t)4 * ((size_t)d.Nr * d.Nr + 4 * d.Nr), s>>>(
-                    d.Nr, w.J, w.r, w.active, w.hp, 0, nullptr, w.delta), count_launch(c);
-            else
-                k_rom_lu<float><<<(unsigned)B, 256, 0, s>>>(d.Nr, w.J, w.r, w.active, w.hp, 0, nullptr, w.delta),
-                    count_launch(c);
-            if (hp_any && d.Nr <= ROM_LU4_NR64)
-                k_rom_lu4<double><<<(unsigned)nhp, LU4_T, (size_t)8 * ((size_t)d.Nr * d.Nr + 4 * d.Nr), s>>>(
-                    d.Nr, w.J64, w.r, w.active, w.hp, 1, w.hplist, w.delta), count_launch(c);
-            else if (hp_any)
-                k_rom_lu<double><<<(unsigned)nhp, 256, 0, s>>>(d.Nr, w.J64, w.r, w.active, w.hp, 1, w.hplist,
-                                                               w.delta), count_launch(c);
+            {
+                const unsigned lt = d.Nr <= 96 ? LU4_T : 256;
+                if (lu4_smem(d.Nr, 4) <= ROM_LU4_SMEM)
+                    k_rom_lu4<float><<<(unsigned)B, lt, lu4_smem(d.Nr, 4), s>>>(d.Nr, w.J, w.r, w.active, w.hp, 0,
+                                                                                 nullptr, w.delta), count_launch(c);
+                else
+                    k_rom_lu<float><<<(unsigned)B, 256, 0, s>>>(d.Nr, w.J, w.r, w.active, w.hp, 0, nullptr, w.delta),
+                        count_launch(c);
+                if (hp_any && lu4_smem(d.Nr, 8) <= ROM_LU4_SMEM)
+                    k_rom_lu4<double><<<(unsigned)nhp, lt, lu4_smem(d.Nr, 8), s>>>(d.Nr, w.J64, w.r, w.active, w.hp,
+                                                                                    1, w.hplist, w.delta),
+                        count_launch(c);
+                else if (hp_any)
+                    k_rom_lu<double><<<(unsigned)nhp, 256, 0, s>>>(d.Nr, w.J64, w.r, w.active, w.hp, 1, w.hplist,
+                                                                   w.delta), count_launch(c);
+            }
             {
                 const unsigned nkt = (unsigned)((d.nloc + UN_K - 1) / UN_K);
                 k_rom_unorm<<<dim3(nkt, (unsigned)((B + UN_B - 1) / UN_B)), 256, 0, s>>>(d, B, w.delta, w.active,
