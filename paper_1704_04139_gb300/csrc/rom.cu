@@ -95,6 +95,8 @@ struct RomWork {
     double* GU64 = nullptr;    // B x M x Nr     their G U_loc
     double* J64 = nullptr;     // B x Nr x Nr    their Newton matrices
     int* hplist = nullptr;     // B: the instances with hp (compacted at each count; order irrelevant)
+    int* alist = nullptr;      // B: the active instances on the FP32 matrix (compacted at each count)
+    int n_alist = -1;          // host: its length at the last count (-1: not counted yet: all B)
     int hp_any = 0;            // host: number of instances with hp at the last count
     double* prm = nullptr;
     uint8_t *gate = nullptr, *gate2 = nullptr;
@@ -133,9 +135,11 @@ static T* rom_alloc(std::vector<void*>& list, size_t n) {
 // u_loc[b] = U_loc a[b] in float-float arithmetic (products by FMA
 // TwoProduct, sums by TwoSum: ~2^-46 of the terms' magnitudes, a few times
 // faster than FP64 on GB300), stored as FP64
-__global__ void k_rom_gather(RomDev d, const double* __restrict__ a, double* __restrict__ uloc) {
+__global__ void k_rom_gather(RomDev d, const double* __restrict__ a, double* __restrict__ uloc,
+                             const int* __restrict__ active) {
     __shared__ float2 sa[ROM_NR_MAX];
     const int b = blockIdx.y;
+    if (active && !active[b]) return;   // a converged instance keeps its reconstruction
     for (int j = threadIdx.x; j < d.Nr; j += blockDim.x) sa[j] = df_from_double(a[(int64_t)b * d.Nr + j]);
     __syncthreads();
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
@@ -271,12 +275,14 @@ __global__ void k_rom_gu(RomDev d, int B, const float* __restrict__ G, const int
 // 16 staged in shared memory.  Column c = b Nr + j.
 constexpr int JT_ROWS = 64, JT_COLS = 64, JT_K = 16;
 __global__ void __launch_bounds__(256)
-k_rom_jac(RomDev d, int B, const double* __restrict__ prm, const float* __restrict__ GU,
-          const int* __restrict__ hp, float* __restrict__ J) {
+k_rom_jac(RomDev d, int B, int nlist, const int* __restrict__ alist, const double* __restrict__ prm,
+          const float* __restrict__ GU, const int* __restrict__ hp, float* __restrict__ J) {
     __shared__ float As[JT_K][JT_ROWS];
     __shared__ float Bs[JT_K][JT_COLS];
     const int Nr = d.Nr, M = d.M;
-    const int64_t ncol = (int64_t)B * Nr;
+    // columns c = l Nr + j of the listed instances b = alist[l] (all B in order without a list)
+    const int64_t ncol = (int64_t)(alist ? nlist : B) * Nr;
+    const int64_t gstride = (int64_t)B * Nr;   // row stride of GU
     const int64_t c0 = (int64_t)blockIdx.x * JT_COLS;
     const int i0 = blockIdx.y * JT_ROWS;
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
@@ -293,7 +299,13 @@ k_rom_jac(RomDev d, int B, const double* __restrict__ prm, const float* __restri
         for (int e = threadIdx.x; e < JT_K * JT_COLS; e += 256) {
             const int k = e / JT_COLS, q = e % JT_COLS;
             const int64_t c = c0 + q;
-            Bs[k][q] = (c < ncol && k0 + k < M) ? GU[(int64_t)(k0 + k) * ncol + c] : 0.f;
+            float v = 0.f;
+            if (c < ncol && k0 + k < M) {
+                const int64_t l = c / Nr;
+                const int64_t b = alist ? alist[l] : l;
+                v = GU[(int64_t)(k0 + k) * gstride + b * Nr + (c - l * Nr)];
+            }
+            Bs[k][q] = v;
         }
         __syncthreads();
 #pragma unroll
@@ -314,7 +326,8 @@ k_rom_jac(RomDev d, int B, const double* __restrict__ prm, const float* __restri
     for (int q = 0; q < 4; ++q) {
         const int64_t c = c0 + tx * 4 + q;
         if (c >= ncol) continue;
-        const int b = (int)(c / Nr), j = (int)(c % Nr);
+        const int l = (int)(c / Nr), j = (int)(c % Nr);
+        const int b = alist ? alist[l] : l;
         if (hp[b]) continue;   // its Newton matrix is the FP64 one
         const float dt_inv = (float)prm[RP * b + 3];
 #pragma unroll
@@ -687,19 +700,21 @@ k_rom_apply(RomDev d, int nkt, double* __restrict__ a, const double* __restrict_
 // out[0] = active instances, out[1] = instances on the FP64 Newton matrix
 // (active or not), listed in list[0, out[1]) (one block; the list's order
 // does not matter: every instance's arithmetic is its own)
+// out[2] = active instances on the FP32 matrix, listed in alist[0, out[2])
 __global__ void k_rom_count_hp(int B, const int* __restrict__ active, const int* __restrict__ hp,
-                               int* __restrict__ out, int* __restrict__ list) {
-    __shared__ int c0, c1;
-    if (threadIdx.x == 0) { c0 = 0; c1 = 0; }
+                               int* __restrict__ out, int* __restrict__ list, int* __restrict__ alist) {
+    __shared__ int c0, c1, c2;
+    if (threadIdx.x == 0) { c0 = 0; c1 = 0; c2 = 0; }
     __syncthreads();
     int a = 0;
     for (int b = threadIdx.x; b < B; b += blockDim.x) {
         a += active[b] != 0;
         if (hp[b]) list[atomicAdd(&c1, 1)] = b;
+        else if (active[b]) alist[atomicAdd(&c2, 1)] = b;
     }
     atomicAdd(&c0, a);
     __syncthreads();
-    if (threadIdx.x == 0) { out[0] = c0; out[1] = c1; }
+    if (threadIdx.x == 0) { out[0] = c0; out[1] = c1; out[2] = c2; }
 }
 
 // copy src -> dst for instances with mask[b] (all instances if mask is null)
@@ -1067,6 +1082,7 @@ static int rom_work_alloc(mb_rom* R, int B) {
     w.dpart = rom_alloc<float>(L, (size_t)B * ((d.nloc + UN_K - 1) / UN_K));
     w.hp = rom_alloc<int>(L, B);
     w.hplist = rom_alloc<int>(L, B);
+    w.alist = rom_alloc<int>(L, B);
     w.pit = rom_alloc<int>(L, B);
     w.dnprev = rom_alloc<float>(L, B);
     w.G64 = rom_alloc<double>(L, (size_t)B * (d.M ? d.M : 1) * GMAX);
@@ -1165,7 +1181,7 @@ int rom_batch_step(mb_rom* R) {
     const unsigned gt = (unsigned)(((int64_t)(d.ngate ? d.ngate : 1) * B + 255) / 256);
     int hcount = 0;
     k_rom_copy<<<nb, 256, 0, s>>>(d.Nr, B, nullptr, w.a, w.a_old), count_launch(c);
-    k_rom_gather<<<gg, 256, 0, s>>>(d, w.a_old, w.uloc_old), count_launch(c);
+    k_rom_gather<<<gg, 256, 0, s>>>(d, w.a_old, w.uloc_old, nullptr), count_launch(c);
     if (d.ngate) k_rom_gate<<<gt, 256, 0, s>>>(d, B, w.uloc_old, w.uloc_old, n_thr, w.gate), count_launch(c);
     k_rom_set_active<<<bb, 256, 0, s>>>(B, nullptr, w.failed, w.pass_on, nullptr, w.hp), count_launch(c);
     w.hp_any = 0;
@@ -1177,7 +1193,7 @@ int rom_batch_step(mb_rom* R) {
             // within a step, so the count of the previous iteration covers this one)
             const int nhp = w.hp_any;
             const bool hp_any = nhp > 0;
-            k_rom_gather<<<gg, 256, 0, s>>>(d, w.a, w.uloc), count_launch(c);
+            k_rom_gather<<<gg, 256, 0, s>>>(d, w.a, w.uloc, w.active), count_launch(c);
             if (d.M) {
                 k_rom_ei<false><<<ge, 128, 0, s>>>(d, c->P, c->Pf, B, w.uloc, w.gate, w.prm, w.active, w.hp,
                                                    w.hplist, w.f, w.G, w.G64), count_launch(c);
@@ -1191,9 +1207,16 @@ int rom_batch_step(mb_rom* R) {
                 k_rom_gu<<<(unsigned)(((int64_t)d.M * B * 32 + 255) / 256), 256, 0, s>>>(d, B, w.G, w.active, w.hp,
                                                                                            w.GU), count_launch(c);
             }
-            k_rom_jac<<<dim3((unsigned)(((int64_t)B * d.Nr + JT_COLS - 1) / JT_COLS),
-                             (unsigned)((d.Nr + JT_ROWS - 1) / JT_ROWS)),
-                        256, 0, s>>>(d, B, w.prm, w.GU, w.hp, w.J), count_launch(c);
+            {
+                // the first iteration of a pass: every instance; later: the listed active FP32 ones
+                const bool listed = it > 0 && w.n_alist >= 0;
+                const int ncols = listed ? w.n_alist : B;
+                if (ncols > 0)
+                    k_rom_jac<<<dim3((unsigned)(((int64_t)ncols * d.Nr + JT_COLS - 1) / JT_COLS),
+                                     (unsigned)((d.Nr + JT_ROWS - 1) / JT_ROWS)),
+                                256, 0, s>>>(d, B, ncols, listed ? w.alist : nullptr, w.prm, w.GU, w.hp, w.J),
+                        count_launch(c);
+            }
             if (hp_any)
                 k_rom_jac64<<<dim3((unsigned)d.Nr, (unsigned)nhp), 128, 0, s>>>(d, w.prm, w.GU64, w.active, w.hp,
                                                                                  w.hplist, w.J64), count_launch(c);
@@ -1221,17 +1244,18 @@ int rom_batch_step(mb_rom* R) {
                 k_rom_apply<<<(unsigned)B, 32, 0, s>>>(d, (int)nkt, w.a, w.delta, w.dpart, w.active, w.failed,
                                                        w.its, w.pit, w.hp, w.dnprev), count_launch(c);
             }
-            int hc[2] = {0, 0};
-            k_rom_count_hp<<<1, 256, 0, s>>>(B, w.active, w.hp, w.counts, w.hplist), count_launch(c);
-            MB_CUDA(cudaMemcpyAsync(hc, w.counts, 8, cudaMemcpyDeviceToHost, s));
+            int hc[3] = {0, 0, 0};
+            k_rom_count_hp<<<1, 256, 0, s>>>(B, w.active, w.hp, w.counts, w.hplist, w.alist), count_launch(c);
+            MB_CUDA(cudaMemcpyAsync(hc, w.counts, 12, cudaMemcpyDeviceToHost, s));
             MB_CUDA(cudaStreamSynchronize(s));
             w.hp_any = hc[1];
+            w.n_alist = hc[2];
             if (hc[0] == 0) break;
         }
         // instances still iterating after the iteration limit have failed
         k_rom_fail_active<<<bb, 256, 0, s>>>(B, w.active, w.failed), count_launch(c);
         if (!d.ngate) break;
-        k_rom_gather<<<gg, 256, 0, s>>>(d, w.a, w.uloc), count_launch(c);
+        k_rom_gather<<<gg, 256, 0, s>>>(d, w.a, w.uloc, nullptr), count_launch(c);
         k_rom_gate<<<gt, 256, 0, s>>>(d, B, w.uloc, w.uloc_old, n_thr, w.gate2), count_launch(c);
         k_rom_flips<<<(unsigned)B, 256, 0, s>>>(d.ngate, B, w.gate, w.gate2, w.failed, w.pass_on, w.flips, w.gate,
                                                pass == ROM_PASSES ? 1 : 0), count_launch(c);
