@@ -44,6 +44,20 @@ int mb_debug_fine(mb_cell* cell, float* dinv, float* fc, float* rowdiag);
  * col = 0 c, 1 phi; 14 x N x 2 floats. */
 int mb_debug_fine_stencil(mb_cell* cell, float* out);
 
+/* The reduced model's Newton-matrix kernel on given arrays: J[b] = P GU_b +
+ * Ms dt_inv[b] + Alin for b < B (P Nr x M row-major, GU M x (B Nr) row-major
+ * with column b Nr + j, Ms and Alin Nr x Nr, J B x Nr x Nr); tc = 1 the
+ * tensor-core (3xTF32) kernel, 0 FP32 FMA. */
+int mb_debug_rom_jac(int Nr, int M, int B, const float* P, const float* GU, const float* Ms, const float* Alin,
+                     const double* dt_inv, int tc, float* J);
+/* The reduced model's Newton-step LU kernel on given matrices: delta[b] =
+ * -J[b]^-1 r[b] for b < B (J B x Nr x Nr row-major, r and delta B x Nr), in
+ * FP64 (fp64 = 1) or FP32 arithmetic, the matrix in shared memory (in_place =
+ * 0; MB_EINVAL when it does not fit) or factorised in place in device memory. */
+int mb_debug_rom_lu(int Nr, int B, int fp64, int in_place, const double* J, const double* r, double* delta);
+/* Use (on = 1, the default) or not the tensor-core Newton-matrix kernel in the online solve. */
+int mb_debug_rom_tensor(mb_rom* rom, int on);
+
 /* The solver's own Newton residual (interface currents evaluated once per
  * face, then the voxel rows) at u, u_old with gates gate (uint8[F]); the
  * result equals mb_residual's up to the rounding of the summation order.

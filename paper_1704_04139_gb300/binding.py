@@ -148,6 +148,9 @@ def _declare(lib):
     fn("mb_debug_level_op", C.c_int, [VP, C.c_int, VP, VP, VP])
     fn("mb_debug_fine", C.c_int, [VP, VP, VP, VP])
     fn("mb_debug_fine_stencil", C.c_int, [VP, VP])
+    fn("mb_debug_rom_jac", C.c_int, [C.c_int, C.c_int, C.c_int, VP, VP, VP, VP, VP, C.c_int, VP])
+    fn("mb_debug_rom_tensor", C.c_int, [VP, C.c_int])
+    fn("mb_debug_rom_lu", C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, VP, VP, VP])
     fn("mb_debug_residual_split", C.c_int, [VP, VP, VP, VP, C.c_double, C.c_double, VP])
     return lib
 
@@ -416,6 +419,10 @@ class Rom:
         out["ok"] = rc == 0
         return out
 
+    def debug_tensor(self, on):
+        """Newton-matrix GEMM on the tensor cores (3xTF32, the default) or FP32 FMA."""
+        _check(lib().mb_debug_rom_tensor(self.h, 1 if on else 0))
+
     def close(self):
         if getattr(self, "h", None):
             lib().mb_rom_destroy(self.h)
@@ -488,3 +495,30 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+def debug_rom_jac(P, GU, Ms, Alin, dt_inv, tc=True):
+    """The reduced model's Newton-matrix kernel on given arrays: J[b] = P GU[b] +
+    Ms dt_inv[b] + Alin (GU shape (B, M, Nr)); tc selects the tensor-core kernel."""
+    P = np.ascontiguousarray(P, dtype=np.float32)
+    Nr, M = P.shape
+    B = len(dt_inv)
+    gu = np.ascontiguousarray(np.transpose(np.asarray(GU, dtype=np.float32), (1, 0, 2)).reshape(M, B * Nr))
+    ms = np.ascontiguousarray(Ms, dtype=np.float32)
+    al = np.ascontiguousarray(Alin, dtype=np.float32)
+    dti = np.ascontiguousarray(dt_inv, dtype=np.float64)
+    J = np.empty((B, Nr, Nr), dtype=np.float32)
+    _check(lib().mb_debug_rom_jac(Nr, M, B, _ptr(P), _ptr(gu), _ptr(ms), _ptr(al), _ptr(dti), 1 if tc else 0,
+                                  _ptr(J)))
+    return J
+
+
+def debug_rom_lu(J, r, fp64=True, in_place=False):
+    """The reduced model's Newton-step LU kernel: delta[b] = -J[b]^-1 r[b] (J shape (B, Nr, Nr))."""
+    J = np.ascontiguousarray(J, dtype=np.float64)
+    r = np.ascontiguousarray(r, dtype=np.float64)
+    B, Nr = r.shape
+    delta = np.empty((B, Nr))
+    _check(lib().mb_debug_rom_lu(Nr, B, 1 if fp64 else 0, 1 if in_place else 0, _ptr(J), _ptr(r), _ptr(delta)))
+    return delta
+

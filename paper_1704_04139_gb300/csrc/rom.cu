@@ -54,6 +54,7 @@ enum RomTerm : int8_t { T_NONE = 0, T_GE = 1, T_KE = 2, T_LE = 3, T_EE = 4 };
 
 struct RomDev {
     int Nr = 0, Mbv = 0, M1c = 0, M = 0, nloc = 0, ngate = 0;
+    int tc = 1;                // Newton-matrix GEMM on the tensor cores (3xTF32), else FP32 FMA
     double* UlocR = nullptr;   // nloc x Nr
     double* us = nullptr;      // nloc unknown scales
     int8_t* ttype = nullptr;   // M x TMAX
@@ -67,7 +68,7 @@ struct RomDev {
     double* P = nullptr;       // Nr x M (Pbv | P1c)
     double* Ms = nullptr;      // Nr x Nr
     double* Alin = nullptr;    // Nr x Nr
-    float* Pf = nullptr;       // FP32 copies for the Newton matrix: P, Ms, Alin, UlocR, UlocC, us
+    float* Ptf = nullptr;      // FP32 copies for the Newton matrix: P^T (M x Nr), Ms, Alin, UlocR, UlocC, us
     float* Msf = nullptr;
     float* Alinf = nullptr;
     float* UlocRf = nullptr;
@@ -273,71 +274,147 @@ __global__ void k_rom_gu(RomDev d, int B, const float* __restrict__ G, const int
 // J[b][i][j].  Tile: 64 rows (blockIdx.y) x 64 columns (blockIdx.x) per block
 // of 256 threads, each thread 4 rows x 4 columns in registers, K in chunks of
 // 16 staged in shared memory.  Column c = b Nr + j.
-constexpr int JT_ROWS = 64, JT_COLS = 64, JT_K = 16;
+constexpr int JT_ROWS = 64, JT_COLS = 64, JT_K = 32, JT_PAD = 8;
+
+// TF32 tensor-core pieces (mma.sync m16n8k8, FP32 accumulation).  A value
+// is split as big + small, both TF32 (big rounded to nearest, small the
+// rounded remainder), and a product as big*big + big*small + small*big,
+// which keeps about FP32 accuracy (the dropped small*small term is ~2^-22 of
+// the product).
+__device__ inline uint32_t to_tf32(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return r;
+}
+__device__ inline void tf32_split(float x, uint32_t& big, uint32_t& small) {
+    big = to_tf32(x);
+    small = to_tf32(x - __uint_as_float(big));
+}
+__device__ inline void mma_tf32(float (&c)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+template <bool TC>
 __global__ void __launch_bounds__(256)
 k_rom_jac(RomDev d, int B, int nlist, const int* __restrict__ alist, const double* __restrict__ prm,
           const float* __restrict__ GU, const int* __restrict__ hp, float* __restrict__ J) {
-    __shared__ float As[JT_K][JT_ROWS];
-    __shared__ float Bs[JT_K][JT_COLS];
+    __shared__ float As[JT_K][JT_ROWS + JT_PAD];
+    __shared__ float Bs[JT_K][JT_COLS + JT_PAD];
     const int Nr = d.Nr, M = d.M;
     // columns c = l Nr + j of the listed instances b = alist[l] (all B in order without a list)
-    const int64_t ncol = (int64_t)(alist ? nlist : B) * Nr;
+    const int ncol = (alist ? nlist : B) * Nr;
     const int64_t gstride = (int64_t)B * Nr;   // row stride of GU
-    const int64_t c0 = (int64_t)blockIdx.x * JT_COLS;
+    const int c0 = blockIdx.x * JT_COLS;
     const int i0 = blockIdx.y * JT_ROWS;
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    // loader: this thread fills column lq of both tiles at K rows kq + 4 m; the row of P^T
+    // and the column of GU it reads are fixed over the K loop
+    constexpr int LK = JT_K / 4;
+    const int lq = threadIdx.x & 63, kq = threadIdx.x >> 6;
+    const bool arow = i0 + lq < Nr, bcol = c0 + lq < ncol;
+    int64_t boff = 0;
+    if (bcol) {
+        const int l = (c0 + lq) / Nr;
+        boff = (int64_t)(alist ? alist[l] : l) * Nr + (c0 + lq - l * Nr);
+    }
+    float ra[LK], rb[LK];
+    auto fetch = [&](int k0) {
+#pragma unroll
+        for (int m = 0; m < LK; ++m) {
+            const int k = k0 + kq + 4 * m;
+            ra[m] = (arow && k < M) ? d.Ptf[(int64_t)k * Nr + i0 + lq] : 0.f;
+            rb[m] = (bcol && k < M) ? GU[(int64_t)k * gstride + boff] : 0.f;
+        }
+    };
     float acc[4][4];
 #pragma unroll
     for (int r = 0; r < 4; ++r)
 #pragma unroll
-        for (int q = 0; q < 4; ++q) acc[r][q] = 0.f;
+        for (int c = 0; c < 4; ++c) acc[r][c] = 0.f;
+    fetch(0);
     for (int k0 = 0; k0 < M; k0 += JT_K) {
-        for (int e = threadIdx.x; e < JT_K * JT_ROWS; e += 256) {
-            const int k = e / JT_ROWS, i = e % JT_ROWS;
-            As[k][i] = (i0 + i < Nr && k0 + k < M) ? d.Pf[(int64_t)(i0 + i) * M + k0 + k] : 0.f;
-        }
-        for (int e = threadIdx.x; e < JT_K * JT_COLS; e += 256) {
-            const int k = e / JT_COLS, q = e % JT_COLS;
-            const int64_t c = c0 + q;
-            float v = 0.f;
-            if (c < ncol && k0 + k < M) {
-                const int64_t l = c / Nr;
-                const int64_t b = alist ? alist[l] : l;
-                v = GU[(int64_t)(k0 + k) * gstride + b * Nr + (c - l * Nr)];
-            }
-            Bs[k][q] = v;
+#pragma unroll
+        for (int m = 0; m < LK; ++m) {
+            As[kq + 4 * m][lq] = ra[m];
+            Bs[kq + 4 * m][lq] = rb[m];
         }
         __syncthreads();
+        if (k0 + JT_K < M) fetch(k0 + JT_K);   // next slice in flight during this one's products
+        if (TC) {
+            // warp (wr, wc) owns rows wr*32 + [0,32), columns wc*16 + [0,16): 2 x 2 tiles of 16 x 8
+            const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+            const int wr = wid >> 2, wc = wid & 3;
 #pragma unroll
-        for (int k = 0; k < JT_K; ++k) {
-            float a[4], bq[4];
+            for (int ks = 0; ks < JT_K; ks += 8) {
+                uint32_t ab[2][4], as_[2][4], bb[2][2], bs_[2][2];
 #pragma unroll
-            for (int r = 0; r < 4; ++r) a[r] = As[k][ty * 4 + r];
+                for (int mi = 0; mi < 2; ++mi) {
+                    const int rb = wr * 32 + mi * 16;
+                    tf32_split(As[ks + t][rb + g], ab[mi][0], as_[mi][0]);
+                    tf32_split(As[ks + t][rb + g + 8], ab[mi][1], as_[mi][1]);
+                    tf32_split(As[ks + t + 4][rb + g], ab[mi][2], as_[mi][2]);
+                    tf32_split(As[ks + t + 4][rb + g + 8], ab[mi][3], as_[mi][3]);
+                }
 #pragma unroll
-            for (int q = 0; q < 4; ++q) bq[q] = Bs[k][tx * 4 + q];
+                for (int ni = 0; ni < 2; ++ni) {
+                    const int cb = wc * 16 + ni * 8;
+                    tf32_split(Bs[ks + t][cb + g], bb[ni][0], bs_[ni][0]);
+                    tf32_split(Bs[ks + t + 4][cb + g], bb[ni][1], bs_[ni][1]);
+                }
 #pragma unroll
-            for (int r = 0; r < 4; ++r)
+                for (int mi = 0; mi < 2; ++mi)
 #pragma unroll
-                for (int q = 0; q < 4; ++q) acc[r][q] = fmaf(a[r], bq[q], acc[r][q]);
+                    for (int ni = 0; ni < 2; ++ni) {
+                        float(&cc)[4] = acc[mi * 2 + ni];
+                        mma_tf32(cc, as_[mi], bb[ni]);
+                        mma_tf32(cc, ab[mi], bs_[ni]);
+                        mma_tf32(cc, ab[mi], bb[ni]);
+                    }
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < JT_K; ++k) {
+                float a[4], bq[4];
+#pragma unroll
+                for (int r = 0; r < 4; ++r) a[r] = As[k][ty * 4 + r];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) bq[q] = Bs[k][tx * 4 + q];
+#pragma unroll
+                for (int r = 0; r < 4; ++r)
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) acc[r][q] = fmaf(a[r], bq[q], acc[r][q]);
+            }
         }
         __syncthreads();
     }
+    // result element (r, q) of this thread: row and column within the tile
+    auto row_of = [&](int r, int q) -> int {
+        if (!TC) return ty * 4 + r;
+        const int wid = threadIdx.x >> 5, g = (threadIdx.x & 31) >> 2;
+        return (wid >> 2) * 32 + (r >> 1) * 16 + g + ((q >> 1) ? 8 : 0);
+    };
+    auto col_of = [&](int r, int q) -> int {
+        if (!TC) return tx * 4 + q;
+        const int wid = threadIdx.x >> 5, t = threadIdx.x & 3;
+        return (wid & 3) * 16 + (r & 1) * 8 + 2 * t + (q & 1);
+    };
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        const int64_t c = c0 + tx * 4 + q;
-        if (c >= ncol) continue;
-        const int l = (int)(c / Nr), j = (int)(c % Nr);
-        const int b = alist ? alist[l] : l;
-        if (hp[b]) continue;   // its Newton matrix is the FP64 one
-        const float dt_inv = (float)prm[RP * b + 3];
+    for (int r = 0; r < 4; ++r)
 #pragma unroll
-        for (int r = 0; r < 4; ++r) {
-            const int i = i0 + ty * 4 + r;
-            if (i >= Nr) continue;
+        for (int q = 0; q < 4; ++q) {
+            const int c = c0 + col_of(r, q);
+            const int i = i0 + row_of(r, q);
+            if (c >= ncol || i >= Nr) continue;
+            const int l = c / Nr, j = c - l * Nr;
+            const int b = alist ? alist[l] : l;
+            if (hp[b]) continue;   // its Newton matrix is the FP64 one
+            const float dt_inv = (float)prm[RP * b + 3];
             J[((int64_t)b * Nr + i) * Nr + j] =
                 acc[r][q] + d.Msf[(int64_t)i * Nr + j] * dt_inv + d.Alinf[(int64_t)i * Nr + j];
         }
-    }
 }
 
 
@@ -399,141 +476,52 @@ k_rom_resid(RomDev d, const double* __restrict__ a, const double* __restrict__ a
     }
 }
 
-// delta[b] = -J[b]^-1 r[b] in FP32 (r FP64 on input, delta FP64 on output):
-// row then column equilibration, LU with partial pivoting (ties: lowest
-// row), forward elimination of the right-hand side during the
-// factorisation, back substitution.  One block per instance, J[b] overwritten.
+// delta[b] = -J[b]^-1 r[b] in the precision T of J (r and delta FP64): row
+// then column equilibration, LU with partial pivoting (ties: lowest row),
+// forward elimination of the right-hand side during the factorisation (so the
+// L factor is never stored), back substitution.  One block per instance; the
+// matrix is copied to shared memory (SMEM, lu_smem(Nr, sizeof(T)) <=
+// ROM_LU_SMEM, opt-in above 48 KB, set at mb_rom_create) or factorised in place
+// in J.  Per column k: warp 0 reduces the per-warp pivot candidates, all threads
+// swap the two rows, then warp w eliminates rows k+1+w, k+1+w+nw, ... with its
+// lanes along the columns and keeps the largest |A[i][k+1]| of its rows as the
+// next column's candidate (two or three barriers per column).  1/A[k][k] is
+// kept in x[k] for warp 0's back substitution.  128 threads up to Nr 96, 1024
+// beyond (one block per SM at the larger sizes: warps hide the latency).
+constexpr int ROM_LU_SMEM = 220 * 1024;
+constexpr int LU_T_SMALL = 128, LU_T_LARGE = 1024;
+__host__ __device__ constexpr size_t lu_smem(int Nr, size_t elem) { return elem * ((size_t)Nr * Nr + 4 * (size_t)Nr); }
 template <class T>
-__global__ void __launch_bounds__(256)
+__device__ inline void lu_pick(T& best, int& bi, T v2, int i2) {
+    if (v2 > best || (v2 == best && i2 < bi)) { best = v2; bi = i2; }
+}
+template <class T, bool SMEM>
+__global__ void __launch_bounds__(1024, 1)
 k_rom_lu(int Nr, T* __restrict__ J, const double* __restrict__ r, const int* __restrict__ active,
          const int* __restrict__ hp, int want_hp, const int* __restrict__ list, double* __restrict__ delta) {
     const int b = list ? list[blockIdx.x] : blockIdx.x;
     if (!active[b] || (hp[b] != 0) != (want_hp != 0)) return;
-    __shared__ T sh[256];
-    __shared__ T rs[ROM_NR_MAX], cs[ROM_NR_MAX], rhs[ROM_NR_MAX], x[ROM_NR_MAX];
-    __shared__ int spiv;
-    T* A = J + (int64_t)b * Nr * Nr;
-    for (int i = threadIdx.x; i < Nr; i += blockDim.x) {
-        T m = T(0);
-        for (int j = 0; j < Nr; ++j) m = fmax(m, fabs(A[(int64_t)i * Nr + j]));
-        rs[i] = m > T(0) ? T(1) / m : T(1);
-    }
-    __syncthreads();
-    for (int j = threadIdx.x; j < Nr; j += blockDim.x) {
-        T m = T(0);
-        for (int i = 0; i < Nr; ++i) m = fmax(m, fabs(A[(int64_t)i * Nr + j] * rs[i]));
-        cs[j] = m > T(0) ? T(1) / m : T(1);
-    }
-    __syncthreads();
-    for (int idx = threadIdx.x; idx < Nr * Nr; idx += blockDim.x) {
-        const int i = idx / Nr, j = idx % Nr;
-        A[idx] *= rs[i] * cs[j];
-    }
-    for (int i = threadIdx.x; i < Nr; i += blockDim.x) rhs[i] = (T)(-r[(int64_t)b * Nr + i]) * rs[i];
-    __syncthreads();
-    for (int k = 0; k < Nr; ++k) {
-        // pivot: largest |A[i][k]|, i >= k, lowest index on ties
-        T best = T(-1);
-        int bi = k;
-        for (int i = k + threadIdx.x; i < Nr; i += blockDim.x) {
-            T v = fabs(A[(int64_t)i * Nr + k]);
-            if (v > best) { best = v; bi = i; }
-        }
-        // reduce (value, index)
-        sh[threadIdx.x] = best;
-        __shared__ int shi[256];
-        shi[threadIdx.x] = bi;
-        __syncthreads();
-        for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-            if (threadIdx.x < s) {
-                T v2 = sh[threadIdx.x + s];
-                int i2 = shi[threadIdx.x + s];
-                if (v2 > sh[threadIdx.x] || (v2 == sh[threadIdx.x] && i2 < shi[threadIdx.x])) {
-                    sh[threadIdx.x] = v2;
-                    shi[threadIdx.x] = i2;
-                }
-            }
-            __syncthreads();
-        }
-        if (threadIdx.x == 0) spiv = shi[0];
-        __syncthreads();
-        const int piv = spiv;
-        if (piv != k) {
-            for (int j = threadIdx.x; j < Nr; j += blockDim.x) {
-                T t = A[(int64_t)k * Nr + j];
-                A[(int64_t)k * Nr + j] = A[(int64_t)piv * Nr + j];
-                A[(int64_t)piv * Nr + j] = t;
-            }
-            if (threadIdx.x == 0) {
-                T t = rhs[k]; rhs[k] = rhs[piv]; rhs[piv] = t;
-            }
-        }
-        __syncthreads();
-        const T akk = A[(int64_t)k * Nr + k];
-        const T inv = akk != T(0) ? T(1) / akk : T(0);
-        // multipliers and right-hand side
-        for (int i = k + 1 + threadIdx.x; i < Nr; i += blockDim.x) {
-            T l = A[(int64_t)i * Nr + k] * inv;
-            A[(int64_t)i * Nr + k] = l;
-            rhs[i] -= l * rhs[k];
-        }
-        __syncthreads();
-        const int m = Nr - k - 1;
-        for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x) {
-            const int i = k + 1 + idx / m, j = k + 1 + idx % m;
-            A[(int64_t)i * Nr + j] -= A[(int64_t)i * Nr + k] * A[(int64_t)k * Nr + j];
-        }
-        __syncthreads();
-    }
-    // back substitution
-    for (int k = Nr - 1; k >= 0; --k) {
-        T part = T(0);
-        for (int j = k + 1 + threadIdx.x; j < Nr; j += blockDim.x) part += A[(int64_t)k * Nr + j] * x[j];
-        sh[threadIdx.x] = part;
-        __syncthreads();
-        for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-            if (threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
-            __syncthreads();
-        }
-        if (threadIdx.x == 0) {
-            const T akk = A[(int64_t)k * Nr + k];
-            x[k] = akk != T(0) ? (rhs[k] - sh[0]) / akk : T(0);
-        }
-        __syncthreads();
-    }
-    for (int j = threadIdx.x; j < Nr; j += blockDim.x) delta[(int64_t)b * Nr + j] = (double)(x[j] * cs[j]);
-}
-
-// The same factorisation and solve with four or eight warps per instance, the
-// matrix in shared memory (lu4_smem(Nr) <= ROM_LU4_SMEM): per column one warp finds the pivot,
-// then all threads swap, form the multipliers and update the trailing block
-// (four barriers per column); warp 0 does the back substitution.
-// Matrix sizes held in shared memory: up to ROM_LU4_SMEM bytes (opt-in above
-// 48 KB, set at mb_rom_create); 128 threads up to Nr 96, 256 beyond.
-constexpr int ROM_LU4_SMEM = 220 * 1024;
-constexpr int LU4_T = 128;
-__host__ __device__ constexpr size_t lu4_smem(int Nr, size_t elem) { return elem * ((size_t)Nr * Nr + 4 * (size_t)Nr); }
-template <class T>
-__global__ void __launch_bounds__(256)
-k_rom_lu4(int Nr, T* __restrict__ J, const double* __restrict__ r, const int* __restrict__ active,
-          const int* __restrict__ hp, int want_hp, const int* __restrict__ list, double* __restrict__ delta) {
-    const int b = list ? list[blockIdx.x] : blockIdx.x;
-    if (!active[b] || (hp[b] != 0) != (want_hp != 0)) return;
     extern __shared__ __align__(16) unsigned char lu_raw[];
-    T* A = reinterpret_cast<T*>(lu_raw);   // Nr x Nr
-    T* rs = A + Nr * Nr;          // row scales
-    T* cs = rs + Nr;              // column scales
-    T* rhs = cs + Nr;
-    T* x = rhs + Nr;
+    T* const sm = reinterpret_cast<T*>(lu_raw);
+    T* const Jb = J + (int64_t)b * Nr * Nr;
+    T* const A = SMEM ? sm : Jb;                 // Nr x Nr, row-major
+    T* const rs = SMEM ? sm + Nr * Nr : sm;      // row scales
+    T* const cs = rs + Nr;                       // column scales
+    T* const rhs = cs + Nr;
+    T* const x = rhs + Nr;                       // 1/A[k][k], then the solution
+    __shared__ T wbest[32];
+    __shared__ int widx[32];
     __shared__ int spiv;
-    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    const T* Jb = J + (int64_t)b * Nr * Nr;
-    for (int e = tid; e < Nr * Nr; e += blockDim.x) A[e] = Jb[e];
-    __syncthreads();
-    for (int i = tid; i < Nr; i += blockDim.x) {
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
+    if (SMEM) {
+        for (int e = tid; e < Nr * Nr; e += blockDim.x) A[e] = Jb[e];
+        __syncthreads();
+    }
+    for (int i = wid; i < Nr; i += nw) {
         T m = T(0);
-        for (int j = 0; j < Nr; ++j) m = fmax(m, fabs(A[i * Nr + j]));
-        rs[i] = m > T(0) ? T(1) / m : T(1);
+        for (int j = lane; j < Nr; j += 32) m = fmax(m, fabs(A[i * Nr + j]));
+        for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if (lane == 0) rs[i] = m > T(0) ? T(1) / m : T(1);
     }
     __syncthreads();
     for (int j = tid; j < Nr; j += blockDim.x) {
@@ -542,28 +530,35 @@ k_rom_lu4(int Nr, T* __restrict__ J, const double* __restrict__ r, const int* __
         cs[j] = m > T(0) ? T(1) / m : T(1);
     }
     __syncthreads();
-    for (int e = tid; e < Nr * Nr; e += blockDim.x) A[e] *= rs[e / Nr] * cs[e % Nr];
+    for (int i = wid; i < Nr; i += nw)
+        for (int j = lane; j < Nr; j += 32) A[i * Nr + j] *= rs[i] * cs[j];
     for (int i = tid; i < Nr; i += blockDim.x) rhs[i] = (T)(-r[(int64_t)b * Nr + i]) * rs[i];
+    __syncthreads();
+    {
+        // candidates for the first pivot
+        T best = T(-1);
+        int bi = Nr;
+        for (int i = tid; i < Nr; i += blockDim.x) lu_pick(best, bi, fabs(A[i * Nr]), i);
+        for (int o = 16; o > 0; o >>= 1)
+            lu_pick(best, bi, __shfl_xor_sync(0xffffffffu, best, o), __shfl_xor_sync(0xffffffffu, bi, o));
+        if (lane == 0) {
+            wbest[wid] = best;
+            widx[wid] = bi;
+        }
+    }
     __syncthreads();
     for (int k = 0; k < Nr; ++k) {
         if (wid == 0) {
-            T best = T(-1);
-            int bi = k;
-            for (int i = k + lane; i < Nr; i += 32) {
-                const T v = fabs(A[i * Nr + k]);
-                if (v > best) { best = v; bi = i; }
-            }
-            for (int o = 16; o > 0; o >>= 1) {
-                const T v2 = __shfl_xor_sync(0xffffffffu, best, o);
-                const int i2 = __shfl_xor_sync(0xffffffffu, bi, o);
-                if (v2 > best || (v2 == best && i2 < bi)) { best = v2; bi = i2; }
-            }
-            if (lane == 0) spiv = bi;
+            T best = lane < nw ? wbest[lane] : T(-1);
+            int bi = lane < nw ? widx[lane] : Nr;
+            for (int o = 16; o > 0; o >>= 1)
+                lu_pick(best, bi, __shfl_xor_sync(0xffffffffu, best, o), __shfl_xor_sync(0xffffffffu, bi, o));
+            if (lane == 0) spiv = bi < Nr ? bi : k;
         }
         __syncthreads();
-        const int piv = spiv;
+        const int piv = spiv;   // the same in every thread: the branch below is uniform
         if (piv != k) {
-            for (int j = tid; j < Nr; j += blockDim.x) {
+            for (int j = k + tid; j < Nr; j += blockDim.x) {
                 const T t = A[k * Nr + j];
                 A[k * Nr + j] = A[piv * Nr + j];
                 A[piv * Nr + j] = t;
@@ -573,20 +568,26 @@ k_rom_lu4(int Nr, T* __restrict__ J, const double* __restrict__ r, const int* __
                 rhs[k] = rhs[piv];
                 rhs[piv] = t;
             }
+            __syncthreads();
         }
-        __syncthreads();
         const T akk = A[k * Nr + k];
         const T inv = akk != T(0) ? T(1) / akk : T(0);
-        for (int i = k + 1 + tid; i < Nr; i += blockDim.x) {
+        const T rk = rhs[k];
+        if (tid == 0) x[k] = inv;
+        T best = T(-1);
+        int bi = Nr;
+        for (int i = k + 1 + wid; i < Nr; i += nw) {
             const T l = A[i * Nr + k] * inv;
-            A[i * Nr + k] = l;
-            rhs[i] -= l * rhs[k];
+            for (int j = k + 1 + lane; j < Nr; j += 32) {
+                const T v = A[i * Nr + j] - l * A[k * Nr + j];
+                A[i * Nr + j] = v;
+                if (j == k + 1) lu_pick(best, bi, fabs(v), i);
+            }
+            if (lane == 0) rhs[i] -= l * rk;
         }
-        __syncthreads();
-        const int m = Nr - k - 1;
-        for (int e = tid; e < m * m; e += blockDim.x) {
-            const int i = k + 1 + e / m, j = k + 1 + e % m;
-            A[i * Nr + j] -= A[i * Nr + k] * A[k * Nr + j];
+        if (lane == 0) {   // column k+1 lives in lane 0 of every warp
+            wbest[wid] = best;
+            widx[wid] = bi;
         }
         __syncthreads();
     }
@@ -595,15 +596,26 @@ k_rom_lu4(int Nr, T* __restrict__ J, const double* __restrict__ r, const int* __
             T part = T(0);
             for (int j = k + 1 + lane; j < Nr; j += 32) part += A[k * Nr + j] * x[j];
             for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
-            if (lane == 0) {
-                const T a_kk = A[k * Nr + k];
-                x[k] = a_kk != T(0) ? (rhs[k] - part) / a_kk : T(0);
-            }
+            if (lane == 0) x[k] = (rhs[k] - part) * x[k];
             __syncwarp();
         }
     }
     __syncthreads();
     for (int j = tid; j < Nr; j += blockDim.x) delta[(int64_t)b * Nr + j] = (double)(x[j] * cs[j]);
+}
+
+// Launch the LU solve of the listed instances (all B without a list) with
+// want_hp selecting the FP32 (0) or FP64 (1) Newton matrices.
+template <class T>
+static void launch_rom_lu(int Nr, int nblk, T* J, const double* r, const int* active, const int* hp, int want_hp,
+                          const int* list, double* delta, cudaStream_t s) {
+    const unsigned lt = Nr <= 96 ? LU_T_SMALL : LU_T_LARGE;
+    if (lu_smem(Nr, sizeof(T)) <= ROM_LU_SMEM)
+        k_rom_lu<T, true><<<(unsigned)nblk, lt, lu_smem(Nr, sizeof(T)), s>>>(Nr, J, r, active, hp, want_hp, list,
+                                                                             delta);
+    else
+        k_rom_lu<T, false><<<(unsigned)nblk, lt, 4 * sizeof(T) * (size_t)Nr, s>>>(Nr, J, r, active, hp, want_hp,
+                                                                                 list, delta);
 }
 
 // Step length of all instances: the scaled max-norm of the reconstructed
@@ -790,6 +802,22 @@ __global__ void k_rom_slot_start(RomDev d, int b, double I_app, double s_i0, dou
         its[b] = 0;
         flips[b] = 0;
         hp[b] = 0;
+    }
+}
+
+// start every slot b < B (parameters already in prm): a = a0, counters zero, not failed
+__global__ void k_rom_batch_start(RomDev d, int B, double* __restrict__ a, int* __restrict__ failed,
+                                  long long* __restrict__ its, long long* __restrict__ flips, int* __restrict__ hp) {
+    const int64_t n = (int64_t)B * d.Nr;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+        const int b = (int)(e / d.Nr), j = (int)(e - (int64_t)b * d.Nr);
+        a[e] = d.a0[j];
+        if (j == 0) {
+            failed[b] = 0;
+            its[b] = 0;
+            flips[b] = 0;
+            hp[b] = 0;
+        }
     }
 }
 
@@ -1051,15 +1079,22 @@ static int rom_build_host(mb_rom* R, const mb_rom_data* dd) {
                                cudaSuccess;
     }
     if (ok)
-        ok = upf(d.Pf, P.data(), P.size()) && upf(d.Msf, dd->Ms, (size_t)Nr * Nr) &&
+    if (ok) {
+        std::vector<double> Pt((size_t)M * Nr);
+        for (int i = 0; i < Nr; ++i)
+            for (int k = 0; k < M; ++k) Pt[(size_t)k * Nr + i] = P[(size_t)i * M + k];
+        ok = upf(d.Ptf, Pt.data(), Pt.size());
+    }
+    if (ok)
+        ok = upf(d.Msf, dd->Ms, (size_t)Nr * Nr) &&
              upf(d.Alinf, dd->Alin, (size_t)Nr * Nr) && upf(d.UlocRf, UlocR.data(), UlocR.size()) &&
              upf(d.UlocCf, UlocC.data(), UlocC.size()) && upf(d.usf, us.data(), us.size());
     // shared memory of the LU kernels beyond the default 48 KB
     if (ok)
-        ok = cudaFuncSetAttribute(k_rom_lu4<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, ROM_LU4_SMEM) ==
-                 cudaSuccess &&
-             cudaFuncSetAttribute(k_rom_lu4<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, ROM_LU4_SMEM) ==
-                 cudaSuccess;
+        ok = cudaFuncSetAttribute(k_rom_lu<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  ROM_LU_SMEM) == cudaSuccess &&
+             cudaFuncSetAttribute(k_rom_lu<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  ROM_LU_SMEM) == cudaSuccess;
     if (!ok) return cuda_fail(cudaGetLastError(), "rom upload");
     return MB_OK;
 }
@@ -1212,31 +1247,25 @@ int rom_batch_step(mb_rom* R) {
                 const bool listed = it > 0 && w.n_alist >= 0;
                 const int ncols = listed ? w.n_alist : B;
                 if (ncols > 0)
-                    k_rom_jac<<<dim3((unsigned)(((int64_t)ncols * d.Nr + JT_COLS - 1) / JT_COLS),
-                                     (unsigned)((d.Nr + JT_ROWS - 1) / JT_ROWS)),
-                                256, 0, s>>>(d, B, ncols, listed ? w.alist : nullptr, w.prm, w.GU, w.hp, w.J),
-                        count_launch(c);
+                {
+                    const dim3 gj((unsigned)(((int64_t)ncols * d.Nr + JT_COLS - 1) / JT_COLS),
+                                  (unsigned)((d.Nr + JT_ROWS - 1) / JT_ROWS));
+                    const int* al = listed ? w.alist : nullptr;
+                    if (d.tc)
+                        k_rom_jac<true><<<gj, 256, 0, s>>>(d, B, ncols, al, w.prm, w.GU, w.hp, w.J);
+                    else
+                        k_rom_jac<false><<<gj, 256, 0, s>>>(d, B, ncols, al, w.prm, w.GU, w.hp, w.J);
+                    count_launch(c);
+                }
             }
             if (hp_any)
                 k_rom_jac64<<<dim3((unsigned)d.Nr, (unsigned)nhp), 128, 0, s>>>(d, w.prm, w.GU64, w.active, w.hp,
                                                                                  w.hplist, w.J64), count_launch(c);
             k_rom_resid<<<(unsigned)B, 128, 0, s>>>(d, w.a, w.a_old, w.prm, w.f, w.active, w.r), count_launch(c);
-            {
-                const unsigned lt = d.Nr <= 96 ? LU4_T : 256;
-                if (lu4_smem(d.Nr, 4) <= ROM_LU4_SMEM)
-                    k_rom_lu4<float><<<(unsigned)B, lt, lu4_smem(d.Nr, 4), s>>>(d.Nr, w.J, w.r, w.active, w.hp, 0,
-                                                                                 nullptr, w.delta), count_launch(c);
-                else
-                    k_rom_lu<float><<<(unsigned)B, 256, 0, s>>>(d.Nr, w.J, w.r, w.active, w.hp, 0, nullptr, w.delta),
-                        count_launch(c);
-                if (hp_any && lu4_smem(d.Nr, 8) <= ROM_LU4_SMEM)
-                    k_rom_lu4<double><<<(unsigned)nhp, lt, lu4_smem(d.Nr, 8), s>>>(d.Nr, w.J64, w.r, w.active, w.hp,
-                                                                                    1, w.hplist, w.delta),
-                        count_launch(c);
-                else if (hp_any)
-                    k_rom_lu<double><<<(unsigned)nhp, 256, 0, s>>>(d.Nr, w.J64, w.r, w.active, w.hp, 1, w.hplist,
-                                                                   w.delta), count_launch(c);
-            }
+            launch_rom_lu<float>(d.Nr, B, w.J, w.r, w.active, w.hp, 0, nullptr, w.delta, s), count_launch(c);
+            if (hp_any)
+                launch_rom_lu<double>(d.Nr, nhp, w.J64, w.r, w.active, w.hp, 1, w.hplist, w.delta, s),
+                    count_launch(c);
             {
                 const unsigned nkt = (unsigned)((d.nloc + UN_K - 1) / UN_K);
                 k_rom_unorm<<<dim3(nkt, (unsigned)((B + UN_B - 1) / UN_B)), 256, 0, s>>>(d, B, w.delta, w.active,
@@ -1317,8 +1346,24 @@ extern "C" int mb_rom_solve_batch(mb_rom* R, int B, const mb_rom_params* prm, in
     const int ncol = n_steps + 1;
     int rc = rom_batch_alloc(R, B);
     if (rc) { set_error("mb_rom_solve_batch: device memory"); return rc; }
-    for (int b = 0; b < B; ++b)
-        if ((rc = rom_slot_start(R, b, prm[b], dt))) return rc;
+    {
+        // every instance's parameters in one copy, then one start kernel
+        std::vector<double> hp((size_t)RP * B);
+        for (int b = 0; b < B; ++b) {
+            hp[(size_t)RP * b] = prm[b].I_app;
+            hp[(size_t)RP * b + 1] = prm[b].s_i0;
+            hp[(size_t)RP * b + 2] = prm[b].k_pl;
+            hp[(size_t)RP * b + 3] = 1.0 / dt;
+        }
+        RomWork& w = R->w;
+        cudaStream_t s = R->cell->stream;
+        MB_CUDA(cudaMemcpyAsync(w.prm, hp.data(), 8 * hp.size(), cudaMemcpyHostToDevice, s));
+        const int64_t n = (int64_t)B * R->d.Nr;
+        k_rom_batch_start<<<(unsigned)std::min<int64_t>((n + 255) / 256, 4096), 256, 0, s>>>(
+            R->d, B, w.a, w.failed, w.its, w.flips, w.hp), count_launch(R->cell);
+        MB_CUDA_LAUNCH("rom_batch_start");
+        MB_CUDA(cudaStreamSynchronize(s));   // the host parameter buffer goes out of scope
+    }
     std::vector<double> hV(B), hS(B);
     std::vector<int> hf(B);
     for (int step = 0; step <= n_steps; ++step) {
@@ -1342,5 +1387,112 @@ extern "C" int mb_rom_solve_batch(mb_rom* R, int B, const mb_rom_params* prm, in
         set_error("mb_rom_solve_batch: reduced Newton did not converge for some instances");
         return MB_ENOCONV;
     }
+    return MB_OK;
+}
+
+// ------------------------------------------------------------ test hooks
+#include "../../include/mb_debug.h"
+
+extern "C" int mb_debug_rom_jac(int Nr, int M, int B, const float* P, const float* GU, const float* Ms,
+                                const float* Alin, const double* dt_inv, int tc, float* J) {
+    if (Nr < 1 || M < 1 || B < 1 || !P || !GU || !Ms || !Alin || !dt_inv || !J) {
+        set_error("mb_debug_rom_jac: invalid argument");
+        return MB_EINVAL;
+    }
+    std::vector<void*> bufs;
+    RomDev d;
+    d.Nr = Nr;
+    d.M = M;
+    d.tc = tc;
+    auto dev = [&](const void* h, size_t bytes) -> void* {
+        void* p = nullptr;
+        if (cudaMalloc(&p, bytes ? bytes : 1) != cudaSuccess) return nullptr;
+        bufs.push_back(p);
+        if (h && cudaMemcpy(p, h, bytes, cudaMemcpyHostToDevice) != cudaSuccess) return nullptr;
+        return p;
+    };
+    std::vector<double> prm((size_t)RP * B, 0.0);
+    for (int b = 0; b < B; ++b) prm[(size_t)RP * b + 3] = dt_inv[b];
+    std::vector<int> hp(B, 0);
+    std::vector<float> Pt((size_t)M * Nr);
+    for (int i = 0; i < Nr; ++i)
+        for (int k = 0; k < M; ++k) Pt[(size_t)k * Nr + i] = P[(size_t)i * M + k];
+    d.Ptf = (float*)dev(Pt.data(), 4 * Pt.size());
+    d.Msf = (float*)dev(Ms, 4 * (size_t)Nr * Nr);
+    d.Alinf = (float*)dev(Alin, 4 * (size_t)Nr * Nr);
+    float* gu = (float*)dev(GU, 4 * (size_t)M * B * Nr);
+    double* dprm = (double*)dev(prm.data(), 8 * prm.size());
+    int* dhp = (int*)dev(hp.data(), 4 * (size_t)B);
+    float* dJ = (float*)dev(nullptr, 4 * (size_t)B * Nr * Nr);
+    int rc = MB_OK;
+    if (!d.Ptf || !d.Msf || !d.Alinf || !gu || !dprm || !dhp || !dJ) {
+        rc = cuda_fail(cudaGetLastError(), "debug_rom_jac alloc");
+    } else {
+        const dim3 gj((unsigned)(((int64_t)B * Nr + JT_COLS - 1) / JT_COLS), (unsigned)((Nr + JT_ROWS - 1) / JT_ROWS));
+        if (tc)
+            k_rom_jac<true><<<gj, 256>>>(d, B, B, nullptr, dprm, gu, dhp, dJ);
+        else
+            k_rom_jac<false><<<gj, 256>>>(d, B, B, nullptr, dprm, gu, dhp, dJ);
+        cudaError_t e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaMemcpy(J, dJ, 4 * (size_t)B * Nr * Nr, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) rc = cuda_fail(e, "debug_rom_jac");
+    }
+    for (void* p : bufs) cudaFree(p);
+    return rc;
+}
+
+template <class T>
+static int debug_rom_lu(int Nr, int B, int in_place, const double* J, const double* r, double* delta) {
+    const bool smem = !in_place;
+    if (smem && lu_smem(Nr, sizeof(T)) > ROM_LU_SMEM) {
+        set_error("mb_debug_rom_lu: matrix too large for shared memory");
+        return MB_EINVAL;
+    }
+    std::vector<T> hJ(J, J + (size_t)B * Nr * Nr);
+    std::vector<int> ones(B, 1), zeros(B, 0);
+    T* dJ = nullptr;
+    double *dr = nullptr, *dd = nullptr;
+    int *da = nullptr, *dh = nullptr;
+    cudaError_t e = cudaMalloc(&dJ, sizeof(T) * hJ.size());
+    if (e == cudaSuccess) e = cudaMalloc(&dr, 8 * (size_t)B * Nr);
+    if (e == cudaSuccess) e = cudaMalloc(&dd, 8 * (size_t)B * Nr);
+    if (e == cudaSuccess) e = cudaMalloc(&da, 4 * (size_t)B);
+    if (e == cudaSuccess) e = cudaMalloc(&dh, 4 * (size_t)B);
+    if (e == cudaSuccess) e = cudaMemcpy(dJ, hJ.data(), sizeof(T) * hJ.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(dr, r, 8 * (size_t)B * Nr, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(da, ones.data(), 4 * (size_t)B, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(dh, zeros.data(), 4 * (size_t)B, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && smem)
+        e = cudaFuncSetAttribute(k_rom_lu<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, ROM_LU_SMEM);
+    if (e == cudaSuccess) {
+        const unsigned lt = Nr <= 96 ? LU_T_SMALL : LU_T_LARGE;
+        if (smem)
+            k_rom_lu<T, true><<<(unsigned)B, lt, lu_smem(Nr, sizeof(T))>>>(Nr, dJ, dr, da, dh, 0, nullptr, dd);
+        else
+            k_rom_lu<T, false><<<(unsigned)B, lt, 4 * sizeof(T) * (size_t)Nr>>>(Nr, dJ, dr, da, dh, 0, nullptr, dd);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(delta, dd, 8 * (size_t)B * Nr, cudaMemcpyDeviceToHost);
+    cudaFree(dJ);
+    cudaFree(dr);
+    cudaFree(dd);
+    cudaFree(da);
+    cudaFree(dh);
+    return e == cudaSuccess ? MB_OK : cuda_fail(e, "debug_rom_lu");
+}
+
+extern "C" int mb_debug_rom_lu(int Nr, int B, int fp64, int in_place, const double* J, const double* r,
+                               double* delta) {
+    if (Nr < 1 || Nr > ROM_NR_MAX || B < 1 || !J || !r || !delta) {
+        set_error("mb_debug_rom_lu: invalid argument");
+        return MB_EINVAL;
+    }
+    return fp64 ? debug_rom_lu<double>(Nr, B, in_place, J, r, delta)
+                : debug_rom_lu<float>(Nr, B, in_place, J, r, delta);
+}
+
+extern "C" int mb_debug_rom_tensor(mb_rom* R, int on) {
+    if (!R) return MB_EINVAL;
+    R->d.tc = on ? 1 : 0;
     return MB_OK;
 }

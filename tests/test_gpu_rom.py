@@ -127,3 +127,67 @@ def test_rom_wide_matches_oracle(params, wide_case):
         assert np.max(np.abs(out["s_ac"][b] - ref["s_ac"])) <= 1e-9 * np.max(np.abs(ref["s_ac"])), b
     g.close()
     gc.close()
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("tc", [True, False])
+def test_rom_newton_matrix_kernel(tc):
+    """The Newton-matrix kernel against an FP64 product: J_b = P GU_b + Ms/dt_b + Alin,
+    ragged in rows (70), the contraction (100) and the columns (3 x 70); both kernels
+    keep FP32 accuracy (the tensor-core one as three TF32 products)."""
+    B = _gpu()
+    rng = np.random.default_rng(7)
+    Nr, M, nb = 70, 100, 3
+    P = rng.standard_normal((Nr, M)).astype(np.float32)
+    GU = rng.standard_normal((nb, M, Nr)).astype(np.float32)
+    Ms = rng.standard_normal((Nr, Nr)).astype(np.float32)
+    Al = rng.standard_normal((Nr, Nr)).astype(np.float32)
+    dti = np.array([0.5, 2.0, 10.0])
+    J = B.debug_rom_jac(P, GU, Ms, Al, dti, tc=tc)
+    P64, G64 = P.astype(np.float64), GU.astype(np.float64)
+    for b in range(nb):
+        ref = P64 @ G64[b] + Ms.astype(np.float64) * np.float32(dti[b]) + Al.astype(np.float64)
+        # |P| |GU| bounds the rounding of an FP32 sum of M products
+        scale = np.abs(P64) @ np.abs(G64[b]) + np.abs(Ms) * dti[b] + np.abs(Al)
+        assert np.all(np.abs(J[b] - ref) <= 4 * M * 2.0 ** -24 * scale), b
+
+
+@pytest.mark.gpu
+def test_rom_tensor_newton_matrix_same_result(params, case):
+    """The online solve with the tensor-core Newton matrix converges to the same
+    reduced trajectory as with the FP32-FMA one (the matrix only steers Newton)."""
+    B = _gpu()
+    lab, oc, rom = case
+    gc, g = _gpu_rom(B, lab, params, rom)
+    prm = [(c * oc.i_1c, s, k) for (c, s, k) in [(-2.0, 1.0, 1.0), (1.0, 0.9, 0.5)]]
+    g.debug_tensor(True)
+    a = g.solve(prm, 4, 1.0)
+    g.debug_tensor(False)
+    b = g.solve(prm, 4, 1.0)
+    assert a["ok"] and b["ok"]
+    assert np.max(np.abs(a["V"] - b["V"])) <= 1e-9 * np.max(np.abs(a["V"]))
+    g.close()
+    gc.close()
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("Nr,fp64,in_place", [(70, True, False), (70, False, False), (112, True, True),
+                                              (150, False, True), (209, False, False), (209, True, True)])
+def test_rom_newton_step_lu_kernel(Nr, fp64, in_place):
+    """The Newton-step LU kernel against a library solve: random matrices with rows
+    scaled over twelve decades (the equilibration removes that) and a zero leading
+    diagonal (the pivoting has to move it), in shared memory or in place."""
+    B = _gpu()
+    rng = np.random.default_rng(Nr)
+    nb = 5
+    J = rng.standard_normal((nb, Nr, Nr))
+    J[:, 0, 0] = 0.0
+    J *= 10.0 ** rng.uniform(-6, 6, (nb, Nr, 1))
+    r = rng.standard_normal((nb, Nr))
+    d = B.debug_rom_lu(J, r, fp64=fp64, in_place=in_place)
+    for b in range(nb):
+        ref = -np.linalg.solve(J[b], r[b])
+        scale = np.max(np.abs(ref))
+        # error of a backward-stable solve: ~ cond(equilibrated J) * unit roundoff
+        tol = 1e-9 if fp64 else 2e-3
+        assert np.max(np.abs(d[b] - ref)) <= tol * scale, (b, np.max(np.abs(d[b] - ref)) / scale)
