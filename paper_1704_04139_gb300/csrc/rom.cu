@@ -19,8 +19,9 @@
 // active-set passes of the full-order step.
 // Precision: the state a, the reconstruction, the interpolated terms f and
 // the residual are FP64, so the converged solution is the FP64 one; the
-// Newton matrix (GU, the contraction P GU as one GEMM over all instances,
-// its LU) and the step-length norm are FP32 (an inexact Newton iteration:
+// Newton matrix (GU, the contraction P GU as one GEMM over all instances on
+// the tensor cores with FP32 accuracy, its LU) and the step-length norm are
+// FP32 (an inexact Newton iteration:
 // GB300's FP64 rate is a small fraction of its FP32 rate).  An instance
 // switches to an FP64 Newton matrix (FP64 derivatives, G U_loc, contraction
 // and LU) for the rest of its time step when its iteration stagnates (a full
@@ -269,11 +270,14 @@ __global__ void k_rom_gu(RomDev d, int B, const float* __restrict__ G, const int
     }
 }
 
-// Newton matrices of all instances as one FP32 GEMM, C = P [GU_0 | GU_1 | ...]
-// (Nr x M times M x B Nr), plus Ms/dt_b + Alin, written instance-major
-// J[b][i][j].  Tile: 64 rows (blockIdx.y) x 64 columns (blockIdx.x) per block
-// of 256 threads, each thread 4 rows x 4 columns in registers, K in chunks of
-// 16 staged in shared memory.  Column c = b Nr + j.
+// Newton matrices of the listed instances as one GEMM with FP32 accuracy,
+// C = P [GU_b0 | GU_b1 | ...] (Nr x M times M x nlist Nr), plus Ms/dt_b + Alin,
+// written instance-major J[b][i][j].  Tile: 64 rows (blockIdx.y) x 64 columns
+// (blockIdx.x) per block of 256 threads, K in slices of 32 staged in shared
+// memory (P read from its K-major copy, the next slice fetched into registers
+// while the current one is multiplied).  TC: eight warps of 32 x 16 results on
+// the tensor cores (three TF32 products per pair, below); else FP32 FMA with
+// 4 x 4 results per thread.  Column c = l Nr + j of instance b = alist[l].
 constexpr int JT_ROWS = 64, JT_COLS = 64, JT_K = 32, JT_PAD = 8;
 
 // TF32 tensor-core pieces (mma.sync m16n8k8, FP32 accumulation).  A value
