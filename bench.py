@@ -238,8 +238,8 @@ def rom_paper_dims(B, params, args, torch):
            "dims": {"n_r": rom.n_r, "ei_interface": rom.n_bv, "ei_migration": rom.n_1c,
                     "requested": list(ROM_DIMS_PAPER)},
            "instances": args.rom_instances, "steps": steps, "dt_s": 1.0,
-           "precision": "f64 state and residual; float-float reconstruction; f32 Newton matrix and LU with "
-                        "per-instance escalation to f64",
+           "precision": "f64 state and residual; float-float reconstruction; Newton matrix with f32 accuracy "
+                        "(3xTF32 on the tensor cores) and f32 LU, with per-instance escalation to f64",
            "instance_steps_per_s": inst_steps / wall, "solves_per_s": args.rom_instances / wall, "wall_s": wall,
            "build_s": build_s, "newton_its_per_instance_step": out["newton_its"] / inst_steps,
            "failed": out["failed"], "V_rel_err_vs_full_order_2_instances": errs}
@@ -391,6 +391,9 @@ def main():
     ap.add_argument("--rom-paper-steps", type=int, default=3,
                     help="timed steps of the paper-size reduced model (a sample of its 600-step protocol)")
     ap.add_argument("--serve-requests", type=int, default=1000)
+    ap.add_argument("--rom-only", action="store_true",
+                    help="run only the paper-size reduced model (build, timed batch, error check) and print its "
+                         "JSON object: the command the reduced-model launch lists are taken with")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -404,6 +407,10 @@ def main():
         from paper_1704_04139_gb300 import build
         build.build()
     params = syn.load_params()
+    if args.rom_only:
+        if rank == 0:
+            print(json.dumps({"rom": rom_paper_dims(B, params, args, torch)}))
+        return 0
     labels = workload_labels(args.workload)
     prec = B.PREC_MIXED if args.precision == "mixed" else B.PREC_FP64
     opts = B.default_opts(precision=prec, newton_tol=1e-9, krylov_rtol=1e-4 if prec else 1e-6,
