@@ -239,7 +239,8 @@ def rom_paper_dims(B, params, args, torch):
                     "requested": list(ROM_DIMS_PAPER)},
            "instances": args.rom_instances, "steps": steps, "dt_s": 1.0,
            "precision": "f64 state and residual; float-float reconstruction; Newton matrix with f32 accuracy "
-                        "(3xTF32 on the tensor cores) and f32 LU, with per-instance escalation to f64",
+                        "(3xTF32 on the tensor cores) and f32 LU; escalated instances by f64 GMRES preconditioned "
+                        "by their f32 LU",
            "instance_steps_per_s": inst_steps / wall, "solves_per_s": args.rom_instances / wall, "wall_s": wall,
            "build_s": build_s, "newton_its_per_instance_step": out["newton_its"] / inst_steps,
            "failed": out["failed"], "V_rel_err_vs_full_order_2_instances": errs}

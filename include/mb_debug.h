@@ -55,6 +55,9 @@ int mb_debug_rom_jac(int Nr, int M, int B, const float* P, const float* GU, cons
  * FP64 (fp64 = 1) or FP32 arithmetic, the matrix in shared memory (in_place =
  * 0; MB_EINVAL when it does not fit) or factorised in place in device memory. */
 int mb_debug_rom_lu(int Nr, int B, int fp64, int in_place, const double* J, const double* r, double* delta);
+/* Escalated instances of the online solve: GMRES on FP64 products preconditioned by
+ * the instance's last FP32 LU (on = 1, the default), or the FP64 Newton matrix and LU (0). */
+int mb_debug_rom_refine(mb_rom* rom, int on);
 /* Use (on = 1, the default) or not the tensor-core Newton-matrix kernel in the online solve. */
 int mb_debug_rom_tensor(mb_rom* rom, int on);
 

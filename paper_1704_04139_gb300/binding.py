@@ -150,6 +150,7 @@ def _declare(lib):
     fn("mb_debug_fine_stencil", C.c_int, [VP, VP])
     fn("mb_debug_rom_jac", C.c_int, [C.c_int, C.c_int, C.c_int, VP, VP, VP, VP, VP, C.c_int, VP])
     fn("mb_debug_rom_tensor", C.c_int, [VP, C.c_int])
+    fn("mb_debug_rom_refine", C.c_int, [VP, C.c_int])
     fn("mb_debug_rom_lu", C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, VP, VP, VP])
     fn("mb_debug_residual_split", C.c_int, [VP, VP, VP, VP, C.c_double, C.c_double, VP])
     return lib
@@ -418,6 +419,10 @@ class Rom:
             _check(rc)
         out["ok"] = rc == 0
         return out
+
+    def debug_refine(self, on):
+        """Escalated instances by GMRES preconditioned with the FP32 LU (on, the default) or the FP64 LU (off)."""
+        _check(lib().mb_debug_rom_refine(self.h, 1 if on else 0))
 
     def debug_tensor(self, on):
         """Newton-matrix GEMM on the tensor cores (3xTF32, the default) or FP32 FMA."""

@@ -56,6 +56,7 @@ enum RomTerm : int8_t { T_NONE = 0, T_GE = 1, T_KE = 2, T_LE = 3, T_EE = 4 };
 struct RomDev {
     int Nr = 0, Mbv = 0, M1c = 0, M = 0, nloc = 0, ngate = 0;
     int tc = 1;                // Newton-matrix GEMM on the tensor cores (3xTF32), else FP32 FMA
+    int ir = 1;                // escalated instances: GMRES on FP64 products preconditioned by the kept FP32 LU
     double* UlocR = nullptr;   // nloc x Nr
     double* us = nullptr;      // nloc unknown scales
     int8_t* ttype = nullptr;   // M x TMAX
@@ -97,6 +98,8 @@ struct RomWork {
     double* GU64 = nullptr;    // B x M x Nr     their G U_loc
     double* J64 = nullptr;     // B x Nr x Nr    their Newton matrices
     int* hplist = nullptr;     // B: the instances with hp (compacted at each count; order irrelevant)
+    int* lpiv = nullptr;       // B x Nr   pivot rows of the kept FP32 LU factors (in J; refinement mode)
+    float* lsc = nullptr;      // B x 2 Nr their row and column scales
     int* alist = nullptr;      // B: the active instances on the FP32 matrix (compacted at each count)
     int n_alist = -1;          // host: its length at the last count (-1: not counted yet: all B)
     int hp_any = 0;            // host: number of instances with hp at the last count
@@ -492,6 +495,9 @@ k_rom_resid(RomDev d, const double* __restrict__ a, const double* __restrict__ a
 // next column's candidate (two or three barriers per column).  1/A[k][k] is
 // kept in x[k] for warp 0's back substitution.  128 threads up to Nr 96, 1024
 // beyond (one block per SM at the larger sizes: warps hide the latency).
+// KEEP: the factors stay in J (whole rows swapped, multipliers stored below
+// the diagonal), with the pivot rows in piv_out[b] and the row and column
+// scales in sc_out[b] (Nr each), for k_rom_gmres's preconditioner.
 constexpr int ROM_LU_SMEM = 220 * 1024;
 constexpr int LU_T_SMALL = 128, LU_T_LARGE = 1024;
 __host__ __device__ constexpr size_t lu_smem(int Nr, size_t elem) { return elem * ((size_t)Nr * Nr + 4 * (size_t)Nr); }
@@ -499,10 +505,11 @@ template <class T>
 __device__ inline void lu_pick(T& best, int& bi, T v2, int i2) {
     if (v2 > best || (v2 == best && i2 < bi)) { best = v2; bi = i2; }
 }
-template <class T, bool SMEM>
+template <class T, bool SMEM, bool KEEP = false>
 __global__ void __launch_bounds__(1024, 1)
 k_rom_lu(int Nr, T* __restrict__ J, const double* __restrict__ r, const int* __restrict__ active,
-         const int* __restrict__ hp, int want_hp, const int* __restrict__ list, double* __restrict__ delta) {
+         const int* __restrict__ hp, int want_hp, const int* __restrict__ list, double* __restrict__ delta,
+         int* __restrict__ piv_out = nullptr, T* __restrict__ sc_out = nullptr) {
     const int b = list ? list[blockIdx.x] : blockIdx.x;
     if (!active[b] || (hp[b] != 0) != (want_hp != 0)) return;
     extern __shared__ __align__(16) unsigned char lu_raw[];
@@ -561,8 +568,9 @@ k_rom_lu(int Nr, T* __restrict__ J, const double* __restrict__ r, const int* __r
         }
         __syncthreads();
         const int piv = spiv;   // the same in every thread: the branch below is uniform
+        if (KEEP && tid == 0) piv_out[(int64_t)b * Nr + k] = piv;
         if (piv != k) {
-            for (int j = k + tid; j < Nr; j += blockDim.x) {
+            for (int j = (KEEP ? 0 : k) + tid; j < Nr; j += blockDim.x) {
                 const T t = A[k * Nr + j];
                 A[k * Nr + j] = A[piv * Nr + j];
                 A[piv * Nr + j] = t;
@@ -587,6 +595,10 @@ k_rom_lu(int Nr, T* __restrict__ J, const double* __restrict__ r, const int* __r
                 A[i * Nr + j] = v;
                 if (j == k + 1) lu_pick(best, bi, fabs(v), i);
             }
+            if (KEEP) {
+                __syncwarp();   // every lane has read A[i][k] before lane 0 overwrites it
+                if (lane == 0) A[i * Nr + k] = l;
+            }
             if (lane == 0) rhs[i] -= l * rk;
         }
         if (lane == 0) {   // column k+1 lives in lane 0 of every warp
@@ -606,20 +618,256 @@ k_rom_lu(int Nr, T* __restrict__ J, const double* __restrict__ r, const int* __r
     }
     __syncthreads();
     for (int j = tid; j < Nr; j += blockDim.x) delta[(int64_t)b * Nr + j] = (double)(x[j] * cs[j]);
+    if (KEEP) {
+        if (SMEM)
+            for (int e = tid; e < Nr * Nr; e += blockDim.x) Jb[e] = A[e];
+        for (int j = tid; j < Nr; j += blockDim.x) {
+            sc_out[(int64_t)b * 2 * Nr + j] = rs[j];
+            sc_out[(int64_t)b * 2 * Nr + Nr + j] = cs[j];
+        }
+    }
 }
 
 // Launch the LU solve of the listed instances (all B without a list) with
 // want_hp selecting the FP32 (0) or FP64 (1) Newton matrices.
 template <class T>
 static void launch_rom_lu(int Nr, int nblk, T* J, const double* r, const int* active, const int* hp, int want_hp,
-                          const int* list, double* delta, cudaStream_t s) {
+                          const int* list, double* delta, cudaStream_t s, int* piv = nullptr, T* sc = nullptr) {
     const unsigned lt = Nr <= 96 ? LU_T_SMALL : LU_T_LARGE;
+    if (piv) {   // keep the factors
+        if (lu_smem(Nr, sizeof(T)) <= ROM_LU_SMEM)
+            k_rom_lu<T, true, true><<<(unsigned)nblk, lt, lu_smem(Nr, sizeof(T)), s>>>(Nr, J, r, active, hp, want_hp,
+                                                                                       list, delta, piv, sc);
+        else
+            k_rom_lu<T, false, true><<<(unsigned)nblk, lt, 4 * sizeof(T) * (size_t)Nr, s>>>(
+                Nr, J, r, active, hp, want_hp, list, delta, piv, sc);
+        return;
+    }
     if (lu_smem(Nr, sizeof(T)) <= ROM_LU_SMEM)
         k_rom_lu<T, true><<<(unsigned)nblk, lt, lu_smem(Nr, sizeof(T)), s>>>(Nr, J, r, active, hp, want_hp, list,
                                                                              delta);
     else
         k_rom_lu<T, false><<<(unsigned)nblk, lt, 4 * sizeof(T) * (size_t)Nr, s>>>(Nr, J, r, active, hp, want_hp,
                                                                                  list, delta);
+}
+
+// Newton step of an escalated instance (hp[b], refinement mode): delta =
+// -J64^-1 r by right-preconditioned restarted GMRES(m) in FP64 on products
+// J64 z = Ms z/dt + Alin z + P (GU64[b] z) (GU64 = G U_loc in FP64, formed by
+// k_rom_gu64; the FP64 Newton matrix itself is never formed), preconditioned by
+// the instance's FP32 LU kept from its last FP32-matrix iteration (row scales,
+// row swaps, unit-lower and upper triangular solves, column scales; FP64
+// arithmetic on the FP32 factors).  Stops when the residual estimate falls
+// below eta |r| or after `cycles` restarts; Arnoldi by classical Gram-Schmidt
+// with one reorthogonalisation, Givens rotations on thread 0.  One block of
+// 256 threads per listed instance; shared memory gmres_smem(Nr, M, m) doubles.
+__host__ __device__ constexpr size_t gmres_smem(int Nr, int M, int m) {
+    return 8 * ((size_t)(m + 1) * Nr + (size_t)M + 3 * (size_t)Nr + (size_t)(m + 1) * m + 4 * (size_t)(m + 1) + 40 +
+                ((size_t)Nr + 1) / 2);
+}
+constexpr int GMRES_M = 16, GMRES_CYCLES = 2;
+constexpr double GMRES_ETA = 1e-6;
+__device__ inline double warp_sum_d(double v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__global__ void __launch_bounds__(256)
+k_rom_gmres(RomDev d, const double* __restrict__ prm, const double* __restrict__ GU64, const double* __restrict__ r,
+            const float* __restrict__ J, const int* __restrict__ lpiv, const float* __restrict__ lsc,
+            const int* __restrict__ active, const int* __restrict__ hp, const int* __restrict__ hplist, int m,
+            int cycles, double eta, double* __restrict__ delta) {
+    const int b = hplist[blockIdx.x];
+    if (!active[b] || !hp[b]) return;
+    const int Nr = d.Nr, M = d.M;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
+    extern __shared__ __align__(16) unsigned char gm_raw[];
+    double* const V = reinterpret_cast<double*>(gm_raw);   // (m+1) x Nr Krylov basis
+    double* const t = V + (size_t)(m + 1) * Nr;           // M: GU64 z
+    double* const z = t + M;                              // Nr
+    double* const w = z + Nr;                             // Nr
+    double* const x = w + Nr;                             // Nr: the solution
+    double* const H = x + Nr;                             // (m+1) x m, column j at H + j (m+1)
+    double* const gv = H + (size_t)(m + 1) * m;           // m+1: rotated right-hand side
+    double* const cr = gv + (m + 1);                      // m: Givens cosines
+    double* const sr = cr + (m + 1);                      // m: Givens sines
+    double* const hy = sr + (m + 1);                      // m+1: projections, then y
+    double* const red = hy + (m + 1);                     // 40: reduction scratch and flags
+    int* const ps = reinterpret_cast<int*>(red + 40);     // Nr pivot rows
+    const float* const LU = J + (int64_t)b * Nr * Nr;
+    const int* const pv = lpiv + (int64_t)b * Nr;
+    const float* const rsc = lsc + (int64_t)b * 2 * Nr;
+    const float* const csc = rsc + Nr;
+    const double* const GUb = GU64 + (int64_t)b * M * Nr;
+    const double dt_inv = prm[RP * b + 3];
+    for (int k = tid; k < Nr; k += blockDim.x) ps[k] = pv[k];
+
+    // sum over the block of one value per thread, returned to every thread
+    auto block_sum = [&](double v) -> double {
+        v = warp_sum_d(v);
+        if (lane == 0) red[wid] = v;
+        __syncthreads();
+        if (wid == 0) {
+            double u = lane < nw ? red[lane] : 0.0;
+            u = warp_sum_d(u);
+            if (lane == 0) red[32] = u;
+        }
+        __syncthreads();
+        const double tot = red[32];
+        __syncthreads();
+        return tot;
+    };
+    // dst = M^-1 src (src, dst distinct shared vectors)
+    auto precond = [&](const double* src, double* dst) {
+        for (int i = tid; i < Nr; i += blockDim.x) dst[i] = (double)rsc[i] * src[i];
+        __syncthreads();
+        if (tid == 0)
+            for (int k = 0; k < Nr; ++k) {
+                const int p = ps[k];
+                if (p != k) {
+                    const double tmp = dst[k];
+                    dst[k] = dst[p];
+                    dst[p] = tmp;
+                }
+            }
+        __syncthreads();
+        if (wid == 0) {
+            for (int i = 1; i < Nr; ++i) {   // unit lower triangle
+                double a = 0.0;
+                for (int k = lane; k < i; k += 32) a += (double)LU[(int64_t)i * Nr + k] * dst[k];
+                a = warp_sum_d(a);
+                if (lane == 0) dst[i] -= a;
+                __syncwarp();
+            }
+            for (int i = Nr - 1; i >= 0; --i) {   // upper triangle
+                double a = 0.0;
+                for (int k = i + 1 + lane; k < Nr; k += 32) a += (double)LU[(int64_t)i * Nr + k] * dst[k];
+                a = warp_sum_d(a);
+                if (lane == 0) {
+                    const double u = (double)LU[(int64_t)i * Nr + i];
+                    dst[i] = u != 0.0 ? (dst[i] - a) / u : 0.0;
+                }
+                __syncwarp();
+            }
+        }
+        __syncthreads();
+        for (int i = tid; i < Nr; i += blockDim.x) dst[i] *= (double)csc[i];
+        __syncthreads();
+    };
+    // dst = J64 src
+    auto matvec = [&](const double* src, double* dst) {
+        for (int p = wid; p < M; p += nw) {
+            double a = 0.0;
+            for (int j = lane; j < Nr; j += 32) a += GUb[(int64_t)p * Nr + j] * src[j];
+            a = warp_sum_d(a);
+            if (lane == 0) t[p] = a;
+        }
+        __syncthreads();
+        for (int i = wid; i < Nr; i += nw) {
+            double a = 0.0;
+            for (int p = lane; p < M; p += 32) a += d.P[(int64_t)i * M + p] * t[p];
+            for (int j = lane; j < Nr; j += 32)
+                a += (d.Ms[(int64_t)i * Nr + j] * dt_inv + d.Alin[(int64_t)i * Nr + j]) * src[j];
+            a = warp_sum_d(a);
+            if (lane == 0) dst[i] = a;
+        }
+        __syncthreads();
+    };
+
+    for (int i = tid; i < Nr; i += blockDim.x) x[i] = 0.0;
+    __syncthreads();
+    double beta0 = 0.0;
+    for (int cyc = 0; cyc < cycles; ++cyc) {
+        // w = -r - J64 x
+        if (cyc == 0) {
+            for (int i = tid; i < Nr; i += blockDim.x) w[i] = -r[(int64_t)b * Nr + i];
+            __syncthreads();
+        } else {
+            matvec(x, w);
+            for (int i = tid; i < Nr; i += blockDim.x) w[i] = -r[(int64_t)b * Nr + i] - w[i];
+            __syncthreads();
+        }
+        double ss = 0.0;
+        for (int i = tid; i < Nr; i += blockDim.x) ss += w[i] * w[i];
+        const double beta = sqrt(block_sum(ss));
+        if (cyc == 0) beta0 = beta;
+        if (!(beta > eta * beta0) || !(beta > 0.0)) break;   // converged, zero or not finite
+        for (int i = tid; i < Nr; i += blockDim.x) V[i] = w[i] / beta;
+        if (tid == 0) {
+            gv[0] = beta;
+            for (int i = 1; i <= m; ++i) gv[i] = 0.0;
+        }
+        __syncthreads();
+        int kdim = 0;
+        for (int j = 0; j < m; ++j) {
+            precond(V + (size_t)j * Nr, z);
+            matvec(z, w);
+            double* const Hj = H + (size_t)j * (m + 1);
+            for (int pass = 0; pass < 2; ++pass) {
+                for (int i = wid; i <= j; i += nw) {
+                    double a = 0.0;
+                    for (int l = lane; l < Nr; l += 32) a += V[(size_t)i * Nr + l] * w[l];
+                    a = warp_sum_d(a);
+                    if (lane == 0) hy[i] = a;
+                }
+                __syncthreads();
+                for (int l = tid; l < Nr; l += blockDim.x) {
+                    double a = w[l];
+                    for (int i = 0; i <= j; ++i) a -= hy[i] * V[(size_t)i * Nr + l];
+                    w[l] = a;
+                }
+                if (tid == 0)
+                    for (int i = 0; i <= j; ++i) Hj[i] = (pass ? Hj[i] : 0.0) + hy[i];
+                __syncthreads();
+            }
+            double sw = 0.0;
+            for (int l = tid; l < Nr; l += blockDim.x) sw += w[l] * w[l];
+            const double hn = sqrt(block_sum(sw));
+            for (int l = tid; l < Nr; l += blockDim.x) V[(size_t)(j + 1) * Nr + l] = hn > 0.0 ? w[l] / hn : 0.0;
+            if (tid == 0) {
+                Hj[j + 1] = hn;
+                for (int i = 0; i < j; ++i) {   // earlier rotations
+                    const double h0 = Hj[i], h1 = Hj[i + 1];
+                    Hj[i] = cr[i] * h0 + sr[i] * h1;
+                    Hj[i + 1] = -sr[i] * h0 + cr[i] * h1;
+                }
+                const double a0 = Hj[j], a1 = Hj[j + 1];
+                const double rho = hypot(a0, a1);
+                const double c = rho > 0.0 ? a0 / rho : 1.0, sn = rho > 0.0 ? a1 / rho : 0.0;
+                cr[j] = c;
+                sr[j] = sn;
+                Hj[j] = rho;
+                Hj[j + 1] = 0.0;
+                gv[j + 1] = -sn * gv[j];
+                gv[j] = c * gv[j];
+                red[33] = (!(fabs(gv[j + 1]) > eta * beta0) || !(hn > 0.0)) ? 1.0 : 0.0;
+            }
+            __syncthreads();
+            kdim = j + 1;
+            const bool done = red[33] != 0.0;
+            __syncthreads();
+            if (done) break;
+        }
+        // y = H^-1 g (upper triangular, kdim x kdim); x += M^-1 (V y)
+        if (tid == 0)
+            for (int i = kdim - 1; i >= 0; --i) {
+                double a = gv[i];
+                for (int l = i + 1; l < kdim; ++l) a -= H[(size_t)l * (m + 1) + i] * hy[l];
+                const double hii = H[(size_t)i * (m + 1) + i];
+                hy[i] = hii != 0.0 ? a / hii : 0.0;
+            }
+        __syncthreads();
+        for (int l = tid; l < Nr; l += blockDim.x) {
+            double a = 0.0;
+            for (int i = 0; i < kdim; ++i) a += hy[i] * V[(size_t)i * Nr + l];
+            w[l] = a;
+        }
+        __syncthreads();
+        precond(w, z);
+        for (int l = tid; l < Nr; l += blockDim.x) x[l] += z[l];
+        __syncthreads();
+    }
+    // a residual that is not finite gives a step that is not, as the LU path does
+    for (int l = tid; l < Nr; l += blockDim.x) delta[(int64_t)b * Nr + l] = isfinite(beta0) ? x[l] : beta0;
 }
 
 // Step length of all instances: the scaled max-norm of the reconstructed
@@ -1098,7 +1346,11 @@ static int rom_build_host(mb_rom* R, const mb_rom_data* dd) {
         ok = cudaFuncSetAttribute(k_rom_lu<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   ROM_LU_SMEM) == cudaSuccess &&
              cudaFuncSetAttribute(k_rom_lu<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  ROM_LU_SMEM) == cudaSuccess;
+                                  ROM_LU_SMEM) == cudaSuccess &&
+             cudaFuncSetAttribute(k_rom_lu<float, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  ROM_LU_SMEM) == cudaSuccess &&
+             cudaFuncSetAttribute(k_rom_gmres, cudaFuncAttributeMaxDynamicSharedMemorySize, ROM_LU_SMEM) ==
+                 cudaSuccess;
     if (!ok) return cuda_fail(cudaGetLastError(), "rom upload");
     return MB_OK;
 }
@@ -1127,6 +1379,8 @@ static int rom_work_alloc(mb_rom* R, int B) {
     w.G64 = rom_alloc<double>(L, (size_t)B * (d.M ? d.M : 1) * GMAX);
     w.GU64 = rom_alloc<double>(L, (size_t)B * (d.M ? d.M : 1) * d.Nr);
     w.J64 = rom_alloc<double>(L, (size_t)B * d.Nr * d.Nr);
+    w.lpiv = rom_alloc<int>(L, (size_t)B * d.Nr);
+    w.lsc = rom_alloc<float>(L, (size_t)B * 2 * d.Nr);
     w.GU = rom_alloc<float>(L, (size_t)B * (d.M ? d.M : 1) * d.Nr);
     w.prm = rom_alloc<double>(L, (size_t)B * RP);
     w.gate = rom_alloc<uint8_t>(L, (size_t)B * (d.ngate ? d.ngate : 1));
@@ -1219,6 +1473,8 @@ int rom_batch_step(mb_rom* R) {
     const unsigned ge = (unsigned)(((int64_t)d.M * B + 127) / 128);
     const unsigned gt = (unsigned)(((int64_t)(d.ngate ? d.ngate : 1) * B + 255) / 256);
     int hcount = 0;
+    // escalated instances by GMRES on FP64 products (needs the interpolation points and room for the basis)
+    const bool refine = d.ir && d.M > 0 && gmres_smem(d.Nr, d.M, GMRES_M) <= (size_t)ROM_LU_SMEM;
     k_rom_copy<<<nb, 256, 0, s>>>(d.Nr, B, nullptr, w.a, w.a_old), count_launch(c);
     k_rom_gather<<<gg, 256, 0, s>>>(d, w.a_old, w.uloc_old, nullptr), count_launch(c);
     if (d.ngate) k_rom_gate<<<gt, 256, 0, s>>>(d, B, w.uloc_old, w.uloc_old, n_thr, w.gate), count_launch(c);
@@ -1262,12 +1518,19 @@ int rom_batch_step(mb_rom* R) {
                     count_launch(c);
                 }
             }
-            if (hp_any)
+            if (hp_any && !refine)
                 k_rom_jac64<<<dim3((unsigned)d.Nr, (unsigned)nhp), 128, 0, s>>>(d, w.prm, w.GU64, w.active, w.hp,
                                                                                  w.hplist, w.J64), count_launch(c);
             k_rom_resid<<<(unsigned)B, 128, 0, s>>>(d, w.a, w.a_old, w.prm, w.f, w.active, w.r), count_launch(c);
-            launch_rom_lu<float>(d.Nr, B, w.J, w.r, w.active, w.hp, 0, nullptr, w.delta, s), count_launch(c);
-            if (hp_any)
+            launch_rom_lu<float>(d.Nr, B, w.J, w.r, w.active, w.hp, 0, nullptr, w.delta, s,
+                                 refine ? w.lpiv : nullptr, refine ? w.lsc : nullptr),
+                count_launch(c);
+            if (hp_any && refine)
+                k_rom_gmres<<<(unsigned)nhp, 256, gmres_smem(d.Nr, d.M, GMRES_M), s>>>(
+                    d, w.prm, w.GU64, w.r, w.J, w.lpiv, w.lsc, w.active, w.hp, w.hplist, GMRES_M, GMRES_CYCLES,
+                    GMRES_ETA, w.delta),
+                    count_launch(c);
+            else if (hp_any)
                 launch_rom_lu<double>(d.Nr, nhp, w.J64, w.r, w.active, w.hp, 1, w.hplist, w.delta, s),
                     count_launch(c);
             {
@@ -1493,6 +1756,12 @@ extern "C" int mb_debug_rom_lu(int Nr, int B, int fp64, int in_place, const doub
     }
     return fp64 ? debug_rom_lu<double>(Nr, B, in_place, J, r, delta)
                 : debug_rom_lu<float>(Nr, B, in_place, J, r, delta);
+}
+
+extern "C" int mb_debug_rom_refine(mb_rom* R, int on) {
+    if (!R) return MB_EINVAL;
+    R->d.ir = on ? 1 : 0;
+    return MB_OK;
 }
 
 extern "C" int mb_debug_rom_tensor(mb_rom* R, int on) {

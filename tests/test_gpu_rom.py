@@ -191,3 +191,27 @@ def test_rom_newton_step_lu_kernel(Nr, fp64, in_place):
         # error of a backward-stable solve: ~ cond(equilibrated J) * unit roundoff
         tol = 1e-9 if fp64 else 2e-3
         assert np.max(np.abs(d[b] - ref)) <= tol * scale, (b, np.max(np.abs(d[b] - ref)) / scale)
+
+
+@pytest.mark.gpu
+def test_rom_refine_matches_oracle(params, wide_case):
+    """Escalated instances by GMRES on FP64 products, preconditioned by the FP32 LU
+    kept from their last FP32-matrix iteration: the 112-mode model (whose FP32 matrix
+    cannot converge, so instances escalate) reaches the oracle's trajectory at 1e-9
+    and the FP64-LU path's."""
+    B = _gpu()
+    lab, oc, rom = wide_case
+    gc, g = _gpu_rom(B, lab, params, rom)
+    prm = [(c * oc.i_1c, s, k) for (c, s, k) in [(-3.0, 1.1, 0.7), (-1.5, 0.8, 2.0), (-4.5, 0.6, 4.0)]]
+    g.debug_refine(False)
+    lu = g.solve(prm, 3, 1.0)
+    g.debug_refine(True)
+    out = g.solve(prm, 3, 1.0)
+    assert out["ok"] and out["failed"] == 0
+    for b, p in enumerate(prm):
+        ref = R.solve(rom, p[0], p[1], p[2], 1.0, 3)
+        assert np.max(np.abs(out["V"][b] - ref["V_cell"])) <= 1e-9 * np.max(np.abs(ref["V_cell"])), b
+        assert np.max(np.abs(out["s_ac"][b] - ref["s_ac"])) <= 1e-9 * np.max(np.abs(ref["s_ac"])), b
+    assert np.max(np.abs(out["V"] - lu["V"])) <= 1e-9 * np.max(np.abs(lu["V"]))
+    g.close()
+    gc.close()
