@@ -21,14 +21,16 @@
 // the residual are FP64, so the converged solution is the FP64 one; the
 // Newton matrix (GU, the contraction P GU as one GEMM over all instances on
 // the tensor cores with FP32 accuracy, its LU) and the step-length norm are
-// FP32 (an inexact Newton iteration:
-// GB300's FP64 rate is a small fraction of its FP32 rate).  An instance
-// switches to an FP64 Newton matrix (FP64 derivatives, G U_loc, contraction
-// and LU) for the rest of its time step when its iteration stagnates (a full
-// step whose norm fell by less than 10 %, from the third iteration of a
-// pass) or has not converged after ROM_HP_AFTER iterations: an FP32 matrix
-// cannot converge when the equilibrated reduced Jacobian's condition number
-// approaches 1/eps_32 (POD modes kept down to tiny singular values).
+// FP32 (an inexact Newton iteration: GB300's FP64 rate is a small fraction of
+// its FP32 rate).  An instance escalates for the rest of its time step when
+// its iteration stagnates (a full step whose norm fell by less than 10 %,
+// from the third iteration of a pass) or has not converged after
+// ROM_HP_AFTER iterations: an FP32 matrix cannot converge when the
+// equilibrated reduced Jacobian's condition number approaches 1/eps_32 (POD
+// modes kept down to tiny singular values).  Escalated: FP64 derivatives and
+// G U_loc, then the Newton step by GMRES on FP64 products preconditioned by
+// the instance's FP32 LU kept from its last FP32-matrix iteration (ir, the
+// default), or by an FP64 Newton matrix and LU.
 #include <cuda_runtime.h>
 #include <math.h>
 
@@ -91,7 +93,7 @@ struct RomWork {
     double *uloc = nullptr, *uloc_old = nullptr, *f = nullptr;
     float* G = nullptr;        // B x M x GMAX derivative lists (FP32: they only feed the Newton matrix)
     float* dpart = nullptr;    // B x ceil(nloc / UN_K): partial maxima of the step-length norm
-    int* hp = nullptr;         // B: instance uses the FP64 Newton matrix (for the rest of the time step)
+    int* hp = nullptr;         // B: instance has escalated to FP64 (for the rest of the time step)
     int* pit = nullptr;        // B: iterations in the current pass
     float* dnprev = nullptr;   // B: step norm of the previous iteration
     double* G64 = nullptr;     // B x M x GMAX   FP64 derivative lists of the hp instances
@@ -961,7 +963,7 @@ k_rom_apply(RomDev d, int nkt, double* __restrict__ a, const double* __restrict_
     }
 }
 
-// out[0] = active instances, out[1] = instances on the FP64 Newton matrix
+// out[0] = active instances, out[1] = escalated (FP64) instances
 // (active or not), listed in list[0, out[1]) (one block; the list's order
 // does not matter: every instance's arithmetic is its own)
 // out[2] = active instances on the FP32 matrix, listed in alist[0, out[2])
@@ -1484,7 +1486,7 @@ int rom_batch_step(mb_rom* R) {
         k_rom_copy<<<nb, 256, 0, s>>>(d.Nr, B, w.pass_on, w.a_old, w.a), count_launch(c);
         k_rom_set_active<<<bb, 256, 0, s>>>(B, w.pass_on, w.failed, w.active, w.pit, nullptr), count_launch(c);
         for (int it = 0; it < ROM_MAXIT; ++it) {
-            // FP64 Newton-matrix kernels only while some instance uses them (hp only turns on
+            // escalated-instance kernels only while some instance uses them (hp only turns on
             // within a step, so the count of the previous iteration covers this one)
             const int nhp = w.hp_any;
             const bool hp_any = nhp > 0;
