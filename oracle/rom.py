@@ -57,10 +57,17 @@ the unknown scales (c_ref, 1 V, n_c), stop after the first update with
 lam ||U_loc delta||_s <= tol.  The reduced linear systems are solved by LU
 after row and column equilibration.
 
+7. The hierarchical a-posteriori error estimate (Eq. ap4:estimate): the
+   distance of the reduced model's reconstruction from a larger validation
+   model's, per field and time step, scaled by 1/(1 - theta).
+
 Parity status: pinned by tests/test_oracle_rom.py (the split reproduces the
 full-order residual; the EI identity at the points; a ROM whose bases and EI
 spaces contain the training trajectory reproduces that trajectory; rest-state
-invariance at zero current; the reduced residual is affine in mu).  The
+invariance at zero current; the reduced residual is affine in mu; the error
+estimate is the L^2 norm of a constant field in closed form, scales as
+1/(1 - theta), vanishes for identical models and equals the true error when
+the validation model reproduces the full-order trajectory).  The
 accuracy of a truncated ROM against the full-order model is not pinned by the
 paper for these inputs (parity unpinned for that comparison).
 """
@@ -340,6 +347,31 @@ def build(cell, snaps, dims, pod_tol=1e-10, ei_tol=1e-12):
     rom.Uloc = U[rom.closure, :]
     rom.us_loc = cell.unknown_scale()[rom.closure]
     return rom
+
+
+def error_estimate(rom, rom_val, A, A_val, theta=0.0):
+    """Hierarchical a-posteriori error estimate of Sec. workflow:MOR (Eqs.
+    ap4:saturation and ap4:estimate): per time step n,
+        e_c[n]   = ||c~_n - c^_n|| / (1 - theta),
+        e_phi[n] = ||phi~_n - phi^_n|| / (1 - theta),
+    where (c~, phi~) = U a is the reconstruction of the reduced model and
+    (c^, phi^) = U^ a^ that of a larger validation model (V~ within V^ and
+    larger interpolation bases) over the same steps, and || || is the L^2
+    norm of the voxel grid (weight V per voxel value: the inner product the
+    POD uses).  Under the saturation assumption with constant theta in [0, 1)
+    these bound the reduced model's errors against the full-order solution.
+    e_n is the same difference of the plated-Li inventory (weight A per face
+    value), a state the paper's estimate does not have.  A and A_val are the
+    coefficient trajectories, shapes (steps, N_r) and (steps, N_r^)."""
+    if not 0.0 <= theta < 1.0:
+        raise ValueError("theta must lie in [0, 1)")
+    cell = rom.cell
+    N = cell.N
+    w = weights(cell)
+    D = np.atleast_2d(A) @ rom.U.T - np.atleast_2d(A_val) @ rom_val.U.T   # steps x unknowns
+    s = 1.0 / (1.0 - theta)
+    blocks = {"c": slice(0, N), "phi": slice(N, 2 * N), "n": slice(2 * N, None)}
+    return {k: s * np.sqrt(np.sum(w[b] * D[:, b] ** 2, axis=1)) for k, b in blocks.items()}
 
 
 def stencil_closure(cell, points):

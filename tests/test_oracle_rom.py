@@ -114,3 +114,67 @@ def test_pod_bases_are_w_orthonormal(trained):
     w = R.weights(cell)
     G = rom.U.T @ (w[:, None] * rom.U)
     assert np.allclose(G, np.eye(G.shape[0]), atol=1e-10)
+
+
+def test_error_estimate_norm_of_a_constant_field(tiny):
+    """The estimate's norm is the L^2 norm of the voxel grid: two models whose
+    reconstructions differ by a constant delta in one field give delta times the
+    square root of that field's measure (N V for c and phi, F A for the plated Li)
+    in that field and zero in the others, scaled by 1/(1 - theta) (Eq. ap4:estimate)."""
+    cell = tiny
+    N, F = cell.N, cell.F_pl
+    n = cell.n_unknowns
+
+    class M:
+        pass
+
+    zero = M()
+    zero.cell, zero.U = cell, np.zeros((n, 1))
+    for name, sl, measure in (("c", slice(0, N), N * cell.V), ("phi", slice(N, 2 * N), N * cell.V),
+                              ("n", slice(2 * N, n), F * cell.A)):
+        ind = M()
+        ind.cell = cell
+        ind.U = np.zeros((n, 1))
+        ind.U[sl, 0] = 1.0
+        delta = np.array([[0.0], [2.5], [-7.0]])
+        for theta in (0.0, 0.5, 0.9):
+            est = R.error_estimate(zero, ind, np.zeros((3, 1)), delta, theta)
+            expect = np.abs(delta[:, 0]) * np.sqrt(measure) / (1.0 - theta)
+            assert np.allclose(est[name], expect, rtol=1e-14, atol=0.0), (name, theta)
+            for other in {"c", "phi", "n"} - {name}:
+                assert np.all(est[other] == 0.0)
+    with pytest.raises(ValueError):
+        R.error_estimate(zero, zero, np.zeros((1, 1)), np.zeros((1, 1)), 1.0)
+
+
+def test_error_estimate_is_the_error_for_an_exact_validation_model(trained):
+    """With theta = 0 and a validation model that reproduces the full-order
+    trajectory (bases and EI spaces spanning it), the estimate is the reduced
+    model's true error up to the validation model's own error: by the triangle
+    inequality | ||c~ - c^|| - ||c~ - c|| | <= ||c^ - c|| (Eq. ap4:estimate with
+    its saturation assumption met); identical models estimate zero."""
+    cell, mu, snaps, traj, full = trained
+    w = R.weights(cell)
+    N = cell.N
+    full.a0 = full.U.T @ (w * traj[0])
+    of = R.solve(full, mu, 1.0, 1.0, 1.0, len(traj) - 1)
+    small = R.build(cell, snaps, (4, 3, 8, 8), pod_tol=1e-15, ei_tol=1e-14)
+    small.a0 = small.U.T @ (w * traj[0])
+    os_ = R.solve(small, mu, 1.0, 1.0, 1.0, len(traj) - 1)
+    est = R.error_estimate(small, full, os_["a"], of["a"])
+
+    def dist(u, v, sl):
+        d = (u - v)[sl]
+        return float(np.sqrt(np.dot(w[sl] * d, d)))
+
+    for n in range(len(traj)):
+        u_s, u_v = small.U @ os_["a"][n], full.U @ of["a"][n]
+        for key, sl in (("c", slice(0, N)), ("phi", slice(N, 2 * N))):
+            true = dist(u_s, traj[n], sl)
+            val = dist(u_v, traj[n], sl)
+            assert abs(est[key][n] - true) <= val + 1e-14 * dist(traj[n], 0 * traj[n], sl), (key, n)
+    # a real truncation error, far above the validation model's
+    assert np.all(est["c"][1:] > 1e3 * max(dist(full.U @ of["a"][n], traj[n], slice(0, N))
+                                           for n in range(len(traj))))
+    same = R.error_estimate(small, small, os_["a"], os_["a"])
+    assert all(np.all(v == 0.0) for v in same.values())
