@@ -361,11 +361,11 @@ k_rom_jac(RomDev d, int B, int nlist, const int* __restrict__ alist, const doubl
                 uint32_t ab[2][4], as_[2][4], bb[2][2], bs_[2][2];
 #pragma unroll
                 for (int mi = 0; mi < 2; ++mi) {
-                    const int rb = wr * 32 + mi * 16;
-                    tf32_split(As[ks + t][rb + g], ab[mi][0], as_[mi][0]);
-                    tf32_split(As[ks + t][rb + g + 8], ab[mi][1], as_[mi][1]);
-                    tf32_split(As[ks + t + 4][rb + g], ab[mi][2], as_[mi][2]);
-                    tf32_split(As[ks + t + 4][rb + g + 8], ab[mi][3], as_[mi][3]);
+                    const int r0 = wr * 32 + mi * 16;
+                    tf32_split(As[ks + t][r0 + g], ab[mi][0], as_[mi][0]);
+                    tf32_split(As[ks + t][r0 + g + 8], ab[mi][1], as_[mi][1]);
+                    tf32_split(As[ks + t + 4][r0 + g], ab[mi][2], as_[mi][2]);
+                    tf32_split(As[ks + t + 4][r0 + g + 8], ab[mi][3], as_[mi][3]);
                 }
 #pragma unroll
                 for (int ni = 0; ni < 2; ++ni) {
@@ -419,7 +419,7 @@ k_rom_jac(RomDev d, int B, int nlist, const int* __restrict__ alist, const doubl
             if (c >= ncol || i >= Nr) continue;
             const int l = c / Nr, j = c - l * Nr;
             const int b = alist ? alist[l] : l;
-            if (hp[b]) continue;   // its Newton matrix is the FP64 one
+            if (hp[b]) continue;   // escalated: J[b] keeps the LU factors of its last FP32 iteration
             const float dt_inv = (float)prm[RP * b + 3];
             J[((int64_t)b * Nr + i) * Nr + j] =
                 acc[r][q] + d.Msf[(int64_t)i * Nr + j] * dt_inv + d.Alinf[(int64_t)i * Nr + j];
@@ -488,7 +488,7 @@ k_rom_resid(RomDev d, const double* __restrict__ a, const double* __restrict__ a
 // delta[b] = -J[b]^-1 r[b] in the precision T of J (r and delta FP64): row
 // then column equilibration, LU with partial pivoting (ties: lowest row),
 // forward elimination of the right-hand side during the factorisation (so the
-// L factor is never stored), back substitution.  One block per instance; the
+// L factor is stored only with KEEP), back substitution.  One block per instance; the
 // matrix is copied to shared memory (SMEM, lu_smem(Nr, sizeof(T)) <=
 // ROM_LU_SMEM, opt-in above 48 KB, set at mb_rom_create) or factorised in place
 // in J.  Per column k: warp 0 reduces the per-warp pivot candidates, all threads
