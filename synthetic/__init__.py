@@ -2,8 +2,8 @@
 
 This package holds input generation only: a counter-based PRNG (SplitMix64),
 Boolean-sphere voxel microstructures, small hand-made label grids for the
-closed-form tests, parameter-study samplers, and the loader of the parameter
-table (``params.json``).  It contains none of the method's arithmetic (no
+closed-form tests, parameter-study samplers, the germ-grain initial plated
+lithium (``plating``), and the loader of the parameter table (``params.json``).  It contains none of the method's arithmetic (no
 flux, kinetics, time stepping, reduction or 1C conversion); each side of the
 parity check implements those on its own.
 
