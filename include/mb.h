@@ -263,8 +263,14 @@ int mb_rom_destroy(mb_rom* rom);
  * coefficients (may be NULL).  Newton per step and instance: step length
  * min(1, 0.25 / |U_loc delta|_s) on the stencil closure of the points,
  * converged at lam |U_loc delta|_s <= 1e-12, at most 30 iterations;
- * plating active-set passes as mb_step (at most 3).  Returns MB_ENOCONV if
- * some instance failed (its outputs are then NaN from that step on). */
+ * plating active-set passes as mb_step (at most 3).  The state, the
+ * interpolated terms and the residual are FP64 (the converged result is the
+ * FP64 one); the Newton matrix is formed with FP32 accuracy (three TF32
+ * tensor-core products per operand pair) and factorised in FP32; an instance
+ * whose iteration stagnates, or that has not converged after 8 iterations,
+ * takes its Newton steps for the rest of the time step by FP64 GMRES
+ * preconditioned with its last FP32 LU.  Returns MB_ENOCONV if some instance
+ * failed (its outputs are then NaN from that step on). */
 int mb_rom_solve_batch(mb_rom* rom, int B, const mb_rom_params* prm, int n_steps, double dt, double* V_out,
                        double* sac_out, double* a_final, mb_rom_info* info);
 
