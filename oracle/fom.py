@@ -58,7 +58,8 @@ the step is re-solved from u_old if any face flipped (at most 3 passes).
 Parity status: pinned by tests/test_oracle_fom.py (closed forms T1, T2, T4,
 T5, T6, rest-state invariance T3, Li conservation T7, affine-in-current T9,
 mirror symmetry T10, and the complex-step Jacobian against central
-differences T8).
+differences T8) and tests/test_oracle_pins.py (the cathode's Butler-Volmer
+face in closed form and its small-current linearisation).
 """
 import numpy as np
 import scipy.sparse as sp

@@ -67,7 +67,10 @@ spaces contain the training trajectory reproduces that trajectory; rest-state
 invariance at zero current; the reduced residual is affine in mu; the error
 estimate is the L^2 norm of a constant field in closed form, scales as
 1/(1 - theta), vanishes for identical models and equals the true error when
-the validation model reproduces the full-order trajectory).  The
+the validation model reproduces the full-order trajectory) and by
+tests/test_oracle_pins.py (EI-Greedy's selection sequence on a hand-worked
+training matrix with ties; POD truncation keeps the dominant directions of a
+snapshot matrix built from known singular values).  The
 accuracy of a truncated ROM against the full-order model is not pinned by the
 paper for these inputs (parity unpinned for that comparison).
 """
