@@ -91,13 +91,20 @@ typedef struct {
                               at least one tile of 256 cells per SM stage rows, right-hand side and
                               iterate in shared memory by bulk asynchronous copies (persistent,
                               double-buffered) */
+    int    pass_start;     /* Newton start of plating active-set passes after the first: 0 u_old
+                              (the previous time level); 1 (default) the previous pass's converged
+                              state.  The solution of a pass depends only on its frozen gates, not on
+                              the start. */
 } mb_solver_opts;
 
 typedef struct {
     int    newton_its;     /* summed over passes and sub-steps */
     int    krylov_its;
     int    passes;
-    int    flips;          /* plating gates flipped between passes */
+    int    flips;          /* plating gates flipped between passes (re-solved) */
+    int    unresolved_flips; /* gates that still flipped after the last allowed pass: the accepted
+                              state is then not consistent with its gates on these faces (0 when
+                              the active set settled) */
     int    halvings;
     double dt_used;
     double V_cell;         /* mean Phi over the t = nt-1 collector layer (s_cp) */
@@ -345,7 +352,8 @@ int mb_serve_destroy(mb_server* srv);
  * device share the one scratch array, so calls that overlap in time (other
  * threads, other streams, other cells) race: order them on one stream or on
  * the host.  MB_EINVAL for a cell with more than MB_NOALLOC_MAX_FACES plating
- * faces or an invalid argument; MB_ECUDA on a CUDA error.  A failing call
+ * faces, when the current device is not the cell's, or for an invalid
+ * argument; MB_ECUDA on a CUDA error.  A failing call
  * stores its message for mb_last_error in host memory. */
 #define MB_NOALLOC_MAX_FACES 4194304
 int mb_residual_dev_noalloc(mb_cell* cell, const double* u, const double* u_old, double dt, double I_app,

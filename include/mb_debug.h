@@ -68,6 +68,11 @@ int mb_debug_rom_tensor(mb_rom* rom, int on);
 int mb_debug_residual_split(mb_cell* cell, const double* u, const double* u_old, const uint8_t* gate,
                             double dt, double I_app, double* r);
 
+/* Full-order cells of a server: alive now, the most alive at one time since
+ * mb_serve_create, and the measured device memory of one cell (0 before the
+ * first cell exists). */
+int mb_debug_serve_cells(mb_server* srv, int* alive, int* peak, int64_t* cell_bytes);
+
 #ifdef __cplusplus
 }
 #endif

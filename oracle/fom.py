@@ -463,7 +463,8 @@ class Cell:
                 break
             flips += nflip
             gate = g2
-        info = dict(newton_its=its, passes=npass, flips=flips, gate=gate)
+        unresolved = nflip if nflip and npass == max_passes else 0
+        info = dict(newton_its=its, passes=npass, flips=flips, unresolved_flips=unresolved, gate=gate)
         info.update(self.functionals(u))
         return u, info
 

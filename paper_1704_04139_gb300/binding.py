@@ -39,12 +39,14 @@ class SolverOpts(C.Structure):
                 ("gmres_m", C.c_int), ("krylov_maxit", C.c_int), ("krylov_rtol", C.c_double),
                 ("max_passes", C.c_int), ("max_halvings", C.c_int), ("mg_coarse_cells", C.c_int),
                 ("mg_smooth", C.c_int), ("mg_kcycle", C.c_int), ("mg_coarse_pre", C.c_int),
-                ("mg_coarse_post", C.c_int), ("mg_bf16", C.c_int), ("mg_stream", C.c_int)]
+                ("mg_coarse_post", C.c_int), ("mg_bf16", C.c_int), ("mg_stream", C.c_int),
+                ("pass_start", C.c_int)]
 
 
 class StepInfo(C.Structure):
     _fields_ = [("newton_its", C.c_int), ("krylov_its", C.c_int), ("passes", C.c_int),
-                ("flips", C.c_int), ("halvings", C.c_int), ("dt_used", C.c_double),
+                ("flips", C.c_int), ("unresolved_flips", C.c_int), ("halvings", C.c_int),
+                ("dt_used", C.c_double),
                 ("V_cell", C.c_double), ("mean_c_solid", C.c_double), ("Li_total", C.c_double),
                 ("Li_anode", C.c_double), ("Li_plated", C.c_double), ("res_norm", C.c_double)]
 
@@ -130,6 +132,7 @@ def _declare(lib):
     fn("mb_serve_submit", C.c_int, [VP, C.POINTER(Request), C.POINTER(C.c_uint64)])
     fn("mb_serve_poll", C.c_int, [VP, C.c_uint64, C.POINTER(Result)])
     fn("mb_serve_destroy", C.c_int, [VP])
+    fn("mb_debug_serve_cells", C.c_int, [VP, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int64)])
     fn("mb_rom_dims", C.c_int, [VP, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)])
     fn("mb_rom_solve_batch", C.c_int, [VP, C.c_int, C.POINTER(RomParams), C.c_int, C.c_double, VP, VP, VP,
                                         C.POINTER(RomInfo)])
@@ -489,6 +492,12 @@ class Server:
         _check(rc)
         del self._n[ticket]
         return dict(status=res.status, V=V, s_ac=S, t_submit=res.t_submit, t_start=res.t_start, t_done=res.t_done)
+
+    def debug_cells(self):
+        """(alive, peak, cell_bytes) of the server's full-order cells."""
+        a, p, cb = C.c_int(), C.c_int(), C.c_int64()
+        _check(lib().mb_debug_serve_cells(self.h, C.byref(a), C.byref(p), C.byref(cb)))
+        return a.value, p.value, cb.value
 
     def close(self):
         if getattr(self, "h", None):

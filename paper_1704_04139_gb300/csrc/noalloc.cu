@@ -23,10 +23,9 @@ static __device__ __align__(256) uint8_t g_gate_scratch[MB_NOALLOC_MAX_FACES];
 constexpr int MAX_DEVICES = 64;
 std::atomic<uint8_t*> g_scratch_addr[MAX_DEVICES];
 
-// Address of the scratch array on the current device, resolved once per device.
-int scratch_address(uint8_t** out) {
-    int dev = -1;
-    MB_CUDA(cudaGetDevice(&dev));
+// Address of the scratch array on device dev (the current device), resolved
+// once per device.
+int scratch_address(int dev, uint8_t** out) {
     if (dev < 0 || dev >= MAX_DEVICES) {
         ::mb::set_error("mb_residual_dev_noalloc: device index out of range");
         return MB_EINVAL;
@@ -56,8 +55,16 @@ extern "C" int mb_residual_dev_noalloc(mb_cell* c, const double* u, const double
                         "holds (MB_NOALLOC_MAX_FACES)");
         return MB_EINVAL;
     }
+    // the cell's buffers live on c->device: the scratch address and the
+    // launches must be those of that device
+    int dev = -1;
+    MB_CUDA(cudaGetDevice(&dev));
+    if (dev != c->device) {
+        ::mb::set_error("mb_residual_dev_noalloc: the current device is not the cell's device");
+        return MB_EINVAL;
+    }
     uint8_t* gate = nullptr;
-    int rc = scratch_address(&gate);
+    int rc = scratch_address(dev, &gate);
     if (rc) return rc;
     cudaStream_t s = (cudaStream_t)stream;
     rc = ::mb::launch_gate_residual_unprofiled(c, u, u_old, gate, dt, I_app, r, s);

@@ -39,6 +39,7 @@
 #include <math.h>
 #include <stdio.h>
 
+#include <atomic>
 #include <vector>
 
 #include "mb_internal.h"
@@ -152,6 +153,10 @@ struct Precond {
     double* kH = nullptr;      // (KCYC_MAX+1) x KCYC_MAX + scalars
     double* kred = nullptr;    // RED_BLOCKS x 8 partials
 };
+
+// set when a staged sweep timed out and could not drain its bulk copies: the
+// plain sweep is used from then on in this process
+static std::atomic<bool> g_staged_broken{false};
 
 static const dim3 PB(32, 8, 1);
 static inline dim3 pgrid(int nt, int ny, int nz) { return dim3((nz + 31) / 32, (ny + 7) / 8, nt); }
@@ -1068,8 +1073,10 @@ k_lvl_smooth_staged(Level L, const DF4* __restrict__ x_in, const DF4* __restrict
         if (!ok) {
             if (tid == 0) {
                 atomicOr(err, 1);
+                // drain the copies in flight; if that wait gives up too, copies
+                // may still land in this CTA's shared memory after it exits
                 for (int k = 0; k < 2; ++k)
-                    if (pending[k]) mbar_wait_bounded(&bar[k], parity[k]);
+                    if (pending[k] && !mbar_wait_bounded(&bar[k], parity[k])) atomicOr(err, 2);
             }
             return;
         }
@@ -1464,7 +1471,7 @@ static void lvl_smooth(mb_cell* c, Level& L, const DF4* xin, const DF4* ec, int 
     if (timed) prof_begin(c, s, &ev);
     const Precond* p = c->pc;
     const int64_t ntiles = (L.cells + SWT - 1) / SWT;
-    if (p->b16 && c->opt.mg_stream == 2 && xin && ntiles >= p->nsm)
+    if (p->b16 && c->opt.mg_stream == 2 && xin && ntiles >= p->nsm && !g_staged_broken.load())
         k_lvl_smooth_staged<<<p->nsm, SWT, SW_SMEM, s>>>(L, xin, ec, ccny, ccnz, OMEGA_COARSE, xout, p->err);
     else if (p->b16)
         k_lvl_smooth<true><<<g, 256, 0, s>>>(L, xin, ec, ccny, ccnz, OMEGA_COARSE, xout,
@@ -1657,10 +1664,20 @@ static void fine_product(mb_cell* c, const float2* zin, float* tout) {
 }
 
 int precond_check(mb_cell* c) {
+    Precond* p = c->pc;
     int h = 0;
-    MB_CUDA(cudaMemcpyAsync(&h, c->pc->err, 4, cudaMemcpyDeviceToHost, c->stream));
+    MB_CUDA(cudaMemcpyAsync(&h, p->err, 4, cudaMemcpyDeviceToHost, c->stream));
     MB_CUDA(cudaStreamSynchronize(c->stream));
     if (h) {
+        MB_CUDA(cudaMemsetAsync(p->err, 0, 4, c->stream));
+        if (h & 2) {
+            // a staged sweep could not drain its copies: never launch it again in
+            // this process; the graphs that contain it are captured anew
+            g_staged_broken.store(true);
+            for (auto& G : p->graphs) graph_free(G);
+            p->graphs.clear();
+            p->pending = -1;
+        }
         set_error("preconditioner: a bounded wait for staged operator data gave up");
         return MB_ETIMEOUT;
     }

@@ -44,6 +44,8 @@ struct mb_server {
     bool stop = false;
     int64_t fom_bytes = 0;         // device memory of running full-order cells
     int64_t fom_cell_bytes = 0;    // per cell (measured on the first one)
+    bool measuring = false;        // a worker is creating the first cell (its size is not known yet)
+    int fom_cells = 0, fom_cells_peak = 0;   // full-order cells alive now / at most
     std::thread rom_thread;
     std::vector<std::thread> fom_threads;
     std::chrono::steady_clock::time_point t0;
@@ -145,44 +147,60 @@ double cell_potential(mb_cell* c) {
 // A worker keeps the cell it created for its first request and resets its
 // state for the next ones (no device allocation or release, which would
 // synchronise the device, in steady state).  A worker without a cell is
-// admitted while the cells' device memory stays within the budget.
+// admitted while the cells' device memory stays within the budget; until the
+// first cell has been created and measured, only one worker at a time may
+// create one (its size is charged once known), and one cell is always allowed.
+bool fom_admit(const mb_server* S, bool has_cell) {
+    if (has_cell) return true;
+    if (S->measuring) return false;
+    if (S->fom_cells == 0) return true;
+    if (S->fom_cell_bytes == 0) return false;
+    return S->fom_bytes + S->fom_cell_bytes <= S->o.fom_budget_bytes;
+}
+
 void fom_loop(mb_server* S) {
     cudaSetDevice(S->device);
     mb_cell* c = nullptr;
     int64_t charged = 0;   // this worker's share of fom_bytes
     for (;;) {
         std::shared_ptr<Req> q;
+        bool measure = false;
         {
             std::unique_lock<std::mutex> lk(S->m);
-            S->cv.wait(lk, [&]() {
-                return S->stop || (!S->fom_q.empty() &&
-                                   (c || S->fom_bytes == 0 || S->fom_bytes + S->fom_cell_bytes <= S->o.fom_budget_bytes));
-            });
+            S->cv.wait(lk, [&]() { return S->stop || (!S->fom_q.empty() && fom_admit(S, c != nullptr)); });
             if (S->stop) break;
             q = S->fom_q.front();
             S->fom_q.pop_front();
             if (!c) {
+                measure = S->fom_cell_bytes == 0;
+                if (measure) S->measuring = true;
                 charged = S->fom_cell_bytes;
                 S->fom_bytes += charged;
+                S->fom_cells += 1;
+                if (S->fom_cells > S->fom_cells_peak) S->fom_cells_peak = S->fom_cells;
             }
             q->t_start = S->now();
         }
         int rc = MB_OK;
         if (!c) {
             rc = mb_cell_create(S->labels.data(), S->o.nt, S->o.ny, S->o.nz, S->o.h, &S->prm, &S->fopts, &c);
-            if (!rc) {
-                mb_cell_info info;
-                mb_cell_info_get(c, &info);
+            {
                 std::lock_guard<std::mutex> lk(S->m);
-                if (!S->fom_cell_bytes) S->fom_cell_bytes = info.device_bytes;
-                S->fom_bytes += info.device_bytes - charged;
-                charged = info.device_bytes;
-            } else {
-                c = nullptr;
-                std::lock_guard<std::mutex> lk(S->m);
-                S->fom_bytes -= charged;
-                charged = 0;
+                if (!rc) {
+                    mb_cell_info info;
+                    mb_cell_info_get(c, &info);
+                    if (!S->fom_cell_bytes) S->fom_cell_bytes = info.device_bytes;
+                    S->fom_bytes += info.device_bytes - charged;
+                    charged = info.device_bytes;
+                } else {
+                    c = nullptr;
+                    S->fom_bytes -= charged;
+                    S->fom_cells -= 1;
+                    charged = 0;
+                }
+                if (measure) S->measuring = false;
             }
+            S->cv.notify_all();
         } else {
             rc = mb::launch_init_state(c, c->u);
             if (!rc && cudaStreamSynchronize(c->stream) != cudaSuccess)
@@ -211,6 +229,7 @@ void fom_loop(mb_server* S) {
         mb_cell_destroy(c);
         std::lock_guard<std::mutex> lk(S->m);
         S->fom_bytes -= charged;
+        S->fom_cells -= 1;
     }
 }
 
@@ -296,5 +315,15 @@ extern "C" int mb_serve_destroy(mb_server* S) {
     for (auto& t : S->fom_threads)
         if (t.joinable()) t.join();
     delete S;
+    return MB_OK;
+}
+
+// ------------------------------------------------------------ test hooks
+extern "C" int mb_debug_serve_cells(mb_server* S, int* alive, int* peak, int64_t* cell_bytes) {
+    if (!S || !alive || !peak || !cell_bytes) { set_error("mb_debug_serve_cells: invalid argument"); return MB_EINVAL; }
+    std::lock_guard<std::mutex> lk(S->m);
+    *alive = S->fom_cells;
+    *peak = S->fom_cells_peak;
+    *cell_bytes = S->fom_cell_bytes;
     return MB_OK;
 }

@@ -395,11 +395,13 @@ void krylov_destroy(mb_cell* c) {
 
 static constexpr double DELTA_MAX = 0.25;
 
-// Newton with frozen gates from c->u_old; c->u holds the result.
-static int newton(mb_cell* c, double dt, double I_app, int* its_out, int* kits, double* rnorm_out, bool* ok) {
+// Newton with frozen gates for the step from c->u_old; c->u holds the start
+// (from_old: u_old) and the result.
+static int newton(mb_cell* c, double dt, double I_app, bool from_old, int* its_out, int* kits, double* rnorm_out,
+                  bool* ok) {
     int64_t n = c->n;
     cudaStream_t s = c->stream;
-    MB_CUDA(cudaMemcpyAsync(c->u, c->u_old, 8 * n, cudaMemcpyDeviceToDevice, s));
+    if (from_old) MB_CUDA(cudaMemcpyAsync(c->u, c->u_old, 8 * n, cudaMemcpyDeviceToDevice, s));
     *ok = false;
     for (int it = 1; it <= c->opt.newton_maxit; ++it) {
         int rc = launch_residual_split(c, c->u, c->u_old, c->gate, dt, I_app, c->r, s);
@@ -452,7 +454,11 @@ static int try_step(mb_cell* c, double dt, double I_app, mb_step_info* info, boo
         int its = 0;
         double rn = 0;
         bool nok = false;
-        rc = newton(c, dt, I_app, &its, &info->krylov_its, &rn, &nok);
+        // passes after the first start from the previous pass's converged state
+        // when pass_start = 1 (the solution under the new gates differs from it
+        // only near the flipped faces)
+        const bool from_old = pass == 1 || c->opt.pass_start == 0;
+        rc = newton(c, dt, I_app, from_old, &its, &info->krylov_its, &rn, &nok);
         if (rc) return rc;
         info->newton_its += its;
         info->passes = pass;
@@ -463,7 +469,13 @@ static int try_step(mb_cell* c, double dt, double I_app, mb_step_info* info, boo
         if (rc) return rc;
         int64_t flips = 0;
         if ((rc = count_diff_u8(c, c->gate, c->gate2, F, &flips))) return rc;
-        if (flips == 0 || pass == c->opt.max_passes) { *ok = true; return MB_OK; }
+        if (flips == 0) { *ok = true; return MB_OK; }
+        if (pass == c->opt.max_passes) {
+            // accepted with the last pass's gates; the faces that still flip are reported
+            info->unresolved_flips += (int)flips;
+            *ok = true;
+            return MB_OK;
+        }
         info->flips += (int)flips;
         MB_CUDA(cudaMemcpyAsync(c->gate, c->gate2, F, cudaMemcpyDeviceToDevice, s));
     }
@@ -480,6 +492,7 @@ int newton_step(mb_cell* c, double dt, double I_app, mb_step_info* info) {
         int nsub = 1 << h;
         double dts = dt / nsub;
         bool all_ok = true;
+        info->unresolved_flips = 0;   // counts the sub-steps of the accepted attempt only
         MB_CUDA(cudaMemcpyAsync(c->u, c->u_pass, 8 * n, cudaMemcpyDeviceToDevice, s));
         for (int k = 0; k < nsub; ++k) {
             MB_CUDA(cudaMemcpyAsync(c->u_old, c->u, 8 * n, cudaMemcpyDeviceToDevice, s));

@@ -93,3 +93,32 @@ def test_serving_mix_equals_alone(params):
     assert np.array_equal(rf2["V"][1:], np.array(V_fom2))
     g.close()
     gc.close()
+
+
+@pytest.mark.gpu
+def test_full_order_admission_by_device_memory(params):
+    """With a device-memory budget of one cell and four workers, full-order
+    requests never hold more than one cell at a time: before the first cell's
+    size is known only one worker may create one, and afterwards a second cell
+    does not fit the budget.  All requests still complete."""
+    B = _gpu()
+    lab = syn.full_cell(4, 4, 5, 3, 5, 0.35, 0.35, ("uniform", 1, 2), (1, 2))
+    probe = B.Cell(lab, 1e-6, params)
+    one_cell = int(probe.device_bytes)
+    i1 = probe.i_1c
+    probe.close()
+    srv = B.Server(labels=lab, params=params, fom_budget_bytes=one_cell, fom_workers=4)
+    tickets = [srv.submit(B.REQ_FOM, -2.0 * i1, 1.0, 1.0, 2, 1.0) for _ in range(8)]
+    res = _wait(srv, tickets)
+    alive, peak, cell_bytes = srv.debug_cells()
+    srv.close()
+    assert all(r["status"] == 0 for r in res.values())
+    assert peak == 1 and cell_bytes == one_cell
+    # a budget of two cells admits a second one
+    srv = B.Server(labels=lab, params=params, fom_budget_bytes=2 * one_cell, fom_workers=4)
+    tickets = [srv.submit(B.REQ_FOM, -2.0 * i1, 1.0, 1.0, 4, 1.0) for _ in range(8)]
+    res = _wait(srv, tickets)
+    _, peak2, _ = srv.debug_cells()
+    srv.close()
+    assert all(r["status"] == 0 for r in res.values())
+    assert 1 <= peak2 <= 2

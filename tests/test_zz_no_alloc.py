@@ -75,3 +75,26 @@ def test_noalloc_residual_rejects_invalid_arguments(params):
     with pytest.raises(B.MBError):
         cell.residual_dev_noalloc(du, du, 0.0, 0.0, r)
     cell.close()
+
+
+@pytest.mark.gpu
+def test_noalloc_residual_rejects_another_device(params):
+    """A call made while another device is current is refused: the scratch
+    address and the launches would belong to a device that does not hold the
+    cell's buffers.  Needs two devices."""
+    import torch
+    B = _gpu()
+    if torch.cuda.device_count() < 2:
+        pytest.skip("needs two CUDA devices")
+    lab = syn.full_cell(4, 4, 5, 3, 5, 0.35, 0.35, ("uniform", 1, 2), (1, 2))
+    torch.cuda.set_device(0)
+    cell = B.Cell(lab, 1e-6, params, B.default_opts())
+    du = torch.tensor(cell.state(), device="cuda:0")
+    r = torch.empty_like(du)
+    torch.cuda.set_device(1)
+    try:
+        with pytest.raises(B.MBError):
+            cell.residual_dev_noalloc(du, du, 1.0, 0.0, r)
+    finally:
+        torch.cuda.set_device(0)
+    cell.close()
