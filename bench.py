@@ -54,6 +54,61 @@ def workload_labels(name):
 CRATE = {"cell128x128x256": -2.0, "cell16x16x48": -1.0, "cell64x64x128": -2.0}
 
 
+def fom_opts(B, prec, args):
+    """Solver options of the full-order bench: Newton to 1e-10 in the scaled
+    max-norm (the production tolerance), Krylov relative residual 1e-4 (mixed)
+    or 1e-6 (FP64)."""
+    return B.default_opts(precision=prec, newton_tol=1e-10, krylov_rtol=1e-4 if prec else 1e-6,
+                          newton_maxit=20, krylov_maxit=300, max_halvings=3,
+                          mg_bf16=0 if args.fp32_coarse else 1, mg_stream=args.mg_stream)
+
+
+def step_record(infos):
+    """Per-step solver record of the timed steps."""
+    keys = ("newton_its", "krylov_its", "passes", "flips", "unresolved_flips", "halvings", "dt_used", "res_norm")
+    return {k: [i[k] for i in infos] for k in keys}
+
+
+def fields_rel_err(a, b, N):
+    """Max-norm error of a against b per field, relative to b's max-norm."""
+    out = {}
+    for name, sl in (("c", slice(0, N)), ("phi", slice(N, 2 * N)), ("n_plated", slice(2 * N, None))):
+        ref = b[sl]
+        scale = float(np.max(np.abs(ref))) if ref.size else 0.0
+        out[name] = float(np.max(np.abs(a[sl] - ref)) / scale) if scale > 0 else 0.0
+    return out
+
+
+def fp64_arm(B, labels, params, args, torch, V_mixed, u_mixed):
+    """The same warm-up and timed steps with the FP64 solver (linearisation
+    from the FP64 state in FP64, Krylov to 1e-6), timed with CUDA events on
+    the cell's stream; the mixed run's cell potential of every timed step and
+    its final fields are compared with it."""
+    cell = B.Cell(labels, 1e-6, params, fom_opts(B, B.PREC_FP64, args))
+    I = CRATE[args.workload] * cell.i_1c
+    for _ in range(args.warmup):
+        cell.step(1.0, I)
+    stream = torch.cuda.ExternalStream(cell.stream_ptr())
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    infos = [cell.step(1.0, I) for _ in range(args.steps)]
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    V = np.array([i["V_cell"] for i in infos])
+    u64 = cell.state()
+    N = cell.N
+    cell.close()
+    return {"value": args.steps / (ms / 1000.0), "unit": UNIT, "ms_per_step": ms / args.steps,
+            "precision": "f64 linearisation and residual; Krylov relative residual 1e-6",
+            "mixed_vs_fp64": {"V_max_rel_err": float(np.max(np.abs(np.asarray(V_mixed) - V) / np.abs(V))),
+                              "fields_max_rel_err_final": fields_rel_err(u_mixed, u64, N),
+                              "bounds": {"V": 1e-6, "fields": 1e-5}},
+            "solver": step_record(infos)}
+
+
 def max_over_ranks(x, dist, device):
     """The largest x over the ranks of the process group (x without one)."""
     if dist is None:
@@ -385,7 +440,8 @@ def main():
                     help="smoother and coarse-level products from FP32 operators instead of their BF16 copies")
     ap.add_argument("--mg-stream", type=int, default=0, choices=[0, 1, 2],
                     help="operator fetch of the BF16 coarse sweeps: 0 plain, 1 L2 prefetch, 2 staged in shared memory")
-    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--no-fp64-arm", action="store_true",
+                    help="skip the FP64 run of the same steps (and the mixed-vs-FP64 errors)")
     ap.add_argument("--no-rom", action="store_true", help="skip the reduced-model and serving measurements")
     ap.add_argument("--rom-instances", type=int, default=1024)
     ap.add_argument("--rom-steps", type=int, default=60)
@@ -414,14 +470,13 @@ def main():
         return 0
     labels = workload_labels(args.workload)
     prec = B.PREC_MIXED if args.precision == "mixed" else B.PREC_FP64
-    opts = B.default_opts(precision=prec, newton_tol=1e-9, krylov_rtol=1e-4 if prec else 1e-6,
-                          newton_maxit=20, krylov_maxit=300, max_halvings=3,
-                          mg_bf16=0 if args.fp32_coarse else 1, mg_stream=args.mg_stream)
+    opts = fom_opts(B, prec, args)
     cell = B.Cell(labels, 1e-6, params, opts)
     I = CRATE[args.workload] * cell.i_1c
     dt = 1.0
     for _ in range(args.warmup):
         cell.step(dt, I)
+    u_start = cell.state()          # the timed steps start here; e2e replays them from it
     stream = torch.cuda.ExternalStream(cell.stream_ptr())
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
@@ -453,20 +508,26 @@ def main():
     if dist is not None:
         dist.barrier()
     value = whole_job_value(ws, args.steps, dt, ms)
+    u_end = cell.state()
 
-    # end to end through the C-ABI with host buffers: state uploaded from
-    # pinned host memory before and read back after every step
+    # end to end through the C-ABI with host buffers, on the same steps: the
+    # state saved before the timed steps is uploaded from pinned host memory
+    # before, and read back after, every step of the replay
     u_host = torch.empty(cell.n, dtype=torch.float64).pin_memory().numpy()
-    u_host[:] = cell.state()
+    u_host[:] = u_start
     torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
     t0 = time.perf_counter()
-    for _ in range(args.e2e_steps):
+    for _ in range(args.steps):
         cell.set_state(u_host)
         cell.step(dt, I)
         cell.state(out=u_host)
-    e2e_wall = time.perf_counter() - t0
-    e2e = {"value": ws * args.e2e_steps * dt / e2e_wall, "unit": UNIT,
-           "h2d_bytes_per_step": 8 * cell.n, "d2h_bytes_per_step": 8 * cell.n}
+    e2e_wall = max_over_ranks(time.perf_counter() - t0, dist, "cuda")
+    e2e = {"value": ws * args.steps * dt / e2e_wall, "unit": UNIT,
+           "h2d_bytes_per_step": 8 * cell.n, "d2h_bytes_per_step": 8 * cell.n,
+           "steps": "the timed steps, replayed from the state saved before them",
+           "replay_identical": bool(np.array_equal(u_host, u_end))}
 
     # roofline of the dominant timed kernel: the fine smoothing sweep k_fine_stencil,
     # the Krylov operator's stencil JVP k_jvp_lin, or the level-1 smoothing sweep
@@ -510,6 +571,9 @@ def main():
                       for k, v in kinds.items()}}
 
     cell.close()
+    arm64 = None
+    if rank == 0 and ws == 1 and prec == B.PREC_MIXED and not args.no_fp64_arm:
+        arm64 = fp64_arm(B, labels, params, args, torch, [i["V_cell"] for i in infos], u_end)
     rom = rom_small = serve = None
     if rank == 0 and ws == 1 and not args.no_rom:
         rom = rom_paper_dims(B, params, args, torch)
@@ -531,9 +595,10 @@ def main():
                           "l2": "working set > 129 MB L2, no flush", "parallelism": "replicas" if ws > 1 else "1 GPU"},
                "clocks": clk, "e2e": e2e, "gpu_launches": int(launches), "roofline": roof,
                "cpu_baseline": cpu,
-               "solver": {"newton_its": [i["newton_its"] for i in infos], "krylov_its": [i["krylov_its"] for i in infos],
-                          "V_cell": infos[-1]["V_cell"], "precond_ms": ms_pc, "precond_calls": n_pc,
-                          "residual_ms": ms_res, "residual_calls": n_res},
+               "solver": dict(step_record(infos), V_cell=[i["V_cell"] for i in infos],
+                              newton_tol=opts.newton_tol, krylov_rtol=opts.krylov_rtol,
+                              precond_ms=ms_pc, precond_calls=n_pc, residual_ms=ms_res, residual_calls=n_res),
+               "fp64_arm": arm64,
                "rom": rom, "rom_small": rom_small, "serve": serve}
         print(json.dumps(out))
     if dist is not None:

@@ -95,6 +95,10 @@ typedef struct {
                               (the previous time level); 1 (default) the previous pass's converged
                               state.  The solution of a pass depends only on its frozen gates, not on
                               the start. */
+    int    mg_tail;        /* 1 (default): the V-cycle on the coarse levels that one wave of the GPU
+                              covers (level 2 down) runs as one persistent cooperative launch with
+                              grid barriers instead of one launch per sweep (same results); 0: per-level
+                              launches.  Applies to BF16 operators (mg_bf16 = 1). */
 } mb_solver_opts;
 
 typedef struct {
@@ -280,6 +284,30 @@ int mb_rom_destroy(mb_rom* rom);
  * failed (its outputs are then NaN from that step on). */
 int mb_rom_solve_batch(mb_rom* rom, int B, const mb_rom_params* prm, int n_steps, double dt, double* V_out,
                        double* sac_out, double* a_final, mb_rom_info* info);
+
+/* Hierarchical a-posteriori error estimate (Sec. workflow:MOR, Eqs.
+ * ap4:saturation and ap4:estimate): B instances with parameters prm run
+ * n_steps steps of size dt in the reduced model `rom` and in a larger
+ * validation model `rom_val` of the same cell; per instance, step and field,
+ *   est = ||U a - U_val a_val||_W / (1 - theta),
+ * the L^2 norm of the voxel grid (weight V per voxel value, A per plated-Li
+ * face value) of the difference of the two reconstructions, for the fields
+ * c, phi and n (the plated-Li inventory, a state the paper's estimate does
+ * not have).  rom_val's basis must be W-orthonormal on each field (as the
+ * POD of mb_rom_build and of the oracle gives); rom's need not lie in its
+ * span.  The maps between the two bases are formed on the host at the first
+ * call for a pair (O(n N_r^2) flops) and kept with rom; per step the
+ * estimate costs O(N_val N_r + N_r^2) FP64 flops per instance on the
+ * coefficients (no reconstruction).  est_out: host double[B * (n_steps + 1)
+ * * 3], instance-major, then step, then field (c, phi, n); V_out and
+ * V_val_out (may be NULL): host double[B * (n_steps + 1)], the two models'
+ * cell potentials.  theta in [0, 1).  MB_EINVAL for models of different
+ * cells or a validation basis that is not W-orthonormal per field;
+ * MB_ENOCONV (estimates NaN from then on) if an instance failed in either
+ * model. */
+int mb_rom_estimate_batch(mb_rom* rom, mb_rom* rom_val, double theta, int B, const mb_rom_params* prm,
+                          int n_steps, double dt, double* V_out, double* V_val_out, double* est_out,
+                          mb_rom_info* info);
 
 /* ---- serving loop (parameter-study queries; no counterpart in the paper) ----
  * Requests arrive at any time (mb_serve_submit never blocks).  Reduced-model

@@ -40,7 +40,7 @@ class SolverOpts(C.Structure):
                 ("max_passes", C.c_int), ("max_halvings", C.c_int), ("mg_coarse_cells", C.c_int),
                 ("mg_smooth", C.c_int), ("mg_kcycle", C.c_int), ("mg_coarse_pre", C.c_int),
                 ("mg_coarse_post", C.c_int), ("mg_bf16", C.c_int), ("mg_stream", C.c_int),
-                ("pass_start", C.c_int)]
+                ("pass_start", C.c_int), ("mg_tail", C.c_int)]
 
 
 class StepInfo(C.Structure):
@@ -136,6 +136,8 @@ def _declare(lib):
     fn("mb_rom_dims", C.c_int, [VP, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)])
     fn("mb_rom_solve_batch", C.c_int, [VP, C.c_int, C.POINTER(RomParams), C.c_int, C.c_double, VP, VP, VP,
                                         C.POINTER(RomInfo)])
+    fn("mb_rom_estimate_batch", C.c_int, [VP, VP, C.c_double, C.c_int, C.POINTER(RomParams), C.c_int, C.c_double,
+                                          VP, VP, VP, C.POINTER(RomInfo)])
     fn("mb_jvp", C.c_int, [VP, VP, VP, C.c_double, VP, VP])
     fn("mb_jvp_dev", C.c_int, [VP, VP, VP, C.c_double, VP, VP, VP])
     fn("mb_jvp_f32_dev", C.c_int, [VP, VP, VP, C.c_double, VP, VP, VP])
@@ -422,6 +424,22 @@ class Rom:
             _check(rc)
         out["ok"] = rc == 0
         return out
+
+    def estimate(self, val, params, n_steps, dt, theta=0.0):
+        """Hierarchical error estimate against the validation model `val`
+        (mb_rom_estimate_batch).  Returns dict est (B, n_steps+1, 3: c, phi,
+        n), V and V_val (B, n_steps+1) and the counts."""
+        B = len(params)
+        prm = (RomParams * B)(*[RomParams(*map(float, p)) for p in params])
+        est = np.empty((B, n_steps + 1, 3))
+        V = np.empty((B, n_steps + 1))
+        Vv = np.empty((B, n_steps + 1))
+        info = RomInfo()
+        rc = lib().mb_rom_estimate_batch(self.h, val.h, float(theta), B, prm, int(n_steps), float(dt), _ptr(V),
+                                         _ptr(Vv), _ptr(est), C.byref(info))
+        if rc != 0 and rc != -4:
+            _check(rc)
+        return dict(est=est, V=V, V_val=Vv, newton_its=int(info.newton_its), failed=int(info.failed), ok=rc == 0)
 
     def debug_refine(self, on):
         """Escalated instances by GMRES preconditioned with the FP32 LU (on, the default) or the FP64 LU (off)."""

@@ -115,6 +115,7 @@ void mb_opts_default(mb_solver_opts* o) {
     o->mg_bf16 = 1;
     o->mg_stream = 0;
     o->pass_start = 1;
+    o->mg_tail = 1;
 }
 
 static int check_opts(const mb_solver_opts* o) {
@@ -125,7 +126,7 @@ static int check_opts(const mb_solver_opts* o) {
         !(o->krylov_rtol > 0) || o->mg_kcycle < 1 || o->mg_kcycle > 16 || o->mg_smooth < 1 || o->mg_smooth > 8 ||
         (o->mg_bf16 != 0 && o->mg_bf16 != 1) || o->mg_coarse_pre < 1 || o->mg_coarse_pre > 4 ||
         o->mg_coarse_post < 1 || o->mg_coarse_post > 4 || o->mg_stream < 0 || o->mg_stream > 2 ||
-        (o->pass_start != 0 && o->pass_start != 1))
+        (o->pass_start != 0 && o->pass_start != 1) || (o->mg_tail != 0 && o->mg_tail != 1))
         return MB_EINVAL;
     return MB_OK;
 }

@@ -38,6 +38,7 @@
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdio.h>
+#include <string.h>
 
 #include <atomic>
 #include <vector>
@@ -144,7 +145,10 @@ struct Precond {
     int nsm = 0;               // SMs of the device (grid of the persistent staged sweep)
     int pf[3] = {0, 0, 0};     // L2 prefetch distance (blocks of one resident wave) of the BF16
                                // sweep, fused first sweeps and product
-    int* err = nullptr;        // device flag: a bounded wait of a staged sweep gave up
+    int* err = nullptr;        // device flag: a bounded wait gave up (1 staged sweep, 2 its drain, 4 the tail)
+    unsigned* tbar = nullptr;  // grid barrier of the persistent coarse tail
+    int tail_l0 = 0;           // first level of the persistent tail (0: none)
+    int tail_blocks = 0;       // its grid (blocks of TAIL_THREADS, all co-resident)
     int nu_fine = 0;           // fine-level block-Jacobi sweeps before and after the coarse correction
     // level-1 K-cycle workspace
     float* kV = nullptr;       // (KCYC_MAX+1) x m4  FP32 basis
@@ -157,6 +161,9 @@ struct Precond {
 // set when a staged sweep timed out and could not drain its bulk copies: the
 // plain sweep is used from then on in this process
 static std::atomic<bool> g_staged_broken{false};
+// set when a persistent coarse tail timed out at a grid barrier, or a graph
+// containing it could not be captured: per-level launches from then on
+static std::atomic<bool> g_tail_broken{false};
 
 static const dim3 PB(32, 8, 1);
 static inline dim3 pgrid(int nt, int ny, int nz) { return dim3((nz + 31) / 32, (ny + 7) / 8, nt); }
@@ -642,12 +649,87 @@ __global__ void k_coarse_invert(int n, double* __restrict__ A, double* __restric
     }
 }
 
+// The same inverse with the matrix held in shared memory and inverted in
+// place (Gauss-Jordan with row interchanges; the interchanges are undone as
+// column swaps at the end), one block of 1024 threads, n <= CINV_SMEM_MAX.
+// Per pivot column: warp 0 finds the pivot (largest magnitude, lowest row on
+// ties), the rows are swapped, column k is saved and the pivot row scaled,
+// then every other row is eliminated.  FP64 throughout.
+constexpr int CINV_SMEM_MAX = 160;       // 160^2 doubles = 200 KB of shared memory
+constexpr int CINV_THREADS = 1024;
+__global__ void __launch_bounds__(CINV_THREADS)
+k_coarse_invert_smem(int n, const double* __restrict__ A, double* __restrict__ Ainv, int* __restrict__ stat) {
+    extern __shared__ __align__(16) double sA[];   // n x n, then colk[n]
+    __shared__ int perm[CINV_SMEM_MAX];
+    __shared__ int piv;
+    __shared__ double pval;
+    double* colk = sA + n * n;
+    const int tid = threadIdx.x;
+    for (int i = tid; i < n * n; i += blockDim.x) sA[i] = A[i];
+    __syncthreads();
+    for (int k = 0; k < n; ++k) {
+        if (tid < 32) {
+            double best = -1.0;
+            int bi = n;
+            for (int r = k + tid; r < n; r += 32) {
+                const double v = fabs(sA[r * n + k]);
+                if (v > best) { best = v; bi = r; }
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                const double v2 = __shfl_down_sync(0xffffffffu, best, o);
+                const int i2 = __shfl_down_sync(0xffffffffu, bi, o);
+                if (v2 > best || (v2 == best && i2 < bi)) { best = v2; bi = i2; }
+            }
+            if (tid == 0) {
+                piv = bi;
+                pval = sA[bi * n + k];
+                perm[k] = bi;
+                if (pval == 0.0) *stat = 1;
+            }
+        }
+        __syncthreads();
+        const int p = piv;
+        if (p != k) {
+            for (int j = tid; j < n; j += blockDim.x) {
+                const double t = sA[k * n + j];
+                sA[k * n + j] = sA[p * n + j];
+                sA[p * n + j] = t;
+            }
+            __syncthreads();
+        }
+        const double inv = pval != 0.0 ? 1.0 / pval : 0.0;
+        // column k of the other rows (read before the elimination overwrites it)
+        // and the scaled pivot row (its diagonal becomes 1/pivot)
+        for (int i = tid; i < n; i += blockDim.x)
+            if (i != k) colk[i] = sA[i * n + k];
+        for (int j = tid; j < n; j += blockDim.x) sA[k * n + j] = (j == k ? 1.0 : sA[k * n + j]) * inv;
+        __syncthreads();
+        for (int idx = tid; idx < n * n; idx += blockDim.x) {
+            const int i = idx / n, j = idx - i * n;
+            if (i == k) continue;
+            sA[idx] = (j == k ? 0.0 : sA[idx]) - colk[i] * sA[k * n + j];
+        }
+        __syncthreads();
+    }
+    // undo the row interchanges as column swaps, last first
+    for (int k = n - 1; k >= 0; --k) {
+        const int p = perm[k];
+        if (p != k) {
+            for (int i = tid; i < n; i += blockDim.x) {
+                const double t = sA[i * n + k];
+                sA[i * n + k] = sA[i * n + p];
+                sA[i * n + p] = t;
+            }
+            __syncthreads();
+        }
+    }
+    for (int i = tid; i < n * n; i += blockDim.x) Ainv[i] = sA[i];
+}
+
 // x = Ainv b (FP64 accumulation), one block; x stored float-float.  One warp
 // per row (coalesced loads of Ainv), lane partial sums combined by shuffles.
-__global__ void k_coarse_solve(int n, const double* __restrict__ Ainv, const float4* __restrict__ b,
-                               DF4* __restrict__ x) {
-    __shared__ double sb[COARSE_MAX];
-    __shared__ double sx[COARSE_MAX];
+__device__ inline void coarse_solve_block(int n, const double* __restrict__ Ainv, const float4* b, DF4* x,
+                                          double* sb, double* sx) {
     const float* bf = reinterpret_cast<const float*>(b);
     for (int i = threadIdx.x; i < n; i += blockDim.x) sb[i] = (double)bf[i];
     __syncthreads();
@@ -662,6 +744,12 @@ __global__ void k_coarse_solve(int n, const double* __restrict__ Ainv, const flo
     for (int cell = threadIdx.x; cell < n / NCLS; cell += blockDim.x)
         x[cell] = df4_pack(df_from_double(sx[4 * cell]), df_from_double(sx[4 * cell + 1]),
                            df_from_double(sx[4 * cell + 2]), df_from_double(sx[4 * cell + 3]));
+}
+__global__ void k_coarse_solve(int n, const double* __restrict__ Ainv, const float4* __restrict__ b,
+                               DF4* __restrict__ x) {
+    __shared__ double sb[COARSE_MAX];
+    __shared__ double sx[COARSE_MAX];
+    coarse_solve_block(n, Ainv, b, x, sb, sx);
 }
 
 // ------------------------------------------------ assembled fine smoother
@@ -1001,12 +1089,13 @@ __device__ inline void lvl_prefetch(const Level& L, int64_t blk, int r0, int r1,
 // pf > 0 (BF16 operators, blocks of SWT threads): the block's thread 0 first
 // prefetches into L2 the operator rows, right-hand side and iterate of block
 // blockIdx.x + pf, about one resident wave ahead
+// one cell of a damped block-Jacobi sweep (the body of k_lvl_smooth)
 template <bool B16>
-__global__ void k_lvl_smooth(Level L, const DF4* __restrict__ x_in, const DF4* __restrict__ ec, int ccny,
-                             int ccnz, float omega, DF4* __restrict__ x_out, int pf) {
-    if (B16 && pf > 0 && threadIdx.x == 0) lvl_prefetch(L, (int64_t)blockIdx.x + pf, 0, 32, x_in);
-    int64_t cell = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (cell >= L.cells) return;
+// (no __restrict__ on the iterates: the persistent tail reads in one phase what
+// another block wrote in an earlier phase of the same launch, so these loads
+// must not take the read-only non-coherent path)
+__device__ inline void smooth_cell(const Level& L, const DF4* x_in, const DF4* ec, int ccny, int ccnz, float omega,
+                                   DF4* x_out, int64_t cell) {
     int t, y, z;
     cell_coords(L, cell, t, y, z);
     if (!x_in && !ec) {
@@ -1020,6 +1109,15 @@ __global__ void k_lvl_smooth(Level L, const DF4* __restrict__ x_in, const DF4* _
     DF4 xe = xeff(x_in, ec, ccny, ccnz, t, y, z, cell);
     float4 r = f4sub(L.b[cell], cell_apply<B16>(L, x_in, ec, ccny, ccnz, t, y, z, cell, xe));
     x_out[cell] = df4_add_f(xe, f4scale(omega, lvl_mv<B16>(L, 7, cell, r)));
+}
+
+template <bool B16>
+__global__ void k_lvl_smooth(Level L, const DF4* __restrict__ x_in, const DF4* __restrict__ ec, int ccny,
+                             int ccnz, float omega, DF4* __restrict__ x_out, int pf) {
+    if (B16 && pf > 0 && threadIdx.x == 0) lvl_prefetch(L, (int64_t)blockIdx.x + pf, 0, 32, x_in);
+    int64_t cell = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (cell >= L.cells) return;
+    smooth_cell<B16>(L, x_in, ec, ccny, ccnz, omega, x_out, cell);
 }
 
 // ---------------------------------------- staged sweep (bulk async copies)
@@ -1115,10 +1213,7 @@ k_lvl_smooth_staged(Level L, const DF4* __restrict__ x_in, const DF4* __restrict
 // with x1 = omega Sinv b evaluated where it is needed (the cell and its
 // neighbours), bit-identical to two k_lvl_smooth launches
 template <bool B16>
-__global__ void k_lvl_smooth2(Level L, float omega, DF4* __restrict__ x_out, int pf) {
-    if (B16 && pf > 0 && threadIdx.x == 0) lvl_prefetch(L, (int64_t)blockIdx.x + pf, 0, 32, nullptr);
-    int64_t cell = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (cell >= L.cells) return;
+__device__ inline void smooth2_cell(const Level& L, float omega, DF4* x_out, int64_t cell) {
     int t, y, z;
     cell_coords(L, cell, t, y, z);
     const DF4 x1 = first_sweep<B16>(L, cell, omega);
@@ -1126,6 +1221,14 @@ __global__ void k_lvl_smooth2(Level L, float omega, DF4* __restrict__ x_out, int
                          return first_sweep<B16>(L, nb, omega);
                      }));
     x_out[cell] = df4_add_f(x1, f4scale(omega, lvl_mv<B16>(L, 7, cell, r)));
+}
+
+template <bool B16>
+__global__ void k_lvl_smooth2(Level L, float omega, DF4* __restrict__ x_out, int pf) {
+    if (B16 && pf > 0 && threadIdx.x == 0) lvl_prefetch(L, (int64_t)blockIdx.x + pf, 0, 32, nullptr);
+    int64_t cell = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (cell >= L.cells) return;
+    smooth2_cell<B16>(L, omega, x_out, cell);
 }
 
 template <bool B16>
@@ -1140,9 +1243,10 @@ __global__ void k_lvl_matvec(Level L, const DF4* __restrict__ x, float4* __restr
 
 // bc(parent) = sum over children of (b - A x): one thread per child (eight
 // consecutive threads per parent), summed by shuffles within the octet
+// thread tid of the restriction (eight consecutive threads per parent; whole
+// warps must call it together)
 template <bool B16>
-__global__ void k_lvl_restrict(Level L, const DF4* __restrict__ x, Level C) {
-    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+__device__ inline void restrict_thread(const Level& L, const DF4* x, const Level& C, int64_t tid) {
     const int64_t cell = tid >> 3;
     const int k = (int)(tid & 7);
     float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -1163,6 +1267,137 @@ __global__ void k_lvl_restrict(Level L, const DF4* __restrict__ x, Level C) {
         r.w += __shfl_xor_sync(0xffffffffu, r.w, o);
     }
     if (k == 0 && cell < C.cells) C.b[cell] = r;
+}
+
+template <bool B16>
+__global__ void k_lvl_restrict(Level L, const DF4* __restrict__ x, Level C) {
+    restrict_thread<B16>(L, x, C, (int64_t)blockIdx.x * blockDim.x + threadIdx.x);
+}
+
+// ------------------------------------- coarse tail in one persistent launch
+// The V-cycle on levels l0..nlev (BF16 operators) as one cooperative launch:
+// the phases of the per-level kernels (fused first sweeps, further
+// pre-sweeps, restriction, the coarsest dense solve by block 0, post-sweeps
+// with the prolonged correction) run the same per-cell code in grid-stride
+// loops, separated by a grid barrier instead of kernel boundaries, so the
+// results are bit-identical to the per-level launches.  Every barrier wait is
+// bounded: on a timeout a block sets bit 4 of *err and returns (the kernel
+// holds no asynchronous copies).  Iterates alternate between x and x2 of each
+// level exactly as the host-side sequence does.
+constexpr int TAIL_THREADS = 256;
+constexpr int TAIL_SPIN = 1 << 20;        // polls (64 ns apart) per barrier before giving up
+
+struct TailLv {
+    int nt, ny, nz;
+    int64_t cells, pst;
+    const uint2* pk;
+    float4* b;
+    DF4* x;
+    DF4* x2;
+};
+struct TailArgs {
+    int l0, nlev, nu_pre, nu_post, ncoarse;
+    const double* cinv;
+    unsigned* bar;       // [0] arrivals, [1] generation: zeroed before each launch
+    int* err;
+    TailLv lv[MAX_LEVELS + 1];
+};
+
+__device__ inline Level tail_level(const TailLv& t) {
+    Level L;
+    L.nt = t.nt; L.ny = t.ny; L.nz = t.nz;
+    L.cells = t.cells;
+    L.pst = t.pst;
+    L.pk = const_cast<uint2*>(t.pk);
+    L.b = t.b;
+    return L;
+}
+
+// grid barrier; false if the wait gave up
+__device__ inline bool tail_barrier(unsigned* bar, unsigned& gen) {
+    __syncthreads();
+    int ok = 1;
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned arrived = atomicAdd(&bar[0], 1u) + 1u;
+        if (arrived == gridDim.x) {
+            atomicExch(&bar[0], 0u);
+            __threadfence();
+            atomicExch(&bar[1], gen + 1u);
+        } else {
+            const volatile unsigned* g = bar + 1;
+            int i = 0;
+            while (*g == gen) {
+                if (++i > TAIL_SPIN) { ok = 0; break; }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+    }
+    ++gen;
+    return __syncthreads_and(ok) != 0;
+}
+
+__global__ void __launch_bounds__(TAIL_THREADS) k_vtail(TailArgs a) {
+    __shared__ double sb[COARSE_MAX];
+    __shared__ double sx[COARSE_MAX];
+    unsigned gen = 0;
+    unsigned par = 0;    // bit l: level l's current iterate is x2
+    const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t gs = (int64_t)gridDim.x * blockDim.x;
+    auto X = [&](int l) { return ((par >> l) & 1u) ? a.lv[l].x2 : a.lv[l].x; };
+    auto Y = [&](int l) { return ((par >> l) & 1u) ? a.lv[l].x : a.lv[l].x2; };
+#define TAIL_SYNC()                                        \
+    do {                                                   \
+        if (!tail_barrier(a.bar, gen)) {                   \
+            if (threadIdx.x == 0) atomicOr(a.err, 4);      \
+            return;                                        \
+        }                                                  \
+    } while (0)
+    for (int l = a.l0; l < a.nlev; ++l) {
+        const Level L = tail_level(a.lv[l]);
+        DF4* x = X(l);
+        for (int64_t cell = gtid; cell < L.cells; cell += gs) {
+            if (a.nu_pre >= 2) smooth2_cell<true>(L, OMEGA_COARSE, x, cell);
+            else smooth_cell<true>(L, nullptr, nullptr, 0, 0, OMEGA_COARSE, x, cell);
+        }
+        TAIL_SYNC();
+        for (int k = 2; k < a.nu_pre; ++k) {
+            const DF4* xi = X(l);
+            DF4* xo = Y(l);
+            for (int64_t cell = gtid; cell < L.cells; cell += gs)
+                smooth_cell<true>(L, xi, nullptr, 0, 0, OMEGA_COARSE, xo, cell);
+            par ^= 1u << l;
+            TAIL_SYNC();
+        }
+        const Level C = tail_level(a.lv[l + 1]);
+        const int64_t nthr = (8 * C.cells + 31) / 32 * 32;     // whole warps (the octet shuffles)
+        for (int64_t t = gtid; t < nthr; t += gs) restrict_thread<true>(L, X(l), C, t);
+        TAIL_SYNC();
+    }
+    if (blockIdx.x == 0) coarse_solve_block(a.ncoarse, a.cinv, a.lv[a.nlev].b, X(a.nlev), sb, sx);
+    for (int l = a.nlev - 1; l >= a.l0; --l) {
+        TAIL_SYNC();
+        const Level L = tail_level(a.lv[l]);
+        const TailLv& C = a.lv[l + 1];
+        {
+            const DF4* xi = X(l);
+            const DF4* ec = X(l + 1);
+            DF4* xo = Y(l);
+            for (int64_t cell = gtid; cell < L.cells; cell += gs)
+                smooth_cell<true>(L, xi, ec, C.ny, C.nz, OMEGA_COARSE, xo, cell);
+            par ^= 1u << l;
+        }
+        for (int k = 1; k < a.nu_post; ++k) {
+            TAIL_SYNC();
+            const DF4* xi = X(l);
+            DF4* xo = Y(l);
+            for (int64_t cell = gtid; cell < L.cells; cell += gs)
+                smooth_cell<true>(L, xi, nullptr, 0, 0, OMEGA_COARSE, xo, cell);
+            par ^= 1u << l;
+        }
+    }
+#undef TAIL_SYNC
 }
 
 // ----------------------------------------------------- fine <-> level 1
@@ -1357,6 +1592,9 @@ int precond_create(mb_cell* c) {
         if (cudaFuncSetAttribute(k_lvl_smooth_staged, cudaFuncAttributeMaxDynamicSharedMemorySize, SW_SMEM) !=
             cudaSuccess)
             return cuda_fail(cudaGetLastError(), "staged sweep shared memory");
+        if (cudaFuncSetAttribute(k_coarse_invert_smem, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 8 * (CINV_SMEM_MAX * CINV_SMEM_MAX + CINV_SMEM_MAX)) != cudaSuccess)
+            return cuda_fail(cudaGetLastError(), "coarse inverse shared memory");
         int nb[3] = {0, 0, 0};
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb[0], k_lvl_smooth<true>, 256, 0) != cudaSuccess ||
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb[1], k_lvl_smooth2<true>, 256, 0) != cudaSuccess ||
@@ -1417,6 +1655,24 @@ int precond_create(mb_cell* c) {
     p->kH = (double*)cell_alloc(c, 8 * (size_t)((KCYC_MAX + 1) * KCYC_MAX + 128));
     p->kred = (double*)cell_alloc(c, 8 * (size_t)RED_BLOCKS * 8);
     if (!p->cdense || !p->cinv || !p->cstat || !p->kV || !p->kZ || !p->kw || !p->kH || !p->kred) return MB_ENOMEM;
+    // persistent coarse tail: from the first level >= 2 that one resident wave of
+    // TAIL_THREADS-thread blocks covers (at most two blocks per SM, all co-resident)
+    p->tbar = (unsigned*)cell_alloc(c, 16);
+    if (!p->tbar) return MB_ENOMEM;
+    p->tail_l0 = 0;
+    if (c->opt.mg_tail && p->b16 && p->nlev >= 3) {
+        int dev = 0, coop = 0, occ = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_vtail, TAIL_THREADS, 0) != cudaSuccess)
+            return cuda_fail(cudaGetLastError(), "coarse tail occupancy");
+        if (coop && occ >= 1) {
+            p->tail_blocks = (occ < 2 ? occ : 2) * p->nsm;
+            const int64_t cap = (int64_t)p->tail_blocks * TAIL_THREADS;
+            for (int l = 2; l < p->nlev; ++l)
+                if (p->lv[l].cells <= cap) { p->tail_l0 = l; break; }
+        }
+    }
     return MB_OK;
 }
 
@@ -1456,7 +1712,11 @@ int precond_setup(mb_cell* c, const float* u32, const uint8_t* gate, double dt) 
     Level& Lc = p->lv[p->nlev];
     k_coarse_dense<<<(n + 127) / 128, 128, 0, s>>>(Lc, n, p->cdense), ::mb::count_launch(c);
     MB_CUDA(cudaMemsetAsync(p->cstat, 0, 4, s));
-    k_coarse_invert<<<1, 256, 0, s>>>(n, p->cdense, p->cinv, p->cstat), ::mb::count_launch(c);
+    if (n <= CINV_SMEM_MAX)
+        k_coarse_invert_smem<<<1, CINV_THREADS, (size_t)8 * (n * n + n), s>>>(n, p->cdense, p->cinv, p->cstat);
+    else
+        k_coarse_invert<<<1, 256, 0, s>>>(n, p->cdense, p->cinv, p->cstat);
+    ::mb::count_launch(c);
     MB_CUDA_LAUNCH("precond_setup");
     return MB_OK;
 }
@@ -1510,10 +1770,51 @@ static void lvl_matvec(mb_cell* c, Level& L, const DF4* x, float* y) {
     ::mb::count_launch(c);
 }
 
+// the V-cycle on levels tail_l0..nlev as one cooperative launch (k_vtail)
+static void launch_tail(mb_cell* c) {
+    Precond* p = c->pc;
+    cudaStream_t s = c->stream;
+    TailArgs a;
+    memset(&a, 0, sizeof(a));
+    a.l0 = p->tail_l0;
+    a.nlev = p->nlev;
+    a.nu_pre = c->opt.mg_coarse_pre;
+    a.nu_post = c->opt.mg_coarse_post;
+    a.ncoarse = p->ncoarse;
+    a.cinv = p->cinv;
+    a.bar = p->tbar;
+    a.err = p->err;
+    for (int l = a.l0; l <= p->nlev; ++l) {
+        const Level& L = p->lv[l];
+        a.lv[l] = TailLv{L.nt, L.ny, L.nz, L.cells, L.pst, L.pk, L.b, L.x, L.x2};
+    }
+    cudaMemsetAsync(p->tbar, 0, 8, s);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)p->tail_blocks);
+    cfg.blockDim = dim3(TAIL_THREADS);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeCooperative;
+    at[0].val.cooperative = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, k_vtail, a);
+    ::mb::count_launch(c);
+    // the kernel alternates each level's iterates as the per-level sequence does
+    const int swaps = (c->opt.mg_coarse_pre > 2 ? c->opt.mg_coarse_pre - 2 : 0) + c->opt.mg_coarse_post;
+    if (swaps & 1)
+        for (int l = a.l0; l < p->nlev; ++l) std::swap(p->lv[l].x, p->lv[l].x2);
+}
+
 // V-cycle on levels l..nlev with right-hand side lv[l].b; result in lv[l].x
 static void vcycle(mb_cell* c, int l) {
     Precond* p = c->pc;
     cudaStream_t s = c->stream;
+    if (p->tail_l0 && l == p->tail_l0 && !g_tail_broken.load()) {
+        launch_tail(c);
+        return;
+    }
     Level& L = p->lv[l];
     if (l == p->nlev) {
         k_coarse_solve<<<1, 256, 0, s>>>(p->ncoarse, p->cinv, L.b, L.x), ::mb::count_launch(c);
@@ -1670,10 +1971,12 @@ int precond_check(mb_cell* c) {
     MB_CUDA(cudaStreamSynchronize(c->stream));
     if (h) {
         MB_CUDA(cudaMemsetAsync(p->err, 0, 4, c->stream));
-        if (h & 2) {
-            // a staged sweep could not drain its copies: never launch it again in
-            // this process; the graphs that contain it are captured anew
-            g_staged_broken.store(true);
+        if (h & 6) {
+            // a staged sweep could not drain its copies, or a persistent tail gave up
+            // at a grid barrier: never launch that kernel again in this process; the
+            // graphs that contain it are captured anew
+            if (h & 2) g_staged_broken.store(true);
+            if (h & 4) g_tail_broken.store(true);
             for (auto& G : p->graphs) graph_free(G);
             p->graphs.clear();
             p->pending = -1;
@@ -1816,7 +2119,13 @@ int precond_apply(mb_cell* c, const float* u32, const uint8_t* gate, double dt, 
     }
     if (idx < 0) {
         PcGraph G;
-        if (!capture_graph(c, r, z, G)) {
+        bool ok = capture_graph(c, r, z, G);
+        if (!ok && p->tail_l0 && !g_tail_broken.load()) {
+            // a cooperative launch that cannot be captured: per-level launches instead
+            g_tail_broken.store(true);
+            ok = capture_graph(c, r, z, G);
+        }
+        if (!ok) {
             p->graphs_off = true;
             return precond_apply(c, u32, gate, dt, r, z, false);
         }

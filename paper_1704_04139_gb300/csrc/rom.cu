@@ -116,11 +116,29 @@ struct RomWork {
 
 }  // namespace mb
 
+namespace mb {
+// Maps of the hierarchical error estimate between this model (the reduced
+// one) and a validation model (mb_rom_estimate_batch), for one validation model.
+struct RomEst {
+    const mb_rom* val = nullptr;
+    int Nv = 0;
+    double* T = nullptr;       // Nv x Nr: Uv_f^T W U_f, f the field of validation mode j (row j)
+    double* G = nullptr;       // 3 x Nr x Nr: R_f^T W R_f, R_f = U_f - Uv_f T_f (U_f outside span Uv_f)
+    int* fld = nullptr;        // Nv: field of validation mode j (0 c, 1 phi, 2 n; -1 none)
+    int gon[3] = {0, 0, 0};    // G_f has a nonzero entry
+    double* est = nullptr;     // B x 3 estimates of the current step
+    int Bcap = 0;
+    std::vector<void*> bufs;
+};
+}  // namespace mb
+
 struct mb_rom {
     mb_cell* cell = nullptr;
     mb::RomDev d;
     std::vector<void*> owned;
     mb::RomWork w;
+    std::vector<double> hU;    // host copy of the basis (n x Nr, row-major): the error estimate's maps
+    mb::RomEst est;
 };
 
 namespace mb {
@@ -1579,6 +1597,7 @@ extern "C" int mb_rom_create(mb_cell* cell, const mb_rom_data* d, mb_rom** out) 
     }
     mb_rom* R = new mb_rom();
     R->cell = cell;
+    R->hU.assign(d->U, d->U + (size_t)cell->n * d->n_r);
     int rc = rom_build_host(R, d);
     if (rc) {
         if (rc == MB_EINVAL) set_error("mb_rom_create: point outside the residual or too many terms per point");
@@ -1601,10 +1620,36 @@ extern "C" int mb_rom_dims(mb_rom* R, int* n_r, int* n_bv, int* n_1c) {
 extern "C" int mb_rom_destroy(mb_rom* R) {
     if (!R) return MB_EINVAL;
     rom_work_free(R->w);
+    for (void* p : R->est.bufs) cudaFree(p);
     for (void* p : R->owned) cudaFree(p);
     delete R;
     return MB_OK;
 }
+
+namespace mb {
+// B slots started at the initial coefficients with the instance parameters prm
+static int rom_batch_begin(mb_rom* R, int B, const mb_rom_params* prm, double dt) {
+    int rc = rom_batch_alloc(R, B);
+    if (rc) { set_error("reduced model: device memory for the batch"); return rc; }
+    // every instance's parameters in one copy, then one start kernel
+    std::vector<double> hp((size_t)RP * B);
+    for (int b = 0; b < B; ++b) {
+        hp[(size_t)RP * b] = prm[b].I_app;
+        hp[(size_t)RP * b + 1] = prm[b].s_i0;
+        hp[(size_t)RP * b + 2] = prm[b].k_pl;
+        hp[(size_t)RP * b + 3] = 1.0 / dt;
+    }
+    RomWork& w = R->w;
+    cudaStream_t s = R->cell->stream;
+    MB_CUDA(cudaMemcpyAsync(w.prm, hp.data(), 8 * hp.size(), cudaMemcpyHostToDevice, s));
+    const int64_t n = (int64_t)B * R->d.Nr;
+    k_rom_batch_start<<<(unsigned)std::min<int64_t>((n + 255) / 256, 4096), 256, 0, s>>>(
+        R->d, B, w.a, w.failed, w.its, w.flips, w.hp), count_launch(R->cell);
+    MB_CUDA_LAUNCH("rom_batch_start");
+    MB_CUDA(cudaStreamSynchronize(s));   // the host parameter buffer goes out of scope
+    return MB_OK;
+}
+}  // namespace mb
 
 extern "C" int mb_rom_solve_batch(mb_rom* R, int B, const mb_rom_params* prm, int n_steps, double dt, double* V_out,
                                   double* sac_out, double* a_final, mb_rom_info* info) {
@@ -1613,26 +1658,8 @@ extern "C" int mb_rom_solve_batch(mb_rom* R, int B, const mb_rom_params* prm, in
         return MB_EINVAL;
     }
     const int ncol = n_steps + 1;
-    int rc = rom_batch_alloc(R, B);
-    if (rc) { set_error("mb_rom_solve_batch: device memory"); return rc; }
-    {
-        // every instance's parameters in one copy, then one start kernel
-        std::vector<double> hp((size_t)RP * B);
-        for (int b = 0; b < B; ++b) {
-            hp[(size_t)RP * b] = prm[b].I_app;
-            hp[(size_t)RP * b + 1] = prm[b].s_i0;
-            hp[(size_t)RP * b + 2] = prm[b].k_pl;
-            hp[(size_t)RP * b + 3] = 1.0 / dt;
-        }
-        RomWork& w = R->w;
-        cudaStream_t s = R->cell->stream;
-        MB_CUDA(cudaMemcpyAsync(w.prm, hp.data(), 8 * hp.size(), cudaMemcpyHostToDevice, s));
-        const int64_t n = (int64_t)B * R->d.Nr;
-        k_rom_batch_start<<<(unsigned)std::min<int64_t>((n + 255) / 256, 4096), 256, 0, s>>>(
-            R->d, B, w.a, w.failed, w.its, w.flips, w.hp), count_launch(R->cell);
-        MB_CUDA_LAUNCH("rom_batch_start");
-        MB_CUDA(cudaStreamSynchronize(s));   // the host parameter buffer goes out of scope
-    }
+    int rc = rom_batch_begin(R, B, prm, dt);
+    if (rc) return rc;
     std::vector<double> hV(B), hS(B);
     std::vector<int> hf(B);
     for (int step = 0; step <= n_steps; ++step) {
@@ -1654,6 +1681,236 @@ extern "C" int mb_rom_solve_batch(mb_rom* R, int B, const mb_rom_params* prm, in
     if (info) *info = inf;
     if (inf.failed) {
         set_error("mb_rom_solve_batch: reduced Newton did not converge for some instances");
+        return MB_ENOCONV;
+    }
+    return MB_OK;
+}
+
+// ------------------------------------------- hierarchical error estimate
+// Eq. ap4:estimate with the saturation constant theta of Eq. ap4:saturation:
+// per field f (c, phi, plated-Li n) and step, e_f = ||U_f a - Uv_f av||_W /
+// (1 - theta), U the reduced model's basis, Uv the validation model's, W the
+// L^2 weights of the voxel grid (V per voxel value, A per face value).  With
+// Uv W-orthonormal on each field, U_f a = Uv_f (T_f a) + R_f a with R_f a
+// W-orthogonal to span Uv_f, so
+//   e_f^2 = || T_f a - av|_f ||_2^2 + a^T G_f a,   G_f = R_f^T W R_f,
+// T_f and G_f formed once from the bases (no cancellation between the two
+// models' reconstructions); per instance and step only O(Nv Nr + Nr^2) flops on
+// the coefficients.  One block per instance, FP64, deterministic sums.
+namespace mb {
+
+constexpr int EST_THREADS = 256;
+
+__global__ void __launch_bounds__(EST_THREADS)
+k_rom_estimate(int Nr, int Nv, const double* __restrict__ a, const double* __restrict__ av,
+               const double* __restrict__ T, const int* __restrict__ fld, const double* __restrict__ G, int g0, int g1,
+               int g2, const int* __restrict__ failed, const int* __restrict__ failed_v, double scale,
+               double* __restrict__ est) {
+    __shared__ double sa[ROM_NR_MAX];
+    __shared__ double part[EST_THREADS / 32][3];
+    const int b = blockIdx.x;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int i = threadIdx.x; i < Nr; i += blockDim.x) sa[i] = a[(int64_t)b * Nr + i];
+    __syncthreads();
+    double acc[3] = {0.0, 0.0, 0.0};
+    // || T a - av ||^2 per field: one warp per validation mode
+    for (int j = wid; j < Nv; j += nw) {
+        const int f = fld[j];
+        if (f < 0) continue;
+        double t = 0.0;
+        for (int i = lane; i < Nr; i += 32) t = fma(T[(int64_t)j * Nr + i], sa[i], t);
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+        if (lane == 0) {
+            const double d = t - av[(int64_t)b * Nv + j];
+            acc[f] = fma(d, d, acc[f]);
+        }
+    }
+    // a^T G_f a: one warp per row of G_f
+    const int gon[3] = {g0, g1, g2};
+    for (int f = 0; f < 3; ++f) {
+        if (!gon[f]) continue;
+        const double* Gf = G + (int64_t)f * Nr * Nr;
+        for (int i = wid; i < Nr; i += nw) {
+            double t = 0.0;
+            for (int k = lane; k < Nr; k += 32) t = fma(Gf[(int64_t)i * Nr + k], sa[k], t);
+            for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+            if (lane == 0) acc[f] = fma(sa[i], t, acc[f]);
+        }
+    }
+    if (lane == 0)
+        for (int f = 0; f < 3; ++f) part[wid][f] = acc[f];
+    __syncthreads();
+    if (threadIdx.x < 3) {
+        double sum = 0.0;
+        for (int w = 0; w < nw; ++w) sum += part[w][threadIdx.x];
+        const bool bad = failed[b] || failed_v[b];
+        est[(int64_t)b * 3 + threadIdx.x] = bad ? NAN : scale * sqrt(fmax(sum, 0.0));
+    }
+}
+
+// field of unknown i: 0 concentration, 1 potential, 2 plated-Li face
+static inline int est_field(int64_t i, int64_t N) { return i < N ? 0 : (i < 2 * N ? 1 : 2); }
+
+// T, G_f and the fields of the validation modes for the pair (R, Rv)
+static int rom_est_setup(mb_rom* R, mb_rom* Rv) {
+    RomEst& E = R->est;
+    if (E.val == Rv && E.T) return MB_OK;
+    for (void* p : E.bufs) cudaFree(p);
+    E = RomEst();
+    const mb_cell* c = R->cell;
+    const int64_t n = c->n, N = c->D.N;
+    const int Nr = R->d.Nr, Nv = Rv->d.Nr;
+    const std::vector<double>& U = R->hU;
+    const std::vector<double>& Uv = Rv->hU;
+    const double wv = c->P.V, wa = c->P.A;
+    auto wt = [&](int64_t i) { return i < 2 * N ? wv : wa; };
+    // field of each validation mode (its nonzero rows must lie in one field)
+    std::vector<int> fld(Nv, -1);
+    for (int64_t i = 0; i < n; ++i) {
+        const int f = est_field(i, N);
+        for (int j = 0; j < Nv; ++j)
+            if (Uv[(size_t)i * Nv + j] != 0.0) {
+                if (fld[j] >= 0 && fld[j] != f) {
+                    set_error("mb_rom_estimate_batch: a validation mode spans more than one field");
+                    return MB_EINVAL;
+                }
+                fld[j] = f;
+            }
+    }
+    std::vector<int> vm[3], um[3];   // validation modes of each field; reduced modes nonzero there
+    for (int j = 0; j < Nv; ++j)
+        if (fld[j] >= 0) vm[fld[j]].push_back(j);
+    {
+        std::vector<char> seen((size_t)3 * Nr, 0);
+        for (int64_t i = 0; i < n; ++i) {
+            const int f = est_field(i, N);
+            for (int k = 0; k < Nr; ++k)
+                if (U[(size_t)i * Nr + k] != 0.0 && !seen[(size_t)f * Nr + k]) {
+                    seen[(size_t)f * Nr + k] = 1;
+                    um[f].push_back(k);
+                }
+        }
+        for (int f = 0; f < 3; ++f) std::sort(um[f].begin(), um[f].end());
+    }
+    // Uv must be W-orthonormal on each field
+    std::vector<double> Gv((size_t)Nv * Nv, 0.0);
+    for (int64_t i = 0; i < n; ++i) {
+        const std::vector<int>& V = vm[est_field(i, N)];
+        const double w = wt(i);
+        for (size_t p = 0; p < V.size(); ++p) {
+            const double x = w * Uv[(size_t)i * Nv + V[p]];
+            if (x == 0.0) continue;
+            for (size_t q = 0; q < V.size(); ++q) Gv[(size_t)V[p] * Nv + V[q]] += x * Uv[(size_t)i * Nv + V[q]];
+        }
+    }
+    for (int f = 0; f < 3; ++f)
+        for (int p : vm[f])
+            for (int q : vm[f])
+                if (fabs(Gv[(size_t)p * Nv + q] - (p == q ? 1.0 : 0.0)) > 1e-8) {
+                    set_error("mb_rom_estimate_batch: the validation basis is not W-orthonormal on each field");
+                    return MB_EINVAL;
+                }
+    // T[j][k] = sum over rows of field f(j) of w Uv[., j] U[., k]
+    std::vector<double> T((size_t)Nv * Nr, 0.0);
+    for (int64_t i = 0; i < n; ++i) {
+        const int f = est_field(i, N);
+        const double w = wt(i);
+        for (int j : vm[f]) {
+            const double x = w * Uv[(size_t)i * Nv + j];
+            if (x == 0.0) continue;
+            for (int k : um[f]) T[(size_t)j * Nr + k] += x * U[(size_t)i * Nr + k];
+        }
+    }
+    // G_f = sum over rows of field f of w r r^T, r = U row - Uv row T (only the modes nonzero there)
+    std::vector<double> G((size_t)3 * Nr * Nr, 0.0);
+    std::vector<double> r(Nr);
+    for (int64_t i = 0; i < n; ++i) {
+        const int f = est_field(i, N);
+        if (um[f].empty()) continue;
+        const double w = wt(i);
+        for (int k : um[f]) {
+            double x = U[(size_t)i * Nr + k];
+            for (int j : vm[f]) x -= Uv[(size_t)i * Nv + j] * T[(size_t)j * Nr + k];
+            r[k] = x;
+        }
+        double* Gf = G.data() + (size_t)f * Nr * Nr;
+        for (int k : um[f]) {
+            const double x = w * r[k];
+            if (x == 0.0) continue;
+            for (int l : um[f]) Gf[(size_t)k * Nr + l] += x * r[l];
+        }
+    }
+    for (int f = 0; f < 3; ++f)
+        for (size_t q = 0; q < (size_t)Nr * Nr && !E.gon[f]; ++q) E.gon[f] = G[(size_t)f * Nr * Nr + q] != 0.0;
+    E.T = rom_alloc<double>(E.bufs, T.size());
+    E.G = rom_alloc<double>(E.bufs, G.size());
+    E.fld = rom_alloc<int>(E.bufs, Nv);
+    if (!E.T || !E.G || !E.fld) return MB_ENOMEM;
+    MB_CUDA(cudaMemcpy(E.T, T.data(), 8 * T.size(), cudaMemcpyHostToDevice));
+    MB_CUDA(cudaMemcpy(E.G, G.data(), 8 * G.size(), cudaMemcpyHostToDevice));
+    MB_CUDA(cudaMemcpy(E.fld, fld.data(), 4 * fld.size(), cudaMemcpyHostToDevice));
+    E.val = Rv;
+    E.Nv = Nv;
+    return MB_OK;
+}
+
+}  // namespace mb
+
+extern "C" int mb_rom_estimate_batch(mb_rom* R, mb_rom* Rv, double theta, int B, const mb_rom_params* prm,
+                                     int n_steps, double dt, double* V_out, double* Vv_out, double* est_out,
+                                     mb_rom_info* info) {
+    if (!R || !Rv || R == Rv || !(theta >= 0.0 && theta < 1.0) || B < 1 || !prm || n_steps < 0 || !(dt > 0) ||
+        !est_out) {
+        set_error("mb_rom_estimate_batch: invalid argument");
+        return MB_EINVAL;
+    }
+    if (R->cell->n != Rv->cell->n || R->cell->D.N != Rv->cell->D.N) {
+        set_error("mb_rom_estimate_batch: the two models belong to cells of different sizes");
+        return MB_EINVAL;
+    }
+    int rc = rom_est_setup(R, Rv);
+    if (rc) return rc;
+    RomEst& E = R->est;
+    if (E.Bcap < B) {
+        E.est = rom_alloc<double>(E.bufs, (size_t)3 * B);
+        if (!E.est) { set_error("mb_rom_estimate_batch: device memory"); return MB_ENOMEM; }
+        E.Bcap = B;
+    }
+    if ((rc = rom_batch_begin(R, B, prm, dt)) || (rc = rom_batch_begin(Rv, B, prm, dt))) return rc;
+    const int ncol = n_steps + 1;
+    const double scale = 1.0 / (1.0 - theta);
+    std::vector<double> hV(B), hS(B), hVv(B), hSv(B), he((size_t)3 * B);
+    std::vector<int> hf(B), hfv(B);
+    cudaStream_t s = R->cell->stream;
+    for (int step = 0; step <= n_steps; ++step) {
+        if (step > 0 && ((rc = rom_batch_step(R)) || (rc = rom_batch_step(Rv)))) return rc;
+        // both streams are idle after their outputs are read
+        if ((rc = rom_batch_outputs(R, hV.data(), hS.data(), hf.data())) ||
+            (rc = rom_batch_outputs(Rv, hVv.data(), hSv.data(), hfv.data())))
+            return rc;
+        k_rom_estimate<<<(unsigned)B, EST_THREADS, 0, s>>>(R->d.Nr, E.Nv, R->w.a, Rv->w.a, E.T, E.fld, E.G, E.gon[0],
+                                                          E.gon[1], E.gon[2], R->w.failed, Rv->w.failed, scale,
+                                                          E.est), count_launch(R->cell);
+        MB_CUDA_LAUNCH("rom_estimate");
+        MB_CUDA(cudaMemcpyAsync(he.data(), E.est, 8 * he.size(), cudaMemcpyDeviceToHost, s));
+        MB_CUDA(cudaStreamSynchronize(s));
+        for (int b = 0; b < B; ++b) {
+            for (int f = 0; f < 3; ++f) est_out[((size_t)b * ncol + step) * 3 + f] = he[(size_t)b * 3 + f];
+            if (V_out) V_out[(size_t)b * ncol + step] = hf[b] ? NAN : hV[b];
+            if (Vv_out) Vv_out[(size_t)b * ncol + step] = hfv[b] ? NAN : hVv[b];
+        }
+    }
+    mb_rom_info inf{0, 0, 0};
+    for (int b = 0; b < B; ++b) {
+        long long its = 0, flips = 0;
+        if ((rc = rom_slot_stats(R, b, &its, &flips, nullptr))) return rc;
+        inf.newton_its += its;
+        inf.flips += flips;
+        inf.failed += (hf[b] || hfv[b]) ? 1 : 0;
+    }
+    if (info) *info = inf;
+    if (inf.failed) {
+        set_error("mb_rom_estimate_batch: reduced Newton did not converge for some instances");
         return MB_ENOCONV;
     }
     return MB_OK;

@@ -7,13 +7,13 @@ compare against (tests/golden/fom_*.npz).  Calls only oracle/ and synthetic/.
   the rest state, 60 implicit Euler steps of dt = 1 s (the paper's 60 s
   protocol, Sec. results).  Stored: the functionals of every step and the
   whole state after steps 1, 30 and 60.
-* cell32x32x96: the same generator rules at twice the size (anode 40 |
-  separator 16 | cathode 40), seeds (13, 14), plated lithium seeded on every
+* cell24x24x72: the same generator rules at 1.5 times the size (anode 30 |
+  separator 12 | cathode 30), seeds (13, 14), plated lithium seeded on every
   third graphite-electrolyte face (4e-5 mol/m^2), 3 steps of a 2C charge.
   Large enough for a multigrid hierarchy of five levels.  Stored: the
   functionals of every step and every fifth unknown of the final state.
 
-Usage: python tests/golden/make_fom_trajectories.py [cfg1|cell32x32x96 ...]
+Usage: python tests/golden/make_fom_trajectories.py [cfg1|cell24x24x72 ...]
 """
 import os
 import sys
@@ -31,7 +31,7 @@ from oracle.fom import Cell  # noqa: E402
 CASES = {
     "cfg1": dict(geom=(16, 16, 20, 8, 20, 0.35, 0.35, ("uniform", 2, 4), (11, 12)), crate=-1.0, steps=60,
                  seed_n=None, keep=(1, 30, 60), stride=1),
-    "cell32x32x96": dict(geom=(32, 32, 40, 16, 40, 0.35, 0.35, ("uniform", 2, 4), (13, 14)), crate=-2.0, steps=3,
+    "cell24x24x72": dict(geom=(24, 24, 30, 12, 30, 0.35, 0.35, ("uniform", 2, 4), (13, 14)), crate=-2.0, steps=3,
                          seed_n=4e-5, keep=(3,), stride=5),
 }
 

@@ -150,3 +150,4 @@ def test_step_parity(params, geom, precision, tol):
         assert all(v <= tol for v in rel.values()), (k, rel, info)
         assert abs(info["V_cell"] - oinfo["V_cell"]) <= tol * abs(oinfo["V_cell"])
         assert abs(info["Li_total"] - oinfo["Li_total"]) <= 1e-12 * oinfo["Li_total"]
+        assert info["passes"] == oinfo["passes"] and info["unresolved_flips"] == oinfo["unresolved_flips"], k

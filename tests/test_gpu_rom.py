@@ -44,6 +44,23 @@ def _gpu_rom(B, lab, params, rom):
 PRM = [(-3.5, 1.2, 0.5), (-1.0, 1.0, 1.0), (-4.5, 0.6, 4.0)]
 
 
+def _coef_check(rom, a_gpu, a_ref, tol):
+    """Final coefficients element by element, per block (c modes, plated-Li
+    modes, phi modes) relative to the block's largest coefficient, and the
+    reconstruction on the stencil closure of the points (the values the
+    model's nonlinear terms see) in the unknown scales."""
+    blocks = (slice(0, rom.nc), slice(rom.nc, rom.rc), slice(rom.rc, rom.rc + rom.rp))
+    for name, sl in zip(("c", "n", "phi"), blocks):
+        ref = a_ref[sl]
+        if ref.size == 0 or np.max(np.abs(ref)) == 0:
+            continue
+        err = np.max(np.abs(a_gpu[sl] - ref)) / np.max(np.abs(ref))
+        assert err <= tol, (name, err)
+    ug = rom.Uloc @ a_gpu
+    uo = rom.Uloc @ a_ref
+    assert np.max(np.abs(ug - uo) / rom.us_loc) <= tol
+
+
 @pytest.mark.gpu
 def test_rom_solve_matches_oracle(params, case):
     B = _gpu()
@@ -125,6 +142,7 @@ def test_rom_wide_matches_oracle(params, wide_case):
         ref = R.solve(rom, p[0], p[1], p[2], 1.0, 3)
         assert np.max(np.abs(out["V"][b] - ref["V_cell"])) <= 1e-9 * np.max(np.abs(ref["V_cell"])), b
         assert np.max(np.abs(out["s_ac"][b] - ref["s_ac"])) <= 1e-9 * np.max(np.abs(ref["s_ac"])), b
+        _coef_check(rom, out["a"][b], ref["a"][-1], 1e-8)
     g.close()
     gc.close()
 
@@ -212,6 +230,8 @@ def test_rom_refine_matches_oracle(params, wide_case):
         ref = R.solve(rom, p[0], p[1], p[2], 1.0, 3)
         assert np.max(np.abs(out["V"][b] - ref["V_cell"])) <= 1e-9 * np.max(np.abs(ref["V_cell"])), b
         assert np.max(np.abs(out["s_ac"][b] - ref["s_ac"])) <= 1e-9 * np.max(np.abs(ref["s_ac"])), b
+        _coef_check(rom, out["a"][b], ref["a"][-1], 1e-8)
+        _coef_check(rom, lu["a"][b], ref["a"][-1], 1e-8)
     assert np.max(np.abs(out["V"] - lu["V"])) <= 1e-9 * np.max(np.abs(lu["V"]))
     g.close()
     gc.close()

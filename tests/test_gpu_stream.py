@@ -49,3 +49,33 @@ def test_stream_modes_bit_identical(params):
         assert np.array_equal(cells[s].state(), cells[0].state())
     for cell in cells.values():
         cell.close()
+
+
+def test_coarse_tail_bit_identical(params):
+    """The persistent coarse tail (levels 2 down to the coarsest solve in one
+    cooperative launch, grid barriers between the phases) runs the per-level
+    kernels' per-cell code in the same order: preconditioner applications and
+    implicit steps are bit-identical to per-level launches."""
+    B, torch = _gpu()
+    lab = syn.full_cell(64, 64, 53, 22, 53, 0.35, 0.35, ("uniform", 2, 4), (31, 32))
+    cells = {t: B.Cell(lab, 1e-6, params, B.default_opts(precision=1, newton_tol=1e-10, krylov_rtol=1e-4,
+                                                         mg_tail=t)) for t in (0, 1)}
+    a = cells[1]
+    assert len(a.debug_levels()) >= 4
+    rng = np.random.default_rng(9)
+    N = a.N
+    u = a.state()
+    u[:N] *= 1.0 + 0.01 * rng.standard_normal(N)
+    u[N:2 * N] += 0.002 * rng.standard_normal(N)
+    gate = np.zeros(a.F, np.uint8)
+    r = rng.standard_normal(a.n)
+    z = {t: cells[t].debug_precond(u, gate, 1.0, r) for t in cells}
+    assert np.all(np.isfinite(z[0]))
+    assert np.array_equal(z[1], z[0])
+    I = -2.0 * a.i_1c
+    for _ in range(2):
+        info = {t: cells[t].step(1.0, I) for t in cells}
+        assert info[1]["krylov_its"] == info[0]["krylov_its"] and info[1]["V_cell"] == info[0]["V_cell"]
+    assert np.array_equal(cells[1].state(), cells[0].state())
+    for cell in cells.values():
+        cell.close()
