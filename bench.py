@@ -60,7 +60,8 @@ def fom_opts(B, prec, args):
     or 1e-6 (FP64)."""
     return B.default_opts(precision=prec, newton_tol=1e-10, krylov_rtol=1e-4 if prec else 1e-6,
                           newton_maxit=20, krylov_maxit=300, max_halvings=3,
-                          mg_bf16=0 if args.fp32_coarse else 1, mg_stream=args.mg_stream)
+                          mg_bf16=0 if args.fp32_coarse else 1, mg_stream=args.mg_stream,
+                          mg_tail=0 if args.no_mg_tail else 1)
 
 
 def step_record(infos):
@@ -287,6 +288,7 @@ def rom_paper_dims(B, params, args, torch):
         V = np.array([fc.step(1.0, prm[b][0])["V_cell"] for _ in range(steps)])
         fc.close()
         errs.append(float(np.max(np.abs(out["V"][b][1:] - V)) / np.max(np.abs(V))))
+    est = rom_error_estimate(B, cell, rom, snap, prm, steps)
     res = {"workload": "ROM of the %s cell at the paper's dimensions, snapshots at (C-rate, i0 scale, k_pl) = "
                        "(0.5, 0.5, 0.1), (5, 2, 10), (2, 1, 1), (1, 1, 1), 60 steps each; %d of the 600 steps "
                        "timed" % (ROM_CELL, steps),
@@ -298,9 +300,43 @@ def rom_paper_dims(B, params, args, torch):
                         "by their f32 LU",
            "instance_steps_per_s": inst_steps / wall, "solves_per_s": args.rom_instances / wall, "wall_s": wall,
            "build_s": build_s, "newton_its_per_instance_step": out["newton_its"] / inst_steps,
-           "failed": out["failed"], "V_rel_err_vs_full_order_2_instances": errs}
+           "failed": out["failed"], "V_rel_err_vs_full_order_2_instances": errs,
+           "error_estimate": est}
     rom.close()
     cell.close()
+    return res
+
+
+def rom_error_estimate(B, cell, rom, snap, prm, steps, n_inst=256):
+    """The paper's certification step (Sec. workflow:MOR, Eq. ap4:estimate):
+    a reduced model with 97 % of the validation model's basis vectors and
+    interpolation points per block, built from the same snapshots, estimated
+    against the validation model `rom` on n_inst instances over the timed
+    steps with theta = 0.  Relative errors as the paper states them: L-inf in
+    time of the estimate over L-inf in time of the validation field's L^2
+    norm, the largest over the instances."""
+    import math
+    nc, nn, nphi = rom.block_dims()
+    d97 = tuple(int(math.ceil(0.97 * x)) for x in (nc, nn, nphi, rom.n_bv, rom.n_1c))
+    t0 = time.perf_counter()
+    r97 = B.Rom.build(cell, snap, 1.0, 60, d97, pod_tol=1e-9)
+    build_s = time.perf_counter() - t0
+    n_inst = min(n_inst, len(prm))
+    t0 = time.perf_counter()
+    out = r97.estimate(rom, prm[:n_inst], steps, 1.0, 0.0)
+    wall = time.perf_counter() - t0
+    e, nv = out["est"], out["norm_val"]
+    rel = {k: float(np.max(np.max(e[:, :, f], axis=1) / np.max(nv[:, :, f], axis=1)))
+           for f, k in enumerate(("c", "phi", "n_plated"))}
+    v_err = float(np.max(np.abs(out["V"] - out["V_val"]) / np.abs(out["V_val"])))
+    res = {"reduced_dims": {"n_r": r97.n_r, "blocks_c_n_phi": list(r97.block_dims()), "ei_interface": r97.n_bv,
+                            "ei_migration": r97.n_1c},
+           "validation_dims": {"n_r": rom.n_r, "blocks_c_n_phi": [nc, nn, nphi], "ei_interface": rom.n_bv,
+                               "ei_migration": rom.n_1c},
+           "instances": n_inst, "steps": steps, "theta": 0.0, "max_rel_estimate": rel,
+           "V_rel_diff_reduced_vs_validation": v_err, "failed": out["failed"], "wall_s": wall,
+           "build_s": build_s}
+    r97.close()
     return res
 
 
@@ -440,6 +476,8 @@ def main():
                     help="smoother and coarse-level products from FP32 operators instead of their BF16 copies")
     ap.add_argument("--mg-stream", type=int, default=0, choices=[0, 1, 2],
                     help="operator fetch of the BF16 coarse sweeps: 0 plain, 1 L2 prefetch, 2 staged in shared memory")
+    ap.add_argument("--no-mg-tail", action="store_true",
+                    help="coarse V-cycle levels by per-level launches instead of one persistent launch")
     ap.add_argument("--no-fp64-arm", action="store_true",
                     help="skip the FP64 run of the same steps (and the mixed-vs-FP64 errors)")
     ap.add_argument("--no-rom", action="store_true", help="skip the reduced-model and serving measurements")
@@ -592,6 +630,7 @@ def main():
                           "device_bytes": int(cell.device_bytes),
                           "dt_s": dt, "crate": CRATE[args.workload], "precision": args.precision,
                           "coarse_operators": "fp32" if args.fp32_coarse else "bf16", "mg_stream": args.mg_stream,
+                          "mg_tail": 0 if args.no_mg_tail else 1,
                           "l2": "working set > 129 MB L2, no flush", "parallelism": "replicas" if ws > 1 else "1 GPU"},
                "clocks": clk, "e2e": e2e, "gpu_launches": int(launches), "roofline": roof,
                "cpu_baseline": cpu,

@@ -262,6 +262,9 @@ typedef struct {
 int mb_rom_build(mb_cell* cell, const mb_rom_build_opts* o, mb_rom** out);
 /* Dimensions of a reduced model: N_r and the two numbers of points. */
 int mb_rom_dims(mb_rom* rom, int* n_r, int* n_bv, int* n_1c);
+/* Reduced modes by field: basis columns supported only on the concentration
+ * rows (n_c), the plated-Li face rows (n_n) or the potential rows (n_phi). */
+int mb_rom_block_dims(mb_rom* rom, int* n_c, int* n_n, int* n_phi);
 
 /* Build the reduced model of `cell` from the arrays of d (MB_EINVAL on
  * inconsistent sizes or points outside the residual). */
@@ -301,13 +304,15 @@ int mb_rom_solve_batch(mb_rom* rom, int B, const mb_rom_params* prm, int n_steps
  * coefficients (no reconstruction).  est_out: host double[B * (n_steps + 1)
  * * 3], instance-major, then step, then field (c, phi, n); V_out and
  * V_val_out (may be NULL): host double[B * (n_steps + 1)], the two models'
- * cell potentials.  theta in [0, 1).  MB_EINVAL for models of different
+ * cell potentials; norm_val_out (may be NULL): as est_out, the W-norms of
+ * the validation model's fields (the denominators of relative errors).
+ * theta in [0, 1).  MB_EINVAL for models of different
  * cells or a validation basis that is not W-orthonormal per field;
  * MB_ENOCONV (estimates NaN from then on) if an instance failed in either
  * model. */
 int mb_rom_estimate_batch(mb_rom* rom, mb_rom* rom_val, double theta, int B, const mb_rom_params* prm,
                           int n_steps, double dt, double* V_out, double* V_val_out, double* est_out,
-                          mb_rom_info* info);
+                          double* norm_val_out, mb_rom_info* info);
 
 /* ---- serving loop (parameter-study queries; no counterpart in the paper) ----
  * Requests arrive at any time (mb_serve_submit never blocks).  Reduced-model

@@ -58,6 +58,11 @@ int mb_debug_rom_lu(int Nr, int B, int fp64, int in_place, const double* J, cons
 /* Escalated instances of the online solve: GMRES on FP64 products preconditioned by
  * the instance's last FP32 LU (on = 1, the default), or the FP64 Newton matrix and LU (0). */
 int mb_debug_rom_refine(mb_rom* rom, int on);
+/* Take each time step of the online solve as one CUDA graph launch (on = 1,
+ * the default: conditional nodes run the active-set passes, the Newton
+ * iterations and the escalated branch on the device) or drive the loops from
+ * the host (0).  Both give the same results. */
+int mb_debug_rom_graph(mb_rom* rom, int on);
 /* Use (on = 1, the default) or not the tensor-core Newton-matrix kernel in the online solve. */
 int mb_debug_rom_tensor(mb_rom* rom, int on);
 

@@ -137,7 +137,8 @@ def _declare(lib):
     fn("mb_rom_solve_batch", C.c_int, [VP, C.c_int, C.POINTER(RomParams), C.c_int, C.c_double, VP, VP, VP,
                                         C.POINTER(RomInfo)])
     fn("mb_rom_estimate_batch", C.c_int, [VP, VP, C.c_double, C.c_int, C.POINTER(RomParams), C.c_int, C.c_double,
-                                          VP, VP, VP, C.POINTER(RomInfo)])
+                                          VP, VP, VP, VP, C.POINTER(RomInfo)])
+    fn("mb_rom_block_dims", C.c_int, [VP, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)])
     fn("mb_jvp", C.c_int, [VP, VP, VP, C.c_double, VP, VP])
     fn("mb_jvp_dev", C.c_int, [VP, VP, VP, C.c_double, VP, VP, VP])
     fn("mb_jvp_f32_dev", C.c_int, [VP, VP, VP, C.c_double, VP, VP, VP])
@@ -154,6 +155,7 @@ def _declare(lib):
     fn("mb_debug_fine", C.c_int, [VP, VP, VP, VP])
     fn("mb_debug_fine_stencil", C.c_int, [VP, VP])
     fn("mb_debug_rom_jac", C.c_int, [C.c_int, C.c_int, C.c_int, VP, VP, VP, VP, VP, C.c_int, VP])
+    fn("mb_debug_rom_graph", C.c_int, [VP, C.c_int])
     fn("mb_debug_rom_tensor", C.c_int, [VP, C.c_int])
     fn("mb_debug_rom_refine", C.c_int, [VP, C.c_int])
     fn("mb_debug_rom_lu", C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, VP, VP, VP])
@@ -432,18 +434,29 @@ class Rom:
         B = len(params)
         prm = (RomParams * B)(*[RomParams(*map(float, p)) for p in params])
         est = np.empty((B, n_steps + 1, 3))
+        nrm = np.empty((B, n_steps + 1, 3))
         V = np.empty((B, n_steps + 1))
         Vv = np.empty((B, n_steps + 1))
         info = RomInfo()
         rc = lib().mb_rom_estimate_batch(self.h, val.h, float(theta), B, prm, int(n_steps), float(dt), _ptr(V),
-                                         _ptr(Vv), _ptr(est), C.byref(info))
+                                         _ptr(Vv), _ptr(est), _ptr(nrm), C.byref(info))
         if rc != 0 and rc != -4:
             _check(rc)
-        return dict(est=est, V=V, V_val=Vv, newton_its=int(info.newton_its), failed=int(info.failed), ok=rc == 0)
+        return dict(est=est, norm_val=nrm, V=V, V_val=Vv, newton_its=int(info.newton_its),
+                    failed=int(info.failed), ok=rc == 0)
+
+    def block_dims(self):
+        """(n_c, n_n, n_phi): reduced modes by field."""
+        a, b_, c = C.c_int(), C.c_int(), C.c_int()
+        _check(lib().mb_rom_block_dims(self.h, C.byref(a), C.byref(b_), C.byref(c)))
+        return a.value, b_.value, c.value
 
     def debug_refine(self, on):
         """Escalated instances by GMRES preconditioned with the FP32 LU (on, the default) or the FP64 LU (off)."""
         _check(lib().mb_debug_rom_refine(self.h, 1 if on else 0))
+
+    def debug_graph(self, on):
+        _check(lib().mb_debug_rom_graph(self.h, int(bool(on))))
 
     def debug_tensor(self, on):
         """Newton-matrix GEMM on the tensor cores (3xTF32, the default) or FP32 FMA."""

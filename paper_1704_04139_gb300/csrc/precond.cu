@@ -1284,7 +1284,7 @@ __global__ void k_lvl_restrict(Level L, const DF4* __restrict__ x, Level C) {
 // bounded: on a timeout a block sets bit 4 of *err and returns (the kernel
 // holds no asynchronous copies).  Iterates alternate between x and x2 of each
 // level exactly as the host-side sequence does.
-constexpr int TAIL_THREADS = 256;
+constexpr int TAIL_THREADS = 512;
 constexpr int TAIL_SPIN = 1 << 20;        // polls (64 ns apart) per barrier before giving up
 
 struct TailLv {
@@ -1338,7 +1338,7 @@ __device__ inline bool tail_barrier(unsigned* bar, unsigned& gen) {
     return __syncthreads_and(ok) != 0;
 }
 
-__global__ void __launch_bounds__(TAIL_THREADS) k_vtail(TailArgs a) {
+__global__ void __launch_bounds__(TAIL_THREADS, 1) k_vtail(TailArgs a) {
     __shared__ double sb[COARSE_MAX];
     __shared__ double sx[COARSE_MAX];
     unsigned gen = 0;
@@ -1655,8 +1655,10 @@ int precond_create(mb_cell* c) {
     p->kH = (double*)cell_alloc(c, 8 * (size_t)((KCYC_MAX + 1) * KCYC_MAX + 128));
     p->kred = (double*)cell_alloc(c, 8 * (size_t)RED_BLOCKS * 8);
     if (!p->cdense || !p->cinv || !p->cstat || !p->kV || !p->kZ || !p->kw || !p->kH || !p->kred) return MB_ENOMEM;
-    // persistent coarse tail: from the first level >= 2 that one resident wave of
-    // TAIL_THREADS-thread blocks covers (at most two blocks per SM, all co-resident)
+    // persistent coarse tail: from the first level >= 2 that one block of
+    // TAIL_THREADS threads per SM covers; its grid is one block per
+    // TAIL_THREADS cells of that level (all co-resident), so a small cell's
+    // tail is a single block and does not wait for the whole GPU
     p->tbar = (unsigned*)cell_alloc(c, 16);
     if (!p->tbar) return MB_ENOMEM;
     p->tail_l0 = 0;
@@ -1667,10 +1669,13 @@ int precond_create(mb_cell* c) {
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_vtail, TAIL_THREADS, 0) != cudaSuccess)
             return cuda_fail(cudaGetLastError(), "coarse tail occupancy");
         if (coop && occ >= 1) {
-            p->tail_blocks = (occ < 2 ? occ : 2) * p->nsm;
-            const int64_t cap = (int64_t)p->tail_blocks * TAIL_THREADS;
+            const int64_t cap = (int64_t)p->nsm * TAIL_THREADS;
             for (int l = 2; l < p->nlev; ++l)
-                if (p->lv[l].cells <= cap) { p->tail_l0 = l; break; }
+                if (p->lv[l].cells <= cap) {
+                    p->tail_l0 = l;
+                    p->tail_blocks = (int)((p->lv[l].cells + TAIL_THREADS - 1) / TAIL_THREADS);
+                    break;
+                }
         }
     }
     return MB_OK;

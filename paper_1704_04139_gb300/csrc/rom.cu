@@ -58,6 +58,7 @@ enum RomTerm : int8_t { T_NONE = 0, T_GE = 1, T_KE = 2, T_LE = 3, T_EE = 4 };
 struct RomDev {
     int Nr = 0, Mbv = 0, M1c = 0, M = 0, nloc = 0, ngate = 0;
     int tc = 1;                // Newton-matrix GEMM on the tensor cores (3xTF32), else FP32 FMA
+    int graph = 1;             // a time step as one CUDA graph (else driven from the host)
     int ir = 1;                // escalated instances: GMRES on FP64 products preconditioned by the kept FP32 LU
     double* UlocR = nullptr;   // nloc x Nr
     double* us = nullptr;      // nloc unknown scales
@@ -111,6 +112,11 @@ struct RomWork {
     long long* its = nullptr;
     long long* flips = nullptr;
     double *V = nullptr, *S = nullptr;
+    // one reduced time step as a CUDA graph (conditional nodes run the passes,
+    // the Newton iterations and the escalated branch on the device)
+    cudaGraphExec_t gexec = nullptr;
+    int* ctl = nullptr;        // device: [0] Newton iteration of the pass, [1] passes done
+    bool graph_failed = false; // the graph could not be built: host-driven steps
     std::vector<void*> bufs;
 };
 
@@ -127,6 +133,7 @@ struct RomEst {
     int* fld = nullptr;        // Nv: field of validation mode j (0 c, 1 phi, 2 n; -1 none)
     int gon[3] = {0, 0, 0};    // G_f has a nonzero entry
     double* est = nullptr;     // B x 3 estimates of the current step
+    double* nrm = nullptr;     // B x 3 norms of the validation model's fields
     int Bcap = 0;
     std::vector<void*> bufs;
 };
@@ -144,9 +151,13 @@ struct mb_rom {
 namespace mb {
 
 static void rom_work_free(RomWork& w) {
+    if (w.gexec) cudaGraphExecDestroy(w.gexec);
     for (void* p : w.bufs) cudaFree(p);
     w = RomWork();
 }
+
+// field of unknown i: 0 concentration, 1 potential, 2 plated-Li face
+static inline int est_field(int64_t i, int64_t N) { return i < N ? 0 : (i < 2 * N ? 1 : 2); }
 
 template <class T>
 static T* rom_alloc(std::vector<void*>& list, size_t n) {
@@ -207,7 +218,10 @@ __global__ void k_rom_ei(RomDev d, DevParams P, ParT<float> Pf, int B, const dou
     if (i >= (int64_t)d.M * B) return;   // HP: B = length of hplist
     int b = (int)(i / d.M);
     const int p = (int)(i % d.M);
-    if (HP) b = hplist[b];
+    if (HP) {
+        b = hplist[b];
+        if (b < 0) return;   // past the end of the list (launched for the whole batch)
+    }
     if (!active[b] || (hp[b] != 0) != HP) return;
     const double* u = uloc + (int64_t)b * d.nloc;
     const double s_i0 = prm[RP * b + 1], k_pl = prm[RP * b + 2];
@@ -327,15 +341,23 @@ __device__ inline void mma_tf32(float (&c)[4], const uint32_t (&a)[4], const uin
 template <bool TC>
 __global__ void __launch_bounds__(256)
 k_rom_jac(RomDev d, int B, int nlist, const int* __restrict__ alist, const double* __restrict__ prm,
-          const float* __restrict__ GU, const int* __restrict__ hp, float* __restrict__ J) {
+          const float* __restrict__ GU, const int* __restrict__ hp, float* __restrict__ J,
+          const int* __restrict__ dit, const int* __restrict__ dnlist) {
     __shared__ float As[JT_K][JT_ROWS + JT_PAD];
     __shared__ float Bs[JT_K][JT_COLS + JT_PAD];
     const int Nr = d.Nr, M = d.M;
+    // device-side choice (a launch inside a graph, grid for the whole batch):
+    // the first iteration of a pass takes every instance, later ones the list
+    if (dit) {
+        if (*dit > 0) nlist = *dnlist;
+        else alist = nullptr;
+    }
     // columns c = l Nr + j of the listed instances b = alist[l] (all B in order without a list)
     const int ncol = (alist ? nlist : B) * Nr;
     const int64_t gstride = (int64_t)B * Nr;   // row stride of GU
     const int c0 = blockIdx.x * JT_COLS;
     const int i0 = blockIdx.y * JT_ROWS;
+    if (c0 >= ncol) return;   // the block's columns are all past the end
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
     // loader: this thread fills column lq of both tiles at K rows kq + 4 m; the row of P^T
     // and the column of GU it reads are fixed over the K loop
@@ -448,34 +470,45 @@ k_rom_jac(RomDev d, int B, int nlist, const int* __restrict__ alist, const doubl
 // FP64 Newton matrix of the instances with hp[b]: GU64[b][p][:] = G64[b][p] U_loc
 // (one block per point and instance), then J64[b] = Ms/dt + Alin + P GU64[b]
 // (one block per row and instance)
+// listed instances k = blockIdx.y, blockIdx.y + gridDim.y, ... < nmax (a
+// negative list entry ends the list)
 __global__ void k_rom_gu64(RomDev d, const double* __restrict__ G, const int* __restrict__ active,
-                           const int* __restrict__ hp, const int* __restrict__ hplist, double* __restrict__ GU) {
-    const int p = blockIdx.x, b = hplist[blockIdx.y];
-    if (!active[b] || !hp[b]) return;
-    const double* Gp = G + ((int64_t)b * d.M + p) * GMAX;
+                           const int* __restrict__ hp, const int* __restrict__ hplist, int nmax,
+                           double* __restrict__ GU) {
+    const int p = blockIdx.x;
     const int32_t* gi = d.gidx + (int64_t)p * GMAX;
-    for (int j = threadIdx.x; j < d.Nr; j += blockDim.x) {
-        double acc = 0.0;
-        for (int e = 0; e < GMAX; ++e) {
-            const int s = gi[e];
-            if (s < 0) break;
-            acc += Gp[e] * d.UlocR[(int64_t)s * d.Nr + j];
+    for (int k = blockIdx.y; k < nmax; k += gridDim.y) {
+        const int b = hplist[k];
+        if (b < 0) return;
+        if (!active[b] || !hp[b]) continue;
+        const double* Gp = G + ((int64_t)b * d.M + p) * GMAX;
+        for (int j = threadIdx.x; j < d.Nr; j += blockDim.x) {
+            double acc = 0.0;
+            for (int e = 0; e < GMAX; ++e) {
+                const int s = gi[e];
+                if (s < 0) break;
+                acc += Gp[e] * d.UlocR[(int64_t)s * d.Nr + j];
+            }
+            GU[((int64_t)b * d.M + p) * d.Nr + j] = acc;
         }
-        GU[((int64_t)b * d.M + p) * d.Nr + j] = acc;
     }
 }
 __global__ void k_rom_jac64(RomDev d, const double* __restrict__ prm, const double* __restrict__ GU,
                             const int* __restrict__ active, const int* __restrict__ hp,
-                            const int* __restrict__ hplist, double* __restrict__ J) {
-    const int i = blockIdx.x, b = hplist[blockIdx.y];
-    if (!active[b] || !hp[b]) return;
-    const double dt_inv = prm[RP * b + 3];
+                            const int* __restrict__ hplist, int nmax, double* __restrict__ J) {
+    const int i = blockIdx.x;
     const double* Pi = d.P + (int64_t)i * d.M;
-    const double* GUb = GU + (int64_t)b * d.M * d.Nr;
-    for (int j = threadIdx.x; j < d.Nr; j += blockDim.x) {
-        double acc = d.Ms[(int64_t)i * d.Nr + j] * dt_inv + d.Alin[(int64_t)i * d.Nr + j];
-        for (int p = 0; p < d.M; ++p) acc += Pi[p] * GUb[(int64_t)p * d.Nr + j];
-        J[((int64_t)b * d.Nr + i) * d.Nr + j] = acc;
+    for (int k = blockIdx.y; k < nmax; k += gridDim.y) {
+        const int b = hplist[k];
+        if (b < 0) return;
+        if (!active[b] || !hp[b]) continue;
+        const double dt_inv = prm[RP * b + 3];
+        const double* GUb = GU + (int64_t)b * d.M * d.Nr;
+        for (int j = threadIdx.x; j < d.Nr; j += blockDim.x) {
+            double acc = d.Ms[(int64_t)i * d.Nr + j] * dt_inv + d.Alin[(int64_t)i * d.Nr + j];
+            for (int p = 0; p < d.M; ++p) acc += Pi[p] * GUb[(int64_t)p * d.Nr + j];
+            J[((int64_t)b * d.Nr + i) * d.Nr + j] = acc;
+        }
     }
 }
 
@@ -531,6 +564,7 @@ k_rom_lu(int Nr, T* __restrict__ J, const double* __restrict__ r, const int* __r
          const int* __restrict__ hp, int want_hp, const int* __restrict__ list, double* __restrict__ delta,
          int* __restrict__ piv_out = nullptr, T* __restrict__ sc_out = nullptr) {
     const int b = list ? list[blockIdx.x] : blockIdx.x;
+    if (b < 0) return;   // past the end of the list (launched for the whole batch)
     if (!active[b] || (hp[b] != 0) != (want_hp != 0)) return;
     extern __shared__ __align__(16) unsigned char lu_raw[];
     T* const sm = reinterpret_cast<T*>(lu_raw);
@@ -697,6 +731,7 @@ k_rom_gmres(RomDev d, const double* __restrict__ prm, const double* __restrict__
             const int* __restrict__ active, const int* __restrict__ hp, const int* __restrict__ hplist, int m,
             int cycles, double eta, double* __restrict__ delta) {
     const int b = hplist[blockIdx.x];
+    if (b < 0) return;   // past the end of the list (launched for the whole batch)
     if (!active[b] || !hp[b]) return;
     const int Nr = d.Nr, M = d.M;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
@@ -999,6 +1034,9 @@ __global__ void k_rom_count_hp(int B, const int* __restrict__ active, const int*
     atomicAdd(&c0, a);
     __syncthreads();
     if (threadIdx.x == 0) { out[0] = c0; out[1] = c1; out[2] = c2; }
+    // end both lists with -1 (kernels launched for the whole batch stop there)
+    for (int b = c1 + threadIdx.x; b < B; b += blockDim.x) list[b] = -1;
+    for (int b = c2 + threadIdx.x; b < B; b += blockDim.x) alist[b] = -1;
 }
 
 // copy src -> dst for instances with mask[b] (all instances if mask is null)
@@ -1024,7 +1062,8 @@ __global__ void k_rom_set_active(int B, const int* __restrict__ on, const int* _
 // (g1 and gate may be the same buffer: g1 is read before the barrier, gate written after it)
 __global__ void k_rom_flips(int ngate, int B, const uint8_t* g1, const uint8_t* __restrict__ g2,
                             const int* __restrict__ failed, int* __restrict__ pass_on, long long* __restrict__ flips,
-                            uint8_t* gate, int last_pass) {
+                            uint8_t* gate, int last_pass, const int* __restrict__ dpass) {
+    if (dpass) last_pass = *dpass + 1 >= ROM_PASSES;   // pass number kept on the device (graph launch)
     const int b = blockIdx.x;
     __shared__ int cnt;
     if (threadIdx.x == 0) cnt = 0;
@@ -1409,6 +1448,7 @@ static int rom_work_alloc(mb_rom* R, int B) {
     w.failed = rom_alloc<int>(L, B);
     w.pass_on = rom_alloc<int>(L, B);
     w.counts = rom_alloc<int>(L, 4);
+    w.ctl = rom_alloc<int>(L, 4);
     w.its = rom_alloc<long long>(L, B);
     w.flips = rom_alloc<long long>(L, B);
     w.V = rom_alloc<double>(L, (size_t)B);
@@ -1477,111 +1517,348 @@ int rom_slot_stats(mb_rom* R, int b, long long* its, long long* flips, double* a
     return MB_OK;
 }
 
-// one implicit Euler step of every occupied slot (reduced Newton with the
-// plating active-set passes); a slot whose Newton iteration fails is marked
-// failed (and skipped from then on)
-int rom_batch_step(mb_rom* R) {
+// ---- the kernels of one reduced time step, by phase.  Host mode launches
+// the escalated-instance kernels over the counted lists; graph mode launches
+// them for the whole batch (the lists end at -1) and reads the Newton
+// iteration and pass numbers from device memory.
+// the step's start: a_old = a, its reconstruction and gates, every slot's pass on
+static void step_begin(mb_rom* R, cudaStream_t s) {
     mb_cell* c = R->cell;
-    cudaStream_t s = c->stream;
     const RomDev& d = R->d;
     RomWork& w = R->w;
     const int B = w.B;
     const unsigned nb = (unsigned)(((int64_t)B * d.Nr + 255) / 256);
     const unsigned bb = (unsigned)((B + 255) / 256);
-    const double n_thr = GATE_N_REL * c->P.nc;
     const dim3 gg((unsigned)((d.nloc + 255) / 256), (unsigned)B);
-    const unsigned ge = (unsigned)(((int64_t)d.M * B + 127) / 128);
     const unsigned gt = (unsigned)(((int64_t)(d.ngate ? d.ngate : 1) * B + 255) / 256);
-    int hcount = 0;
-    // escalated instances by GMRES on FP64 products (needs the interpolation points and room for the basis)
-    const bool refine = d.ir && d.M > 0 && gmres_smem(d.Nr, d.M, GMRES_M) <= (size_t)ROM_LU_SMEM;
     k_rom_copy<<<nb, 256, 0, s>>>(d.Nr, B, nullptr, w.a, w.a_old), count_launch(c);
     k_rom_gather<<<gg, 256, 0, s>>>(d, w.a_old, w.uloc_old, nullptr), count_launch(c);
-    if (d.ngate) k_rom_gate<<<gt, 256, 0, s>>>(d, B, w.uloc_old, w.uloc_old, n_thr, w.gate), count_launch(c);
+    if (d.ngate)
+        k_rom_gate<<<gt, 256, 0, s>>>(d, B, w.uloc_old, w.uloc_old, GATE_N_REL * c->P.nc, w.gate), count_launch(c);
     k_rom_set_active<<<bb, 256, 0, s>>>(B, nullptr, w.failed, w.pass_on, nullptr, w.hp), count_launch(c);
+}
+
+// a pass's start: its slots restart from a_old
+static void pass_begin(mb_rom* R, cudaStream_t s) {
+    mb_cell* c = R->cell;
+    const RomDev& d = R->d;
+    RomWork& w = R->w;
+    const int B = w.B;
+    const unsigned nb = (unsigned)(((int64_t)B * d.Nr + 255) / 256);
+    const unsigned bb = (unsigned)((B + 255) / 256);
+    k_rom_copy<<<nb, 256, 0, s>>>(d.Nr, B, w.pass_on, w.a_old, w.a), count_launch(c);
+    k_rom_set_active<<<bb, 256, 0, s>>>(B, w.pass_on, w.failed, w.active, w.pit, nullptr), count_launch(c);
+}
+
+static bool rom_refine(const RomDev& d) {
+    return d.ir && d.M > 0 && gmres_smem(d.Nr, d.M, GMRES_M) <= (size_t)ROM_LU_SMEM;
+}
+
+// escalated instances, part A: FP64 interpolated terms and derivatives, G U_loc in
+// FP64 (and, without refinement, their FP64 Newton matrices)
+static void iter_hp_a(mb_rom* R, cudaStream_t s, int nhp, bool graph) {
+    mb_cell* c = R->cell;
+    const RomDev& d = R->d;
+    RomWork& w = R->w;
+    const int n = graph ? w.B : nhp;
+    k_rom_ei<true><<<(unsigned)(((int64_t)d.M * n + 127) / 128), 128, 0, s>>>(
+        d, c->P, c->Pf, n, w.uloc, w.gate, w.prm, w.active, w.hp, w.hplist, w.f, w.G, w.G64), count_launch(c);
+    const unsigned gy = (unsigned)(graph ? std::min(n, 64) : n);
+    k_rom_gu64<<<dim3((unsigned)d.M, gy), 64, 0, s>>>(d, w.G64, w.active, w.hp, w.hplist, n, w.GU64), count_launch(c);
+    if (!rom_refine(d))
+        k_rom_jac64<<<dim3((unsigned)d.Nr, gy), 128, 0, s>>>(d, w.prm, w.GU64, w.active, w.hp, w.hplist, n, w.J64),
+            count_launch(c);
+}
+
+// escalated instances, part B: their Newton steps (GMRES on FP64 products, or the FP64 LU)
+static void iter_hp_b(mb_rom* R, cudaStream_t s, int nhp, bool graph) {
+    mb_cell* c = R->cell;
+    const RomDev& d = R->d;
+    RomWork& w = R->w;
+    const int n = graph ? w.B : nhp;
+    if (rom_refine(d))
+        k_rom_gmres<<<(unsigned)n, 256, gmres_smem(d.Nr, d.M, GMRES_M), s>>>(
+            d, w.prm, w.GU64, w.r, w.J, w.lpiv, w.lsc, w.active, w.hp, w.hplist, GMRES_M, GMRES_CYCLES, GMRES_ETA,
+            w.delta), count_launch(c);
+    else
+        launch_rom_lu<double>(d.Nr, n, w.J64, w.r, w.active, w.hp, 1, w.hplist, w.delta, s), count_launch(c);
+}
+
+// one reduced Newton iteration of the active slots.  Host mode: hp_any and the
+// list length n_alist come from the host's last count; graph mode: the
+// escalated parts are left to the caller (conditional nodes) and the GEMM
+// reads the iteration number and the list length from device memory.
+static void iter_main_a(mb_rom* R, cudaStream_t s) {
+    mb_cell* c = R->cell;
+    const RomDev& d = R->d;
+    RomWork& w = R->w;
+    const int B = w.B;
+    const dim3 gg((unsigned)((d.nloc + 255) / 256), (unsigned)B);
+    k_rom_gather<<<gg, 256, 0, s>>>(d, w.a, w.uloc, w.active), count_launch(c);
+    if (d.M)
+        k_rom_ei<false><<<(unsigned)(((int64_t)d.M * B + 127) / 128), 128, 0, s>>>(
+            d, c->P, c->Pf, B, w.uloc, w.gate, w.prm, w.active, w.hp, w.hplist, w.f, w.G, w.G64), count_launch(c);
+}
+static void iter_main_b(mb_rom* R, cudaStream_t s, bool listed, int ncols, const int* dit) {
+    mb_cell* c = R->cell;
+    const RomDev& d = R->d;
+    RomWork& w = R->w;
+    const int B = w.B;
+    if (d.M)
+        k_rom_gu<<<(unsigned)(((int64_t)d.M * B * 32 + 255) / 256), 256, 0, s>>>(d, B, w.G, w.active, w.hp, w.GU),
+            count_launch(c);
+    if (ncols > 0) {
+        const dim3 gj((unsigned)(((int64_t)ncols * d.Nr + JT_COLS - 1) / JT_COLS),
+                      (unsigned)((d.Nr + JT_ROWS - 1) / JT_ROWS));
+        const int* al = (listed || dit) ? w.alist : nullptr;
+        const int* dn = dit ? w.counts + 2 : nullptr;
+        if (d.tc)
+            k_rom_jac<true><<<gj, 256, 0, s>>>(d, B, ncols, al, w.prm, w.GU, w.hp, w.J, dit, dn);
+        else
+            k_rom_jac<false><<<gj, 256, 0, s>>>(d, B, ncols, al, w.prm, w.GU, w.hp, w.J, dit, dn);
+        count_launch(c);
+    }
+    k_rom_resid<<<(unsigned)B, 128, 0, s>>>(d, w.a, w.a_old, w.prm, w.f, w.active, w.r), count_launch(c);
+    const bool refine = rom_refine(d);
+    launch_rom_lu<float>(d.Nr, B, w.J, w.r, w.active, w.hp, 0, nullptr, w.delta, s, refine ? w.lpiv : nullptr,
+                         refine ? w.lsc : nullptr),
+        count_launch(c);
+}
+static void iter_main_c(mb_rom* R, cudaStream_t s) {
+    mb_cell* c = R->cell;
+    const RomDev& d = R->d;
+    RomWork& w = R->w;
+    const int B = w.B;
+    const unsigned nkt = (unsigned)((d.nloc + UN_K - 1) / UN_K);
+    k_rom_unorm<<<dim3(nkt, (unsigned)((B + UN_B - 1) / UN_B)), 256, 0, s>>>(d, B, w.delta, w.active, w.dpart),
+        count_launch(c);
+    k_rom_apply<<<(unsigned)B, 32, 0, s>>>(d, (int)nkt, w.a, w.delta, w.dpart, w.active, w.failed, w.its, w.pit, w.hp,
+                                           w.dnprev), count_launch(c);
+    k_rom_count_hp<<<1, 256, 0, s>>>(B, w.active, w.hp, w.counts, w.hplist, w.alist), count_launch(c);
+}
+
+// a pass's end: instances still iterating have failed; the gates are re-taken
+// and the slots whose gates flipped take another pass (pass_on)
+static void pass_end(mb_rom* R, cudaStream_t s, int last_pass, const int* dpass) {
+    mb_cell* c = R->cell;
+    const RomDev& d = R->d;
+    RomWork& w = R->w;
+    const int B = w.B;
+    const unsigned bb = (unsigned)((B + 255) / 256);
+    k_rom_fail_active<<<bb, 256, 0, s>>>(B, w.active, w.failed), count_launch(c);
+    if (!d.ngate) return;
+    const dim3 gg((unsigned)((d.nloc + 255) / 256), (unsigned)B);
+    const unsigned gt = (unsigned)(((int64_t)d.ngate * B + 255) / 256);
+    k_rom_gather<<<gg, 256, 0, s>>>(d, w.a, w.uloc, nullptr), count_launch(c);
+    k_rom_gate<<<gt, 256, 0, s>>>(d, B, w.uloc, w.uloc_old, GATE_N_REL * c->P.nc, w.gate2), count_launch(c);
+    k_rom_flips<<<(unsigned)B, 256, 0, s>>>(d.ngate, B, w.gate, w.gate2, w.failed, w.pass_on, w.flips, w.gate,
+                                           last_pass, dpass), count_launch(c);
+    k_rom_count<<<1, 256, 0, s>>>(B, w.pass_on, w.counts + 3), count_launch(c);
+}
+
+// one implicit Euler step of every occupied slot, driven from the host (a
+// count read back after every Newton iteration and pass)
+static int rom_batch_step_host(mb_rom* R) {
+    mb_cell* c = R->cell;
+    cudaStream_t s = c->stream;
+    const RomDev& d = R->d;
+    RomWork& w = R->w;
+    const int B = w.B;
+    step_begin(R, s);
     w.hp_any = 0;
     for (int pass = 1; pass <= ROM_PASSES; ++pass) {
-        k_rom_copy<<<nb, 256, 0, s>>>(d.Nr, B, w.pass_on, w.a_old, w.a), count_launch(c);
-        k_rom_set_active<<<bb, 256, 0, s>>>(B, w.pass_on, w.failed, w.active, w.pit, nullptr), count_launch(c);
+        pass_begin(R, s);
         for (int it = 0; it < ROM_MAXIT; ++it) {
             // escalated-instance kernels only while some instance uses them (hp only turns on
             // within a step, so the count of the previous iteration covers this one)
             const int nhp = w.hp_any;
-            const bool hp_any = nhp > 0;
-            k_rom_gather<<<gg, 256, 0, s>>>(d, w.a, w.uloc, w.active), count_launch(c);
-            if (d.M) {
-                k_rom_ei<false><<<ge, 128, 0, s>>>(d, c->P, c->Pf, B, w.uloc, w.gate, w.prm, w.active, w.hp,
-                                                   w.hplist, w.f, w.G, w.G64), count_launch(c);
-                if (hp_any) {
-                    k_rom_ei<true><<<(unsigned)(((int64_t)d.M * nhp + 127) / 128), 128, 0, s>>>(
-                        d, c->P, c->Pf, nhp, w.uloc, w.gate, w.prm, w.active, w.hp, w.hplist, w.f, w.G, w.G64),
-                        count_launch(c);
-                    k_rom_gu64<<<dim3((unsigned)d.M, (unsigned)nhp), 64, 0, s>>>(d, w.G64, w.active, w.hp, w.hplist,
-                                                                                  w.GU64), count_launch(c);
-                }
-                k_rom_gu<<<(unsigned)(((int64_t)d.M * B * 32 + 255) / 256), 256, 0, s>>>(d, B, w.G, w.active, w.hp,
-                                                                                           w.GU), count_launch(c);
-            }
-            {
-                // the first iteration of a pass: every instance; later: the listed active FP32 ones
-                const bool listed = it > 0 && w.n_alist >= 0;
-                const int ncols = listed ? w.n_alist : B;
-                if (ncols > 0)
-                {
-                    const dim3 gj((unsigned)(((int64_t)ncols * d.Nr + JT_COLS - 1) / JT_COLS),
-                                  (unsigned)((d.Nr + JT_ROWS - 1) / JT_ROWS));
-                    const int* al = listed ? w.alist : nullptr;
-                    if (d.tc)
-                        k_rom_jac<true><<<gj, 256, 0, s>>>(d, B, ncols, al, w.prm, w.GU, w.hp, w.J);
-                    else
-                        k_rom_jac<false><<<gj, 256, 0, s>>>(d, B, ncols, al, w.prm, w.GU, w.hp, w.J);
-                    count_launch(c);
-                }
-            }
-            if (hp_any && !refine)
-                k_rom_jac64<<<dim3((unsigned)d.Nr, (unsigned)nhp), 128, 0, s>>>(d, w.prm, w.GU64, w.active, w.hp,
-                                                                                 w.hplist, w.J64), count_launch(c);
-            k_rom_resid<<<(unsigned)B, 128, 0, s>>>(d, w.a, w.a_old, w.prm, w.f, w.active, w.r), count_launch(c);
-            launch_rom_lu<float>(d.Nr, B, w.J, w.r, w.active, w.hp, 0, nullptr, w.delta, s,
-                                 refine ? w.lpiv : nullptr, refine ? w.lsc : nullptr),
-                count_launch(c);
-            if (hp_any && refine)
-                k_rom_gmres<<<(unsigned)nhp, 256, gmres_smem(d.Nr, d.M, GMRES_M), s>>>(
-                    d, w.prm, w.GU64, w.r, w.J, w.lpiv, w.lsc, w.active, w.hp, w.hplist, GMRES_M, GMRES_CYCLES,
-                    GMRES_ETA, w.delta),
-                    count_launch(c);
-            else if (hp_any)
-                launch_rom_lu<double>(d.Nr, nhp, w.J64, w.r, w.active, w.hp, 1, w.hplist, w.delta, s),
-                    count_launch(c);
-            {
-                const unsigned nkt = (unsigned)((d.nloc + UN_K - 1) / UN_K);
-                k_rom_unorm<<<dim3(nkt, (unsigned)((B + UN_B - 1) / UN_B)), 256, 0, s>>>(d, B, w.delta, w.active,
-                                                                                         w.dpart), count_launch(c);
-                k_rom_apply<<<(unsigned)B, 32, 0, s>>>(d, (int)nkt, w.a, w.delta, w.dpart, w.active, w.failed,
-                                                       w.its, w.pit, w.hp, w.dnprev), count_launch(c);
-            }
+            iter_main_a(R, s);
+            if (nhp > 0) iter_hp_a(R, s, nhp, false);
+            // the first iteration of a pass: every instance; later: the listed active FP32 ones
+            const bool listed = it > 0 && w.n_alist >= 0;
+            iter_main_b(R, s, listed, listed ? w.n_alist : B, nullptr);
+            if (nhp > 0) iter_hp_b(R, s, nhp, false);
+            iter_main_c(R, s);
             int hc[3] = {0, 0, 0};
-            k_rom_count_hp<<<1, 256, 0, s>>>(B, w.active, w.hp, w.counts, w.hplist, w.alist), count_launch(c);
             MB_CUDA(cudaMemcpyAsync(hc, w.counts, 12, cudaMemcpyDeviceToHost, s));
             MB_CUDA(cudaStreamSynchronize(s));
             w.hp_any = hc[1];
             w.n_alist = hc[2];
             if (hc[0] == 0) break;
         }
-        // instances still iterating after the iteration limit have failed
-        k_rom_fail_active<<<bb, 256, 0, s>>>(B, w.active, w.failed), count_launch(c);
+        pass_end(R, s, pass == ROM_PASSES ? 1 : 0, nullptr);
         if (!d.ngate) break;
-        k_rom_gather<<<gg, 256, 0, s>>>(d, w.a, w.uloc, nullptr), count_launch(c);
-        k_rom_gate<<<gt, 256, 0, s>>>(d, B, w.uloc, w.uloc_old, n_thr, w.gate2), count_launch(c);
-        k_rom_flips<<<(unsigned)B, 256, 0, s>>>(d.ngate, B, w.gate, w.gate2, w.failed, w.pass_on, w.flips, w.gate,
-                                               pass == ROM_PASSES ? 1 : 0), count_launch(c);
-        k_rom_count<<<1, 256, 0, s>>>(B, w.pass_on, w.counts), count_launch(c);
-        MB_CUDA(cudaMemcpyAsync(&hcount, w.counts, 4, cudaMemcpyDeviceToHost, s));
+        int hcount = 0;
+        MB_CUDA(cudaMemcpyAsync(&hcount, w.counts + 3, 4, cudaMemcpyDeviceToHost, s));
         MB_CUDA(cudaStreamSynchronize(s));
         if (hcount == 0) break;
     }
     MB_CUDA_LAUNCH("rom_step");
     return MB_OK;
+}
+
+// ---- graph mode: control kernels and the capture
+__global__ void k_rom_ctl_step(int* ctl, int* counts) {
+    ctl[1] = 0;       // passes done
+    counts[1] = 0;    // no escalated instance at the start of a step
+}
+__global__ void k_rom_ctl_pass_begin(int* ctl, cudaGraphConditionalHandle h_it) {
+    ctl[0] = 0;
+    cudaGraphSetConditional(h_it, 1u);
+}
+__global__ void k_rom_ctl_iter_begin(const int* counts, cudaGraphConditionalHandle h_a, cudaGraphConditionalHandle h_b) {
+    const unsigned v = counts[1] > 0 ? 1u : 0u;   // escalated instances at the last count
+    cudaGraphSetConditional(h_a, v);
+    cudaGraphSetConditional(h_b, v);
+}
+__global__ void k_rom_ctl_iter_end(int* ctl, const int* counts, cudaGraphConditionalHandle h_it) {
+    const int it = ++ctl[0];
+    cudaGraphSetConditional(h_it, (counts[0] > 0 && it < ROM_MAXIT) ? 1u : 0u);
+}
+__global__ void k_rom_ctl_pass_end(int* ctl, const int* counts, int ngate, cudaGraphConditionalHandle h_pass) {
+    const int p = ++ctl[1];
+    cudaGraphSetConditional(h_pass, (ngate && counts[3] > 0 && p < ROM_PASSES) ? 1u : 0u);
+}
+
+// a conditional handle of the graph being captured on s
+static int cap_handle(cudaStream_t s, unsigned dflt, unsigned flags, cudaGraphConditionalHandle* h) {
+    cudaStreamCaptureStatus st;
+    cudaGraph_t g = nullptr;
+    MB_CUDA(cudaStreamGetCaptureInfo(s, &st, nullptr, &g, nullptr, nullptr, nullptr));
+    if (st != cudaStreamCaptureStatusActive) { set_error("reduced step graph: capture not active"); return MB_ECUDA; }
+    MB_CUDA(cudaGraphConditionalHandleCreate(h, g, dflt, flags));
+    return MB_OK;
+}
+// a conditional node on handle h at the current point of the capture on s;
+// *body is its body graph, to be filled by capturing another stream into it
+static int cap_node(cudaStream_t s, cudaGraphConditionalNodeType type, cudaGraphConditionalHandle h,
+                    cudaGraph_t* body) {
+    cudaStreamCaptureStatus st;
+    cudaGraph_t g = nullptr;
+    const cudaGraphNode_t* deps = nullptr;
+    const cudaGraphEdgeData* ed = nullptr;
+    size_t nd = 0;
+    MB_CUDA(cudaStreamGetCaptureInfo(s, &st, nullptr, &g, &deps, &ed, &nd));
+    if (st != cudaStreamCaptureStatusActive) { set_error("reduced step graph: capture not active"); return MB_ECUDA; }
+    cudaGraphNodeParams np = {};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = h;
+    np.conditional.type = type;
+    np.conditional.size = 1;
+    cudaGraphNode_t node;
+    MB_CUDA(cudaGraphAddNode(&node, g, deps, ed, nd, &np));
+    *body = np.conditional.phGraph_out[0];
+    MB_CUDA(cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+    return MB_OK;
+}
+static int cap_into(cudaStream_t s, cudaGraph_t body) {
+    MB_CUDA(cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    return MB_OK;
+}
+static int cap_end(cudaStream_t s) {
+    cudaGraph_t g = nullptr;
+    MB_CUDA(cudaStreamEndCapture(s, &g));
+    return MB_OK;
+}
+
+// The step as one graph (s0 the top level, s1..s3 fill the nested bodies):
+//   step start; while (passes) { pass start; while (Newton iterations) {
+//   gather and FP32-path terms; if (escalated) { part A }; GU, GEMM, residual,
+//   FP32 LU; if (escalated) { part B }; step length, update, counts }; pass end }
+// The loop and branch conditions are set by control kernels from the device
+// counts, in the order in which the host-driven step takes its decisions.
+static int rom_graph_capture(mb_rom* R, cudaStream_t s0, cudaStream_t s1, cudaStream_t s2, cudaStream_t s3) {
+    RomWork& w = R->w;
+    const RomDev& d = R->d;
+    int rc;
+    cudaGraphConditionalHandle h_pass, h_it, h_a, h_b;
+    cudaGraph_t bp, bi, ba, bb;
+    step_begin(R, s0);
+    k_rom_ctl_step<<<1, 1, 0, s0>>>(w.ctl, w.counts);
+    if ((rc = cap_handle(s0, 1u, cudaGraphCondAssignDefault, &h_pass))) return rc;
+    if ((rc = cap_node(s0, cudaGraphCondTypeWhile, h_pass, &bp))) return rc;
+    // pass body
+    if ((rc = cap_into(s1, bp))) return rc;
+    pass_begin(R, s1);
+    if ((rc = cap_handle(s1, 0u, 0u, &h_it))) return rc;
+    k_rom_ctl_pass_begin<<<1, 1, 0, s1>>>(w.ctl, h_it);
+    if ((rc = cap_node(s1, cudaGraphCondTypeWhile, h_it, &bi))) return rc;
+    // Newton iteration body
+    if ((rc = cap_into(s2, bi))) return rc;
+    if ((rc = cap_handle(s2, 0u, 0u, &h_a)) || (rc = cap_handle(s2, 0u, 0u, &h_b))) return rc;
+    k_rom_ctl_iter_begin<<<1, 1, 0, s2>>>(w.counts, h_a, h_b);
+    iter_main_a(R, s2);
+    if ((rc = cap_node(s2, cudaGraphCondTypeIf, h_a, &ba))) return rc;
+    if ((rc = cap_into(s3, ba))) return rc;
+    iter_hp_a(R, s3, 0, true);
+    if ((rc = cap_end(s3))) return rc;
+    iter_main_b(R, s2, false, w.B, w.ctl);
+    if ((rc = cap_node(s2, cudaGraphCondTypeIf, h_b, &bb))) return rc;
+    if ((rc = cap_into(s3, bb))) return rc;
+    iter_hp_b(R, s3, 0, true);
+    if ((rc = cap_end(s3))) return rc;
+    iter_main_c(R, s2);
+    k_rom_ctl_iter_end<<<1, 1, 0, s2>>>(w.ctl, w.counts, h_it);
+    if ((rc = cap_end(s2))) return rc;
+    // rest of the pass body
+    pass_end(R, s1, 0, w.ctl + 1);
+    k_rom_ctl_pass_end<<<1, 1, 0, s1>>>(w.ctl, w.counts, d.ngate, h_pass);
+    if ((rc = cap_end(s1))) return rc;
+    (void)bi;
+    return MB_OK;
+}
+
+static int rom_graph_build(mb_rom* R) {
+    mb_cell* c = R->cell;
+    cudaStream_t s0 = c->stream, aux[3] = {nullptr, nullptr, nullptr};
+    for (auto& a : aux) MB_CUDA(cudaStreamCreateWithFlags(&a, cudaStreamNonBlocking));
+    const int64_t saved = c->launches;
+    int rc = MB_OK;
+    if (cudaStreamBeginCapture(s0, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        rc = cuda_fail(cudaGetLastError(), "reduced step graph: begin capture");
+    } else {
+        rc = rom_graph_capture(R, s0, aux[0], aux[1], aux[2]);
+        // end every capture still open (after a failure), innermost first
+        for (int k = 2; k >= 0; --k) {
+            cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+            cudaStreamIsCapturing(aux[k], &st);
+            if (st != cudaStreamCaptureStatusNone) {
+                cudaGraph_t g = nullptr;
+                cudaStreamEndCapture(aux[k], &g);
+            }
+        }
+        cudaGraph_t g = nullptr;
+        const cudaError_t e = cudaStreamEndCapture(s0, &g);
+        if (!rc && (e != cudaSuccess || !g)) rc = cuda_fail(e, "reduced step graph: end capture");
+        if (!rc && cudaGraphInstantiate(&R->w.gexec, g, 0) != cudaSuccess)
+            rc = cuda_fail(cudaGetLastError(), "reduced step graph: instantiate");
+        if (g) cudaGraphDestroy(g);
+    }
+    c->launches = saved;
+    for (auto& a : aux) cudaStreamDestroy(a);
+    if (rc) {
+        R->w.gexec = nullptr;
+        cudaGetLastError();
+    }
+    return rc;
+}
+
+// one implicit Euler step of every occupied slot (reduced Newton with the
+// plating active-set passes); a slot whose Newton iteration fails is marked
+// failed (and skipped from then on).  By default the whole step is one CUDA
+// graph launch (built at the batch's first step); without it (or if it cannot
+// be built) the host drives the loops.
+int rom_batch_step(mb_rom* R) {
+    RomWork& w = R->w;
+    if (R->d.graph && !w.graph_failed) {
+        if (!w.gexec && rom_graph_build(R)) w.graph_failed = true;
+        if (w.gexec) {
+            MB_CUDA(cudaGraphLaunch(w.gexec, R->cell->stream));
+            count_launch(R->cell);
+            return MB_OK;
+        }
+    }
+    return rom_batch_step_host(R);
 }
 
 }  // namespace mb
@@ -1614,6 +1891,26 @@ extern "C" int mb_rom_dims(mb_rom* R, int* n_r, int* n_bv, int* n_1c) {
     if (n_r) *n_r = R->d.Nr;
     if (n_bv) *n_bv = R->d.Mbv;
     if (n_1c) *n_1c = R->d.M1c;
+    return MB_OK;
+}
+
+extern "C" int mb_rom_block_dims(mb_rom* R, int* n_c, int* n_n, int* n_phi) {
+    if (!R) { set_error("mb_rom_block_dims: invalid argument"); return MB_EINVAL; }
+    const int64_t N = R->cell->D.N, n = R->cell->n;
+    const int Nr = R->d.Nr;
+    int cnt[3] = {0, 0, 0};
+    for (int k = 0; k < Nr; ++k) {
+        int f = -1;
+        for (int64_t i = 0; i < n; ++i)
+            if (R->hU[(size_t)i * Nr + k] != 0.0) {
+                const int fi = est_field(i, N);
+                f = (f < 0 || f == fi) ? fi : 3;
+            }
+        if (f >= 0 && f < 3) ++cnt[f];
+    }
+    if (n_c) *n_c = cnt[0];
+    if (n_phi) *n_phi = cnt[1];
+    if (n_n) *n_n = cnt[2];
     return MB_OK;
 }
 
@@ -1705,15 +2002,17 @@ __global__ void __launch_bounds__(EST_THREADS)
 k_rom_estimate(int Nr, int Nv, const double* __restrict__ a, const double* __restrict__ av,
                const double* __restrict__ T, const int* __restrict__ fld, const double* __restrict__ G, int g0, int g1,
                int g2, const int* __restrict__ failed, const int* __restrict__ failed_v, double scale,
-               double* __restrict__ est) {
+               double* __restrict__ est, double* __restrict__ nrm) {
     __shared__ double sa[ROM_NR_MAX];
     __shared__ double part[EST_THREADS / 32][3];
+    __shared__ double npart[EST_THREADS / 32][3];
     const int b = blockIdx.x;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (int i = threadIdx.x; i < Nr; i += blockDim.x) sa[i] = a[(int64_t)b * Nr + i];
     __syncthreads();
-    double acc[3] = {0.0, 0.0, 0.0};
-    // || T a - av ||^2 per field: one warp per validation mode
+    double acc[3] = {0.0, 0.0, 0.0}, nacc[3] = {0.0, 0.0, 0.0};
+    // || T a - av ||^2 per field: one warp per validation mode; and ||av||^2 per
+    // field (= ||Uv_f av||_W^2, Uv W-orthonormal on each field)
     for (int j = wid; j < Nv; j += nw) {
         const int f = fld[j];
         if (f < 0) continue;
@@ -1721,8 +2020,10 @@ k_rom_estimate(int Nr, int Nv, const double* __restrict__ a, const double* __res
         for (int i = lane; i < Nr; i += 32) t = fma(T[(int64_t)j * Nr + i], sa[i], t);
         for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
         if (lane == 0) {
-            const double d = t - av[(int64_t)b * Nv + j];
+            const double x = av[(int64_t)b * Nv + j];
+            const double d = t - x;
             acc[f] = fma(d, d, acc[f]);
+            nacc[f] = fma(x, x, nacc[f]);
         }
     }
     // a^T G_f a: one warp per row of G_f
@@ -1738,18 +2039,23 @@ k_rom_estimate(int Nr, int Nv, const double* __restrict__ a, const double* __res
         }
     }
     if (lane == 0)
-        for (int f = 0; f < 3; ++f) part[wid][f] = acc[f];
+        for (int f = 0; f < 3; ++f) {
+            part[wid][f] = acc[f];
+            npart[wid][f] = nacc[f];
+        }
     __syncthreads();
     if (threadIdx.x < 3) {
-        double sum = 0.0;
-        for (int w = 0; w < nw; ++w) sum += part[w][threadIdx.x];
+        double sum = 0.0, nsum = 0.0;
+        for (int w = 0; w < nw; ++w) {
+            sum += part[w][threadIdx.x];
+            nsum += npart[w][threadIdx.x];
+        }
         const bool bad = failed[b] || failed_v[b];
         est[(int64_t)b * 3 + threadIdx.x] = bad ? NAN : scale * sqrt(fmax(sum, 0.0));
+        nrm[(int64_t)b * 3 + threadIdx.x] = bad ? NAN : sqrt(nsum);
     }
 }
 
-// field of unknown i: 0 concentration, 1 potential, 2 plated-Li face
-static inline int est_field(int64_t i, int64_t N) { return i < N ? 0 : (i < 2 * N ? 1 : 2); }
 
 // T, G_f and the fields of the validation modes for the pair (R, Rv)
 static int rom_est_setup(mb_rom* R, mb_rom* Rv) {
@@ -1858,7 +2164,7 @@ static int rom_est_setup(mb_rom* R, mb_rom* Rv) {
 
 extern "C" int mb_rom_estimate_batch(mb_rom* R, mb_rom* Rv, double theta, int B, const mb_rom_params* prm,
                                      int n_steps, double dt, double* V_out, double* Vv_out, double* est_out,
-                                     mb_rom_info* info) {
+                                     double* norm_out, mb_rom_info* info) {
     if (!R || !Rv || R == Rv || !(theta >= 0.0 && theta < 1.0) || B < 1 || !prm || n_steps < 0 || !(dt > 0) ||
         !est_out) {
         set_error("mb_rom_estimate_batch: invalid argument");
@@ -1873,13 +2179,14 @@ extern "C" int mb_rom_estimate_batch(mb_rom* R, mb_rom* Rv, double theta, int B,
     RomEst& E = R->est;
     if (E.Bcap < B) {
         E.est = rom_alloc<double>(E.bufs, (size_t)3 * B);
-        if (!E.est) { set_error("mb_rom_estimate_batch: device memory"); return MB_ENOMEM; }
+        E.nrm = rom_alloc<double>(E.bufs, (size_t)3 * B);
+        if (!E.est || !E.nrm) { set_error("mb_rom_estimate_batch: device memory"); return MB_ENOMEM; }
         E.Bcap = B;
     }
     if ((rc = rom_batch_begin(R, B, prm, dt)) || (rc = rom_batch_begin(Rv, B, prm, dt))) return rc;
     const int ncol = n_steps + 1;
     const double scale = 1.0 / (1.0 - theta);
-    std::vector<double> hV(B), hS(B), hVv(B), hSv(B), he((size_t)3 * B);
+    std::vector<double> hV(B), hS(B), hVv(B), hSv(B), he((size_t)3 * B), hn((size_t)3 * B);
     std::vector<int> hf(B), hfv(B);
     cudaStream_t s = R->cell->stream;
     for (int step = 0; step <= n_steps; ++step) {
@@ -1890,12 +2197,16 @@ extern "C" int mb_rom_estimate_batch(mb_rom* R, mb_rom* Rv, double theta, int B,
             return rc;
         k_rom_estimate<<<(unsigned)B, EST_THREADS, 0, s>>>(R->d.Nr, E.Nv, R->w.a, Rv->w.a, E.T, E.fld, E.G, E.gon[0],
                                                           E.gon[1], E.gon[2], R->w.failed, Rv->w.failed, scale,
-                                                          E.est), count_launch(R->cell);
+                                                          E.est, E.nrm), count_launch(R->cell);
         MB_CUDA_LAUNCH("rom_estimate");
         MB_CUDA(cudaMemcpyAsync(he.data(), E.est, 8 * he.size(), cudaMemcpyDeviceToHost, s));
+        MB_CUDA(cudaMemcpyAsync(hn.data(), E.nrm, 8 * hn.size(), cudaMemcpyDeviceToHost, s));
         MB_CUDA(cudaStreamSynchronize(s));
         for (int b = 0; b < B; ++b) {
-            for (int f = 0; f < 3; ++f) est_out[((size_t)b * ncol + step) * 3 + f] = he[(size_t)b * 3 + f];
+            for (int f = 0; f < 3; ++f) {
+                est_out[((size_t)b * ncol + step) * 3 + f] = he[(size_t)b * 3 + f];
+                if (norm_out) norm_out[((size_t)b * ncol + step) * 3 + f] = hn[(size_t)b * 3 + f];
+            }
             if (V_out) V_out[(size_t)b * ncol + step] = hf[b] ? NAN : hV[b];
             if (Vv_out) Vv_out[(size_t)b * ncol + step] = hfv[b] ? NAN : hVv[b];
         }
@@ -1956,9 +2267,9 @@ extern "C" int mb_debug_rom_jac(int Nr, int M, int B, const float* P, const floa
     } else {
         const dim3 gj((unsigned)(((int64_t)B * Nr + JT_COLS - 1) / JT_COLS), (unsigned)((Nr + JT_ROWS - 1) / JT_ROWS));
         if (tc)
-            k_rom_jac<true><<<gj, 256>>>(d, B, B, nullptr, dprm, gu, dhp, dJ);
+            k_rom_jac<true><<<gj, 256>>>(d, B, B, nullptr, dprm, gu, dhp, dJ, nullptr, nullptr);
         else
-            k_rom_jac<false><<<gj, 256>>>(d, B, B, nullptr, dprm, gu, dhp, dJ);
+            k_rom_jac<false><<<gj, 256>>>(d, B, B, nullptr, dprm, gu, dhp, dJ, nullptr, nullptr);
         cudaError_t e = cudaGetLastError();
         if (e == cudaSuccess) e = cudaMemcpy(J, dJ, 4 * (size_t)B * Nr * Nr, cudaMemcpyDeviceToHost);
         if (e != cudaSuccess) rc = cuda_fail(e, "debug_rom_jac");
@@ -2020,6 +2331,12 @@ extern "C" int mb_debug_rom_lu(int Nr, int B, int fp64, int in_place, const doub
 extern "C" int mb_debug_rom_refine(mb_rom* R, int on) {
     if (!R) return MB_EINVAL;
     R->d.ir = on ? 1 : 0;
+    return MB_OK;
+}
+
+extern "C" int mb_debug_rom_graph(mb_rom* R, int on) {
+    if (!R) return MB_EINVAL;
+    R->d.graph = on ? 1 : 0;
     return MB_OK;
 }
 

@@ -235,3 +235,28 @@ def test_rom_refine_matches_oracle(params, wide_case):
     assert np.max(np.abs(out["V"] - lu["V"])) <= 1e-9 * np.max(np.abs(lu["V"]))
     g.close()
     gc.close()
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("which", ["case", "wide_case"])
+def test_rom_step_graph_bit_identical(params, request, which):
+    """A reduced time step as one CUDA graph (conditional nodes run the
+    active-set passes, the Newton iterations and the escalated-instance branch
+    on the device) gives bit-identical trajectories, coefficients and counts to
+    the host-driven step.  The 112-mode model escalates instances, so the
+    escalated branch runs inside the graph."""
+    B = _gpu()
+    lab, oc, rom = request.getfixturevalue(which)
+    gc, g = _gpu_rom(B, lab, params, rom)
+    prm = [(c * oc.i_1c, s, k) for (c, s, k) in [(-3.0, 1.1, 0.7), (-1.5, 0.8, 2.0), (-4.5, 0.6, 4.0),
+                                                  (0.0, 1.0, 1.0), (2.0, 1.3, 0.3)]]
+    g.debug_graph(False)
+    host = g.solve(prm, 3, 1.0)
+    g.debug_graph(True)
+    graph = g.solve(prm, 3, 1.0)
+    assert host["ok"] and graph["ok"]
+    assert np.array_equal(host["V"], graph["V"]) and np.array_equal(host["s_ac"], graph["s_ac"])
+    assert np.array_equal(host["a"], graph["a"])
+    assert host["newton_its"] == graph["newton_its"] and host["flips"] == graph["flips"]
+    g.close()
+    gc.close()

@@ -88,6 +88,13 @@ def test_error_estimate_matches_oracle(params, models, which):
         for f, key in enumerate(("c", "phi", "n")):
             scale = np.sqrt(np.sum(w[fields[f]] * recon[:, fields[f]] ** 2, axis=1))
             assert np.all(np.abs(out["est"][b, :, f] - ref[key]) <= 1e-8 * scale + 1e-300), (b, key)
+    # the validation model's field norms, and the block dimensions
+    for b, p in enumerate(prm):
+        recon = a_val["a"][b] @ val.U.T
+        for f in range(3):
+            nref = np.sqrt(np.sum(w[fields[f]] * recon[fields[f]] ** 2))
+            assert abs(out["norm_val"][b, -1, f] - nref) <= 1e-12 * nref + 1e-300
+    assert g_val.block_dims() == (val.nc, val.nn, val.rp)
     # the estimate scales as 1 / (1 - theta)
     out0 = g_red.estimate(g_val, prm, steps, 1.0, 0.0)
     assert np.allclose(out0["est"] / (1 - theta), out["est"], rtol=1e-14, atol=0)
