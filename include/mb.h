@@ -158,6 +158,35 @@ int mb_state_set(mb_cell* cell, const double* u);
  * Returns MB_ENOCONV when every halving failed (state unchanged). */
 int mb_step(mb_cell* cell, double dt, double I_app, mb_step_info* info);
 
+/* Adaptive time step (Sec. workflow:discretization: the step size is
+ * adapted; the controller is this library's).  One accepted implicit Euler
+ * step of size at most dt_try: its local error is estimated from the two
+ * previous states (the state before the last accepted adaptive step, the
+ * current one) as e = dt/(2 dt + dt_prev) |u_new - u_pred|_s, u_pred their
+ * linear extrapolation to t + dt and |.|_s the max-norm scaled by the
+ * unknown scales (c_ref, 1 V, n_c); a step with e > tol is rejected and
+ * retried with dt * clamp(0.9 sqrt(tol/e), 0.2, 2) (down to dt_min, at most
+ * max_rejects times); the accepted step proposes dt_next by the same factor
+ * within [dt_min, dt_max].  Without a history (after mb_cell_create,
+ * mb_state_set, mb_step or mb_adapt_reset) the step of size dt_try is
+ * accepted without an estimate.  The first call allocates two state-size
+ * buffers.  info as mb_step (summed over the tried steps); MB_ENOCONV as
+ * mb_step (state unchanged). */
+typedef struct {
+    double tol;            /* local error bound in the scaled max-norm */
+    double dt_min, dt_max; /* step size bounds (s) */
+    int    max_rejects;    /* rejected tries per accepted step */
+} mb_adapt_opts;
+typedef struct {
+    double dt_used;        /* size of the accepted step (s) */
+    double dt_next;        /* proposed size of the next step (s) */
+    double err;            /* its local error estimate (0 without history) */
+    int    rejects;        /* rejected tries before it */
+} mb_adapt_info;
+int mb_step_adaptive(mb_cell* cell, double dt_try, double I_app, const mb_adapt_opts* o, mb_adapt_info* ai,
+                     mb_step_info* info);
+int mb_adapt_reset(mb_cell* cell);
+
 /* FP64 residual R(u; u_old, dt, I_app) of Eq. (ap4:detailed) with plating
  * gates gate (uint8[F], 1 = active; NULL = gates taken at u_old as mb_step
  * does).  u, u_old, r: double[n]. */

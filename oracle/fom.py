@@ -468,6 +468,45 @@ class Cell:
         info.update(self.functionals(u))
         return u, info
 
+    # ----------------------------------------------------------- adaptive dt
+    def local_error(self, u_new, u_start, u_hist, dt, dt_hist):
+        """Local error estimate of the implicit Euler step from u_start (time
+        t) to u_new (t + dt), with u_hist the state at t - dt_hist, in the
+        max-norm scaled by the unknown scales.  For a smooth solution the
+        implicit Euler step errs by (dt^2/2) u'' and the linear extrapolation
+        u_pred = u_start + (dt/dt_hist)(u_start - u_hist) by -dt(dt +
+        dt_hist)/2 u'', so u_new - u_pred = dt(2 dt + dt_hist)/2 u'' and the
+        step's local error is dt/(2 dt + dt_hist) (u_new - u_pred) to leading
+        order."""
+        u_pred = u_start + (dt / dt_hist) * (u_start - u_hist)
+        return float(np.max(np.abs(u_new - u_pred) / self.unknown_scale())) * dt / (2.0 * dt + dt_hist)
+
+    def step_adaptive(self, u_start, u_hist, dt_hist, dt_try, I_app, tol, dt_min=1e-3, dt_max=60.0,
+                      s_i0=1.0, k_pl=1.0, max_rejects=10):
+        """One accepted step of adaptive size (Sec. workflow:discretization
+        adapts the time step; the controller is the build's).  Without a
+        history (u_hist None) the step of size dt_try is accepted as is.
+        Otherwise a step with local error estimate e > tol is rejected and
+        retried with dt * clamp(0.9 sqrt(tol / e), 0.2, 2) (first order
+        method: exponent 1/2), down to dt_min, at most max_rejects times; the
+        accepted step proposes the next size by the same factor, within
+        [dt_min, dt_max].  Returns (u_new, info) with dt_used, dt_next, err,
+        rejects."""
+        dt = min(max(dt_try, dt_min), dt_max)
+        rejects = 0
+        while True:
+            u, info = self.step(u_start, dt, I_app, s_i0, k_pl)
+            if u_hist is None:
+                info.update(dt_used=dt, dt_next=dt, err=0.0, rejects=0)
+                return u, info
+            e = self.local_error(u, u_start, u_hist, dt, dt_hist)
+            fac = 2.0 if e == 0.0 else min(2.0, max(0.2, 0.9 * np.sqrt(tol / e)))
+            if e <= tol or dt <= dt_min or rejects >= max_rejects:
+                info.update(dt_used=dt, dt_next=min(max(dt * fac, dt_min), dt_max), err=e, rejects=rejects)
+                return u, info
+            rejects += 1
+            dt = max(dt * fac, dt_min)
+
     # ------------------------------------------------------------ functionals
     def functionals(self, u):
         """Linear outputs (Sec. 2.5, s_cp and s_ac) and Li inventories."""

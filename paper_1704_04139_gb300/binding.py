@@ -54,6 +54,14 @@ class StepInfo(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class AdaptOpts(C.Structure):
+    _fields_ = [("tol", C.c_double), ("dt_min", C.c_double), ("dt_max", C.c_double), ("max_rejects", C.c_int)]
+
+
+class AdaptInfo(C.Structure):
+    _fields_ = [("dt_used", C.c_double), ("dt_next", C.c_double), ("err", C.c_double), ("rejects", C.c_int)]
+
+
 class CellInfo(C.Structure):
     _fields_ = [("n_vox", C.c_int64), ("n_faces", C.c_int64), ("n_unknowns", C.c_int64),
                 ("nt", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("h", C.c_double),
@@ -121,6 +129,9 @@ def _declare(lib):
     fn("mb_plating_faces", C.c_int, [VP, VP, VP, VP])
     fn("mb_state_get", C.c_int, [VP, VP])
     fn("mb_state_set", C.c_int, [VP, VP])
+    fn("mb_step_adaptive", C.c_int, [VP, C.c_double, C.c_double, C.POINTER(AdaptOpts), C.POINTER(AdaptInfo),
+                                     C.POINTER(StepInfo)])
+    fn("mb_adapt_reset", C.c_int, [VP])
     fn("mb_step", C.c_int, [VP, C.c_double, C.c_double, C.POINTER(StepInfo)])
     fn("mb_residual", C.c_int, [VP, VP, VP, VP, C.c_double, C.c_double, VP])
     fn("mb_residual_dev", C.c_int, [VP, VP, VP, VP, C.c_double, C.c_double, VP, VP])
@@ -274,6 +285,20 @@ class Cell:
         info = StepInfo()
         _check(lib().mb_step(self.h, float(dt), float(I_app), C.byref(info)))
         return info.as_dict()
+
+    def step_adaptive(self, dt_try, I_app, tol, dt_min=1e-3, dt_max=60.0, max_rejects=10):
+        """One accepted adaptive step (mb_step_adaptive): the step info dict
+        plus dt_used, dt_next, err and rejects."""
+        o = AdaptOpts(float(tol), float(dt_min), float(dt_max), int(max_rejects))
+        ai = AdaptInfo()
+        info = StepInfo()
+        _check(lib().mb_step_adaptive(self.h, float(dt_try), float(I_app), C.byref(o), C.byref(ai), C.byref(info)))
+        out = info.as_dict()
+        out.update(dt_used=ai.dt_used, dt_next=ai.dt_next, err=ai.err, rejects=ai.rejects)
+        return out
+
+    def adapt_reset(self):
+        _check(lib().mb_adapt_reset(self.h))
 
     def residual(self, u, u_old, dt, I_app, gate=None):
         u = np.ascontiguousarray(u, np.float64); uo = np.ascontiguousarray(u_old, np.float64)

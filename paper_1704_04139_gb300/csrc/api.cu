@@ -262,13 +262,33 @@ int mb_state_set(mb_cell* c, const double* u) {
     if (!c || !u) { set_error("mb_state_set: invalid argument"); return MB_EINVAL; }
     MB_CUDA(cudaMemcpyAsync(c->u, u, 8 * c->n, cudaMemcpyHostToDevice, c->stream));
     MB_CUDA(cudaStreamSynchronize(c->stream));
+    c->has_hist = false;
     return MB_OK;
 }
 
 int mb_step(mb_cell* c, double dt, double I_app, mb_step_info* info) {
     if (!c || !(dt > 0) || !(fabs(I_app) < 1e300)) { set_error("mb_step: invalid argument"); return MB_EINVAL; }
     mb_step_info tmp;
+    c->has_hist = false;   // a fixed step ends the adaptive history
     return newton_step(c, dt, I_app, info ? info : &tmp);
+}
+
+int mb_step_adaptive(mb_cell* c, double dt_try, double I_app, const mb_adapt_opts* o, mb_adapt_info* ai,
+                     mb_step_info* info) {
+    if (!c || !o || !(dt_try > 0) || !(fabs(I_app) < 1e300) || !(o->tol > 0) || !(o->dt_min > 0) ||
+        !(o->dt_max >= o->dt_min) || o->max_rejects < 0) {
+        set_error("mb_step_adaptive: invalid argument");
+        return MB_EINVAL;
+    }
+    mb_step_info tmp;
+    mb_adapt_info atmp;
+    return adaptive_step(c, dt_try, I_app, o, ai ? ai : &atmp, info ? info : &tmp);
+}
+
+int mb_adapt_reset(mb_cell* c) {
+    if (!c) { set_error("mb_adapt_reset: invalid argument"); return MB_EINVAL; }
+    c->has_hist = false;
+    return MB_OK;
 }
 
 int mb_residual_dev(mb_cell* c, const double* u, const double* u_old, const uint8_t* gate, double dt,

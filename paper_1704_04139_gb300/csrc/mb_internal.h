@@ -120,6 +120,13 @@ struct mb_cell {
     mb::Precond* pc = nullptr;
     mb::Krylov* kd = nullptr;
 
+    // adaptive time stepping (mb_step_adaptive): the state before the last
+    // accepted adaptive step and that step's size; allocated at the first call
+    double* u_hist = nullptr;      // n
+    double* u_save = nullptr;      // n (start of the step being tried)
+    bool has_hist = false;
+    double dt_hist = 0.0;
+
     mb::Prof prof;
     int64_t launches = 0;          // kernel launches issued by the library for this cell
 
@@ -242,6 +249,8 @@ int rom_slot_stats(mb_rom* R, int b, long long* its, long long* flips, double* a
 
 // ---- solver.cu ----
 int newton_step(mb_cell* c, double dt, double I_app, mb_step_info* info);
+int adaptive_step(mb_cell* c, double dt_try, double I_app, const mb_adapt_opts* o, mb_adapt_info* ai,
+                  mb_step_info* info);
 void krylov_destroy(mb_cell* c);   // frees the host structs; buffers stay owned by the cell
 
 }  // namespace mb

@@ -513,4 +513,71 @@ int newton_step(mb_cell* c, double dt, double I_app, mb_step_info* info) {
     return MB_ENOCONV;
 }
 
+// d = u_new - (u_start + r (u_start - u_hist)): the step's distance from the
+// linear extrapolation of the two previous states (r = dt / dt_hist)
+__global__ void k_lte_diff(const double* __restrict__ u_new, const double* __restrict__ u_start,
+                           const double* __restrict__ u_hist, double r, double* __restrict__ d, int64_t n) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) d[i] = u_new[i] - (u_start[i] + r * (u_start[i] - u_hist[i]));
+}
+
+// One accepted adaptive step (see mb_step_adaptive): local error e =
+// dt/(2 dt + dt_hist) |u_new - u_pred|_s, retries with dt * clamp(0.9
+// sqrt(tol/e), 0.2, 2) while e > tol.
+int adaptive_step(mb_cell* c, double dt_try, double I_app, const mb_adapt_opts* o, mb_adapt_info* ai,
+                  mb_step_info* info) {
+    const int64_t n = c->n;
+    cudaStream_t s = c->stream;
+    if (!c->u_hist) {
+        c->u_hist = (double*)cell_alloc(c, 8 * (size_t)n);
+        c->u_save = (double*)cell_alloc(c, 8 * (size_t)n);
+        if (!c->u_hist || !c->u_save) { set_error("mb_step_adaptive: device memory"); return MB_ENOMEM; }
+    }
+    memset(ai, 0, sizeof(*ai));
+    mb_step_info sum;
+    memset(&sum, 0, sizeof(sum));
+    double dt = fmin(fmax(dt_try, o->dt_min), o->dt_max);
+    MB_CUDA(cudaMemcpyAsync(c->u_save, c->u, 8 * n, cudaMemcpyDeviceToDevice, s));
+    for (int rejects = 0;; ++rejects) {
+        mb_step_info one;
+        int rc = newton_step(c, dt, I_app, &one);
+        sum.newton_its += one.newton_its;
+        sum.krylov_its += one.krylov_its;
+        sum.flips += one.flips;
+        if (rc) {
+            *info = sum;
+            return rc;
+        }
+        double e = 0.0, fac = 1.0;
+        const bool hist = c->has_hist;
+        if (hist) {
+            k_lte_diff<<<nblk(n), 256, 0, s>>>(c->u, c->u_save, c->u_hist, dt / c->dt_hist, c->du, n),
+                ::mb::count_launch(c);
+            MB_CUDA_LAUNCH("lte_diff");
+            if ((rc = scaled_maxnorm(c, c->du, 0, dt, &e))) return rc;
+            e *= dt / (2.0 * dt + c->dt_hist);
+            fac = e == 0.0 ? 2.0 : fmin(2.0, fmax(0.2, 0.9 * sqrt(o->tol / e)));
+        }
+        if (!hist || e <= o->tol || dt <= o->dt_min || rejects >= o->max_rejects) {
+            // accept: the start of this step becomes the history
+            std::swap(c->u_hist, c->u_save);
+            c->dt_hist = dt;
+            c->has_hist = true;
+            ai->dt_used = dt;
+            ai->dt_next = hist ? fmin(fmax(dt * fac, o->dt_min), o->dt_max) : dt;
+            ai->err = e;
+            ai->rejects = rejects;
+            const int nits = sum.newton_its, kits = sum.krylov_its, flips = sum.flips;
+            *info = one;
+            info->newton_its = nits;
+            info->krylov_its = kits;
+            info->flips = flips;
+            return MB_OK;
+        }
+        // reject: back to the start, smaller step
+        MB_CUDA(cudaMemcpyAsync(c->u, c->u_save, 8 * n, cudaMemcpyDeviceToDevice, s));
+        dt = fmax(dt * fac, o->dt_min);
+    }
+}
+
 }  // namespace mb

@@ -231,3 +231,79 @@ def test_pod_pin_detects_planted_mistakes():
     for pod in (trailing, full_weight):
         with pytest.raises(AssertionError):
             _pod_check(pod)
+
+
+# ------------------------------------------------------------- adaptive time step
+def _mode_cell(params, n=10, h=1e-7):
+    # the graphite slab of T1: zero-flux ends, cosine eigenmode of the discrete
+    # diffusion operator with rate lam = (4 D / h^2) sin^2(pi / (2 n))
+    cell = Cell(syn.slab_1d([CN] + [syn.G] * n + [CN]), h, params)
+    D = params["G"]["D"]
+    lam = 4.0 * D / h ** 2 * math.sin(math.pi / (2 * n)) ** 2
+    mode = np.cos(math.pi * (np.arange(n) + 0.5) / n)
+    return cell, lam, mode
+
+
+def _mode_state(cell, params, mode, amp):
+    n = len(mode)
+    u = cell.initial_state()
+    cmax = params["G"]["cmax"]
+    u[1:1 + n] = 0.5 * cmax + amp * cmax * mode
+    return u
+
+
+@pytest.mark.parametrize("dt,dt_hist", [(0.05, 0.05), (0.05, 0.1), (0.1, 0.03)])
+def test_local_error_estimate_is_the_implicit_euler_error(params, dt, dt_hist):
+    """On a diffusion eigenmode the solution of the semi-discrete system is
+    known in time (amplitude a e^{-lam t}) and the implicit Euler step has the
+    amplitude a / (1 + lam dt): the local error estimate from the two previous
+    exact states approaches the step's true error |a/(1+lam dt) - a e^{-lam
+    dt}| (in the unknown scale c_max) as lam dt -> 0."""
+    cell, lam, mode = _mode_cell(params)
+    a = 0.1
+    u_hist = _mode_state(cell, params, mode, a * math.exp(lam * dt_hist))
+    u_start = _mode_state(cell, params, mode, a)
+    u_new, _ = cell.step(u_start, dt, 0.0)
+    true = abs(a / (1 + lam * dt) - a * math.exp(-lam * dt)) * np.max(np.abs(mode))
+    est = cell.local_error(u_new, u_start, u_hist, dt, dt_hist)
+    assert abs(est / true - 1.0) < 5 * lam * (dt + dt_hist), (est, true)
+
+
+def test_local_error_pin_detects_planted_mistakes(params, monkeypatch):
+    """The pin fails when the estimate's factor is dt / (dt + dt_hist) (a
+    plausible slip: off by 3/2 for equal steps) or when the extrapolation
+    uses the wrong sign."""
+    def wrong_factor(self, u_new, u_start, u_hist, dt, dt_hist):
+        u_pred = u_start + (dt / dt_hist) * (u_start - u_hist)
+        return float(np.max(np.abs(u_new - u_pred) / self.unknown_scale())) * dt / (dt + dt_hist)
+
+    def wrong_sign(self, u_new, u_start, u_hist, dt, dt_hist):
+        u_pred = u_start - (dt / dt_hist) * (u_start - u_hist)
+        return float(np.max(np.abs(u_new - u_pred) / self.unknown_scale())) * dt / (2.0 * dt + dt_hist)
+
+    for mut in (wrong_factor, wrong_sign):
+        monkeypatch.setattr(Cell, "local_error", mut)
+        with pytest.raises(AssertionError):
+            test_local_error_estimate_is_the_implicit_euler_error(params, 0.05, 0.05)
+        monkeypatch.undo()
+
+
+def test_adaptive_step_controller(params):
+    """The controller: without history the step is taken as given; a step
+    whose estimate exceeds tol is rejected and retried smaller; an accepted
+    step proposes dt * clamp(0.9 sqrt(tol/e), 0.2, 2); a stationary state
+    (zero estimate) doubles the step, up to dt_max."""
+    cell, lam, mode = _mode_cell(params)
+    u0 = _mode_state(cell, params, mode, 0.1)
+    u1, i1 = cell.step_adaptive(u0, None, None, 1.0, 0.0, tol=1e-6)
+    assert i1["dt_used"] == 1.0 and i1["rejects"] == 0
+    # a tolerance the 1 s step cannot meet: rejections down to an accepted size
+    u2, i2 = cell.step_adaptive(u1, u0, 1.0, 1.0, 0.0, tol=1e-7)
+    assert i2["rejects"] >= 1 and i2["dt_used"] < 1.0 and i2["err"] <= 1e-7
+    fac = min(2.0, max(0.2, 0.9 * math.sqrt(1e-7 / i2["err"])))
+    assert abs(i2["dt_next"] - i2["dt_used"] * fac) <= 1e-15 * i2["dt_used"]
+    # rest state: nothing changes, the estimate is zero, the step doubles
+    r0 = cell.initial_state()
+    r1, _ = cell.step_adaptive(r0, None, None, 2.0, 0.0, tol=1e-6)
+    r2, i3 = cell.step_adaptive(r1, r0, 2.0, 2.0, 0.0, tol=1e-6, dt_max=3.0)
+    assert i3["err"] == 0.0 and i3["dt_next"] == 3.0
