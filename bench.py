@@ -61,7 +61,7 @@ def fom_opts(B, prec, args):
     return B.default_opts(precision=prec, newton_tol=1e-10, krylov_rtol=1e-4 if prec else 1e-6,
                           newton_maxit=20, krylov_maxit=300, max_halvings=3,
                           mg_bf16=0 if args.fp32_coarse else 1, mg_stream=args.mg_stream,
-                          mg_tail=0 if args.no_mg_tail else 1)
+                          mg_tail=1 if args.mg_tail else 0)
 
 
 def step_record(infos):
@@ -257,7 +257,7 @@ ROM_DIMS = (60, 30, 30, 200, 150)     # POD c, plated Li, phi; EI interface, mig
 ROM_DIMS_PAPER = (183, 40, 69, 952, 1027)   # the paper's 183 c / 69 phi modes, 952 BV / 1027 lambda points
 
 
-def rom_paper_dims(B, params, args, torch):
+def rom_paper_dims(B, params, args, torch, estimate=True):
     """The reduced model at the paper's dimensions (as far as the 16x16x48
     cell's snapshots support them): snapshots at four parameter points
     (C-rate 0.5, 5, 2, 1) over 60 steps, POD to 1e-9; a timed batch of
@@ -288,7 +288,7 @@ def rom_paper_dims(B, params, args, torch):
         V = np.array([fc.step(1.0, prm[b][0])["V_cell"] for _ in range(steps)])
         fc.close()
         errs.append(float(np.max(np.abs(out["V"][b][1:] - V)) / np.max(np.abs(V))))
-    est = rom_error_estimate(B, cell, rom, snap, prm, steps)
+    est = rom_error_estimate(B, cell, rom, snap, prm, steps) if estimate else None
     res = {"workload": "ROM of the %s cell at the paper's dimensions, snapshots at (C-rate, i0 scale, k_pl) = "
                        "(0.5, 0.5, 0.1), (5, 2, 10), (2, 1, 1), (1, 1, 1), 60 steps each; %d of the 600 steps "
                        "timed" % (ROM_CELL, steps),
@@ -326,8 +326,10 @@ def rom_error_estimate(B, cell, rom, snap, prm, steps, n_inst=256):
     out = r97.estimate(rom, prm[:n_inst], steps, 1.0, 0.0)
     wall = time.perf_counter() - t0
     e, nv = out["est"], out["norm_val"]
-    rel = {k: float(np.max(np.max(e[:, :, f], axis=1) / np.max(nv[:, :, f], axis=1)))
-           for f, k in enumerate(("c", "phi", "n_plated"))}
+    rel = {}
+    for f, k in enumerate(("c", "phi", "n_plated")):
+        den = np.max(nv[:, :, f], axis=1)
+        rel[k] = float(np.max(np.max(e[:, :, f], axis=1) / den)) if np.all(den > 0) else None
     v_err = float(np.max(np.abs(out["V"] - out["V_val"]) / np.abs(out["V_val"])))
     res = {"reduced_dims": {"n_r": r97.n_r, "blocks_c_n_phi": list(r97.block_dims()), "ei_interface": r97.n_bv,
                             "ei_migration": r97.n_1c},
@@ -476,8 +478,8 @@ def main():
                     help="smoother and coarse-level products from FP32 operators instead of their BF16 copies")
     ap.add_argument("--mg-stream", type=int, default=0, choices=[0, 1, 2],
                     help="operator fetch of the BF16 coarse sweeps: 0 plain, 1 L2 prefetch, 2 staged in shared memory")
-    ap.add_argument("--no-mg-tail", action="store_true",
-                    help="coarse V-cycle levels by per-level launches instead of one persistent launch")
+    ap.add_argument("--mg-tail", action="store_true",
+                    help="coarse V-cycle levels in one persistent cooperative launch instead of per-level launches")
     ap.add_argument("--no-fp64-arm", action="store_true",
                     help="skip the FP64 run of the same steps (and the mixed-vs-FP64 errors)")
     ap.add_argument("--no-rom", action="store_true", help="skip the reduced-model and serving measurements")
@@ -486,6 +488,9 @@ def main():
     ap.add_argument("--rom-paper-steps", type=int, default=3,
                     help="timed steps of the paper-size reduced model (a sample of its 600-step protocol)")
     ap.add_argument("--serve-requests", type=int, default=1000)
+    ap.add_argument("--experiment", action="store_true",
+                    help="also run the paper's half-cell model-reduction experiment at reduced size "
+                         "(paper_1704_04139_gb300.experiment) and add its results under 'experiment'")
     ap.add_argument("--rom-only", action="store_true",
                     help="run only the paper-size reduced model (build, timed batch, error check) and print its "
                          "JSON object: the command the reduced-model launch lists are taken with")
@@ -504,7 +509,7 @@ def main():
     params = syn.load_params()
     if args.rom_only:
         if rank == 0:
-            print(json.dumps({"rom": rom_paper_dims(B, params, args, torch)}))
+            print(json.dumps({"rom": rom_paper_dims(B, params, args, torch, estimate=False)}))
         return 0
     labels = workload_labels(args.workload)
     prec = B.PREC_MIXED if args.precision == "mixed" else B.PREC_FP64
@@ -617,6 +622,10 @@ def main():
         rom = rom_paper_dims(B, params, args, torch)
         rom_small, serve = rom_and_serve(B, params, args, torch)
 
+    experiment = None
+    if rank == 0 and ws == 1 and args.experiment:
+        from paper_1704_04139_gb300 import experiment as X
+        experiment = X.run_study(B, params)
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         v, wall, sample = oracle_sample(labels, params, np.sign(CRATE[args.workload]))
@@ -630,7 +639,7 @@ def main():
                           "device_bytes": int(cell.device_bytes),
                           "dt_s": dt, "crate": CRATE[args.workload], "precision": args.precision,
                           "coarse_operators": "fp32" if args.fp32_coarse else "bf16", "mg_stream": args.mg_stream,
-                          "mg_tail": 0 if args.no_mg_tail else 1,
+                          "mg_tail": 1 if args.mg_tail else 0,
                           "l2": "working set > 129 MB L2, no flush", "parallelism": "replicas" if ws > 1 else "1 GPU"},
                "clocks": clk, "e2e": e2e, "gpu_launches": int(launches), "roofline": roof,
                "cpu_baseline": cpu,
@@ -639,6 +648,8 @@ def main():
                               precond_ms=ms_pc, precond_calls=n_pc, residual_ms=ms_res, residual_calls=n_res),
                "fp64_arm": arm64,
                "rom": rom, "rom_small": rom_small, "serve": serve}
+        if experiment is not None:
+            out["experiment"] = experiment
         print(json.dumps(out))
     if dist is not None:
         dist.destroy_process_group()

@@ -95,10 +95,12 @@ typedef struct {
                               (the previous time level); 1 (default) the previous pass's converged
                               state.  The solution of a pass depends only on its frozen gates, not on
                               the start. */
-    int    mg_tail;        /* 1 (default): the V-cycle on the coarse levels that one wave of the GPU
-                              covers (level 2 down) runs as one persistent cooperative launch with
-                              grid barriers instead of one launch per sweep (same results); 0: per-level
-                              launches.  Applies to BF16 operators (mg_bf16 = 1). */
+    int    mg_tail;        /* 1: the V-cycle on the coarse levels that one wave of the GPU covers
+                              (level 2 down) runs as one persistent cooperative launch with grid
+                              barriers instead of one launch per sweep (same results); 0 (default):
+                              per-level launches, measured faster on GB300 inside the preconditioner's
+                              CUDA graph (2.27 against 2.43 ms per application on a 4.2M-voxel cell).
+                              Applies to BF16 operators (mg_bf16 = 1). */
 } mb_solver_opts;
 
 typedef struct {
@@ -155,7 +157,10 @@ int mb_state_set(mb_cell* cell, const double* u);
 
 /* One implicit Euler step of Eq. (ap4:detailed): Newton-Krylov with the
  * plating active-set passes; dt halved on failure up to max_halvings times.
- * Returns MB_ENOCONV when every halving failed (state unchanged). */
+ * Newton updates are capped at 0.25 in the scaled max-norm of the voxel
+ * unknowns (c, phi); the plated-Li inventories are not capped; convergence
+ * is tested on every unknown.  Returns MB_ENOCONV when every halving failed
+ * (state unchanged). */
 int mb_step(mb_cell* cell, double dt, double I_app, mb_step_info* info);
 
 /* Adaptive time step (Sec. workflow:discretization: the step size is
@@ -304,8 +309,10 @@ int mb_rom_destroy(mb_rom* rom);
  * (host double[B * (n_steps + 1)], instance-major, entry 0 the initial
  * state) receive s_cp and s_ac; a_final (host double[B * n_r]) the final
  * coefficients (may be NULL).  Newton per step and instance: step length
- * min(1, 0.25 / |U_loc delta|_s) on the stencil closure of the points,
- * converged at lam |U_loc delta|_s <= 1e-12, at most 30 iterations;
+ * min(1, 0.25 / |U_loc delta|_s) over the voxel unknowns (c, phi) of the
+ * stencil closure of the points (the plated-Li inventories are not capped),
+ * converged at lam |U_loc delta|_s <= 1e-12 over all of them, at most 30
+ * iterations;
  * plating active-set passes as mb_step (at most 3).  The state, the
  * interpolated terms and the residual are FP64 (the converged result is the
  * FP64 one); the Newton matrix is formed with FP32 accuracy (three TF32
@@ -316,6 +323,16 @@ int mb_rom_destroy(mb_rom* rom);
  * failed (its outputs are then NaN from that step on). */
 int mb_rom_solve_batch(mb_rom* rom, int B, const mb_rom_params* prm, int n_steps, double dt, double* V_out,
                        double* sac_out, double* a_final, mb_rom_info* info);
+
+/* As mb_rom_solve_batch, with the reduced coefficients of every step in
+ * a_traj (host double[B * (n_steps + 1) * n_r], instance-major, then step;
+ * entry 0 the initial coefficients): the reduced trajectories, from which
+ * U a reconstructs the fields (Sec. workflow:MOR). */
+int mb_rom_solve_batch_traj(mb_rom* rom, int B, const mb_rom_params* prm, int n_steps, double dt, double* V_out,
+                            double* sac_out, double* a_traj, mb_rom_info* info);
+/* The reduced basis U in the full state layout (host double[n * n_r],
+ * row-major: row i is unknown i of [c | phi | n_pl]). */
+int mb_rom_basis(mb_rom* rom, double* U);
 
 /* Hierarchical a-posteriori error estimate (Sec. workflow:MOR, Eqs.
  * ap4:saturation and ap4:estimate): B instances with parameters prm run

@@ -422,9 +422,12 @@ class Cell:
         """Newton's method with sparse direct LU (SciPy SuperLU) for the linear
         correction equations (the paper's BEST solver used AMG there, Sec. 2.4).
 
-        Step length: lam = min(1, DELTA_MAX / ||delta||_s) where ||.||_s is the
-        max-norm scaled by the unknown scales (c_ref, 1 V, n_c); DELTA_MAX = 0.25.
-        Stops after the first applied update with lam * ||delta||_s <= tol.
+        Step length: lam = min(1, DELTA_MAX / ||delta_v||_s) where ||.||_s is
+        the max-norm scaled by the unknown scales (c_ref, 1 V, n_c) and delta_v
+        the update of the voxel unknowns (c, phi: the arguments of the
+        exponentials; the plated inventories enter linearly and through the
+        saturating f_pre and are not capped); DELTA_MAX = 0.25.  Stops after
+        the first applied update with lam * ||delta||_s <= tol (all unknowns).
         With a list `record`, every iterate (after each update) is appended
         together with the gate it was computed with."""
         u = u0.copy()
@@ -436,7 +439,8 @@ class Cell:
             dn = np.max(np.abs(d) / us)
             if not np.isfinite(dn):
                 return u, it, False
-            lam = 1.0 if dn <= DELTA_MAX else DELTA_MAX / dn
+            dv = np.max(np.abs(d[:2 * self.N]) / us[:2 * self.N])
+            lam = 1.0 if dv <= DELTA_MAX else DELTA_MAX / dv
             u = u + lam * d
             if record is not None:
                 record.append((u.copy(), np.array(gate, dtype=np.float64)))

@@ -448,10 +448,15 @@ def solve(rom, mu, s_i0, k_pl, dt, n_steps, tol=TOL_NEWTON, maxit=30):
                 r = reduced_residual(rom, a, a_old, dt, mu, s_i0, k_pl, gate)
                 Jr = reduced_jacobian(rom, a, dt, s_i0, k_pl, gate)
                 d = equilibrated_solve(Jr, -r)
-                dn = np.max(np.abs(rom.Uloc @ d) / rom.us_loc) if len(rom.us_loc) else 0.0
+                du = np.abs(rom.Uloc @ d) / rom.us_loc
+                dn = np.max(du) if len(du) else 0.0
                 if not np.isfinite(dn):
                     break
-                lam = 1.0 if dn <= DELTA_MAX else DELTA_MAX / dn
+                # the step length caps the closure's voxel unknowns (c, phi), as the
+                # full-order Newton does; convergence on all of them
+                vox = rom.closure < 2 * N
+                dv = np.max(du[vox]) if np.any(vox) else 0.0
+                lam = 1.0 if dv <= DELTA_MAX else DELTA_MAX / dv
                 a = a + lam * d
                 its_total += 1
                 if lam * dn <= tol:

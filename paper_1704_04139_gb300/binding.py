@@ -147,6 +147,9 @@ def _declare(lib):
     fn("mb_rom_dims", C.c_int, [VP, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)])
     fn("mb_rom_solve_batch", C.c_int, [VP, C.c_int, C.POINTER(RomParams), C.c_int, C.c_double, VP, VP, VP,
                                         C.POINTER(RomInfo)])
+    fn("mb_rom_solve_batch_traj", C.c_int, [VP, C.c_int, C.POINTER(RomParams), C.c_int, C.c_double, VP, VP, VP,
+                                             C.POINTER(RomInfo)])
+    fn("mb_rom_basis", C.c_int, [VP, VP])
     fn("mb_rom_estimate_batch", C.c_int, [VP, VP, C.c_double, C.c_int, C.POINTER(RomParams), C.c_int, C.c_double,
                                           VP, VP, VP, VP, C.POINTER(RomInfo)])
     fn("mb_rom_block_dims", C.c_int, [VP, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)])
@@ -451,6 +454,26 @@ class Rom:
             _check(rc)
         out["ok"] = rc == 0
         return out
+
+    def solve_traj(self, params, n_steps, dt):
+        """As solve, with the coefficients of every step: a (B, n_steps+1, n_r)."""
+        B = len(params)
+        prm = (RomParams * B)(*[RomParams(*map(float, p)) for p in params])
+        V = np.empty((B, n_steps + 1))
+        S = np.empty((B, n_steps + 1))
+        A = np.empty((B, n_steps + 1, self.n_r))
+        info = RomInfo()
+        rc = lib().mb_rom_solve_batch_traj(self.h, B, prm, int(n_steps), float(dt), _ptr(V), _ptr(S), _ptr(A),
+                                           C.byref(info))
+        if rc != 0 and rc != -4:
+            _check(rc)
+        return dict(V=V, s_ac=S, a=A, newton_its=int(info.newton_its), failed=int(info.failed), ok=rc == 0)
+
+    def basis(self, n):
+        """The reduced basis U (n, n_r) in the full state layout."""
+        U = np.empty((n, self.n_r))
+        _check(lib().mb_rom_basis(self.h, _ptr(U)))
+        return U
 
     def estimate(self, val, params, n_steps, dt, theta=0.0):
         """Hierarchical error estimate against the validation model `val`

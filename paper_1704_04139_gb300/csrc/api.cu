@@ -115,7 +115,7 @@ void mb_opts_default(mb_solver_opts* o) {
     o->mg_bf16 = 1;
     o->mg_stream = 0;
     o->pass_start = 1;
-    o->mg_tail = 1;
+    o->mg_tail = 0;
 }
 
 static int check_opts(const mb_solver_opts* o) {

@@ -782,7 +782,8 @@ int launch_gate_residual_unprofiled(mb_cell* c, const double* u, const double* u
 __global__ void __launch_bounds__(RED_THREADS)
 k_scaled_max(Dims D, const uint32_t* __restrict__ vc, const double* __restrict__ x, InvScales is,
              double* partials) {
-    double acc[1] = {0.0};
+    // [0] over every unknown, [1] over the voxel unknowns (c, phi) only
+    double acc[2] = {0.0, 0.0};
     int64_t n = 2 * D.N + D.F;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         double s;
@@ -792,8 +793,9 @@ k_scaled_max(Dims D, const uint32_t* __restrict__ vc, const double* __restrict__
         double a = fabs(x[i]) * s;
         if (!(a == a)) a = 1e300;   // NaN -> huge
         acc[0] = fmax(acc[0], a);
+        if (i < 2 * D.N) acc[1] = fmax(acc[1], a);
     }
-    block_reduce_store<1, true>(acc, partials);
+    block_reduce_store<2, true>(acc, partials);
 }
 
 InvScales inv_scales(const mb_cell* c, int which, double dt) {
@@ -806,14 +808,15 @@ InvScales inv_scales(const mb_cell* c, int which, double dt) {
     return is;
 }
 
-int scaled_maxnorm(mb_cell* c, const double* x, int which, double dt, double* out) {
+int scaled_maxnorm(mb_cell* c, const double* x, int which, double dt, double* out, double* out_vox) {
     cudaStream_t s = c->stream;
     k_scaled_max<<<RED_BLOCKS, RED_THREADS, 0, s>>>(c->D, c->vcode, x, inv_scales(c, which, dt), c->red), ::mb::count_launch(c);
-    k_reduce_final<true><<<1, RED_THREADS, 0, s>>>(c->red, 1, c->red_out), ::mb::count_launch(c);
+    k_reduce_final<true><<<2, RED_THREADS, 0, s>>>(c->red, 2, c->red_out), ::mb::count_launch(c);
     MB_CUDA_LAUNCH("scaled_max");
-    MB_CUDA(cudaMemcpyAsync(c->h_red, c->red_out, 8, cudaMemcpyDeviceToHost, s));
+    MB_CUDA(cudaMemcpyAsync(c->h_red, c->red_out, 16, cudaMemcpyDeviceToHost, s));
     MB_CUDA(cudaStreamSynchronize(s));
     *out = c->h_red[0];
+    if (out_vox) *out_vox = c->h_red[1];
     return MB_OK;
 }
 

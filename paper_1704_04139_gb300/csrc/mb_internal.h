@@ -215,7 +215,8 @@ struct InvScales {
 };
 InvScales inv_scales(const mb_cell* c, int which, double dt);
 // scaled max norms: which = 0 unknown scale, 1 residual scale (needs dt)
-int scaled_maxnorm(mb_cell* c, const double* x, int which, double dt, double* out);
+// (out_vox, if given: the same norm over the voxel unknowns c and phi only)
+int scaled_maxnorm(mb_cell* c, const double* x, int which, double dt, double* out, double* out_vox = nullptr);
 int functionals(mb_cell* c, const double* u, mb_step_info* info);
 int count_diff_u8(mb_cell* c, const uint8_t* a, const uint8_t* b, int64_t n, int64_t* out);
 

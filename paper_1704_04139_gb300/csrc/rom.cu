@@ -33,6 +33,7 @@
 // default), or by an FP64 Newton matrix and LU.
 #include <cuda_runtime.h>
 #include <math.h>
+#include <string.h>
 
 #include <algorithm>
 #include <type_traits>
@@ -80,6 +81,7 @@ struct RomDev {
     float* UlocCf = nullptr;
     float2* UlocCdf = nullptr; // Nr x nloc float-float copy for the reconstruction
     float* usf = nullptr;
+    float* uscf = nullptr;     // nloc: the scales of the step-length cap (voxel slots; +inf for face slots)
     double* bbnd = nullptr;    // Nr
     double* scp = nullptr;     // Nr
     double* sac = nullptr;     // Nr
@@ -969,43 +971,58 @@ k_rom_unorm(RomDev d, int B, const double* __restrict__ delta, const int* __rest
         }
         __syncthreads();
     }
-    // per instance: max over this thread's 4 slots, then over the warp's 32 threads
+    // per instance: max over this thread's 4 slots, then over the warp's 32
+    // threads: over every slot (dpart) and over the voxel slots only (the
+    // step-length cap: dpart + B * gridDim.x)
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-        float m = 0.f;
+        float m = 0.f, mc = 0.f;
 #pragma unroll
         for (int s = 0; s < 4; ++s) {
             const int k = k0 + tx + 32 * s;
             if (k < d.nloc) {
-                const float v = fabsf(acc[s][q]) / d.usf[k];
+                const float a = fabsf(acc[s][q]);
+                const float v = a / d.usf[k], vc = a / d.uscf[k];
                 m = (v == v) ? fmaxf(m, v) : INFINITY;
+                mc = (vc == vc) ? fmaxf(mc, vc) : INFINITY;
             }
         }
-        for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+        for (int o = 16; o > 0; o >>= 1) {
+            m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+            mc = fmaxf(mc, __shfl_xor_sync(0xffffffffu, mc, o));
+        }
         const int b = b0 + ty * 4 + q;
-        if (tx == 0 && b < B) dpart[(int64_t)b * gridDim.x + blockIdx.x] = m;
+        if (tx == 0 && b < B) {
+            dpart[(int64_t)b * gridDim.x + blockIdx.x] = m;
+            dpart[((int64_t)B + b) * gridDim.x + blockIdx.x] = mc;
+        }
     }
 }
 
 // step length and convergence of instance b from the partial maxima (one warp per instance)
 __global__ void __launch_bounds__(32)
-k_rom_apply(RomDev d, int nkt, double* __restrict__ a, const double* __restrict__ delta,
+k_rom_apply(RomDev d, int B, int nkt, double* __restrict__ a, const double* __restrict__ delta,
             const float* __restrict__ dpart, int* __restrict__ active, int* __restrict__ failed,
             long long* __restrict__ its, int* __restrict__ pit, int* __restrict__ hp, float* __restrict__ dnprev) {
     const int b = blockIdx.x, lane = threadIdx.x;
     if (!active[b]) return;
-    float m = 0.f;
+    float m = 0.f, mc = 0.f;
     for (int t = lane; t < nkt; t += 32) {
-        const float v = dpart[(int64_t)b * nkt + t];
+        const float v = dpart[(int64_t)b * nkt + t], vc = dpart[((int64_t)B + b) * nkt + t];
         m = (v == v) ? fmaxf(m, v) : INFINITY;
+        mc = (vc == vc) ? fmaxf(mc, vc) : INFINITY;
     }
-    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-    const double dn = (double)m;
+    for (int o = 16; o > 0; o >>= 1) {
+        m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+        mc = fmaxf(mc, __shfl_xor_sync(0xffffffffu, mc, o));
+    }
+    const double dn = (double)m, dv = (double)mc;
     if (!(dn < INFINITY)) {
         if (lane == 0) { failed[b] = 1; active[b] = 0; }
         return;
     }
-    const double lam = dn <= ROM_DELTA_MAX ? 1.0 : ROM_DELTA_MAX / dn;
+    // the step length caps the voxel unknowns; convergence on all of them
+    const double lam = dv <= ROM_DELTA_MAX ? 1.0 : ROM_DELTA_MAX / dv;
     for (int j = lane; j < d.Nr; j += 32) a[(int64_t)b * d.Nr + j] += lam * delta[(int64_t)b * d.Nr + j];
     if (lane == 0) {
         its[b] += 1;
@@ -1400,6 +1417,13 @@ static int rom_build_host(mb_rom* R, const mb_rom_data* dd) {
         ok = upf(d.Msf, dd->Ms, (size_t)Nr * Nr) &&
              upf(d.Alinf, dd->Alin, (size_t)Nr * Nr) && upf(d.UlocRf, UlocR.data(), UlocR.size()) &&
              upf(d.UlocCf, UlocC.data(), UlocC.size()) && upf(d.usf, us.data(), us.size());
+    if (ok) {
+        // the step length caps the closure's voxel unknowns only (face slots: scale +inf)
+        std::vector<double> usc(us);
+        for (int64_t k = 0; k < nloc; ++k)
+            if (closure[k] >= 2 * N) usc[k] = INFINITY;
+        ok = upf(d.uscf, usc.data(), usc.size());
+    }
     // shared memory of the LU kernels beyond the default 48 KB
     if (ok)
         ok = cudaFuncSetAttribute(k_rom_lu<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1429,7 +1453,7 @@ static int rom_work_alloc(mb_rom* R, int B) {
     w.uloc_old = rom_alloc<double>(L, (size_t)B * d.nloc);
     w.f = rom_alloc<double>(L, (size_t)B * d.M);
     w.G = rom_alloc<float>(L, (size_t)B * (d.M ? d.M : 1) * GMAX);
-    w.dpart = rom_alloc<float>(L, (size_t)B * ((d.nloc + UN_K - 1) / UN_K));
+    w.dpart = rom_alloc<float>(L, (size_t)2 * B * ((d.nloc + UN_K - 1) / UN_K));
     w.hp = rom_alloc<int>(L, B);
     w.hplist = rom_alloc<int>(L, B);
     w.alist = rom_alloc<int>(L, B);
@@ -1632,8 +1656,8 @@ static void iter_main_c(mb_rom* R, cudaStream_t s) {
     const unsigned nkt = (unsigned)((d.nloc + UN_K - 1) / UN_K);
     k_rom_unorm<<<dim3(nkt, (unsigned)((B + UN_B - 1) / UN_B)), 256, 0, s>>>(d, B, w.delta, w.active, w.dpart),
         count_launch(c);
-    k_rom_apply<<<(unsigned)B, 32, 0, s>>>(d, (int)nkt, w.a, w.delta, w.dpart, w.active, w.failed, w.its, w.pit, w.hp,
-                                           w.dnprev), count_launch(c);
+    k_rom_apply<<<(unsigned)B, 32, 0, s>>>(d, B, (int)nkt, w.a, w.delta, w.dpart, w.active, w.failed, w.its, w.pit,
+                                           w.hp, w.dnprev), count_launch(c);
     k_rom_count_hp<<<1, 256, 0, s>>>(B, w.active, w.hp, w.counts, w.hplist, w.alist), count_launch(c);
 }
 
@@ -1948,16 +1972,39 @@ static int rom_batch_begin(mb_rom* R, int B, const mb_rom_params* prm, double dt
 }
 }  // namespace mb
 
+static int rom_solve(mb_rom* R, int B, const mb_rom_params* prm, int n_steps, double dt, double* V_out,
+                     double* sac_out, double* a_final, double* a_traj, mb_rom_info* info);
+
 extern "C" int mb_rom_solve_batch(mb_rom* R, int B, const mb_rom_params* prm, int n_steps, double dt, double* V_out,
                                   double* sac_out, double* a_final, mb_rom_info* info) {
     if (!R || B < 1 || !prm || n_steps < 0 || !(dt > 0) || !V_out || !sac_out) {
         set_error("mb_rom_solve_batch: invalid argument");
         return MB_EINVAL;
     }
+    return rom_solve(R, B, prm, n_steps, dt, V_out, sac_out, a_final, nullptr, info);
+}
+
+extern "C" int mb_rom_solve_batch_traj(mb_rom* R, int B, const mb_rom_params* prm, int n_steps, double dt,
+                                       double* V_out, double* sac_out, double* a_traj, mb_rom_info* info) {
+    if (!R || B < 1 || !prm || n_steps < 0 || !(dt > 0) || !V_out || !sac_out || !a_traj) {
+        set_error("mb_rom_solve_batch_traj: invalid argument");
+        return MB_EINVAL;
+    }
+    return rom_solve(R, B, prm, n_steps, dt, V_out, sac_out, nullptr, a_traj, info);
+}
+
+extern "C" int mb_rom_basis(mb_rom* R, double* U) {
+    if (!R || !U) { set_error("mb_rom_basis: invalid argument"); return MB_EINVAL; }
+    memcpy(U, R->hU.data(), sizeof(double) * R->hU.size());
+    return MB_OK;
+}
+
+static int rom_solve(mb_rom* R, int B, const mb_rom_params* prm, int n_steps, double dt, double* V_out,
+                     double* sac_out, double* a_final, double* a_traj, mb_rom_info* info) {
     const int ncol = n_steps + 1;
     int rc = rom_batch_begin(R, B, prm, dt);
     if (rc) return rc;
-    std::vector<double> hV(B), hS(B);
+    std::vector<double> hV(B), hS(B), ha(a_traj ? (size_t)B * R->d.Nr : 0);
     std::vector<int> hf(B);
     for (int step = 0; step <= n_steps; ++step) {
         if (step > 0 && (rc = rom_batch_step(R))) return rc;
@@ -1965,6 +2012,12 @@ extern "C" int mb_rom_solve_batch(mb_rom* R, int B, const mb_rom_params* prm, in
         for (int b = 0; b < B; ++b) {
             V_out[(size_t)b * ncol + step] = hf[b] ? NAN : hV[b];
             sac_out[(size_t)b * ncol + step] = hf[b] ? NAN : hS[b];
+        }
+        if (a_traj) {
+            const int Nr = R->d.Nr;
+            MB_CUDA(cudaMemcpy(ha.data(), R->w.a, 8 * ha.size(), cudaMemcpyDeviceToHost));
+            for (int b = 0; b < B; ++b)
+                memcpy(a_traj + ((size_t)b * ncol + step) * Nr, ha.data() + (size_t)b * Nr, 8 * (size_t)Nr);
         }
     }
     mb_rom_info inf{0, 0, 0};

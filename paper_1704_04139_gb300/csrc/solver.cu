@@ -416,10 +416,15 @@ static int newton(mb_cell* c, double dt, double I_app, bool from_old, int* its_o
         if (rc == MB_ENOCONV) { *its_out = it; return MB_OK; }
         if (rc) return rc;
         *kits += ki;
-        double dn;
-        if ((rc = scaled_maxnorm(c, c->du, 0, dt, &dn))) return rc;
+        // the step length caps the update of the voxel unknowns (c, phi: the
+        // arguments of the exponentials); the plated inventories enter linearly
+        // and through the saturating f_pre, so their update is not capped (a
+        // stripping layer of many critical thicknesses would otherwise crawl);
+        // convergence is tested on every unknown
+        double dn, dv;
+        if ((rc = scaled_maxnorm(c, c->du, 0, dt, &dn, &dv))) return rc;
         if (!(dn < 1e200)) { *its_out = it; return MB_OK; }
-        double lam = dn <= DELTA_MAX ? 1.0 : DELTA_MAX / dn;
+        double lam = dv <= DELTA_MAX ? 1.0 : DELTA_MAX / dv;
         if (debug_level() > 0)
             fprintf(stderr, "[mb] newton it %d |R|_s %.3e |d|_s %.3e lam %.3f krylov %d relres %.2e\n", it, rn,
                     dn, lam, ki, rr);

