@@ -63,7 +63,9 @@ int mb_debug_rom_refine(mb_rom* rom, int on);
  * iterations and the escalated branch on the device) or drive the loops from
  * the host (0).  Both give the same results. */
 int mb_debug_rom_graph(mb_rom* rom, int on);
-/* Use (on = 1, the default) or not the tensor-core Newton-matrix kernel in the online solve. */
+/* The online solve's Newton-matrix GEMM: 2 on tcgen05 with the accumulator in
+ * tensor memory (models with N_r <= 256), 1 (the default) mma.sync tensor-core
+ * kernel, 0 FP32 FMA; all three with FP32 accuracy (3xTF32 on the tensor cores). */
 int mb_debug_rom_tensor(mb_rom* rom, int on);
 
 /* The solver's own Newton residual (interface currents evaluated once per

@@ -508,7 +508,7 @@ class Rom:
 
     def debug_tensor(self, on):
         """Newton-matrix GEMM on the tensor cores (3xTF32, the default) or FP32 FMA."""
-        _check(lib().mb_debug_rom_tensor(self.h, 1 if on else 0))
+        _check(lib().mb_debug_rom_tensor(self.h, int(on)))
 
     def close(self):
         if getattr(self, "h", None):
@@ -592,7 +592,8 @@ class Server:
 
 def debug_rom_jac(P, GU, Ms, Alin, dt_inv, tc=True):
     """The reduced model's Newton-matrix kernel on given arrays: J[b] = P GU[b] +
-    Ms dt_inv[b] + Alin (GU shape (B, M, Nr)); tc selects the tensor-core kernel."""
+    Ms dt_inv[b] + Alin (GU shape (B, M, Nr)); tc: 2 the tcgen05 kernel (TMEM
+    accumulator), 1 (or True) the mma.sync tensor-core kernel, 0 FP32 FMA."""
     P = np.ascontiguousarray(P, dtype=np.float32)
     Nr, M = P.shape
     B = len(dt_inv)
@@ -601,8 +602,7 @@ def debug_rom_jac(P, GU, Ms, Alin, dt_inv, tc=True):
     al = np.ascontiguousarray(Alin, dtype=np.float32)
     dti = np.ascontiguousarray(dt_inv, dtype=np.float64)
     J = np.empty((B, Nr, Nr), dtype=np.float32)
-    _check(lib().mb_debug_rom_jac(Nr, M, B, _ptr(P), _ptr(gu), _ptr(ms), _ptr(al), _ptr(dti), 1 if tc else 0,
-                                  _ptr(J)))
+    _check(lib().mb_debug_rom_jac(Nr, M, B, _ptr(P), _ptr(gu), _ptr(ms), _ptr(al), _ptr(dti), int(tc), _ptr(J)))
     return J
 
 

@@ -75,6 +75,9 @@ struct RomDev {
     double* Ms = nullptr;      // Nr x Nr
     double* Alin = nullptr;    // Nr x Nr
     float* Ptf = nullptr;      // FP32 copies for the Newton matrix: P^T (M x Nr), Ms, Alin, UlocR, UlocC, us
+    float* Pbf = nullptr;      // TF32 head and tail of P (Npad x Mpad, row-major, zero padded): the
+    float* Psf = nullptr;      //   tcgen05 GEMM's B operand
+    int Npad = 0, Mpad = 0;    // Nr rounded up to 16, M rounded up to the K slice
     float* Msf = nullptr;
     float* Alinf = nullptr;
     float* UlocRf = nullptr;
@@ -118,6 +121,7 @@ struct RomWork {
     // the Newton iterations and the escalated branch on the device)
     cudaGraphExec_t gexec = nullptr;
     int* ctl = nullptr;        // device: [0] Newton iteration of the pass, [1] passes done
+    int* tcerr = nullptr;      // device: a bounded wait of the tcgen05 GEMM gave up
     bool graph_failed = false; // the graph could not be built: host-driven steps
     std::vector<void*> bufs;
 };
@@ -468,6 +472,235 @@ k_rom_jac(RomDev d, int B, int nlist, const int* __restrict__ alist, const doubl
         }
 }
 
+
+// ---- the same Newton-matrix GEMM on the 5th-generation tensor cores
+// (tcgen05.mma kind::tf32, accumulator in tensor memory).  One CTA of 128
+// threads computes C^T for 128 GEMM columns (the MMA's M = TMEM lanes) and all
+// N_r rows (the MMA's N = TMEM columns, N_r padded to a multiple of 16 <= 256):
+// D[m][n] = sum_k GU[k][c0 + m] P[n][k].  K in slices of T5_K staged in shared
+// memory in the no-swizzle K-major layout of 8-row x 16-byte core matrices
+// (row r, element k at (k/4) LBO + (r/8) 128 + (r%8) 16 + (k%4) 4 bytes, LBO =
+// rows x 16), each operand as a TF32 head and tail (the 3xTF32 split of the
+// mma.sync kernel: small*big + big*small + big*big per K step), the P head and
+// tail precomputed (Pbf, Psf: N_pad x M_pad, row-major, zero padded).  One
+// thread issues the MMAs; their completion is signalled on an mbarrier by
+// tcgen05.commit.  Every wait is bounded: on a timeout the CTA sets *err,
+// waits (bounded) for its MMAs, frees its tensor memory and returns.
+constexpr int T5_M = 128, T5_K = 32, T5_THREADS = 128, T5_NMAX = 256;
+constexpr int T5_SPIN = 1 << 22;
+constexpr int T5_A_BYTES = T5_M * T5_K * 4;            // one A tile (16 KB)
+constexpr int T5_B_BYTES = T5_NMAX * T5_K * 4;         // one B tile (32 KB)
+constexpr int T5_TILES = 2 * T5_A_BYTES + 2 * T5_B_BYTES;   // 96 KB
+// the CTA's shared memory is padded well beyond the tiles, so that no
+// descriptor offset of the layout above can leave the allocation
+constexpr int T5_SMEM = 225 * 1024;
+
+__device__ inline uint32_t t5_smem(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+// shared-memory matrix descriptor: start address, leading (K-direction) and
+// stride (8-row-group) byte offsets, descriptor version 1, no swizzle
+__device__ inline uint64_t t5_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+    uint64_t d = 0;
+    d |= (uint64_t)((addr >> 4) & 0x3FFFu);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1 << 46;
+    return d;
+}
+// instruction descriptor of kind::tf32: FP32 accumulator, TF32 A and B, both
+// K-major, N >> 3 at bit 17, M >> 4 at bit 24
+__host__ __device__ constexpr uint32_t t5_idesc(int M, int N) {
+    return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+__device__ inline void t5_mma(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t accum) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}"
+        ::"r"(tmem_d), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum)
+        : "memory");
+}
+__device__ inline void t5_commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(t5_smem(bar))
+                 : "memory");
+}
+__device__ inline void t5_mbar_init(uint64_t* bar) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(t5_smem(bar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ inline bool t5_wait(uint64_t* bar, uint32_t parity) {
+    for (int i = 0; i < T5_SPIN; ++i) {
+        uint32_t ok;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(ok)
+            : "r"(t5_smem(bar)), "r"(parity)
+            : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+__device__ inline void t5_ld16(uint32_t taddr, float (&v)[16]) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int q = 0; q < 16; ++q) v[q] = __uint_as_float(r[q]);
+}
+
+// TF32 head and tail of P for the tcgen05 GEMM's B operand, from its K-major
+// FP32 copy Ptf (M x Nr): Pbf, Psf (Npad x Mpad, row-major, zero padded)
+__global__ void k_rom_psplit(int Nr, int M, int Npad, int Mpad, const float* __restrict__ Ptf,
+                             float* __restrict__ Pbf, float* __restrict__ Psf) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (int64_t)Npad * Mpad) return;
+    const int n = (int)(e / Mpad), k = (int)(e % Mpad);
+    uint32_t hb = 0u, hs = 0u;
+    if (n < Nr && k < M) tf32_split(Ptf[(int64_t)k * Nr + n], hb, hs);
+    Pbf[e] = __uint_as_float(hb);
+    Psf[e] = __uint_as_float(hs);
+}
+
+__global__ void __launch_bounds__(T5_THREADS, 1)
+k_rom_jac5(RomDev d, int B, int nlist, const int* __restrict__ alist, const double* __restrict__ prm,
+           const float* __restrict__ GU, const int* __restrict__ hp, float* __restrict__ J,
+           const int* __restrict__ dit, const int* __restrict__ dnlist, int* __restrict__ err) {
+    extern __shared__ __align__(1024) uint8_t t5_raw[];
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ uint32_t tmem_slot;
+    const int Nr = d.Nr, M = d.M, NP = d.Npad, MP = d.Mpad;
+    if (dit) {
+        if (*dit > 0) nlist = *dnlist;
+        else alist = nullptr;
+    }
+    const int ncol = (alist ? nlist : B) * Nr;
+    const int64_t gstride = (int64_t)B * Nr;
+    const int c0 = blockIdx.x * T5_M;
+    if (c0 >= ncol) return;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    uint8_t* const Ab = t5_raw;
+    uint8_t* const As = t5_raw + T5_A_BYTES;
+    uint8_t* const Bb = t5_raw + 2 * T5_A_BYTES;
+    uint8_t* const Bs = Bb + T5_B_BYTES;
+    const uint32_t lbo_a = T5_M * 16, lbo_b = (uint32_t)NP * 16;
+    if (tid == 0) t5_mbar_init(&bar);
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(t5_smem(&tmem_slot)),
+                     "r"(T5_NMAX));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_slot;
+    // this thread's GEMM column (its A row), fixed over the K loop
+    const int c = c0 + tid;
+    const bool cvalid = c < ncol;
+    int64_t boff = 0;
+    if (cvalid) {
+        const int l = c / Nr;
+        boff = (int64_t)(alist ? alist[l] : l) * Nr + (c - l * Nr);
+    }
+    const uint32_t idesc = t5_idesc(T5_M, NP);
+    bool ok = true;
+    int nslices = 0;
+    float ra[T5_K];
+    auto fetch = [&](int k0) {
+#pragma unroll
+        for (int kk = 0; kk < T5_K; ++kk) {
+            const int k = k0 + kk;
+            ra[kk] = (cvalid && k < M) ? GU[(int64_t)k * gstride + boff] : 0.f;
+        }
+    };
+    fetch(0);
+    for (int k0 = 0; k0 < M; k0 += T5_K, ++nslices) {
+        // the previous slice's MMAs have read the tiles
+        if (nslices > 0 && !t5_wait(&bar, (uint32_t)(nslices - 1) & 1u)) { ok = false; break; }
+        // A: this thread's column, K chunks of 4 as 16-byte stores (head and tail)
+#pragma unroll
+        for (int q = 0; q < T5_K / 4; ++q) {
+            uint32_t hb[4], hs[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) tf32_split(ra[4 * q + e], hb[e], hs[e]);
+            const uint32_t off = (uint32_t)q * lbo_a + (uint32_t)(tid >> 3) * 128u + (uint32_t)(tid & 7) * 16u;
+            *reinterpret_cast<uint4*>(Ab + off) = make_uint4(hb[0], hb[1], hb[2], hb[3]);
+            *reinterpret_cast<uint4*>(As + off) = make_uint4(hs[0], hs[1], hs[2], hs[3]);
+        }
+        // B: rows n < NP of the precomputed P head and tail, 16-byte chunks
+        for (int e = tid; e < NP * (T5_K / 4); e += T5_THREADS) {
+            const int n = e >> 3, q = e & 7;
+            const int64_t g = (int64_t)n * MP + k0 + 4 * q;
+            const uint32_t off = (uint32_t)q * lbo_b + (uint32_t)(n >> 3) * 128u + (uint32_t)(n & 7) * 16u;
+            *reinterpret_cast<float4*>(Bb + off) = *reinterpret_cast<const float4*>(d.Pbf + g);
+            *reinterpret_cast<float4*>(Bs + off) = *reinterpret_cast<const float4*>(d.Psf + g);
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+            for (int s = 0; s < T5_K / 8; ++s) {
+                const uint32_t ka = (uint32_t)(2 * s) * lbo_a, kb = (uint32_t)(2 * s) * lbo_b;
+                const uint64_t dab = t5_desc(t5_smem(Ab) + ka, lbo_a, 128), das = t5_desc(t5_smem(As) + ka, lbo_a, 128);
+                const uint64_t dbb = t5_desc(t5_smem(Bb) + kb, lbo_b, 128), dbs = t5_desc(t5_smem(Bs) + kb, lbo_b, 128);
+                t5_mma(tmem, das, dbb, idesc, (k0 > 0 || s > 0) ? 1u : 0u);
+                t5_mma(tmem, dab, dbs, idesc, 1u);
+                t5_mma(tmem, dab, dbb, idesc, 1u);
+            }
+            t5_commit(&bar);
+        }
+        if (k0 + T5_K < M) fetch(k0 + T5_K);   // the next slice in flight during the MMAs
+    }
+    if (ok && nslices > 0 && !t5_wait(&bar, (uint32_t)(nslices - 1) & 1u)) ok = false;
+    if (!ok) {
+        if (tid == 0) {
+            atomicOr(err, 1);
+            t5_wait(&bar, (uint32_t)(nslices - 1) & 1u);   // bounded: the MMAs in flight
+        }
+    } else {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        // epilogue: warp w reads TMEM lanes 32w.. (its 32 columns), 16 rows per load
+        const int l = cvalid ? c / Nr : 0, j = c - l * Nr;
+        const int b = cvalid ? (alist ? alist[l] : l) : 0;
+        const bool wr = cvalid && !hp[b];   // escalated: J[b] keeps the LU factors of its last FP32 iteration
+        const float dt_inv = wr ? (float)prm[RP * b + 3] : 0.f;
+        for (int n0 = 0; n0 < NP; n0 += 16) {
+            float v[16];
+            t5_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)n0, v);
+            if (wr) {
+#pragma unroll
+                for (int q = 0; q < 16; ++q) {
+                    const int i = n0 + q;
+                    if (i < Nr)
+                        J[((int64_t)b * Nr + i) * Nr + j] =
+                            v[q] + d.Msf[(int64_t)i * Nr + j] * dt_inv + d.Alinf[(int64_t)i * Nr + j];
+                }
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(T5_NMAX));
+}
+
+// host: prepare the tcgen05 GEMM's P operand and its shared memory (false:
+// this model cannot use it, N_r > 256)
+static bool t5_prepare(RomDev& d, std::vector<void*>& owned) {
+    if (d.Nr > T5_NMAX || d.M < 1) return false;
+    d.Npad = (d.Nr + 15) / 16 * 16;
+    d.Mpad = (d.M + T5_K - 1) / T5_K * T5_K;
+    const size_t n = (size_t)d.Npad * d.Mpad;
+    d.Pbf = rom_alloc<float>(owned, n);
+    d.Psf = rom_alloc<float>(owned, n);
+    if (!d.Pbf || !d.Psf) return false;
+    if (cudaFuncSetAttribute(k_rom_jac5, cudaFuncAttributeMaxDynamicSharedMemorySize, T5_SMEM) != cudaSuccess)
+        return false;
+    k_rom_psplit<<<(unsigned)((n + 255) / 256), 256>>>(d.Nr, d.M, d.Npad, d.Mpad, d.Ptf, d.Pbf, d.Psf);
+    return cudaGetLastError() == cudaSuccess && cudaDeviceSynchronize() == cudaSuccess;
+}
 
 // FP64 Newton matrix of the instances with hp[b]: GU64[b][p][:] = G64[b][p] U_loc
 // (one block per point and instance), then J64[b] = Ms/dt + Alin + P GU64[b]
@@ -1413,6 +1646,11 @@ static int rom_build_host(mb_rom* R, const mb_rom_data* dd) {
             for (int k = 0; k < M; ++k) Pt[(size_t)k * Nr + i] = P[(size_t)i * M + k];
         ok = upf(d.Ptf, Pt.data(), Pt.size());
     }
+    // the tcgen05 GEMM's operand (models with N_r <= 256; others keep the mma.sync kernel)
+    if (ok && !t5_prepare(d, R->owned)) {
+        d.Pbf = d.Psf = nullptr;
+        cudaGetLastError();
+    }
     if (ok)
         ok = upf(d.Msf, dd->Ms, (size_t)Nr * Nr) &&
              upf(d.Alinf, dd->Alin, (size_t)Nr * Nr) && upf(d.UlocRf, UlocR.data(), UlocR.size()) &&
@@ -1473,6 +1711,7 @@ static int rom_work_alloc(mb_rom* R, int B) {
     w.pass_on = rom_alloc<int>(L, B);
     w.counts = rom_alloc<int>(L, 4);
     w.ctl = rom_alloc<int>(L, 4);
+    w.tcerr = rom_alloc<int>(L, 4);
     w.its = rom_alloc<long long>(L, B);
     w.flips = rom_alloc<long long>(L, B);
     w.V = rom_alloc<double>(L, (size_t)B);
@@ -1499,6 +1738,7 @@ int rom_batch_alloc(mb_rom* R, int B) {
     MB_CUDA(cudaMemsetAsync(w.flips, 0, 8 * B, s));
     MB_CUDA(cudaMemsetAsync(w.hp, 0, 4 * B, s));
     MB_CUDA(cudaMemsetAsync(w.pit, 0, 4 * B, s));
+    MB_CUDA(cudaMemsetAsync(w.tcerr, 0, 16, s));
     MB_CUDA(cudaStreamSynchronize(s));
     w.hp_any = 0;
     return MB_OK;
@@ -1528,7 +1768,14 @@ int rom_batch_outputs(mb_rom* R, double* hV, double* hS, int* hfailed) {
     MB_CUDA(cudaMemcpyAsync(hV, w.V, 8 * B, cudaMemcpyDeviceToHost, s));
     MB_CUDA(cudaMemcpyAsync(hS, w.S, 8 * B, cudaMemcpyDeviceToHost, s));
     if (hfailed) MB_CUDA(cudaMemcpyAsync(hfailed, w.failed, 4 * B, cudaMemcpyDeviceToHost, s));
+    int terr = 0;
+    MB_CUDA(cudaMemcpyAsync(&terr, w.tcerr, 4, cudaMemcpyDeviceToHost, s));
     MB_CUDA(cudaStreamSynchronize(s));
+    if (terr) {
+        R->d.tc = 1;   // the tcgen05 GEMM gave up waiting: the mma.sync kernel from now on
+        set_error("reduced model: a bounded wait of the tcgen05 Newton-matrix GEMM gave up");
+        return MB_ETIMEOUT;
+    }
     return MB_OK;
 }
 
@@ -1636,7 +1883,10 @@ static void iter_main_b(mb_rom* R, cudaStream_t s, bool listed, int ncols, const
                       (unsigned)((d.Nr + JT_ROWS - 1) / JT_ROWS));
         const int* al = (listed || dit) ? w.alist : nullptr;
         const int* dn = dit ? w.counts + 2 : nullptr;
-        if (d.tc)
+        if (d.tc == 2 && d.Pbf)
+            k_rom_jac5<<<(unsigned)(((int64_t)ncols * d.Nr + T5_M - 1) / T5_M), T5_THREADS, T5_SMEM, s>>>(
+                d, B, ncols, al, w.prm, w.GU, w.hp, w.J, dit, dn, w.tcerr);
+        else if (d.tc)
             k_rom_jac<true><<<gj, 256, 0, s>>>(d, B, ncols, al, w.prm, w.GU, w.hp, w.J, dit, dn);
         else
             k_rom_jac<false><<<gj, 256, 0, s>>>(d, B, ncols, al, w.prm, w.GU, w.hp, w.J, dit, dn);
@@ -2319,13 +2569,29 @@ extern "C" int mb_debug_rom_jac(int Nr, int M, int B, const float* P, const floa
         rc = cuda_fail(cudaGetLastError(), "debug_rom_jac alloc");
     } else {
         const dim3 gj((unsigned)(((int64_t)B * Nr + JT_COLS - 1) / JT_COLS), (unsigned)((Nr + JT_ROWS - 1) / JT_ROWS));
-        if (tc)
+        int* derr = (int*)dev(nullptr, 16);
+        if (derr) cudaMemset(derr, 0, 16);
+        if (tc == 2) {
+            if (!derr || !t5_prepare(d, bufs)) {
+                set_error("debug_rom_jac: the tcgen05 GEMM cannot run this size");
+                rc = MB_EINVAL;
+            } else {
+                k_rom_jac5<<<(unsigned)(((int64_t)B * Nr + T5_M - 1) / T5_M), T5_THREADS, T5_SMEM>>>(
+                    d, B, B, nullptr, dprm, gu, dhp, dJ, nullptr, nullptr, derr);
+            }
+        } else if (tc) {
             k_rom_jac<true><<<gj, 256>>>(d, B, B, nullptr, dprm, gu, dhp, dJ, nullptr, nullptr);
-        else
+        } else {
             k_rom_jac<false><<<gj, 256>>>(d, B, B, nullptr, dprm, gu, dhp, dJ, nullptr, nullptr);
-        cudaError_t e = cudaGetLastError();
-        if (e == cudaSuccess) e = cudaMemcpy(J, dJ, 4 * (size_t)B * Nr * Nr, cudaMemcpyDeviceToHost);
-        if (e != cudaSuccess) rc = cuda_fail(e, "debug_rom_jac");
+        }
+        if (!rc) {
+            cudaError_t e = cudaGetLastError();
+            if (e == cudaSuccess) e = cudaMemcpy(J, dJ, 4 * (size_t)B * Nr * Nr, cudaMemcpyDeviceToHost);
+            int herr = 0;
+            if (e == cudaSuccess && derr) e = cudaMemcpy(&herr, derr, 4, cudaMemcpyDeviceToHost);
+            if (e != cudaSuccess) rc = cuda_fail(e, "debug_rom_jac");
+            else if (herr) { set_error("debug_rom_jac: a bounded wait of the tcgen05 GEMM gave up"); rc = MB_ETIMEOUT; }
+        }
     }
     for (void* p : bufs) cudaFree(p);
     return rc;
@@ -2394,7 +2660,11 @@ extern "C" int mb_debug_rom_graph(mb_rom* R, int on) {
 }
 
 extern "C" int mb_debug_rom_tensor(mb_rom* R, int on) {
-    if (!R) return MB_EINVAL;
-    R->d.tc = on ? 1 : 0;
+    if (!R || on < 0 || on > 2) return MB_EINVAL;
+    if (on == 2 && !R->d.Pbf) {
+        set_error("mb_debug_rom_tensor: the tcgen05 GEMM does not take this model (N_r > 256)");
+        return MB_EINVAL;
+    }
+    R->d.tc = on;
     return MB_OK;
 }

@@ -148,19 +148,21 @@ def test_rom_wide_matches_oracle(params, wide_case):
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("tc", [True, False])
-def test_rom_newton_matrix_kernel(tc):
-    """The Newton-matrix kernel against an FP64 product: J_b = P GU_b + Ms/dt_b + Alin,
-    ragged in rows (70), the contraction (100) and the columns (3 x 70); both kernels
-    keep FP32 accuracy (the tensor-core one as three TF32 products)."""
+@pytest.mark.parametrize("tc,Nr,M,nb", [(1, 70, 100, 3), (0, 70, 100, 3), (2, 70, 100, 3), (2, 209, 1000, 5),
+                                        (2, 256, 64, 1)])
+def test_rom_newton_matrix_kernel(tc, Nr, M, nb):
+    """The Newton-matrix kernels against an FP64 product: J_b = P GU_b + Ms/dt_b + Alin,
+    ragged in rows (70, 209), the contraction (100, 1000) and the columns (nb x Nr);
+    all keep FP32 accuracy: FP32 FMA (0), three TF32 products per pair on mma.sync
+    (1) or on tcgen05 with the accumulator in tensor memory (2; also the largest
+    reduced dimension it takes, 256)."""
     B = _gpu()
-    rng = np.random.default_rng(7)
-    Nr, M, nb = 70, 100, 3
+    rng = np.random.default_rng(7 + Nr)
     P = rng.standard_normal((Nr, M)).astype(np.float32)
     GU = rng.standard_normal((nb, M, Nr)).astype(np.float32)
     Ms = rng.standard_normal((Nr, Nr)).astype(np.float32)
     Al = rng.standard_normal((Nr, Nr)).astype(np.float32)
-    dti = np.array([0.5, 2.0, 10.0])
+    dti = np.array([0.5, 2.0, 10.0, 1.0, 4.0])[:nb]
     J = B.debug_rom_jac(P, GU, Ms, Al, dti, tc=tc)
     P64, G64 = P.astype(np.float64), GU.astype(np.float64)
     for b in range(nb):
@@ -171,19 +173,22 @@ def test_rom_newton_matrix_kernel(tc):
 
 
 @pytest.mark.gpu
-def test_rom_tensor_newton_matrix_same_result(params, case):
-    """The online solve with the tensor-core Newton matrix converges to the same
-    reduced trajectory as with the FP32-FMA one (the matrix only steers Newton)."""
+@pytest.mark.parametrize("which", ["case", "wide_case"])
+def test_rom_tensor_newton_matrix_same_result(params, request, which):
+    """The online solve with either tensor-core Newton matrix (mma.sync, or
+    tcgen05 with the accumulator in tensor memory) converges to the same reduced
+    trajectory as with the FP32-FMA one (the matrix only steers Newton)."""
     B = _gpu()
-    lab, oc, rom = case
+    lab, oc, rom = request.getfixturevalue(which)
     gc, g = _gpu_rom(B, lab, params, rom)
-    prm = [(c * oc.i_1c, s, k) for (c, s, k) in [(-2.0, 1.0, 1.0), (1.0, 0.9, 0.5)]]
-    g.debug_tensor(True)
-    a = g.solve(prm, 4, 1.0)
-    g.debug_tensor(False)
-    b = g.solve(prm, 4, 1.0)
-    assert a["ok"] and b["ok"]
-    assert np.max(np.abs(a["V"] - b["V"])) <= 1e-9 * np.max(np.abs(a["V"]))
+    prm = [(c * oc.i_1c, s, k) for (c, s, k) in [(-2.0, 1.0, 1.0), (1.0, 0.9, 0.5), (-4.0, 0.7, 3.0)]]
+    out = {}
+    for tc in (1, 0, 2):
+        g.debug_tensor(tc)
+        out[tc] = g.solve(prm, 4, 1.0)
+        assert out[tc]["ok"], tc
+    for tc in (0, 2):
+        assert np.max(np.abs(out[tc]["V"] - out[1]["V"])) <= 1e-9 * np.max(np.abs(out[1]["V"])), tc
     g.close()
     gc.close()
 
