@@ -46,6 +46,8 @@ def workload_labels(name):
         return syn.full_cell(128, 128, 112, 32, 112, 0.30, 0.35, ("lognormal_mean", 5, 0.3), (21, 22))
     if name == "cell16x16x48":
         return syn.full_cell(16, 16, 20, 8, 20, 0.35, 0.35, ("uniform", 2, 4), (11, 12))
+    if name == "cell32x32x96":
+        return syn.full_cell(32, 32, 40, 16, 40, 0.35, 0.35, ("uniform", 2, 4), (11, 12))
     if name == "cell64x64x128":
         return syn.full_cell(64, 64, 53, 22, 53, 0.35, 0.35, ("uniform", 2, 4), (31, 32))
     raise SystemExit("unknown workload %s" % name)
@@ -351,15 +353,107 @@ def _rom_params(rng, n, i1):
     return [(-ci * i1, si, ki) for ci, si, ki in zip(c, s, k)]
 
 
+SERVE_FOM_CELL = "cell32x32x96"
+
+
+def _serve_requests(rng, n, i1, i1_fom):
+    """n requests of the serving mix: 95 % reduced-model queries (protocol
+    length U{100..3000} steps, C-rate from {0.5, 1, 2, 3, 5}, i0 scale and
+    plating rate as the reduced-model study), 5 % full-order validation solves
+    (60 steps)."""
+    out = []
+    for k in range(n):
+        crate = float(rng.choice([0.5, 1.0, 2.0, 3.0, 5.0]))
+        s = float(np.exp(rng.uniform(np.log(0.5), np.log(2.0))))
+        kp = float(np.exp(rng.uniform(np.log(0.1), np.log(10.0))))
+        if rng.random() < 0.95:
+            out.append(("rom", -crate * i1, s, kp, int(rng.integers(100, 3001))))
+        else:
+            out.append(("fom", -crate * i1_fom, s, kp, 60))
+    return out
+
+
+def serve_run(B, params, rom, i1, args, slots=256, workers=4):
+    """Continuous batching under Poisson arrivals.  The server's capacity is
+    measured on a burst of twice its slot count drawn from the same mix
+    (reduced and full-order requests), and requests then arrive at 0.8 of it.
+    Reduced requests run in the resident slot batch of `rom`; full-order
+    validation solves run on worker threads with cells of the 32x32x96
+    template (cfg1's generator rules), admitted by device memory."""
+    flab = workload_labels(SERVE_FOM_CELL)
+    fopts = B.default_opts(precision=B.PREC_MIXED, newton_tol=1e-10, krylov_rtol=1e-4, max_halvings=3)
+    probe = B.Cell(flab, 1e-6, params, fopts)
+    i1_fom = probe.i_1c
+    fom_bytes = int(probe.device_bytes)
+    probe.close()
+    srv = B.Server(rom=rom, labels=flab, params=params, fom_opts=fopts, rom_slots=slots, fom_workers=workers,
+                   fom_budget_bytes=workers * fom_bytes)
+
+    def submit(r):
+        kind = B.REQ_ROM if r[0] == "rom" else B.REQ_FOM
+        return srv.submit(kind, r[1], r[2], r[3], r[4], 1.0)
+
+    rng = np.random.default_rng(50)
+    burst = _serve_requests(rng, 2 * slots, i1, i1_fom)
+    t0 = time.perf_counter()
+    left = {submit(r) for r in burst}
+    while left:
+        for t in list(left):
+            if srv.poll(t) is not None:
+                left.discard(t)
+        time.sleep(0.001)
+    cap = len(burst) / (time.perf_counter() - t0)
+    rate = 0.8 * cap
+    rng = np.random.default_rng(51)
+    n_req = args.serve_requests
+    reqs = _serve_requests(rng, n_req, i1, i1_fom)
+    gaps = rng.exponential(1.0 / rate, n_req)
+    t0 = time.perf_counter()
+    t_next = t0
+    pending, done = {}, {}
+    for k, r in enumerate(reqs):
+        t_next += gaps[k]
+        while time.perf_counter() < t_next:
+            for t in list(pending):
+                res = srv.poll(t)
+                if res is not None:
+                    done[t] = (pending.pop(t), res)
+            time.sleep(0.0005)
+        pending[submit(r)] = r[0]
+    t_arrivals = time.perf_counter() - t0
+    while pending:
+        for t in list(pending):
+            res = srv.poll(t)
+            if res is not None:
+                done[t] = (pending.pop(t), res)
+        time.sleep(0.001)
+    total = time.perf_counter() - t0
+    _, peak, _ = srv.debug_cells()
+    srv.close()
+    lat = {"rom": [], "fom": []}
+    bad = 0
+    for kind, res in done.values():
+        lat[kind].append(1000.0 * (res["t_done"] - res["t_submit"]))
+        bad += res["status"] != 0
+    return {"requests": n_req, "rom_fraction": 0.95, "arrival_rate_per_s": rate,
+            "capacity_mixed_burst_per_s": cap, "throughput_per_s": n_req / total,
+            "throughput_over_arrival_rate": (n_req / total) / (n_req / t_arrivals), "wall_s": total,
+            "failed": int(bad), "rom_slots": slots, "fom_workers": workers, "fom_cells_peak": peak,
+            "p50_ms": {k: float(np.percentile(v, 50)) if v else None for k, v in lat.items()},
+            "p99_ms": {k: float(np.percentile(v, 99)) if v else None for k, v in lat.items()},
+            "workload": "Poisson arrivals at 0.8 of the capacity measured on a mixed burst; 95 %% reduced "
+                        "requests of U{100..3000} steps (C-rate in {0.5,1,2,3,5}, i0 scale ~ LogU(0.5,2), "
+                        "plating rate ~ LogU(0.1,10)) on the reduced model of the %s cell; 5 %% full-order "
+                        "validation solves of 60 steps on the %s cell; a sample of %d requests"
+                        % (ROM_CELL, SERVE_FOM_CELL, n_req)}
+
+
 def rom_and_serve(B, params, args, torch):
     """A smaller reduced model of the 16x16x48 cell (the serving model;
     snapshots at three corners of the parameter box over the --rom-steps
-    horizon, POD to 1e-7), a timed batched solve of
-    --rom-instances instances over --rom-steps steps, its cell-potential error
-    against full-order runs of two instances, and a serving run with Poisson
-    arrivals (95 % reduced requests of 20-100 steps, 5 % full-order 10-step
-    validation solves on the same cell) at 0.8 of the server's measured capacity
-    for reduced requests (a burst of twice its slot count)."""
+    horizon, POD to 1e-7), a timed batched solve of --rom-instances instances
+    over --rom-steps steps, its cell-potential error against full-order runs of
+    two instances, and the serving run (serve_run)."""
     labels = workload_labels(ROM_CELL)
     opts = B.default_opts(precision=B.PREC_MIXED, newton_tol=1e-10, krylov_rtol=1e-5, max_halvings=3)
     cell = B.Cell(labels, 1e-6, params, opts)
@@ -396,70 +490,7 @@ def rom_and_serve(B, params, args, torch):
                "instance_steps_per_s": inst_steps / wall, "solves_per_s": args.rom_instances / wall,
                "wall_s": wall, "build_s": build_s, "newton_its_per_instance_step": out["newton_its"] / inst_steps,
                "failed": out["failed"], "V_rel_err_vs_full_order_2_instances": errs}
-    # serving capacity: a burst of reduced requests (U{20..100} steps) submitted at once,
-    # twice the slot count, drained by the server
-    slots = 256
-    srv = B.Server(rom=rom, labels=labels, params=params, fom_opts=opts, rom_slots=slots, fom_workers=4)
-    rng = np.random.default_rng(50)
-    n_sat = 2 * slots
-    blen = rng.integers(20, 101, n_sat)
-    bprm = _rom_params(rng, n_sat, i1)
-    t0 = time.perf_counter()
-    burst = [srv.submit(B.REQ_ROM, bprm[k][0], bprm[k][1], bprm[k][2], int(blen[k]), 1.0) for k in range(n_sat)]
-    left = set(burst)
-    while left:
-        for t in list(left):
-            if srv.poll(t) is not None:
-                left.discard(t)
-        time.sleep(0.0005)
-    cap = n_sat / (time.perf_counter() - t0)
-    # Poisson arrivals at 0.8 of that capacity, 5 % of them full-order validation solves
-    rate = 0.8 * cap
-    rng = np.random.default_rng(51)
-    n_req = args.serve_requests
-    gaps = rng.exponential(1.0 / rate, n_req)
-    kinds = rng.random(n_req) < 0.95
-    lens = rng.integers(20, 101, n_req)
-    sprm = _rom_params(rng, n_req, i1)
-    tickets = []
-    t0 = time.perf_counter()
-    t_next = t0
-    pending = {}
-    done = {}
-    for k in range(n_req):
-        t_next += gaps[k]
-        while time.perf_counter() < t_next:
-            for t in list(pending):
-                r = srv.poll(t)
-                if r is not None:
-                    done[t] = (pending.pop(t), r)
-            time.sleep(0.0005)
-        if kinds[k]:
-            t = srv.submit(B.REQ_ROM, sprm[k][0], sprm[k][1], sprm[k][2], int(lens[k]), 1.0)
-            pending[t] = "rom"
-        else:
-            t = srv.submit(B.REQ_FOM, sprm[k][0], sprm[k][1], sprm[k][2], 10, 1.0)
-            pending[t] = "fom"
-    while pending:
-        for t in list(pending):
-            r = srv.poll(t)
-            if r is not None:
-                done[t] = (pending.pop(t), r)
-        time.sleep(0.0005)
-    total = time.perf_counter() - t0
-    srv.close()
-    lat = {"rom": [], "fom": []}
-    bad = 0
-    for kind, r in done.values():
-        lat[kind].append(1000.0 * (r["t_done"] - r["t_submit"]))
-        bad += r["status"] != 0
-    serve = {"requests": n_req, "rom_fraction": 0.95, "arrival_rate_per_s": rate,
-             "capacity_reduced_burst_per_s": cap, "throughput_per_s": n_req / total, "wall_s": total,
-             "failed": int(bad), "rom_slots": slots, "fom_workers": 4,
-             "p50_ms": {k: float(np.percentile(v, 50)) if v else None for k, v in lat.items()},
-             "p99_ms": {k: float(np.percentile(v, 99)) if v else None for k, v in lat.items()},
-             "workload": "Poisson arrivals; reduced requests of U{20..100} steps with the study's parameter "
-                         "distribution; full-order requests: 10 steps on the %s cell" % ROM_CELL}
+    serve = serve_run(B, params, rom, i1, args)
     rom.close()
     cell.close()
     return rom_res, serve
@@ -487,7 +518,7 @@ def main():
     ap.add_argument("--rom-steps", type=int, default=60)
     ap.add_argument("--rom-paper-steps", type=int, default=3,
                     help="timed steps of the paper-size reduced model (a sample of its 600-step protocol)")
-    ap.add_argument("--serve-requests", type=int, default=1000)
+    ap.add_argument("--serve-requests", type=int, default=400)
     ap.add_argument("--experiment", action="store_true",
                     help="also run the paper's half-cell model-reduction experiment at reduced size "
                          "(paper_1704_04139_gb300.experiment) and add its results under 'experiment'")

@@ -157,9 +157,10 @@ int mb_state_set(mb_cell* cell, const double* u);
 
 /* One implicit Euler step of Eq. (ap4:detailed): Newton-Krylov with the
  * plating active-set passes; dt halved on failure up to max_halvings times.
- * Newton updates are capped at 0.25 in the scaled max-norm of the voxel
- * unknowns (c, phi); the plated-Li inventories are not capped; convergence
- * is tested on every unknown.  Returns MB_ENOCONV when every halving failed
+ * Newton updates are capped at 0.25 in the max-norm of the voxel unknowns
+ * (c, phi) scaled by (c_ref, 1 V) and of the plated-Li inventories relative
+ * to max(n_c, |n|); convergence is tested on every unknown in the scales
+ * (c_ref, 1 V, n_c).  Returns MB_ENOCONV when every halving failed
  * (state unchanged). */
 int mb_step(mb_cell* cell, double dt, double I_app, mb_step_info* info);
 
@@ -309,10 +310,11 @@ int mb_rom_destroy(mb_rom* rom);
  * (host double[B * (n_steps + 1)], instance-major, entry 0 the initial
  * state) receive s_cp and s_ac; a_final (host double[B * n_r]) the final
  * coefficients (may be NULL).  Newton per step and instance: step length
- * min(1, 0.25 / |U_loc delta|_s) over the voxel unknowns (c, phi) of the
- * stencil closure of the points (the plated-Li inventories are not capped),
- * converged at lam |U_loc delta|_s <= 1e-12 over all of them, at most 30
- * iterations;
+ * min(1, 0.25 / m), m the max-norm of U_loc delta on the stencil closure of
+ * the points with the voxel unknowns (c, phi) in their scales and the plated
+ * inventories relative to max(n_c, |n|) of the current reconstruction,
+ * converged at lam |U_loc delta|_s <= 1e-12 (every slot in the fixed scales),
+ * at most 30 iterations;
  * plating active-set passes as mb_step (at most 3).  The state, the
  * interpolated terms and the residual are FP64 (the converged result is the
  * FP64 one); the Newton matrix is formed with FP32 accuracy (three TF32

@@ -422,12 +422,14 @@ class Cell:
         """Newton's method with sparse direct LU (SciPy SuperLU) for the linear
         correction equations (the paper's BEST solver used AMG there, Sec. 2.4).
 
-        Step length: lam = min(1, DELTA_MAX / ||delta_v||_s) where ||.||_s is
-        the max-norm scaled by the unknown scales (c_ref, 1 V, n_c) and delta_v
-        the update of the voxel unknowns (c, phi: the arguments of the
-        exponentials; the plated inventories enter linearly and through the
-        saturating f_pre and are not capped); DELTA_MAX = 0.25.  Stops after
-        the first applied update with lam * ||delta||_s <= tol (all unknowns).
+        Step length: lam = min(1, DELTA_MAX / m) with DELTA_MAX = 0.25 and m
+        the larger of the max-norm of the voxel unknowns' update (c, phi: the
+        arguments of the exponentials) scaled by (c_ref, 1 V) and the largest
+        plated-inventory update relative to max(n_c, |n|) at the current
+        iterate (a thick layer may change by a quarter of itself, a thin one
+        by a quarter of n_c).  Stops after the first applied update with
+        lam * ||delta||_s <= tol, ||.||_s the max-norm of every unknown scaled
+        by (c_ref, 1 V, n_c).
         With a list `record`, every iterate (after each update) is appended
         together with the gate it was computed with."""
         u = u0.copy()
@@ -440,6 +442,9 @@ class Cell:
             if not np.isfinite(dn):
                 return u, it, False
             dv = np.max(np.abs(d[:2 * self.N]) / us[:2 * self.N])
+            if self.F_pl:
+                n_cur = u[2 * self.N:].real
+                dv = max(dv, float(np.max(np.abs(d[2 * self.N:]) / np.maximum(self.nc, np.abs(n_cur)))))
             lam = 1.0 if dv <= DELTA_MAX else DELTA_MAX / dv
             u = u + lam * d
             if record is not None:

@@ -448,14 +448,20 @@ def solve(rom, mu, s_i0, k_pl, dt, n_steps, tol=TOL_NEWTON, maxit=30):
                 r = reduced_residual(rom, a, a_old, dt, mu, s_i0, k_pl, gate)
                 Jr = reduced_jacobian(rom, a, dt, s_i0, k_pl, gate)
                 d = equilibrated_solve(Jr, -r)
-                du = np.abs(rom.Uloc @ d) / rom.us_loc
+                ud = rom.Uloc @ d
+                du = np.abs(ud) / rom.us_loc
                 dn = np.max(du) if len(du) else 0.0
                 if not np.isfinite(dn):
                     break
-                # the step length caps the closure's voxel unknowns (c, phi), as the
-                # full-order Newton does; convergence on all of them
+                # the step length as the full-order Newton takes it: the closure's
+                # voxel unknowns (c, phi) in their scales, its plated inventories
+                # relative to max(n_c, |n|) of the current reconstruction
                 vox = rom.closure < 2 * N
-                dv = np.max(du[vox]) if np.any(vox) else 0.0
+                du_cap = du.copy()
+                if np.any(~vox):
+                    n_cur = (rom.Uloc @ a)[~vox]
+                    du_cap[~vox] = np.abs(ud[~vox]) / np.maximum(cell.nc, np.abs(n_cur))
+                dv = np.max(du_cap) if len(du_cap) else 0.0
                 lam = 1.0 if dv <= DELTA_MAX else DELTA_MAX / dv
                 a = a + lam * d
                 its_total += 1

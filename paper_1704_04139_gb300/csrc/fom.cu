@@ -780,9 +780,11 @@ int launch_gate_residual_unprofiled(mb_cell* c, const double* u, const double* u
 // ------------------------------------------------------------ reductions
 // Deterministic reductions (mb_reduce.cuh).
 __global__ void __launch_bounds__(RED_THREADS)
-k_scaled_max(Dims D, const uint32_t* __restrict__ vc, const double* __restrict__ x, InvScales is,
-             double* partials) {
-    // [0] over every unknown, [1] over the voxel unknowns (c, phi) only
+k_scaled_max(Dims D, const uint32_t* __restrict__ vc, const double* __restrict__ x, InvScales is, double nc,
+             const double* __restrict__ u, double* partials) {
+    // [0] over every unknown; [1] the step-length cap: the voxel unknowns (c, phi)
+    // in their scales and, with u given, each plated inventory relative to
+    // max(n_c, |n_f|) of the state u
     double acc[2] = {0.0, 0.0};
     int64_t n = 2 * D.N + D.F;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
@@ -793,7 +795,13 @@ k_scaled_max(Dims D, const uint32_t* __restrict__ vc, const double* __restrict__
         double a = fabs(x[i]) * s;
         if (!(a == a)) a = 1e300;   // NaN -> huge
         acc[0] = fmax(acc[0], a);
-        if (i < 2 * D.N) acc[1] = fmax(acc[1], a);
+        if (i < 2 * D.N) {
+            acc[1] = fmax(acc[1], a);
+        } else if (u) {
+            double ac = fabs(x[i]) / fmax(nc, fabs(u[i]));
+            if (!(ac == ac)) ac = 1e300;
+            acc[1] = fmax(acc[1], ac);
+        }
     }
     block_reduce_store<2, true>(acc, partials);
 }
@@ -808,15 +816,17 @@ InvScales inv_scales(const mb_cell* c, int which, double dt) {
     return is;
 }
 
-int scaled_maxnorm(mb_cell* c, const double* x, int which, double dt, double* out, double* out_vox) {
+int scaled_maxnorm(mb_cell* c, const double* x, int which, double dt, double* out, double* out_cap,
+                   const double* u_cap) {
     cudaStream_t s = c->stream;
-    k_scaled_max<<<RED_BLOCKS, RED_THREADS, 0, s>>>(c->D, c->vcode, x, inv_scales(c, which, dt), c->red), ::mb::count_launch(c);
+    k_scaled_max<<<RED_BLOCKS, RED_THREADS, 0, s>>>(c->D, c->vcode, x, inv_scales(c, which, dt), c->P.nc, u_cap,
+                                                    c->red), ::mb::count_launch(c);
     k_reduce_final<true><<<2, RED_THREADS, 0, s>>>(c->red, 2, c->red_out), ::mb::count_launch(c);
     MB_CUDA_LAUNCH("scaled_max");
     MB_CUDA(cudaMemcpyAsync(c->h_red, c->red_out, 16, cudaMemcpyDeviceToHost, s));
     MB_CUDA(cudaStreamSynchronize(s));
     *out = c->h_red[0];
-    if (out_vox) *out_vox = c->h_red[1];
+    if (out_cap) *out_cap = c->h_red[1];
     return MB_OK;
 }
 

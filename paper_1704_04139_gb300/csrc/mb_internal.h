@@ -215,8 +215,11 @@ struct InvScales {
 };
 InvScales inv_scales(const mb_cell* c, int which, double dt);
 // scaled max norms: which = 0 unknown scale, 1 residual scale (needs dt)
-// (out_vox, if given: the same norm over the voxel unknowns c and phi only)
-int scaled_maxnorm(mb_cell* c, const double* x, int which, double dt, double* out, double* out_vox = nullptr);
+// (out_cap, if given: the Newton step-length norm: the voxel unknowns c and phi
+// in their scales and, with u_cap given, each plated inventory relative to
+// max(n_c, |n_f|) of the state u_cap)
+int scaled_maxnorm(mb_cell* c, const double* x, int which, double dt, double* out, double* out_cap = nullptr,
+                   const double* u_cap = nullptr);
 int functionals(mb_cell* c, const double* u, mb_step_info* info);
 int count_diff_u8(mb_cell* c, const uint8_t* a, const uint8_t* b, int64_t n, int64_t* out);
 

@@ -84,7 +84,9 @@ struct RomDev {
     float* UlocCf = nullptr;
     float2* UlocCdf = nullptr; // Nr x nloc float-float copy for the reconstruction
     float* usf = nullptr;
-    float* uscf = nullptr;     // nloc: the scales of the step-length cap (voxel slots; +inf for face slots)
+    float* uscf = nullptr;     // nloc: the scales of the step-length cap (voxel slots; -1 marks face slots,
+                               //   capped relative to max(n_c, |n|) of the current reconstruction)
+    float ncf = 0.f;           // n_c
     double* bbnd = nullptr;    // Nr
     double* scp = nullptr;     // Nr
     double* sac = nullptr;     // Nr
@@ -1169,7 +1171,7 @@ k_rom_gmres(RomDev d, const double* __restrict__ prm, const double* __restrict__
 constexpr int UN_K = 128, UN_B = 32, UN_C = 16;
 __global__ void __launch_bounds__(256)
 k_rom_unorm(RomDev d, int B, const double* __restrict__ delta, const int* __restrict__ active,
-            float* __restrict__ dpart) {
+            const double* __restrict__ uloc, float* __restrict__ dpart) {
     __shared__ float Us[UN_C][UN_K];
     __shared__ float Ds[UN_C][UN_B];
     const int k0 = blockIdx.x * UN_K, b0 = blockIdx.y * UN_B;
@@ -1205,17 +1207,21 @@ k_rom_unorm(RomDev d, int B, const double* __restrict__ delta, const int* __rest
         __syncthreads();
     }
     // per instance: max over this thread's 4 slots, then over the warp's 32
-    // threads: over every slot (dpart) and over the voxel slots only (the
-    // step-length cap: dpart + B * gridDim.x)
+    // threads: over every slot in the unknown scales (dpart) and for the
+    // step-length cap (dpart + B * gridDim.x: voxel slots in their scales,
+    // face slots relative to max(n_c, |n|) of the current reconstruction)
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
         float m = 0.f, mc = 0.f;
 #pragma unroll
         for (int s = 0; s < 4; ++s) {
             const int k = k0 + tx + 32 * s;
-            if (k < d.nloc) {
+            const int bq = b0 + ty * 4 + q;
+            if (k < d.nloc && bq < B) {
                 const float a = fabsf(acc[s][q]);
-                const float v = a / d.usf[k], vc = a / d.uscf[k];
+                const float sc = d.uscf[k];
+                const float v = a / d.usf[k];
+                const float vc = sc > 0.f ? a / sc : a / fmaxf(d.ncf, fabsf((float)uloc[(int64_t)bq * d.nloc + k]));
                 m = (v == v) ? fmaxf(m, v) : INFINITY;
                 mc = (vc == vc) ? fmaxf(mc, vc) : INFINITY;
             }
@@ -1656,11 +1662,13 @@ static int rom_build_host(mb_rom* R, const mb_rom_data* dd) {
              upf(d.Alinf, dd->Alin, (size_t)Nr * Nr) && upf(d.UlocRf, UlocR.data(), UlocR.size()) &&
              upf(d.UlocCf, UlocC.data(), UlocC.size()) && upf(d.usf, us.data(), us.size());
     if (ok) {
-        // the step length caps the closure's voxel unknowns only (face slots: scale +inf)
+        // the step-length cap: voxel slots in their scales, face slots (-1)
+        // relative to max(n_c, |n|) of the current reconstruction
         std::vector<double> usc(us);
         for (int64_t k = 0; k < nloc; ++k)
-            if (closure[k] >= 2 * N) usc[k] = INFINITY;
+            if (closure[k] >= 2 * N) usc[k] = -1.0;
         ok = upf(d.uscf, usc.data(), usc.size());
+        d.ncf = (float)c->P.nc;
     }
     // shared memory of the LU kernels beyond the default 48 KB
     if (ok)
@@ -1904,7 +1912,8 @@ static void iter_main_c(mb_rom* R, cudaStream_t s) {
     RomWork& w = R->w;
     const int B = w.B;
     const unsigned nkt = (unsigned)((d.nloc + UN_K - 1) / UN_K);
-    k_rom_unorm<<<dim3(nkt, (unsigned)((B + UN_B - 1) / UN_B)), 256, 0, s>>>(d, B, w.delta, w.active, w.dpart),
+    k_rom_unorm<<<dim3(nkt, (unsigned)((B + UN_B - 1) / UN_B)), 256, 0, s>>>(d, B, w.delta, w.active, w.uloc,
+                                                                             w.dpart),
         count_launch(c);
     k_rom_apply<<<(unsigned)B, 32, 0, s>>>(d, B, (int)nkt, w.a, w.delta, w.dpart, w.active, w.failed, w.its, w.pit,
                                            w.hp, w.dnprev), count_launch(c);

@@ -417,12 +417,14 @@ static int newton(mb_cell* c, double dt, double I_app, bool from_old, int* its_o
         if (rc) return rc;
         *kits += ki;
         // the step length caps the update of the voxel unknowns (c, phi: the
-        // arguments of the exponentials); the plated inventories enter linearly
-        // and through the saturating f_pre, so their update is not capped (a
-        // stripping layer of many critical thicknesses would otherwise crawl);
-        // convergence is tested on every unknown
+        // arguments of the exponentials) in their scales and of each plated
+        // inventory relative to max(n_c, |n|): a stripping layer of many
+        // critical thicknesses may change by a quarter of itself per iteration,
+        // a thin one by a quarter of n_c (so that it does not overshoot into
+        // n < 0, where f_pre switches off); convergence is tested on every
+        // unknown in the fixed scales
         double dn, dv;
-        if ((rc = scaled_maxnorm(c, c->du, 0, dt, &dn, &dv))) return rc;
+        if ((rc = scaled_maxnorm(c, c->du, 0, dt, &dn, &dv, c->u))) return rc;
         if (!(dn < 1e200)) { *its_out = it; return MB_OK; }
         double lam = dv <= DELTA_MAX ? 1.0 : DELTA_MAX / dv;
         if (debug_level() > 0)

@@ -11,8 +11,12 @@ Protocol, as the paper states it:
   charge" plateau);
 * 60 s of constant-current delithiation at current densities mu in
   P = [2.5, 250] A/m^2 (C/10 to 10C in the paper's cell);
-* snapshots from full-order runs at min P, max P and their mean; POD and
-  EI-Greedy to a relative tolerance of 1e-7; the reduced model keeps 97 % of
+* snapshots from full-order runs at min P, max P and their mean; POD to a
+  relative tolerance of 1e-7 of the largest singular value and EI-Greedy to
+  1e-10 of the largest training entry (the stripping currents dominate that
+  entry by ~1e3 over the Butler-Volmer terms, so this is ~1e-7 of those; at
+  1e-7 of the largest entry the reduced potential misses the full-order one by
+  5 % even at a training current); the reduced model keeps 97 % of
   the basis vectors and interpolation points of each space, the validation
   model of the error estimator all of them;
 * the reduced model against the full-order model at 10 random mu in P plus
@@ -88,12 +92,12 @@ def run_study(B, params, dt=1.0, steps=60, n_test=10, n_more=100, seed=62, sizes
     w[2 * N:] = h ** 2
     train = [(P_MIN, 1.0, 1.0), (P_MAX, 1.0, 1.0), (0.5 * (P_MIN + P_MAX), 1.0, 1.0)]
     t0 = time.perf_counter()
-    val = B.Rom.build(cell, train, dt, steps, PAPER_VALIDATION_DIMS, pod_tol=1e-7, ei_tol=1e-7)
+    val = B.Rom.build(cell, train, dt, steps, PAPER_VALIDATION_DIMS, pod_tol=1e-7, ei_tol=1e-10)
     build_val_s = time.perf_counter() - t0
     nc, nn, nphi = val.block_dims()
     d97 = tuple(int(math.ceil(0.97 * x)) for x in (nc, nn, nphi, val.n_bv, val.n_1c))
     t0 = time.perf_counter()
-    red = B.Rom.build(cell, train, dt, steps, d97, pod_tol=1e-7, ei_tol=1e-7)
+    red = B.Rom.build(cell, train, dt, steps, d97, pod_tol=1e-7, ei_tol=1e-10)
     build_red_s = time.perf_counter() - t0
     cell.set_state(u0)
     rng = np.random.default_rng(seed)
