@@ -95,6 +95,10 @@ typedef struct {
                               (the previous time level); 1 (default) the previous pass's converged
                               state.  The solution of a pass depends only on its frozen gates, not on
                               the start. */
+    int    mg_kcycle_reorth; /* 1 (default): the level-1 K-cycle orthogonalises by two classical
+                              Gram-Schmidt passes; 0: one pass */
+    int    krylov_forcing; /* 0 (default): every linear solve to krylov_rtol; 1: Eisenstat-Walker
+                              forcing terms (choice 2, safeguarded) within [krylov_rtol, 0.1] */
     int    mg_tail;        /* 1: the V-cycle on the coarse levels that one wave of the GPU covers
                               (level 2 down) runs as one persistent cooperative launch with grid
                               barriers instead of one launch per sweep (same results); 0 (default):

@@ -40,7 +40,8 @@ class SolverOpts(C.Structure):
                 ("max_passes", C.c_int), ("max_halvings", C.c_int), ("mg_coarse_cells", C.c_int),
                 ("mg_smooth", C.c_int), ("mg_kcycle", C.c_int), ("mg_coarse_pre", C.c_int),
                 ("mg_coarse_post", C.c_int), ("mg_bf16", C.c_int), ("mg_stream", C.c_int),
-                ("pass_start", C.c_int), ("mg_tail", C.c_int)]
+                ("pass_start", C.c_int), ("mg_kcycle_reorth", C.c_int), ("krylov_forcing", C.c_int),
+                ("mg_tail", C.c_int)]
 
 
 class StepInfo(C.Structure):

@@ -119,6 +119,8 @@ struct PcGraph {
     float2* z = nullptr;
     int kcyc = 0;
     int nu = 0;
+    int reorth = 0;
+    int tail = 0;
     cudaGraphExec_t exec = nullptr;
     int64_t nodes = 0;                 // kernels per execution
     std::vector<ProfPair> ev;          // timing events recorded by the graph (prof graphs)
@@ -1892,7 +1894,13 @@ static void kcycle_l1(mb_cell* c) {
         cudaMemcpyAsync(Zj, L.x, sizeof(DF4) * L.cells, cudaMemcpyDeviceToDevice, s);
         lvl_matvec(c, L, Zj, p->kw);
         kdots(c, p->kV, m4, j + 1, p->kw, m4, h1);
-        if (j + 1 <= 8) {
+        if (!c->opt.mg_kcycle_reorth && j + 1 <= 8) {
+            // one classical Gram-Schmidt pass, fused with the norm that follows it
+            cudaMemsetAsync(h2, 0, 8 * (size_t)(j + 1), s);
+            k_kupd_dot<true><<<RED_BLOCKS, RED_THREADS, 0, s>>>(p->kV, m4, j + 1, h1, p->kw, m4, p->kred),
+                ::mb::count_launch(c);
+            k_reduce_final<false><<<1, RED_THREADS, 0, s>>>(p->kred, 1, wn2), ::mb::count_launch(c);
+        } else if (j + 1 <= 8) {
             // CGS2 with each update fused into the products that follow it
             k_kupd_dot<false><<<RED_BLOCKS, RED_THREADS, 0, s>>>(p->kV, m4, j + 1, h1, p->kw, m4, p->kred),
                 ::mb::count_launch(c);
@@ -2082,6 +2090,8 @@ static bool capture_graph(mb_cell* c, const float* r, float2* z, PcGraph& G) {
     G.z = z;
     G.kcyc = p->kcyc;
     G.nu = p->nu_fine;
+    G.reorth = c->opt.mg_kcycle_reorth;
+    G.tail = c->opt.mg_tail;
     if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
         cudaGetLastError();
         return false;
@@ -2120,7 +2130,11 @@ int precond_apply(mb_cell* c, const float* u32, const uint8_t* gate, double dt, 
     int idx = -1;
     for (size_t i = 0; i < p->graphs.size(); ++i) {
         const PcGraph& G = p->graphs[i];
-        if (G.r == r && G.z == z && G.kcyc == p->kcyc && G.nu == p->nu_fine) { idx = (int)i; break; }
+        if (G.r == r && G.z == z && G.kcyc == p->kcyc && G.nu == p->nu_fine && G.reorth == c->opt.mg_kcycle_reorth &&
+            G.tail == c->opt.mg_tail) {
+            idx = (int)i;
+            break;
+        }
     }
     if (idx < 0) {
         PcGraph G;

@@ -364,7 +364,7 @@ static int krylov_create(mb_cell* c, Krylov** out) {
 }
 
 // Solve J delta = -R at the current c->u (FP64 residual in c->r) into c->du.
-static int linear_solve(mb_cell* c, double dt, int* its, double* relres) {
+static int linear_solve(mb_cell* c, double dt, double rtol, int* its, double* relres) {
     int64_t n = c->n;
     cudaStream_t s = c->stream;
     k_convert<double, float><<<nblk(n), 256, 0, s>>>(c->u, c->u32, n), ::mb::count_launch(c);
@@ -380,7 +380,7 @@ static int linear_solve(mb_cell* c, double dt, int* its, double* relres) {
     Krylov* K = c->kd;
     k_scale_rhs<<<nblk(n), 256, 0, s>>>(c->D, c->vcode, c->r, inv_scales(c, 1, dt), c->rowinv, K->b), ::mb::count_launch(c);
     OpCtx o{c->u32, c->gate, dt};
-    rc = fgmres(c, K, o, c->opt.krylov_rtol, c->opt.krylov_maxit, its, relres);
+    rc = fgmres(c, K, o, rtol, c->opt.krylov_maxit, its, relres);
     if (!rc) rc = precond_check(c);
     if (rc) return rc;
     k_unscale<<<nblk(n), 256, 0, s>>>(c->P, c->D, c->vcode, K->x, c->du), ::mb::count_launch(c);
@@ -403,6 +403,7 @@ static int newton(mb_cell* c, double dt, double I_app, bool from_old, int* its_o
     cudaStream_t s = c->stream;
     if (from_old) MB_CUDA(cudaMemcpyAsync(c->u, c->u_old, 8 * n, cudaMemcpyDeviceToDevice, s));
     *ok = false;
+    double rn_prev = 0.0, eta_prev = 0.0;
     for (int it = 1; it <= c->opt.newton_maxit; ++it) {
         int rc = launch_residual_split(c, c->u, c->u_old, c->gate, dt, I_app, c->r, s);
         if (rc) return rc;
@@ -410,9 +411,26 @@ static int newton(mb_cell* c, double dt, double I_app, bool from_old, int* its_o
         if ((rc = scaled_maxnorm(c, c->r, 1, dt, &rn))) return rc;
         *rnorm_out = rn;
         if (!(rn < 1e200)) { *its_out = it; return MB_OK; }
+        // forcing term of the linear solve: fixed krylov_rtol, or (krylov_forcing
+        // = 1) Eisenstat and Walker's choice 2, eta = 0.9 (|R_k| / |R_k-1|)^2
+        // safeguarded by 0.9 eta_prev^2 when that exceeds 0.1, within
+        // [krylov_rtol, 0.1] (0.1 at the first iteration)
+        double eta = c->opt.krylov_rtol;
+        if (c->opt.krylov_forcing) {
+            if (it == 1) {
+                eta = 0.1;
+            } else {
+                eta = 0.9 * (rn / rn_prev) * (rn / rn_prev);
+                const double sg = 0.9 * eta_prev * eta_prev;
+                if (sg > 0.1) eta = fmax(eta, sg);
+            }
+            eta = fmin(0.1, fmax(eta, c->opt.krylov_rtol));
+        }
+        rn_prev = rn;
+        eta_prev = eta;
         int ki = 0;
         double rr = 0;
-        rc = linear_solve(c, dt, &ki, &rr);
+        rc = linear_solve(c, dt, eta, &ki, &rr);
         if (rc == MB_ENOCONV) { *its_out = it; return MB_OK; }
         if (rc) return rc;
         *kits += ki;
@@ -440,7 +458,7 @@ static int newton(mb_cell* c, double dt, double I_app, bool from_old, int* its_o
             MB_CUDA(cudaStreamSynchronize(s));
         }
         // a small update only means convergence if the linear solve made progress
-        if (lam * dn <= c->opt.newton_tol && rr <= 0.5) {
+        if (lam * dn <= c->opt.newton_tol && rr <= fmax(0.5, eta)) {
             *its_out = it;
             *ok = true;
             return MB_OK;
