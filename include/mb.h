@@ -299,6 +299,13 @@ typedef struct {
     double pod_tol, ei_tol;          /* relative cut-offs */
 } mb_rom_build_opts;
 int mb_rom_build(mb_cell* cell, const mb_rom_build_opts* o, mb_rom** out);
+/* The pair of Sec. workflow:MOR's certification step from one snapshot set:
+ * the validation model with the bounds and tolerances of o (*rom_val), and the
+ * reduced model that keeps ceil(frac x) of each of its POD blocks and of each
+ * of its EI bases (*rom; the paper's 97 %: frac = 0.97).  Both are truncations
+ * of the same POD and EI-Greedy, so the validation bases contain the reduced
+ * ones (mb_rom_estimate_batch). */
+int mb_rom_build_pair(mb_cell* cell, const mb_rom_build_opts* o, double frac, mb_rom** rom, mb_rom** rom_val);
 /* Dimensions of a reduced model: N_r and the two numbers of points. */
 int mb_rom_dims(mb_rom* rom, int* n_r, int* n_bv, int* n_1c);
 /* Reduced modes by field: basis columns supported only on the concentration

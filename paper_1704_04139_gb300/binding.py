@@ -139,6 +139,7 @@ def _declare(lib):
     fn("mb_residual_dev_noalloc", C.c_int, [VP, VP, VP, C.c_double, C.c_double, VP, VP])
     fn("mb_rom_create", C.c_int, [VP, C.POINTER(RomData), C.POINTER(VP)])
     fn("mb_rom_destroy", C.c_int, [VP])
+    fn("mb_rom_build_pair", C.c_int, [VP, C.POINTER(RomBuildOpts), C.c_double, C.POINTER(VP), C.POINTER(VP)])
     fn("mb_rom_build", C.c_int, [VP, C.POINTER(RomBuildOpts), C.POINTER(VP)])
     fn("mb_serve_create", C.c_int, [C.POINTER(ServeOpts), C.POINTER(VP)])
     fn("mb_serve_submit", C.c_int, [VP, C.POINTER(Request), C.POINTER(C.c_uint64)])
@@ -423,6 +424,27 @@ class Rom:
         _check(lib().mb_rom_dims(h, C.byref(nr), C.byref(nb), C.byref(n1)))
         self.n_r, self.n_bv, self.n_1c = nr.value, nb.value, n1.value
         return self
+
+    @classmethod
+    def build_pair(cls, cell, params, dt, n_steps, dims, frac=0.97, pod_tol=1e-7, ei_tol=1e-12):
+        """mb_rom_build_pair: (reduced, validation) models from one snapshot set,
+        the reduced one keeping ceil(frac x) of each validation space."""
+        prm = (RomParams * len(params))(*[RomParams(*map(float, p)) for p in params])
+        o = RomBuildOpts(len(params), C.cast(prm, VP), float(dt), int(n_steps), *[int(x) for x in dims],
+                         float(pod_tol), float(ei_tol))
+        hr, hv = VP(), VP()
+        _check(lib().mb_rom_build_pair(cell.h, C.byref(o), float(frac), C.byref(hr), C.byref(hv)))
+        out = []
+        for h in (hr, hv):
+            self = cls.__new__(cls)
+            self.h = h
+            self.cell = cell
+            self._keep = []
+            nr, nb, n1 = C.c_int(), C.c_int(), C.c_int()
+            _check(lib().mb_rom_dims(h, C.byref(nr), C.byref(nb), C.byref(n1)))
+            self.n_r, self.n_bv, self.n_1c = nr.value, nb.value, n1.value
+            out.append(self)
+        return out[0], out[1]
 
     def __init__(self, cell, U, p_bv, p_1c, Ms, Alin, bbnd, Pbv, P1c, s_cp, s_ac, a0):
         f64 = lambda a: np.ascontiguousarray(a, np.float64)

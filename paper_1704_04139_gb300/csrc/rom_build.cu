@@ -486,19 +486,19 @@ static int ei_greedy(mb_cell* c, Dev& dv, int64_t L, int K, double* T, int mmax,
 
 using namespace mb;
 
-extern "C" int mb_rom_build(mb_cell* c, const mb_rom_build_opts* o, mb_rom** out) {
-    if (!c || !o || !out || o->n_params < 1 || !o->params || !(o->dt > 0) || o->n_steps < 1 || o->n_c < 0 ||
-        o->n_n < 0 || o->n_phi < 0 || o->m_bv < 0 || o->m_1c < 0 || o->n_c + o->n_n + o->n_phi < 1) {
-        set_error("mb_rom_build: invalid argument");
-        return MB_EINVAL;
-    }
+static bool build_opts_ok(const mb_rom_build_opts* o) {
+    return o && o->n_params >= 1 && o->params && o->dt > 0 && o->n_steps >= 1 && o->n_c >= 0 && o->n_n >= 0 &&
+           o->n_phi >= 0 && o->m_bv >= 0 && o->m_1c >= 0 && o->n_c + o->n_n + o->n_phi >= 1;
+}
+
+// 1. snapshots: every Newton stage of n_steps steps at each parameter point,
+// from the cell's current state (restored afterwards), with its gates
+static int collect_snapshots(mb_cell* c, const mb_rom_build_opts* o, std::vector<double>& u_init,
+                             std::vector<std::vector<double>>& su, std::vector<std::vector<uint8_t>>& sg) {
     const int64_t N = c->D.N, F = c->D.F, n = c->n;
     cudaStream_t s = c->stream;
-    // --- 1. snapshots from the cell's current state
-    std::vector<double> u_init(n);
+    u_init.resize(n);
     MB_CUDA(cudaMemcpy(u_init.data(), c->u, 8 * n, cudaMemcpyDeviceToHost));
-    std::vector<std::vector<double>> su;
-    std::vector<std::vector<uint8_t>> sg;
     const double s0 = c->s_i0, k0 = c->k_pl;
     int rc = MB_OK;
     {
@@ -528,8 +528,20 @@ extern "C" int mb_rom_build(mb_cell* c, const mb_rom_build_opts* o, mb_rom** out
     c->snap_g = nullptr;
     c->s_i0 = s0;
     c->k_pl = k0;
+    c->has_hist = false;
     MB_CUDA(cudaMemcpy(c->u, u_init.data(), 8 * n, cudaMemcpyHostToDevice));
-    if (rc) return rc;
+    return rc;
+}
+
+// 2.-4. POD, EI-Greedy and projections from the snapshots; dims (may be
+// NULL) receive the sizes taken: modes of c, n, phi, then the two numbers of
+// points
+static int rom_from_snapshots(mb_cell* c, const mb_rom_build_opts* o, const std::vector<double>& u_init,
+                              const std::vector<std::vector<double>>& su, const std::vector<std::vector<uint8_t>>& sg,
+                              mb_rom** out, int* dims) {
+    const int64_t N = c->D.N, F = c->D.F, n = c->n;
+    cudaStream_t s = c->stream;
+    int rc = MB_OK;
     const int K = (int)su.size();
     Dev dv;
     // snapshot blocks, column-major
@@ -686,5 +698,50 @@ extern "C" int mb_rom_build(mb_cell* c, const mb_rom_build_opts* o, mb_rom** out
     }
     mb_rom_data d{Nr, Mb, M1, Ur.data(), Pbv.data(), P1c.data(), Ms.data(), Al.data(), bb.data(), Pb.data(),
                   P1.data(), scp.data(), sac.data(), a0.data()};
+    if (dims) {
+        dims[0] = rcn; dims[1] = rnn; dims[2] = rpn; dims[3] = Mb; dims[4] = M1;
+    }
     return mb_rom_create(c, &d, out);
+}
+
+extern "C" int mb_rom_build(mb_cell* c, const mb_rom_build_opts* o, mb_rom** out) {
+    if (!c || !out || !build_opts_ok(o)) {
+        set_error("mb_rom_build: invalid argument");
+        return MB_EINVAL;
+    }
+    std::vector<double> u_init;
+    std::vector<std::vector<double>> su;
+    std::vector<std::vector<uint8_t>> sg;
+    int rc = collect_snapshots(c, o, u_init, su, sg);
+    if (rc) return rc;
+    return rom_from_snapshots(c, o, u_init, su, sg, out, nullptr);
+}
+
+extern "C" int mb_rom_build_pair(mb_cell* c, const mb_rom_build_opts* o, double frac, mb_rom** rom,
+                                 mb_rom** rom_val) {
+    if (!c || !rom || !rom_val || !build_opts_ok(o) || !(frac > 0.0 && frac <= 1.0)) {
+        set_error("mb_rom_build_pair: invalid argument");
+        return MB_EINVAL;
+    }
+    std::vector<double> u_init;
+    std::vector<std::vector<double>> su;
+    std::vector<std::vector<uint8_t>> sg;
+    int rc = collect_snapshots(c, o, u_init, su, sg);
+    if (rc) return rc;
+    int dims[5];
+    if ((rc = rom_from_snapshots(c, o, u_init, su, sg, rom_val, dims))) return rc;
+    // the reduced model: ceil(frac x) of the validation model's modes per block and points per basis
+    mb_rom_build_opts o2 = *o;
+    auto part = [&](int x) { return (int)ceil(frac * (double)x - 1e-9); };
+    o2.n_c = part(dims[0]);
+    o2.n_n = part(dims[1]);
+    o2.n_phi = part(dims[2]);
+    o2.m_bv = part(dims[3]);
+    o2.m_1c = part(dims[4]);
+    if ((rc = rom_from_snapshots(c, &o2, u_init, su, sg, rom, nullptr))) {
+        mb_rom_destroy(*rom_val);
+        *rom_val = nullptr;
+        return rc;
+    }
+    return MB_OK;
 }

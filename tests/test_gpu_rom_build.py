@@ -75,3 +75,36 @@ def test_truncated_rom_near_full_order(params):
     assert np.max(np.abs(out["V"][0] - V_ref)) <= 1e-3 * np.max(np.abs(V_ref))
     rom.close()
     gc.close()
+
+
+@pytest.mark.gpu
+def test_build_pair_is_nested(params):
+    """mb_rom_build_pair: the reduced model keeps ceil(0.97 x) of each of the
+    validation model's POD blocks and EI bases, from the same snapshots, so its
+    basis is the validation basis's leading columns of each block (the nested
+    pair the error estimate assumes); the estimate then has no remainder term
+    and is small where the two models agree."""
+    import math
+    B = _gpu()
+    lab = LAB()
+    oc = OCell(lab, 1e-6, params)
+    gc = B.Cell(lab, 1e-6, params)
+    gc.set_state(_seeded(oc))
+    i1 = oc.i_1c
+    snap = [(-2 * i1, 1.0, 1.0), (-5 * i1, 0.7, 3.0)]
+    red, val = B.Rom.build_pair(gc, snap, 1.0, 5, (40, 40, 40, 80, 80), frac=0.97, pod_tol=1e-9)
+    bv, br = val.block_dims(), red.block_dims()
+    assert br == tuple(int(math.ceil(0.97 * x - 1e-9)) for x in bv)
+    assert red.n_bv == int(math.ceil(0.97 * val.n_bv - 1e-9)) and red.n_1c == int(math.ceil(0.97 * val.n_1c - 1e-9))
+    n = gc.n
+    Ur, Uv = red.basis(n), val.basis(n)
+    offs_r, offs_v = np.cumsum((0,) + br), np.cumsum((0,) + bv)
+    for k in range(3):
+        a = Ur[:, offs_r[k]:offs_r[k + 1]]
+        b = Uv[:, offs_v[k]:offs_v[k] + br[k]]
+        assert np.max(np.abs(a - b)) <= 1e-12 * max(np.max(np.abs(b)), 1e-300), k
+    out = red.estimate(val, [(-3 * i1, 1.1, 0.7)], 3, 1.0)
+    assert out["ok"] and np.all(np.isfinite(out["est"]))
+    red.close()
+    val.close()
+    gc.close()
