@@ -278,6 +278,8 @@ def rom_paper_dims(B, params, args, torch, estimate=True):
     else:
         r97, rom = None, B.Rom.build(cell, snap, 1.0, 60, ROM_DIMS_PAPER, pod_tol=1e-9)
     build_s = time.perf_counter() - t0
+    if args.rom_gemm >= 0:
+        rom.debug_tensor(args.rom_gemm)
     rng = np.random.default_rng(43)
     prm = _rom_params(rng, args.rom_instances, i1)
     steps = args.rom_paper_steps
@@ -353,6 +355,7 @@ def _rom_params(rng, n, i1):
 
 
 SERVE_FOM_CELL = "cell32x32x96"
+V_CUTOFF = 4.2   # charge protocols end at the 4.2 V limit (the cfg2 protocol's cutoff)
 
 
 def _serve_requests(rng, n, i1, i1_fom):
@@ -390,7 +393,7 @@ def serve_run(B, params, rom, i1, args, slots=256, workers=4):
 
     def submit(r):
         kind = B.REQ_ROM if r[0] == "rom" else B.REQ_FOM
-        return srv.submit(kind, r[1], r[2], r[3], r[4], 1.0)
+        return srv.submit(kind, r[1], r[2], r[3], r[4], 1.0, v_cutoff=V_CUTOFF)
 
     rng = np.random.default_rng(50)
     burst = _serve_requests(rng, 2 * slots, i1, i1_fom)
@@ -430,14 +433,16 @@ def serve_run(B, params, rom, i1, args, slots=256, workers=4):
     _, peak, _ = srv.debug_cells()
     srv.close()
     lat = {"rom": [], "fom": []}
-    bad = 0
+    bad = cut = 0
     for kind, res in done.values():
         lat[kind].append(1000.0 * (res["t_done"] - res["t_submit"]))
-        bad += res["status"] != 0
+        bad += res["status"] not in (B.MB_OK, B.MB_ECUTOFF)
+        cut += res["status"] == B.MB_ECUTOFF
     return {"requests": n_req, "rom_fraction": 0.95, "arrival_rate_per_s": rate,
             "capacity_mixed_burst_per_s": cap, "throughput_per_s": n_req / total,
             "throughput_over_arrival_rate": (n_req / total) / (n_req / t_arrivals), "wall_s": total,
-            "failed": int(bad), "rom_slots": slots, "fom_workers": workers, "fom_cells_peak": peak,
+            "failed": int(bad), "ended_at_cutoff": int(cut), "v_cutoff": V_CUTOFF, "rom_slots": slots,
+            "fom_workers": workers, "fom_cells_peak": peak,
             "p50_ms": {k: float(np.percentile(v, 50)) if v else None for k, v in lat.items()},
             "p99_ms": {k: float(np.percentile(v, 99)) if v else None for k, v in lat.items()},
             "workload": "Poisson arrivals at 0.8 of the capacity measured on a mixed burst; 95 %% reduced "
@@ -525,6 +530,9 @@ def main():
     ap.add_argument("--experiment", action="store_true",
                     help="also run the paper's half-cell model-reduction experiment at reduced size "
                          "(paper_1704_04139_gb300.experiment) and add its results under 'experiment'")
+    ap.add_argument("--rom-gemm", type=int, default=-1, choices=[-1, 0, 1, 2],
+                    help="Newton-matrix GEMM of the paper-size reduced model: 2 tcgen05, 1 mma.sync, 0 FP32 FMA "
+                         "(-1: the library's choice)")
     ap.add_argument("--rom-only", action="store_true",
                     help="run only the paper-size reduced model (build, timed batch, error check) and print its "
                          "JSON object: the command the reduced-model launch lists are taken with")

@@ -405,10 +405,13 @@ typedef struct {
     mb_rom_params prm;               /* current density, exchange-current scale, plating rate scale */
     int n_steps;                     /* protocol length */
     double dt;                       /* step (s) */
+    double v_cutoff;                 /* > 0: the protocol ends after the first step whose cell potential
+                                        reaches v_cutoff (status MB_ECUTOFF, n_steps the steps done) */
 } mb_request;
 
 typedef struct {
-    int status;                      /* MB_OK, MB_ENOCONV or another error of the request */
+    int status;                      /* MB_OK, MB_ECUTOFF (ended at the voltage limit), MB_ENOCONV or
+                                        another error of the request */
     int n_steps;                     /* steps done */
     double t_submit, t_start, t_done;/* server clock (s since mb_serve_create) */
     double* V;                       /* caller-provided, n_steps + 1 cell potentials (may be NULL) */

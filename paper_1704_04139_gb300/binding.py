@@ -107,7 +107,8 @@ class Result(C.Structure):
 
 
 class Request(C.Structure):
-    _fields_ = [("kind", C.c_int), ("prm", RomParams), ("n_steps", C.c_int), ("dt", C.c_double)]
+    _fields_ = [("kind", C.c_int), ("prm", RomParams), ("n_steps", C.c_int), ("dt", C.c_double),
+                ("v_cutoff", C.c_double)]
 
 
 class RomInfo(C.Structure):
@@ -575,8 +576,9 @@ class Server:
         self.h = hnd
         self._n = {}
 
-    def submit(self, kind, I_app, s_i0, k_pl, n_steps, dt):
-        r = Request(int(kind), RomParams(float(I_app), float(s_i0), float(k_pl)), int(n_steps), float(dt))
+    def submit(self, kind, I_app, s_i0, k_pl, n_steps, dt, v_cutoff=0.0):
+        r = Request(int(kind), RomParams(float(I_app), float(s_i0), float(k_pl)), int(n_steps), float(dt),
+                    float(v_cutoff))
         t = C.c_uint64()
         _check(lib().mb_serve_submit(self.h, C.byref(r), C.byref(t)))
         self._n[t.value] = int(n_steps)
@@ -593,7 +595,8 @@ class Server:
             return None
         _check(rc)
         del self._n[ticket]
-        return dict(status=res.status, V=V, s_ac=S, t_submit=res.t_submit, t_start=res.t_start, t_done=res.t_done)
+        return dict(status=res.status, n_steps=res.n_steps, V=V, s_ac=S, t_submit=res.t_submit,
+                    t_start=res.t_start, t_done=res.t_done)
 
     def debug_cells(self):
         """(alive, peak, cell_bytes) of the server's full-order cells."""

@@ -126,6 +126,7 @@ void rom_loop(mb_server* S) {
                 q->V.push_back(hV[b]);
                 q->S.push_back(hS[b]);
                 if ((int)q->V.size() == q->r.n_steps + 1) finish(S, q, MB_OK);
+                else if (q->r.v_cutoff > 0.0 && hV[b] >= q->r.v_cutoff) finish(S, q, MB_ECUTOFF);
             }
             if (q->done) {
                 mb::rom_slot_clear(R, b);
@@ -217,6 +218,10 @@ void fom_loop(mb_server* S) {
             if (!rc) {
                 q->V.push_back(info.V_cell);
                 q->S.push_back(info.mean_c_solid);
+                if (q->r.v_cutoff > 0.0 && info.V_cell >= q->r.v_cutoff && k + 1 < q->r.n_steps) {
+                    rc = MB_ECUTOFF;
+                    break;
+                }
             }
         }
         {

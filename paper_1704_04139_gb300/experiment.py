@@ -40,7 +40,10 @@ import time
 import numpy as np
 
 P_MIN, P_MAX = 2.5, 250.0                    # A/m^2, the paper's parameter domain
-PAPER_VALIDATION_DIMS = (183, 40, 69, 952, 1027)   # upper bounds (c, plated Li, phi, BV, 1/c points)
+PAPER_VALIDATION_DIMS = (183, 40, 69, 952, 1027)   # the paper's validation model (c, plated Li, phi, BV, 1/c)
+# bounds of the reduced-size experiment's validation model: the paper's mode counts, at most 400 points per
+# interpolated operator (each EI-Greedy step is a pass over the whole training matrix)
+STUDY_DIMS = (183, 40, 69, 400, 400)
 
 
 def half_cell_inputs(params, ny=32, nz=32, n_anode=48, n_sep=12, n_foil=2, porosity=0.35,
@@ -92,7 +95,7 @@ def run_study(B, params, dt=1.0, steps=60, n_test=10, n_more=100, seed=62, sizes
     w[2 * N:] = h ** 2
     train = [(P_MIN, 1.0, 1.0), (P_MAX, 1.0, 1.0), (0.5 * (P_MIN + P_MAX), 1.0, 1.0)]
     t0 = time.perf_counter()
-    red, val = B.Rom.build_pair(cell, train, dt, steps, PAPER_VALIDATION_DIMS, frac=0.97, pod_tol=1e-7,
+    red, val = B.Rom.build_pair(cell, train, dt, steps, STUDY_DIMS, frac=0.97, pod_tol=1e-7,
                                 ei_tol=1e-10)
     build_s = time.perf_counter() - t0
     nc, nn, nphi = val.block_dims()
