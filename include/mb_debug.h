@@ -80,6 +80,13 @@ int mb_debug_residual_split(mb_cell* cell, const double* u, const double* u_old,
  * first cell exists). */
 int mb_debug_serve_cells(mb_server* srv, int* alive, int* peak, int64_t* cell_bytes);
 
+/* The offline build's symmetric eigensolver (host code, no device needed):
+ * A = V diag(w) V^T for a symmetric n x n matrix A (host, row-major, read
+ * only), w (host double[n], unordered) and V (host double[n*n], row-major,
+ * column j the unit eigenvector of w[j]).  MB_EINVAL for n < 1, a null
+ * pointer, or when the QR iteration does not converge. */
+int mb_debug_symeig(int n, const double* A, double* w, double* V);
+
 #ifdef __cplusplus
 }
 #endif

@@ -177,6 +177,7 @@ def _declare(lib):
     fn("mb_debug_rom_refine", C.c_int, [VP, C.c_int])
     fn("mb_debug_rom_lu", C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, VP, VP, VP])
     fn("mb_debug_residual_split", C.c_int, [VP, VP, VP, VP, C.c_double, C.c_double, VP])
+    fn("mb_debug_symeig", C.c_int, [C.c_int, VP, VP, VP])
     return lib
 
 
@@ -630,6 +631,17 @@ def debug_rom_jac(P, GU, Ms, Alin, dt_inv, tc=True):
     J = np.empty((B, Nr, Nr), dtype=np.float32)
     _check(lib().mb_debug_rom_jac(Nr, M, B, _ptr(P), _ptr(gu), _ptr(ms), _ptr(al), _ptr(dti), int(tc), _ptr(J)))
     return J
+
+
+def debug_symeig(A):
+    """The offline build's symmetric eigensolver on a host matrix: (w, V)
+    with A = V diag(w) V^T, eigenvalues unordered."""
+    A = np.ascontiguousarray(A, dtype=np.float64)
+    n = A.shape[0]
+    w = np.zeros(n)
+    V = np.zeros((n, n))
+    _check(lib().mb_debug_symeig(n, _ptr(A), _ptr(w), _ptr(V)))
+    return w, V
 
 
 def debug_rom_lu(J, r, fp64=True, in_place=False):

@@ -63,3 +63,47 @@ def test_create_rejects_bad_arguments_without_gpu(libpath):
                                       ctypes.byref(p), None, ctypes.byref(h))
     assert rc == binding.MB_EINVAL
     assert b"labels" in binding.lib().mb_last_error()
+
+
+@pytest.mark.parametrize("kind", ["random", "repeated", "gram", "diagonal", "tiny"])
+def test_host_eigensolver(libpath, kind):
+    """The offline build's symmetric eigensolver (host code) against the
+    definition A V = V diag(w), V^T V = I, and against LAPACK's eigenvalues
+    (numpy.linalg.eigvalsh), to a few ulps of ||A||: random matrices, a
+    spectrum with repeated eigenvalues, a rank-deficient Gram matrix whose
+    singular values span 12 decades (the POD's input), diagonal input (no
+    reflector, no rotation) and n = 1, 2."""
+    import numpy as np
+    from paper_1704_04139_gb300 import binding
+    rng = np.random.default_rng(5)
+    cases = []
+    if kind == "random":
+        for n in (3, 17, 96):
+            X = rng.standard_normal((n, n))
+            cases.append(X + X.T)
+    elif kind == "repeated":
+        Q, _ = np.linalg.qr(rng.standard_normal((40, 40)))
+        cases.append((Q * np.repeat([3.0, -1.0, 0.0, 2.0], 10)) @ Q.T)
+    elif kind == "gram":
+        S = rng.standard_normal((600, 30)) @ rng.standard_normal((30, 120)) * np.logspace(0, -12, 120)
+        cases.append(S.T @ S)
+    elif kind == "diagonal":
+        cases.append(np.diag(rng.standard_normal(12)))
+    else:
+        cases += [np.array([[2.5]]), np.array([[1.0, 2.0], [2.0, -1.0]])]
+    for A in cases:
+        n = A.shape[0]
+        w, V = binding.debug_symeig(A)
+        scale = np.max(np.abs(A))
+        assert np.max(np.abs(A @ V - V * w)) <= 1e-13 * n * scale
+        assert np.max(np.abs(V.T @ V - np.eye(n))) <= 1e-13 * n
+        assert np.max(np.abs(np.sort(w) - np.linalg.eigvalsh(A))) <= 1e-14 * n * scale
+
+
+def test_host_eigensolver_rejects_bad_arguments(libpath):
+    import numpy as np
+    from paper_1704_04139_gb300 import binding
+    w = np.zeros(1)
+    rc = binding.lib().mb_debug_symeig(0, w.ctypes.data_as(ctypes.c_void_p), w.ctypes.data_as(ctypes.c_void_p),
+                                       w.ctypes.data_as(ctypes.c_void_p))
+    assert rc == binding.MB_EINVAL
