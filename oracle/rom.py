@@ -53,9 +53,10 @@ the reduced system): from the previous time step's coefficients, with the
 full-order rule on the reconstructed update restricted to the stencil
 closure of the EI points (the only values the interpolated nonlinearities
 see): step length min(1, 0.25 / ||U_loc delta||_s) in the max-norm scaled by
-the unknown scales (c_ref, 1 V, n_c), stop after the first update with
-lam ||U_loc delta||_s <= tol.  The reduced linear systems are solved by LU
-after row and column equilibration.
+the voxel unknowns' scales (c_ref, 1 V) and, for plated inventories, by
+max(n_c, |n|) of the current reconstruction; stop after the first update with
+lam ||U_loc delta||_s <= tol in the same scaled norm.  The reduced linear
+systems are solved by LU after row and column equilibration.
 
 7. The hierarchical a-posteriori error estimate (Eq. ap4:estimate): the
    distance of the reduced model's reconstruction from a larger validation
@@ -455,7 +456,11 @@ def solve(rom, mu, s_i0, k_pl, dt, n_steps, tol=TOL_NEWTON, maxit=30):
                     break
                 # the step length as the full-order Newton takes it: the closure's
                 # voxel unknowns (c, phi) in their scales, its plated inventories
-                # relative to max(n_c, |n|) of the current reconstruction
+                # relative to max(n_c, |n|) of the current reconstruction.  The
+                # reduced iteration also stops in these scales: a plated layer of
+                # ~1e3 n_c (Sec. workflow:degradation_modeling) strips at currents
+                # whose exp sensitivity turns the rounding of the reconstruction
+                # (~1e-16 of phi in FP64) into updates above 1e-12 n_c
                 vox = rom.closure < 2 * N
                 du_cap = du.copy()
                 if np.any(~vox):
@@ -465,7 +470,7 @@ def solve(rom, mu, s_i0, k_pl, dt, n_steps, tol=TOL_NEWTON, maxit=30):
                 lam = 1.0 if dv <= DELTA_MAX else DELTA_MAX / dv
                 a = a + lam * d
                 its_total += 1
-                if lam * dn <= tol:
+                if lam * dv <= tol:
                     ok = True
                     break
             if not ok:

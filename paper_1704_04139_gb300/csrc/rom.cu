@@ -14,11 +14,14 @@
 //   gather u_loc = U_loc a; evaluate f and its sparse derivative rows G;
 //   GU = G U_loc; J = Ms/dt + Alin + P GU; r as above; solve J delta = -r by
 //   LU with partial pivoting after row/column equilibration; step length
-//   min(1, 0.25 / |U_loc delta|_s), converged at lam |U_loc delta|_s <= 1e-12.
+//   min(1, 0.25 / |U_loc delta|_s), converged at lam |U_loc delta|_s <= 1e-12,
+//   |.|_s the max-norm with voxel slots in their scales and plated
+//   inventories relative to max(n_c, |n|).
 // Plating gates: the full-order rule on the reconstruction, with the
 // active-set passes of the full-order step.
-// Precision: the state a, the reconstruction, the interpolated terms f and
-// the residual are FP64, so the converged solution is the FP64 one; the
+// Precision: the state a, the interpolated terms f and the residual are
+// FP64 and the reconstruction float-float, so the converged solution is the
+// FP64 one up to ~2^-44 of the reconstruction; the
 // Newton matrix (GU, the contraction P GU as one GEMM over all instances on
 // the tensor cores with FP32 accuracy, its LU) and the step-length norm are
 // FP32 (an inexact Newton iteration: GB300's FP64 rate is a small fraction of
@@ -1260,15 +1263,18 @@ k_rom_apply(RomDev d, int B, int nkt, double* __restrict__ a, const double* __re
         if (lane == 0) { failed[b] = 1; active[b] = 0; }
         return;
     }
-    // the step length caps the voxel unknowns; convergence on all of them
+    // step length and convergence in the same scaled max-norm: voxel slots in
+    // their scales, plated inventories relative to max(n_c, |n|) (in units of
+    // n_c alone, the rounding of a thick stripping layer's reconstruction,
+    // amplified by the exponential kinetics, stays above the tolerance)
     const double lam = dv <= ROM_DELTA_MAX ? 1.0 : ROM_DELTA_MAX / dv;
     for (int j = lane; j < d.Nr; j += 32) a[(int64_t)b * d.Nr + j] += lam * delta[(int64_t)b * d.Nr + j];
     if (lane == 0) {
         its[b] += 1;
-        if (lam * dn <= ROM_TOL) active[b] = 0;
+        if (lam * dv <= ROM_TOL) active[b] = 0;
         const int k = ++pit[b];
-        if (k >= ROM_HP_AFTER || (k >= 3 && lam == 1.0 && m > 0.9f * dnprev[b])) hp[b] = 1;
-        dnprev[b] = m;
+        if (k >= ROM_HP_AFTER || (k >= 3 && lam == 1.0 && mc > 0.9f * dnprev[b])) hp[b] = 1;
+        dnprev[b] = mc;
     }
 }
 
