@@ -63,8 +63,8 @@ def fom_opts(B, prec, args):
     return B.default_opts(precision=prec, newton_tol=1e-10, krylov_rtol=1e-4 if prec else 1e-6,
                           newton_maxit=20, krylov_maxit=300, max_halvings=3,
                           mg_bf16=0 if args.fp32_coarse else 1, mg_stream=args.mg_stream,
-                          mg_tail=1 if args.mg_tail else 0, krylov_forcing=1 if args.ew else 0,
-                          mg_kcycle_reorth=0 if args.kcycle_cgs1 else 1)
+                          mg_tail=1 if args.mg_tail else 0, krylov_forcing=0 if args.no_ew else 1,
+                          mg_kcycle_reorth=1 if args.kcycle_cgs2 else 0)
 
 
 def step_record(infos):
@@ -513,10 +513,10 @@ def main():
                     help="smoother and coarse-level products from FP32 operators instead of their BF16 copies")
     ap.add_argument("--mg-stream", type=int, default=0, choices=[0, 1, 2],
                     help="operator fetch of the BF16 coarse sweeps: 0 plain, 1 L2 prefetch, 2 staged in shared memory")
-    ap.add_argument("--kcycle-cgs1", action="store_true",
-                    help="one Gram-Schmidt pass in the level-1 K-cycle instead of two (mg_kcycle_reorth = 0)")
-    ap.add_argument("--ew", action="store_true",
-                    help="Eisenstat-Walker forcing terms for the linear solves (krylov_forcing = 1)")
+    ap.add_argument("--kcycle-cgs2", action="store_true",
+                    help="two Gram-Schmidt passes in the level-1 K-cycle instead of one (mg_kcycle_reorth = 1)")
+    ap.add_argument("--no-ew", action="store_true",
+                    help="every linear solve to krylov_rtol instead of Eisenstat-Walker forcing (krylov_forcing = 0)")
     ap.add_argument("--mg-tail", action="store_true",
                     help="coarse V-cycle levels in one persistent cooperative launch instead of per-level launches")
     ap.add_argument("--no-fp64-arm", action="store_true",
@@ -681,8 +681,8 @@ def main():
                           "device_bytes": int(cell.device_bytes),
                           "dt_s": dt, "crate": CRATE[args.workload], "precision": args.precision,
                           "coarse_operators": "fp32" if args.fp32_coarse else "bf16", "mg_stream": args.mg_stream,
-                          "mg_tail": 1 if args.mg_tail else 0, "krylov_forcing": 1 if args.ew else 0,
-                          "mg_kcycle_reorth": 0 if args.kcycle_cgs1 else 1,
+                          "mg_tail": 1 if args.mg_tail else 0, "krylov_forcing": 0 if args.no_ew else 1,
+                          "mg_kcycle_reorth": 1 if args.kcycle_cgs2 else 0,
                           "l2": "working set > 129 MB L2, no flush", "parallelism": "replicas" if ws > 1 else "1 GPU"},
                "clocks": clk, "e2e": e2e, "gpu_launches": int(launches), "roofline": roof,
                "cpu_baseline": cpu,
