@@ -285,9 +285,12 @@ def rom_paper_dims(B, params, args, torch, estimate=True):
     steps = args.rom_paper_steps
     rom.solve(prm[:8], 1, 1.0)
     torch.cuda.synchronize()
+    if args.rom_host_loop:
+        rom.debug_graph(False)
     t0 = time.perf_counter()
     out = rom.solve(prm, steps, 1.0)
     wall = time.perf_counter() - t0
+    tune = rom.gemm_tuning()
     inst_steps = args.rom_instances * steps
     errs = []
     for b in range(2):
@@ -310,6 +313,10 @@ def rom_paper_dims(B, params, args, torch, estimate=True):
            "build_s": build_s, "build_note": "validation and 97 % models from one snapshot set" if estimate else None,
            "newton_its_per_instance_step": out["newton_its"] / inst_steps,
            "failed": out["failed"], "V_rel_err_vs_full_order_2_instances": errs,
+           "gemm": {"variant": ["f32 fma", "mma.sync 3xtf32", "tcgen05 3xtf32"][tune[0]],
+                    "autotune_ms_per_launch": {"f32 fma": tune[1][0], "mma.sync 3xtf32": tune[1][1],
+                                               "tcgen05 3xtf32": tune[1][2]} if args.rom_gemm < 0 else None},
+           "step_mode": "host loop" if args.rom_host_loop else "one CUDA graph per time step",
            "error_estimate": est}
     rom.close()
     cell.close()
@@ -523,6 +530,9 @@ def main():
                     help="skip the FP64 run of the same steps (and the mixed-vs-FP64 errors)")
     ap.add_argument("--no-rom", action="store_true", help="skip the reduced-model and serving measurements")
     ap.add_argument("--rom-instances", type=int, default=1024)
+    ap.add_argument("--rom-host-loop", action="store_true",
+                    help="reduced steps driven from the host instead of one CUDA graph per step (same results; "
+                         "every kernel a separate launch, for a profiler's launch list)")
     ap.add_argument("--rom-steps", type=int, default=60)
     ap.add_argument("--rom-paper-steps", type=int, default=3,
                     help="timed steps of the paper-size reduced model (a sample of its 600-step protocol)")

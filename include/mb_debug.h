@@ -64,9 +64,14 @@ int mb_debug_rom_refine(mb_rom* rom, int on);
  * the host (0).  Both give the same results. */
 int mb_debug_rom_graph(mb_rom* rom, int on);
 /* The online solve's Newton-matrix GEMM: 2 on tcgen05 with the accumulator in
- * tensor memory (models with N_r <= 256), 1 (the default) mma.sync tensor-core
- * kernel, 0 FP32 FMA; all three with FP32 accuracy (3xTF32 on the tensor cores). */
+ * tensor memory (models with N_r <= 256), 1 mma.sync tensor-core kernel, 0
+ * FP32 FMA; all three with FP32 accuracy (3xTF32 on the tensor cores).  By
+ * default the first batch of each (N_r, M, B) times the variants the model
+ * admits and keeps the fastest; this call fixes the variant instead. */
 int mb_debug_rom_tensor(mb_rom* rom, int on);
+/* The variant in use (as above) and the last autotuning's time per variant
+ * in ms per launch over the whole batch (ms[3]; -1 where not timed). */
+int mb_debug_rom_gemm_tuning(mb_rom* rom, int* choice, float* ms);
 
 /* The solver's own Newton residual (interface currents evaluated once per
  * face, then the voxel rows) at u, u_old with gates gate (uint8[F]); the

@@ -174,6 +174,7 @@ def _declare(lib):
     fn("mb_debug_rom_jac", C.c_int, [C.c_int, C.c_int, C.c_int, VP, VP, VP, VP, VP, C.c_int, VP])
     fn("mb_debug_rom_graph", C.c_int, [VP, C.c_int])
     fn("mb_debug_rom_tensor", C.c_int, [VP, C.c_int])
+    fn("mb_debug_rom_gemm_tuning", C.c_int, [VP, C.POINTER(C.c_int), C.POINTER(C.c_float)])
     fn("mb_debug_rom_refine", C.c_int, [VP, C.c_int])
     fn("mb_debug_rom_lu", C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, VP, VP, VP])
     fn("mb_debug_residual_split", C.c_int, [VP, VP, VP, VP, C.c_double, C.c_double, VP])
@@ -532,8 +533,16 @@ class Rom:
         _check(lib().mb_debug_rom_graph(self.h, int(bool(on))))
 
     def debug_tensor(self, on):
-        """Newton-matrix GEMM on the tensor cores (3xTF32, the default) or FP32 FMA."""
+        """Fix the Newton-matrix GEMM variant: 2 tcgen05, 1 mma.sync (both 3xTF32), 0 FP32 FMA
+        (default: autotuned per batch shape)."""
         _check(lib().mb_debug_rom_tensor(self.h, int(on)))
+
+    def gemm_tuning(self):
+        """(variant in use, ms per launch of variants 0, 1, 2 at the last autotuning; -1 = not timed)."""
+        ch = C.c_int()
+        ms = (C.c_float * 3)()
+        _check(lib().mb_debug_rom_gemm_tuning(self.h, C.byref(ch), ms))
+        return ch.value, [float(x) for x in ms]
 
     def close(self):
         if getattr(self, "h", None):

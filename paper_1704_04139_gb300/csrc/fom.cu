@@ -310,9 +310,10 @@ k_residual(ParT<T> P, Dims D, const uint32_t* __restrict__ vc, const T* __restri
 // evaluates the Butler-Volmer and plating current densities of every
 // interface face once (FP64; the transcendental part of the residual), then
 // k_residual_split assembles every voxel's rows from them and the bulk and
-// conduction fluxes.  Same arithmetic per term as k_residual, which
-// evaluates each interface current twice (once from each side); the C-ABI
-// residual entry points use that single-kernel form.
+// conduction fluxes.  Same arithmetic per term as k_residual (which
+// evaluates each interface current twice, once from each side; the C-ABI
+// residual entry points use that single-kernel form) except the migration
+// flux's 1/(c_v + c_w), taken by rcp_nr (~1 ulp) instead of a division.
 __global__ void __launch_bounds__(256)
 k_iface_current(DevParams P, Dims D, const uint32_t* __restrict__ vc, const int32_t* __restrict__ if_s,
                 const int32_t* __restrict__ if_e, const double* __restrict__ u, const uint8_t* __restrict__ gate,
@@ -337,6 +338,16 @@ __global__ void __launch_bounds__(256)
 k_residual_split(DevParams P, Dims D, const uint32_t* __restrict__ vc, const double* __restrict__ u,
                  const double* __restrict__ uold, const double* __restrict__ icur, double dt_inv, double I_app,
                  double* __restrict__ r) {
+    // the phase-indexed coefficient tables in shared memory: indexed by the
+    // threads' own phases, kernel-parameter (constant bank) loads would be
+    // serialised over the distinct phases of a warp
+    __shared__ double s_gD[6], s_gs[36];
+    {
+        const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+        if (tid < 6) s_gD[tid] = P.gD[tid];
+        if (tid < 36) s_gs[tid] = P.gsig[tid / 6][tid % 6];
+        __syncthreads();
+    }
     int z, y, t;
     vox_coords(D, z, y, t);
     if (z >= D.nz || y >= D.ny) return;
@@ -359,14 +370,14 @@ k_residual_split(DevParams P, Dims D, const uint32_t* __restrict__ vc, const dou
             const double cw = u[w], pw = u[N + w];
             const double S = fmax(cv, P.cmin[PE]) + fmax(cw, P.cmin[PE]);
             const double dc = cw - cv, dp = pw - pv;
-            const double j = -P.E_gk * dp - P.E_gm * dc / S;
+            const double j = -P.E_gk * dp - P.E_gm * dc * rcp_nr(S);
             rc += -P.E_gD * dc + P.E_tF * j;
             rp += j;
         } else if (lv == lw && (lv == PG || lv == PK)) {
-            rc += -P.gD[lv] * (u[w] - cv);
-            rp += -P.gsig[lv][lw] * (u[N + w] - pv);
+            rc += -s_gD[lv] * (u[w] - cv);
+            rp += -s_gs[lv * 6 + lw] * (u[N + w] - pv);
         } else if (lv != PE && lw != PE) {
-            rp += -P.gsig[lv][lw] * (u[N + w] - pv);
+            rp += -s_gs[lv * 6 + lw] * (u[N + w] - pv);
         } else if (lw == PE && (lv == PG || lv == PK || lv == PL)) {
             const int64_t i = ibase++;
             const double ibv = icur[i], ipl = icur[NI + i];
@@ -603,6 +614,19 @@ __global__ void __launch_bounds__(256, 4)
 k_jvp_lin(ParT<float> P, Dims D, const uint32_t* __restrict__ vc, const float* __restrict__ c32,
           const float* __restrict__ icoef, const float* __restrict__ rowinv, const float* __restrict__ scal,
           const float2* __restrict__ x, float* __restrict__ y_out) {
+    // phase-indexed tables and the solve's scalars in shared memory (indexed
+    // by the threads' own phases; see k_residual_split)
+    __shared__ float s_cref[6], s_gD[6], s_gs[36], s_scal[9];
+    {
+        const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+        if (tid < 6) {
+            s_cref[tid] = P.cref[tid];
+            s_gD[tid] = P.gD[tid];
+        }
+        if (tid < 36) s_gs[tid] = P.gsig[tid / 6][tid % 6];
+        if (tid < 9) s_scal[tid] = scal[tid];
+        __syncthreads();
+    }
     int z, y, t;
     vox_coords(D, z, y, t);
     if (z >= D.nz || y >= D.ny) return;
@@ -611,10 +635,10 @@ k_jvp_lin(ParT<float> P, Dims D, const uint32_t* __restrict__ vc, const float* _
     const int v = t * syz + y * nz + z;
     const float2* __restrict__ xp = x + D.N;        // potentials
     const float2* __restrict__ xn = x + 2 * D.N;    // plating faces
-    const float dt_inv = scal[0];
+    const float dt_inv = s_scal[0];
     const uint32_t code = vc[v];
     const int lv = vc_phase(code);
-    const float crv = P.cref[lv], crE = P.cref[PE];
+    const float crv = s_cref[lv], crE = P.cref[PE];
     const float2 xcv = x[v], xpv = xp[v];
     const float dcv = df_val(xcv) * crv, dpv = df_val(xpv);
     const float A = P.A, AF = P.A * P.invF;
@@ -661,10 +685,10 @@ k_jvp_lin(ParT<float> P, Dims D, const uint32_t* __restrict__ vc, const float* _
             q4 = P.E_tF * p4;
         } else if (lv == lw && (lv == PG || lv == PK)) {
             ddc = df_diff(xcw, xcv) * crv;
-            q2 = -P.gD[lv];
-            p1 = -P.gsig[lv][lw];
+            q2 = -s_gD[lv];
+            p1 = -s_gs[lv * 6 + lw];
         } else if (lv != PE && lw != PE) {
-            p1 = -P.gsig[lv][lw];   // conduction between electronic conductors
+            p1 = -s_gs[lv * 6 + lw];   // conduction between electronic conductors
         } else if (vkin && lw == PE) {
             // solid v next to electrolyte w: interface face ibase (deta = -ddp)
             const int i = ibase++;
@@ -683,14 +707,14 @@ k_jvp_lin(ParT<float> P, Dims D, const uint32_t* __restrict__ vc, const float* _
             }
             if (lv == PG) {
                 const float dipl = -ip_eta * ddp + ip_ce * dcw + ip_n * dnf;
-                y_out[2 * D.N + i] = (P.invF * dipl + dnf * dt_inv) * scal[8] * rowinv[2 * D.N + i];
+                y_out[2 * D.N + i] = (P.invF * dipl + dnf * dt_inv) * s_scal[8] * rowinv[2 * D.N + i];
             }
         } else if (lv == PE && (lw == PG || lw == PK || lw == PL)) {
             // electrolyte v next to solid w: di = (i_eta + ip_eta) ddp + i_cs dc_w + (i_ce + ip_ce) dc_v + ip_n dn
             const int i = (int)vc_fbase(cw_code) + __popc(vc_emask(cw_code) & ((1u << opp_dir(d)) - 1u));
             const float i_eta = icoef[i], ip_eta = icoef[NI + i], i_cs = icoef[2 * NI + i];
             const float i_ce = icoef[3 * NI + i], ip_ce = icoef[4 * NI + i], ip_n = icoef[5 * NI + i];
-            dcw = df_val(xcw) * P.cref[lw];
+            dcw = df_val(xcw) * s_cref[lw];
             if (lw == PG) dnf = df_val(xn[i]) * P.nc;
             p1 = -A * (i_eta + ip_eta);
             p3 = -A * (i_ce + ip_ce);
@@ -705,9 +729,9 @@ k_jvp_lin(ParT<float> P, Dims D, const uint32_t* __restrict__ vc, const float* _
         jc += q1 * ddp + q2 * ddc + q3 * dcv + q4 * dcw + q5 * dnf;
     }
     if (t == 0 && lv == PCN) jp += P.g_dir * dpv;
-    if (has_c(lv)) jc = (jc + P.V * dt_inv * dcv) * scal[1 + lv];
+    if (has_c(lv)) jc = (jc + P.V * dt_inv * dcv) * s_scal[1 + lv];
     else jc = dcv;
-    jp *= scal[7];
+    jp *= s_scal[7];
     jc *= rowinv[v];
     jp *= rowinv[D.N + v];
     y_out[v] = jc;

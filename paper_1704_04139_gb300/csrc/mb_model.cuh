@@ -74,6 +74,21 @@ __host__ __device__ inline bool has_c(int p) { return p == PE || p == PG || p ==
 
 template <class T> __device__ inline T tmax(T a, T b) { return a > b ? a : b; }
 
+// 1/S in FP64 on the FMA pipe: the FP32 reciprocal refined by two
+// Newton-Raphson steps x <- x + x (1 - S x), each of which squares the
+// relative error (2^-24 -> 2^-48 -> below the FP64 rounding of the last FMA),
+// so the result is within ~1 ulp of 1/S.  Outside the FP32 exponent range
+// the plain division.
+__device__ inline double rcp_nr(double S) {
+    const double a = fabs(S);
+    if (!(a > 1e-30 && a < 1e30)) return 1.0 / S;
+    double x = (double)__frcp_rn((float)S);
+    double e = fma(-S, x, 1.0);
+    x = fma(x, e, x);
+    e = fma(-S, x, 1.0);
+    return fma(x, e, x);
+}
+
 template <class T>
 __device__ inline T ocp_val(const T* a, T x) {
     return T(a[0]) + T(a[1]) * x + T(a[2]) * exp(-T(a[3]) * x) + T(a[4]) * tanh((x - T(a[5])) / T(a[6]));

@@ -41,6 +41,8 @@
 #include <algorithm>
 #include <type_traits>
 #include <map>
+#include <mutex>
+#include <tuple>
 #include <vector>
 
 #include "mb_internal.h"
@@ -157,6 +159,8 @@ struct mb_rom {
     mb::RomWork w;
     std::vector<double> hU;    // host copy of the basis (n x Nr, row-major): the error estimate's maps
     mb::RomEst est;
+    bool tc_forced = false;    // the GEMM variant was set by mb_debug_rom_tensor (no autotuning)
+    float tune_ms[3] = {-1.f, -1.f, -1.f};   // the last autotuning's time per variant (-1: not timed)
 };
 
 namespace mb {
@@ -1651,7 +1655,6 @@ static int rom_build_host(mb_rom* R, const mb_rom_data* dd) {
         ok = d.UlocCdf && cudaMemcpy(d.UlocCdf, h.data(), 8 * (h.size() ? h.size() : 1), cudaMemcpyHostToDevice) ==
                                cudaSuccess;
     }
-    if (ok)
     if (ok) {
         std::vector<double> Pt((size_t)M * Nr);
         for (int i = 0; i < Nr; ++i)
@@ -1884,6 +1887,93 @@ static void iter_main_a(mb_rom* R, cudaStream_t s) {
         k_rom_ei<false><<<(unsigned)(((int64_t)d.M * B + 127) / 128), 128, 0, s>>>(
             d, c->P, c->Pf, B, w.uloc, w.gate, w.prm, w.active, w.hp, w.hplist, w.f, w.G, w.G64), count_launch(c);
 }
+// the Newton-matrix GEMM in variant tc (0 FP32 FMA, 1 mma.sync 3xTF32, 2 tcgen05 3xTF32)
+static void launch_rom_jac(mb_rom* R, cudaStream_t s, int tc, int ncols, const int* al, const int* dit,
+                           const int* dn) {
+    const RomDev& d = R->d;
+    RomWork& w = R->w;
+    const int B = w.B;
+    const dim3 gj((unsigned)(((int64_t)ncols * d.Nr + JT_COLS - 1) / JT_COLS), (unsigned)((d.Nr + JT_ROWS - 1) / JT_ROWS));
+    if (tc == 2 && d.Pbf)
+        k_rom_jac5<<<(unsigned)(((int64_t)ncols * d.Nr + T5_M - 1) / T5_M), T5_THREADS, T5_SMEM, s>>>(
+            d, B, ncols, al, w.prm, w.GU, w.hp, w.J, dit, dn, w.tcerr);
+    else if (tc)
+        k_rom_jac<true><<<gj, 256, 0, s>>>(d, B, ncols, al, w.prm, w.GU, w.hp, w.J, dit, dn);
+    else
+        k_rom_jac<false><<<gj, 256, 0, s>>>(d, B, ncols, al, w.prm, w.GU, w.hp, w.J, dit, dn);
+}
+
+// Autotuning of the Newton-matrix GEMM: the first batch of each (N_r, M, B)
+// times every variant the model admits on the batch's own buffers (GU
+// zeroed; one warm-up and three timed launches over all B instances, CUDA
+// events on the cell's stream) and keeps the fastest; later batches of the
+// same shape reuse the choice.  The three variants give FP32-accurate
+// matrices (tested against each other to 1e-9 on reduced trajectories), so
+// the choice changes the time only.
+struct TuneRec {
+    int choice;
+    float ms[3];
+};
+static std::mutex g_tune_mu;
+static std::map<std::tuple<int, int, int>, TuneRec> g_tune;
+
+static int rom_tune_gemm(mb_rom* R) {
+    const RomDev& d = R->d;
+    RomWork& w = R->w;
+    if (R->tc_forced || d.M == 0) return MB_OK;
+    const auto key = std::make_tuple(d.Nr, d.M, w.B);
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune.find(key);
+        if (it != g_tune.end()) {
+            R->d.tc = it->second.choice;
+            for (int k = 0; k < 3; ++k) R->tune_ms[k] = it->second.ms[k];
+            return MB_OK;
+        }
+    }
+    cudaStream_t s = R->cell->stream;
+    MB_CUDA(cudaMemsetAsync(w.GU, 0, sizeof(float) * (size_t)w.B * d.M * d.Nr, s));
+    cudaEvent_t e0, e1;
+    MB_CUDA(cudaEventCreate(&e0));
+    MB_CUDA(cudaEventCreate(&e1));
+    int best = d.tc;
+    float best_ms = 1e30f;
+    for (int tc = 0; tc <= 2; ++tc) {
+        R->tune_ms[tc] = -1.f;
+        if (tc == 2 && !d.Pbf) continue;
+        launch_rom_jac(R, s, tc, w.B, nullptr, nullptr, nullptr);
+        cudaEventRecord(e0, s);
+        for (int k = 0; k < 3; ++k) launch_rom_jac(R, s, tc, w.B, nullptr, nullptr, nullptr);
+        cudaEventRecord(e1, s);
+        cudaError_t e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        int terr = 0;
+        if (e == cudaSuccess) e = cudaMemcpy(&terr, w.tcerr, 4, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) {
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            return cuda_fail(e, "reduced model: GEMM autotuning");
+        }
+        if (terr) {   // a bounded wait of the tcgen05 kernel gave up: not a candidate
+            MB_CUDA(cudaMemset(w.tcerr, 0, 16));
+            continue;
+        }
+        R->tune_ms[tc] = ms / 3.f;
+        if (ms < best_ms) { best_ms = ms; best = tc; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    MB_CUDA_LAUNCH("rom_tune_gemm");
+    R->d.tc = best;
+    TuneRec rec;
+    rec.choice = best;
+    for (int k = 0; k < 3; ++k) rec.ms[k] = R->tune_ms[k];
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune[key] = rec;
+    return MB_OK;
+}
+
 static void iter_main_b(mb_rom* R, cudaStream_t s, bool listed, int ncols, const int* dit) {
     mb_cell* c = R->cell;
     const RomDev& d = R->d;
@@ -1893,17 +1983,9 @@ static void iter_main_b(mb_rom* R, cudaStream_t s, bool listed, int ncols, const
         k_rom_gu<<<(unsigned)(((int64_t)d.M * B * 32 + 255) / 256), 256, 0, s>>>(d, B, w.G, w.active, w.hp, w.GU),
             count_launch(c);
     if (ncols > 0) {
-        const dim3 gj((unsigned)(((int64_t)ncols * d.Nr + JT_COLS - 1) / JT_COLS),
-                      (unsigned)((d.Nr + JT_ROWS - 1) / JT_ROWS));
         const int* al = (listed || dit) ? w.alist : nullptr;
         const int* dn = dit ? w.counts + 2 : nullptr;
-        if (d.tc == 2 && d.Pbf)
-            k_rom_jac5<<<(unsigned)(((int64_t)ncols * d.Nr + T5_M - 1) / T5_M), T5_THREADS, T5_SMEM, s>>>(
-                d, B, ncols, al, w.prm, w.GU, w.hp, w.J, dit, dn, w.tcerr);
-        else if (d.tc)
-            k_rom_jac<true><<<gj, 256, 0, s>>>(d, B, ncols, al, w.prm, w.GU, w.hp, w.J, dit, dn);
-        else
-            k_rom_jac<false><<<gj, 256, 0, s>>>(d, B, ncols, al, w.prm, w.GU, w.hp, w.J, dit, dn);
+        launch_rom_jac(R, s, d.tc, ncols, al, dit, dn);
         count_launch(c);
     }
     k_rom_resid<<<(unsigned)B, 128, 0, s>>>(d, w.a, w.a_old, w.prm, w.f, w.active, w.r), count_launch(c);
@@ -2233,7 +2315,7 @@ static int rom_batch_begin(mb_rom* R, int B, const mb_rom_params* prm, double dt
         R->d, B, w.a, w.failed, w.its, w.flips, w.hp), count_launch(R->cell);
     MB_CUDA_LAUNCH("rom_batch_start");
     MB_CUDA(cudaStreamSynchronize(s));   // the host parameter buffer goes out of scope
-    return MB_OK;
+    return rom_tune_gemm(R);
 }
 }  // namespace mb
 
@@ -2681,5 +2763,13 @@ extern "C" int mb_debug_rom_tensor(mb_rom* R, int on) {
         return MB_EINVAL;
     }
     R->d.tc = on;
+    R->tc_forced = true;
+    return MB_OK;
+}
+
+extern "C" int mb_debug_rom_gemm_tuning(mb_rom* R, int* choice, float* ms) {
+    if (!R || !choice || !ms) { set_error("mb_debug_rom_gemm_tuning: invalid argument"); return MB_EINVAL; }
+    *choice = R->d.tc;
+    for (int k = 0; k < 3; ++k) ms[k] = R->tune_ms[k];
     return MB_OK;
 }

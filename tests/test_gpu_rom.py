@@ -194,6 +194,31 @@ def test_rom_tensor_newton_matrix_same_result(params, request, which):
 
 
 @pytest.mark.gpu
+def test_rom_gemm_autotuning(params, request):
+    """Without a fixed variant, the first batch times every GEMM variant the
+    model admits and keeps the fastest; the solve then gives exactly what the
+    same variant gives when fixed (same kernels, same arithmetic)."""
+    B = _gpu()
+    lab, oc, rom = request.getfixturevalue("case")
+    gc, g = _gpu_rom(B, lab, params, rom)
+    prm = [(c * oc.i_1c, s, k) for (c, s, k) in [(-2.0, 1.0, 1.0), (1.0, 0.9, 0.5), (-4.0, 0.7, 3.0)]]
+    auto = g.solve(prm, 3, 1.0)
+    choice, ms = g.gemm_tuning()
+    assert auto["ok"] and choice in (0, 1, 2)
+    timed = [m for m in ms if m >= 0]
+    assert len(timed) >= 2 and ms[choice] == min(timed)
+    g.close()
+    g2 = B.Rom(gc, rom.U, rom.Pbv, rom.P1c, rom.Ms, rom.Alin, rom.bbnd, rom.Pbv_proj, rom.P1c_proj,
+               rom.s_cp, rom.s_ac, rom.a0)
+    g2.debug_tensor(choice)
+    fixed = g2.solve(prm, 3, 1.0)
+    assert np.array_equal(fixed["V"], auto["V"])
+    assert g2.gemm_tuning()[0] == choice
+    g2.close()
+    gc.close()
+
+
+@pytest.mark.gpu
 @pytest.mark.parametrize("Nr,fp64,in_place", [(70, True, False), (70, False, False), (112, True, True),
                                               (150, False, True), (209, False, False), (209, True, True)])
 def test_rom_newton_step_lu_kernel(Nr, fp64, in_place):
