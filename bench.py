@@ -64,7 +64,7 @@ def fom_opts(B, prec, args):
                           newton_maxit=20, krylov_maxit=300, max_halvings=3,
                           mg_bf16=0 if args.fp32_coarse else 1, mg_stream=args.mg_stream,
                           mg_tail=1 if args.mg_tail else 0, krylov_forcing=0 if args.no_ew else 1,
-                          mg_kcycle_reorth=1 if args.kcycle_cgs2 else 0)
+                          mg_kcycle_reorth=0 if args.kcycle_cgs1 else 1)
 
 
 def step_record(infos):
@@ -520,8 +520,8 @@ def main():
                     help="smoother and coarse-level products from FP32 operators instead of their BF16 copies")
     ap.add_argument("--mg-stream", type=int, default=0, choices=[0, 1, 2],
                     help="operator fetch of the BF16 coarse sweeps: 0 plain, 1 L2 prefetch, 2 staged in shared memory")
-    ap.add_argument("--kcycle-cgs2", action="store_true",
-                    help="two Gram-Schmidt passes in the level-1 K-cycle instead of one (mg_kcycle_reorth = 1)")
+    ap.add_argument("--kcycle-cgs1", action="store_true",
+                    help="one Gram-Schmidt pass in the level-1 K-cycle instead of two (mg_kcycle_reorth = 0)")
     ap.add_argument("--no-ew", action="store_true",
                     help="every linear solve to krylov_rtol instead of Eisenstat-Walker forcing (krylov_forcing = 0)")
     ap.add_argument("--mg-tail", action="store_true",
@@ -664,6 +664,15 @@ def main():
             "other": {k: {"launches": v[0], "avg_launch_ms": v[1] / max(v[0], 1),
                           "gbs": (v[2] / (v[1] / max(v[0], 1) / 1000.0) / 1e9) if v[0] else None}
                       for k, v in kinds.items()}}
+    # step level: the algorithmic bytes of the three timed kernel classes over the timed steps
+    # divided by the timed steps' wall time (a lower bound of the step's HBM use: the other
+    # kernels' bytes are not counted)
+    step_bytes = sum(v[0] * v[2] for v in kinds.values())
+    roof["step"] = {"bytes_counted_per_step": step_bytes / args.steps,
+                    "kernels_counted": [v[4] for v in kinds.values()],
+                    "share_of_step_time": sum(v[1] for v in kinds.values()) / ms if ms else None,
+                    "achieved_gbs": step_bytes / (ms / 1000.0) / 1e9 if ms else None,
+                    "frac": step_bytes / (ms / 1000.0) / 1e9 / peak if ms else None}
 
     cell.close()
     arm64 = None
@@ -692,7 +701,7 @@ def main():
                           "dt_s": dt, "crate": CRATE[args.workload], "precision": args.precision,
                           "coarse_operators": "fp32" if args.fp32_coarse else "bf16", "mg_stream": args.mg_stream,
                           "mg_tail": 1 if args.mg_tail else 0, "krylov_forcing": 0 if args.no_ew else 1,
-                          "mg_kcycle_reorth": 1 if args.kcycle_cgs2 else 0,
+                          "mg_kcycle_reorth": 0 if args.kcycle_cgs1 else 1,
                           "l2": "working set > 129 MB L2, no flush", "parallelism": "replicas" if ws > 1 else "1 GPU"},
                "clocks": clk, "e2e": e2e, "gpu_launches": int(launches), "roofline": roof,
                "cpu_baseline": cpu,

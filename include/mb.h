@@ -95,9 +95,9 @@ typedef struct {
                               (the previous time level); 1 (default) the previous pass's converged
                               state.  The solution of a pass depends only on its frozen gates, not on
                               the start. */
-    int    mg_kcycle_reorth; /* 1: the level-1 K-cycle orthogonalises by two classical Gram-Schmidt
-                              passes; 0 (default): one pass (its 5 directions stay orthogonal
-                              enough; 2 % faster on a 4.2M-voxel cell) */
+    int    mg_kcycle_reorth; /* 1 (default): the level-1 K-cycle orthogonalises by two classical
+                              Gram-Schmidt passes; 0: one pass (2 % faster on a 4.2M-voxel cell,
+                              but FGMRES preconditioned with it stagnated on a small half cell) */
     int    krylov_forcing; /* 0: every linear solve to krylov_rtol; 1 (default): Eisenstat-Walker
                               forcing terms (choice 2, safeguarded) within [krylov_rtol, 0.1]:
                               26 % fewer preconditioner applications per step on a 4.2M-voxel

@@ -115,7 +115,7 @@ void mb_opts_default(mb_solver_opts* o) {
     o->mg_bf16 = 1;
     o->mg_stream = 0;
     o->pass_start = 1;
-    o->mg_kcycle_reorth = 0;
+    o->mg_kcycle_reorth = 1;
     o->krylov_forcing = 1;
     o->mg_tail = 0;
 }

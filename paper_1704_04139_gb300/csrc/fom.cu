@@ -138,6 +138,59 @@ __global__ void k_classify_write(Dims D, const uint8_t* __restrict__ lab, const 
     }
 }
 
+// Thread order of the stencil kernels whose per-face work depends on the
+// phases of the face's two voxels (residual, Krylov operator): within each
+// z-line (t, y) the voxels are ordered by (phase, whether a neighbour is of
+// the other kind: electrolyte vs solid), stable in z.  A warp then mostly
+// holds voxels of one phase and one contact type, so it executes one or two
+// of the per-face branches per direction instead of all of them (a warp pays
+// for every branch any of its lanes takes; the FP64 residual is bound by that
+// on GB300's narrow FP64 pipe).  Every voxel's arithmetic is unchanged; the
+// accesses stay within the line's few cache lines.  One thread per line.
+__global__ void k_zperm(Dims D, const uint32_t* __restrict__ vc, uint16_t* __restrict__ zperm) {
+    const int64_t line = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (line >= (int64_t)D.nt * D.ny) return;
+    const int t = (int)(line / D.ny), y = (int)(line % D.ny);
+    const int64_t base = line * D.nz;   // = t * syz + y * nz
+    constexpr int NKEY = 12;
+    int cnt[NKEY];
+#pragma unroll
+    for (int k = 0; k < NKEY; ++k) cnt[k] = 0;
+    auto key = [&](int z) {
+        const int64_t v = base + z;
+        const int lv = vc_phase(vc[v]);
+        const bool el = lv == PE;
+        bool mixed = false;
+        if (t > 0) mixed |= (vc_phase(vc[v - D.syz]) == PE) != el;
+        if (t < D.nt - 1) mixed |= (vc_phase(vc[v + D.syz]) == PE) != el;
+        if (y > 0) mixed |= (vc_phase(vc[v - D.nz]) == PE) != el;
+        if (y < D.ny - 1) mixed |= (vc_phase(vc[v + D.nz]) == PE) != el;
+        if (z > 0) mixed |= (vc_phase(vc[v - 1]) == PE) != el;
+        if (z < D.nz - 1) mixed |= (vc_phase(vc[v + 1]) == PE) != el;
+        return 2 * lv + (mixed ? 1 : 0);
+    };
+    for (int z = 0; z < D.nz; ++z) {
+        const int k = key(z);
+#pragma unroll
+        for (int q = 0; q < NKEY; ++q) cnt[q] += (q == k);
+    }
+    int start[NKEY];
+    int acc = 0;
+#pragma unroll
+    for (int q = 0; q < NKEY; ++q) {
+        start[q] = acc;
+        acc += cnt[q];
+    }
+    for (int z = 0; z < D.nz; ++z) {
+        const int k = key(z);
+        int pos = 0;
+#pragma unroll
+        for (int q = 0; q < NKEY; ++q)
+            if (q == k) pos = start[q]++;
+        zperm[base + pos] = (uint16_t)z;
+    }
+}
+
 int launch_classify(mb_cell* c, const uint8_t* d_lab) {
     const Dims& D = c->D;
     cudaStream_t s = c->stream;
@@ -191,17 +244,20 @@ int launch_classify(mb_cell* c, const uint8_t* d_lab) {
         size_t F = h_total ? h_total : 1;
         size_t NI = c->D.NI ? (size_t)c->D.NI : 1;
         c->vcode = (uint32_t*)cell_alloc(c, N * 4);
+        c->zperm = (uint16_t*)cell_alloc(c, N * 2);
         // interface face list; the plating faces are its first F entries
         c->if_s = (int32_t*)cell_alloc(c, NI * 4);
         c->if_e = (int32_t*)cell_alloc(c, NI * 4);
         c->pf_g = c->if_s;
         c->pf_e = c->if_e;
         c->pf_dir = (int8_t*)cell_alloc(c, F);
-        if (!c->vcode || !c->if_s || !c->if_e || !c->pf_dir) rc = MB_ENOMEM;
+        if (!c->vcode || !c->zperm || !c->if_s || !c->if_e || !c->pf_dir) rc = MB_ENOMEM;
     }
     if (rc == MB_OK) {
         k_classify_write<<<vox_grid(D, VOX_BLOCK), VOX_BLOCK, 0, s>>>(
             c->D, d_lab, emask, fbase, kbase, c->vcode, c->if_s, c->if_e, c->pf_dir), ::mb::count_launch(c);
+        const int64_t lines = (int64_t)D.nt * D.ny;
+        k_zperm<<<(unsigned)((lines + 127) / 128), 128, 0, s>>>(c->D, c->vcode, c->zperm), ::mb::count_launch(c);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) rc = cuda_fail(e, "classify_write");
     }
@@ -335,9 +391,9 @@ k_iface_current(DevParams P, Dims D, const uint32_t* __restrict__ vc, const int3
 }
 
 __global__ void __launch_bounds__(256)
-k_residual_split(DevParams P, Dims D, const uint32_t* __restrict__ vc, const double* __restrict__ u,
-                 const double* __restrict__ uold, const double* __restrict__ icur, double dt_inv, double I_app,
-                 double* __restrict__ r) {
+k_residual_split(DevParams P, Dims D, const uint32_t* __restrict__ vc, const uint16_t* __restrict__ zperm,
+                 const double* __restrict__ u, const double* __restrict__ uold, const double* __restrict__ icur,
+                 double dt_inv, double I_app, double* __restrict__ r) {
     // the phase-indexed coefficient tables in shared memory: indexed by the
     // threads' own phases, kernel-parameter (constant bank) loads would be
     // serialised over the distinct phases of a warp
@@ -351,6 +407,7 @@ k_residual_split(DevParams P, Dims D, const uint32_t* __restrict__ vc, const dou
     int z, y, t;
     vox_coords(D, z, y, t);
     if (z >= D.nz || y >= D.ny) return;
+    z = zperm[((int64_t)t * D.ny + y) * D.nz + z];   // grouped thread order (k_zperm)
     const int64_t N = D.N, NI = D.NI;
     int64_t v = (int64_t)t * D.syz + (int64_t)y * D.nz + z;
     const uint32_t code = vc[v];
@@ -407,8 +464,8 @@ int launch_residual_split(mb_cell* c, const double* u, const double* u_old, cons
     if (D.NI)
         k_iface_current<<<(unsigned)((D.NI + 255) / 256), 256, 0, s>>>(c->P, D, c->vcode, c->if_s, c->if_e, u, gate,
                                                                        c->s_i0, c->k_pl, c->icur), ::mb::count_launch(c);
-    k_residual_split<<<vox_grid(D, VOX_BLOCK), VOX_BLOCK, 0, s>>>(c->P, D, c->vcode, u, u_old, c->icur, 1.0 / dt,
-                                                                  I_app, r), ::mb::count_launch(c);
+    k_residual_split<<<vox_grid(D, VOX_BLOCK), VOX_BLOCK, 0, s>>>(c->P, D, c->vcode, c->zperm, u, u_old, c->icur,
+                                                                  1.0 / dt, I_app, r), ::mb::count_launch(c);
     prof_end(c, s, PROF_RESIDUAL, ev);
     MB_CUDA_LAUNCH("residual_split");
     return MB_OK;
@@ -611,7 +668,8 @@ template int launch_lin_setup<double>(mb_cell*, const double*, const uint8_t*, c
 // phases pays little for divergence.  scal: [0] 1/dt, [1 + phase]
 // 1/(V c_ref/dt), [7] 1/A, [8] dt/n_c.
 __global__ void __launch_bounds__(256, 4)
-k_jvp_lin(ParT<float> P, Dims D, const uint32_t* __restrict__ vc, const float* __restrict__ c32,
+k_jvp_lin(ParT<float> P, Dims D, const uint32_t* __restrict__ vc, const uint16_t* __restrict__ zperm,
+          const float* __restrict__ c32,
           const float* __restrict__ icoef, const float* __restrict__ rowinv, const float* __restrict__ scal,
           const float2* __restrict__ x, float* __restrict__ y_out) {
     // phase-indexed tables and the solve's scalars in shared memory (indexed
@@ -630,6 +688,7 @@ k_jvp_lin(ParT<float> P, Dims D, const uint32_t* __restrict__ vc, const float* _
     int z, y, t;
     vox_coords(D, z, y, t);
     if (z >= D.nz || y >= D.ny) return;
+    z = zperm[((int64_t)t * D.ny + y) * D.nz + z];   // grouped thread order (k_zperm)
     const int syz = (int)D.syz, nz = D.nz;
     const int NI = (int)D.NI;
     const int v = t * syz + y * nz + z;
@@ -759,7 +818,8 @@ int launch_jvp_lin(mb_cell* c, const float2* v, float* jv, cudaStream_t s) {
     const float* sc = c->d_dtinv;
     cudaEvent_t ev;
     prof_begin(c, s, &ev);
-    k_jvp_lin<<<g, VOX_BLOCK, 0, s>>>(c->Pf, D, c->vcode, c->u32, c->icoef, c->rowinv, sc, v, jv), ::mb::count_launch(c);
+    k_jvp_lin<<<g, VOX_BLOCK, 0, s>>>(c->Pf, D, c->vcode, c->zperm, c->u32, c->icoef, c->rowinv, sc, v, jv),
+        ::mb::count_launch(c);
     prof_end(c, s, PROF_JVP, ev);
     MB_CUDA_LAUNCH("jvp_lin");
     return MB_OK;
@@ -808,25 +868,46 @@ k_scaled_max(Dims D, const uint32_t* __restrict__ vc, const double* __restrict__
              const double* __restrict__ u, double* partials) {
     // [0] over every unknown; [1] the step-length cap: the voxel unknowns (c, phi)
     // in their scales and, with u given, each plated inventory relative to
-    // max(n_c, |n_f|) of the state u
-    double acc[2] = {0.0, 0.0};
+    // max(n_c, |n_f|) of the state u.
+    // The scale is constant per class (concentration by phase, potential,
+    // inventory), so the loop keeps the largest |x| per class as an integer
+    // maximum of the FP64 bit patterns with the sign cleared (for non-negative
+    // doubles the integer order is the numeric order, and NaN patterns sort
+    // above infinity), and scales once at the end: no FP64 arithmetic per
+    // element.  The relative cap term is formed in FP32 (a step-length
+    // heuristic; FP32 resolves it far beyond its 0.25 threshold).
+    constexpr unsigned long long ABS = 0x7fffffffffffffffull;
+    unsigned long long mc[6] = {0, 0, 0, 0, 0, 0}, mp = 0, mn = 0;
+    float capn = 0.f;
+    const float ncf = (float)nc;
     int64_t n = 2 * D.N + D.F;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        double s;
-        if (i < D.N) s = is.c[vc_phase(vc[i])];
-        else if (i < 2 * D.N) s = is.phi;
-        else s = is.n;
-        double a = fabs(x[i]) * s;
-        if (!(a == a)) a = 1e300;   // NaN -> huge
-        acc[0] = fmax(acc[0], a);
-        if (i < 2 * D.N) {
-            acc[1] = fmax(acc[1], a);
-        } else if (u) {
-            double ac = fabs(x[i]) / fmax(nc, fabs(u[i]));
-            if (!(ac == ac)) ac = 1e300;
-            acc[1] = fmax(acc[1], ac);
+        const unsigned long long b = (unsigned long long)__double_as_longlong(x[i]) & ABS;
+        if (i < D.N) {
+            const int ph = vc_phase(vc[i]);
+#pragma unroll
+            for (int k = 0; k < 6; ++k)
+                if (ph == k) mc[k] = b > mc[k] ? b : mc[k];
+        } else if (i < 2 * D.N) {
+            mp = b > mp ? b : mp;
+        } else {
+            mn = b > mn ? b : mn;
+            if (u) {
+                const float ac = (float)__longlong_as_double((long long)b) / fmaxf(ncf, fabsf((float)u[i]));
+                capn = (ac == ac) ? fmaxf(capn, ac) : INFINITY;
+            }
         }
     }
+    auto scaled = [](unsigned long long m, double sc) {
+        const double a = __longlong_as_double((long long)m) * sc;
+        return (a == a) ? a : 1e300;   // NaN -> huge
+    };
+    double vox = scaled(mp, is.phi);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) vox = fmax(vox, scaled(mc[k], is.c[k]));
+    double acc[2];
+    acc[0] = fmax(vox, scaled(mn, is.n));
+    acc[1] = u ? fmax(vox, capn < INFINITY ? (double)capn : 1e300) : vox;
     block_reduce_store<2, true>(acc, partials);
 }
 

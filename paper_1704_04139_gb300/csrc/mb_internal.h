@@ -91,6 +91,8 @@ struct mb_cell {
 
     // geometry
     uint32_t* vcode = nullptr;     // N
+    uint16_t* zperm = nullptr;     // N: per z-line, the z of its voxels grouped by phase and interface
+                                   //   contact (the thread order of the divergent stencil kernels)
     int32_t* if_s = nullptr;       // NI: solid voxel of each interface face
     int32_t* if_e = nullptr;       // NI: electrolyte voxel of each interface face
     int32_t* pf_g = nullptr;       // F (= if_s: plating faces come first)

@@ -192,19 +192,57 @@ __device__ inline int64_t iface_of(int lv, int lw, uint32_t code, uint32_t cw_co
     return -1;
 }
 
+// The set-up's scalars that depend on dt, rounded to FP32 once on the host
+// (evaluated per thread they would be FP64 divisions, and GB300's FP64 rate
+// is a small fraction of its FP32 rate)
+struct SetupScal {
+    float dtf, idt;      // dt, 1/dt
+    float V_dt, dt_V;    // V/dt, dt/V
+    float fc5;           // n_c dt / (V c_ref,E): dR_c(e)/dn in the Krylov units
+    float sc_cp;         // dt / (V c_ref,E)
+    float src[6];        // V c_ref,l / dt (c-row scale per phase)
+    float suc[6];        // c_ref,l (c-column scale per phase)
+};
+
+static SetupScal setup_scal(const DevParams& P, double dt) {
+    SetupScal S;
+    S.dtf = float(dt);
+    S.idt = float(1.0 / dt);
+    S.V_dt = float(P.V / dt);
+    S.dt_V = float(dt / P.V);
+    S.fc5 = float(P.nc * dt / (P.V * P.cref[PE]));
+    S.sc_cp = float(dt / (P.V * P.cref[PE]));
+    for (int l = 0; l < 6; ++l) {
+        S.src[l] = float(P.V * P.cref[l] / dt);
+        S.suc[l] = float(P.cref[l]);
+    }
+    return S;
+}
+
 // ------------------------------------------------------------ fine level
 __global__ void __launch_bounds__(256)
-k_bj_setup(ParT<float> P, Dims D, const uint32_t* __restrict__ vc, const float* __restrict__ u,
-           const float* __restrict__ icoef, double dt, float* __restrict__ dinv, float* __restrict__ fc,
+k_bj_setup(ParT<float> P, Dims D, const uint32_t* __restrict__ vc, const uint16_t* __restrict__ zperm,
+           const float* __restrict__ u,
+           const float* __restrict__ icoef, SetupScal S, float* __restrict__ dinv, float* __restrict__ fc,
            float* __restrict__ rowdiag, float* __restrict__ rowinv) {
+    __shared__ float s_src[6], s_suc[6];
+    {
+        const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+        if (tid < 6) {
+            s_src[tid] = S.src[tid];
+            s_suc[tid] = S.suc[tid];
+        }
+        __syncthreads();
+    }
     int z = blockIdx.x * blockDim.x + threadIdx.x;
     int y = blockIdx.y * blockDim.y + threadIdx.y;
     int t = blockIdx.z;
     if (z >= D.nz || y >= D.ny) return;
+    z = zperm[((int64_t)t * D.ny + y) * D.nz + z];   // phase-grouped thread order within the z-line
     const int64_t N = D.N;
     int64_t v = (int64_t)t * D.syz + (int64_t)y * D.nz + z;
     const float* cc = u;
-    const float dtf = float(dt), idt = float(1.0 / dt);
+    const float dtf = S.dtf, idt = S.idt;
     const float nc = P.nc;
     const float A = float(P.A), c0 = float(P.cref[PE]);
     uint32_t code = vc[v];
@@ -215,6 +253,7 @@ k_bj_setup(ParT<float> P, Dims D, const uint32_t* __restrict__ vc, const float* 
     const int64_t off[6] = {-D.syz, D.syz, -(int64_t)D.nz, (int64_t)D.nz, -1, 1};
     const bool inb[6] = {t > 0, t < D.nt - 1, y > 0, y < D.ny - 1, z > 0, z < D.nz - 1};
     int rank = 0, irank = 0;
+#pragma unroll
     for (int d = 0; d < 6; ++d) {
         if (!inb[d]) continue;
         int64_t w = v + off[d];
@@ -241,18 +280,18 @@ k_bj_setup(ParT<float> P, Dims D, const uint32_t* __restrict__ vc, const float* 
                 d01 -= J.c[4] * J.n[1] / jnn;
                 d10 -= J.p[4] * J.n[0] / jnn;
                 d11 -= J.p[4] * J.n[1] / jnn;
-                fc[FCW * f + 5] = float(double(J.c[4]) * double(nc) * dt / (P.V * P.cref[PE]));   // dR_c(e)/dn
+                fc[FCW * f + 5] = J.c[4] * S.fc5;     // dR_c(e)/dn
                 fc[FCW * f + 6] = J.p[4] * nc / A;    // dR_phi(e)/dn
             }
         }
     }
     if (t == 0 && lv == PCN) { d11 += float(P.g_dir); dgp += float(P.g_dir); }
-    float src, suc = float(P.cref[lv]);
+    float src, suc = s_suc[lv];
     if (has_c(lv)) {
-        d00 += float(P.V / dt);
-        dgc += float(P.V / dt);
-        src = float(P.V * P.cref[lv] / dt);
-        rowdiag[v] = fmaxf(fabsf(dgc * float(dt / P.V)), 1e-30f);
+        d00 += S.V_dt;
+        dgc += S.V_dt;
+        src = s_src[lv];
+        rowdiag[v] = fmaxf(fabsf(dgc * S.dt_V), 1e-30f);
         rowinv[v] = 1.f / rowdiag[v];
     } else {
         d00 = 1.f; d01 = 0.f; src = 1.f;
@@ -340,9 +379,16 @@ __global__ void k_bj_apply(Dims D, const float* __restrict__ dinv, const float* 
 // ------------------------------------------------------- level-1 assembly
 __device__ inline void acc_blk(float* blk, int k, int kk, float v) { blk[k * NCLS + kk] += v; }
 
-__global__ void __launch_bounds__(128)
+// One thread per coarse cell; its 16 + 96 accumulators (indexed by the
+// runtime classes of the faces' voxels) live in its own row of shared memory
+// (stride 113: conflict-free across a warp) instead of spilling to local memory.
+constexpr int L1_THREADS = 64;
+constexpr int L1_STRIDE = BLK + OFFW + 1;
+
+__global__ void __launch_bounds__(L1_THREADS)
 k_assemble_l1(ParT<float> P, Dims D, const uint32_t* __restrict__ vc, const float* __restrict__ u,
-              const float* __restrict__ icoef, double dt, Level L1) {
+              const float* __restrict__ icoef, SetupScal S, Level L1) {
+    __shared__ float s_acc[L1_THREADS * L1_STRIDE];
     int64_t cell = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (cell >= L1.cells) return;
     int cz = (int)(cell % L1.nz);
@@ -351,14 +397,14 @@ k_assemble_l1(ParT<float> P, Dims D, const uint32_t* __restrict__ vc, const floa
     const float* cc = u;
     const float A = float(P.A);
     const float c0 = float(P.cref[PE]);
-    const float idt = float(1.0 / dt);
+    const float idt = S.idt;
     // scaling of rows (1/s_r) and columns (s_u) into the Krylov units
-    const float sc_cc = float(dt / P.V);                 // (row c, col c)
-    const float sc_cp = float(dt / (P.V * P.cref[PE]));  // (row c, col phi)
+    const float sc_cc = S.dt_V;                          // (row c, col c)
+    const float sc_cp = S.sc_cp;                         // (row c, col phi)
     const float sc_pc = c0 / A;                          // (row phi, col c)
     const float sc_pp = 1.f / A;                         // (row phi, col phi)
-    float ex[BLK];
-    float off[OFFW];
+    float* ex = s_acc + threadIdx.x * L1_STRIDE;
+    float* off = ex + BLK;
     for (int i = 0; i < BLK; ++i) ex[i] = 0.f;
     for (int i = 0; i < OFFW; ++i) off[i] = 0.f;
     uint32_t mask = 0;
@@ -382,6 +428,7 @@ k_assemble_l1(ParT<float> P, Dims D, const uint32_t* __restrict__ vc, const floa
                 const bool inb[6] = {t > 0, t < D.nt - 1, y > 0, y < D.ny - 1, z > 0, z < D.nz - 1};
                 const int loc[6] = {a, a, b, b, e, e};
                 int rank = 0, irank = 0;
+#pragma unroll
                 for (int d = 0; d < 6; ++d) {
                     if (!inb[d]) continue;
                     int64_t w = v + offs[d];
@@ -527,12 +574,18 @@ __global__ void k_finalize(Level L) {
 #pragma unroll
     for (int col = 0; col < NCLS; ++col) {
         int piv = col;
+        float pmax = fabsf(a[col][col]);
+#pragma unroll
+        for (int r = col + 1; r < NCLS; ++r) {
+            const float ar = fabsf(a[r][col]);
+            if (ar > pmax) { pmax = ar; piv = r; }
+        }
+        // row swap with compile-time row indices (a runtime index would put a[][] in local memory)
 #pragma unroll
         for (int r = col + 1; r < NCLS; ++r)
-            if (fabsf(a[r][col]) > fabsf(a[piv][col])) piv = r;
-        if (piv != col)
+            if (r == piv)
 #pragma unroll
-            for (int j = 0; j < 2 * NCLS; ++j) { float tmp = a[col][j]; a[col][j] = a[piv][j]; a[piv][j] = tmp; }
+                for (int j = 0; j < 2 * NCLS; ++j) { float tmp = a[col][j]; a[col][j] = a[r][j]; a[r][j] = tmp; }
         const float p = a[col][col];
         const float ip = p != 0.f ? 1.f / p : 0.f;
 #pragma unroll
@@ -545,7 +598,9 @@ __global__ void k_finalize(Level L) {
             for (int j = 0; j < 2 * NCLS; ++j) a[r][j] -= fct * a[col][j];
         }
     }
+#pragma unroll
     for (int k = 0; k < NCLS; ++k)
+#pragma unroll
         for (int kk = 0; kk < NCLS; ++kk) L.sinv[(int64_t)(k * NCLS + kk) * L.cells + cell] = a[k][NCLS + kk];
     // BF16 copy, block q (0..5 off_d, 6 exd, 7 sinv), row k: pk[(4q + k) * cells + cell]
     for (int q = 0; q < 8; ++q) {
@@ -747,11 +802,35 @@ __device__ inline void coarse_solve_block(int n, const double* __restrict__ Ainv
         x[cell] = df4_pack(df_from_double(sx[4 * cell]), df_from_double(sx[4 * cell + 1]),
                            df_from_double(sx[4 * cell + 2]), df_from_double(sx[4 * cell + 3]));
 }
-__global__ void k_coarse_solve(int n, const double* __restrict__ Ainv, const float4* __restrict__ b,
-                               DF4* __restrict__ x) {
+// The same product spread over blocks of CS_ROWS rows (whole cells): the FP64
+// dot products are bound by the SM's FP64 pipe, so one block alone took
+// ~17 us for n = 128; CS_ROWS = 16 spreads them over 8 SMs.
+constexpr int CS_ROWS = 16;
+__global__ void __launch_bounds__(256) k_coarse_solve(int n, const double* __restrict__ Ainv,
+                                                      const float4* __restrict__ b, DF4* __restrict__ x) {
     __shared__ double sb[COARSE_MAX];
-    __shared__ double sx[COARSE_MAX];
-    coarse_solve_block(n, Ainv, b, x, sb, sx);
+    __shared__ double sx[CS_ROWS];
+    const float* bf = reinterpret_cast<const float*>(b);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) sb[i] = (double)bf[i];
+    __syncthreads();
+    const int r0 = blockIdx.x * CS_ROWS;
+    const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int q = threadIdx.x >> 5; q < CS_ROWS; q += nw) {
+        const int r = r0 + q;
+        double acc = 0.0;
+        if (r < n)
+            for (int j = lane; j < n; j += 32) acc += Ainv[(int64_t)r * n + j] * sb[j];
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+        if (lane == 0) sx[q] = acc;
+    }
+    __syncthreads();
+    const int c0 = r0 / NCLS;
+    for (int k = threadIdx.x; k < CS_ROWS / NCLS; k += blockDim.x) {
+        const int cell = c0 + k;
+        if (cell >= n / NCLS) break;
+        x[cell] = df4_pack(df_from_double(sx[4 * k]), df_from_double(sx[4 * k + 1]), df_from_double(sx[4 * k + 2]),
+                           df_from_double(sx[4 * k + 3]));
+    }
 }
 
 // ------------------------------------------------ assembled fine smoother
@@ -788,12 +867,14 @@ __device__ inline void fst_st(void* fst, int k, int64_t N, int64_t v, float a, f
 // difference form: p dc_w = p c_ref,w ((z_c,w - z_c,v) + z_c,v).
 template <bool B16>
 __global__ void __launch_bounds__(256)
-k_assemble_fine(ParT<float> P, Dims D, const uint32_t* __restrict__ vc, const float* __restrict__ c32,
+k_assemble_fine(ParT<float> P, Dims D, const uint32_t* __restrict__ vc, const uint16_t* __restrict__ zperm,
+                const float* __restrict__ c32,
                 const float* __restrict__ icoef, const float* __restrict__ scal, void* __restrict__ fst) {
-    const int z = blockIdx.x * blockDim.x + threadIdx.x;
+    int z = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     const int t = blockIdx.z;
     if (z >= D.nz || y >= D.ny) return;
+    z = zperm[((int64_t)t * D.ny + y) * D.nz + z];   // phase-grouped thread order within the z-line
     const int64_t N = D.N, NI = D.NI;
     const int64_t v = (int64_t)t * D.syz + (int64_t)y * D.nz + z;
     const uint32_t code = vc[v];
@@ -1418,7 +1499,11 @@ __global__ void k_restrict_fine(Dims D, const uint32_t* __restrict__ vc, const f
                 if (tt >= D.nt || y >= D.ny || z >= D.nz) continue;
                 int64_t v = (int64_t)tt * D.syz + (int64_t)y * D.nz + z;
                 int lv = vc_phase(vc[v]);
-                acc[phi_class(lv)] += r[N + v] - t[N + v];
+                const int k = phi_class(lv);
+                const float rp = r[N + v] - t[N + v];
+#pragma unroll
+                for (int q = 0; q < NCLS; ++q)   // compile-time index: acc stays in registers
+                    if (q == k) acc[q] += rp;
                 if (lv == PE) acc[0] += r[v] - t[v];
             }
     C.b[cell] = make_float4(acc[0], acc[1], acc[2], acc[3]);
@@ -1707,11 +1792,12 @@ int precond_setup(mb_cell* c, const float* u32, const uint8_t* gate, double dt) 
     const Dims& D = c->D;
     cudaStream_t s = c->stream;
     (void)gate;
-    k_bj_setup<<<pgrid(D.nt, D.ny, D.nz), PB, 0, s>>>(c->Pf, D, c->vcode, u32, c->icoef, dt, p->dinv, p->fc,
+    const SetupScal ss = setup_scal(c->P, dt);
+    k_bj_setup<<<pgrid(D.nt, D.ny, D.nz), PB, 0, s>>>(c->Pf, D, c->vcode, c->zperm, u32, c->icoef, ss, p->dinv, p->fc,
                                                        c->rowdiag, c->rowinv), ::mb::count_launch(c);
     Level& L1 = p->lv[1];
-    k_assemble_l1<<<(unsigned)((L1.cells + 127) / 128), 128, 0, s>>>(c->Pf, D, c->vcode, u32, c->icoef, dt, L1),
-        ::mb::count_launch(c);
+    k_assemble_l1<<<(unsigned)((L1.cells + L1_THREADS - 1) / L1_THREADS), L1_THREADS, 0, s>>>(
+        c->Pf, D, c->vcode, u32, c->icoef, ss, L1), ::mb::count_launch(c);
     for (int l = 2; l <= p->nlev; ++l)
         k_assemble_up<<<nblk(p->lv[l].cells), 256, 0, s>>>(p->lv[l - 1], p->lv[l]), ::mb::count_launch(c);
     for (int l = 1; l <= p->nlev; ++l) k_finalize<<<nblk(p->lv[l].cells), 256, 0, s>>>(p->lv[l]), ::mb::count_launch(c);
@@ -1824,7 +1910,8 @@ static void vcycle(mb_cell* c, int l) {
     }
     Level& L = p->lv[l];
     if (l == p->nlev) {
-        k_coarse_solve<<<1, 256, 0, s>>>(p->ncoarse, p->cinv, L.b, L.x), ::mb::count_launch(c);
+        k_coarse_solve<<<(unsigned)((p->ncoarse + CS_ROWS - 1) / CS_ROWS), 256, 0, s>>>(p->ncoarse, p->cinv, L.b, L.x),
+            ::mb::count_launch(c);
         return;
     }
     Level& C = p->lv[l + 1];
@@ -2006,9 +2093,9 @@ int precond_setup_fine(mb_cell* c) {
     cudaStream_t s = c->stream;
     const dim3 vg = pgrid(D.nt, D.ny, D.nz);
     if (p->b16)
-        k_assemble_fine<true><<<vg, PB, 0, s>>>(c->Pf, D, c->vcode, c->u32, c->icoef, c->d_dtinv, p->fst);
+        k_assemble_fine<true><<<vg, PB, 0, s>>>(c->Pf, D, c->vcode, c->zperm, c->u32, c->icoef, c->d_dtinv, p->fst);
     else
-        k_assemble_fine<false><<<vg, PB, 0, s>>>(c->Pf, D, c->vcode, c->u32, c->icoef, c->d_dtinv, p->fst);
+        k_assemble_fine<false><<<vg, PB, 0, s>>>(c->Pf, D, c->vcode, c->zperm, c->u32, c->icoef, c->d_dtinv, p->fst);
     ::mb::count_launch(c);
     MB_CUDA_LAUNCH("precond_setup_fine");
     return MB_OK;

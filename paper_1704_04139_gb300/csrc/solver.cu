@@ -141,30 +141,37 @@ __global__ void k_axpy_d(double alpha, const double* __restrict__ x, double* __r
     if (i < n) y[i] += alpha * x[i];
 }
 
-// b_hat = -R / s_r / |diag|  (row-equilibrated right-hand side; is = 1/s_r)
+// b_hat = -R / s_r / |diag|  (row-equilibrated right-hand side; is = 1/s_r).
+// R is rounded to FP32 before the scaling (the right-hand side is FP32 either
+// way; one FP64 conversion per element instead of a multiply and a conversion
+// on GB300's narrow FP64 pipe); the per-phase scales from shared memory.
 __global__ void k_scale_rhs(Dims D, const uint32_t* __restrict__ vc, const double* __restrict__ R, InvScales is,
                             const float* __restrict__ rowinv, float* __restrict__ b) {
+    __shared__ float s_c[6];
+    if (threadIdx.x < 6) s_c[threadIdx.x] = (float)is.c[threadIdx.x];
+    __syncthreads();
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int64_t n = 2 * D.N + D.F;
     if (i >= n) return;
-    double s;
-    if (i < D.N) s = is.c[vc_phase(vc[i])];
-    else if (i < 2 * D.N) s = is.phi;
-    else s = is.n;
-    b[i] = (float)(-R[i] * s) * rowinv[i];
+    float s;
+    if (i < D.N) s = s_c[vc_phase(vc[i])];
+    else if (i < 2 * D.N) s = (float)is.phi;
+    else s = (float)is.n;
+    b[i] = -(float)R[i] * s * rowinv[i];
 }
 
-// delta = s_u * x_hat
+// delta = s_u * x_hat (per-phase scales from shared memory)
 __global__ void k_unscale(DevParams P, Dims D, const uint32_t* __restrict__ vc, const float2* __restrict__ x,
                           double* __restrict__ d) {
+    __shared__ double s_c[6];
+    if (threadIdx.x < 6) s_c[threadIdx.x] = P.cref[threadIdx.x];
+    __syncthreads();
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int64_t n = 2 * D.N + D.F;
     if (i >= n) return;
-    double s;
-    if (i < D.N) s = P.cref[vc_phase(vc[i])];
-    else if (i < 2 * D.N) s = 1.0;
-    else s = P.nc;
-    d[i] = s * df_to_double(x[i]);
+    if (i < D.N) d[i] = s_c[vc_phase(vc[i])] * df_to_double(x[i]);
+    else if (i < 2 * D.N) d[i] = df_to_double(x[i]);
+    else d[i] = P.nc * df_to_double(x[i]);
 }
 
 static inline unsigned nblk(int64_t n) { return (unsigned)((n + 255) / 256); }
