@@ -283,7 +283,7 @@ def rom_paper_dims(B, params, args, torch, estimate=True):
     rng = np.random.default_rng(43)
     prm = _rom_params(rng, args.rom_instances, i1)
     steps = args.rom_paper_steps
-    rom.solve(prm[:8], 1, 1.0)
+    rom.solve(prm, 1, 1.0)     # warm-up on the timed batch's shape (allocation, autotuning, graph capture)
     torch.cuda.synchronize()
     if args.rom_host_loop:
         rom.debug_graph(False)

@@ -130,6 +130,7 @@ struct RomWork {
     int* ctl = nullptr;        // device: [0] Newton iteration of the pass, [1] passes done
     int* tcerr = nullptr;      // device: a bounded wait of the tcgen05 GEMM gave up
     bool graph_failed = false; // the graph could not be built: host-driven steps
+    int g_tc = -1, g_ir = -1;  // the GEMM variant and escalation mode the graph was captured with
     std::vector<void*> bufs;
 };
 
@@ -1742,9 +1743,12 @@ static int rom_work_alloc(mb_rom* R, int B) {
 // A batch of B slots; an empty slot is marked failed and skipped by every
 // kernel.  Each occupied slot advances one time step per rom_batch_step.
 int rom_batch_alloc(mb_rom* R, int B) {
-    int rc = rom_work_alloc(R, B);
-    if (rc) return rc;
     RomWork& w = R->w;
+    // a batch of the same size reuses the buffers (and with them the captured step graph)
+    if (!(w.B == B && !w.bufs.empty())) {
+        int rc = rom_work_alloc(R, B);
+        if (rc) return rc;
+    }
     cudaStream_t s = R->cell->stream;
     std::vector<int> ones(B, 1);
     MB_CUDA(cudaMemcpyAsync(w.failed, ones.data(), 4 * B, cudaMemcpyHostToDevice, s));
@@ -2222,7 +2226,15 @@ static int rom_graph_build(mb_rom* R) {
 int rom_batch_step(mb_rom* R) {
     RomWork& w = R->w;
     if (R->d.graph && !w.graph_failed) {
-        if (!w.gexec && rom_graph_build(R)) w.graph_failed = true;
+        if (w.gexec && (w.g_tc != R->d.tc || w.g_ir != R->d.ir)) {   // captured with other kernels
+            cudaGraphExecDestroy(w.gexec);
+            w.gexec = nullptr;
+        }
+        if (!w.gexec) {
+            if (rom_graph_build(R)) w.graph_failed = true;
+            w.g_tc = R->d.tc;
+            w.g_ir = R->d.ir;
+        }
         if (w.gexec) {
             MB_CUDA(cudaGraphLaunch(w.gexec, R->cell->stream));
             count_launch(R->cell);
