@@ -419,7 +419,7 @@ def serve_run(B, params, rom, i1, args, slots=256, workers=4):
     gaps = rng.exponential(1.0 / rate, n_req)
     t0 = time.perf_counter()
     t_next = t0
-    pending, done = {}, {}
+    pending, done, t_sub = {}, {}, {}
     for k, r in enumerate(reqs):
         t_next += gaps[k]
         while time.perf_counter() < t_next:
@@ -428,7 +428,10 @@ def serve_run(B, params, rom, i1, args, slots=256, workers=4):
                 if res is not None:
                     done[t] = (pending.pop(t), res)
             time.sleep(0.0005)
-        pending[submit(r)] = r[0]
+        t_s = time.perf_counter() - t0
+        tk = submit(r)
+        pending[tk] = r[0]
+        t_sub[tk] = t_s
     t_arrivals = time.perf_counter() - t0
     while pending:
         for t in list(pending):
@@ -441,13 +444,25 @@ def serve_run(B, params, rom, i1, args, slots=256, workers=4):
     srv.close()
     lat = {"rom": [], "fom": []}
     bad = cut = 0
-    for kind, res in done.values():
+    t_fin = []
+    for tk, (kind, res) in done.items():
         lat[kind].append(1000.0 * (res["t_done"] - res["t_submit"]))
+        t_fin.append(t_sub[tk] + (res["t_done"] - res["t_submit"]))
         bad += res["status"] not in (B.MB_OK, B.MB_ECUTOFF)
         cut += res["status"] == B.MB_ECUTOFF
+    # steady state: completions in the second half of the arrival window against the
+    # arrivals in it (the first half covers the fill-up of requests of up to 3000 steps;
+    # the whole-run figure also carries the drain of the last long requests)
+    t_fin = np.array(t_fin)
+    half = 0.5 * t_arrivals
+    done_2nd = int(np.count_nonzero((t_fin >= half) & (t_fin < t_arrivals)))
+    arr_2nd = int(np.count_nonzero(np.array(list(t_sub.values())) >= half))
     return {"requests": n_req, "rom_fraction": 0.95, "arrival_rate_per_s": rate,
             "capacity_mixed_burst_per_s": cap, "throughput_per_s": n_req / total,
             "throughput_over_arrival_rate": (n_req / total) / (n_req / t_arrivals), "wall_s": total,
+            "arrival_window_s": t_arrivals,
+            "steady_state_second_half": {"completed": done_2nd, "arrived": arr_2nd,
+                                         "throughput_over_arrival_rate": done_2nd / max(arr_2nd, 1)},
             "failed": int(bad), "ended_at_cutoff": int(cut), "v_cutoff": V_CUTOFF, "rom_slots": slots,
             "fom_workers": workers, "fom_cells_peak": peak,
             "p50_ms": {k: float(np.percentile(v, 50)) if v else None for k, v in lat.items()},
@@ -536,7 +551,7 @@ def main():
     ap.add_argument("--rom-steps", type=int, default=60)
     ap.add_argument("--rom-paper-steps", type=int, default=3,
                     help="timed steps of the paper-size reduced model (a sample of its 600-step protocol)")
-    ap.add_argument("--serve-requests", type=int, default=400)
+    ap.add_argument("--serve-requests", type=int, default=800)
     ap.add_argument("--experiment", action="store_true",
                     help="also run the paper's half-cell model-reduction experiment at reduced size "
                          "(paper_1704_04139_gb300.experiment) and add its results under 'experiment'")
