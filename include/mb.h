@@ -327,7 +327,9 @@ int mb_rom_destroy(mb_rom* rom);
  * min(1, 0.25 / m), m the max-norm of U_loc delta on the stencil closure of
  * the points with the voxel unknowns (c, phi) in their scales and the plated
  * inventories relative to max(n_c, |n|) of the current reconstruction,
- * converged at lam m <= 1e-12 (the same scaled norm), at most 30 iterations;
+ * converged at lam m <= 1e-12 (the same scaled norm) or at a full step with
+ * m <= 1e-10 that did not halve the previous m (the rounding floor of the
+ * reconstruction), at most 30 iterations;
  * plating active-set passes as mb_step (at most 3).  The state, the
  * interpolated terms and the residual are FP64 and the reconstruction at the
  * points float-float (~2^-44 relative; the converged result is the FP64 one

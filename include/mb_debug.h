@@ -69,6 +69,10 @@ int mb_debug_rom_graph(mb_rom* rom, int on);
  * default the first batch of each (N_r, M, B) times the variants the model
  * admits and keeps the fastest; this call fixes the variant instead. */
 int mb_debug_rom_tensor(mb_rom* rom, int on);
+/* State of slot b of the last batch: failed (0 no, 1 still iterating at the
+ * iteration limit, 2 a non-finite update), the Newton iterations of its last
+ * pass, the last scaled update norm and whether it had escalated to FP64. */
+int mb_debug_rom_slot(mb_rom* rom, int b, int* failed, int* pass_its, float* last_norm, int* escalated);
 /* The variant in use (as above) and the last autotuning's time per variant
  * in ms per launch over the whole batch (ms[3]; -1 where not timed). */
 int mb_debug_rom_gemm_tuning(mb_rom* rom, int* choice, float* ms);

@@ -175,6 +175,8 @@ def _declare(lib):
     fn("mb_debug_rom_graph", C.c_int, [VP, C.c_int])
     fn("mb_debug_rom_tensor", C.c_int, [VP, C.c_int])
     fn("mb_debug_rom_gemm_tuning", C.c_int, [VP, C.POINTER(C.c_int), C.POINTER(C.c_float)])
+    fn("mb_debug_rom_slot", C.c_int, [VP, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_float),
+                                      C.POINTER(C.c_int)])
     fn("mb_debug_rom_refine", C.c_int, [VP, C.c_int])
     fn("mb_debug_rom_lu", C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, VP, VP, VP])
     fn("mb_debug_residual_split", C.c_int, [VP, VP, VP, VP, C.c_double, C.c_double, VP])
@@ -536,6 +538,13 @@ class Rom:
         """Fix the Newton-matrix GEMM variant: 2 tcgen05, 1 mma.sync (both 3xTF32), 0 FP32 FMA
         (default: autotuned per batch shape)."""
         _check(lib().mb_debug_rom_tensor(self.h, int(on)))
+
+    def debug_slot(self, b):
+        """(failed 0/1 limit/2 non-finite, iterations of the last pass, last scaled update norm, escalated)."""
+        f, it, e = C.c_int(), C.c_int(), C.c_int()
+        nrm = C.c_float()
+        _check(lib().mb_debug_rom_slot(self.h, int(b), C.byref(f), C.byref(it), C.byref(nrm), C.byref(e)))
+        return f.value, it.value, nrm.value, e.value
 
     def gemm_tuning(self):
         """(variant in use, ms per launch of variants 0, 1, 2 at the last autotuning; -1 = not timed)."""

@@ -198,23 +198,23 @@ __device__ inline int64_t iface_of(int lv, int lw, uint32_t code, uint32_t cw_co
 struct SetupScal {
     float dtf, idt;      // dt, 1/dt
     float V_dt, dt_V;    // V/dt, dt/V
-    float fc5;           // n_c dt / (V c_ref,E): dR_c(e)/dn in the Krylov units
-    float sc_cp;         // dt / (V c_ref,E)
+    double fc5;          // n_c dt / (V c_ref,E): dR_c(e)/dn in the Krylov units (one FP64 product per face)
     float src[6];        // V c_ref,l / dt (c-row scale per phase)
     float suc[6];        // c_ref,l (c-column scale per phase)
 };
 
-static SetupScal setup_scal(const DevParams& P, double dt) {
+static SetupScal setup_scal(const DevParamsF& P, double dt) {
+    // the values the kernels formerly evaluated per thread from the FP32
+    // parameter copy, with the same roundings
     SetupScal S;
     S.dtf = float(dt);
     S.idt = float(1.0 / dt);
-    S.V_dt = float(P.V / dt);
-    S.dt_V = float(dt / P.V);
-    S.fc5 = float(P.nc * dt / (P.V * P.cref[PE]));
-    S.sc_cp = float(dt / (P.V * P.cref[PE]));
+    S.V_dt = float(double(P.V) / dt);
+    S.dt_V = float(dt / double(P.V));
+    S.fc5 = double(P.nc) * dt / double(P.V * P.cref[PE]);
     for (int l = 0; l < 6; ++l) {
-        S.src[l] = float(P.V * P.cref[l] / dt);
-        S.suc[l] = float(P.cref[l]);
+        S.src[l] = float(double(P.V * P.cref[l]) / dt);
+        S.suc[l] = P.cref[l];
     }
     return S;
 }
@@ -280,7 +280,7 @@ k_bj_setup(ParT<float> P, Dims D, const uint32_t* __restrict__ vc, const uint16_
                 d01 -= J.c[4] * J.n[1] / jnn;
                 d10 -= J.p[4] * J.n[0] / jnn;
                 d11 -= J.p[4] * J.n[1] / jnn;
-                fc[FCW * f + 5] = J.c[4] * S.fc5;     // dR_c(e)/dn
+                fc[FCW * f + 5] = float(double(J.c[4]) * S.fc5);   // dR_c(e)/dn
                 fc[FCW * f + 6] = J.p[4] * nc / A;    // dR_phi(e)/dn
             }
         }
@@ -379,16 +379,9 @@ __global__ void k_bj_apply(Dims D, const float* __restrict__ dinv, const float* 
 // ------------------------------------------------------- level-1 assembly
 __device__ inline void acc_blk(float* blk, int k, int kk, float v) { blk[k * NCLS + kk] += v; }
 
-// One thread per coarse cell; its 16 + 96 accumulators (indexed by the
-// runtime classes of the faces' voxels) live in its own row of shared memory
-// (stride 113: conflict-free across a warp) instead of spilling to local memory.
-constexpr int L1_THREADS = 64;
-constexpr int L1_STRIDE = BLK + OFFW + 1;
-
-__global__ void __launch_bounds__(L1_THREADS)
+__global__ void __launch_bounds__(128)
 k_assemble_l1(ParT<float> P, Dims D, const uint32_t* __restrict__ vc, const float* __restrict__ u,
-              const float* __restrict__ icoef, SetupScal S, Level L1) {
-    __shared__ float s_acc[L1_THREADS * L1_STRIDE];
+              const float* __restrict__ icoef, double dt, Level L1) {
     int64_t cell = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (cell >= L1.cells) return;
     int cz = (int)(cell % L1.nz);
@@ -397,14 +390,14 @@ k_assemble_l1(ParT<float> P, Dims D, const uint32_t* __restrict__ vc, const floa
     const float* cc = u;
     const float A = float(P.A);
     const float c0 = float(P.cref[PE]);
-    const float idt = S.idt;
+    const float idt = float(1.0 / dt);
     // scaling of rows (1/s_r) and columns (s_u) into the Krylov units
-    const float sc_cc = S.dt_V;                          // (row c, col c)
-    const float sc_cp = S.sc_cp;                         // (row c, col phi)
+    const float sc_cc = float(dt / P.V);                 // (row c, col c)
+    const float sc_cp = float(dt / (P.V * P.cref[PE]));  // (row c, col phi)
     const float sc_pc = c0 / A;                          // (row phi, col c)
     const float sc_pp = 1.f / A;                         // (row phi, col phi)
-    float* ex = s_acc + threadIdx.x * L1_STRIDE;
-    float* off = ex + BLK;
+    float ex[BLK];
+    float off[OFFW];
     for (int i = 0; i < BLK; ++i) ex[i] = 0.f;
     for (int i = 0; i < OFFW; ++i) off[i] = 0.f;
     uint32_t mask = 0;
@@ -428,7 +421,6 @@ k_assemble_l1(ParT<float> P, Dims D, const uint32_t* __restrict__ vc, const floa
                 const bool inb[6] = {t > 0, t < D.nt - 1, y > 0, y < D.ny - 1, z > 0, z < D.nz - 1};
                 const int loc[6] = {a, a, b, b, e, e};
                 int rank = 0, irank = 0;
-#pragma unroll
                 for (int d = 0; d < 6; ++d) {
                     if (!inb[d]) continue;
                     int64_t w = v + offs[d];
@@ -1792,12 +1784,12 @@ int precond_setup(mb_cell* c, const float* u32, const uint8_t* gate, double dt) 
     const Dims& D = c->D;
     cudaStream_t s = c->stream;
     (void)gate;
-    const SetupScal ss = setup_scal(c->P, dt);
+    const SetupScal ss = setup_scal(c->Pf, dt);
     k_bj_setup<<<pgrid(D.nt, D.ny, D.nz), PB, 0, s>>>(c->Pf, D, c->vcode, c->zperm, u32, c->icoef, ss, p->dinv, p->fc,
                                                        c->rowdiag, c->rowinv), ::mb::count_launch(c);
     Level& L1 = p->lv[1];
-    k_assemble_l1<<<(unsigned)((L1.cells + L1_THREADS - 1) / L1_THREADS), L1_THREADS, 0, s>>>(
-        c->Pf, D, c->vcode, u32, c->icoef, ss, L1), ::mb::count_launch(c);
+    k_assemble_l1<<<(unsigned)((L1.cells + 127) / 128), 128, 0, s>>>(c->Pf, D, c->vcode, u32, c->icoef, dt, L1),
+        ::mb::count_launch(c);
     for (int l = 2; l <= p->nlev; ++l)
         k_assemble_up<<<nblk(p->lv[l].cells), 256, 0, s>>>(p->lv[l - 1], p->lv[l]), ::mb::count_launch(c);
     for (int l = 1; l <= p->nlev; ++l) k_finalize<<<nblk(p->lv[l].cells), 256, 0, s>>>(p->lv[l]), ::mb::count_launch(c);

@@ -14,7 +14,9 @@
 //   gather u_loc = U_loc a; evaluate f and its sparse derivative rows G;
 //   GU = G U_loc; J = Ms/dt + Alin + P GU; r as above; solve J delta = -r by
 //   LU with partial pivoting after row/column equilibration; step length
-//   min(1, 0.25 / |U_loc delta|_s), converged at lam |U_loc delta|_s <= 1e-12,
+//   min(1, 0.25 / |U_loc delta|_s), converged at lam |U_loc delta|_s <= 1e-12
+//   (or at a full step below 1e-10 that did not halve the previous one: the
+//   rounding floor of the reconstruction),
 //   |.|_s the max-norm with voxel slots in their scales and plated
 //   inventories relative to max(n_c, |n|).
 // Plating gates: the full-order rule on the reconstruction, with the
@@ -56,6 +58,7 @@ constexpr int ROM_MAXIT = 30;
 constexpr int ROM_PASSES = 3;
 constexpr double ROM_DELTA_MAX = 0.25;
 constexpr double ROM_TOL = 1e-12;
+constexpr double ROM_TOL_FLOOR = 1e-10;   // the full-order production tolerance (rounding-floor stop)
 constexpr int RP = 4;            // per-instance parameters: I_app, s_i0, k_pl, 1/dt
 constexpr int ROM_HP_AFTER = 8;  // FP32-matrix iterations of a pass before an instance switches to FP64
 
@@ -1265,7 +1268,7 @@ k_rom_apply(RomDev d, int B, int nkt, double* __restrict__ a, const double* __re
     }
     const double dn = (double)m, dv = (double)mc;
     if (!(dn < INFINITY)) {
-        if (lane == 0) { failed[b] = 1; active[b] = 0; }
+        if (lane == 0) { failed[b] = 2; active[b] = 0; }   // 2: a non-finite update
         return;
     }
     // step length and convergence in the same scaled max-norm: voxel slots in
@@ -1276,8 +1279,12 @@ k_rom_apply(RomDev d, int B, int nkt, double* __restrict__ a, const double* __re
     for (int j = lane; j < d.Nr; j += 32) a[(int64_t)b * d.Nr + j] += lam * delta[(int64_t)b * d.Nr + j];
     if (lane == 0) {
         its[b] += 1;
-        if (lam * dv <= ROM_TOL) active[b] = 0;
         const int k = ++pit[b];
+        // converged: below the tolerance, or a full step below ROM_TOL_FLOOR that no
+        // longer halves the previous update (the iteration has reached the rounding
+        // floor of the reconstruction; Newton's own convergence is quadratic)
+        if (lam * dv <= ROM_TOL || (lam == 1.0 && dv <= ROM_TOL_FLOOR && k >= 2 && mc >= 0.5f * dnprev[b]))
+            active[b] = 0;
         if (k >= ROM_HP_AFTER || (k >= 3 && lam == 1.0 && mc > 0.9f * dnprev[b])) hp[b] = 1;
         dnprev[b] = mc;
     }
@@ -1402,7 +1409,7 @@ __global__ void k_rom_batch_start(RomDev d, int B, double* __restrict__ a, int* 
 __global__ void k_rom_fail_active(int B, int* __restrict__ active, int* __restrict__ failed) {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b < B && active[b]) {
-        failed[b] = 1;
+        failed[b] = 1;   // 1: still iterating after the iteration limit
         active[b] = 0;
     }
 }
@@ -2776,6 +2783,20 @@ extern "C" int mb_debug_rom_tensor(mb_rom* R, int on) {
     }
     R->d.tc = on;
     R->tc_forced = true;
+    return MB_OK;
+}
+
+extern "C" int mb_debug_rom_slot(mb_rom* R, int b, int* failed, int* pass_its, float* last_norm, int* escalated) {
+    if (!R || b < 0 || b >= R->w.B || !failed || !pass_its || !last_norm || !escalated) {
+        set_error("mb_debug_rom_slot: invalid argument");
+        return MB_EINVAL;
+    }
+    const RomWork& w = R->w;
+    if (cudaMemcpy(failed, w.failed + b, 4, cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(pass_its, w.pit + b, 4, cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(last_norm, w.dnprev + b, 4, cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(escalated, w.hp + b, 4, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return cuda_fail(cudaGetLastError(), "mb_debug_rom_slot");
     return MB_OK;
 }
 

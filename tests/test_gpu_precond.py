@@ -352,7 +352,7 @@ def test_precond_drives_fgmres(params):
     E = sp.diags(1.0 / gc.debug_fine()[2].astype(np.float64))
     Ae = (E @ A).tocsr()                 # the row-equilibrated Krylov operator
     b = np.random.default_rng(5).standard_normal(gc.n)
-    x, its, rel = _fgmres(lambda v: Ae @ v, b, lambda r: gc.debug_precond(u, gate, dt, r))
+    x, its, rel = _fgmres(lambda v: Ae @ v, b, lambda r: gc.debug_precond(u, gate, dt, r), maxit=200)
     # with the collectors at 1e5 S/m and the foil at 1e7 S/m next to 1-100 S/m
     # electrodes this unrestarted FGMRES takes about 135 iterations
     assert rel <= 1e-6 and its <= 200, (its, rel)
