@@ -330,7 +330,9 @@ int mb_rom_destroy(mb_rom* rom);
  * converged at lam m <= 1e-12 (the same scaled norm) or at a full step with
  * m <= 1e-10 that did not halve the previous m (the rounding floor of the
  * reconstruction), at most 30 iterations;
- * plating active-set passes as mb_step (at most 3).  The state, the
+ * plating active-set passes as mb_step (at most 3); an instance whose step
+ * fails retakes it from the state before it as 2^h steps of dt / 2^h, h = 1
+ * .. max_halvings of the cell's options (as mb_step halves its step).  The state, the
  * interpolated terms and the residual are FP64 and the reconstruction at the
  * points float-float (~2^-44 relative; the converged result is the FP64 one
  * to that rounding); the Newton matrix is formed with FP32 accuracy (three TF32

@@ -431,66 +431,91 @@ def equilibrated_solve(J, b):
     return c * np.linalg.solve(Jr * c[None, :], r * b)
 
 
-def solve(rom, mu, s_i0, k_pl, dt, n_steps, tol=TOL_NEWTON, maxit=30):
-    """Reduced trajectory from a0: returns dict with a (n_steps+1, N_r),
-    V_cell and s_ac per step (index 0 = initial), newton iterations and
-    gate flips."""
+class _NoConvergence(RuntimeError):
+    pass
+
+
+def _step(rom, a_old, mu, s_i0, k_pl, dt, tol, maxit):
+    """One implicit Euler step of the reduced model from a_old: the plating
+    active-set passes, each a reduced Newton iteration.  Returns (a, Newton
+    iterations, gate flips); raises _NoConvergence."""
     cell = rom.cell
     N = cell.N
+    its = flips = 0
+    u_old = rom.U @ a_old
+    n_old = u_old[2 * N:]
+    gate = cell.gate_at(u_old, n_old)
+    for npass in range(1, MAX_PASSES + 1):
+        a = a_old.copy()
+        ok = False
+        dv_prev = np.inf
+        for it in range(1, maxit + 1):
+            r = reduced_residual(rom, a, a_old, dt, mu, s_i0, k_pl, gate)
+            Jr = reduced_jacobian(rom, a, dt, s_i0, k_pl, gate)
+            d = equilibrated_solve(Jr, -r)
+            ud = rom.Uloc @ d
+            du = np.abs(ud) / rom.us_loc
+            dn = np.max(du) if len(du) else 0.0
+            if not np.isfinite(dn):
+                break
+            # the step length as the full-order Newton takes it: the closure's
+            # voxel unknowns (c, phi) in their scales, its plated inventories
+            # relative to max(n_c, |n|) of the current reconstruction.  The
+            # reduced iteration also stops in these scales: a plated layer of
+            # ~1e3 n_c (Sec. workflow:degradation_modeling) strips at currents
+            # whose exp sensitivity turns the rounding of the reconstruction
+            # (~1e-16 of phi in FP64) into updates above 1e-12 n_c
+            vox = rom.closure < 2 * N
+            du_cap = du.copy()
+            if np.any(~vox):
+                n_cur = (rom.Uloc @ a)[~vox]
+                du_cap[~vox] = np.abs(ud[~vox]) / np.maximum(cell.nc, np.abs(n_cur))
+            dv = np.max(du_cap) if len(du_cap) else 0.0
+            lam = 1.0 if dv <= DELTA_MAX else DELTA_MAX / dv
+            a = a + lam * d
+            its += 1
+            # converged below tol, or at a full step below TOL_FLOOR that no longer
+            # halves the previous update (the rounding floor of the reconstruction;
+            # Newton's own convergence is quadratic)
+            if lam * dv <= tol or (lam == 1.0 and dv <= TOL_FLOOR and it >= 2 and dv >= 0.5 * dv_prev):
+                ok = True
+                break
+            dv_prev = dv
+        if not ok:
+            raise _NoConvergence("oracle reduced Newton did not converge")
+        g2 = cell.gate_at(rom.U @ a, n_old)
+        cf = rom.closure_faces
+        nflip = int(np.count_nonzero(g2[cf] != gate[cf]))
+        if nflip == 0 or npass == MAX_PASSES:
+            break
+        flips += nflip
+        gate = g2
+    return a, its, flips
+
+
+def solve(rom, mu, s_i0, k_pl, dt, n_steps, tol=TOL_NEWTON, maxit=30, max_halvings=0):
+    """Reduced trajectory from a0: returns dict with a (n_steps+1, N_r),
+    V_cell and s_ac per step (index 0 = initial), newton iterations and
+    gate flips.  A step that fails is retaken from the state before it as
+    2^h steps of dt / 2^h, h = 1 .. max_halvings (the full-order step's dt
+    halving); RuntimeError when the smallest substeps fail too."""
     a = rom.a0.copy()
     A_traj = [a.copy()]
     its_total = 0
     flips_total = 0
     for _ in range(n_steps):
         a_old = a.copy()
-        u_old = rom.U @ a_old
-        n_old = u_old[2 * N:]
-        gate = cell.gate_at(u_old, n_old)
-        for npass in range(1, MAX_PASSES + 1):
-            a = a_old.copy()
-            ok = False
-            dv_prev = np.inf
-            for it in range(1, maxit + 1):
-                r = reduced_residual(rom, a, a_old, dt, mu, s_i0, k_pl, gate)
-                Jr = reduced_jacobian(rom, a, dt, s_i0, k_pl, gate)
-                d = equilibrated_solve(Jr, -r)
-                ud = rom.Uloc @ d
-                du = np.abs(ud) / rom.us_loc
-                dn = np.max(du) if len(du) else 0.0
-                if not np.isfinite(dn):
-                    break
-                # the step length as the full-order Newton takes it: the closure's
-                # voxel unknowns (c, phi) in their scales, its plated inventories
-                # relative to max(n_c, |n|) of the current reconstruction.  The
-                # reduced iteration also stops in these scales: a plated layer of
-                # ~1e3 n_c (Sec. workflow:degradation_modeling) strips at currents
-                # whose exp sensitivity turns the rounding of the reconstruction
-                # (~1e-16 of phi in FP64) into updates above 1e-12 n_c
-                vox = rom.closure < 2 * N
-                du_cap = du.copy()
-                if np.any(~vox):
-                    n_cur = (rom.Uloc @ a)[~vox]
-                    du_cap[~vox] = np.abs(ud[~vox]) / np.maximum(cell.nc, np.abs(n_cur))
-                dv = np.max(du_cap) if len(du_cap) else 0.0
-                lam = 1.0 if dv <= DELTA_MAX else DELTA_MAX / dv
-                a = a + lam * d
-                its_total += 1
-                # converged below tol, or at a full step below TOL_FLOOR that no longer
-                # halves the previous update (the rounding floor of the reconstruction;
-                # Newton's own convergence is quadratic)
-                if lam * dv <= tol or (lam == 1.0 and dv <= TOL_FLOOR and it >= 2 and dv >= 0.5 * dv_prev):
-                    ok = True
-                    break
-                dv_prev = dv
-            if not ok:
-                raise RuntimeError("oracle reduced Newton did not converge")
-            g2 = cell.gate_at(rom.U @ a, n_old)
-            cf = rom.closure_faces
-            nflip = int(np.count_nonzero(g2[cf] != gate[cf]))
-            if nflip == 0 or npass == MAX_PASSES:
+        for h in range(0, max_halvings + 1):
+            try:
+                a = a_old.copy()
+                for _k in range(2 ** h):
+                    a, its, flips = _step(rom, a, mu, s_i0, k_pl, dt / 2 ** h, tol, maxit)
+                    its_total += its
+                    flips_total += flips
                 break
-            flips_total += nflip
-            gate = g2
+            except _NoConvergence:
+                if h == max_halvings:
+                    raise RuntimeError("oracle reduced Newton did not converge")
         A_traj.append(a.copy())
     A_traj = np.array(A_traj)
     return dict(a=A_traj, V_cell=A_traj @ rom.s_cp, s_ac=A_traj @ rom.s_ac,

@@ -134,6 +134,9 @@ struct RomWork {
     int* tcerr = nullptr;      // device: a bounded wait of the tcgen05 GEMM gave up
     bool graph_failed = false; // the graph could not be built: host-driven steps
     int g_tc = -1, g_ir = -1;  // the GEMM variant and escalation mode the graph was captured with
+    double* a_hold = nullptr;  // B x Nr: the state before the step (dt halving restarts from it)
+    int* retry = nullptr;      // B: instances retaking the step with halved dt
+    std::vector<double> hprm;  // host copy of the instance parameters (RP per instance)
     std::vector<void*> bufs;
 };
 
@@ -499,11 +502,11 @@ k_rom_jac(RomDev d, int B, int nlist, const int* __restrict__ alist, const doubl
 // thread issues the MMAs; their completion is signalled on an mbarrier by
 // tcgen05.commit.  Every wait is bounded: on a timeout the CTA sets *err,
 // waits (bounded) for its MMAs, frees its tensor memory and returns.
-constexpr int T5_M = 128, T5_K = 32, T5_THREADS = 128, T5_NMAX = 256;
+constexpr int T5_M = 128, T5_K = 32, T5_THREADS = 256, T5_NMAX = 256;
 constexpr int T5_SPIN = 1 << 22;
 constexpr int T5_A_BYTES = T5_M * T5_K * 4;            // one A tile (16 KB)
 constexpr int T5_B_BYTES = T5_NMAX * T5_K * 4;         // one B tile (32 KB)
-constexpr int T5_TILES = 2 * T5_A_BYTES + 2 * T5_B_BYTES;   // 96 KB
+constexpr int T5_TILES = 2 * T5_A_BYTES + 2 * T5_B_BYTES;   // 96 KB per pipeline stage (two stages)
 // the CTA's shared memory is padded well beyond the tiles, so that no
 // descriptor offset of the layout above can leave the allocation
 constexpr int T5_SMEM = 225 * 1024;
@@ -581,9 +584,17 @@ __global__ void __launch_bounds__(T5_THREADS, 1)
 k_rom_jac5(RomDev d, int B, int nlist, const int* __restrict__ alist, const double* __restrict__ prm,
            const float* __restrict__ GU, const int* __restrict__ hp, float* __restrict__ J,
            const int* __restrict__ dit, const int* __restrict__ dnlist, int* __restrict__ err) {
+    // Two pipeline stages of (A head, A tail, B head, B tail) tiles: while the
+    // tensor core runs the MMAs of slice k - 1 from one stage, the CTA fills
+    // the other with slice k (A: the 128 column owners split their
+    // prefetched GU values into TF32 head and tail; B: all 256 threads copy
+    // the precomputed P head and tail rows), then the prefetch of slice k + 1
+    // goes out.  A stage is refilled only after the commit of the MMAs that
+    // read it (slice k - 2) has arrived on its mbarrier.
     extern __shared__ __align__(1024) uint8_t t5_raw[];
-    __shared__ __align__(8) uint64_t bar;
+    __shared__ __align__(8) uint64_t bar[2];
     __shared__ uint32_t tmem_slot;
+    __shared__ int s_ok;   // thread 0's bounded wait, broadcast (every thread leaves the loop together)
     const int Nr = d.Nr, M = d.M, NP = d.Npad, MP = d.Mpad;
     if (dit) {
         if (*dit > 0) nlist = *dnlist;
@@ -593,13 +604,13 @@ k_rom_jac5(RomDev d, int B, int nlist, const int* __restrict__ alist, const doub
     const int64_t gstride = (int64_t)B * Nr;
     const int c0 = blockIdx.x * T5_M;
     if (c0 >= ncol) return;
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    uint8_t* const Ab = t5_raw;
-    uint8_t* const As = t5_raw + T5_A_BYTES;
-    uint8_t* const Bb = t5_raw + 2 * T5_A_BYTES;
-    uint8_t* const Bs = Bb + T5_B_BYTES;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const bool owner = tid < T5_M;   // owns GEMM column c0 + tid (its A row)
     const uint32_t lbo_a = T5_M * 16, lbo_b = (uint32_t)NP * 16;
-    if (tid == 0) t5_mbar_init(&bar);
+    if (tid == 0) {
+        t5_mbar_init(&bar[0]);
+        t5_mbar_init(&bar[1]);
+    }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(t5_smem(&tmem_slot)),
                      "r"(T5_NMAX));
@@ -609,9 +620,8 @@ k_rom_jac5(RomDev d, int B, int nlist, const int* __restrict__ alist, const doub
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = tmem_slot;
-    // this thread's GEMM column (its A row), fixed over the K loop
     const int c = c0 + tid;
-    const bool cvalid = c < ncol;
+    const bool cvalid = owner && c < ncol;
     int64_t boff = 0;
     if (cvalid) {
         const int l = c / Nr;
@@ -619,7 +629,7 @@ k_rom_jac5(RomDev d, int B, int nlist, const int* __restrict__ alist, const doub
     }
     const uint32_t idesc = t5_idesc(T5_M, NP);
     bool ok = true;
-    int nslices = 0;
+    const int nsl = (M + T5_K - 1) / T5_K;
     float ra[T5_K];
     auto fetch = [&](int k0) {
 #pragma unroll
@@ -628,21 +638,32 @@ k_rom_jac5(RomDev d, int B, int nlist, const int* __restrict__ alist, const doub
             ra[kk] = (cvalid && k < M) ? GU[(int64_t)k * gstride + boff] : 0.f;
         }
     };
-    fetch(0);
-    for (int k0 = 0; k0 < M; k0 += T5_K, ++nslices) {
-        // the previous slice's MMAs have read the tiles
-        if (nslices > 0 && !t5_wait(&bar, (uint32_t)(nslices - 1) & 1u)) { ok = false; break; }
-        // A: this thread's column, K chunks of 4 as 16-byte stores (head and tail)
-#pragma unroll
-        for (int q = 0; q < T5_K / 4; ++q) {
-            uint32_t hb[4], hs[4];
-#pragma unroll
-            for (int e = 0; e < 4; ++e) tf32_split(ra[4 * q + e], hb[e], hs[e]);
-            const uint32_t off = (uint32_t)q * lbo_a + (uint32_t)(tid >> 3) * 128u + (uint32_t)(tid & 7) * 16u;
-            *reinterpret_cast<uint4*>(Ab + off) = make_uint4(hb[0], hb[1], hb[2], hb[3]);
-            *reinterpret_cast<uint4*>(As + off) = make_uint4(hs[0], hs[1], hs[2], hs[3]);
+    if (owner) fetch(0);
+    int k = 0;
+    for (; k < nsl; ++k) {
+        const int st = k & 1;
+        uint8_t* const Ab = t5_raw + st * T5_TILES;
+        uint8_t* const As = Ab + T5_A_BYTES;
+        uint8_t* const Bb = Ab + 2 * T5_A_BYTES;
+        uint8_t* const Bs = Bb + T5_B_BYTES;
+        // the MMAs of slice k - 2 have read this stage (thread 0 waits, bounded)
+        if (k >= 2) {
+            if (tid == 0) s_ok = t5_wait(&bar[st], (uint32_t)((k - 2) >> 1) & 1u) ? 1 : 0;
+            __syncthreads();
+            if (!s_ok) { ok = false; break; }
         }
-        // B: rows n < NP of the precomputed P head and tail, 16-byte chunks
+        if (owner) {
+#pragma unroll
+            for (int q = 0; q < T5_K / 4; ++q) {
+                uint32_t hb[4], hs[4];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) tf32_split(ra[4 * q + e], hb[e], hs[e]);
+                const uint32_t off = (uint32_t)q * lbo_a + (uint32_t)(tid >> 3) * 128u + (uint32_t)(tid & 7) * 16u;
+                *reinterpret_cast<uint4*>(Ab + off) = make_uint4(hb[0], hb[1], hb[2], hb[3]);
+                *reinterpret_cast<uint4*>(As + off) = make_uint4(hs[0], hs[1], hs[2], hs[3]);
+            }
+        }
+        const int k0 = k * T5_K;
         for (int e = tid; e < NP * (T5_K / 4); e += T5_THREADS) {
             const int n = e >> 3, q = e & 7;
             const int64_t g = (int64_t)n * MP + k0 + 4 * q;
@@ -659,21 +680,28 @@ k_rom_jac5(RomDev d, int B, int nlist, const int* __restrict__ alist, const doub
                 const uint32_t ka = (uint32_t)(2 * s) * lbo_a, kb = (uint32_t)(2 * s) * lbo_b;
                 const uint64_t dab = t5_desc(t5_smem(Ab) + ka, lbo_a, 128), das = t5_desc(t5_smem(As) + ka, lbo_a, 128);
                 const uint64_t dbb = t5_desc(t5_smem(Bb) + kb, lbo_b, 128), dbs = t5_desc(t5_smem(Bs) + kb, lbo_b, 128);
-                t5_mma(tmem, das, dbb, idesc, (k0 > 0 || s > 0) ? 1u : 0u);
+                t5_mma(tmem, das, dbb, idesc, (k > 0 || s > 0) ? 1u : 0u);
                 t5_mma(tmem, dab, dbs, idesc, 1u);
                 t5_mma(tmem, dab, dbb, idesc, 1u);
             }
-            t5_commit(&bar);
+            t5_commit(&bar[st]);
         }
-        if (k0 + T5_K < M) fetch(k0 + T5_K);   // the next slice in flight during the MMAs
+        if (owner && k + 1 < nsl) fetch((k + 1) * T5_K);   // the next slice in flight during the MMAs
     }
-    if (ok && nslices > 0 && !t5_wait(&bar, (uint32_t)(nslices - 1) & 1u)) ok = false;
+    // every MMA has completed once the last slice's commit has arrived (a commit
+    // tracks all earlier tcgen05 operations of the issuing thread)
+    const int last = ok ? nsl - 1 : k - 1;
+    if (ok && nsl > 0) {
+        if (tid == 0) s_ok = t5_wait(&bar[last & 1], (uint32_t)(last >> 1) & 1u) ? 1 : 0;
+        __syncthreads();
+        ok = s_ok != 0;
+    }
     if (!ok) {
         if (tid == 0) {
             atomicOr(err, 1);
-            t5_wait(&bar, (uint32_t)(nslices - 1) & 1u);   // bounded: the MMAs in flight
+            if (last >= 0) t5_wait(&bar[last & 1], (uint32_t)(last >> 1) & 1u);   // bounded: the MMAs in flight
         }
-    } else {
+    } else if (warp < 4) {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         // epilogue: warp w reads TMEM lanes 32w.. (its 32 columns), 16 rows per load
         const int l = cvalid ? c / Nr : 0, j = c - l * Nr;
@@ -1741,6 +1769,8 @@ static int rom_work_alloc(mb_rom* R, int B) {
     w.flips = rom_alloc<long long>(L, B);
     w.V = rom_alloc<double>(L, (size_t)B);
     w.S = rom_alloc<double>(L, (size_t)B);
+    w.a_hold = rom_alloc<double>(L, (size_t)B * d.Nr);
+    w.retry = rom_alloc<int>(L, B);
     for (void* p : L)
         if (!p) { rom_work_free(w); return MB_ENOMEM; }
     return MB_OK;
@@ -2329,6 +2359,7 @@ static int rom_batch_begin(mb_rom* R, int B, const mb_rom_params* prm, double dt
     RomWork& w = R->w;
     cudaStream_t s = R->cell->stream;
     MB_CUDA(cudaMemcpyAsync(w.prm, hp.data(), 8 * hp.size(), cudaMemcpyHostToDevice, s));
+    w.hprm = hp;
     const int64_t n = (int64_t)B * R->d.Nr;
     k_rom_batch_start<<<(unsigned)std::min<int64_t>((n + 255) / 256, 4096), 256, 0, s>>>(
         R->d, B, w.a, w.failed, w.its, w.flips, w.hp), count_launch(R->cell);
@@ -2365,6 +2396,62 @@ extern "C" int mb_rom_basis(mb_rom* R, double* U) {
     return MB_OK;
 }
 
+namespace mb {
+// One time step of every occupied slot with dt halving, as the full-order
+// step does: the instances whose reduced Newton failed in the step restart
+// from the state before it and take 2^h steps of dt / 2^h (h = 1 ..
+// max_halvings, all in the same batch, the other slots held as failed
+// meanwhile); an instance fails only when the smallest substeps fail too.
+int rom_step_halving(mb_rom* R, int max_halvings) {
+    RomWork& w = R->w;
+    const int B = w.B, Nr = R->d.Nr;
+    cudaStream_t s = R->cell->stream;
+    const unsigned nb = (unsigned)(((int64_t)B * Nr + 255) / 256);
+    std::vector<int> f0(B), f1(B);
+    if (max_halvings > 0) {
+        MB_CUDA(cudaMemcpyAsync(f0.data(), w.failed, 4 * B, cudaMemcpyDeviceToHost, s));
+        MB_CUDA(cudaMemcpyAsync(w.a_hold, w.a, 8 * (size_t)B * Nr, cudaMemcpyDeviceToDevice, s));
+    }
+    int rc = rom_batch_step(R);
+    if (rc || max_halvings <= 0) return rc;
+    MB_CUDA(cudaMemcpyAsync(f1.data(), w.failed, 4 * B, cudaMemcpyDeviceToHost, s));
+    MB_CUDA(cudaStreamSynchronize(s));
+    std::vector<int> retry(B, 0);
+    int nretry = 0;
+    for (int b = 0; b < B; ++b)
+        if (f1[b] && !f0[b]) { retry[b] = 1; ++nretry; }
+    if (!nretry) return MB_OK;
+    std::vector<double> hp = w.hprm;
+    for (int h = 1; h <= max_halvings && nretry; ++h) {
+        // retried slots restart from the held state with dt / 2^h; the others are held
+        std::vector<int> hold(B);
+        for (int b = 0; b < B; ++b) {
+            hold[b] = retry[b] ? 0 : 1;
+            hp[(size_t)RP * b + 3] = retry[b] ? w.hprm[(size_t)RP * b + 3] * (double)(1 << h) : w.hprm[(size_t)RP * b + 3];
+        }
+        MB_CUDA(cudaMemcpyAsync(w.retry, retry.data(), 4 * B, cudaMemcpyHostToDevice, s));
+        MB_CUDA(cudaMemcpyAsync(w.failed, hold.data(), 4 * B, cudaMemcpyHostToDevice, s));
+        MB_CUDA(cudaMemcpyAsync(w.prm, hp.data(), 8 * hp.size(), cudaMemcpyHostToDevice, s));
+        k_rom_copy<<<nb, 256, 0, s>>>(Nr, B, w.retry, w.a_hold, w.a), count_launch(R->cell);
+        MB_CUDA(cudaStreamSynchronize(s));   // the host buffers above go out of scope
+        for (int k = 0; k < (1 << h); ++k)
+            if ((rc = rom_batch_step(R))) return rc;
+        MB_CUDA(cudaMemcpy(f1.data(), w.failed, 4 * B, cudaMemcpyDeviceToHost));
+        nretry = 0;
+        for (int b = 0; b < B; ++b) {
+            retry[b] = retry[b] && f1[b];
+            nretry += retry[b];
+        }
+    }
+    // the parameters and the failure flags of every slot back (the held ones as before the step)
+    for (int b = 0; b < B; ++b) f1[b] = f0[b] || retry[b];
+    MB_CUDA(cudaMemcpyAsync(w.failed, f1.data(), 4 * B, cudaMemcpyHostToDevice, s));
+    MB_CUDA(cudaMemcpyAsync(w.prm, w.hprm.data(), 8 * w.hprm.size(), cudaMemcpyHostToDevice, s));
+    MB_CUDA(cudaStreamSynchronize(s));
+    return MB_OK;
+}
+}  // namespace mb
+
 static int rom_solve(mb_rom* R, int B, const mb_rom_params* prm, int n_steps, double dt, double* V_out,
                      double* sac_out, double* a_final, double* a_traj, mb_rom_info* info) {
     const int ncol = n_steps + 1;
@@ -2373,7 +2460,7 @@ static int rom_solve(mb_rom* R, int B, const mb_rom_params* prm, int n_steps, do
     std::vector<double> hV(B), hS(B), ha(a_traj ? (size_t)B * R->d.Nr : 0);
     std::vector<int> hf(B);
     for (int step = 0; step <= n_steps; ++step) {
-        if (step > 0 && (rc = rom_batch_step(R))) return rc;
+        if (step > 0 && (rc = rom_step_halving(R, R->cell->opt.max_halvings))) return rc;
         if ((rc = rom_batch_outputs(R, hV.data(), hS.data(), hf.data()))) return rc;
         for (int b = 0; b < B; ++b) {
             V_out[(size_t)b * ncol + step] = hf[b] ? NAN : hV[b];
@@ -2609,7 +2696,9 @@ extern "C" int mb_rom_estimate_batch(mb_rom* R, mb_rom* Rv, double theta, int B,
     std::vector<int> hf(B), hfv(B);
     cudaStream_t s = R->cell->stream;
     for (int step = 0; step <= n_steps; ++step) {
-        if (step > 0 && ((rc = rom_batch_step(R)) || (rc = rom_batch_step(Rv)))) return rc;
+        if (step > 0 && ((rc = rom_step_halving(R, R->cell->opt.max_halvings)) ||
+                         (rc = rom_step_halving(Rv, Rv->cell->opt.max_halvings))))
+            return rc;
         // both streams are idle after their outputs are read
         if ((rc = rom_batch_outputs(R, hV.data(), hS.data(), hf.data())) ||
             (rc = rom_batch_outputs(Rv, hVv.data(), hSv.data(), hfv.data())))

@@ -181,3 +181,29 @@ def test_error_estimate_is_the_error_for_an_exact_validation_model(trained):
                                            for n in range(len(traj))))
     same = R.error_estimate(small, small, os_["a"], os_["a"])
     assert all(np.all(v == 0.0) for v in same.values())
+
+
+def test_dt_halving_retakes_failed_steps(trained, monkeypatch):
+    """A failed step is retaken from the state before it as 2^h steps of
+    dt / 2^h, h = 1 .. max_halvings.  The failure is planted on the host: the
+    step raises for dt > 0.3, so the solve must settle at h = 2 and equal four
+    direct steps of 0.25 (a wrong restart state, dt or substep count breaks the
+    equality), and with max_halvings = 1 it must fail."""
+    cell, mu, snaps, traj, rom = trained
+    real = R._step
+    calls = []
+
+    def flaky(rom_, a_old, mu_, s_i0, k_pl, dt, tol, maxit):
+        calls.append(dt)
+        if dt > 0.3:
+            raise R._NoConvergence("planted")
+        return real(rom_, a_old, mu_, s_i0, k_pl, dt, tol, maxit)
+
+    direct = R.solve(rom, mu, 1.0, 1.0, 0.25, 4)
+    monkeypatch.setattr(R, "_step", flaky)
+    out = R.solve(rom, mu, 1.0, 1.0, 1.0, 1, max_halvings=3)
+    assert calls == [1.0, 0.5, 0.25, 0.25, 0.25, 0.25]
+    assert np.array_equal(out["a"][-1], direct["a"][-1])
+    assert out["newton_its"] == direct["newton_its"]
+    with pytest.raises(RuntimeError):
+        R.solve(rom, mu, 1.0, 1.0, 1.0, 1, max_halvings=1)
