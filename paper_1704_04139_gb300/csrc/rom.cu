@@ -83,8 +83,8 @@ struct RomDev {
     double* Ms = nullptr;      // Nr x Nr
     double* Alin = nullptr;    // Nr x Nr
     float* Ptf = nullptr;      // FP32 copies for the Newton matrix: P^T (M x Nr), Ms, Alin, UlocR, UlocC, us
-    float* Pbf = nullptr;      // TF32 head and tail of P (Npad x Mpad, row-major, zero padded): the
-    float* Psf = nullptr;      //   tcgen05 GEMM's B operand
+    float* Pbf = nullptr;      // TF32 head and tail of P, the tcgen05 GEMM's B operand, stored per K
+    float* Psf = nullptr;      //   slice of 32 in its shared-memory tile layout (Mpad/32 tiles of Npad x 32)
     int Npad = 0, Mpad = 0;    // Nr rounded up to 16, M rounded up to the K slice
     float* Msf = nullptr;
     float* Alinf = nullptr;
@@ -498,10 +498,13 @@ k_rom_jac(RomDev d, int B, int nlist, const int* __restrict__ alist, const doubl
 // (row r, element k at (k/4) LBO + (r/8) 128 + (r%8) 16 + (k%4) 4 bytes, LBO =
 // rows x 16), each operand as a TF32 head and tail (the 3xTF32 split of the
 // mma.sync kernel: small*big + big*small + big*big per K step), the P head and
-// tail precomputed (Pbf, Psf: N_pad x M_pad, row-major, zero padded).  One
-// thread issues the MMAs; their completion is signalled on an mbarrier by
-// tcgen05.commit.  Every wait is bounded: on a timeout the CTA sets *err,
-// waits (bounded) for its MMAs, frees its tensor memory and returns.
+// tail precomputed once per model directly in that tile layout, one
+// contiguous N_pad x 32 tile per K slice (Pbf, Psf), so that each slice's B
+// tiles arrive by two bulk asynchronous copies (cp.async.bulk, completion
+// counted in bytes on an mbarrier).  One thread issues the copies and the
+// MMAs; the MMAs' completion is signalled on an mbarrier by tcgen05.commit.
+// Every wait is bounded: on a timeout the CTA sets *err, waits (bounded) for
+// its copies and MMAs in flight, frees its tensor memory and returns.
 constexpr int T5_M = 128, T5_K = 32, T5_THREADS = 256, T5_NMAX = 256;
 constexpr int T5_SPIN = 1 << 22;
 constexpr int T5_A_BYTES = T5_M * T5_K * 4;            // one A tile (16 KB)
@@ -568,7 +571,9 @@ __device__ inline void t5_ld16(uint32_t taddr, float (&v)[16]) {
 }
 
 // TF32 head and tail of P for the tcgen05 GEMM's B operand, from its K-major
-// FP32 copy Ptf (M x Nr): Pbf, Psf (Npad x Mpad, row-major, zero padded)
+// FP32 copy Ptf (M x Nr), zero padded to Npad x Mpad and stored tile by tile:
+// element (n, k) of K slice s = k / 32 at s Npad 32 + the byte offset
+// (k%32 / 4) (Npad 16) + (n/8) 128 + (n%8) 16 + (k%4) 4 of the kernel's layout
 __global__ void k_rom_psplit(int Nr, int M, int Npad, int Mpad, const float* __restrict__ Ptf,
                              float* __restrict__ Pbf, float* __restrict__ Psf) {
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -576,8 +581,21 @@ __global__ void k_rom_psplit(int Nr, int M, int Npad, int Mpad, const float* __r
     const int n = (int)(e / Mpad), k = (int)(e % Mpad);
     uint32_t hb = 0u, hs = 0u;
     if (n < Nr && k < M) tf32_split(Ptf[(int64_t)k * Nr + n], hb, hs);
-    Pbf[e] = __uint_as_float(hb);
-    Psf[e] = __uint_as_float(hs);
+    const int sl = k / T5_K, kk = k % T5_K;
+    const int64_t o = (int64_t)sl * Npad * T5_K +
+                      ((int64_t)(kk >> 2) * Npad * 16 + (n >> 3) * 128 + (n & 7) * 16 + (kk & 3) * 4) / 4;
+    Pbf[o] = __uint_as_float(hb);
+    Psf[o] = __uint_as_float(hs);
+}
+
+__device__ inline void t5_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(t5_smem(bar)), "r"(bytes) : "memory");
+}
+// global -> shared bulk copy of `bytes` (16-byte aligned, a multiple of 16), counted on bar
+__device__ inline void t5_bulk(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(t5_smem(dst)), "l"(src), "r"(bytes), "r"(t5_smem(bar))
+                 : "memory");
 }
 
 __global__ void __launch_bounds__(T5_THREADS, 1)
@@ -586,16 +604,18 @@ k_rom_jac5(RomDev d, int B, int nlist, const int* __restrict__ alist, const doub
            const int* __restrict__ dit, const int* __restrict__ dnlist, int* __restrict__ err) {
     // Two pipeline stages of (A head, A tail, B head, B tail) tiles: while the
     // tensor core runs the MMAs of slice k - 1 from one stage, the CTA fills
-    // the other with slice k (A: the 128 column owners split their
-    // prefetched GU values into TF32 head and tail; B: all 256 threads copy
-    // the precomputed P head and tail rows), then the prefetch of slice k + 1
-    // goes out.  A stage is refilled only after the commit of the MMAs that
-    // read it (slice k - 2) has arrived on its mbarrier.
+    // the other with slice k (B: two bulk copies of the precomputed P head and
+    // tail tiles, issued first; A: the 128 column owners split their
+    // prefetched GU values into TF32 head and tail), then the prefetch of
+    // slice k + 1 goes out.  A stage is refilled only after the commit of the
+    // MMAs that read it (slice k - 2) has arrived on its mbarrier.
     extern __shared__ __align__(1024) uint8_t t5_raw[];
-    __shared__ __align__(8) uint64_t bar[2];
+    __shared__ __align__(8) uint64_t bar[2];    // MMA completion per stage
+    __shared__ __align__(8) uint64_t barb[2];   // B-tile arrival per stage
     __shared__ uint32_t tmem_slot;
     __shared__ int s_ok;   // thread 0's bounded wait, broadcast (every thread leaves the loop together)
-    const int Nr = d.Nr, M = d.M, NP = d.Npad, MP = d.Mpad;
+    const int Nr = d.Nr, M = d.M, NP = d.Npad;
+    const uint32_t tile_b = (uint32_t)NP * T5_K * 4;   // bytes of one B tile (head or tail)
     if (dit) {
         if (*dit > 0) nlist = *dnlist;
         else alist = nullptr;
@@ -610,6 +630,8 @@ k_rom_jac5(RomDev d, int B, int nlist, const int* __restrict__ alist, const doub
     if (tid == 0) {
         t5_mbar_init(&bar[0]);
         t5_mbar_init(&bar[1]);
+        t5_mbar_init(&barb[0]);
+        t5_mbar_init(&barb[1]);
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(t5_smem(&tmem_slot)),
@@ -629,6 +651,7 @@ k_rom_jac5(RomDev d, int B, int nlist, const int* __restrict__ alist, const doub
     }
     const uint32_t idesc = t5_idesc(T5_M, NP);
     bool ok = true;
+    int bcopy = -1;   // a slice whose B copies may still be in flight after a timeout
     const int nsl = (M + T5_K - 1) / T5_K;
     float ra[T5_K];
     auto fetch = [&](int k0) {
@@ -652,6 +675,11 @@ k_rom_jac5(RomDev d, int B, int nlist, const int* __restrict__ alist, const doub
             __syncthreads();
             if (!s_ok) { ok = false; break; }
         }
+        if (tid == 0) {   // B tiles of slice k: bulk copies counted on barb[st]
+            t5_expect_tx(&barb[st], 2u * tile_b);
+            t5_bulk(Bb, d.Pbf + (int64_t)k * NP * T5_K, tile_b, &barb[st]);
+            t5_bulk(Bs, d.Psf + (int64_t)k * NP * T5_K, tile_b, &barb[st]);
+        }
         if (owner) {
 #pragma unroll
             for (int q = 0; q < T5_K / 4; ++q) {
@@ -663,16 +691,14 @@ k_rom_jac5(RomDev d, int B, int nlist, const int* __restrict__ alist, const doub
                 *reinterpret_cast<uint4*>(As + off) = make_uint4(hs[0], hs[1], hs[2], hs[3]);
             }
         }
-        const int k0 = k * T5_K;
-        for (int e = tid; e < NP * (T5_K / 4); e += T5_THREADS) {
-            const int n = e >> 3, q = e & 7;
-            const int64_t g = (int64_t)n * MP + k0 + 4 * q;
-            const uint32_t off = (uint32_t)q * lbo_b + (uint32_t)(n >> 3) * 128u + (uint32_t)(n & 7) * 16u;
-            *reinterpret_cast<float4*>(Bb + off) = *reinterpret_cast<const float4*>(d.Pbf + g);
-            *reinterpret_cast<float4*>(Bs + off) = *reinterpret_cast<const float4*>(d.Psf + g);
-        }
+        if (tid == 0) s_ok = t5_wait(&barb[st], (uint32_t)(k >> 1) & 1u) ? 1 : 0;   // the B tiles have landed
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
+        if (!s_ok) {
+            ok = false;
+            bcopy = k;
+            break;
+        }
         if (tid == 0) {
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 #pragma unroll
@@ -700,6 +726,7 @@ k_rom_jac5(RomDev d, int B, int nlist, const int* __restrict__ alist, const doub
         if (tid == 0) {
             atomicOr(err, 1);
             if (last >= 0) t5_wait(&bar[last & 1], (uint32_t)(last >> 1) & 1u);   // bounded: the MMAs in flight
+            if (bcopy >= 0) t5_wait(&barb[bcopy & 1], (uint32_t)(bcopy >> 1) & 1u);   // bounded: the copies
         }
     } else if (warp < 4) {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
