@@ -382,10 +382,8 @@ def _serve_requests(rng, n, i1, i1_fom):
     return out
 
 
-def serve_run(B, params, rom, i1, args, slots=512, workers=4):
-    """Continuous batching under Poisson arrivals.  The slot count covers the
-    requests in service at the arrival rate (Little's law: ~12 requests/s x
-    ~1,550 steps of ~16 ms on average exceeded 256 slots).  The server's capacity is
+def serve_run(B, params, rom, i1, args, slots=256, workers=4, load=0.7):
+    """Continuous batching under Poisson arrivals.  The server's capacity is
     measured on a burst of twice its slot count drawn from the same mix
     (reduced and full-order requests), and requests then arrive at 0.8 of it.
     Reduced requests run in the resident slot batch of `rom`; full-order
@@ -414,7 +412,7 @@ def serve_run(B, params, rom, i1, args, slots=512, workers=4):
                 left.discard(t)
         time.sleep(0.001)
     cap = len(burst) / (time.perf_counter() - t0)
-    rate = 0.8 * cap
+    rate = load * cap
     rng = np.random.default_rng(51)
     n_req = args.serve_requests
     reqs = _serve_requests(rng, n_req, i1, i1_fom)
@@ -469,11 +467,11 @@ def serve_run(B, params, rom, i1, args, slots=512, workers=4):
             "fom_workers": workers, "fom_cells_peak": peak,
             "p50_ms": {k: float(np.percentile(v, 50)) if v else None for k, v in lat.items()},
             "p99_ms": {k: float(np.percentile(v, 99)) if v else None for k, v in lat.items()},
-            "workload": "Poisson arrivals at 0.8 of the capacity measured on a mixed burst; 95 %% reduced "
+            "workload": "Poisson arrivals at %.1f of the capacity measured on a mixed burst; 95 %% reduced "
                         "requests of U{100..3000} steps (C-rate in {0.5,1,2,3,5}, i0 scale ~ LogU(0.5,2), "
                         "plating rate ~ LogU(0.1,10)) on the reduced model of the %s cell; 5 %% full-order "
                         "validation solves of 60 steps on the %s cell; a sample of %d requests"
-                        % (ROM_CELL, SERVE_FOM_CELL, n_req)}
+                        % (load, ROM_CELL, SERVE_FOM_CELL, n_req)}
 
 
 def rom_and_serve(B, params, args, torch):

@@ -379,32 +379,10 @@ __global__ void k_bj_apply(Dims D, const float* __restrict__ dinv, const float* 
 // ------------------------------------------------------- level-1 assembly
 __device__ inline void acc_blk(float* blk, int k, int kk, float v) { blk[k * NCLS + kk] += v; }
 
-// Four threads per coarse cell, thread kr accumulating the cell's block row
-// kr (4 self entries and 6 x 4 outgoing ones, all in registers: the column
-// and direction indices are compile-time after unrolling).  Every thread
-// evaluates all faces of the cell; each accumulator receives the same terms
-// in the same order as a one-thread-per-cell assembly would add them.
-#define L1_ACC_EX(row, col, val)                                                   \
-    do {                                                                          \
-        if ((row) == kr) {                                                        \
-            const float v_ = (val);                                               \
-            _Pragma("unroll") for (int q_ = 0; q_ < NCLS; ++q_) if (q_ == (col)) ex4[q_] += v_; \
-        }                                                                         \
-    } while (0)
-#define L1_ACC_OD(row, col, val)                                                  \
-    do {                                                                          \
-        if ((row) == kr) {                                                        \
-            const float v_ = (val);                                               \
-            _Pragma("unroll") for (int q_ = 0; q_ < NCLS; ++q_) if (q_ == (col)) of4[d][q_] += v_; \
-        }                                                                         \
-    } while (0)
-
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(128)
 k_assemble_l1(ParT<float> P, Dims D, const uint32_t* __restrict__ vc, const float* __restrict__ u,
               const float* __restrict__ icoef, double dt, Level L1) {
-    const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int64_t cell = gt >> 2;
-    const int kr = (int)(gt & 3);
+    int64_t cell = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (cell >= L1.cells) return;
     int cz = (int)(cell % L1.nz);
     int cy = (int)((cell / L1.nz) % L1.ny);
@@ -418,12 +396,10 @@ k_assemble_l1(ParT<float> P, Dims D, const uint32_t* __restrict__ vc, const floa
     const float sc_cp = float(dt / (P.V * P.cref[PE]));  // (row c, col phi)
     const float sc_pc = c0 / A;                          // (row phi, col c)
     const float sc_pp = 1.f / A;                         // (row phi, col phi)
-    float ex4[NCLS] = {0.f, 0.f, 0.f, 0.f};
-    float of4[6][NCLS];
-#pragma unroll
-    for (int d = 0; d < 6; ++d)
-#pragma unroll
-        for (int q = 0; q < NCLS; ++q) of4[d][q] = 0.f;
+    float ex[BLK];
+    float off[OFFW];
+    for (int i = 0; i < BLK; ++i) ex[i] = 0.f;
+    for (int i = 0; i < OFFW; ++i) off[i] = 0.f;
     uint32_t mask = 0;
     for (int a = 0; a < 2; ++a)
         for (int b = 0; b < 2; ++b)
@@ -437,15 +413,14 @@ k_assemble_l1(ParT<float> P, Dims D, const uint32_t* __restrict__ vc, const floa
                 mask |= 1u << kv;
                 if (lv == PE) {
                     mask |= 1u;
-                    L1_ACC_EX(0, 0, 1.f);   // storage V/dt, scaled
+                    acc_blk(ex, 0, 0, 1.f);   // storage V/dt, scaled
                 }
-                if (t == 0 && lv == PCN) L1_ACC_EX(kv, kv, float(P.g_dir) * sc_pp);
+                if (t == 0 && lv == PCN) acc_blk(ex, kv, kv, float(P.g_dir) * sc_pp);
                 float cv = cc[v];
                 const int64_t offs[6] = {-D.syz, D.syz, -(int64_t)D.nz, (int64_t)D.nz, -1, 1};
                 const bool inb[6] = {t > 0, t < D.nt - 1, y > 0, y < D.ny - 1, z > 0, z < D.nz - 1};
                 const int loc[6] = {a, a, b, b, e, e};
                 int rank = 0, irank = 0;
-#pragma unroll
                 for (int d = 0; d < 6; ++d) {
                     if (!inb[d]) continue;
                     int64_t w = v + offs[d];
@@ -454,6 +429,7 @@ k_assemble_l1(ParT<float> P, Dims D, const uint32_t* __restrict__ vc, const floa
                     int kw = phi_class(lw);
                     // neighbour outside this coarse cell?
                     bool other = (d & 1) ? (loc[d] == 1) : (loc[d] == 0);
+                    float* od = off + d * BLK;
                     int64_t f = face_of(lv, lw, code, cw_code, d, rank);
                     float cw = cc[w];
                     FaceJac<float> J;
@@ -466,22 +442,22 @@ k_assemble_l1(ParT<float> P, Dims D, const uint32_t* __restrict__ vc, const floa
                         float S = fmaxf(cv, cmin) + fmaxf(cw, cmin);
                         float exc = float(P.E_gm) * (cw - cv) / (S * S) *
                                     ((cv >= cmin ? 1.f : 0.f) + (cw >= cmin ? 1.f : 0.f));
-                        L1_ACC_EX(0, 0, float(P.E_tF) * exc * sc_cc);
-                        L1_ACC_EX(1, 0, exc * sc_pc);
+                        acc_blk(ex, 0, 0, float(P.E_tF) * exc * sc_cc);
+                        acc_blk(ex, 1, 0, exc * sc_pc);
                         if (other) {
-                            L1_ACC_OD(0, 0, J.c[2] * sc_cc);
-                            L1_ACC_OD(0, 1, J.c[3] * sc_cp);
-                            L1_ACC_OD(1, 0, J.p[2] * sc_pc);
-                            L1_ACC_OD(1, 1, J.p[3] * sc_pp);
+                            acc_blk(od, 0, 0, J.c[2] * sc_cc);
+                            acc_blk(od, 0, 1, J.c[3] * sc_cp);
+                            acc_blk(od, 1, 0, J.p[2] * sc_pc);
+                            acc_blk(od, 1, 1, J.p[3] * sc_pp);
                         }
                     } else if (lv != PE && lw != PE) {
                         // conduction between electronic conductors (solid c rows are not coarse)
                         if (kv == kw) {
-                            if (other) L1_ACC_OD(kv, kv, J.p[3] * sc_pp);
+                            if (other) acc_blk(od, kv, kv, J.p[3] * sc_pp);
                         } else {
-                            L1_ACC_EX(kv, kv, J.p[1] * sc_pp);
-                            L1_ACC_EX(kv, kw, J.p[3] * sc_pp);
-                            if (other) L1_ACC_OD(kv, kw, J.p[3] * sc_pp);
+                            acc_blk(ex, kv, kv, J.p[1] * sc_pp);
+                            acc_blk(ex, kv, kw, J.p[3] * sc_pp);
+                            if (other) acc_blk(od, kv, kw, J.p[3] * sc_pp);
                         }
                     } else if (lv != PE) {
                         // solid v, electrolyte w (interface kinetics; zero for collectors)
@@ -492,12 +468,12 @@ k_assemble_l1(ParT<float> P, Dims D, const uint32_t* __restrict__ vc, const floa
                             s_pc -= J.p[4] * J.n[2] / jnn;
                             s_pe -= J.p[4] * J.n[3] / jnn;
                         }
-                        L1_ACC_EX(kv, kv, s_pp * sc_pp);
-                        L1_ACC_EX(kv, 0, s_pc * sc_pc);
-                        L1_ACC_EX(kv, 1, s_pe * sc_pp);
+                        acc_blk(ex, kv, kv, s_pp * sc_pp);
+                        acc_blk(ex, kv, 0, s_pc * sc_pc);
+                        acc_blk(ex, kv, 1, s_pe * sc_pp);
                         if (other) {
-                            L1_ACC_OD(kv, 0, s_pc * sc_pc);
-                            L1_ACC_OD(kv, 1, s_pe * sc_pp);
+                            acc_blk(od, kv, 0, s_pc * sc_pc);
+                            acc_blk(od, kv, 1, s_pe * sc_pp);
                         }
                     } else {
                         // electrolyte v, solid w
@@ -508,26 +484,22 @@ k_assemble_l1(ParT<float> P, Dims D, const uint32_t* __restrict__ vc, const floa
                             cc0 -= J.c[4] * J.n[0] / jnn; cc1 -= J.c[4] * J.n[1] / jnn; cc3 -= J.c[4] * J.n[3] / jnn;
                             pp0 -= J.p[4] * J.n[0] / jnn; pp1 -= J.p[4] * J.n[1] / jnn; pp3 -= J.p[4] * J.n[3] / jnn;
                         }
-                        L1_ACC_EX(0, 0, cc0 * sc_cc);
-                        L1_ACC_EX(0, 1, cc1 * sc_cp);
-                        L1_ACC_EX(0, kw, cc3 * sc_cp);
-                        L1_ACC_EX(1, 0, pp0 * sc_pc);
-                        L1_ACC_EX(1, 1, pp1 * sc_pp);
-                        L1_ACC_EX(1, kw, pp3 * sc_pp);
+                        acc_blk(ex, 0, 0, cc0 * sc_cc);
+                        acc_blk(ex, 0, 1, cc1 * sc_cp);
+                        acc_blk(ex, 0, kw, cc3 * sc_cp);
+                        acc_blk(ex, 1, 0, pp0 * sc_pc);
+                        acc_blk(ex, 1, 1, pp1 * sc_pp);
+                        acc_blk(ex, 1, kw, pp3 * sc_pp);
                         if (other) {
-                            L1_ACC_OD(0, kw, cc3 * sc_cp);
-                            L1_ACC_OD(1, kw, pp3 * sc_pp);
+                            acc_blk(od, 0, kw, cc3 * sc_cp);
+                            acc_blk(od, 1, kw, pp3 * sc_pp);
                         }
                     }
                 }
             }
-#pragma unroll
-    for (int q = 0; q < NCLS; ++q) L1.ex[(int64_t)(kr * NCLS + q) * L1.cells + cell] = ex4[q];
-#pragma unroll
-    for (int d = 0; d < 6; ++d)
-#pragma unroll
-        for (int q = 0; q < NCLS; ++q) L1.off[(int64_t)(d * BLK + kr * NCLS + q) * L1.cells + cell] = of4[d][q];
-    if (kr == 0) L1.mask[cell] = (uint8_t)mask;
+    for (int i = 0; i < BLK; ++i) L1.ex[(int64_t)i * L1.cells + cell] = ex[i];
+    for (int i = 0; i < OFFW; ++i) L1.off[(int64_t)i * L1.cells + cell] = off[i];
+    L1.mask[cell] = (uint8_t)mask;
 }
 
 // Galerkin coarsening of a coarse level: row sums add up; a child's outgoing
@@ -1816,7 +1788,7 @@ int precond_setup(mb_cell* c, const float* u32, const uint8_t* gate, double dt) 
     k_bj_setup<<<pgrid(D.nt, D.ny, D.nz), PB, 0, s>>>(c->Pf, D, c->vcode, c->zperm, u32, c->icoef, ss, p->dinv, p->fc,
                                                        c->rowdiag, c->rowinv), ::mb::count_launch(c);
     Level& L1 = p->lv[1];
-    k_assemble_l1<<<(unsigned)((4 * L1.cells + 255) / 256), 256, 0, s>>>(c->Pf, D, c->vcode, u32, c->icoef, dt, L1),
+    k_assemble_l1<<<(unsigned)((L1.cells + 127) / 128), 128, 0, s>>>(c->Pf, D, c->vcode, u32, c->icoef, dt, L1),
         ::mb::count_launch(c);
     for (int l = 2; l <= p->nlev; ++l)
         k_assemble_up<<<nblk(p->lv[l].cells), 256, 0, s>>>(p->lv[l - 1], p->lv[l]), ::mb::count_launch(c);
