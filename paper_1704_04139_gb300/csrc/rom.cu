@@ -80,6 +80,9 @@ struct RomDev {
     int32_t* gidx = nullptr;   // M x GMAX closure slots of the derivative list, -1 unused
     int32_t* gface = nullptr;  // ngate x 3 closure slots (phi_g, phi_e, n) of the gated faces
     double* P = nullptr;       // Nr x M (Pbv | P1c)
+    float2* Pdf = nullptr;     // float-float copies of P, Ms, Alin: the escalated GMRES's products
+    float2* Msdf = nullptr;
+    float2* Alindf = nullptr;
     double* Ms = nullptr;      // Nr x Nr
     double* Alin = nullptr;    // Nr x Nr
     float* Ptf = nullptr;      // FP32 copies for the Newton matrix: P^T (M x Nr), Ms, Alin, UlocR, UlocC, us
@@ -301,31 +304,48 @@ __global__ void k_rom_ei(RomDev d, DevParams P, ParT<float> Pf, int B, const dou
     for (int e = 0; e < GMAX; ++e) Gp[e] = g[e];
 }
 
-// GU[b][p][:] = sum_e G[b][p][e] U_loc[gidx[p][e]][:]
-// GU[p][b][j] = sum_e G[b][p][e] U_loc[gidx[p][e]][j] (FP32); inactive
-// instances write zeros so that the GEMM below reads defined values
-// one warp per (point, instance): lanes over j
-__global__ void k_rom_gu(RomDev d, int B, const float* __restrict__ G, const int* __restrict__ active,
-                         const int* __restrict__ hp, float* __restrict__ GU) {
-    const int64_t wg = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (wg >= (int64_t)d.M * B) return;
-    const int b = (int)(wg / d.M), p = (int)(wg % d.M);
-    float* out = GU + ((int64_t)p * B + b) * d.Nr;
-    if (!active[b] || hp[b]) {
-        for (int j = lane; j < d.Nr; j += 32) out[j] = 0.f;
-        return;
-    }
-    const float* Gp = G + ((int64_t)b * d.M + p) * GMAX;
+// GU[p][b][j] = sum_e G[b][p][e] U_loc[gidx[p][e]][j] (FP32); inactive and
+// escalated instances write zeros so that the GEMM reads defined values.
+// One block per (point p, chunk of GU_INST instances): the point's closure
+// rows of U_loc (at most GMAX x Nr) are staged in shared memory once and
+// shared by the chunk's instances (read for every instance from L2 they
+// made the kernel L2-bound); warps take instances, lanes the columns j.
+constexpr int GU_INST = 64;
+__global__ void __launch_bounds__(256) k_rom_gu(RomDev d, int B, const float* __restrict__ G,
+                                                const int* __restrict__ active, const int* __restrict__ hp,
+                                                float* __restrict__ GU) {
+    extern __shared__ __align__(16) float gu_s[];   // ne x Nr staged rows of U_loc
+    const int p = blockIdx.x, b0 = blockIdx.y * GU_INST;
+    const int Nr = d.Nr;
     const int32_t* gi = d.gidx + (int64_t)p * GMAX;
-    for (int j = lane; j < d.Nr; j += 32) {
-        float acc = 0.f;
-        for (int e = 0; e < GMAX; ++e) {
-            const int s = gi[e];
-            if (s < 0) break;
-            acc = fmaf(Gp[e], d.UlocRf[(int64_t)s * d.Nr + j], acc);
+    int ne = 0;
+    while (ne < GMAX && gi[ne] >= 0) ++ne;
+    for (int e = threadIdx.x; e < ne * Nr; e += blockDim.x) {
+        const int q = e / Nr, j = e - q * Nr;
+        gu_s[e] = d.UlocRf[(int64_t)gi[q] * Nr + j];
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int bi = wid; bi < GU_INST; bi += nw) {
+        const int b = b0 + bi;
+        if (b >= B) break;
+        float* out = GU + ((int64_t)p * B + b) * Nr;
+        if (!active[b] || hp[b]) {
+            for (int j = lane; j < Nr; j += 32) out[j] = 0.f;
+            continue;
         }
-        out[j] = acc;
+        const float* Gp = G + ((int64_t)b * d.M + p) * GMAX;
+        const float gl = lane < ne ? Gp[lane] : 0.f;   // the instance's derivative list, one entry per lane
+        for (int j0 = 0; j0 < Nr; j0 += 32) {   // every lane takes every shuffle
+            const int j = j0 + lane;
+            const bool in = j < Nr;
+            float acc = 0.f;
+            for (int e = 0; e < ne; ++e) {
+                const float ge = __shfl_sync(0xffffffffu, gl, e);
+                if (in) acc = fmaf(ge, gu_s[e * Nr + j], acc);
+            }
+            if (in) out[j] = acc;
+        }
     }
 }
 
@@ -775,6 +795,9 @@ static bool t5_prepare(RomDev& d, std::vector<void*>& owned) {
 // (one block per row and instance)
 // listed instances k = blockIdx.y, blockIdx.y + gridDim.y, ... < nmax (a
 // negative list entry ends the list)
+// DF: the result as a float-float pair (the GMRES path's operand) in the same
+// 8 bytes per entry, else FP64 (the FP64 Newton matrix path)
+template <bool DF>
 __global__ void k_rom_gu64(RomDev d, const double* __restrict__ G, const int* __restrict__ active,
                            const int* __restrict__ hp, const int* __restrict__ hplist, int nmax,
                            double* __restrict__ GU) {
@@ -792,7 +815,9 @@ __global__ void k_rom_gu64(RomDev d, const double* __restrict__ G, const int* __
                 if (s < 0) break;
                 acc += Gp[e] * d.UlocR[(int64_t)s * d.Nr + j];
             }
-            GU[((int64_t)b * d.M + p) * d.Nr + j] = acc;
+            const int64_t o = ((int64_t)b * d.M + p) * d.Nr + j;
+            if (DF) reinterpret_cast<float2*>(GU)[o] = df_from_double(acc);
+            else GU[o] = acc;
         }
     }
 }
@@ -1019,7 +1044,7 @@ static void launch_rom_lu(int Nr, int nblk, T* J, const double* r, const int* ac
 // with one reorthogonalisation, Givens rotations on thread 0.  One block of
 // 256 threads per listed instance; shared memory gmres_smem(Nr, M, m) doubles.
 __host__ __device__ constexpr size_t gmres_smem(int Nr, int M, int m) {
-    return 8 * ((size_t)(m + 1) * Nr + (size_t)M + 3 * (size_t)Nr + (size_t)(m + 1) * m + 4 * (size_t)(m + 1) + 40 +
+    return 8 * ((size_t)(m + 1) * Nr + (size_t)M + 4 * (size_t)Nr + (size_t)(m + 1) * m + 4 * (size_t)(m + 1) + 40 +
                 ((size_t)Nr + 1) / 2);
 }
 constexpr int GMRES_M = 16, GMRES_CYCLES = 2;
@@ -1049,13 +1074,16 @@ k_rom_gmres(RomDev d, const double* __restrict__ prm, const double* __restrict__
     double* const cr = gv + (m + 1);                      // m: Givens cosines
     double* const sr = cr + (m + 1);                      // m: Givens sines
     double* const hy = sr + (m + 1);                      // m+1: projections, then y
-    double* const red = hy + (m + 1);                     // 40: reduction scratch and flags
+    float2* const sdf = reinterpret_cast<float2*>(hy + (m + 1));   // Nr: the product's input as float-float
+    double* const red = hy + (m + 1) + Nr;                // 40: reduction scratch and flags
     int* const ps = reinterpret_cast<int*>(red + 40);     // Nr pivot rows
     const float* const LU = J + (int64_t)b * Nr * Nr;
     const int* const pv = lpiv + (int64_t)b * Nr;
     const float* const rsc = lsc + (int64_t)b * 2 * Nr;
     const float* const csc = rsc + Nr;
-    const double* const GUb = GU64 + (int64_t)b * M * Nr;
+    // the instance's G U_loc as float-float pairs (k_rom_gu64<true>)
+    const float2* const GUb = reinterpret_cast<const float2*>(GU64) + (int64_t)b * M * Nr;
+    float2* const tdf = reinterpret_cast<float2*>(t);
     const double dt_inv = prm[RP * b + 3];
     for (int k = tid; k < Nr; k += blockDim.x) ps[k] = pv[k];
 
@@ -1111,22 +1139,50 @@ k_rom_gmres(RomDev d, const double* __restrict__ prm, const double* __restrict__
         for (int i = tid; i < Nr; i += blockDim.x) dst[i] *= (double)csc[i];
         __syncthreads();
     };
-    // dst = J64 src
+    // dst = J src with J = Ms/dt + Alin + P (G U_loc): float-float operands and
+    // compensated dot products (Dot2 of Ogita, Rump and Oishi, "Accurate sum
+    // and dot product", SIAM J. Sci. Comput. 26, 2005: TwoProduct per term,
+    // TwoSum into the running sum, the errors gathered in a second FP32 sum),
+    // as accurate as a dot product in ~48-bit arithmetic, on the FP32 pipe
+    // (GB300's FP64 pipe took ~64x longer for these products)
+    auto dot2 = [](float2 a, float2 b, float& sh, float& sc) {
+        const float pr = a.x * b.x;
+        float q = fmaf(a.x, b.x, -pr);
+        q = fmaf(a.x, b.y, fmaf(a.y, b.x, q));
+        const float tt = sh + pr, z = tt - sh;
+        sc += q + ((sh - (tt - z)) + (pr - z));
+        sh = tt;
+    };
+    auto dot2_warp = [](float& sh, float& sc) {
+        for (int o = 16; o > 0; o >>= 1) {
+            const float s2 = __shfl_xor_sync(0xffffffffu, sh, o), c2 = __shfl_xor_sync(0xffffffffu, sc, o);
+            const float tt = sh + s2, z = tt - sh;
+            sc += c2 + ((sh - (tt - z)) + (s2 - z));
+            sh = tt;
+        }
+    };
     auto matvec = [&](const double* src, double* dst) {
+        for (int j = tid; j < Nr; j += blockDim.x) sdf[j] = df_from_double(src[j]);
+        __syncthreads();
         for (int p = wid; p < M; p += nw) {
-            double a = 0.0;
-            for (int j = lane; j < Nr; j += 32) a += GUb[(int64_t)p * Nr + j] * src[j];
-            a = warp_sum_d(a);
-            if (lane == 0) t[p] = a;
+            float sh = 0.f, sc = 0.f;
+            for (int j = lane; j < Nr; j += 32) dot2(GUb[(int64_t)p * Nr + j], sdf[j], sh, sc);
+            dot2_warp(sh, sc);
+            if (lane == 0) tdf[p] = df_fast2sum(sh, sc);
         }
         __syncthreads();
         for (int i = wid; i < Nr; i += nw) {
-            double a = 0.0;
-            for (int p = lane; p < M; p += 32) a += d.P[(int64_t)i * M + p] * t[p];
-            for (int j = lane; j < Nr; j += 32)
-                a += (d.Ms[(int64_t)i * Nr + j] * dt_inv + d.Alin[(int64_t)i * Nr + j]) * src[j];
-            a = warp_sum_d(a);
-            if (lane == 0) dst[i] = a;
+            float s1 = 0.f, c1 = 0.f, s2 = 0.f, c2 = 0.f, s3 = 0.f, c3 = 0.f;
+            for (int p = lane; p < M; p += 32) dot2(d.Pdf[(int64_t)i * M + p], tdf[p], s1, c1);
+            for (int j = lane; j < Nr; j += 32) {
+                dot2(d.Msdf[(int64_t)i * Nr + j], sdf[j], s2, c2);
+                dot2(d.Alindf[(int64_t)i * Nr + j], sdf[j], s3, c3);
+            }
+            dot2_warp(s1, c1);
+            dot2_warp(s2, c2);
+            dot2_warp(s3, c3);
+            if (lane == 0)
+                dst[i] = ((double)s1 + (double)c1) + dt_inv * ((double)s2 + (double)c2) + ((double)s3 + (double)c3);
         }
         __syncthreads();
     };
@@ -1704,6 +1760,16 @@ static int rom_build_host(mb_rom* R, const mb_rom_data* dd) {
               upr(d.bbnd, dd->bbnd, Nr) && upr(d.scp, dd->s_cp, Nr) && upr(d.sac, dd->s_ac, Nr) &&
               upr(d.a0, dd->a0, Nr);
     if (ok && !gface.empty()) ok = up(d.gface, gface);
+    auto updf = [&](float2*& dst, const double* src, size_t cnt) -> bool {
+        std::vector<float2> h(cnt ? cnt : 1);
+        for (size_t i = 0; i < cnt; ++i) h[i] = df_from_double(src[i]);
+        dst = rom_alloc<float2>(R->owned, h.size());
+        if (!dst) return false;
+        return cudaMemcpy(dst, h.data(), 8 * h.size(), cudaMemcpyHostToDevice) == cudaSuccess;
+    };
+    if (ok)
+        ok = updf(d.Pdf, P.data(), P.size()) && updf(d.Msdf, dd->Ms, (size_t)Nr * Nr) &&
+             updf(d.Alindf, dd->Alin, (size_t)Nr * Nr);
     // FP32 copies for the Newton matrix and the step-length norm
     auto upf = [&](float*& dst, const double* src, size_t cnt) -> bool {
         std::vector<float> h(src, src + cnt);
@@ -1751,7 +1817,9 @@ static int rom_build_host(mb_rom* R, const mb_rom_data* dd) {
              cudaFuncSetAttribute(k_rom_lu<float, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   ROM_LU_SMEM) == cudaSuccess &&
              cudaFuncSetAttribute(k_rom_gmres, cudaFuncAttributeMaxDynamicSharedMemorySize, ROM_LU_SMEM) ==
-                 cudaSuccess;
+                 cudaSuccess &&
+             cudaFuncSetAttribute(k_rom_gu, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)(sizeof(float) * GMAX * ROM_NR_MAX)) == cudaSuccess;
     if (!ok) return cuda_fail(cudaGetLastError(), "rom upload");
     return MB_OK;
 }
@@ -1920,7 +1988,11 @@ static void iter_hp_a(mb_rom* R, cudaStream_t s, int nhp, bool graph) {
     k_rom_ei<true><<<(unsigned)(((int64_t)d.M * n + 127) / 128), 128, 0, s>>>(
         d, c->P, c->Pf, n, w.uloc, w.gate, w.prm, w.active, w.hp, w.hplist, w.f, w.G, w.G64), count_launch(c);
     const unsigned gy = (unsigned)(graph ? std::min(n, 64) : n);
-    k_rom_gu64<<<dim3((unsigned)d.M, gy), 64, 0, s>>>(d, w.G64, w.active, w.hp, w.hplist, n, w.GU64), count_launch(c);
+    if (rom_refine(d))
+        k_rom_gu64<true><<<dim3((unsigned)d.M, gy), 64, 0, s>>>(d, w.G64, w.active, w.hp, w.hplist, n, w.GU64);
+    else
+        k_rom_gu64<false><<<dim3((unsigned)d.M, gy), 64, 0, s>>>(d, w.G64, w.active, w.hp, w.hplist, n, w.GU64);
+    count_launch(c);
     if (!rom_refine(d))
         k_rom_jac64<<<dim3((unsigned)d.Nr, gy), 128, 0, s>>>(d, w.prm, w.GU64, w.active, w.hp, w.hplist, n, w.J64),
             count_launch(c);
@@ -2048,7 +2120,8 @@ static void iter_main_b(mb_rom* R, cudaStream_t s, bool listed, int ncols, const
     RomWork& w = R->w;
     const int B = w.B;
     if (d.M)
-        k_rom_gu<<<(unsigned)(((int64_t)d.M * B * 32 + 255) / 256), 256, 0, s>>>(d, B, w.G, w.active, w.hp, w.GU),
+        k_rom_gu<<<dim3((unsigned)d.M, (unsigned)((B + GU_INST - 1) / GU_INST)), 256, sizeof(float) * GMAX * d.Nr, s>>>(
+            d, B, w.G, w.active, w.hp, w.GU),
             count_launch(c);
     if (ncols > 0) {
         const int* al = (listed || dit) ? w.alist : nullptr;
