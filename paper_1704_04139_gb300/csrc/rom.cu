@@ -869,8 +869,9 @@ k_rom_resid(RomDev d, const double* __restrict__ a, const double* __restrict__ a
 // forward elimination of the right-hand side during the factorisation (so the
 // L factor is stored only with KEEP), back substitution.  One block per instance; the
 // matrix is copied to shared memory (SMEM, lu_smem(Nr, sizeof(T)) <=
-// ROM_LU_SMEM, opt-in above 48 KB, set at mb_rom_create) or factorised in place
-// in J.  Per column k: warp 0 reduces the per-warp pivot candidates, all threads
+// ROM_LU_SMEM, opt-in above 48 KB, set at mb_rom_create), or, when it does not
+// fit, its leading rows as far as the dynamic shared memory reaches, the other
+// rows factorised in place in J (row swaps move data between the two).  Per column k: warp 0 reduces the per-warp pivot candidates, all threads
 // swap the two rows, then warp w eliminates rows k+1+w, k+1+w+nw, ... with its
 // lanes along the columns and keeps the largest |A[i][k+1]| of its rows as the
 // next column's candidate (two or three barriers per column).  1/A[k][k] is
@@ -897,41 +898,48 @@ k_rom_lu(int Nr, T* __restrict__ J, const double* __restrict__ r, const int* __r
     extern __shared__ __align__(16) unsigned char lu_raw[];
     T* const sm = reinterpret_cast<T*>(lu_raw);
     T* const Jb = J + (int64_t)b * Nr * Nr;
-    T* const A = SMEM ? sm : Jb;                 // Nr x Nr, row-major
-    T* const rs = SMEM ? sm + Nr * Nr : sm;      // row scales
+    T* const rs = sm;                            // row scales
     T* const cs = rs + Nr;                       // column scales
     T* const rhs = cs + Nr;
     T* const x = rhs + Nr;                       // 1/A[k][k], then the solution
+    T* const rows = x + Nr;                      // rows [0, R) of the matrix in shared memory
+    // rows that fit in the dynamic shared memory (all with SMEM); the others
+    // are factorised in place in J
+    uint32_t dyn;
+    asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dyn));
+    const int R = SMEM ? Nr : min(Nr, max(0, (int)(dyn / sizeof(T)) - 4 * Nr) / Nr);
+    auto row = [&](int i) -> T* { return i < R ? rows + (size_t)i * Nr : Jb + (size_t)i * Nr; };
     __shared__ T wbest[32];
     __shared__ int widx[32];
     __shared__ int spiv;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
-    if (SMEM) {
-        for (int e = tid; e < Nr * Nr; e += blockDim.x) A[e] = Jb[e];
-        __syncthreads();
-    }
+    for (int e = tid; e < R * Nr; e += blockDim.x) rows[e] = Jb[e];
+    __syncthreads();
     for (int i = wid; i < Nr; i += nw) {
+        const T* ri = row(i);
         T m = T(0);
-        for (int j = lane; j < Nr; j += 32) m = fmax(m, fabs(A[i * Nr + j]));
+        for (int j = lane; j < Nr; j += 32) m = fmax(m, fabs(ri[j]));
         for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
         if (lane == 0) rs[i] = m > T(0) ? T(1) / m : T(1);
     }
     __syncthreads();
     for (int j = tid; j < Nr; j += blockDim.x) {
         T m = T(0);
-        for (int i = 0; i < Nr; ++i) m = fmax(m, fabs(A[i * Nr + j] * rs[i]));
+        for (int i = 0; i < Nr; ++i) m = fmax(m, fabs(row(i)[j] * rs[i]));
         cs[j] = m > T(0) ? T(1) / m : T(1);
     }
     __syncthreads();
-    for (int i = wid; i < Nr; i += nw)
-        for (int j = lane; j < Nr; j += 32) A[i * Nr + j] *= rs[i] * cs[j];
+    for (int i = wid; i < Nr; i += nw) {
+        T* ri = row(i);
+        for (int j = lane; j < Nr; j += 32) ri[j] *= rs[i] * cs[j];
+    }
     for (int i = tid; i < Nr; i += blockDim.x) rhs[i] = (T)(-r[(int64_t)b * Nr + i]) * rs[i];
     __syncthreads();
     {
         // candidates for the first pivot
         T best = T(-1);
         int bi = Nr;
-        for (int i = tid; i < Nr; i += blockDim.x) lu_pick(best, bi, fabs(A[i * Nr]), i);
+        for (int i = tid; i < Nr; i += blockDim.x) lu_pick(best, bi, fabs(row(i)[0]), i);
         for (int o = 16; o > 0; o >>= 1)
             lu_pick(best, bi, __shfl_xor_sync(0xffffffffu, best, o), __shfl_xor_sync(0xffffffffu, bi, o));
         if (lane == 0) {
@@ -951,11 +959,13 @@ k_rom_lu(int Nr, T* __restrict__ J, const double* __restrict__ r, const int* __r
         __syncthreads();
         const int piv = spiv;   // the same in every thread: the branch below is uniform
         if (KEEP && tid == 0) piv_out[(int64_t)b * Nr + k] = piv;
+        T* const rk = row(k);
         if (piv != k) {
+            T* const rp = row(piv);
             for (int j = (KEEP ? 0 : k) + tid; j < Nr; j += blockDim.x) {
-                const T t = A[k * Nr + j];
-                A[k * Nr + j] = A[piv * Nr + j];
-                A[piv * Nr + j] = t;
+                const T t = rk[j];
+                rk[j] = rp[j];
+                rp[j] = t;
             }
             if (tid == 0) {
                 const T t = rhs[k];
@@ -964,24 +974,25 @@ k_rom_lu(int Nr, T* __restrict__ J, const double* __restrict__ r, const int* __r
             }
             __syncthreads();
         }
-        const T akk = A[k * Nr + k];
+        const T akk = rk[k];
         const T inv = akk != T(0) ? T(1) / akk : T(0);
-        const T rk = rhs[k];
+        const T rkk = rhs[k];
         if (tid == 0) x[k] = inv;
         T best = T(-1);
         int bi = Nr;
         for (int i = k + 1 + wid; i < Nr; i += nw) {
-            const T l = A[i * Nr + k] * inv;
+            T* const ri = row(i);
+            const T l = ri[k] * inv;
             for (int j = k + 1 + lane; j < Nr; j += 32) {
-                const T v = A[i * Nr + j] - l * A[k * Nr + j];
-                A[i * Nr + j] = v;
+                const T v = ri[j] - l * rk[j];
+                ri[j] = v;
                 if (j == k + 1) lu_pick(best, bi, fabs(v), i);
             }
             if (KEEP) {
                 __syncwarp();   // every lane has read A[i][k] before lane 0 overwrites it
-                if (lane == 0) A[i * Nr + k] = l;
+                if (lane == 0) ri[k] = l;
             }
-            if (lane == 0) rhs[i] -= l * rk;
+            if (lane == 0) rhs[i] -= l * rkk;
         }
         if (lane == 0) {   // column k+1 lives in lane 0 of every warp
             wbest[wid] = best;
@@ -991,8 +1002,9 @@ k_rom_lu(int Nr, T* __restrict__ J, const double* __restrict__ r, const int* __r
     }
     if (wid == 0) {
         for (int k = Nr - 1; k >= 0; --k) {
+            const T* rk = row(k);
             T part = T(0);
-            for (int j = k + 1 + lane; j < Nr; j += 32) part += A[k * Nr + j] * x[j];
+            for (int j = k + 1 + lane; j < Nr; j += 32) part += rk[j] * x[j];
             for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
             if (lane == 0) x[k] = (rhs[k] - part) * x[k];
             __syncwarp();
@@ -1001,8 +1013,7 @@ k_rom_lu(int Nr, T* __restrict__ J, const double* __restrict__ r, const int* __r
     __syncthreads();
     for (int j = tid; j < Nr; j += blockDim.x) delta[(int64_t)b * Nr + j] = (double)(x[j] * cs[j]);
     if (KEEP) {
-        if (SMEM)
-            for (int e = tid; e < Nr * Nr; e += blockDim.x) Jb[e] = A[e];
+        for (int e = tid; e < R * Nr; e += blockDim.x) Jb[e] = rows[e];
         for (int j = tid; j < Nr; j += blockDim.x) {
             sc_out[(int64_t)b * 2 * Nr + j] = rs[j];
             sc_out[(int64_t)b * 2 * Nr + Nr + j] = cs[j];
@@ -1021,7 +1032,7 @@ static void launch_rom_lu(int Nr, int nblk, T* J, const double* r, const int* ac
             k_rom_lu<T, true, true><<<(unsigned)nblk, lt, lu_smem(Nr, sizeof(T)), s>>>(Nr, J, r, active, hp, want_hp,
                                                                                        list, delta, piv, sc);
         else
-            k_rom_lu<T, false, true><<<(unsigned)nblk, lt, 4 * sizeof(T) * (size_t)Nr, s>>>(
+            k_rom_lu<T, false, true><<<(unsigned)nblk, lt, ROM_LU_SMEM, s>>>(
                 Nr, J, r, active, hp, want_hp, list, delta, piv, sc);
         return;
     }
@@ -1029,8 +1040,7 @@ static void launch_rom_lu(int Nr, int nblk, T* J, const double* r, const int* ac
         k_rom_lu<T, true><<<(unsigned)nblk, lt, lu_smem(Nr, sizeof(T)), s>>>(Nr, J, r, active, hp, want_hp, list,
                                                                              delta);
     else
-        k_rom_lu<T, false><<<(unsigned)nblk, lt, 4 * sizeof(T) * (size_t)Nr, s>>>(Nr, J, r, active, hp, want_hp,
-                                                                                 list, delta);
+        k_rom_lu<T, false><<<(unsigned)nblk, lt, ROM_LU_SMEM, s>>>(Nr, J, r, active, hp, want_hp, list, delta);
 }
 
 // Newton step of an escalated instance (hp[b], refinement mode): delta =
@@ -1815,6 +1825,12 @@ static int rom_build_host(mb_rom* R, const mb_rom_data* dd) {
              cudaFuncSetAttribute(k_rom_lu<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   ROM_LU_SMEM) == cudaSuccess &&
              cudaFuncSetAttribute(k_rom_lu<float, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  ROM_LU_SMEM) == cudaSuccess &&
+             cudaFuncSetAttribute(k_rom_lu<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  ROM_LU_SMEM) == cudaSuccess &&
+             cudaFuncSetAttribute(k_rom_lu<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  ROM_LU_SMEM) == cudaSuccess &&
+             cudaFuncSetAttribute(k_rom_lu<float, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   ROM_LU_SMEM) == cudaSuccess &&
              cudaFuncSetAttribute(k_rom_gmres, cudaFuncAttributeMaxDynamicSharedMemorySize, ROM_LU_SMEM) ==
                  cudaSuccess &&
@@ -2923,14 +2939,15 @@ static int debug_rom_lu(int Nr, int B, int in_place, const double* J, const doub
     if (e == cudaSuccess) e = cudaMemcpy(dr, r, 8 * (size_t)B * Nr, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(da, ones.data(), 4 * (size_t)B, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(dh, zeros.data(), 4 * (size_t)B, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess && smem)
-        e = cudaFuncSetAttribute(k_rom_lu<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, ROM_LU_SMEM);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(smem ? k_rom_lu<T, true> : k_rom_lu<T, false>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, ROM_LU_SMEM);
     if (e == cudaSuccess) {
         const unsigned lt = Nr <= 96 ? LU_T_SMALL : LU_T_LARGE;
         if (smem)
             k_rom_lu<T, true><<<(unsigned)B, lt, lu_smem(Nr, sizeof(T))>>>(Nr, dJ, dr, da, dh, 0, nullptr, dd);
         else
-            k_rom_lu<T, false><<<(unsigned)B, lt, 4 * sizeof(T) * (size_t)Nr>>>(Nr, dJ, dr, da, dh, 0, nullptr, dd);
+            k_rom_lu<T, false><<<(unsigned)B, lt, ROM_LU_SMEM>>>(Nr, dJ, dr, da, dh, 0, nullptr, dd);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaMemcpy(delta, dd, 8 * (size_t)B * Nr, cudaMemcpyDeviceToHost);
