@@ -2044,40 +2044,44 @@ static void iter_main_a(mb_rom* R, cudaStream_t s) {
             d, c->P, c->Pf, B, w.uloc, w.gate, w.prm, w.active, w.hp, w.hplist, w.f, w.G, w.G64), count_launch(c);
 }
 // the Newton-matrix GEMM in variant tc (0 FP32 FMA, 1 mma.sync 3xTF32, 2 tcgen05 3xTF32)
-static void launch_rom_jac(mb_rom* R, cudaStream_t s, int tc, int ncols, const int* al, const int* dit,
-                           const int* dn) {
-    const RomDev& d = R->d;
-    RomWork& w = R->w;
-    const int B = w.B;
+static void launch_rom_jac_p(const RomDev& d, cudaStream_t s, int tc, int B, int ncols, const int* al,
+                             const double* prm, const float* GU, const int* hp, float* J, const int* dit,
+                             const int* dn, int* tcerr) {
     const dim3 gj((unsigned)(((int64_t)ncols * d.Nr + JT_COLS - 1) / JT_COLS), (unsigned)((d.Nr + JT_ROWS - 1) / JT_ROWS));
     if (tc == 2 && d.Pbf)
         k_rom_jac5<<<(unsigned)(((int64_t)ncols * d.Nr + T5_M - 1) / T5_M), T5_THREADS, T5_SMEM, s>>>(
-            d, B, ncols, al, w.prm, w.GU, w.hp, w.J, dit, dn, w.tcerr);
+            d, B, ncols, al, prm, GU, hp, J, dit, dn, tcerr);
     else if (tc)
-        k_rom_jac<true><<<gj, 256, 0, s>>>(d, B, ncols, al, w.prm, w.GU, w.hp, w.J, dit, dn);
+        k_rom_jac<true><<<gj, 256, 0, s>>>(d, B, ncols, al, prm, GU, hp, J, dit, dn);
     else
-        k_rom_jac<false><<<gj, 256, 0, s>>>(d, B, ncols, al, w.prm, w.GU, w.hp, w.J, dit, dn);
+        k_rom_jac<false><<<gj, 256, 0, s>>>(d, B, ncols, al, prm, GU, hp, J, dit, dn);
+}
+static void launch_rom_jac(mb_rom* R, cudaStream_t s, int tc, int ncols, const int* al, const int* dit,
+                           const int* dn) {
+    RomWork& w = R->w;
+    launch_rom_jac_p(R->d, s, tc, w.B, ncols, al, w.prm, w.GU, w.hp, w.J, dit, dn, w.tcerr);
 }
 
-// Autotuning of the Newton-matrix GEMM: the first batch of each (N_r, M, B)
-// times every variant the model admits on the batch's own buffers (GU
-// zeroed; one warm-up and three timed launches over all B instances, CUDA
-// events on the cell's stream) and keeps the fastest; later batches of the
-// same shape reuse the choice.  The three variants give FP32-accurate
-// matrices (tested against each other to 1e-9 on reduced trajectories), so
-// the choice changes the time only.
+// Autotuning of the Newton-matrix GEMM: once per model shape (N_r, M), every
+// variant the model admits is timed on a scratch batch of TUNE_B instances
+// (GU zeroed; one warm-up and three timed launches, CUDA events on the
+// cell's stream) and the fastest is kept for every later batch of that
+// shape, whatever its size: the variant, and so the rounding of the Newton
+// matrices, depends on the model only, so an instance gives the same result
+// alone or in any batch.  The three variants give FP32-accurate matrices
+// (tested against each other to 1e-9 on reduced trajectories).
+constexpr int TUNE_B = 256;
 struct TuneRec {
     int choice;
     float ms[3];
 };
 static std::mutex g_tune_mu;
-static std::map<std::tuple<int, int, int>, TuneRec> g_tune;
+static std::map<std::pair<int, int>, TuneRec> g_tune;
 
 static int rom_tune_gemm(mb_rom* R) {
     const RomDev& d = R->d;
-    RomWork& w = R->w;
     if (R->tc_forced || d.M == 0) return MB_OK;
-    const auto key = std::make_tuple(d.Nr, d.M, w.B);
+    const auto key = std::make_pair(d.Nr, d.M);
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         auto it = g_tune.find(key);
@@ -2088,38 +2092,53 @@ static int rom_tune_gemm(mb_rom* R) {
         }
     }
     cudaStream_t s = R->cell->stream;
-    MB_CUDA(cudaMemsetAsync(w.GU, 0, sizeof(float) * (size_t)w.B * d.M * d.Nr, s));
-    cudaEvent_t e0, e1;
-    MB_CUDA(cudaEventCreate(&e0));
-    MB_CUDA(cudaEventCreate(&e1));
+    const int Bt = TUNE_B;
+    float *GU = nullptr, *J = nullptr;
+    double* prm = nullptr;
+    int *hp = nullptr, *terr_d = nullptr;
+    cudaError_t e = cudaMalloc(&GU, sizeof(float) * (size_t)Bt * d.M * d.Nr);
+    if (e == cudaSuccess) e = cudaMalloc(&J, sizeof(float) * (size_t)Bt * d.Nr * d.Nr);
+    if (e == cudaSuccess) e = cudaMalloc(&prm, sizeof(double) * (size_t)Bt * RP);
+    if (e == cudaSuccess) e = cudaMalloc(&hp, sizeof(int) * (size_t)Bt);
+    if (e == cudaSuccess) e = cudaMalloc(&terr_d, 16);
+    if (e == cudaErrorMemoryAllocation) {   // no room for the scratch batch: keep the default variant untuned
+        cudaGetLastError();
+        cudaFree(GU); cudaFree(J); cudaFree(prm); cudaFree(hp); cudaFree(terr_d);
+        return MB_OK;
+    }
+    if (e == cudaSuccess) e = cudaMemsetAsync(GU, 0, sizeof(float) * (size_t)Bt * d.M * d.Nr, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(prm, 0, sizeof(double) * (size_t)Bt * RP, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(hp, 0, sizeof(int) * (size_t)Bt, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(terr_d, 0, 16, s);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
     int best = d.tc;
     float best_ms = 1e30f;
-    for (int tc = 0; tc <= 2; ++tc) {
+    for (int tc = 0; tc <= 2 && e == cudaSuccess; ++tc) {
         R->tune_ms[tc] = -1.f;
         if (tc == 2 && !d.Pbf) continue;
-        launch_rom_jac(R, s, tc, w.B, nullptr, nullptr, nullptr);
+        launch_rom_jac_p(d, s, tc, Bt, Bt, nullptr, prm, GU, hp, J, nullptr, nullptr, terr_d);
         cudaEventRecord(e0, s);
-        for (int k = 0; k < 3; ++k) launch_rom_jac(R, s, tc, w.B, nullptr, nullptr, nullptr);
+        for (int k = 0; k < 3; ++k) launch_rom_jac_p(d, s, tc, Bt, Bt, nullptr, prm, GU, hp, J, nullptr, nullptr, terr_d);
         cudaEventRecord(e1, s);
-        cudaError_t e = cudaEventSynchronize(e1);
+        e = cudaEventSynchronize(e1);
         float ms = 0.f;
         if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
         int terr = 0;
-        if (e == cudaSuccess) e = cudaMemcpy(&terr, w.tcerr, 4, cudaMemcpyDeviceToHost);
-        if (e != cudaSuccess) {
-            cudaEventDestroy(e0);
-            cudaEventDestroy(e1);
-            return cuda_fail(e, "reduced model: GEMM autotuning");
-        }
+        if (e == cudaSuccess) e = cudaMemcpy(&terr, terr_d, 4, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) break;
         if (terr) {   // a bounded wait of the tcgen05 kernel gave up: not a candidate
-            MB_CUDA(cudaMemset(w.tcerr, 0, 16));
+            e = cudaMemset(terr_d, 0, 16);
             continue;
         }
         R->tune_ms[tc] = ms / 3.f;
         if (ms < best_ms) { best_ms = ms; best = tc; }
     }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(GU); cudaFree(J); cudaFree(prm); cudaFree(hp); cudaFree(terr_d);
+    if (e != cudaSuccess) return cuda_fail(e, "reduced model: GEMM autotuning");
     MB_CUDA_LAUNCH("rom_tune_gemm");
     R->d.tc = best;
     TuneRec rec;

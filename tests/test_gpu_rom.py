@@ -195,9 +195,9 @@ def test_rom_tensor_newton_matrix_same_result(params, request, which):
 
 @pytest.mark.gpu
 def test_rom_gemm_autotuning(params, request):
-    """Without a fixed variant, the first batch times every GEMM variant the
-    model admits and keeps the fastest; the solve then gives exactly what the
-    same variant gives when fixed (same kernels, same arithmetic)."""
+    """Without a fixed variant, every GEMM variant the model admits is timed
+    once per model shape and the fastest kept; the solve then gives exactly
+    what the same variant gives when fixed (same kernels, same arithmetic)."""
     B = _gpu()
     lab, oc, rom = request.getfixturevalue("case")
     gc, g = _gpu_rom(B, lab, params, rom)
