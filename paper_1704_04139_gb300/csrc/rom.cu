@@ -1112,41 +1112,47 @@ k_rom_gmres(RomDev d, const double* __restrict__ prm, const double* __restrict__
         __syncthreads();
         return tot;
     };
-    // dst = M^-1 src (src, dst distinct shared vectors)
+    // dst = M^-1 src (src, dst distinct shared vectors): the instance's FP32 LU
+    // applied in FP32 (a fixed linear operator up to rounding; only GMRES's
+    // convergence depends on it, the products and the residual set the
+    // step's accuracy), row-oriented triangular solves on warp 0
+    float* const yf = reinterpret_cast<float*>(sdf);   // Nr floats (sdf is free outside the products)
     auto precond = [&](const double* src, double* dst) {
-        for (int i = tid; i < Nr; i += blockDim.x) dst[i] = (double)rsc[i] * src[i];
+        for (int i = tid; i < Nr; i += blockDim.x) yf[i] = (float)((double)rsc[i] * src[i]);
         __syncthreads();
         if (tid == 0)
             for (int k = 0; k < Nr; ++k) {
                 const int p = ps[k];
                 if (p != k) {
-                    const double tmp = dst[k];
-                    dst[k] = dst[p];
-                    dst[p] = tmp;
+                    const float tmp = yf[k];
+                    yf[k] = yf[p];
+                    yf[p] = tmp;
                 }
             }
         __syncthreads();
         if (wid == 0) {
             for (int i = 1; i < Nr; ++i) {   // unit lower triangle
-                double a = 0.0;
-                for (int k = lane; k < i; k += 32) a += (double)LU[(int64_t)i * Nr + k] * dst[k];
-                a = warp_sum_d(a);
-                if (lane == 0) dst[i] -= a;
+                float a = 0.f;
+                const float* Li = LU + (int64_t)i * Nr;
+                for (int k = lane; k < i; k += 32) a = fmaf(Li[k], yf[k], a);
+                for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+                if (lane == 0) yf[i] -= a;
                 __syncwarp();
             }
             for (int i = Nr - 1; i >= 0; --i) {   // upper triangle
-                double a = 0.0;
-                for (int k = i + 1 + lane; k < Nr; k += 32) a += (double)LU[(int64_t)i * Nr + k] * dst[k];
-                a = warp_sum_d(a);
+                float a = 0.f;
+                const float* Ui = LU + (int64_t)i * Nr;
+                for (int k = i + 1 + lane; k < Nr; k += 32) a = fmaf(Ui[k], yf[k], a);
+                for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
                 if (lane == 0) {
-                    const double u = (double)LU[(int64_t)i * Nr + i];
-                    dst[i] = u != 0.0 ? (dst[i] - a) / u : 0.0;
+                    const float u = Ui[i];
+                    yf[i] = u != 0.f ? (yf[i] - a) / u : 0.f;
                 }
                 __syncwarp();
             }
         }
         __syncthreads();
-        for (int i = tid; i < Nr; i += blockDim.x) dst[i] *= (double)csc[i];
+        for (int i = tid; i < Nr; i += blockDim.x) dst[i] = (double)yf[i] * (double)csc[i];
         __syncthreads();
     };
     // dst = J src with J = Ms/dt + Alin + P (G U_loc): float-float operands and
