@@ -189,14 +189,16 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(self.rows)}
 
 
-def measured_peaks():
+def measured_peaks(key="hbm_gbs"):
+    """A measured peak (MEASURED_PEAKS.json: HBM copy GB/s, or BF16 GEMM TFLOP/s)
+    and "measured", else the recipe's fallback and "fallback"."""
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
         with open(path) as f:
             d = json.load(f)
-        return float(d["hbm_gbs"]), "measured"
+        return float(d[key]), "measured"
     except Exception:
-        return 6800.0, "fallback"
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}[key], "fallback"
 
 
 def kernel_traffic(kernel, workload, mode):
@@ -313,14 +315,34 @@ def rom_paper_dims(B, params, args, torch, estimate=True):
            "build_s": build_s, "build_note": "validation and 97 % models from one snapshot set" if estimate else None,
            "newton_its_per_instance_step": out["newton_its"] / inst_steps,
            "failed": out["failed"], "V_rel_err_vs_full_order_2_instances": errs,
-           "gemm": {"variant": ["f32 fma", "mma.sync 3xtf32", "tcgen05 3xtf32"][tune[0]],
-                    "autotune_ms_per_launch": {"f32 fma": tune[1][0], "mma.sync 3xtf32": tune[1][1],
-                                               "tcgen05 3xtf32": tune[1][2]} if args.rom_gemm < 0 else None},
+           "gemm": rom_gemm_figures(rom, tune, args),
            "step_mode": "host loop" if args.rom_host_loop else "one CUDA graph per time step",
            "error_estimate": est}
     rom.close()
     cell.close()
     return res
+
+
+def rom_gemm_figures(rom, tune, args):
+    """The Newton-matrix GEMM: the variant in use and, from the autotuning
+    (256-instance scratch batch), each variant's time and the tensor rate of
+    the three TF32 products per operand pair against the TF32 peak derived
+    from the measured BF16 one (x 1.1 / 2.25, the nominal dense ratio)."""
+    names = ["f32 fma", "mma.sync 3xtf32", "tcgen05 3xtf32"]
+    out = {"variant": names[tune[0]]}
+    if args.rom_gemm >= 0:
+        return out
+    flops = 3 * 2.0 * rom.n_r * (256 * rom.n_r) * (rom.n_bv + rom.n_1c)
+    peak, kind = measured_peaks("bf16_tflops")
+    tf32 = peak * 1.1 / 2.25 if peak else None
+    out["autotune_ms_per_launch"] = {n: tune[1][k] for k, n in enumerate(names)}
+    out["tensor_rate_tflops"] = {n: (flops / (tune[1][k] * 1e-3) / 1e12 if tune[1][k] > 0 else None)
+                                 for k, n in enumerate(names) if k > 0}
+    out["tf32_peak_tflops"] = tf32
+    out["tf32_peak_kind"] = "%s (bf16 x 1.1/2.25)" % kind
+    t = out["tensor_rate_tflops"].get("tcgen05 3xtf32")
+    out["tcgen05_frac_of_tf32_peak"] = t / tf32 if (t and tf32) else None
+    return out
 
 
 def rom_error_estimate(r97, rom, prm, steps, n_inst=256):
