@@ -983,11 +983,15 @@ k_rom_lu(int Nr, T* __restrict__ J, const double* __restrict__ r, const int* __r
         for (int i = k + 1 + wid; i < Nr; i += nw) {
             T* const ri = row(i);
             const T l = ri[k] * inv;
-            for (int j = k + 1 + lane; j < Nr; j += 32) {
+            int j = k + 1 + lane;
+            if (j < Nr) {   // column k+1 (lane 0) feeds the next pivot search
                 const T v = ri[j] - l * rk[j];
                 ri[j] = v;
-                if (j == k + 1) lu_pick(best, bi, fabs(v), i);
+                if (lane == 0) lu_pick(best, bi, fabs(v), i);
+                j += 32;
             }
+#pragma unroll 4
+            for (; j < Nr; j += 32) ri[j] -= l * rk[j];
             if (KEEP) {
                 __syncwarp();   // every lane has read A[i][k] before lane 0 overwrites it
                 if (lane == 0) ri[k] = l;
