@@ -220,11 +220,14 @@ def test_rom_gemm_autotuning(params, request):
 
 @pytest.mark.gpu
 @pytest.mark.parametrize("Nr,fp64,in_place", [(70, True, False), (70, False, False), (112, True, True),
-                                              (150, False, True), (209, False, False), (209, True, True)])
+                                              (150, False, True), (209, False, False), (209, True, True),
+                                              (260, False, True), (300, False, False)])
 def test_rom_newton_step_lu_kernel(Nr, fp64, in_place):
     """The Newton-step LU kernel against a library solve: random matrices with rows
     scaled over twelve decades (the equilibration removes that) and a zero leading
-    diagonal (the pivoting has to move it), in shared memory or in place."""
+    diagonal (the pivoting has to move it), in shared memory, or with the leading
+    rows in shared memory and the rest in place (FP64 from 166 rows, FP32 from 236:
+    209 and 260, 300 here)."""
     B = _gpu()
     rng = np.random.default_rng(Nr)
     nb = 5
