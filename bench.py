@@ -555,8 +555,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fp32-coarse", action="store_true",
                     help="smoother and coarse-level products from FP32 operators instead of their BF16 copies")
-    ap.add_argument("--mg-stream", type=int, default=0, choices=[0, 1, 2],
-                    help="operator fetch of the BF16 coarse sweeps: 0 plain, 1 L2 prefetch, 2 staged in shared memory")
+    ap.add_argument("--mg-stream", type=int, default=0, choices=[0, 1, 2, 3],
+                    help="operator fetch of the BF16 coarse sweeps: 0 plain, 1 L2 prefetch, 2 staged in shared memory, "
+                         "3 plain at 5 blocks per SM")
     ap.add_argument("--kcycle-cgs1", action="store_true",
                     help="one Gram-Schmidt pass in the level-1 K-cycle instead of two (mg_kcycle_reorth = 0)")
     ap.add_argument("--no-ew", action="store_true",
