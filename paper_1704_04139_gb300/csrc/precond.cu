@@ -1985,12 +1985,22 @@ static void kcycle_l1(mb_cell* c) {
     kdots(c, b, 0, 1, b, m4, b2);
     k_knormalize<<<g, 256, 0, s>>>(b, b2, p->kV, m4), ::mb::count_launch(c);
     float4* bsave = L.b;   // the V-cycle reads lv[1].b: point it at the Krylov vector
+    // with an even number of iterate swaps in the V-cycle the result lands in
+    // the buffer level 1's x pointed at when it began: point it at Z_j directly
+    const int nswap = std::max(c->opt.mg_coarse_pre - 2, 0) + c->opt.mg_coarse_post;
     for (int j = 0; j < K; ++j) {
         float* Vj = p->kV + j * m4;
         DF4* Zj = p->kZ + j * L.cells;
         L.b = reinterpret_cast<float4*>(Vj);
-        vcycle(c, 1);
-        cudaMemcpyAsync(Zj, L.x, sizeof(DF4) * L.cells, cudaMemcpyDeviceToDevice, s);
+        if (nswap % 2 == 0) {
+            DF4* const x0 = L.x;
+            L.x = Zj;
+            vcycle(c, 1);
+            L.x = x0;
+        } else {
+            vcycle(c, 1);
+            cudaMemcpyAsync(Zj, L.x, sizeof(DF4) * L.cells, cudaMemcpyDeviceToDevice, s);
+        }
         lvl_matvec(c, L, Zj, p->kw);
         kdots(c, p->kV, m4, j + 1, p->kw, m4, h1);
         if (!c->opt.mg_kcycle_reorth && j + 1 <= 8) {
