@@ -90,8 +90,8 @@ typedef struct {
                               (bulk asynchronous prefetch); 2 post-smoothing sweeps of levels with
                               at least one tile of 256 cells per SM stage rows, right-hand side and
                               iterate in shared memory by bulk asynchronous copies (persistent,
-                              double-buffered); 3 plain loads with at most 48 registers (5 blocks
-                              of 256 per SM instead of 4) */
+                              double-buffered); 3 plain loads, the level-1 post-smoothing sweeps with
+                              at most 48 registers (5 blocks of 256 per SM instead of 4) */
     int    pass_start;     /* Newton start of plating active-set passes after the first: 0 u_old
                               (the previous time level); 1 (default) the previous pass's converged
                               state.  The solution of a pass depends only on its frozen gates, not on

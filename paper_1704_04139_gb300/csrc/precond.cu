@@ -1306,20 +1306,17 @@ __global__ void k_lvl_smooth2(Level L, float omega, DF4* __restrict__ x_out, int
     smooth2_cell<B16>(L, omega, x_out, cell);
 }
 
-// The two BF16 sweeps with at most 48 registers per thread (5 blocks of 256 per
-// SM instead of 4): more cells' loads in flight for a sweep bound by memory
-// latency at the cost of a few spilled registers (mg_stream = 3).
+// The level-1 BF16 sweep with at most 48 registers per thread (5 blocks of 256
+// per SM instead of 4): more cells' loads in flight for a sweep bound by memory
+// latency at the cost of a few spilled registers (mg_stream = 3; measured 37.7
+// against 41.5 us per level-1 sweep on a 4.2M-voxel cell, but the same bounds
+// on the fused first sweeps and the coarse levels made the step slower).
 __global__ void __launch_bounds__(256, 5) k_lvl_smooth_o5(Level L, const DF4* __restrict__ x_in,
                                                            const DF4* __restrict__ ec, int ccny, int ccnz,
                                                            float omega, DF4* __restrict__ x_out) {
     int64_t cell = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (cell >= L.cells) return;
     smooth_cell<true>(L, x_in, ec, ccny, ccnz, omega, x_out, cell);
-}
-__global__ void __launch_bounds__(256, 5) k_lvl_smooth2_o5(Level L, float omega, DF4* __restrict__ x_out) {
-    int64_t cell = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (cell >= L.cells) return;
-    smooth2_cell<true>(L, omega, x_out, cell);
 }
 
 template <bool B16>
@@ -1834,7 +1831,7 @@ static void lvl_smooth(mb_cell* c, Level& L, const DF4* xin, const DF4* ec, int 
     const int64_t ntiles = (L.cells + SWT - 1) / SWT;
     if (p->b16 && c->opt.mg_stream == 2 && xin && ntiles >= p->nsm && !g_staged_broken.load())
         k_lvl_smooth_staged<<<p->nsm, SWT, SW_SMEM, s>>>(L, xin, ec, ccny, ccnz, OMEGA_COARSE, xout, p->err);
-    else if (p->b16 && c->opt.mg_stream == 3)
+    else if (p->b16 && c->opt.mg_stream == 3 && &L == &p->lv[1])
         k_lvl_smooth_o5<<<g, 256, 0, s>>>(L, xin, ec, ccny, ccnz, OMEGA_COARSE, xout);
     else if (p->b16)
         k_lvl_smooth<true><<<g, 256, 0, s>>>(L, xin, ec, ccny, ccnz, OMEGA_COARSE, xout,
@@ -1847,9 +1844,7 @@ static void lvl_smooth(mb_cell* c, Level& L, const DF4* xin, const DF4* ec, int 
 static void lvl_smooth2(mb_cell* c, Level& L, DF4* xout) {
     cudaStream_t s = c->stream;
     unsigned g = nblk(L.cells);
-    if (c->pc->b16 && c->opt.mg_stream == 3)
-        k_lvl_smooth2_o5<<<g, 256, 0, s>>>(L, OMEGA_COARSE, xout);
-    else if (c->pc->b16)
+    if (c->pc->b16)
         k_lvl_smooth2<true><<<g, 256, 0, s>>>(L, OMEGA_COARSE, xout, c->opt.mg_stream == 1 ? c->pc->pf[1] : 0);
     else
         k_lvl_smooth2<false><<<g, 256, 0, s>>>(L, OMEGA_COARSE, xout, 0);
