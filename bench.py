@@ -555,7 +555,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fp32-coarse", action="store_true",
                     help="smoother and coarse-level products from FP32 operators instead of their BF16 copies")
-    ap.add_argument("--mg-stream", type=int, default=0, choices=[0, 1, 2, 3],
+    ap.add_argument("--mg-stream", type=int, default=3, choices=[0, 1, 2, 3],
                     help="operator fetch of the BF16 coarse sweeps: 0 plain, 1 L2 prefetch, 2 staged in shared memory, "
                          "3 plain at 5 blocks per SM")
     ap.add_argument("--kcycle-cgs1", action="store_true",
@@ -688,8 +688,10 @@ def main():
              "operator": (n_jvp, ms_jvp, 40.0 * N + 24.0 * NI + 16.0 * F, "k_jvp_lin (Krylov operator)",
                           "k_jvp_lin"),
              "level1_smoother": (n_ls, ms_ls, (op_b + 80.0) * c1 + 32.0 * c2 / 2.0,
-                                 "k_lvl_smooth<%s> (level-1 post-smoothing sweep)" % ("true" if opts.mg_bf16 else "false"),
-                                 "k_lvl_smooth")}
+                                 ("k_lvl_smooth_o5 (level-1 post-smoothing sweep, bf16, 5 blocks/SM)"
+                                  if (opts.mg_bf16 and args.mg_stream == 3) else
+                                  "k_lvl_smooth<%s> (level-1 post-smoothing sweep)" % ("true" if opts.mg_bf16 else "false")),
+                                 "k_lvl_smooth_o5" if (opts.mg_bf16 and args.mg_stream == 3) else "k_lvl_smooth")}
     dom = max(kinds, key=lambda k: kinds[k][1])
     n_k, ms_k, bytes_per_launch, kname, kfile = kinds[dom]
     avg_ms = ms_k / max(n_k, 1)

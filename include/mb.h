@@ -84,14 +84,15 @@ typedef struct {
     int    mg_bf16;        /* 1: the fine smoother's stencil and the coarse-level operators are
                               applied from BF16 copies (FP32 arithmetic); 0: FP32 operators */
     int    mg_stream;      /* how the BF16 coarse sweeps and products fetch their operator rows
-                              (same results in every mode): 0 plain loads (default; the fastest
-                              measured on GB300: 50 % occupancy hides the latency); 1 each block first
+                              (same results in every mode): 0 plain loads; 1 each block first
                               prefetches into L2 the rows of the block one resident wave ahead
                               (bulk asynchronous prefetch); 2 post-smoothing sweeps of levels with
                               at least one tile of 256 cells per SM stage rows, right-hand side and
                               iterate in shared memory by bulk asynchronous copies (persistent,
-                              double-buffered); 3 plain loads, the level-1 post-smoothing sweeps with
-                              at most 48 registers (5 blocks of 256 per SM instead of 4) */
+                              double-buffered); 3 (default) plain loads, the level-1 post-smoothing
+                              sweeps with at most 48 registers (5 blocks of 256 per SM instead of 4:
+                              37.3 against 41.1 us per sweep and 1 % faster steps on a 4.2M-voxel
+                              cell, the fastest mode measured) */
     int    pass_start;     /* Newton start of plating active-set passes after the first: 0 u_old
                               (the previous time level); 1 (default) the previous pass's converged
                               state.  The solution of a pass depends only on its frozen gates, not on

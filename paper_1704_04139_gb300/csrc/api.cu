@@ -113,7 +113,7 @@ void mb_opts_default(mb_solver_opts* o) {
     o->mg_coarse_pre = 2;
     o->mg_coarse_post = 2;
     o->mg_bf16 = 1;
-    o->mg_stream = 0;
+    o->mg_stream = 3;
     o->pass_start = 1;
     o->mg_kcycle_reorth = 1;
     o->krylov_forcing = 1;

@@ -35,7 +35,7 @@ def _gpu():
 
 def _bench_opts(B, prec):
     import bench
-    args = types.SimpleNamespace(fp32_coarse=False, mg_stream=0, mg_tail=False, no_ew=False, kcycle_cgs1=False)
+    args = types.SimpleNamespace(fp32_coarse=False, mg_stream=3, mg_tail=False, no_ew=False, kcycle_cgs1=False)
     return bench.fom_opts(B, prec, args)
 
 

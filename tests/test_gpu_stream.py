@@ -1,7 +1,8 @@
 """The ways the coarse sweeps fetch their operator rows compute the same
 thing: plain loads (mg_stream 0), L2 prefetch one resident wave ahead (1)
-and the staged sweep with bulk asynchronous copies into shared memory (2)
-give bit-identical preconditioner applications and implicit steps, on a cell
+the staged sweep with bulk asynchronous copies into shared memory (2) and
+the level-1 sweep at 5 blocks per SM (3) give bit-identical preconditioner
+applications and implicit steps, on a cell
 whose level 1 holds more than one tile of 256 cells per SM, so that the
 staged kernel runs there."""
 import numpy as np
@@ -27,7 +28,7 @@ def test_stream_modes_bit_identical(params):
     B, torch = _gpu()
     lab = syn.full_cell(64, 64, 53, 22, 53, 0.35, 0.35, ("uniform", 2, 4), (31, 32))
     cells = {s: B.Cell(lab, 1e-6, params, B.default_opts(precision=1, newton_tol=1e-10, krylov_rtol=1e-4,
-                                                         mg_stream=s)) for s in (0, 1, 2)}
+                                                         mg_stream=s)) for s in (0, 1, 2, 3)}
     a, b = cells[2], cells[0]
     nsm = torch.cuda.get_device_properties(0).multi_processor_count
     l1 = a.debug_levels()[0]
@@ -41,10 +42,10 @@ def test_stream_modes_bit_identical(params):
     r = rng.standard_normal(a.n)
     z = {s: cells[s].debug_precond(u, gate, 1.0, r) for s in cells}
     assert np.all(np.isfinite(z[0]))
-    assert np.array_equal(z[1], z[0]) and np.array_equal(z[2], z[0])
+    assert np.array_equal(z[1], z[0]) and np.array_equal(z[2], z[0]) and np.array_equal(z[3], z[0])
     I = -2.0 * a.i_1c
     info = {s: cells[s].step(1.0, I) for s in cells}
-    for s in (1, 2):
+    for s in (1, 2, 3):
         assert info[s]["krylov_its"] == info[0]["krylov_its"] and info[s]["V_cell"] == info[0]["V_cell"]
         assert np.array_equal(cells[s].state(), cells[0].state())
     for cell in cells.values():
