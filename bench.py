@@ -64,7 +64,8 @@ def fom_opts(B, prec, args):
                           newton_maxit=20, krylov_maxit=300, max_halvings=3,
                           mg_bf16=0 if args.fp32_coarse else 1, mg_stream=args.mg_stream,
                           mg_tail=1 if args.mg_tail else 0, krylov_forcing=0 if args.no_ew else 1,
-                          mg_kcycle_reorth=0 if args.kcycle_cgs1 else 1)
+                          mg_kcycle_reorth=0 if args.kcycle_cgs1 else 1, mg_kcycle=args.mg_kcycle,
+                          mg_smooth=args.mg_smooth, mg_coarse_pre=args.mg_coarse[0], mg_coarse_post=args.mg_coarse[1])
 
 
 def step_record(infos):
@@ -560,6 +561,10 @@ def main():
                          "3 plain at 5 blocks per SM")
     ap.add_argument("--kcycle-cgs1", action="store_true",
                     help="one Gram-Schmidt pass in the level-1 K-cycle instead of two (mg_kcycle_reorth = 0)")
+    ap.add_argument("--mg-kcycle", type=int, default=5, help="FGMRES iterations of the level-1 K-cycle")
+    ap.add_argument("--mg-smooth", type=int, default=2, help="fine-level sweeps before and after the coarse correction")
+    ap.add_argument("--mg-coarse", type=int, nargs=2, default=[2, 2], metavar=("PRE", "POST"),
+                    help="sweeps before and after the coarse correction on levels >= 1")
     ap.add_argument("--no-ew", action="store_true",
                     help="every linear solve to krylov_rtol instead of Eisenstat-Walker forcing (krylov_forcing = 0)")
     ap.add_argument("--mg-tail", action="store_true",
@@ -741,7 +746,8 @@ def main():
                           "dt_s": dt, "crate": CRATE[args.workload], "precision": args.precision,
                           "coarse_operators": "fp32" if args.fp32_coarse else "bf16", "mg_stream": args.mg_stream,
                           "mg_tail": 1 if args.mg_tail else 0, "krylov_forcing": 0 if args.no_ew else 1,
-                          "mg_kcycle_reorth": 0 if args.kcycle_cgs1 else 1,
+                          "mg_kcycle_reorth": 0 if args.kcycle_cgs1 else 1, "mg_kcycle": args.mg_kcycle,
+                          "mg_smooth": args.mg_smooth, "mg_coarse": list(args.mg_coarse),
                           "l2": "working set > 129 MB L2, no flush", "parallelism": "replicas" if ws > 1 else "1 GPU"},
                "clocks": clk, "e2e": e2e, "gpu_launches": int(launches), "roofline": roof,
                "cpu_baseline": cpu,
