@@ -158,7 +158,6 @@ struct Precond {
     float* kw = nullptr;       // m4
     double* kH = nullptr;      // (KCYC_MAX+1) x KCYC_MAX + scalars
     double* kred = nullptr;    // RED_BLOCKS x 8 partials
-    int* kticket = nullptr;    // ticket counter of the fused reductions (0 between them)
 };
 
 // set when a staged sweep timed out and could not drain its bulk copies: the
@@ -1534,38 +1533,9 @@ __global__ void k_prolong_fine(Dims D, const uint32_t* __restrict__ vc, Level C,
 // Small Krylov kernels whose scalars stay in device memory, so the level-1
 // K-cycle needs no host round trip.  Basis vectors FP32, dot products with
 // FP32 products and FP64 block sums.
-// The K-cycle's reductions end in the kernel that produced the partials: the
-// last block to store its partials (an atomic ticket after a fence, as in the
-// CUDA threadFenceReduction sample) sums each result's RED_BLOCKS partials in
-// the order of k_reduce_final, so the results are the two-kernel ones bit for
-// bit, one launch fewer per reduction; it then resets the ticket counter.
-__device__ inline void last_block_finalize(const double* partials, int nres, double* out, int* ticket) {
-    __shared__ int last;
-    __shared__ double sh[RED_THREADS];
-    __threadfence();   // this block's partial stores, before its ticket
-    __syncthreads();
-    if (threadIdx.x == 0) last = atomicAdd(ticket, 1) == (int)gridDim.x - 1;
-    __syncthreads();
-    if (!last) return;
-    __threadfence();
-    for (int k = 0; k < nres; ++k) {
-        double a = 0.0;
-        for (int i = threadIdx.x; i < RED_BLOCKS; i += blockDim.x) a = a + __ldcg(&partials[k * RED_BLOCKS + i]);
-        sh[threadIdx.x] = a;
-        __syncthreads();
-        for (int st = blockDim.x / 2; st > 0; st >>= 1) {
-            if (threadIdx.x < st) sh[threadIdx.x] = sh[threadIdx.x] + sh[threadIdx.x + st];
-            __syncthreads();
-        }
-        if (threadIdx.x == 0) out[k] = sh[0];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) *ticket = 0;
-}
-
 __global__ void __launch_bounds__(RED_THREADS)
 k_kdot(const float* __restrict__ V, int64_t stride, int cnt, const float* __restrict__ w, int64_t n,
-       double* partials, double* out = nullptr, int* ticket = nullptr) {
+       double* partials) {
     float acc32[8];
 #pragma unroll
     for (int j = 0; j < 8; ++j) acc32[j] = 0.f;
@@ -1576,7 +1546,6 @@ k_kdot(const float* __restrict__ V, int64_t stride, int cnt, const float* __rest
             if (j < cnt) acc32[j] = fmaf(V[j * stride + i], wi, acc32[j]);
     }
     block_reduce_store_f32<8>(acc32, partials);
-    if (ticket) last_block_finalize(partials, cnt, out, ticket);
 }
 
 // w += sign * sum_j h[j] V_j (h on the device; converted once per block)
@@ -1600,7 +1569,7 @@ __global__ void k_kupdate(const float* __restrict__ V, int64_t stride, int cnt, 
 template <bool NORM>
 __global__ void __launch_bounds__(RED_THREADS)
 k_kupd_dot(const float* __restrict__ V, int64_t stride, int cnt, const double* __restrict__ h,
-           float* __restrict__ w, int64_t n, double* partials, double* out = nullptr, int* ticket = nullptr) {
+           float* __restrict__ w, int64_t n, double* partials) {
     constexpr int K = NORM ? 1 : 8;
     __shared__ float hs[8];
     if (threadIdx.x < cnt) hs[threadIdx.x] = (float)h[threadIdx.x];
@@ -1628,7 +1597,6 @@ k_kupd_dot(const float* __restrict__ V, int64_t stride, int cnt, const double* _
         }
     }
     block_reduce_store_f32<K>(acc32, partials);
-    if (ticket) last_block_finalize(partials, NORM ? 1 : cnt, out, ticket);
 }
 
 // out = a / sqrt(max(d2, tiny)) (the scale computed once per block)
@@ -1778,10 +1746,7 @@ int precond_create(mb_cell* c) {
     p->kw = (float*)cell_alloc(c, 4 * (size_t)m4);
     p->kH = (double*)cell_alloc(c, 8 * (size_t)((KCYC_MAX + 1) * KCYC_MAX + 128));
     p->kred = (double*)cell_alloc(c, 8 * (size_t)RED_BLOCKS * 8);
-    p->kticket = (int*)cell_alloc(c, 16);
-    if (!p->cdense || !p->cinv || !p->cstat || !p->kV || !p->kZ || !p->kw || !p->kH || !p->kred || !p->kticket)
-        return MB_ENOMEM;
-    MB_CUDA(cudaMemset(p->kticket, 0, 16));
+    if (!p->cdense || !p->cinv || !p->cstat || !p->kV || !p->kZ || !p->kw || !p->kH || !p->kred) return MB_ENOMEM;
     // persistent coarse tail: from the first level >= 2 that one block of
     // TAIL_THREADS threads per SM covers; its grid is one block per
     // TAIL_THREADS cells of that level (all co-resident), so a small cell's
@@ -1984,8 +1949,8 @@ static void kdots(mb_cell* c, const float* V, int64_t stride, int cnt, const flo
     cudaStream_t s = c->stream;
     for (int j0 = 0; j0 < cnt; j0 += 8) {
         int k = cnt - j0 < 8 ? cnt - j0 : 8;
-        k_kdot<<<RED_BLOCKS, RED_THREADS, 0, s>>>(V + j0 * stride, stride, k, w, n, p->kred, out + j0, p->kticket),
-            ::mb::count_launch(c);
+        k_kdot<<<RED_BLOCKS, RED_THREADS, 0, s>>>(V + j0 * stride, stride, k, w, n, p->kred), ::mb::count_launch(c);
+        k_reduce_final<false><<<k, RED_THREADS, 0, s>>>(p->kred, k, out + j0), ::mb::count_launch(c);
     }
 }
 
@@ -2036,17 +2001,17 @@ static void kcycle_l1(mb_cell* c) {
         if (!c->opt.mg_kcycle_reorth && j + 1 <= 8) {
             // one classical Gram-Schmidt pass, fused with the norm that follows it
             cudaMemsetAsync(h2, 0, 8 * (size_t)(j + 1), s);
-            k_kupd_dot<true><<<RED_BLOCKS, RED_THREADS, 0, s>>>(p->kV, m4, j + 1, h1, p->kw, m4, p->kred, wn2,
-                                                                  p->kticket),
+            k_kupd_dot<true><<<RED_BLOCKS, RED_THREADS, 0, s>>>(p->kV, m4, j + 1, h1, p->kw, m4, p->kred),
                 ::mb::count_launch(c);
+            k_reduce_final<false><<<1, RED_THREADS, 0, s>>>(p->kred, 1, wn2), ::mb::count_launch(c);
         } else if (j + 1 <= 8) {
             // CGS2 with each update fused into the products that follow it
-            k_kupd_dot<false><<<RED_BLOCKS, RED_THREADS, 0, s>>>(p->kV, m4, j + 1, h1, p->kw, m4, p->kred, h2,
-                                                                   p->kticket),
+            k_kupd_dot<false><<<RED_BLOCKS, RED_THREADS, 0, s>>>(p->kV, m4, j + 1, h1, p->kw, m4, p->kred),
                 ::mb::count_launch(c);
-            k_kupd_dot<true><<<RED_BLOCKS, RED_THREADS, 0, s>>>(p->kV, m4, j + 1, h2, p->kw, m4, p->kred, wn2,
-                                                                  p->kticket),
+            k_reduce_final<false><<<j + 1, RED_THREADS, 0, s>>>(p->kred, j + 1, h2), ::mb::count_launch(c);
+            k_kupd_dot<true><<<RED_BLOCKS, RED_THREADS, 0, s>>>(p->kV, m4, j + 1, h2, p->kw, m4, p->kred),
                 ::mb::count_launch(c);
+            k_reduce_final<false><<<1, RED_THREADS, 0, s>>>(p->kred, 1, wn2), ::mb::count_launch(c);
         } else {
             k_kupdate<<<g, 256, 0, s>>>(p->kV, m4, j + 1, h1, -1.f, p->kw, m4), ::mb::count_launch(c);
             kdots(c, p->kV, m4, j + 1, p->kw, m4, h2);
