@@ -371,7 +371,7 @@ static int krylov_create(mb_cell* c, Krylov** out) {
 }
 
 // Solve J delta = -R at the current c->u (FP64 residual in c->r) into c->du.
-static int linear_solve(mb_cell* c, double dt, double rtol, int* its, double* relres) {
+static int linear_solve(mb_cell* c, double dt, double rtol, int* its, double* relres, bool pc_setup = true) {
     int64_t n = c->n;
     cudaStream_t s = c->stream;
     k_convert<double, float><<<nblk(n), 256, 0, s>>>(c->u, c->u32, n), ::mb::count_launch(c);
@@ -381,8 +381,10 @@ static int linear_solve(mb_cell* c, double dt, double rtol, int* its, double* re
     rc = c->opt.precision == MB_PREC_MIXED ? launch_lin_setup<float>(c, c->u32, c->gate, s)
                                            : launch_lin_setup<double>(c, c->u, c->gate, s);
     if (rc) return rc;
-    if ((rc = precond_setup(c, c->u32, c->gate, dt))) return rc;
-    if ((rc = precond_setup_fine(c))) return rc;
+    if (pc_setup) {
+        if ((rc = precond_setup(c, c->u32, c->gate, dt))) return rc;
+        if ((rc = precond_setup_fine(c))) return rc;
+    }
     if (!c->kd && (rc = krylov_create(c, &c->kd))) return rc;
     Krylov* K = c->kd;
     k_scale_rhs<<<nblk(n), 256, 0, s>>>(c->D, c->vcode, c->r, inv_scales(c, 1, dt), c->rowinv, K->b), ::mb::count_launch(c);
@@ -411,6 +413,7 @@ static int newton(mb_cell* c, double dt, double I_app, bool from_old, int* its_o
     if (from_old) MB_CUDA(cudaMemcpyAsync(c->u, c->u_old, 8 * n, cudaMemcpyDeviceToDevice, s));
     *ok = false;
     double rn_prev = 0.0, eta_prev = 0.0;
+    int base_its = 0, last_its = 0;   // Krylov iterations after the last preconditioner rebuild, and of the last solve
     for (int it = 1; it <= c->opt.newton_maxit; ++it) {
         int rc = launch_residual_split(c, c->u, c->u_old, c->gate, dt, I_app, c->r, s);
         if (rc) return rc;
@@ -437,9 +440,15 @@ static int newton(mb_cell* c, double dt, double I_app, bool from_old, int* its_o
         eta_prev = eta;
         int ki = 0;
         double rr = 0;
-        rc = linear_solve(c, dt, eta, &ki, &rr);
+        // the preconditioner: rebuilt every iteration, or (pc_lag) at the first and
+        // whenever the last solve needed clearly more iterations than the first after
+        // the previous rebuild
+        const bool setup = !c->opt.pc_lag || it == 1 || last_its > 1.5 * base_its + 2;
+        rc = linear_solve(c, dt, eta, &ki, &rr, setup);
         if (rc == MB_ENOCONV) { *its_out = it; return MB_OK; }
         if (rc) return rc;
+        if (setup) base_its = ki;
+        last_its = ki;
         *kits += ki;
         // the step length caps the update of the voxel unknowns (c, phi: the
         // arguments of the exponentials) in their scales and of each plated
