@@ -110,13 +110,14 @@ typedef struct {
                               per-level launches, measured faster on GB300 inside the preconditioner's
                               CUDA graph (2.27 against 2.43 ms per application on a 4.2M-voxel cell).
                               Applies to BF16 operators (mg_bf16 = 1). */
-    int    pc_lag;         /* 0 (default): the preconditioner (row scales, condensation, level
-                              operators, coarse inverse, fine stencil) is rebuilt at every Newton
-                              iteration; 1: at the first iteration of each Newton solve and then only
+    int    pc_lag;         /* 0: the preconditioner (row scales, condensation, level operators,
+                              coarse inverse, fine stencil) is rebuilt at every Newton iteration;
+                              1 (default): at the first iteration of each Newton solve and then only
                               when a linear solve took more than 1.5 x + 2 the Krylov iterations of
                               the first solve after the last rebuild (the linearisation of the Krylov
                               operator itself is always current; only convergence speed depends on
-                              the preconditioner's age) */
+                              the preconditioner's age).  On a 4.2M-voxel cell: the same Newton and
+                              Krylov iterations, 111.8 against 120.2 ms per step */
 } mb_solver_opts;
 
 typedef struct {

@@ -118,7 +118,7 @@ void mb_opts_default(mb_solver_opts* o) {
     o->mg_kcycle_reorth = 1;
     o->krylov_forcing = 1;
     o->mg_tail = 0;
-    o->pc_lag = 0;
+    o->pc_lag = 1;
 }
 
 static int check_opts(const mb_solver_opts* o) {
