@@ -66,7 +66,7 @@ def fom_opts(B, prec, args):
                           mg_tail=1 if args.mg_tail else 0, krylov_forcing=0 if args.no_ew else 1,
                           mg_kcycle_reorth=0 if args.kcycle_cgs1 else 1, mg_kcycle=args.mg_kcycle,
                           mg_smooth=args.mg_smooth, mg_coarse_pre=args.mg_coarse[0], mg_coarse_post=args.mg_coarse[1],
-                          pc_lag=0 if args.no_pc_lag else 1)
+                          pc_lag=0 if args.no_pc_lag else 1, pc_lag_drift=args.pc_lag_drift)
 
 
 def step_record(infos):
@@ -564,6 +564,8 @@ def main():
                     help="one Gram-Schmidt pass in the level-1 K-cycle instead of two (mg_kcycle_reorth = 0)")
     ap.add_argument("--no-pc-lag", action="store_true",
                     help="rebuild the preconditioner at every Newton iteration (pc_lag = 0)")
+    ap.add_argument("--pc-lag-drift", type=float, default=0.05,
+                    help="scaled size of the Newton updates after which a lagged preconditioner is rebuilt")
     ap.add_argument("--mg-kcycle", type=int, default=5, help="FGMRES iterations of the level-1 K-cycle")
     ap.add_argument("--mg-smooth", type=int, default=2, help="fine-level sweeps before and after the coarse correction")
     ap.add_argument("--mg-coarse", type=int, nargs=2, default=[2, 2], metavar=("PRE", "POST"),
@@ -751,7 +753,7 @@ def main():
                           "mg_tail": 1 if args.mg_tail else 0, "krylov_forcing": 0 if args.no_ew else 1,
                           "mg_kcycle_reorth": 0 if args.kcycle_cgs1 else 1, "mg_kcycle": args.mg_kcycle,
                           "mg_smooth": args.mg_smooth, "mg_coarse": list(args.mg_coarse),
-                          "pc_lag": 0 if args.no_pc_lag else 1,
+                          "pc_lag": 0 if args.no_pc_lag else 1, "pc_lag_drift": args.pc_lag_drift,
                           "l2": "working set > 129 MB L2, no flush", "parallelism": "replicas" if ws > 1 else "1 GPU"},
                "clocks": clk, "e2e": e2e, "gpu_launches": int(launches), "roofline": roof,
                "cpu_baseline": cpu,

@@ -113,11 +113,20 @@ typedef struct {
     int    pc_lag;         /* 0: the preconditioner (row scales, condensation, level operators,
                               coarse inverse, fine stencil) is rebuilt at every Newton iteration;
                               1 (default): at the first iteration of each Newton solve and then only
-                              when a linear solve took more than 1.5 x + 2 the Krylov iterations of
-                              the first solve after the last rebuild (the linearisation of the Krylov
-                              operator itself is always current; only convergence speed depends on
-                              the preconditioner's age).  On a 4.2M-voxel cell: the same Newton and
-                              Krylov iterations, 111.8 against 120.2 ms per step */
+                              when the iterate has moved by more than pc_lag_drift since the last
+                              rebuild, when a linear solve took more than 1.5 x + 2 the Krylov
+                              iterations of the first solve after the last rebuild, or when a solve
+                              with the lagged preconditioner did not reach its tolerance (that solve
+                              is repeated after the rebuild).  The Krylov operator is always the
+                              current linearisation */
+    double pc_lag_drift;   /* with pc_lag = 1 the preconditioner is rebuilt once the damped Newton
+                              updates since its last rebuild sum to more than this in the step
+                              cap's scaled max-norm (the change of the exponentials' arguments and
+                              of the plated inventories relative to max(n_c, |n|)), so that a lagged
+                              preconditioner only serves iterates close to the one it was built at:
+                              its coarse correction of the near-null potential mode follows the
+                              Butler-Volmer partials, which change fast with the state, and its row
+                              scales define the norm of the Krylov tolerance.  Default 0.05; >= 0 */
 } mb_solver_opts;
 
 typedef struct {

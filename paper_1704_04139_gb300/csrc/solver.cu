@@ -414,6 +414,7 @@ static int newton(mb_cell* c, double dt, double I_app, bool from_old, int* its_o
     *ok = false;
     double rn_prev = 0.0, eta_prev = 0.0;
     int base_its = 0, last_its = 0;   // Krylov iterations after the last preconditioner rebuild, and of the last solve
+    double drift = 0.0;               // sum of the damped updates' scaled sizes since that rebuild
     for (int it = 1; it <= c->opt.newton_maxit; ++it) {
         int rc = launch_residual_split(c, c->u, c->u_old, c->gate, dt, I_app, c->r, s);
         if (rc) return rc;
@@ -440,14 +441,28 @@ static int newton(mb_cell* c, double dt, double I_app, bool from_old, int* its_o
         eta_prev = eta;
         int ki = 0;
         double rr = 0;
-        // the preconditioner: rebuilt every iteration, or (pc_lag) at the first and
-        // whenever the last solve needed clearly more iterations than the first after
-        // the previous rebuild
-        const bool setup = !c->opt.pc_lag || it == 1 || last_its > 1.5 * base_its + 2;
+        // the preconditioner: rebuilt every iteration, or
+        // (pc_lag) at the first, once the iterate has moved more than
+        // pc_lag_drift since the previous rebuild, and whenever the last solve
+        // needed clearly more iterations than the first after that rebuild
+        bool setup = !c->opt.pc_lag || it == 1 || drift > c->opt.pc_lag_drift || last_its > 1.5 * base_its + 2;
         rc = linear_solve(c, dt, eta, &ki, &rr, setup);
+        if (!setup && (rc == MB_ENOCONV || (rc == MB_OK && !(rr <= eta)))) {
+            // the lagged preconditioner left the solve short of its tolerance:
+            // rebuild it at the current iterate and solve again
+            if (debug_level() > 0)
+                fprintf(stderr, "[mb] newton it %d lagged solve missed its tolerance (krylov %d relres %.2e)\n", it,
+                        ki, rr);
+            *kits += ki;
+            setup = true;
+            rc = linear_solve(c, dt, eta, &ki, &rr, true);
+        }
         if (rc == MB_ENOCONV) { *its_out = it; return MB_OK; }
         if (rc) return rc;
-        if (setup) base_its = ki;
+        if (setup) {
+            base_its = ki;
+            drift = 0.0;
+        }
         last_its = ki;
         *kits += ki;
         // the step length caps the update of the voxel unknowns (c, phi: the
@@ -461,9 +476,10 @@ static int newton(mb_cell* c, double dt, double I_app, bool from_old, int* its_o
         if ((rc = scaled_maxnorm(c, c->du, 0, dt, &dn, &dv, c->u))) return rc;
         if (!(dn < 1e200)) { *its_out = it; return MB_OK; }
         double lam = dv <= DELTA_MAX ? 1.0 : DELTA_MAX / dv;
+        drift += lam * dv;
         if (debug_level() > 0)
-            fprintf(stderr, "[mb] newton it %d |R|_s %.3e |d|_s %.3e lam %.3f krylov %d relres %.2e\n", it, rn,
-                    dn, lam, ki, rr);
+            fprintf(stderr, "[mb] newton it %d |R|_s %.3e |d|_s %.3e |d|_v %.3e lam %.3f krylov %d relres %.2e%s\n",
+                    it, rn, dn, dv, lam, ki, rr, setup ? " rebuilt" : "");
         k_axpy_d<<<nblk(n), 256, 0, s>>>(lam, c->du, c->u, n), ::mb::count_launch(c);
         MB_CUDA_LAUNCH("newton update");
         if (c->snap_u) {   // record the Newton stage (reduced-model snapshots)
