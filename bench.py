@@ -63,10 +63,11 @@ def fom_opts(B, prec, args):
     return B.default_opts(precision=prec, newton_tol=1e-10, krylov_rtol=1e-4 if prec else 1e-6,
                           newton_maxit=20, krylov_maxit=300, max_halvings=3,
                           mg_bf16=0 if args.fp32_coarse else 1, mg_stream=args.mg_stream,
-                          mg_tail=1 if args.mg_tail else 0, krylov_forcing=0 if args.no_ew else 1,
+                          mg_tail=args.mg_tail, krylov_forcing=0 if args.no_ew else 1,
                           mg_kcycle_reorth=0 if args.kcycle_cgs1 else 1, mg_kcycle=args.mg_kcycle,
                           mg_smooth=args.mg_smooth, mg_coarse_pre=args.mg_coarse[0], mg_coarse_post=args.mg_coarse[1],
-                          pc_lag=0 if args.no_pc_lag else 1, pc_lag_drift=args.pc_lag_drift)
+                          pc_lag=0 if args.no_pc_lag else 1, pc_lag_drift=args.pc_lag_drift,
+                          mg_pdl=args.mg_pdl)
 
 
 def step_record(infos):
@@ -564,6 +565,8 @@ def main():
                     help="one Gram-Schmidt pass in the level-1 K-cycle instead of two (mg_kcycle_reorth = 0)")
     ap.add_argument("--no-pc-lag", action="store_true",
                     help="rebuild the preconditioner at every Newton iteration (pc_lag = 0)")
+    ap.add_argument("--mg-pdl", type=int, default=0, choices=[0, 1],
+                    help="programmatic dependent launch of the preconditioner's kernels (mg_pdl)")
     ap.add_argument("--pc-lag-drift", type=float, default=0.05,
                     help="scaled size of the Newton updates after which a lagged preconditioner is rebuilt")
     ap.add_argument("--mg-kcycle", type=int, default=5, help="FGMRES iterations of the level-1 K-cycle")
@@ -572,8 +575,9 @@ def main():
                     help="sweeps before and after the coarse correction on levels >= 1")
     ap.add_argument("--no-ew", action="store_true",
                     help="every linear solve to krylov_rtol instead of Eisenstat-Walker forcing (krylov_forcing = 0)")
-    ap.add_argument("--mg-tail", action="store_true",
-                    help="coarse V-cycle levels in one persistent cooperative launch instead of per-level launches")
+    ap.add_argument("--mg-tail", type=int, default=0,
+                    help="coarse V-cycle levels from this one (1: the first that one wave covers) in one persistent "
+                         "cooperative launch instead of per-level launches (0: per-level launches)")
     ap.add_argument("--no-fp64-arm", action="store_true",
                     help="skip the FP64 run of the same steps (and the mixed-vs-FP64 errors)")
     ap.add_argument("--no-rom", action="store_true", help="skip the reduced-model and serving measurements")
@@ -750,10 +754,11 @@ def main():
                           "device_bytes": int(cell.device_bytes),
                           "dt_s": dt, "crate": CRATE[args.workload], "precision": args.precision,
                           "coarse_operators": "fp32" if args.fp32_coarse else "bf16", "mg_stream": args.mg_stream,
-                          "mg_tail": 1 if args.mg_tail else 0, "krylov_forcing": 0 if args.no_ew else 1,
+                          "mg_tail": args.mg_tail, "krylov_forcing": 0 if args.no_ew else 1,
                           "mg_kcycle_reorth": 0 if args.kcycle_cgs1 else 1, "mg_kcycle": args.mg_kcycle,
                           "mg_smooth": args.mg_smooth, "mg_coarse": list(args.mg_coarse),
                           "pc_lag": 0 if args.no_pc_lag else 1, "pc_lag_drift": args.pc_lag_drift,
+                          "mg_pdl": args.mg_pdl,
                           "l2": "working set > 129 MB L2, no flush", "parallelism": "replicas" if ws > 1 else "1 GPU"},
                "clocks": clk, "e2e": e2e, "gpu_launches": int(launches), "roofline": roof,
                "cpu_baseline": cpu,

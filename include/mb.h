@@ -104,12 +104,15 @@ typedef struct {
                               forcing terms (choice 2, safeguarded) within [krylov_rtol, 0.1]:
                               26 % fewer preconditioner applications per step on a 4.2M-voxel
                               cell; the Newton tolerance, and so the converged state, is the same */
-    int    mg_tail;        /* 1: the V-cycle on the coarse levels that one wave of the GPU covers
-                              (level 2 down) runs as one persistent cooperative launch with grid
-                              barriers instead of one launch per sweep (same results); 0 (default):
-                              per-level launches, measured faster on GB300 inside the preconditioner's
-                              CUDA graph (2.27 against 2.43 ms per application on a 4.2M-voxel cell).
-                              Applies to BF16 operators (mg_bf16 = 1). */
+    int    mg_tail;        /* 0 (default): one launch per coarse sweep, restriction and coarsest
+                              solve; 1: the V-cycle from the first level >= 2 that one wave of the
+                              GPU covers (one block of 512 threads per SM) down to the coarsest
+                              solve and back runs as one persistent cooperative launch with grid
+                              barriers between its phases (same results); k >= 2: the same from
+                              the first level >= k that one wave covers (0..16).  Per-level
+                              launches measured faster on GB300 inside the preconditioner's CUDA
+                              graph (2.27 against 2.43 ms per application on a 4.2M-voxel cell with
+                              the tail from level 2).  Applies to BF16 operators (mg_bf16 = 1). */
     int    pc_lag;         /* 0: the preconditioner (row scales, condensation, level operators,
                               coarse inverse, fine stencil) is rebuilt at every Newton iteration;
                               1 (default): at the first iteration of each Newton solve and then only
@@ -127,6 +130,10 @@ typedef struct {
                               its coarse correction of the near-null potential mode follows the
                               Butler-Volmer partials, which change fast with the state, and its row
                               scales define the norm of the Krylov tolerance.  Default 0.05; >= 0 */
+    int    mg_pdl;         /* 1: the kernels of a preconditioner application are launched with
+                              programmatic dependent launch: each may be scheduled while its
+                              predecessor drains and waits, before its first memory access, until
+                              that predecessor has completed (same results); 0: plain launches */
 } mb_solver_opts;
 
 typedef struct {

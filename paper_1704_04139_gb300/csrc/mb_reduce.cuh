@@ -6,6 +6,17 @@
 
 namespace mb {
 
+// Entry of a kernel that may be launched with programmatic dependent launch
+// (programmatic stream serialization): such a launch can be scheduled before
+// its predecessor in the stream has finished, so the kernel first waits until
+// that predecessor has completed and its writes are visible, and only then
+// lets its own successor be scheduled.  Called before any memory access; in a
+// plain launch both instructions return at once.
+__device__ __forceinline__ void pdl_entry() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 template <int K, bool MAX>
 __device__ inline void block_reduce_store(double (&acc)[K], double* partials) {
     __shared__ double sh[K][RED_THREADS / 32];
@@ -53,6 +64,7 @@ __device__ inline void block_reduce_store_f32(float (&acc)[K], double* partials)
 // one block (RED_THREADS threads) per result k; out[k] = reduction of partials[k][*]
 template <bool MAX>
 __global__ void k_reduce_final(const double* __restrict__ partials, int K, double* __restrict__ out) {
+    pdl_entry();
     __shared__ double sh[RED_THREADS];
     int k = blockIdx.x;
     double a = MAX ? -1.0 : 0.0;

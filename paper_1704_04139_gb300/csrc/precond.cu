@@ -121,6 +121,7 @@ struct PcGraph {
     int nu = 0;
     int reorth = 0;
     int tail = 0;
+    int pdl = 0;
     cudaGraphExec_t exec = nullptr;
     int64_t nodes = 0;                 // kernels per execution
     std::vector<ProfPair> ev;          // timing events recorded by the graph (prof graphs)
@@ -309,6 +310,7 @@ k_bj_setup(ParT<float> P, Dims D, const uint32_t* __restrict__ vc, const uint16_
 __global__ void __launch_bounds__(256)
 k_condense_rhs(Dims D, const uint32_t* __restrict__ vc, const float* __restrict__ fc, const float* __restrict__ r,
                const float* __restrict__ rowdiag, float* __restrict__ rv) {
+    pdl_entry();
     int z = blockIdx.x * blockDim.x + threadIdx.x;
     int y = blockIdx.y * blockDim.y + threadIdx.y;
     int t = blockIdx.z;
@@ -347,6 +349,7 @@ k_condense_rhs(Dims D, const uint32_t* __restrict__ vc, const float* __restrict_
 __global__ void k_face_solve(Dims D, const int32_t* __restrict__ pg, const int32_t* __restrict__ pe,
                              const float* __restrict__ fc, const float* __restrict__ r,
                              const float* __restrict__ rowdiag, float2* __restrict__ z) {
+    pdl_entry();
     int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (f >= D.F) return;
     const int64_t N = D.N;
@@ -360,6 +363,7 @@ __global__ void k_face_solve(Dims D, const int32_t* __restrict__ pg, const int32
 // z = omega D^-1 rv  (accumulate = false);  z += omega D^-1 (rv - t)  (accumulate = true); voxel rows
 __global__ void k_bj_apply(Dims D, const float* __restrict__ dinv, const float* __restrict__ rv,
                            const float* __restrict__ t, float omega, bool accumulate, float2* __restrict__ z) {
+    pdl_entry();
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t N = D.N;
     if (i >= N) return;
@@ -800,6 +804,7 @@ __device__ inline void coarse_solve_block(int n, const double* __restrict__ Ainv
 constexpr int CS_ROWS = 16;
 __global__ void __launch_bounds__(256) k_coarse_solve(int n, const double* __restrict__ Ainv,
                                                       const float4* __restrict__ b, DF4* __restrict__ x) {
+    pdl_entry();
     __shared__ double sb[COARSE_MAX];
     __shared__ double sx[CS_ROWS];
     const float* bf = reinterpret_cast<const float*>(b);
@@ -1007,6 +1012,7 @@ template <bool B16, bool SWEEP>
 __global__ void __launch_bounds__(256)
 k_fine_stencil(Dims D, const void* __restrict__ fst, const float* __restrict__ dinv, const float* __restrict__ rv,
                const float2* __restrict__ zin, float omega, float2* __restrict__ zout, float* __restrict__ tout) {
+    pdl_entry();
     const int z = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     const int t = blockIdx.z;
@@ -1189,6 +1195,7 @@ __device__ inline void smooth_cell(const Level& L, const DF4* x_in, const DF4* e
 template <bool B16>
 __global__ void k_lvl_smooth(Level L, const DF4* __restrict__ x_in, const DF4* __restrict__ ec, int ccny,
                              int ccnz, float omega, DF4* __restrict__ x_out, int pf) {
+    pdl_entry();
     if (B16 && pf > 0 && threadIdx.x == 0) lvl_prefetch(L, (int64_t)blockIdx.x + pf, 0, 32, x_in);
     int64_t cell = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (cell >= L.cells) return;
@@ -1300,6 +1307,7 @@ __device__ inline void smooth2_cell(const Level& L, float omega, DF4* x_out, int
 
 template <bool B16>
 __global__ void k_lvl_smooth2(Level L, float omega, DF4* __restrict__ x_out, int pf) {
+    pdl_entry();
     if (B16 && pf > 0 && threadIdx.x == 0) lvl_prefetch(L, (int64_t)blockIdx.x + pf, 0, 32, nullptr);
     int64_t cell = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (cell >= L.cells) return;
@@ -1314,6 +1322,7 @@ __global__ void k_lvl_smooth2(Level L, float omega, DF4* __restrict__ x_out, int
 __global__ void __launch_bounds__(256, 5) k_lvl_smooth_o5(Level L, const DF4* __restrict__ x_in,
                                                            const DF4* __restrict__ ec, int ccny, int ccnz,
                                                            float omega, DF4* __restrict__ x_out) {
+    pdl_entry();
     int64_t cell = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (cell >= L.cells) return;
     smooth_cell<true>(L, x_in, ec, ccny, ccnz, omega, x_out, cell);
@@ -1321,6 +1330,7 @@ __global__ void __launch_bounds__(256, 5) k_lvl_smooth_o5(Level L, const DF4* __
 
 template <bool B16>
 __global__ void k_lvl_matvec(Level L, const DF4* __restrict__ x, float4* __restrict__ y_out, int pf) {
+    pdl_entry();
     if (B16 && pf > 0 && threadIdx.x == 0) lvl_prefetch(L, (int64_t)blockIdx.x + pf, 0, 28, x);
     int64_t cell = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (cell >= L.cells) return;
@@ -1359,6 +1369,7 @@ __device__ inline void restrict_thread(const Level& L, const DF4* x, const Level
 
 template <bool B16>
 __global__ void k_lvl_restrict(Level L, const DF4* __restrict__ x, Level C) {
+    pdl_entry();
     restrict_thread<B16>(L, x, C, (int64_t)blockIdx.x * blockDim.x + threadIdx.x);
 }
 
@@ -1491,6 +1502,7 @@ __global__ void __launch_bounds__(TAIL_THREADS, 1) k_vtail(TailArgs a) {
 // ----------------------------------------------------- fine <-> level 1
 __global__ void k_restrict_fine(Dims D, const uint32_t* __restrict__ vc, const float* __restrict__ r,
                                 const float* __restrict__ t, Level C) {
+    pdl_entry();
     int64_t cell = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (cell >= C.cells) return;
     int ct, cy, cz;
@@ -1516,6 +1528,7 @@ __global__ void k_restrict_fine(Dims D, const uint32_t* __restrict__ vc, const f
 
 __global__ void k_prolong_fine(Dims D, const uint32_t* __restrict__ vc, Level C, const DF4* __restrict__ e1,
                                float2* __restrict__ z) {
+    pdl_entry();
     int zz = blockIdx.x * blockDim.x + threadIdx.x;
     int y = blockIdx.y * blockDim.y + threadIdx.y;
     int t = blockIdx.z;
@@ -1536,6 +1549,7 @@ __global__ void k_prolong_fine(Dims D, const uint32_t* __restrict__ vc, Level C,
 __global__ void __launch_bounds__(RED_THREADS)
 k_kdot(const float* __restrict__ V, int64_t stride, int cnt, const float* __restrict__ w, int64_t n,
        double* partials) {
+    pdl_entry();
     float acc32[8];
 #pragma unroll
     for (int j = 0; j < 8; ++j) acc32[j] = 0.f;
@@ -1551,6 +1565,7 @@ k_kdot(const float* __restrict__ V, int64_t stride, int cnt, const float* __rest
 // w += sign * sum_j h[j] V_j (h on the device; converted once per block)
 __global__ void k_kupdate(const float* __restrict__ V, int64_t stride, int cnt, const double* __restrict__ h,
                           float sign, float* __restrict__ w, int64_t n) {
+    pdl_entry();
     __shared__ float hs[KCYC_MAX + 1];
     if (threadIdx.x < cnt) hs[threadIdx.x] = (float)h[threadIdx.x];
     __syncthreads();
@@ -1570,6 +1585,7 @@ template <bool NORM>
 __global__ void __launch_bounds__(RED_THREADS)
 k_kupd_dot(const float* __restrict__ V, int64_t stride, int cnt, const double* __restrict__ h,
            float* __restrict__ w, int64_t n, double* partials) {
+    pdl_entry();
     constexpr int K = NORM ? 1 : 8;
     __shared__ float hs[8];
     if (threadIdx.x < cnt) hs[threadIdx.x] = (float)h[threadIdx.x];
@@ -1602,6 +1618,7 @@ k_kupd_dot(const float* __restrict__ V, int64_t stride, int cnt, const double* _
 // out = a / sqrt(max(d2, tiny)) (the scale computed once per block)
 __global__ void k_knormalize(const float* __restrict__ a, const double* __restrict__ d2, float* __restrict__ out,
                              int64_t n) {
+    pdl_entry();
     __shared__ float inv;
     if (threadIdx.x == 0) inv = (float)(1.0 / sqrt(fmax(*d2, 1e-300)));
     __syncthreads();
@@ -1613,6 +1630,7 @@ __global__ void k_knormalize(const float* __restrict__ a, const double* __restri
 // H layout: col-major (KCYC_MAX+1) x KCYC_MAX at H[j*(KCYC_MAX+1) + i]
 // After CGS2 of column j: h = h1 + h2, H[j+1, j] = ||w||.
 __global__ void k_kcol(double* H, int j, const double* h1, const double* h2, const double* wn2) {
+    pdl_entry();
     int i = threadIdx.x;
     if (i <= j) H[j * (KCYC_MAX + 1) + i] = h1[i] + h2[i];
     if (i == 0) H[j * (KCYC_MAX + 1) + j + 1] = sqrt(fmax(*wn2, 0.0));
@@ -1621,6 +1639,7 @@ __global__ void k_kcol(double* H, int j, const double* h1, const double* h2, con
 // least squares min || beta e1 - H y || by Givens rotations (one thread);
 // y also written as float-float pairs for the combination kernel
 __global__ void k_klsq(const double* H, const double* b2, int k, double* y, float2* ydf) {
+    pdl_entry();
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     double R[KCYC_MAX + 1][KCYC_MAX];
     double g[KCYC_MAX + 1];
@@ -1652,6 +1671,7 @@ __global__ void k_klsq(const double* H, const double* b2, int k, double* y, floa
 // x = sum_j y_j Z_j in float-float arithmetic
 __global__ void k_kcombine(const DF4* __restrict__ Z, int64_t cells, int k, const float2* __restrict__ ydf,
                            DF4* __restrict__ x) {
+    pdl_entry();
     int64_t cell = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (cell >= cells) return;
     float2 a0 = make_float2(0.f, 0.f), a1 = a0, a2 = a0, a3 = a0;
@@ -1747,8 +1767,8 @@ int precond_create(mb_cell* c) {
     p->kH = (double*)cell_alloc(c, 8 * (size_t)((KCYC_MAX + 1) * KCYC_MAX + 128));
     p->kred = (double*)cell_alloc(c, 8 * (size_t)RED_BLOCKS * 8);
     if (!p->cdense || !p->cinv || !p->cstat || !p->kV || !p->kZ || !p->kw || !p->kH || !p->kred) return MB_ENOMEM;
-    // persistent coarse tail: from the first level >= 2 that one block of
-    // TAIL_THREADS threads per SM covers; its grid is one block per
+    // persistent coarse tail: from the first level >= max(2, mg_tail) that
+    // one block of TAIL_THREADS threads per SM covers; its grid is one block per
     // TAIL_THREADS cells of that level (all co-resident), so a small cell's
     // tail is a single block and does not wait for the whole GPU
     p->tbar = (unsigned*)cell_alloc(c, 16);
@@ -1762,7 +1782,7 @@ int precond_create(mb_cell* c) {
             return cuda_fail(cudaGetLastError(), "coarse tail occupancy");
         if (coop && occ >= 1) {
             const int64_t cap = (int64_t)p->nsm * TAIL_THREADS;
-            for (int l = 2; l < p->nlev; ++l)
+            for (int l = c->opt.mg_tail > 2 ? c->opt.mg_tail : 2; l < p->nlev; ++l)
                 if (p->lv[l].cells <= cap) {
                     p->tail_l0 = l;
                     p->tail_blocks = (int)((p->lv[l].cells + TAIL_THREADS - 1) / TAIL_THREADS);
@@ -1819,6 +1839,28 @@ int precond_setup(mb_cell* c, const float* u32, const uint8_t* gate, double dt) 
     return MB_OK;
 }
 
+// launch of a kernel of the application: plain, or (mg_pdl) with programmatic
+// stream serialization; every kernel launched here starts with pdl_entry()
+template <typename... KArgs, typename... Args>
+static void klaunch(const mb_cell* c, void (*k)(KArgs...), dim3 g, dim3 b, size_t smem, cudaStream_t s,
+                    Args... args) {
+    if (!c->opt.mg_pdl) {
+        k<<<g, b, smem, s>>>(args...);
+        return;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = g;
+    cfg.blockDim = b;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, k, args...);
+}
+
 // launches of the level kernels with the operator storage chosen at set-up
 static void lvl_smooth(mb_cell* c, Level& L, const DF4* xin, const DF4* ec, int ccny, int ccnz, DF4* xout,
                        bool timed = false) {
@@ -1832,12 +1874,12 @@ static void lvl_smooth(mb_cell* c, Level& L, const DF4* xin, const DF4* ec, int 
     if (p->b16 && c->opt.mg_stream == 2 && xin && ntiles >= p->nsm && !g_staged_broken.load())
         k_lvl_smooth_staged<<<p->nsm, SWT, SW_SMEM, s>>>(L, xin, ec, ccny, ccnz, OMEGA_COARSE, xout, p->err);
     else if (p->b16 && c->opt.mg_stream == 3 && &L == &p->lv[1])
-        k_lvl_smooth_o5<<<g, 256, 0, s>>>(L, xin, ec, ccny, ccnz, OMEGA_COARSE, xout);
+        klaunch(c, k_lvl_smooth_o5, g, 256, 0, s, L, xin, ec, ccny, ccnz, OMEGA_COARSE, xout);
     else if (p->b16)
-        k_lvl_smooth<true><<<g, 256, 0, s>>>(L, xin, ec, ccny, ccnz, OMEGA_COARSE, xout,
-                                             c->opt.mg_stream == 1 ? p->pf[0] : 0);
+        klaunch(c, k_lvl_smooth<true>, g, 256, 0, s, L, xin, ec, ccny, ccnz, OMEGA_COARSE, xout,
+                c->opt.mg_stream == 1 ? p->pf[0] : 0);
     else
-        k_lvl_smooth<false><<<g, 256, 0, s>>>(L, xin, ec, ccny, ccnz, OMEGA_COARSE, xout, 0);
+        klaunch(c, k_lvl_smooth<false>, g, 256, 0, s, L, xin, ec, ccny, ccnz, OMEGA_COARSE, xout, 0);
     ::mb::count_launch(c);
     if (timed) prof_end(c, s, PROF_LSMOOTH, ev);
 }
@@ -1845,28 +1887,28 @@ static void lvl_smooth2(mb_cell* c, Level& L, DF4* xout) {
     cudaStream_t s = c->stream;
     unsigned g = nblk(L.cells);
     if (c->pc->b16)
-        k_lvl_smooth2<true><<<g, 256, 0, s>>>(L, OMEGA_COARSE, xout, c->opt.mg_stream == 1 ? c->pc->pf[1] : 0);
+        klaunch(c, k_lvl_smooth2<true>, g, 256, 0, s, L, OMEGA_COARSE, xout, c->opt.mg_stream == 1 ? c->pc->pf[1] : 0);
     else
-        k_lvl_smooth2<false><<<g, 256, 0, s>>>(L, OMEGA_COARSE, xout, 0);
+        klaunch(c, k_lvl_smooth2<false>, g, 256, 0, s, L, OMEGA_COARSE, xout, 0);
     ::mb::count_launch(c);
 }
 static void lvl_restrict(mb_cell* c, Level& L, const DF4* x, Level& C) {
     cudaStream_t s = c->stream;
     unsigned g = nblk(8 * C.cells);
     if (c->pc->b16)
-        k_lvl_restrict<true><<<g, 256, 0, s>>>(L, x, C);
+        klaunch(c, k_lvl_restrict<true>, g, 256, 0, s, L, x, C);
     else
-        k_lvl_restrict<false><<<g, 256, 0, s>>>(L, x, C);
+        klaunch(c, k_lvl_restrict<false>, g, 256, 0, s, L, x, C);
     ::mb::count_launch(c);
 }
 static void lvl_matvec(mb_cell* c, Level& L, const DF4* x, float* y) {
     cudaStream_t s = c->stream;
     unsigned g = nblk(L.cells);
     if (c->pc->b16)
-        k_lvl_matvec<true><<<g, 256, 0, s>>>(L, x, reinterpret_cast<float4*>(y),
+        klaunch(c, k_lvl_matvec<true>, g, 256, 0, s, L, x, reinterpret_cast<float4*>(y),
                                              c->opt.mg_stream == 1 ? c->pc->pf[2] : 0);
     else
-        k_lvl_matvec<false><<<g, 256, 0, s>>>(L, x, reinterpret_cast<float4*>(y), 0);
+        klaunch(c, k_lvl_matvec<false>, g, 256, 0, s, L, x, reinterpret_cast<float4*>(y), 0);
     ::mb::count_launch(c);
 }
 
@@ -1917,7 +1959,7 @@ static void vcycle(mb_cell* c, int l) {
     }
     Level& L = p->lv[l];
     if (l == p->nlev) {
-        k_coarse_solve<<<(unsigned)((p->ncoarse + CS_ROWS - 1) / CS_ROWS), 256, 0, s>>>(p->ncoarse, p->cinv, L.b, L.x),
+        klaunch(c, k_coarse_solve, (unsigned)((p->ncoarse + CS_ROWS - 1) / CS_ROWS), 256, 0, s, p->ncoarse, p->cinv, L.b, L.x),
             ::mb::count_launch(c);
         return;
     }
@@ -1949,8 +1991,8 @@ static void kdots(mb_cell* c, const float* V, int64_t stride, int cnt, const flo
     cudaStream_t s = c->stream;
     for (int j0 = 0; j0 < cnt; j0 += 8) {
         int k = cnt - j0 < 8 ? cnt - j0 : 8;
-        k_kdot<<<RED_BLOCKS, RED_THREADS, 0, s>>>(V + j0 * stride, stride, k, w, n, p->kred), ::mb::count_launch(c);
-        k_reduce_final<false><<<k, RED_THREADS, 0, s>>>(p->kred, k, out + j0), ::mb::count_launch(c);
+        klaunch(c, k_kdot, RED_BLOCKS, RED_THREADS, 0, s, V + j0 * stride, stride, k, w, n, p->kred), ::mb::count_launch(c);
+        klaunch(c, k_reduce_final<false>, k, RED_THREADS, 0, s, p->kred, k, out + j0), ::mb::count_launch(c);
     }
 }
 
@@ -1978,7 +2020,7 @@ static void kcycle_l1(mb_cell* c) {
     float2* ydf = reinterpret_cast<float2*>(sc + 64);
     const float* b = reinterpret_cast<const float*>(L.b);
     kdots(c, b, 0, 1, b, m4, b2);
-    k_knormalize<<<g, 256, 0, s>>>(b, b2, p->kV, m4), ::mb::count_launch(c);
+    klaunch(c, k_knormalize, g, 256, 0, s, b, b2, p->kV, m4), ::mb::count_launch(c);
     float4* bsave = L.b;   // the V-cycle reads lv[1].b: point it at the Krylov vector
     // with an even number of iterate swaps in the V-cycle the result lands in
     // the buffer level 1's x pointed at when it began: point it at Z_j directly
@@ -2001,29 +2043,29 @@ static void kcycle_l1(mb_cell* c) {
         if (!c->opt.mg_kcycle_reorth && j + 1 <= 8) {
             // one classical Gram-Schmidt pass, fused with the norm that follows it
             cudaMemsetAsync(h2, 0, 8 * (size_t)(j + 1), s);
-            k_kupd_dot<true><<<RED_BLOCKS, RED_THREADS, 0, s>>>(p->kV, m4, j + 1, h1, p->kw, m4, p->kred),
+            klaunch(c, k_kupd_dot<true>, RED_BLOCKS, RED_THREADS, 0, s, p->kV, m4, j + 1, h1, p->kw, m4, p->kred),
                 ::mb::count_launch(c);
-            k_reduce_final<false><<<1, RED_THREADS, 0, s>>>(p->kred, 1, wn2), ::mb::count_launch(c);
+            klaunch(c, k_reduce_final<false>, 1, RED_THREADS, 0, s, p->kred, 1, wn2), ::mb::count_launch(c);
         } else if (j + 1 <= 8) {
             // CGS2 with each update fused into the products that follow it
-            k_kupd_dot<false><<<RED_BLOCKS, RED_THREADS, 0, s>>>(p->kV, m4, j + 1, h1, p->kw, m4, p->kred),
+            klaunch(c, k_kupd_dot<false>, RED_BLOCKS, RED_THREADS, 0, s, p->kV, m4, j + 1, h1, p->kw, m4, p->kred),
                 ::mb::count_launch(c);
-            k_reduce_final<false><<<j + 1, RED_THREADS, 0, s>>>(p->kred, j + 1, h2), ::mb::count_launch(c);
-            k_kupd_dot<true><<<RED_BLOCKS, RED_THREADS, 0, s>>>(p->kV, m4, j + 1, h2, p->kw, m4, p->kred),
+            klaunch(c, k_reduce_final<false>, j + 1, RED_THREADS, 0, s, p->kred, j + 1, h2), ::mb::count_launch(c);
+            klaunch(c, k_kupd_dot<true>, RED_BLOCKS, RED_THREADS, 0, s, p->kV, m4, j + 1, h2, p->kw, m4, p->kred),
                 ::mb::count_launch(c);
-            k_reduce_final<false><<<1, RED_THREADS, 0, s>>>(p->kred, 1, wn2), ::mb::count_launch(c);
+            klaunch(c, k_reduce_final<false>, 1, RED_THREADS, 0, s, p->kred, 1, wn2), ::mb::count_launch(c);
         } else {
-            k_kupdate<<<g, 256, 0, s>>>(p->kV, m4, j + 1, h1, -1.f, p->kw, m4), ::mb::count_launch(c);
+            klaunch(c, k_kupdate, g, 256, 0, s, p->kV, m4, j + 1, h1, -1.f, p->kw, m4), ::mb::count_launch(c);
             kdots(c, p->kV, m4, j + 1, p->kw, m4, h2);
-            k_kupdate<<<g, 256, 0, s>>>(p->kV, m4, j + 1, h2, -1.f, p->kw, m4), ::mb::count_launch(c);
+            klaunch(c, k_kupdate, g, 256, 0, s, p->kV, m4, j + 1, h2, -1.f, p->kw, m4), ::mb::count_launch(c);
             kdots(c, p->kw, 0, 1, p->kw, m4, wn2);
         }
-        k_kcol<<<1, 32, 0, s>>>(H, j, h1, h2, wn2), ::mb::count_launch(c);
-        k_knormalize<<<g, 256, 0, s>>>(p->kw, wn2, p->kV + (j + 1) * m4, m4), ::mb::count_launch(c);
+        klaunch(c, k_kcol, 1, 32, 0, s, H, j, h1, h2, wn2), ::mb::count_launch(c);
+        klaunch(c, k_knormalize, g, 256, 0, s, p->kw, wn2, p->kV + (j + 1) * m4, m4), ::mb::count_launch(c);
     }
     L.b = bsave;
-    k_klsq<<<1, 1, 0, s>>>(H, b2, K, y, ydf), ::mb::count_launch(c);
-    k_kcombine<<<nblk(L.cells), 256, 0, s>>>(p->kZ, L.cells, K, ydf, L.x), ::mb::count_launch(c);
+    klaunch(c, k_klsq, 1, 1, 0, s, H, b2, K, y, ydf), ::mb::count_launch(c);
+    klaunch(c, k_kcombine, nblk(L.cells), 256, 0, s, p->kZ, L.cells, K, ydf, L.x), ::mb::count_launch(c);
 }
 
 // ---- MB_DEBUG >= 2: 2-norms of the intermediate vectors of one application
@@ -2063,9 +2105,9 @@ static void fine_sweep(mb_cell* c, const float2* zin, float2* zout) {
     cudaEvent_t ev;
     prof_begin(c, s, &ev);
     if (p->b16)
-        k_fine_stencil<true, true><<<vg, PB, 0, s>>>(D, p->fst, p->dinv, p->rv, zin, OMEGA_FINE, zout, nullptr);
+        klaunch(c, k_fine_stencil<true, true>, vg, PB, 0, s, D, p->fst, p->dinv, p->rv, zin, OMEGA_FINE, zout, nullptr);
     else
-        k_fine_stencil<false, true><<<vg, PB, 0, s>>>(D, p->fst, p->dinv, p->rv, zin, OMEGA_FINE, zout, nullptr);
+        klaunch(c, k_fine_stencil<false, true>, vg, PB, 0, s, D, p->fst, p->dinv, p->rv, zin, OMEGA_FINE, zout, nullptr);
     ::mb::count_launch(c);
     prof_end(c, s, PROF_SMOOTH, ev);
 }
@@ -2075,9 +2117,9 @@ static void fine_product(mb_cell* c, const float2* zin, float* tout) {
     cudaStream_t s = c->stream;
     const dim3 vg = pgrid(D.nt, D.ny, D.nz);
     if (p->b16)
-        k_fine_stencil<true, false><<<vg, PB, 0, s>>>(D, p->fst, nullptr, nullptr, zin, 0.f, nullptr, tout);
+        klaunch(c, k_fine_stencil<true, false>, vg, PB, 0, s, D, p->fst, nullptr, nullptr, zin, 0.f, nullptr, tout);
     else
-        k_fine_stencil<false, false><<<vg, PB, 0, s>>>(D, p->fst, nullptr, nullptr, zin, 0.f, nullptr, tout);
+        klaunch(c, k_fine_stencil<false, false>, vg, PB, 0, s, D, p->fst, nullptr, nullptr, zin, 0.f, nullptr, tout);
     ::mb::count_launch(c);
 }
 
@@ -2130,10 +2172,10 @@ static int apply_body(mb_cell* c, const float* r, float2* z) {
     // condensed right-hand side, then nu_fine damped block-Jacobi sweeps from
     // zero; the sweeps alternate between zs and z, and the first one (from
     // zero) writes where the last one must end up in z
-    k_condense_rhs<<<vg, PB, 0, s>>>(D, c->vcode, p->fc, r, c->rowdiag, p->rv), ::mb::count_launch(c);
+    klaunch(c, k_condense_rhs, vg, PB, 0, s, D, c->vcode, p->fc, r, c->rowdiag, p->rv), ::mb::count_launch(c);
     float2* za = (p->nu_fine - 1) % 2 == 0 ? z : p->zs;
     float2* zb = za == z ? p->zs : z;
-    k_bj_apply<<<nblk(D.N), 256, 0, s>>>(D, p->dinv, p->rv, nullptr, OMEGA_FINE, false, za), ::mb::count_launch(c);
+    klaunch(c, k_bj_apply, nblk(D.N), 256, 0, s, D, p->dinv, p->rv, nullptr, OMEGA_FINE, false, za), ::mb::count_launch(c);
     for (int k = 1; k < p->nu_fine; ++k) {
         fine_sweep(c, za, zb);
         std::swap(za, zb);
@@ -2141,7 +2183,7 @@ static int apply_body(mb_cell* c, const float* r, float2* z) {
     // t = S z for the restricted residual
     fine_product(c, z, p->t);
     Level& L1 = p->lv[1];
-    k_restrict_fine<<<nblk(L1.cells), 256, 0, s>>>(D, c->vcode, p->rv, p->t, L1), ::mb::count_launch(c);
+    klaunch(c, k_restrict_fine, nblk(L1.cells), 256, 0, s, D, c->vcode, p->rv, p->t, L1), ::mb::count_launch(c);
     if (debug_level() >= 2)
         fprintf(stderr, "[mb-pc] |rv| %.3e |z0| %.3e |Sz0| %.3e |b1| %.3e\n", dbg_norm(c, p->rv, 2 * D.N),
                 dbg_norm(c, z, 2 * D.N), dbg_norm(c, p->t, 2 * D.N),
@@ -2152,7 +2194,7 @@ static int apply_body(mb_cell* c, const float* r, float2* z) {
         fprintf(stderr, "[mb-pc] |x1| %.3e |A1 x1| %.3e\n",
                 dbg_norm(c, reinterpret_cast<const float2*>(L1.x), 4 * L1.cells), dbg_norm(c, p->kw, 4 * L1.cells));
     }
-    k_prolong_fine<<<vg, PB, 0, s>>>(D, c->vcode, L1, L1.x, z), ::mb::count_launch(c);
+    klaunch(c, k_prolong_fine, vg, PB, 0, s, D, c->vcode, L1, L1.x, z), ::mb::count_launch(c);
     // nu_fine post-smoothing sweeps (they remove the jumps of the piecewise-constant prolongation)
     za = z;
     zb = p->zs;
@@ -2162,7 +2204,7 @@ static int apply_body(mb_cell* c, const float* r, float2* z) {
     }
     if (za != z) MB_CUDA(cudaMemcpyAsync(z, za, 16 * (size_t)D.N, cudaMemcpyDeviceToDevice, s));
     // back-substitution of the plating rows
-    if (D.F) k_face_solve<<<fg, 256, 0, s>>>(D, c->pf_g, c->pf_e, p->fc, r, c->rowdiag, z), ::mb::count_launch(c);
+    if (D.F) klaunch(c, k_face_solve, fg, 256, 0, s, D, c->pf_g, c->pf_e, p->fc, r, c->rowdiag, z), ::mb::count_launch(c);
     if (debug_level() >= 2) fprintf(stderr, "[mb-pc] |z| %.3e\n", dbg_norm(c, z, c->n));
     MB_CUDA_LAUNCH("precond_apply");
     return MB_OK;
@@ -2196,6 +2238,7 @@ static bool capture_graph(mb_cell* c, const float* r, float2* z, PcGraph& G) {
     G.nu = p->nu_fine;
     G.reorth = c->opt.mg_kcycle_reorth;
     G.tail = c->opt.mg_tail;
+    G.pdl = c->opt.mg_pdl;
     if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
         cudaGetLastError();
         return false;
@@ -2235,7 +2278,7 @@ int precond_apply(mb_cell* c, const float* u32, const uint8_t* gate, double dt, 
     for (size_t i = 0; i < p->graphs.size(); ++i) {
         const PcGraph& G = p->graphs[i];
         if (G.r == r && G.z == z && G.kcyc == p->kcyc && G.nu == p->nu_fine && G.reorth == c->opt.mg_kcycle_reorth &&
-            G.tail == c->opt.mg_tail) {
+            G.tail == c->opt.mg_tail && G.pdl == c->opt.mg_pdl) {
             idx = (int)i;
             break;
         }

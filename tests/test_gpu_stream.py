@@ -53,16 +53,16 @@ def test_stream_modes_bit_identical(params):
 
 
 def test_coarse_tail_bit_identical(params):
-    """The persistent coarse tail (levels 2 down to the coarsest solve in one
-    cooperative launch, grid barriers between the phases) runs the per-level
-    kernels' per-cell code in the same order: preconditioner applications and
-    implicit steps are bit-identical to per-level launches."""
+    """The persistent coarse tail (levels 2, or 3, down to the coarsest solve in
+    one cooperative launch, grid barriers between the phases) runs the
+    per-level kernels' per-cell code in the same order: preconditioner
+    applications and implicit steps are bit-identical to per-level launches."""
     B, torch = _gpu()
     lab = syn.full_cell(64, 64, 53, 22, 53, 0.35, 0.35, ("uniform", 2, 4), (31, 32))
     cells = {t: B.Cell(lab, 1e-6, params, B.default_opts(precision=1, newton_tol=1e-10, krylov_rtol=1e-4,
-                                                         mg_tail=t)) for t in (0, 1)}
+                                                         mg_tail=t)) for t in (0, 1, 3)}
     a = cells[1]
-    assert len(a.debug_levels()) >= 4
+    assert len(a.debug_levels()) >= 5
     rng = np.random.default_rng(9)
     N = a.N
     u = a.state()
@@ -72,12 +72,14 @@ def test_coarse_tail_bit_identical(params):
     r = rng.standard_normal(a.n)
     z = {t: cells[t].debug_precond(u, gate, 1.0, r) for t in cells}
     assert np.all(np.isfinite(z[0]))
-    assert np.array_equal(z[1], z[0])
+    assert np.array_equal(z[1], z[0]) and np.array_equal(z[3], z[0])
     I = -2.0 * a.i_1c
     for _ in range(2):
         info = {t: cells[t].step(1.0, I) for t in cells}
-        assert info[1]["krylov_its"] == info[0]["krylov_its"] and info[1]["V_cell"] == info[0]["V_cell"]
+        for t in (1, 3):
+            assert info[t]["krylov_its"] == info[0]["krylov_its"] and info[t]["V_cell"] == info[0]["V_cell"]
     assert np.array_equal(cells[1].state(), cells[0].state())
+    assert np.array_equal(cells[3].state(), cells[0].state())
     for cell in cells.values():
         cell.close()
 
@@ -102,5 +104,34 @@ def test_lagged_preconditioner_same_solution(params):
     for sl in (slice(0, N), slice(N, 2 * N), slice(2 * N, None)):
         if np.max(np.abs(u0[sl])) > 0:
             assert np.max(np.abs(u1[sl] - u0[sl])) <= 1e-8 * np.max(np.abs(u0[sl]))
+    for cell in cells.values():
+        cell.close()
+
+
+def test_programmatic_dependent_launch_bit_identical(params):
+    """With programmatic dependent launch (mg_pdl = 1) every kernel of an
+    application waits for its predecessor before its first memory access, so
+    preconditioner applications and implicit steps are bit-identical to plain
+    launches (graph-captured and direct)."""
+    B, torch = _gpu()
+    lab = syn.full_cell(64, 64, 53, 22, 53, 0.35, 0.35, ("uniform", 2, 4), (31, 32))
+    cells = {q: B.Cell(lab, 1e-6, params, B.default_opts(precision=1, newton_tol=1e-10, krylov_rtol=1e-4,
+                                                         mg_pdl=q)) for q in (0, 1)}
+    a = cells[1]
+    rng = np.random.default_rng(13)
+    N = a.N
+    u = a.state()
+    u[:N] *= 1.0 + 0.01 * rng.standard_normal(N)
+    u[N:2 * N] += 0.002 * rng.standard_normal(N)
+    gate = np.zeros(a.F, np.uint8)
+    r = rng.standard_normal(a.n)
+    z = {q: cells[q].debug_precond(u, gate, 1.0, r) for q in cells}
+    assert np.all(np.isfinite(z[0]))
+    assert np.array_equal(z[1], z[0])
+    I = -2.0 * a.i_1c
+    for _ in range(2):
+        info = {q: cells[q].step(1.0, I) for q in cells}
+        assert info[1]["krylov_its"] == info[0]["krylov_its"] and info[1]["V_cell"] == info[0]["V_cell"]
+    assert np.array_equal(cells[1].state(), cells[0].state())
     for cell in cells.values():
         cell.close()
