@@ -586,7 +586,7 @@ def main():
                     help="reduced steps driven from the host instead of one CUDA graph per step (same results; "
                          "every kernel a separate launch, for a profiler's launch list)")
     ap.add_argument("--rom-steps", type=int, default=60)
-    ap.add_argument("--rom-paper-steps", type=int, default=3,
+    ap.add_argument("--rom-paper-steps", type=int, default=10,
                     help="timed steps of the paper-size reduced model (a sample of its 600-step protocol)")
     ap.add_argument("--serve-requests", type=int, default=800)
     ap.add_argument("--experiment", action="store_true",
