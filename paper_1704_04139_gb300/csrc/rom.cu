@@ -980,24 +980,34 @@ k_rom_lu(int Nr, T* __restrict__ J, const double* __restrict__ r, const int* __r
         if (tid == 0) x[k] = inv;
         T best = T(-1);
         int bi = Nr;
-        for (int i = k + 1 + wid; i < Nr; i += nw) {
-            T* const ri = row(i);
+        // row i minus l times the pivot row; the callers below pass pointers whose
+        // memory (shared or global) the compiler sees, so that shared-memory rows
+        // are accessed with shared-memory instructions rather than generic ones
+        auto elim = [&](T* ri, const T* rkp, int i) {
             const T l = ri[k] * inv;
             int j = k + 1 + lane;
             if (j < Nr) {   // column k+1 (lane 0) feeds the next pivot search
-                const T v = ri[j] - l * rk[j];
+                const T v = ri[j] - l * rkp[j];
                 ri[j] = v;
                 if (lane == 0) lu_pick(best, bi, fabs(v), i);
                 j += 32;
             }
 #pragma unroll 4
-            for (; j < Nr; j += 32) ri[j] -= l * rk[j];
+            for (; j < Nr; j += 32) ri[j] -= l * rkp[j];
             if (KEEP) {
                 __syncwarp();   // every lane has read A[i][k] before lane 0 overwrites it
                 if (lane == 0) ri[k] = l;
             }
             if (lane == 0) rhs[i] -= l * rkk;
-        }
+        };
+        auto sweep = [&](const T* rkp) {
+            for (int i = k + 1 + wid; i < Nr; i += nw) {
+                if (SMEM || i < R) elim(rows + (size_t)i * Nr, rkp, i);
+                else elim(Jb + (size_t)i * Nr, rkp, i);
+            }
+        };
+        if (SMEM || k < R) sweep(rows + (size_t)k * Nr);
+        else sweep(Jb + (size_t)k * Nr);
         if (lane == 0) {   // column k+1 lives in lane 0 of every warp
             wbest[wid] = best;
             widx[wid] = bi;
