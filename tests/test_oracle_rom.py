@@ -207,3 +207,56 @@ def test_dt_halving_retakes_failed_steps(trained, monkeypatch):
     assert out["newton_its"] == direct["newton_its"]
     with pytest.raises(RuntimeError):
         R.solve(rom, mu, 1.0, 1.0, 1.0, 1, max_halvings=1)
+
+
+def _jacobian_fd_error(rom, cell, traj, mu):
+    """Largest relative difference between the reduced Jacobian's products and
+    central differences of the reduced residual (step 1e-5 in each mode's own
+    scale), over two (s_i0, k_pl) pairs and three directions."""
+    w = R.weights(cell)
+    a_old = rom.U.T @ (w * traj[1])
+    a = rom.U.T @ (w * traj[2])
+    u_old = rom.U @ a_old
+    gate = cell.gate_at(u_old, u_old[2 * cell.N:])
+    assert np.count_nonzero(gate) > 0            # the plating terms take part
+    rng = np.random.default_rng(7)
+    h, dt = 1e-5, 0.1
+    worst = 0.0
+    for s_i0, k_pl in ((1.0, 1.0), (1.7, 0.3)):
+        J = R.reduced_jacobian(rom, a, dt, s_i0, k_pl, gate)
+        for _ in range(3):
+            v = rng.standard_normal(len(a)) * np.maximum(np.abs(a), 1e-6 * np.max(np.abs(a)))
+            rp = R.reduced_residual(rom, a + h * v, a_old, dt, mu, s_i0, k_pl, gate)
+            rm = R.reduced_residual(rom, a - h * v, a_old, dt, mu, s_i0, k_pl, gate)
+            jv = J @ v
+            worst = max(worst, float(np.max(np.abs((rp - rm) / (2 * h) - jv)) / np.max(np.abs(jv))))
+    return worst
+
+
+def _mutated(fn, old, new):
+    """fn recompiled from its source with one planted change (in its module's namespace)."""
+    import inspect
+    import textwrap
+    src = textwrap.dedent(inspect.getsource(fn))
+    assert old in src
+    ns = dict(fn.__globals__)
+    exec(compile(src.replace(old, new), "<planted>", "exec"), ns)
+    return ns[fn.__name__]
+
+
+def test_reduced_jacobian_is_the_residual_derivative(trained, monkeypatch):
+    """The reduced Newton matrix (Ms/dt + Alin + P_bv (s_i0 J_bv + J_ce + k_pl J_pl)
+    U + P_1c J_1c U, Eq. ap4:fully_reduced differentiated) against central
+    differences of the reduced residual: the differences converge as h^2 and
+    agree to ~1e-11 at h = 1e-5, 1e-9 is the bound.  Each plausible slip planted
+    in the oracle's Jacobian (the plating rate constant or the exchange-current
+    scale dropped, the storage term multiplied by dt, the interpolation rows of
+    the migration term left out) fails it."""
+    cell, mu, snaps, traj, rom = trained
+    assert _jacobian_fd_error(rom, cell, traj, mu) <= 1e-9
+    real = R.reduced_jacobian
+    for old, new in (('k_pl * J["pl"]', 'J["pl"]'), ('s_i0 * J["bv"]', 'J["bv"]'),
+                     ("rom.Ms / dt", "rom.Ms * dt"), ("+ rom.P1c_proj @ J1c", "")):
+        monkeypatch.setattr(R, "reduced_jacobian", _mutated(real, old, new))
+        assert _jacobian_fd_error(rom, cell, traj, mu) > 1e-6, (old, new)
+    monkeypatch.setattr(R, "reduced_jacobian", real)
