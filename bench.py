@@ -581,7 +581,7 @@ def main():
     ap.add_argument("--no-fp64-arm", action="store_true",
                     help="skip the FP64 run of the same steps (and the mixed-vs-FP64 errors)")
     ap.add_argument("--no-rom", action="store_true", help="skip the reduced-model and serving measurements")
-    ap.add_argument("--rom-instances", type=int, default=1024)
+    ap.add_argument("--rom-instances", type=int, default=4096)
     ap.add_argument("--rom-host-loop", action="store_true",
                     help="reduced steps driven from the host instead of one CUDA graph per step (same results; "
                          "every kernel a separate launch, for a profiler's launch list)")
