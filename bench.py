@@ -67,7 +67,7 @@ def fom_opts(B, prec, args):
                           mg_kcycle_reorth=0 if args.kcycle_cgs1 else 1, mg_kcycle=args.mg_kcycle,
                           mg_smooth=args.mg_smooth, mg_coarse_pre=args.mg_coarse[0], mg_coarse_post=args.mg_coarse[1],
                           pc_lag=0 if args.no_pc_lag else 1, pc_lag_drift=args.pc_lag_drift,
-                          mg_pdl=args.mg_pdl)
+                          mg_pdl=args.mg_pdl, newton_rate_test=0 if args.no_newton_rate_test else 1)
 
 
 def step_record(infos):
@@ -565,6 +565,8 @@ def main():
                     help="one Gram-Schmidt pass in the level-1 K-cycle instead of two (mg_kcycle_reorth = 0)")
     ap.add_argument("--no-pc-lag", action="store_true",
                     help="rebuild the preconditioner at every Newton iteration (pc_lag = 0)")
+    ap.add_argument("--no-newton-rate-test", action="store_true",
+                    help="stop Newton only on an update below the tolerance (newton_rate_test = 0)")
     ap.add_argument("--mg-pdl", type=int, default=0, choices=[0, 1],
                     help="programmatic dependent launch of the preconditioner's kernels (mg_pdl)")
     ap.add_argument("--pc-lag-drift", type=float, default=0.05,
@@ -758,7 +760,7 @@ def main():
                           "mg_kcycle_reorth": 0 if args.kcycle_cgs1 else 1, "mg_kcycle": args.mg_kcycle,
                           "mg_smooth": args.mg_smooth, "mg_coarse": list(args.mg_coarse),
                           "pc_lag": 0 if args.no_pc_lag else 1, "pc_lag_drift": args.pc_lag_drift,
-                          "mg_pdl": args.mg_pdl,
+                          "mg_pdl": args.mg_pdl, "newton_rate_test": 0 if args.no_newton_rate_test else 1,
                           "l2": "working set > 129 MB L2, no flush", "parallelism": "replicas" if ws > 1 else "1 GPU"},
                "clocks": clk, "e2e": e2e, "gpu_launches": int(launches), "roofline": roof,
                "cpu_baseline": cpu,

@@ -134,6 +134,13 @@ typedef struct {
                               programmatic dependent launch: each may be scheduled while its
                               predecessor drains and waits, before its first memory access, until
                               that predecessor has completed (same results); 0: plain launches */
+    int    newton_rate_test; /* 1 (default): a Newton solve also stops when the error left after the
+                              current update, estimated from two consecutive full steps as
+                              (rho / (1 - rho) + relres) |d_k| with rho = |d_k| / |d_k-1| < 0.5 and
+                              relres the linear solve's relative residual (the scaled max-norm of
+                              the convergence test), is below newton_tol: the iteration that would
+                              only confirm a quadratically converged state is skipped; 0: only an
+                              update below newton_tol stops it */
 } mb_solver_opts;
 
 typedef struct {

@@ -41,7 +41,8 @@ class SolverOpts(C.Structure):
                 ("mg_smooth", C.c_int), ("mg_kcycle", C.c_int), ("mg_coarse_pre", C.c_int),
                 ("mg_coarse_post", C.c_int), ("mg_bf16", C.c_int), ("mg_stream", C.c_int),
                 ("pass_start", C.c_int), ("mg_kcycle_reorth", C.c_int), ("krylov_forcing", C.c_int),
-                ("mg_tail", C.c_int), ("pc_lag", C.c_int), ("pc_lag_drift", C.c_double), ("mg_pdl", C.c_int)]
+                ("mg_tail", C.c_int), ("pc_lag", C.c_int), ("pc_lag_drift", C.c_double), ("mg_pdl", C.c_int),
+                ("newton_rate_test", C.c_int)]
 
 
 class StepInfo(C.Structure):

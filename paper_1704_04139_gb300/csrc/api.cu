@@ -121,6 +121,7 @@ void mb_opts_default(mb_solver_opts* o) {
     o->pc_lag = 1;
     o->pc_lag_drift = 0.05;
     o->mg_pdl = 0;
+    o->newton_rate_test = 1;
 }
 
 static int check_opts(const mb_solver_opts* o) {
@@ -131,7 +132,7 @@ static int check_opts(const mb_solver_opts* o) {
         !(o->krylov_rtol > 0) || o->mg_kcycle < 1 || o->mg_kcycle > 16 || o->mg_smooth < 1 || o->mg_smooth > 8 ||
         (o->mg_bf16 != 0 && o->mg_bf16 != 1) || o->mg_coarse_pre < 1 || o->mg_coarse_pre > 4 ||
         o->mg_coarse_post < 1 || o->mg_coarse_post > 4 || o->mg_stream < 0 || o->mg_stream > 3 ||
-        (o->pass_start != 0 && o->pass_start != 1) || o->mg_tail < 0 || o->mg_tail > 16 || (o->pc_lag != 0 && o->pc_lag != 1) || !(o->pc_lag_drift >= 0) || (o->mg_pdl != 0 && o->mg_pdl != 1) ||
+        (o->pass_start != 0 && o->pass_start != 1) || o->mg_tail < 0 || o->mg_tail > 16 || (o->pc_lag != 0 && o->pc_lag != 1) || !(o->pc_lag_drift >= 0) || (o->mg_pdl != 0 && o->mg_pdl != 1) || (o->newton_rate_test != 0 && o->newton_rate_test != 1) ||
         (o->krylov_forcing != 0 && o->krylov_forcing != 1) ||
         (o->mg_kcycle_reorth != 0 && o->mg_kcycle_reorth != 1))
         return MB_EINVAL;

@@ -415,6 +415,7 @@ static int newton(mb_cell* c, double dt, double I_app, bool from_old, int* its_o
     double rn_prev = 0.0, eta_prev = 0.0;
     int base_its = 0, last_its = 0;   // Krylov iterations after the last preconditioner rebuild, and of the last solve
     double drift = 0.0;               // sum of the damped updates' scaled sizes since that rebuild
+    double dn_prev = 0.0;             // scaled size of the previous update if it was a full step (else 0)
     for (int it = 1; it <= c->opt.newton_maxit; ++it) {
         int rc = launch_residual_split(c, c->u, c->u_old, c->gate, dt, I_app, c->r, s);
         if (rc) return rc;
@@ -489,8 +490,18 @@ static int newton(mb_cell* c, double dt, double I_app, bool from_old, int* its_o
             if (c->D.F) MB_CUDA(cudaMemcpyAsync(c->snap_g->back().data(), c->gate, c->D.F, cudaMemcpyDeviceToHost, s));
             MB_CUDA(cudaStreamSynchronize(s));
         }
-        // a small update only means convergence if the linear solve made progress
-        if (lam * dn <= c->opt.newton_tol && rr <= fmax(0.5, eta)) {
+        // converged: the update is below the tolerance or, with newton_rate_test,
+        // the error left after it is: estimated from the contraction of two full
+        // steps (rho = |d_k| / |d_k-1|, remaining error ~ rho / (1 - rho) |d_k|)
+        // plus the linear solve's own relative residual times |d_k|; a small
+        // update only means convergence if the linear solve made progress
+        bool small = lam * dn <= c->opt.newton_tol;
+        if (!small && c->opt.newton_rate_test && lam == 1.0 && dn_prev > 0.0) {
+            const double rho = dn / dn_prev;
+            small = rho < 0.5 && (rho / (1.0 - rho) + rr) * dn <= c->opt.newton_tol;
+        }
+        dn_prev = lam == 1.0 ? dn : 0.0;
+        if (small && rr <= fmax(0.5, eta)) {
             *its_out = it;
             *ok = true;
             return MB_OK;

@@ -36,7 +36,8 @@ def _gpu():
 def _bench_opts(B, prec):
     import bench
     args = types.SimpleNamespace(fp32_coarse=False, mg_stream=3, mg_tail=0, no_ew=False, kcycle_cgs1=False,
-                                 mg_kcycle=5, mg_smooth=2, mg_coarse=[2, 2], no_pc_lag=False, pc_lag_drift=0.05, mg_pdl=0)
+                                 mg_kcycle=5, mg_smooth=2, mg_coarse=[2, 2], no_pc_lag=False, pc_lag_drift=0.05, mg_pdl=0,
+                                 no_newton_rate_test=False)
     return bench.fom_opts(B, prec, args)
 
 

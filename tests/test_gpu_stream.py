@@ -135,3 +135,31 @@ def test_programmatic_dependent_launch_bit_identical(params):
     assert np.array_equal(cells[1].state(), cells[0].state())
     for cell in cells.values():
         cell.close()
+
+
+def test_newton_rate_test_same_solution(params):
+    """Stopping Newton once the error left after an update, estimated from the
+    contraction of two full steps, is below the tolerance (newton_rate_test =
+    1) skips the confirming iteration but not accuracy: over a 2C charge with
+    plating the states agree with update-based stopping to 1e-9 of each field
+    and 1e-10 of the cell potential (newton_tol 1e-10 in the scaled max-norm),
+    with no more Newton iterations."""
+    B, torch = _gpu()
+    lab = syn.full_cell(32, 32, 40, 16, 40, 0.35, 0.35, ("uniform", 2, 4), (11, 12))
+    cells = {q: B.Cell(lab, 1e-6, params, B.default_opts(precision=1, newton_tol=1e-10, krylov_rtol=1e-4,
+                                                         newton_rate_test=q)) for q in (0, 1)}
+    I = -2.0 * cells[0].i_1c
+    its = {0: 0, 1: 0}
+    for _ in range(4):
+        info = {q: cells[q].step(1.0, I) for q in cells}
+        for q in cells:
+            its[q] += info[q]["newton_its"]
+        assert abs(info[1]["V_cell"] - info[0]["V_cell"]) <= 1e-10 * abs(info[0]["V_cell"])
+    assert its[1] <= its[0]
+    u0, u1 = cells[0].state(), cells[1].state()
+    N = cells[0].N
+    for sl in (slice(0, N), slice(N, 2 * N), slice(2 * N, None)):
+        if np.max(np.abs(u0[sl])) > 0:
+            assert np.max(np.abs(u1[sl] - u0[sl])) <= 1e-9 * np.max(np.abs(u0[sl]))
+    for cell in cells.values():
+        cell.close()
