@@ -140,7 +140,10 @@ typedef struct {
                               relres the linear solve's relative residual (the scaled max-norm of
                               the convergence test), is below newton_tol: the iteration that would
                               only confirm a quadratically converged state is skipped; 0: only an
-                              update below newton_tol stops it */
+                              update below newton_tol stops it.  The reduced models built on this
+                              cell apply the same rule to their Newton iteration (ROM tolerance
+                              1e-12 in the step cap's scaled max-norm, LU or GMRES steps exact
+                              enough that the linear residual term is left out) */
 } mb_solver_opts;
 
 typedef struct {

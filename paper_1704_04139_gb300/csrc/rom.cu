@@ -137,6 +137,7 @@ struct RomWork {
     int* tcerr = nullptr;      // device: a bounded wait of the tcgen05 GEMM gave up
     bool graph_failed = false; // the graph could not be built: host-driven steps
     int g_tc = -1, g_ir = -1;  // the GEMM variant and escalation mode the graph was captured with
+    int g_rate = -1;           // and the Newton stopping rule (newton_rate_test)
     double* a_hold = nullptr;  // B x Nr: the state before the step (dt halving restarts from it)
     int* retry = nullptr;      // B: instances retaking the step with halved dt
     std::vector<double> hprm;  // host copy of the instance parameters (RP per instance)
@@ -1394,7 +1395,8 @@ k_rom_unorm(RomDev d, int B, const double* __restrict__ delta, const int* __rest
 __global__ void __launch_bounds__(32)
 k_rom_apply(RomDev d, int B, int nkt, double* __restrict__ a, const double* __restrict__ delta,
             const float* __restrict__ dpart, int* __restrict__ active, int* __restrict__ failed,
-            long long* __restrict__ its, int* __restrict__ pit, int* __restrict__ hp, float* __restrict__ dnprev) {
+            long long* __restrict__ its, int* __restrict__ pit, int* __restrict__ hp, float* __restrict__ dnprev,
+            int rate) {
     const int b = blockIdx.x, lane = threadIdx.x;
     if (!active[b]) return;
     float m = 0.f, mc = 0.f;
@@ -1423,8 +1425,13 @@ k_rom_apply(RomDev d, int B, int nkt, double* __restrict__ a, const double* __re
         const int k = ++pit[b];
         // converged: below the tolerance, or a full step below ROM_TOL_FLOOR that no
         // longer halves the previous update (the iteration has reached the rounding
-        // floor of the reconstruction; Newton's own convergence is quadratic)
-        if (lam * dv <= ROM_TOL || (lam == 1.0 && dv <= ROM_TOL_FLOOR && k >= 2 && mc >= 0.5f * dnprev[b]))
+        // floor of the reconstruction; Newton's own convergence is quadratic), or
+        // (rate) a full step after a full step whose estimated remaining error
+        // rho / (1 - rho) dv, rho = dv / dv_prev < 0.5, is below the tolerance
+        const double dvp = (double)dnprev[b];
+        const bool by_rate = rate && lam == 1.0 && k >= 2 && dvp <= ROM_DELTA_MAX && dv < 0.5 * dvp &&
+                             dv / (dvp - dv) * dv <= ROM_TOL;
+        if (lam * dv <= ROM_TOL || (lam == 1.0 && dv <= ROM_TOL_FLOOR && k >= 2 && mc >= 0.5f * dnprev[b]) || by_rate)
             active[b] = 0;
         if (k >= ROM_HP_AFTER || (k >= 3 && lam == 1.0 && mc > 0.9f * dnprev[b])) hp[b] = 1;
         dnprev[b] = mc;
@@ -2200,7 +2207,7 @@ static void iter_main_c(mb_rom* R, cudaStream_t s) {
                                                                              w.dpart),
         count_launch(c);
     k_rom_apply<<<(unsigned)B, 32, 0, s>>>(d, B, (int)nkt, w.a, w.delta, w.dpart, w.active, w.failed, w.its, w.pit,
-                                           w.hp, w.dnprev), count_launch(c);
+                                           w.hp, w.dnprev, R->cell->opt.newton_rate_test), count_launch(c);
     k_rom_count_hp<<<1, 256, 0, s>>>(B, w.active, w.hp, w.counts, w.hplist, w.alist), count_launch(c);
 }
 
@@ -2418,14 +2425,15 @@ static int rom_graph_build(mb_rom* R) {
 int rom_batch_step(mb_rom* R) {
     RomWork& w = R->w;
     if (R->d.graph && !w.graph_failed) {
-        if (w.gexec && (w.g_tc != R->d.tc || w.g_ir != R->d.ir)) {   // captured with other kernels
-            cudaGraphExecDestroy(w.gexec);
+        if (w.gexec && (w.g_tc != R->d.tc || w.g_ir != R->d.ir || w.g_rate != R->cell->opt.newton_rate_test)) {
+            cudaGraphExecDestroy(w.gexec);   // captured with other kernels or arguments
             w.gexec = nullptr;
         }
         if (!w.gexec) {
             if (rom_graph_build(R)) w.graph_failed = true;
             w.g_tc = R->d.tc;
             w.g_ir = R->d.ir;
+            w.g_rate = R->cell->opt.newton_rate_test;
         }
         if (w.gexec) {
             MB_CUDA(cudaGraphLaunch(w.gexec, R->cell->stream));
