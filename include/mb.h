@@ -68,7 +68,8 @@ typedef struct {
 
 typedef struct {
     int    precision;      /* MB_PREC_FP64 or MB_PREC_MIXED */
-    double newton_tol;     /* stop when lam*||delta||_s <= tol (scaled max-norm) */
+    double newton_tol;     /* stop when lam*||delta||_s <= tol (scaled max-norm), or when the
+                              estimated remaining error is (newton_rate_test) */
     int    newton_maxit;   /* per active-set pass */
     int    gmres_m;        /* FGMRES restart length */
     int    krylov_maxit;   /* per Newton iteration */
@@ -133,7 +134,9 @@ typedef struct {
     int    mg_pdl;         /* 1: the kernels of a preconditioner application are launched with
                               programmatic dependent launch: each may be scheduled while its
                               predecessor drains and waits, before its first memory access, until
-                              that predecessor has completed (same results); 0: plain launches */
+                              that predecessor has completed (same results); 0 (default): plain
+                              launches, measured faster on GB300 inside the captured graph (111.4
+                              against 112.2 ms per step on a 4.2M-voxel cell) */
     int    newton_rate_test; /* 1 (default): a Newton solve also stops when the error left after the
                               current update, estimated from two consecutive full steps as
                               (rho / (1 - rho) + relres) |d_k| with rho = |d_k| / |d_k-1| < 0.5 and
