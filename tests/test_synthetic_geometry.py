@@ -77,3 +77,22 @@ def test_full_cell_layout_and_connectivity():
     assert np.array_equal(lab, again)
     other = syn.full_cell(ny, nz, na, ns, nc, 0.35, 0.30, ("uniform", 2, 4), (23, 22))
     assert not np.array_equal(lab, other)
+
+
+def test_half_cell_layout():
+    """The half cell of the paper's experiment: CN | graphite in electrolyte |
+    separator | Li foil | CP, every pore reaching the separator, every graphite
+    cluster touching CN, the anode porosity within 0.05 of the request."""
+    ny = nz = 20
+    na, ns, nf = 12, 4, 2
+    lab = syn.half_cell(ny, nz, na, ns, nf, 0.35, ("uniform", 2, 4), 62)
+    assert lab.shape == (na + ns + nf + 2, ny, nz)
+    assert np.all(lab[0] == geo.CN) and np.all(lab[-1] == geo.CP)
+    assert np.all(lab[1 + na:1 + na + ns] == geo.E)
+    assert np.all(lab[1 + na + ns:1 + na + ns + nf] == geo.L)
+    assert set(np.unique(lab[1:1 + na])) <= {geo.E, geo.G}
+    comp, n = _components(lab == geo.E)
+    assert set(np.unique(comp[1 + na:1 + na + ns])) - {0} == set(range(1, n + 1))
+    comp, n = _components((lab == geo.G) | (lab == geo.CN))
+    assert set(np.unique(comp[lab == geo.G])) - {0} <= set(np.unique(comp[lab == geo.CN])) - {0}
+    assert abs(np.mean(lab[1:1 + na] == geo.E) - 0.35) <= 0.05
