@@ -45,9 +45,35 @@ def test_binding_declares_every_symbol(libpath):
 
 
 def test_default_options_roundtrip(libpath):
+    """The library's defaults are the ones include/mb.h documents."""
     from paper_1704_04139_gb300 import binding
     o = binding.default_opts()
     assert o.precision == binding.PREC_FP64 and o.gmres_m > 0 and o.newton_tol > 0
+    want = dict(mg_kcycle=5, mg_coarse_pre=2, mg_coarse_post=2, mg_bf16=1, mg_stream=3, pass_start=1,
+                mg_kcycle_reorth=1, krylov_forcing=1, mg_tail=0, pc_lag=1, mg_pdl=0, newton_rate_test=1)
+    for k, v in want.items():
+        assert getattr(o, k) == v, k
+    assert o.pc_lag_drift == 0.05
+
+
+@pytest.mark.parametrize("field,bad", [("mg_stream", 4), ("mg_tail", 17), ("mg_tail", -1), ("pc_lag", 2),
+                                       ("pc_lag_drift", -0.1), ("pc_lag_drift", float("nan")), ("mg_pdl", 2),
+                                       ("newton_rate_test", 2), ("krylov_forcing", 2), ("mg_kcycle", 0),
+                                       ("mg_kcycle", 17), ("gmres_m", 64), ("newton_tol", 0.0),
+                                       ("mg_coarse_pre", 5), ("precision", 2)])
+def test_create_rejects_bad_options_without_gpu(libpath, field, bad):
+    """Every option is range-checked before any device call."""
+    import numpy as np
+    import synthetic
+    from paper_1704_04139_gb300 import binding
+    p = binding.params_from_dict(synthetic.load_params())
+    lab = synthetic.slab_1d([4, 1, 0, 2, 5], 2, 2)
+    o = binding.default_opts(**{field: bad})
+    h = ctypes.c_void_p()
+    rc = binding.lib().mb_cell_create(lab.ctypes.data_as(ctypes.c_void_p), lab.shape[0], 2, 2, 1e-6,
+                                      ctypes.byref(p), ctypes.byref(o), ctypes.byref(h))
+    assert rc == binding.MB_EINVAL
+    assert b"solver options" in binding.lib().mb_last_error()
 
 
 def test_create_rejects_bad_arguments_without_gpu(libpath):
