@@ -206,7 +206,7 @@ int mb_cell_create(const uint8_t* labels, int nt, int ny, int nz, double h, cons
 }
 
 int mb_cell_destroy(mb_cell* c) {
-    if (!c) return MB_EINVAL;
+    if (!c) { set_error("mb_cell_destroy: invalid argument"); return MB_EINVAL; }
     if (c->stream) cudaStreamSynchronize(c->stream);
     free_cell(c);
     return MB_OK;

@@ -2498,7 +2498,7 @@ extern "C" int mb_rom_block_dims(mb_rom* R, int* n_c, int* n_n, int* n_phi) {
 }
 
 extern "C" int mb_rom_destroy(mb_rom* R) {
-    if (!R) return MB_EINVAL;
+    if (!R) { set_error("mb_rom_destroy: invalid argument"); return MB_EINVAL; }
     rom_work_free(R->w);
     for (void* p : R->est.bufs) cudaFree(p);
     for (void* p : R->owned) cudaFree(p);

@@ -310,7 +310,7 @@ extern "C" int mb_serve_poll(mb_server* S, uint64_t ticket, mb_result* out) {
 }
 
 extern "C" int mb_serve_destroy(mb_server* S) {
-    if (!S) return MB_EINVAL;
+    if (!S) { set_error("mb_serve_destroy: invalid argument"); return MB_EINVAL; }
     {
         std::lock_guard<std::mutex> lk(S->m);
         S->stop = true;

@@ -133,3 +133,22 @@ def test_host_eigensolver_rejects_bad_arguments(libpath):
     rc = binding.lib().mb_debug_symeig(0, w.ctypes.data_as(ctypes.c_void_p), w.ctypes.data_as(ctypes.c_void_p),
                                        w.ctypes.data_as(ctypes.c_void_p))
     assert rc == binding.MB_EINVAL
+
+
+@pytest.mark.parametrize("name,args", [
+    ("mb_cell_destroy", (None,)), ("mb_cell_info_get", (None, None)), ("mb_cell_set_scales", (None, 1.0, 1.0)),
+    ("mb_cell_set_opts", (None, None)), ("mb_state_get", (None, None)), ("mb_state_set", (None, None)),
+    ("mb_step", (None, 1.0, 0.0, None)), ("mb_adapt_reset", (None,)),
+    ("mb_residual", (None, None, None, None, 1.0, 0.0, None)),
+    ("mb_rom_solve_batch", (None, 1, None, 1, 1.0, None, None, None, None)), ("mb_rom_dims", (None, None, None, None)),
+    ("mb_rom_destroy", (None,)), ("mb_rom_basis", (None, None)), ("mb_serve_create", (None, None)),
+    ("mb_serve_submit", (None, None, None)), ("mb_serve_poll", (None, 0, None)), ("mb_serve_destroy", (None,)),
+    ("mb_prof_enable", (None, 1)), ("mb_launch_count", (None, None)), ("mb_cell_stream", (None, None)),
+    ("mb_residual_dev_noalloc", (None, None, None, 1.0, 0.0, None, None))])
+def test_null_arguments_are_rejected_with_a_message(libpath, name, args):
+    """A null handle or pointer gives MB_EINVAL and a message naming the call,
+    before any device work."""
+    from paper_1704_04139_gb300 import binding
+    rc = getattr(binding.lib(), name)(*args)
+    assert rc == binding.MB_EINVAL
+    assert binding.lib().mb_last_error().decode().startswith(name)
