@@ -235,7 +235,10 @@ def oracle_sample(labels, params, crate_sign, nsteps=1):
 
 
 def run_reference(args):
-    rank, local, ws, dist = _dist()
+    # the oracle runs on the host cores: no process group, no device; under
+    # torchrun rank 0 alone runs it and the other ranks exit without work
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     import synthetic as syn
