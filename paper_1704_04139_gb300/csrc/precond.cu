@@ -1322,7 +1322,6 @@ __global__ void k_lvl_smooth2(Level L, float omega, DF4* __restrict__ x_out, int
 __global__ void __launch_bounds__(256, 5) k_lvl_smooth_o5(Level L, const DF4* __restrict__ x_in,
                                                            const DF4* __restrict__ ec, int ccny, int ccnz,
                                                            float omega, DF4* __restrict__ x_out) {
-    pdl_entry();
     int64_t cell = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (cell >= L.cells) return;
     smooth_cell<true>(L, x_in, ec, ccny, ccnz, omega, x_out, cell);
@@ -1840,7 +1839,7 @@ int precond_setup(mb_cell* c, const float* u32, const uint8_t* gate, double dt) 
 }
 
 // launch of a kernel of the application: plain, or (mg_pdl) with programmatic
-// stream serialization; every kernel launched here starts with pdl_entry()
+// stream serialization; every kernel launched through here starts with pdl_entry()
 template <typename... KArgs, typename... Args>
 static void klaunch(const mb_cell* c, void (*k)(KArgs...), dim3 g, dim3 b, size_t smem, cudaStream_t s,
                     Args... args) {
@@ -1874,7 +1873,10 @@ static void lvl_smooth(mb_cell* c, Level& L, const DF4* xin, const DF4* ec, int 
     if (p->b16 && c->opt.mg_stream == 2 && xin && ntiles >= p->nsm && !g_staged_broken.load())
         k_lvl_smooth_staged<<<p->nsm, SWT, SW_SMEM, s>>>(L, xin, ec, ccny, ccnz, OMEGA_COARSE, xout, p->err);
     else if (p->b16 && c->opt.mg_stream == 3 && &L == &p->lv[1])
-        klaunch(c, k_lvl_smooth_o5, g, 256, 0, s, L, xin, ec, ccny, ccnz, OMEGA_COARSE, xout);
+        // always a plain launch (the kernel has no programmatic-launch entry: it
+        // starts after its predecessor completes, and a programmatically launched
+        // successor waits for its completion)
+        k_lvl_smooth_o5<<<g, 256, 0, s>>>(L, xin, ec, ccny, ccnz, OMEGA_COARSE, xout);
     else if (p->b16)
         klaunch(c, k_lvl_smooth<true>, g, 256, 0, s, L, xin, ec, ccny, ccnz, OMEGA_COARSE, xout,
                 c->opt.mg_stream == 1 ? p->pf[0] : 0);
