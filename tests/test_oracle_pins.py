@@ -307,3 +307,17 @@ def test_adaptive_step_controller(params):
     r1, _ = cell.step_adaptive(r0, None, None, 2.0, 0.0, tol=1e-6)
     r2, i3 = cell.step_adaptive(r1, r0, 2.0, 2.0, 0.0, tol=1e-6, dt_max=3.0)
     assert i3["err"] == 0.0 and i3["dt_next"] == 3.0
+
+
+def test_open_circuit_potentials_are_monotone(params):
+    """The project's placeholder open-circuit potentials (the paper prints
+    none) are strictly decreasing in the lithiation x on (0, 1), graphite within
+    0.1-0.8 V and the cathode within 3.5-4.4 V, so that the full cell's
+    open-circuit voltage is monotone in its state of charge."""
+    from oracle.fom import ocp
+    x = np.linspace(0.001, 0.999, 2000)
+    for key, lo, hi in (("G", 0.1, 0.8), ("K", 3.5, 4.4)):
+        a = params[key]["ocp"]
+        u = np.array([ocp(v, a) for v in x])
+        assert np.all(np.diff(u) < 0), key
+        assert lo <= u.min() and u.max() <= hi, key
